@@ -1,0 +1,357 @@
+"""Seeded synthetic problems shaped like the paper's bundle-adjustment workloads.
+
+This module only synthesises scenes: camera placements, 3-D points, which camera
+sees which point, measurement noise, outliers and the initial perturbation of the
+state.  To produce observations it renders the ground-truth scene through its own
+forward camera model (a world simulator, written here independently of both the
+optimiser and the oracle).  It holds no part of the optimiser: no residual
+Jacobians, no normal equations, no linear solver, no update rule.  It is imported
+by the tests, the benchmark and the oracle checks alike; neither the oracle nor the
+CUDA path imports the other.
+
+Camera convention (the Bundle Adjustment in the Large format the paper evaluates
+on, Sec. V): a camera is the 9-vector [w, t, f, k1, k2] with w an angle-axis
+rotation; a world point X maps to P = R(w) X + t, p = -P_xy / P_z (P_z < 0 in
+front), u = f (1 + k1 |p|^2 + k2 |p|^4) p.
+
+Random numbers come from counter-based SplitMix64 streams (Steele, Lea and Flood,
+"Fast splittable pseudorandom number generators", OOPSLA 2014), so one seed gives
+the same bytes on every machine and numpy version.  Normals use the Box-Muller
+transform.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function applied elementwise to a uint64 array."""
+    z = np.atleast_1d(np.asarray(x, dtype=np.uint64)).copy()
+    z ^= z >> np.uint64(30)
+    z *= _MIX1
+    z ^= z >> np.uint64(27)
+    z *= _MIX2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+class Stream:
+    """One counter-based random stream, keyed by (seed, stream id).
+
+    Draw i of the stream is splitmix64(key + (i + 1) * golden), exactly the
+    SplitMix64 sequence started from state `key`.
+    """
+
+    def __init__(self, seed: int, stream: int):
+        base = splitmix64(np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))
+        self.key = splitmix64(base + np.array([stream], dtype=np.uint64) * _GOLDEN)[0]
+        self.counter = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        idx = np.arange(self.counter + 1, self.counter + n + 1, dtype=np.uint64)
+        self.counter += n
+        return splitmix64(self.key + idx * _GOLDEN)
+
+    def uniform(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        """n doubles uniform on [lo, hi) with 53 random bits each."""
+        u = (self.u64(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        return lo + (hi - lo) * u
+
+    def normal(self, n: int, sigma: float = 1.0) -> np.ndarray:
+        m = (n + 1) // 2
+        u1 = 1.0 - self.uniform(m)  # (0, 1]
+        u2 = self.uniform(m)
+        rad = np.sqrt(-2.0 * np.log(u1))
+        z = np.concatenate([rad * np.cos(2.0 * np.pi * u2), rad * np.sin(2.0 * np.pi * u2)])
+        return sigma * z[:n]
+
+    def integers(self, n: int, lo: int, hi: int) -> np.ndarray:
+        """n integers uniform on [lo, hi)."""
+        return (lo + np.floor(self.uniform(n) * (hi - lo))).astype(np.int64)
+
+    def unit_vectors(self, n: int) -> np.ndarray:
+        v = self.normal(3 * n).reshape(n, 3)
+        return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+# --------------------------------------------------------------------------
+# rotation helpers of the world simulator (frame <-> quaternion <-> angle-axis)
+# --------------------------------------------------------------------------
+
+def _quat_from_matrix(R: np.ndarray) -> np.ndarray:
+    """Unit quaternions (w, x, y, z) from rotation matrices (n,3,3), Shepperd's method."""
+    n = R.shape[0]
+    q = np.empty((n, 4))
+    tr = R[:, 0, 0] + R[:, 1, 1] + R[:, 2, 2]
+    cand = np.stack([tr, R[:, 0, 0], R[:, 1, 1], R[:, 2, 2]], axis=1)
+    k = np.argmax(cand, axis=1)
+    for case in range(4):
+        m = k == case
+        if not np.any(m):
+            continue
+        Rm = R[m]
+        if case == 0:
+            s = 2.0 * np.sqrt(1.0 + tr[m])
+            q[m, 0] = 0.25 * s
+            q[m, 1] = (Rm[:, 2, 1] - Rm[:, 1, 2]) / s
+            q[m, 2] = (Rm[:, 0, 2] - Rm[:, 2, 0]) / s
+            q[m, 3] = (Rm[:, 1, 0] - Rm[:, 0, 1]) / s
+        elif case == 1:
+            s = 2.0 * np.sqrt(1.0 + Rm[:, 0, 0] - Rm[:, 1, 1] - Rm[:, 2, 2])
+            q[m, 0] = (Rm[:, 2, 1] - Rm[:, 1, 2]) / s
+            q[m, 1] = 0.25 * s
+            q[m, 2] = (Rm[:, 0, 1] + Rm[:, 1, 0]) / s
+            q[m, 3] = (Rm[:, 0, 2] + Rm[:, 2, 0]) / s
+        elif case == 2:
+            s = 2.0 * np.sqrt(1.0 + Rm[:, 1, 1] - Rm[:, 0, 0] - Rm[:, 2, 2])
+            q[m, 0] = (Rm[:, 0, 2] - Rm[:, 2, 0]) / s
+            q[m, 1] = (Rm[:, 0, 1] + Rm[:, 1, 0]) / s
+            q[m, 2] = 0.25 * s
+            q[m, 3] = (Rm[:, 1, 2] + Rm[:, 2, 1]) / s
+        else:
+            s = 2.0 * np.sqrt(1.0 + Rm[:, 2, 2] - Rm[:, 0, 0] - Rm[:, 1, 1])
+            q[m, 0] = (Rm[:, 1, 0] - Rm[:, 0, 1]) / s
+            q[m, 1] = (Rm[:, 0, 2] + Rm[:, 2, 0]) / s
+            q[m, 2] = (Rm[:, 1, 2] + Rm[:, 2, 1]) / s
+            q[m, 3] = 0.25 * s
+    q[q[:, 0] < 0] *= -1.0
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def _angle_axis_from_quat(q: np.ndarray) -> np.ndarray:
+    v = q[:, 1:]
+    s = np.linalg.norm(v, axis=1)
+    ang = 2.0 * np.arctan2(s, q[:, 0])
+    scale = np.where(s > 1e-12, ang / np.where(s > 1e-12, s, 1.0), 2.0)
+    return v * scale[:, None]
+
+
+def _look_frames(forward: np.ndarray) -> np.ndarray:
+    """World-to-camera rotations whose camera -z axis points along `forward` (n,3)."""
+    z = -forward / np.linalg.norm(forward, axis=1, keepdims=True)
+    up = np.tile(np.array([0.0, 0.0, 1.0]), (len(z), 1))
+    x = np.cross(up, z)
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    y = np.cross(z, x)
+    return np.stack([x, y, z], axis=1)  # rows are the camera axes in world coordinates
+
+
+def render(R: np.ndarray, t: np.ndarray, f: np.ndarray, k1: np.ndarray, k2: np.ndarray,
+           X: np.ndarray) -> np.ndarray:
+    """Noise-free pixel coordinates of points X (n,3) seen by cameras (R (n,3,3), t (n,3), ...)."""
+    Pc = np.einsum("nij,nj->ni", R, X) + t
+    p = -Pc[:, :2] / Pc[:, 2:3]
+    rr = np.sum(p * p, axis=1)
+    return (f * (1.0 + k1 * rr + k2 * rr * rr))[:, None] * p
+
+
+# --------------------------------------------------------------------------
+# bundle-adjustment problems
+# --------------------------------------------------------------------------
+
+@dataclass
+class BAProblem:
+    """A seeded synthetic BA problem.  Edge k observes point pt_idx[k] from camera cam_idx[k]."""
+    name: str
+    seed: int
+    cams_gt: np.ndarray   # (C, 9) float64  [w(3), t(3), f, k1, k2]
+    pts_gt: np.ndarray    # (P, 3) float64
+    cams0: np.ndarray     # (C, 9) initial state
+    pts0: np.ndarray      # (P, 3) initial state
+    cam_idx: np.ndarray   # (E,) int32
+    pt_idx: np.ndarray    # (E,) int32
+    obs: np.ndarray       # (E, 2) float64 pixels
+    is_outlier: np.ndarray  # (E,) bool
+    huber_delta: float | None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cams(self) -> int:
+        return self.cams_gt.shape[0]
+
+    @property
+    def n_pts(self) -> int:
+        return self.pts_gt.shape[0]
+
+    @property
+    def n_edges(self) -> int:
+        return self.cam_idx.shape[0]
+
+
+def _intrinsics(rng: Stream, n: int, k_sigma: float) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    f = 500.0 + rng.uniform(n, -10.0, 10.0)
+    k1 = rng.normal(n, k_sigma)
+    k2 = rng.normal(n, k_sigma)
+    return f, k1, k2
+
+
+def _observe(rng_noise: Stream, R, t, f, k1, k2, X, cam_idx, pt_idx, pixel_sigma,
+             outlier_frac, outlier_range, block=4_000_000):
+    E = cam_idx.shape[0]
+    obs = np.empty((E, 2))
+    for s in range(0, E, block):
+        c = cam_idx[s:s + block]
+        p = pt_idx[s:s + block]
+        obs[s:s + block] = render(R[c], t[c], f[c], k1[c], k2[c], X[p])
+    noise = rng_noise.normal(2 * E, pixel_sigma).reshape(E, 2)
+    if outlier_frac > 0:
+        is_out = rng_noise.uniform(E) < outlier_frac
+        n_out = int(is_out.sum())
+        noise[is_out] = rng_noise.uniform(2 * n_out, -outlier_range, outlier_range).reshape(n_out, 2)
+    else:
+        is_out = np.zeros(E, dtype=bool)
+    return obs + noise, is_out
+
+
+def _perturb(rng: Stream, cams_gt, pts_gt, rot_noise, trans_noise, point_noise):
+    C, P = cams_gt.shape[0], pts_gt.shape[0]
+    cams0 = cams_gt.copy()
+    # rotation noise of magnitude rot_noise about a uniformly random axis, added in the
+    # angle-axis chart; translation and point noise are isotropic Gaussians
+    cams0[:, 0:3] += rot_noise * rng.unit_vectors(C)
+    cams0[:, 3:6] += rng.normal(3 * C, trans_noise).reshape(C, 3)
+    pts0 = pts_gt + rng.normal(3 * P, point_noise).reshape(P, 3)
+    return cams0, pts0
+
+
+def ba_ring(seed: int, n_cams: int = 10, n_pts: int = 500, views: int = 6, radius: float = 15.0,
+            pixel_sigma: float = 1.0, rot_noise: float = 0.02, trans_noise: float = 0.05,
+            point_noise: float = 0.1, k_sigma: float = 1e-3, outlier_frac: float = 0.0,
+            huber_delta: float | None = None, name: str = "ba_ring") -> BAProblem:
+    """Cameras on a ring of `radius` looking at the origin; points uniform in [-5, 5]^3;
+    every point seen by `views` distinct random cameras."""
+    if views > n_cams:
+        raise ValueError("views must not exceed n_cams")
+    rng_geo, rng_vis = Stream(seed, 1), Stream(seed, 2)
+    rng_noise, rng_init = Stream(seed, 3), Stream(seed, 4)
+    phi = 2.0 * np.pi * np.arange(n_cams) / n_cams + rng_geo.uniform(n_cams, -0.1, 0.1)
+    centers = np.stack([radius * np.cos(phi), radius * np.sin(phi),
+                        rng_geo.uniform(n_cams, -2.0, 2.0)], axis=1)
+    R = _look_frames(-centers)
+    t = -np.einsum("nij,nj->ni", R, centers)
+    f, k1, k2 = _intrinsics(rng_geo, n_cams, k_sigma)
+    X = rng_geo.uniform(3 * n_pts, -5.0, 5.0).reshape(n_pts, 3)
+    keys = rng_vis.uniform(n_pts * n_cams).reshape(n_pts, n_cams)
+    chosen = np.argsort(keys, axis=1, kind="stable")[:, :views]
+    pt_idx = np.repeat(np.arange(n_pts), views).astype(np.int32)
+    cam_idx = chosen.reshape(-1).astype(np.int32)
+    order = np.argsort(cam_idx, kind="stable")       # file order: grouped by camera
+    cam_idx, pt_idx = cam_idx[order], pt_idx[order]
+    obs, is_out = _observe(rng_noise, R, t, f, k1, k2, X, cam_idx, pt_idx, pixel_sigma,
+                           outlier_frac, 50.0)
+    w = _angle_axis_from_quat(_quat_from_matrix(R))
+    cams_gt = np.concatenate([w, t, f[:, None], k1[:, None], k2[:, None]], axis=1)
+    cams0, pts0 = _perturb(rng_init, cams_gt, X, rot_noise, trans_noise, point_noise)
+    return BAProblem(name, seed, cams_gt, X, cams0, pts0, cam_idx, pt_idx, obs, is_out,
+                     huber_delta, dict(kind="ring", views=views, pixel_sigma=pixel_sigma))
+
+
+def _pareto_alpha(lo: int, hi: int, mean: float) -> float:
+    k = np.arange(lo, hi + 1, dtype=np.float64)
+    a, b = 0.0, 10.0
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        w = k ** (-m)
+        if (k * w).sum() / w.sum() > mean:
+            a = m
+        else:
+            b = m
+    return 0.5 * (a + b)
+
+
+def track_lengths(rng: Stream, n: int, law: str) -> np.ndarray:
+    """Track lengths (views per point).
+
+    'pareto': discrete power law P(L=k) ~ k^-a on [2, 40] with mean 6.
+    'geom':   L = 2 + G, G geometric on {0, 1, ...} with mean 4.5 (mean L = 6.5), capped at 200.
+    """
+    u = rng.uniform(n)
+    if law == "pareto":
+        k = np.arange(2, 41)
+        w = k ** (-_pareto_alpha(2, 40, 6.0))
+        cdf = np.cumsum(w / w.sum())
+        return k[np.minimum(np.searchsorted(cdf, u, side="right"), len(k) - 1)].astype(np.int64)
+    if law == "geom":
+        q = 4.5 / 5.5
+        g = np.floor(np.log1p(-u) / np.log(q)).astype(np.int64)
+        return np.minimum(2 + g, 200)
+    raise ValueError(law)
+
+
+def ba_path(seed: int, n_cams: int, n_pts: int, law: str = "pareto", spacing: float = 0.1,
+            pixel_sigma: float = 1.0, rot_noise: float = 0.02, trans_noise: float = 0.05,
+            point_noise: float = 0.1, k_sigma: float = 1e-3, outlier_frac: float = 0.01,
+            huber_delta: float | None = 2.0, name: str = "ba_path") -> BAProblem:
+    """Cameras along a smooth random path, looking sideways; each point is anchored at a
+    random camera at depth U[2, 20] and seen by a window of consecutive cameras around
+    the anchor (spatial locality), with track lengths drawn from `law`."""
+    rng_geo, rng_vis = Stream(seed, 11), Stream(seed, 12)
+    rng_noise, rng_init = Stream(seed, 13), Stream(seed, 14)
+    s = np.arange(n_cams) / max(n_cams, 1)
+    amp = rng_geo.uniform(3, 0.1, 0.4)
+    cyc = rng_geo.integers(3, 1, 5)
+    ph = rng_geo.uniform(3, 0.0, 2.0 * np.pi)
+    heading = sum(amp[i] * np.sin(2.0 * np.pi * cyc[i] * s + ph[i]) for i in range(3))
+    tang = np.stack([-np.sin(heading), np.cos(heading), np.zeros(n_cams)], axis=1)
+    centers = np.cumsum(spacing * tang, axis=0)
+    centers[:, 2] = 0.5 * np.sin(2.0 * np.pi * 2.0 * s + ph[0])
+    fwd = np.stack([np.cos(heading), np.sin(heading), np.zeros(n_cams)], axis=1)
+    R = _look_frames(fwd)
+    t = -np.einsum("nij,nj->ni", R, centers)
+    f, k1, k2 = _intrinsics(rng_geo, n_cams, k_sigma)
+
+    anchor = rng_vis.integers(n_pts, 0, n_cams)
+    L = np.minimum(track_lengths(rng_vis, n_pts, law), n_cams)
+    depth = rng_vis.uniform(n_pts, 2.0, 20.0)
+    lat = rng_vis.uniform(n_pts, -0.4, 0.4) * depth
+    up = rng_vis.uniform(n_pts, -0.3, 0.3) * depth
+    X = centers[anchor] + depth[:, None] * fwd[anchor] + lat[:, None] * tang[anchor]
+    X[:, 2] += up
+    start = np.clip(anchor - L // 2, 0, n_cams - L)
+
+    E0 = int(L.sum())
+    pt_e = np.repeat(np.arange(n_pts, dtype=np.int64), L)
+    first = np.repeat(np.cumsum(L) - L, L)
+    cam_e = np.repeat(start, L) + (np.arange(E0, dtype=np.int64) - first)
+    keep = np.einsum("ni,ni->n", X[pt_e] - centers[cam_e], fwd[cam_e]) >= 0.5
+    pt_e, cam_e = pt_e[keep], cam_e[keep]
+    cnt = np.bincount(pt_e, minlength=n_pts)
+    good = cnt >= 2
+    new_id = np.cumsum(good) - 1
+    sel = good[pt_e]
+    pt_e, cam_e = new_id[pt_e[sel]], cam_e[sel]
+    X = X[good]
+    order = np.argsort(cam_e, kind="stable")         # file order: grouped by camera
+    cam_idx = cam_e[order].astype(np.int32)
+    pt_idx = pt_e[order].astype(np.int32)
+    obs, is_out = _observe(rng_noise, R, t, f, k1, k2, X, cam_idx, pt_idx, pixel_sigma,
+                           outlier_frac, 50.0)
+    w = _angle_axis_from_quat(_quat_from_matrix(R))
+    cams_gt = np.concatenate([w, t, f[:, None], k1[:, None], k2[:, None]], axis=1)
+    cams0, pts0 = _perturb(rng_init, cams_gt, X, rot_noise, trans_noise, point_noise)
+    return BAProblem(name, seed, cams_gt, X, cams0, pts0, cam_idx, pt_idx, obs, is_out,
+                     huber_delta, dict(kind="path", law=law, pixel_sigma=pixel_sigma))
+
+
+# Workload presets (sizes of the paper-shaped synthetic inputs).
+def ba_tiny(seed: int = 0, **kw) -> BAProblem:
+    """10 cameras, 500 points, 6 views per point (3,000 observations); no outliers."""
+    return ba_ring(seed, 10, 500, 6, name="ba_tiny_c10_p500", **kw)
+
+
+def ba_medium(seed: int = 1, **kw) -> BAProblem:
+    """1,000 cameras, 500,000 points, 2-40 views per point (mean 6, ~3M observations),
+    1% outliers at U[-50, 50] px, Huber delta 2."""
+    return ba_path(seed, 1000, 500_000, "pareto", name="ba_medium_c1000_p500k", **kw)
+
+
+def ba_large(seed: int = 2, **kw) -> BAProblem:
+    """13,000 cameras, 4.5M points, geometric tracks (mean 6.5, max 200, ~29M observations),
+    1% outliers, Huber delta 2."""
+    return ba_path(seed, 13_000, 4_500_000, "geom", name="ba_large_c13000_p4500k", **kw)
