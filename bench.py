@@ -1,0 +1,294 @@
+"""Benchmark: Levenberg-Marquardt iterations per second on the medium synthetic BA
+workload (1,000 cameras, 500,000 points, ~3.0M observations, 1% outliers, Huber
+delta 2, PCG <= 100 iterations at 1e-6 relative tolerance), mixed precision.
+
+One step = one LM iteration of the whole hot path: edge linearisation, point and
+camera accumulation, camera Schur complement, block-Jacobi PCG on it, point
+back-substitution, FP64 retraction, FP64 candidate cost and the FP64 gain-ratio
+decision.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp64]
+                    [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (exact Schur + dense Cholesky LM) on a
+bounded sub-problem of the same workload.  Under torchrun every rank solves its own
+replica (independent problems: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ba_medium_c1000_p500k_e3M_huber2_outliers1pct"
+METRIC = "LM iter/s"
+
+
+def _cpu_sample_worker(seed: int, ncam: int, iters: int) -> None:
+    """Times the oracle on the first `ncam` cameras' closed sub-problem (runs in a
+    child process with single-threaded BLAS)."""
+    import numpy as np
+
+    from oracle import lm as olm
+    from paper_2509_26581_gb300 import synth
+
+    p = synth.ba_medium(seed)
+    keep = np.ones(p.n_pts, bool)
+    keep[p.pt_idx[p.cam_idx >= ncam]] = False
+    sel = keep[p.pt_idx]
+    pts = np.nonzero(keep)[0]
+    newid = -np.ones(p.n_pts, np.int64)
+    newid[pts] = np.arange(len(pts))
+    prob = olm.ba_problem(p.cams0[:ncam], p.pts0[pts], p.cam_idx[sel], newid[p.pt_idx[sel]],
+                          p.obs[sel], huber_delta=p.huber_delta)
+    t0 = time.perf_counter()
+    olm.levenberg_marquardt(prob, iters)
+    dt = time.perf_counter() - t0
+    print(json.dumps(dict(seconds=dt, iters=iters, edges=int(sel.sum()), points=int(len(pts)),
+                          cams=ncam, full_edges=int(p.n_edges))))
+
+
+def cpu_baseline(seed: int, ncam: int = 80, iters: int = 2) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker",
+                        str(seed), str(ncam), str(iters)], capture_output=True, text=True, env=env,
+                       timeout=1200)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    # edge-proportional scaling to the full workload (favours the oracle: its dense
+    # Cholesky grows with the cube of the camera count)
+    value = d["iters"] / d["seconds"] * d["edges"] / d["full_edges"]
+    return dict(value=value, unit=METRIC, cores=1, kind="oracle",
+                sample=f"{d['iters']} FP64 oracle LM iterations on the closed sub-problem of the "
+                       f"first {d['cams']} cameras ({d['points']} points, {d['edges']} edges) in "
+                       f"{d['seconds']:.2f} s, scaled by edges to the {d['full_edges']}-edge workload")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        return dict(sm_mhz=sm[len(sm) // 2] if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def load_peaks() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def spmv_algorithmic_bytes(E: int, P: int, precision: str) -> float:
+    """Compulsory HBM bytes of one Schur-product launch: every stored Jacobian value
+    (24 per edge) and camera index once, and each point's damped inverse block."""
+    sJ = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    sA = 8 if precision == "fp64" else 4
+    return E * (24 * sJ + 4) + P * 6 * sA
+
+
+def run_ours(args, rank: int, world: int, dist) -> dict | None:
+    import numpy as np
+    import torch
+
+    from paper_2509_26581_gb300 import gpo, synth
+
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    p = synth.ba_medium(args.seed)
+    params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
+                             args.precision, device=dev, stream=stream.cuda_stream)
+    g.optimize(args.warmup, params)               # also freezes the topology and plans memory
+    torch.cuda.synchronize()
+    g.set_profiling(True)
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rep = g.optimize(args.steps, params)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = g.profile()
+    hist = g.history()
+    if dist:
+        import torch.distributed as tdist
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = int(sum(v["launches"] for v in prof.values()))
+
+    # end to end through the public API with host buffers: every step copies the
+    # state in from pinned host memory, runs one LM iteration and reads the state back
+    g.set_profiling(False)
+    cams_h = torch.from_numpy(np.ascontiguousarray(g.get_state(c0, p.n_cams, 9))).pin_memory()
+    pts_h = torch.from_numpy(np.ascontiguousarray(g.get_state(p0, p.n_pts, 3))).pin_memory()
+    out_c = torch.empty_like(cams_h).pin_memory()
+    out_p = torch.empty_like(pts_h).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.set_initial(c0, cams_h.numpy())
+        g.set_initial(p0, pts_h.numpy())
+        g.optimize(1, params)
+        g.get_state(c0, p.n_cams, 9)
+        g.get_state(p0, p.n_pts, 3)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        import torch.distributed as tdist
+        t = torch.tensor([e2e_s], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        return None
+    sp = prof["spmv"]
+    peak, peak_kind = load_peaks()
+    alg = spmv_algorithmic_bytes(p.n_edges, p.n_pts, args.precision)
+    spmv_ms = sp["active_ms"] / max(1, sp["active"])
+    achieved = alg / (spmv_ms * 1e-3) / 1e9
+    state_bytes = (p.n_cams * 9 + p.n_pts * 3) * 8
+    pcg_iters = [h["pcg_iters"] for h in hist]
+    line = dict(
+        metric=METRIC, value=world * args.steps / (ms / 1e3), unit="LM iter/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype={"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
+        data="synthetic",
+        config=dict(workload=WORKLOAD, precision=args.precision, cameras=p.n_cams, points=p.n_pts,
+                    edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, seed=args.seed,
+                    l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
+                    parallelism=f"replicas x{world}"),
+        e2e=dict(value=world * args.steps / e2e_s, unit="LM iter/s", h2d_bytes_per_step=state_bytes,
+                 d2h_bytes_per_step=state_bytes),
+        gpu_launches=launches,
+        roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                      traffic=None, kernel="k_spmv (PCG Schur product)", peak_source=peak_kind,
+                      algorithmic_bytes=alg, avg_ms=spmv_ms),
+        clocks=clk,
+        pcg_iters_per_step=pcg_iters,
+        final_cost=rep.final_cost,
+        kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items()},
+        footprint_bytes=g.footprint(),
+    )
+    return line
+
+
+def run_reference(args, rank: int, world: int) -> dict | None:
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not needed
+    vals = []
+    base = None
+    for _ in range(max(1, args.steps)):
+        base = cpu_baseline(args.seed, ncam=40, iters=1)
+        vals.append(base["value"])
+    v = sum(vals) / len(vals)
+    return dict(metric=METRIC, value=v, unit="LM iter/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 / v, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, precision="fp64-oracle", seed=args.seed),
+                cpu_baseline=dict(kind="oracle", cores=1, sample=base["sample"], value=v, unit=METRIC),
+                e2e=dict(value=v, unit="LM iter/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--cpu-sample-worker":
+        _cpu_sample_worker(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line:
+            print(json.dumps(line))
+        return
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(args.seed)          # before any GPU work in this process
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_ours(args, rank, world, dist)
+    if line is not None:
+        if base is not None:
+            line["cpu_baseline"] = base
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

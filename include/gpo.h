@@ -1,0 +1,259 @@
+/*
+ * gpo.h -- C ABI of the GB300-native Levenberg-Marquardt graph optimiser.
+ *
+ * The library solves weighted nonlinear least squares over a hypergraph of
+ * vertices (parameter blocks) and edges (constraints):
+ *     argmin_x 1/2 sum_e rho(r_e(x)^T Omega_e r_e(x))            (Eq. 1, Eq. 7)
+ * with Levenberg-Marquardt (Eq. 3-6).  Each iteration linearises every edge,
+ * eliminates the 3-D points with a Schur complement, solves the reduced camera
+ * system by block-Jacobi preconditioned conjugate gradients without storing it
+ * (Sec. IV-E) and back-substitutes the points.  Vertices live in FP64; the
+ * linear system is FP64, FP32 or BF16 storage with FP32 accumulation (Sec. IV-E,
+ * Listing 3's Graph<FP, SP>).
+ *
+ * Conventions for every call:
+ *  - Return value: GPO_OK (0) or a negative gpo_status.  No C++ exception
+ *    crosses the ABI.  On error, gpo_last_error(g) gives a message; the graph
+ *    stays usable unless the status is GPO_ERR_CUDA.
+ *  - Host pointers are owned by the caller and only read or written during the
+ *    call.  Device pointers (on_device = 1) must be CUDA device memory of the
+ *    graph's device; copies run on the graph's stream and the call waits for them.
+ *  - All device memory of a graph is owned by the library (allocated through the
+ *    optional allocator hook of gpo_graph_desc) and released by gpo_graph_destroy.
+ *  - A graph is not thread-safe: one host thread at a time per graph.
+ *  - Vertex and edge ids are int64, assigned consecutively from 0 in the order
+ *    of the add calls (vertices and edges have separate counters).
+ */
+#ifndef GPO_H
+#define GPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpo_graph gpo_graph;
+
+typedef enum {
+  GPO_OK = 0,
+  GPO_ERR_ARG = -1,          /* invalid argument (null pointer, bad id, bad size, bad kind) */
+  GPO_ERR_OOM = -2,          /* device memory or the memory budget exhausted */
+  GPO_ERR_STATE = -3,        /* call not allowed in the graph's state (e.g. add after optimize) */
+  GPO_ERR_NUMERIC = -4,      /* non-finite cost at the initial state */
+  GPO_ERR_CUDA = -5,         /* a CUDA call failed; the message names it */
+  GPO_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+  GPO_ERR_UNSUPPORTED = -7   /* valid request that this build does not support */
+} gpo_status;
+
+/* Precision of the linear system (Listing 3: Graph<FP, SP>).  Vertex states, the
+ * retraction, the total cost and the gain ratio are always FP64. */
+typedef enum {
+  GPO_FP64 = 0,       /* Jacobians, Hessian blocks and PCG in FP64 */
+  GPO_FP32 = 1,       /* Jacobians, Hessian blocks and PCG in FP32 */
+  GPO_FP32_BF16 = 2   /* Jacobians stored in BF16, accumulation and PCG in FP32;
+                         gradient from the unrounded FP32 Jacobian; preconditioner
+                         and point-block inverses kept in FP32 (Sec. IV-E) */
+} gpo_precision;
+
+/* Vertex kinds (Listing 1's dimension = tangent block size; state size in brackets).
+ *  GPO_V_BA_CAMERA9: BAL camera [wx wy wz tx ty tz f k1 k2], tangent 9;
+ *                    rotation updated as w <- Log(Exp(dw) Exp(w)), rest additive.
+ *  GPO_V_POINT3:     3-D point [X Y Z], tangent 3, additive; eliminated by Schur. */
+enum { GPO_V_BA_CAMERA9 = 0, GPO_V_POINT3 = 1 };
+
+/* Edge kinds.
+ *  GPO_E_BA_REPROJ: 2-D reprojection (Eq. 7, Sec. V BAL problems).  Vertex ids per
+ *    edge: {camera, point}.  meas: 2 doubles [u v] (pixels).  Residual
+ *    r = f (1 + k1 |p|^2 + k2 |p|^4) p - meas with P = R(w) X + t, p = -P_xy / P_z. */
+enum { GPO_E_BA_REPROJ = 0 };
+
+enum { GPO_LOSS_NONE = 0, GPO_LOSS_HUBER = 1 };
+
+typedef struct {
+  int32_t precision;          /* gpo_precision */
+  int32_t device;             /* CUDA device ordinal */
+  int64_t reserve_vertices;   /* capacity hints (Listing 3/4: reserve); 0 = none */
+  int64_t reserve_edges;
+  void* cuda_stream;          /* cudaStream_t to run on; NULL = the library creates one */
+  /* Optional allocator hook for all device memory (e.g. a framework's caching
+   * allocator).  alloc returns device memory of at least `bytes` bytes aligned to
+   * 256 bytes, or NULL; free releases it.  NULL alloc = cudaMalloc / cudaFree. */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  size_t memory_budget;       /* bytes; 0 = unlimited.  Exceeding it gives GPO_ERR_OOM. */
+} gpo_graph_desc;
+
+/* Levenberg-Marquardt and PCG options (Listing 5: LevenbergMarquardtOptions and
+ * PCGSolver(max_it, tol, rejection_ratio)). */
+typedef struct {
+  double initial_damping;     /* lambda_0 (Listing 5 initial_damping); default 1e-4 */
+  double lambda_min;          /* damping clamp; default 1e-16 */
+  double lambda_max;          /* default 1e32 */
+  double diag_min;            /* D^T D = clamp(diag(H), diag_min, diag_max) (Sec. IV-E) */
+  double diag_max;            /* defaults 1e-6, 1e32 */
+  int32_t damping_mode;       /* 0 = clamped diag(H) (Marquardt), 1 = identity (Eq. 4) */
+  int32_t pcg_max_iters;      /* default 100 */
+  double pcg_tol;             /* default 1e-6 */
+  int32_t pcg_tol_relative;   /* 1: stop at |r| <= tol |g|; 0: stop at |r| <= tol */
+  double pcg_rejection_ratio; /* stop when |r_k| > ratio * min_j |r_j| and return the
+                                 best iterate; <= 0 or inf disables; default 10 */
+  int32_t pcg_normalize;      /* keep the PCG residual at unit norm each iteration
+                                 (Sec. IV-E); -1 = on for FP32/BF16, off for FP64 */
+  int32_t reserved0;
+} gpo_lm_params;
+
+typedef struct {
+  double initial_cost;        /* F(x_0) = 1/2 sum rho, FP64 */
+  double final_cost;          /* F at the returned state */
+  double final_lambda;
+  int32_t iterations;         /* LM iterations run (= max_iters) */
+  int32_t accepted;           /* accepted steps */
+  int32_t pcg_iters_total;
+  int32_t reserved0;
+} gpo_report;
+
+/* One LM iteration's record (gpo_get_history). */
+typedef struct {
+  double cost;                /* F(x) before the step */
+  double cand_cost;           /* F(x [+] dx) */
+  double model_decrease;      /* L(0) - L(dx) = -b^T dx - 1/2 |J dx|^2 */
+  double rho;                 /* gain ratio */
+  double lambda;              /* damping used for this step */
+  double pcg_residual;        /* final |r| / |g| of the PCG solve */
+  int32_t accepted;
+  int32_t pcg_iters;
+} gpo_iter_record;
+
+/* Defaults for the two option structs.  Never fail for non-null pointers. */
+gpo_status gpo_graph_desc_default(gpo_graph_desc* out);
+gpo_status gpo_lm_params_default(gpo_lm_params* out);
+
+/* Creates an empty graph (Listing 3: Graph<FP, SP> graph).  *out receives the handle.
+ * Errors: GPO_ERR_ARG (null, bad precision or device), GPO_ERR_CUDA. */
+gpo_status gpo_graph_create(const gpo_graph_desc* desc, gpo_graph** out);
+
+/* Releases the graph and all its device memory.  NULL is a no-op. */
+gpo_status gpo_graph_destroy(gpo_graph* g);
+
+/* Adds n vertices of `kind` (Listing 4: add_vertex).  block_size must equal the
+ * kind's tangent dimension (9 camera, 3 point).  *first_id (optional) receives the
+ * id of the first new vertex; the others follow consecutively.  Initial state is
+ * zero until gpo_set_initial.  Errors: GPO_ERR_ARG, GPO_ERR_STATE (after optimize). */
+gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int64_t n,
+                            int64_t* first_id);
+
+/* Adds n edges of `kind` (Listing 4: add_factor(ids, obs, precision, data, loss)).
+ *  vertex_ids: n * arity int64 ids, row-major, in the kind's slot order.
+ *  meas:       n * meas_len doubles (2 for GPO_E_BA_REPROJ).
+ *  info:       n * m * m doubles, row-major symmetric positive definite information
+ *              matrices Omega (m = residual size), or NULL for identity (Sec. IV-A:
+ *              a null precision matrix means identity).
+ *  loss_kind:  GPO_LOSS_NONE or GPO_LOSS_HUBER with threshold loss_delta > 0 in
+ *              whitened units (rho(s) = s for s <= delta^2, 2 delta sqrt(s) - delta^2
+ *              otherwise, Eq. 7).
+ * Errors: GPO_ERR_ARG (unknown ids, wrong vertex kinds, non-SPD info, delta <= 0),
+ *         GPO_ERR_STATE (after optimize). */
+gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* vertex_ids,
+                         const double* meas, const double* info, int32_t loss_kind,
+                         double loss_delta, int64_t* first_id);
+
+/* Fixes or frees a vertex (Listing 5: set_fixed).  A fixed vertex keeps its state
+ * bit for bit; its edges still constrain the other vertices.
+ * Errors: GPO_ERR_ARG, GPO_ERR_STATE (after the first optimize). */
+gpo_status gpo_set_fixed(gpo_graph* g, int64_t vertex_id, int32_t fixed);
+
+/* Enables or disables an edge (Listing 5: set_active).  A disabled edge contributes
+ * neither cost nor rows.  Errors: GPO_ERR_ARG, GPO_ERR_STATE (after the first optimize). */
+gpo_status gpo_set_edge_active(gpo_graph* g, int64_t edge_id, int32_t active);
+
+/* Sets the states of vertices first_id .. first_id + n - 1, which must all be of
+ * one kind, from `state` (n rows of the kind's state size, FP64).  on_device = 1:
+ * `state` is a device pointer.  Allowed before and between optimize calls.
+ * Errors: GPO_ERR_ARG, GPO_ERR_CUDA. */
+gpo_status gpo_set_initial(gpo_graph* g, int64_t first_id, int64_t n, const double* state,
+                           int32_t on_device);
+
+/* Runs max_iters Levenberg-Marquardt iterations (Listing 5: levenberg_marquardt).
+ * The first call freezes the topology (sorts edges point-major, plans and
+ * allocates device memory).  params NULL = defaults; out (optional) receives the
+ * report.  The damping and the state carry over to the next call only through
+ * the state: every call starts from params->initial_damping.
+ * Errors: GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_NUMERIC (non-finite initial cost),
+ *         GPO_ERR_UNSUPPORTED (a point seen more than the supported maximum of
+ *         times), GPO_ERR_CUDA. */
+gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* params,
+                        gpo_report* out);
+
+/* F(x) = 1/2 sum_e rho(s_e) at the current state, FP64 (Eq. 1, Eq. 7). */
+gpo_status gpo_get_cost(gpo_graph* g, double* cost);
+
+/* Copies the states of vertices first_id .. first_id + n - 1 (one kind) to `out`. */
+gpo_status gpo_get_state(gpo_graph* g, int64_t first_id, int64_t n, double* out,
+                         int32_t on_device);
+
+/* Copies up to `cap` per-iteration records of the last optimize; *n_out receives
+ * the number written. */
+gpo_status gpo_get_history(gpo_graph* g, gpo_iter_record* out, int32_t cap, int32_t* n_out);
+
+/* Device bytes held by the graph (planned arena plus state buffers). */
+gpo_status gpo_memory_footprint(gpo_graph* g, size_t* bytes);
+
+/* Per-kernel statistics of the kernels the library launches (gpo_get_profile). */
+typedef struct {
+  char name[32];              /* kernel class, e.g. "spmv" (the PCG Schur product) */
+  int64_t launches;           /* kernels launched since gpo_set_profiling (always counted) */
+  int64_t timed_launches;     /* launches bracketed by CUDA events (profiling on) */
+  int64_t active_launches;    /* timed launches that did work: a Schur-product launch after
+                                 its PCG solve stopped returns at once and is not active */
+  double total_ms;            /* summed event time of the timed launches */
+  double active_ms;           /* summed event time of the active launches */
+} gpo_kernel_profile;
+
+/* Resets the counters; enable = 1 also records a pair of CUDA events around every
+ * kernel launch on the graph's stream (timings for gpo_get_profile).  Waits for the
+ * stream.  Errors: GPO_ERR_ARG, GPO_ERR_CUDA. */
+gpo_status gpo_set_profiling(gpo_graph* g, int32_t enable);
+
+/* Writes up to `cap` per-kernel-class records (waits for the stream first);
+ * *n_out receives the number written. */
+gpo_status gpo_get_profile(gpo_graph* g, gpo_kernel_profile* out, int32_t cap, int32_t* n_out);
+
+/* Message of the last failed call on g (g may be NULL for creation errors).
+ * The pointer stays valid until the next call on g. */
+const char* gpo_last_error(const gpo_graph* g);
+
+/* Library version string, e.g. "gpo 0.1 sm_103a". */
+const char* gpo_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostic entry points (used by the parity tests; same kernels as optimize).
+ * ------------------------------------------------------------------------ */
+
+/* Linearises every edge at the current state in the graph's precision.
+ * r_out: n_edges * m doubles (whitened, Huber-weighted residual sqrt(rho') U r);
+ * J_out: n_edges * m * (sum of the edge's vertex tangent sizes) doubles, row-major
+ *        per residual row, vertex blocks in slot order, same weighting, as stored
+ *        (rounded to the storage precision).  Edge order = edge ids; disabled edges
+ *        are written as zeros.  Either pointer may be NULL. */
+gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out);
+
+/* Solves one damped system (H + lambda D^T D) dx = -b at the current state with
+ * the full path (Schur, PCG, back-substitution) and given PCG options, without
+ * changing the state.  dx_out: one row per vertex in id order, each of the
+ * vertex's tangent size (fixed vertices give zeros).  pcg_iters (optional). */
+gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* params,
+                          double* dx_out, int32_t* pcg_iters);
+
+/* Camera Schur blocks at damping lambda: S_out[C][9][9] the diagonal blocks
+ * S_cc = H_cc + lambda D_c - sum_p W H_pp^-1 W^T, g_out[C][9] the reduced right-hand
+ * side -b_c + sum_p W H_pp^-1 b_p, cameras in id order.  Either may be NULL. */
+gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* params,
+                           double* S_out, double* g_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPO_H */

@@ -1,0 +1,1082 @@
+// C ABI of libgpo: graph construction, topology finalisation and memory planning,
+// the Levenberg-Marquardt driver and the diagnostic entry points.
+//
+// Construction follows the paper's problem statement (Listings 3-5: descriptors
+// with reserve / add_vertex / add_factor, set_fixed / set_active, then
+// levenberg_marquardt(graph, options)); see include/gpo.h for the contract.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gpo.h"
+#include "gpo_internal.h"
+
+using gpo::DevBA;
+using gpo::Prec;
+using gpo::Scalars;
+
+// Per-kernel launch counts (always) and CUDA-event timings (when enabled) of the
+// kernels the library launches on the graph's stream.
+enum KernelKind {
+  KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
+  KK_PCG_VECTOR, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT, KK_COUNT
+};
+static const char* const kKernelNames[KK_COUNT] = {
+    "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
+    "pcg_vector", "backsub", "retract", "decide", "commit"};
+
+struct Profiler {
+  bool on = false;
+  int64_t launches[KK_COUNT] = {};
+  int64_t timed[KK_COUNT] = {};
+  int64_t active[KK_COUNT] = {};
+  double ms[KK_COUNT] = {};
+  double active_ms[KK_COUNT] = {};
+  struct Mark { int kind, lm_iter, pcg_k; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+struct gpo_graph {
+  gpo_graph_desc desc{};
+  Prec prec = Prec::F64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // vertices: global id -> (kind, index within kind)
+  std::vector<int8_t> v_kind;
+  std::vector<int64_t> v_local;
+  std::vector<double> cam_state;   // [C][9] (host copy until finalize)
+  std::vector<double> pt_state;    // [P][3]
+  std::vector<uint8_t> cam_fixed, pt_fixed;
+
+  // BA edges (global edge id = index)
+  std::vector<int32_t> e_cam, e_pt;
+  std::vector<double> e_obs;       // [E][2]
+  std::vector<double> e_sqinfo;    // [E][3] upper Cholesky factor, identity if no info
+  std::vector<double> e_delta;     // [E]
+  std::vector<uint8_t> e_active;
+  bool any_info = false;
+
+  // finalized topology
+  bool finalized = false;
+  int ch_max = 0;
+  std::vector<int64_t> sorted_edge;   // sorted position -> edge id
+  std::vector<int32_t> pt_new2old, pt_old2new;
+  std::vector<int32_t> h_ch_e0;
+  std::vector<long long> h_ch_j0;
+  size_t j_elems = 0;
+
+  // device
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  DevBA dev{};
+  Scalars* h_sc = nullptr;         // pinned
+  int* h_flag = nullptr;           // pinned [2]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<gpo::IterRecord> hist;
+  double last_cost = NAN;
+  bool cost_valid = false;
+  Profiler prof;
+  int cur_lm_iter = -1;
+  int cur_pcg_k = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+gpo_status fail(gpo_graph* g, gpo_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (g) g->err = buf;
+  else g_create_err = buf;
+  return st;
+}
+
+#define GPO_CUDA(g, call)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((g), GPO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)
+
+int tangent_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : 3; }
+int state_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : 3; }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device memory plan: requests are laid out in one arena (256-byte aligned).
+struct Plan {
+  struct Req { void** ptr; size_t bytes; };
+  std::vector<Req> reqs;
+  template <class T> void add(T** p, size_t count) { reqs.push_back({reinterpret_cast<void**>(p), count * sizeof(T)}); }
+  void add_raw(void** p, size_t bytes) { reqs.push_back({p, bytes}); }
+  size_t total() const {
+    size_t t = 0;
+    for (auto& r : reqs) t = align_up(t, 256) + align_up(r.bytes, 256);
+    return t;
+  }
+  void assign(char* base) const {
+    size_t t = 0;
+    for (auto& r : reqs) {
+      t = align_up(t, 256);
+      *r.ptr = base + t;
+      t += align_up(r.bytes, 256);
+    }
+  }
+};
+
+size_t at_size(Prec p) { return p == Prec::F64 ? 8 : 4; }
+size_t jt_size(Prec p) { return p == Prec::F64 ? 8 : (p == Prec::F32 ? 4 : 2); }
+
+void release_device(gpo_graph* g) {
+  if (g->arena) {
+    if (g->desc.alloc && g->desc.free) g->desc.free(g->arena, g->desc.alloc_ctx);
+    else cudaFree(g->arena);
+  }
+  g->arena = nullptr;
+  g->arena_bytes = 0;
+}
+
+template <class T>
+cudaError_t up(T* dst, const std::vector<T>& src, cudaStream_t st) {
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+__global__ void k_scatter_rows(double* dst, const double* src, const int32_t* idx, int n, int w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = idx ? idx[i] : i;
+  for (int k = 0; k < w; ++k) dst[(size_t)t * w + k] = src[(size_t)i * w + k];
+}
+__global__ void k_gather_rows(double* dst, const double* src, const int32_t* idx, int n, int w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = idx ? idx[i] : i;
+  for (int k = 0; k < w; ++k) dst[(size_t)i * w + k] = src[(size_t)t * w + k];
+}
+
+}  // namespace
+
+// ============================================================== topology
+
+static gpo_status finalize(gpo_graph* g) {
+  if (g->finalized) return GPO_OK;
+  const int C = (int)g->cam_fixed.size();
+  const int P = (int)g->pt_fixed.size();
+  const int64_t Eall = (int64_t)g->e_cam.size();
+  if (Eall > INT32_MAX / 2) return fail(g, GPO_ERR_UNSUPPORTED, "too many edges (%lld)", (long long)Eall);
+
+  // point order: by the smallest camera index among the point's active edges
+  // (points without active edges last), ties by point index.  Consecutive points
+  // then share cameras, which keeps the per-chunk camera slot count small.
+  std::vector<int32_t> key(P, C);
+  std::vector<int32_t> deg(P, 0);
+  for (int64_t e = 0; e < Eall; ++e)
+    if (g->e_active[e]) {
+      const int p = g->e_pt[e];
+      key[p] = std::min(key[p], g->e_cam[e]);
+      deg[p]++;
+    }
+  std::vector<int32_t> cnt(C + 2, 0);
+  for (int p = 0; p < P; ++p) cnt[key[p] + 1]++;
+  for (int k = 0; k <= C; ++k) cnt[k + 1] += cnt[k];
+  g->pt_new2old.assign(P, 0);
+  g->pt_old2new.assign(P, 0);
+  for (int p = 0; p < P; ++p) {
+    const int np = cnt[key[p]]++;
+    g->pt_new2old[np] = p;
+    g->pt_old2new[p] = np;
+  }
+  // edges: point-major (new point order), then edge id
+  std::vector<int32_t> pt_off(P + 1, 0);
+  for (int p = 0; p < P; ++p) pt_off[g->pt_old2new[p] + 1] = deg[p];
+  for (int p = 0; p < P; ++p) pt_off[p + 1] += pt_off[p];
+  const int E = pt_off[P];
+  int maxdeg = 0;
+  for (int p = 0; p < P; ++p) maxdeg = std::max(maxdeg, deg[p]);
+  g->sorted_edge.assign(E, 0);
+  {
+    std::vector<int32_t> fill(pt_off.begin(), pt_off.end() - 1);
+    for (int64_t e = 0; e < Eall; ++e)
+      if (g->e_active[e]) g->sorted_edge[fill[g->pt_old2new[g->e_pt[e]]]++] = e;
+  }
+  // chunk size
+  int ch = gpo::default_ch_max(g->prec);
+  while (ch < maxdeg) ch *= 2;
+  if (ch > gpo::max_supported_ch(g->prec))
+    return fail(g, GPO_ERR_UNSUPPORTED,
+                "a point has %d observations; this precision supports at most %d per point", maxdeg,
+                gpo::max_supported_ch(g->prec));
+  g->ch_max = ch;
+  // chunks of whole points, at most ch edges and ch points each
+  std::vector<int32_t> ch_e0{0}, ch_p0{0};
+  {
+    int ne = 0, np = 0;
+    for (int p = 0; p < P; ++p) {
+      const int L = pt_off[p + 1] - pt_off[p];
+      if (np > 0 && (ne + L > ch || np + 1 > ch)) {
+        ch_e0.push_back(pt_off[p]);
+        ch_p0.push_back(p);
+        ne = 0;
+        np = 0;
+      }
+      ne += L;
+      np += 1;
+    }
+    if (np > 0) {
+      ch_e0.push_back(E);
+      ch_p0.push_back(P);
+    }
+  }
+  const int NCH = (int)ch_e0.size() - 1;
+  // slots: distinct cameras per chunk, edges sorted by slot
+  std::vector<int32_t> e_cam_s(E), e_pt_s(E);
+  for (int i = 0; i < E; ++i) {
+    const int64_t e = g->sorted_edge[i];
+    e_cam_s[i] = g->e_cam[e];
+    e_pt_s[i] = g->pt_old2new[g->e_pt[e]];
+  }
+  std::vector<uint16_t> e_slot(E), ch_sorted(E);
+  std::vector<int32_t> ch_s0{0}, slot_e0, slot_cam;
+  std::vector<long long> ch_j0(NCH);
+  size_t jpos = 0;
+  {
+    std::vector<std::pair<int32_t, int32_t>> tmp;
+    for (int k = 0; k < NCH; ++k) {
+      const int e0 = ch_e0[k], n = ch_e0[k + 1] - e0;
+      tmp.resize(n);
+      for (int i = 0; i < n; ++i) tmp[i] = {e_cam_s[e0 + i], i};
+      std::sort(tmp.begin(), tmp.end());
+      int slot = -1, prev = -1;
+      for (int q = 0; q < n; ++q) {
+        if (tmp[q].first != prev) {
+          ++slot;
+          prev = tmp[q].first;
+          slot_e0.push_back(e0 + q);
+          slot_cam.push_back(prev);
+        }
+        e_slot[e0 + tmp[q].second] = (uint16_t)slot;
+        ch_sorted[e0 + q] = (uint16_t)tmp[q].second;
+      }
+      ch_s0.push_back((int)slot_cam.size());
+      ch_j0[k] = (long long)jpos;
+      jpos += (size_t)gpo::kJComp * gpo::pad8(n);
+    }
+    slot_e0.push_back(E);
+  }
+  const int NS = (int)slot_cam.size();
+  g->j_elems = jpos;
+  // per camera: its slots in chunk order
+  std::vector<int32_t> cam_s_off(C + 1, 0), cam_s_list(NS);
+  for (int s = 0; s < NS; ++s) cam_s_off[slot_cam[s] + 1]++;
+  for (int c = 0; c < C; ++c) cam_s_off[c + 1] += cam_s_off[c];
+  {
+    std::vector<int32_t> fill(cam_s_off.begin(), cam_s_off.end() - 1);
+    for (int s = 0; s < NS; ++s) cam_s_list[fill[slot_cam[s]]++] = s;
+  }
+  // per-edge data in sorted order
+  std::vector<double> obs_s(2 * (size_t)E), delta_s(E), info_s;
+  for (int i = 0; i < E; ++i) {
+    const int64_t e = g->sorted_edge[i];
+    obs_s[2 * i] = g->e_obs[2 * e];
+    obs_s[2 * i + 1] = g->e_obs[2 * e + 1];
+    delta_s[i] = g->e_delta[e];
+  }
+  if (g->any_info) {
+    info_s.resize(3 * (size_t)E);
+    for (int i = 0; i < E; ++i)
+      for (int k = 0; k < 3; ++k) info_s[3 * i + k] = g->e_sqinfo[3 * g->sorted_edge[i] + k];
+  }
+  std::vector<uint8_t> pt_fixed_s(P);
+  for (int p = 0; p < P; ++p) pt_fixed_s[g->pt_old2new[p]] = g->pt_fixed[p];
+
+  // ---- memory plan
+  const Prec pr = g->prec;
+  const size_t sA = at_size(pr), sJ = jt_size(pr);
+  DevBA d{};
+  d.C = C; d.P = P; d.E = E; d.NCH = NCH; d.NS = NS; d.ch_max = ch;
+  d.ncblk = std::max(1, (C + gpo::kCamPerBlock - 1) / gpo::kCamPerBlock);
+  const int nb_upd = std::max(1, (C + 255) / 256);
+  const int ncblk_max = std::max(d.ncblk, nb_upd);
+  Plan pl;
+  int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d;
+  long long* ch_j0_d;
+  uint16_t *e_slot_d, *ch_sorted_d;
+  uint8_t *cam_fixed_d, *pt_fixed_d;
+  double *obs_d, *delta_d, *info_d = nullptr;
+  pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, 2 * (size_t)E); pl.add(&delta_d, E);
+  if (g->any_info) pl.add(&info_d, 3 * (size_t)E);
+  pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
+  pl.add(&ch_s0_d, NCH + 1); pl.add(&ch_j0_d, std::max(NCH, 1)); pl.add(&e_slot_d, E);
+  pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
+  pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1));
+  pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
+  pl.add(&d.cam, 9 * (size_t)C); pl.add(&d.cam_cand, 9 * (size_t)C);
+  pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
+  pl.add(&d.pt, 3 * (size_t)P); pl.add(&d.pt_cand, 3 * (size_t)P);
+  pl.add_raw(&d.J, std::max<size_t>(jpos, 8) * sJ);
+  pl.add_raw(&d.Hpp, 6 * (size_t)P * sA); pl.add_raw(&d.bp, 3 * (size_t)P * sA);
+  pl.add_raw(&d.Hinv, 6 * (size_t)P * sA); pl.add_raw(&d.dp, 3 * (size_t)P * sA);
+  pl.add_raw(&d.partA, (size_t)gpo::kPartA * NS * sA); pl.add_raw(&d.partB, (size_t)gpo::kPartA * NS * sA);
+  pl.add_raw(&d.partV, 9 * (size_t)NS * sA);
+  pl.add_raw(&d.Hcl, 45 * (size_t)C * sA); pl.add_raw(&d.bc, 9 * (size_t)C * sA);
+  pl.add_raw(&d.S, 45 * (size_t)C * sA); pl.add_raw(&d.Minv, 45 * (size_t)C * sA);
+  pl.add_raw(&d.g, 9 * (size_t)C * sA);
+  pl.add_raw(&d.x, 9 * (size_t)C * sA); pl.add_raw(&d.r, 9 * (size_t)C * sA);
+  pl.add_raw(&d.z, 9 * (size_t)C * sA); pl.add_raw(&d.p, 9 * (size_t)C * sA);
+  pl.add_raw(&d.y, 9 * (size_t)C * sA); pl.add_raw(&d.xbest, 9 * (size_t)C * sA);
+  pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
+  pl.add(&d.cblk_part, 2 * (size_t)ncblk_max);
+  pl.add(&d.sc, 1);
+  pl.add(&d.hist, gpo::kMaxHistory);
+  const size_t bytes = pl.total();
+  if (g->desc.memory_budget && bytes > g->desc.memory_budget)
+    return fail(g, GPO_ERR_OOM, "graph needs %zu bytes of device memory, budget is %zu", bytes,
+                (size_t)g->desc.memory_budget);
+  void* base = nullptr;
+  if (g->desc.alloc && g->desc.free) {
+    base = g->desc.alloc(bytes, g->desc.alloc_ctx);
+    if (!base) return fail(g, GPO_ERR_OOM, "allocator hook returned NULL for %zu bytes", bytes);
+  } else {
+    const cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(g, GPO_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  g->arena = base;
+  g->arena_bytes = bytes;
+  pl.assign(static_cast<char*>(base));
+  d.e_cam = e_cam; d.e_pt = e_pt; d.obs = obs_d; d.e_delta = delta_d; d.e_sqinfo = info_d;
+  d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d; d.ch_j0 = ch_j0_d;
+  d.e_slot = e_slot_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
+  d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
+  d.dbg_r = nullptr;
+  cudaStream_t st = g->stream;
+  GPO_CUDA(g, up(e_cam, e_cam_s, st));
+  GPO_CUDA(g, up(e_pt, e_pt_s, st));
+  GPO_CUDA(g, up(obs_d, obs_s, st));
+  GPO_CUDA(g, up(delta_d, delta_s, st));
+  if (g->any_info) GPO_CUDA(g, up(info_d, info_s, st));
+  GPO_CUDA(g, up(pt_off_d, pt_off, st));
+  GPO_CUDA(g, up(ch_e0_d, ch_e0, st));
+  GPO_CUDA(g, up(ch_p0_d, ch_p0, st));
+  GPO_CUDA(g, up(ch_s0_d, ch_s0, st));
+  GPO_CUDA(g, up(ch_j0_d, ch_j0, st));
+  GPO_CUDA(g, up(e_slot_d, e_slot, st));
+  GPO_CUDA(g, up(ch_sorted_d, ch_sorted, st));
+  GPO_CUDA(g, up(slot_e0_d, slot_e0, st));
+  GPO_CUDA(g, up(slot_cam_d, slot_cam, st));
+  GPO_CUDA(g, up(cam_s_off_d, cam_s_off, st));
+  GPO_CUDA(g, up(cam_s_list_d, cam_s_list, st));
+  GPO_CUDA(g, up(cam_fixed_d, g->cam_fixed, st));
+  GPO_CUDA(g, up(pt_fixed_d, pt_fixed_s, st));
+  GPO_CUDA(g, up(d.cam, g->cam_state, st));
+  {
+    std::vector<double> pts(3 * (size_t)P);
+    for (int p = 0; p < P; ++p)
+      for (int k = 0; k < 3; ++k) pts[3 * (size_t)g->pt_old2new[p] + k] = g->pt_state[3 * (size_t)p + k];
+    GPO_CUDA(g, up(d.pt, pts, st));
+  }
+  GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(jpos, 8) * sJ, st));
+  GPO_CUDA(g, cudaMemsetAsync(d.sc, 0, sizeof(Scalars), st));
+  GPO_CUDA(g, cudaMemsetAsync(d.dp, 0, 3 * (size_t)P * sA, st));
+  GPO_CUDA(g, cudaStreamSynchronize(st));
+  g->h_ch_e0 = ch_e0;
+  g->h_ch_j0 = ch_j0;
+  g->dev = d;
+  g->finalized = true;
+  gpo::launch_cam_prepare(g->dev, false, st);
+  GPO_CUDA(g, cudaGetLastError());
+  return GPO_OK;
+}
+
+// ============================================================== profiling
+
+static cudaEvent_t prof_event(gpo_graph* g) {
+  Profiler& p = g->prof;
+  if (p.pool_used == p.pool.size()) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    p.pool.push_back(e);
+  }
+  return p.pool[p.pool_used++];
+}
+
+// Launches through f (which returns the number of kernels it launched), counting
+// launches and, if profiling is on, bracketing them with events.
+template <class F>
+static void run(gpo_graph* g, int kind, F&& f) {
+  Profiler& p = g->prof;
+  if (p.on) {
+    cudaEvent_t a = prof_event(g), b = prof_event(g);
+    cudaEventRecord(a, g->stream);
+    p.launches[kind] += f();
+    cudaEventRecord(b, g->stream);
+    p.marks.push_back({kind, g->cur_lm_iter, g->cur_pcg_k, a, b});
+  } else {
+    p.launches[kind] += f();
+  }
+}
+
+// Resolves the recorded events (after a stream sync).  A Schur-product launch is
+// active when its PCG iteration ran (iteration index <= that LM iteration's PCG
+// count); later launches of the look-ahead group return at once.
+static void prof_resolve(gpo_graph* g) {
+  Profiler& p = g->prof;
+  for (const auto& m : p.marks) {
+    float el = 0.f;
+    cudaEventElapsedTime(&el, m.a, m.b);
+    p.timed[m.kind]++;
+    p.ms[m.kind] += el;
+    bool act = true;
+    if (m.kind == KK_SPMV && m.lm_iter >= 0 && m.lm_iter < (int)g->hist.size())
+      act = m.pcg_k <= g->hist[m.lm_iter].pcg_iters;
+    if (act) {
+      p.active[m.kind]++;
+      p.active_ms[m.kind] += el;
+    }
+  }
+  p.marks.clear();
+  p.pool_used = 0;
+}
+
+// ============================================================== LM driver
+
+static void fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Scalars& s) {
+  std::memset(&s, 0, sizeof(s));
+  s.lambda = lambda;
+  s.nu = 2.0;
+  s.lambda_min = p.lambda_min;
+  s.lambda_max = p.lambda_max;
+  s.diag_min = p.diag_min;
+  s.diag_max = p.diag_max;
+  s.damping_mode = p.damping_mode;
+  s.need_lin = 1;
+  s.ratio = (p.pcg_rejection_ratio > 0.0 && std::isfinite(p.pcg_rejection_ratio)) ? p.pcg_rejection_ratio : 0.0;
+  s.pcg_tol = p.pcg_tol;
+  s.pcg_rel = p.pcg_tol_relative ? 1 : 0;
+  s.max_it = std::max(1, p.pcg_max_iters);
+  s.normalize = p.pcg_normalize < 0 ? (g->prec != Prec::F64 ? 1 : 0) : (p.pcg_normalize ? 1 : 0);
+  s.sigma = 1.0;
+  s.inv_n = 1.0;
+}
+
+static gpo_status upload_scalars(gpo_graph* g, const Scalars& s) {
+  *g->h_sc = s;
+  GPO_CUDA(g, cudaMemcpyAsync(g->dev.sc, g->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, g->stream));
+  // the pinned staging buffer is reused: make sure the copy has been consumed
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  return GPO_OK;
+}
+
+// PCG iterations with early exit: iterations are launched in groups; after each
+// group the done flag is copied back, and the flag of the previous group decides
+// whether to launch more (one group of look-ahead keeps the GPU busy).
+static gpo_status pcg_solve(gpo_graph* g, int max_it) {
+  const int kGroup = 8;
+  int launched = 0, slot = 0, pending = -1;
+  while (launched < max_it) {
+    const int n = std::min(kGroup, max_it - launched);
+    for (int i = 0; i < n; ++i) {
+      g->cur_pcg_k = launched + i + 1;
+      run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(g->dev, g->prec, g->stream); });
+      run(g, KK_PCG_VECTOR, [&] { return gpo::launch_pcg_vector(g->dev, g->prec, g->stream); });
+    }
+    launched += n;
+    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], &g->dev.sc->pcg_done, sizeof(int),
+                                cudaMemcpyDeviceToHost, g->stream));
+    GPO_CUDA(g, cudaEventRecord(g->ev[slot], g->stream));
+    if (pending >= 0) {
+      GPO_CUDA(g, cudaEventSynchronize(g->ev[pending]));
+      if (g->h_flag[pending]) break;
+    }
+    pending = slot;
+    slot ^= 1;
+  }
+  GPO_CUDA(g, cudaGetLastError());
+  return GPO_OK;
+}
+
+static gpo_status solve_system(gpo_graph* g, int max_it, bool force_lin) {
+  const DevBA& d = g->dev;
+  run(g, KK_LINEARIZE, [&] { gpo::launch_linearize(d, g->prec, force_lin, g->stream); return d.NCH ? 1 : 0; });
+  run(g, KK_SCHUR, [&] { gpo::launch_schur_prepare(d, g->prec, g->stream); return d.NCH ? 1 : 0; });
+  run(g, KK_CAM_FINALIZE, [&] { gpo::launch_cam_finalize(d, g->prec, g->stream); return 1; });
+  GPO_CUDA(g, cudaGetLastError());
+  gpo_status s = pcg_solve(g, max_it);
+  if (s != GPO_OK) return s;
+  g->cur_pcg_k = 0;
+  run(g, KK_BACKSUB, [&] { gpo::launch_backsub(d, g->prec, g->stream); return d.NCH ? 1 : 0; });
+  GPO_CUDA(g, cudaGetLastError());
+  return GPO_OK;
+}
+
+static gpo_status compute_cost(gpo_graph* g, double* out) {
+  const DevBA& d = g->dev;
+  run(g, KK_COST, [&] { gpo::launch_cost(d, false, g->stream); return d.NCH ? 1 : 0; });
+  run(g, KK_COST_REDUCE, [&] { gpo::launch_cost_init(d, g->stream); return 1; });
+  GPO_CUDA(g, cudaMemcpyAsync(g->h_sc, g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->stream));
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  *out = g->h_sc->cost;
+  return GPO_OK;
+}
+
+static gpo_lm_params params_or_default(const gpo_lm_params* p) {
+  gpo_lm_params d;
+  gpo_lm_params_default(&d);
+  return p ? *p : d;
+}
+
+// ============================================================== C ABI
+
+extern "C" {
+
+gpo_status gpo_graph_desc_default(gpo_graph_desc* out) {
+  if (!out) return GPO_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->precision = GPO_FP64;
+  return GPO_OK;
+}
+
+gpo_status gpo_lm_params_default(gpo_lm_params* out) {
+  if (!out) return GPO_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->initial_damping = 1e-4;
+  out->lambda_min = 1e-16;
+  out->lambda_max = 1e32;
+  out->diag_min = 1e-6;
+  out->diag_max = 1e32;
+  out->damping_mode = 0;
+  out->pcg_max_iters = 100;
+  out->pcg_tol = 1e-6;
+  out->pcg_tol_relative = 1;
+  out->pcg_rejection_ratio = 10.0;
+  out->pcg_normalize = -1;
+  return GPO_OK;
+}
+
+const char* gpo_version(void) { return "gpo 0.1 sm_103a"; }
+
+const char* gpo_last_error(const gpo_graph* g) { return g ? g->err.c_str() : g_create_err.c_str(); }
+
+gpo_status gpo_graph_create(const gpo_graph_desc* desc, gpo_graph** out) {
+  if (!desc || !out) return fail(nullptr, GPO_ERR_ARG, "null argument");
+  if (desc->precision < GPO_FP64 || desc->precision > GPO_FP32_BF16)
+    return fail(nullptr, GPO_ERR_ARG, "unknown precision %d", desc->precision);
+  if ((desc->alloc == nullptr) != (desc->free == nullptr))
+    return fail(nullptr, GPO_ERR_ARG, "alloc and free hooks must be given together");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || desc->device < 0 || desc->device >= ndev)
+    return fail(nullptr, GPO_ERR_CUDA, "no CUDA device %d (%s)", desc->device,
+                e != cudaSuccess ? cudaGetErrorString(e) : "out of range");
+  gpo_graph* g = new (std::nothrow) gpo_graph();
+  if (!g) return fail(nullptr, GPO_ERR_OOM, "host allocation failed");
+  g->desc = *desc;
+  g->prec = static_cast<Prec>(desc->precision);
+  e = cudaSetDevice(desc->device);
+  if (e == cudaSuccess) {
+    if (desc->cuda_stream) {
+      g->stream = static_cast<cudaStream_t>(desc->cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+      g->own_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_sc, sizeof(Scalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_flag, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    gpo_graph_destroy(g);
+    return fail(nullptr, GPO_ERR_CUDA, "graph setup failed: %s", cudaGetErrorString(e));
+  }
+  if (desc->reserve_vertices > 0) {
+    g->v_kind.reserve(desc->reserve_vertices);
+    g->v_local.reserve(desc->reserve_vertices);
+  }
+  if (desc->reserve_edges > 0) {
+    g->e_cam.reserve(desc->reserve_edges);
+    g->e_pt.reserve(desc->reserve_edges);
+    g->e_obs.reserve(2 * desc->reserve_edges);
+  }
+  *out = g;
+  return GPO_OK;
+}
+
+gpo_status gpo_graph_destroy(gpo_graph* g) {
+  if (!g) return GPO_OK;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  release_device(g);
+  if (g->h_sc) cudaFreeHost(g->h_sc);
+  if (g->h_flag) cudaFreeHost(g->h_flag);
+  for (auto& ev : g->prof.pool)
+    if (ev) cudaEventDestroy(ev);
+  for (auto& ev : g->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return GPO_OK;
+}
+
+gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int64_t n, int64_t* first_id) {
+  if (!g) return GPO_ERR_ARG;
+  if (g->finalized) return fail(g, GPO_ERR_STATE, "topology is frozen after the first optimize");
+  if (kind != GPO_V_BA_CAMERA9 && kind != GPO_V_POINT3) return fail(g, GPO_ERR_ARG, "unknown vertex kind %d", kind);
+  if (block_size != tangent_dim(kind))
+    return fail(g, GPO_ERR_ARG, "block size %d does not match kind %d (%d)", block_size, kind, tangent_dim(kind));
+  if (n < 0) return fail(g, GPO_ERR_ARG, "negative count");
+  const int64_t id0 = (int64_t)g->v_kind.size();
+  const int64_t loc0 = kind == GPO_V_BA_CAMERA9 ? (int64_t)g->cam_fixed.size() : (int64_t)g->pt_fixed.size();
+  if (loc0 + n > INT32_MAX / 16) return fail(g, GPO_ERR_UNSUPPORTED, "too many vertices of kind %d", kind);
+  g->v_kind.insert(g->v_kind.end(), n, (int8_t)kind);
+  for (int64_t i = 0; i < n; ++i) g->v_local.push_back(loc0 + i);
+  if (kind == GPO_V_BA_CAMERA9) {
+    g->cam_fixed.insert(g->cam_fixed.end(), n, 0);
+    g->cam_state.insert(g->cam_state.end(), 9 * n, 0.0);
+  } else {
+    g->pt_fixed.insert(g->pt_fixed.end(), n, 0);
+    g->pt_state.insert(g->pt_state.end(), 3 * n, 0.0);
+  }
+  if (first_id) *first_id = id0;
+  return GPO_OK;
+}
+
+gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* vertex_ids, const double* meas,
+                         const double* info, int32_t loss_kind, double loss_delta, int64_t* first_id) {
+  if (!g) return GPO_ERR_ARG;
+  if (g->finalized) return fail(g, GPO_ERR_STATE, "topology is frozen after the first optimize");
+  if (kind != GPO_E_BA_REPROJ) return fail(g, GPO_ERR_ARG, "unknown edge kind %d", kind);
+  if (n < 0 || (n > 0 && (!vertex_ids || !meas))) return fail(g, GPO_ERR_ARG, "null ids or measurements");
+  if (loss_kind != GPO_LOSS_NONE && loss_kind != GPO_LOSS_HUBER) return fail(g, GPO_ERR_ARG, "unknown loss %d", loss_kind);
+  if (loss_kind == GPO_LOSS_HUBER && !(loss_delta > 0.0 && std::isfinite(loss_delta)))
+    return fail(g, GPO_ERR_ARG, "Huber threshold must be positive and finite");
+  const int64_t V = (int64_t)g->v_kind.size();
+  const size_t base = g->e_cam.size();
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t c = vertex_ids[2 * i], p = vertex_ids[2 * i + 1];
+    if (c < 0 || c >= V || p < 0 || p >= V || g->v_kind[c] != GPO_V_BA_CAMERA9 || g->v_kind[p] != GPO_V_POINT3) {
+      g->e_cam.resize(base); g->e_pt.resize(base); g->e_obs.resize(2 * base);
+      g->e_delta.resize(base); g->e_active.resize(base); g->e_sqinfo.resize(3 * base);
+      return fail(g, GPO_ERR_ARG, "edge %lld: ids must be (camera, point)", (long long)i);
+    }
+    double u00 = 1.0, u01 = 0.0, u11 = 1.0;
+    if (info) {
+      // Omega = U^T U with U upper triangular: u00 = sqrt(a), u01 = b / u00, u11 = sqrt(d - u01^2)
+      const double a = info[4 * i], b = info[4 * i + 1], b2 = info[4 * i + 2], dd = info[4 * i + 3];
+      const double t = dd - (b / std::sqrt(a)) * (b / std::sqrt(a));
+      if (!(a > 0.0) || !(t > 0.0) || std::fabs(b - b2) > 1e-12 * (std::fabs(a) + std::fabs(dd))) {
+        g->e_cam.resize(base); g->e_pt.resize(base); g->e_obs.resize(2 * base);
+        g->e_delta.resize(base); g->e_active.resize(base); g->e_sqinfo.resize(3 * base);
+        return fail(g, GPO_ERR_ARG, "edge %lld: information matrix is not symmetric positive definite", (long long)i);
+      }
+      u00 = std::sqrt(a);
+      u01 = b / u00;
+      u11 = std::sqrt(t);
+      if (u00 != 1.0 || u01 != 0.0 || u11 != 1.0) g->any_info = true;
+    }
+    g->e_cam.push_back((int32_t)g->v_local[c]);
+    g->e_pt.push_back((int32_t)g->v_local[p]);
+    g->e_obs.push_back(meas[2 * i]);
+    g->e_obs.push_back(meas[2 * i + 1]);
+    g->e_sqinfo.push_back(u00);
+    g->e_sqinfo.push_back(u01);
+    g->e_sqinfo.push_back(u11);
+    g->e_delta.push_back(loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0);
+    g->e_active.push_back(1);
+  }
+  if (first_id) *first_id = (int64_t)base;
+  return GPO_OK;
+}
+
+gpo_status gpo_set_fixed(gpo_graph* g, int64_t vid, int32_t fixed) {
+  if (!g) return GPO_ERR_ARG;
+  if (g->finalized) return fail(g, GPO_ERR_STATE, "fixed flags are frozen after the first optimize");
+  if (vid < 0 || vid >= (int64_t)g->v_kind.size()) return fail(g, GPO_ERR_ARG, "no vertex %lld", (long long)vid);
+  if (g->v_kind[vid] == GPO_V_BA_CAMERA9) g->cam_fixed[g->v_local[vid]] = fixed ? 1 : 0;
+  else g->pt_fixed[g->v_local[vid]] = fixed ? 1 : 0;
+  return GPO_OK;
+}
+
+gpo_status gpo_set_edge_active(gpo_graph* g, int64_t eid, int32_t active) {
+  if (!g) return GPO_ERR_ARG;
+  if (g->finalized) return fail(g, GPO_ERR_STATE, "edge activity is frozen after the first optimize");
+  if (eid < 0 || eid >= (int64_t)g->e_cam.size()) return fail(g, GPO_ERR_ARG, "no edge %lld", (long long)eid);
+  g->e_active[eid] = active ? 1 : 0;
+  return GPO_OK;
+}
+
+static gpo_status check_range(gpo_graph* g, int64_t first, int64_t n, int* kind_out) {
+  if (n < 0 || first < 0 || first + n > (int64_t)g->v_kind.size())
+    return fail(g, GPO_ERR_ARG, "vertex range [%lld, %lld) out of bounds", (long long)first, (long long)(first + n));
+  if (n == 0) { *kind_out = -1; return GPO_OK; }
+  const int k = g->v_kind[first];
+  for (int64_t i = 1; i < n; ++i)
+    if (g->v_kind[first + i] != k) return fail(g, GPO_ERR_ARG, "vertex range mixes kinds");
+  // the range must also be contiguous in the kind's local numbering
+  if (g->v_local[first + n - 1] - g->v_local[first] != n - 1)
+    return fail(g, GPO_ERR_ARG, "vertex range is not contiguous within its kind");
+  *kind_out = k;
+  return GPO_OK;
+}
+
+gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double* state, int32_t on_device) {
+  if (!g) return GPO_ERR_ARG;
+  int kind;
+  gpo_status s = check_range(g, first, n, &kind);
+  if (s != GPO_OK || n == 0) return s;
+  if (!state) return fail(g, GPO_ERR_ARG, "null state");
+  const int w = state_dim(kind);
+  const int64_t loc = g->v_local[first];
+  g->cost_valid = false;
+  if (!g->finalized) {
+    std::vector<double>& dst = kind == GPO_V_BA_CAMERA9 ? g->cam_state : g->pt_state;
+    if (on_device) {
+      GPO_CUDA(g, cudaMemcpy(dst.data() + loc * w, state, n * w * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(dst.data() + loc * w, state, n * w * sizeof(double));
+    }
+    return GPO_OK;
+  }
+  cudaStream_t st = g->stream;
+  if (kind == GPO_V_BA_CAMERA9) {
+    GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * 9, state, n * 9 * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    gpo::launch_cam_prepare(g->dev, false, st);
+  } else {
+    // points live on the device in sorted order
+    int32_t* idx = nullptr;
+    double* tmp = nullptr;
+    GPO_CUDA(g, cudaMallocAsync(&idx, n * sizeof(int32_t), st));
+    GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
+    GPO_CUDA(g, cudaMemcpyAsync(idx, g->pt_old2new.data() + loc, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    GPO_CUDA(g, cudaMemcpyAsync(tmp, state, n * 3 * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    k_scatter_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(g->dev.pt, tmp, idx, (int)n, 3);
+    GPO_CUDA(g, cudaFreeAsync(idx, st));
+    GPO_CUDA(g, cudaFreeAsync(tmp, st));
+  }
+  GPO_CUDA(g, cudaStreamSynchronize(st));
+  return GPO_OK;
+}
+
+gpo_status gpo_get_state(gpo_graph* g, int64_t first, int64_t n, double* out, int32_t on_device) {
+  if (!g) return GPO_ERR_ARG;
+  int kind;
+  gpo_status s = check_range(g, first, n, &kind);
+  if (s != GPO_OK || n == 0) return s;
+  if (!out) return fail(g, GPO_ERR_ARG, "null output");
+  const int w = state_dim(kind);
+  const int64_t loc = g->v_local[first];
+  if (!g->finalized) {
+    const std::vector<double>& src = kind == GPO_V_BA_CAMERA9 ? g->cam_state : g->pt_state;
+    if (on_device) GPO_CUDA(g, cudaMemcpy(out, src.data() + loc * w, n * w * sizeof(double), cudaMemcpyHostToDevice));
+    else std::memcpy(out, src.data() + loc * w, n * w * sizeof(double));
+    return GPO_OK;
+  }
+  cudaStream_t st = g->stream;
+  if (kind == GPO_V_BA_CAMERA9) {
+    GPO_CUDA(g, cudaMemcpyAsync(out, g->dev.cam + loc * 9, n * 9 * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  } else {
+    int32_t* idx = nullptr;
+    double* tmp = nullptr;
+    GPO_CUDA(g, cudaMallocAsync(&idx, n * sizeof(int32_t), st));
+    GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
+    GPO_CUDA(g, cudaMemcpyAsync(idx, g->pt_old2new.data() + loc, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    k_gather_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(tmp, g->dev.pt, idx, (int)n, 3);
+    GPO_CUDA(g, cudaMemcpyAsync(out, tmp, n * 3 * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    GPO_CUDA(g, cudaFreeAsync(idx, st));
+    GPO_CUDA(g, cudaFreeAsync(tmp, st));
+  }
+  GPO_CUDA(g, cudaStreamSynchronize(st));
+  return GPO_OK;
+}
+
+gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* params, gpo_report* out) {
+  if (!g) return GPO_ERR_ARG;
+  if (max_iters < 0) return fail(g, GPO_ERR_ARG, "negative iteration count");
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  const gpo_lm_params prm = params_or_default(params);
+  if (!(prm.initial_damping > 0.0)) return fail(g, GPO_ERR_ARG, "initial damping must be positive");
+  Scalars sc;
+  fill_scalars(g, prm, prm.initial_damping, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
+  double F0;
+  if ((s = compute_cost(g, &F0)) != GPO_OK) return s;
+  if (!std::isfinite(F0)) return fail(g, GPO_ERR_NUMERIC, "initial cost is not finite (%g)", F0);
+  const DevBA& d = g->dev;
+  for (int it = 0; it < max_iters; ++it) {
+    g->cur_lm_iter = it;
+    if ((s = solve_system(g, sc.max_it, false)) != GPO_OK) return s;
+    run(g, KK_RETRACT, [&] { gpo::launch_retract(d, g->prec, g->stream); return (d.C ? 1 : 0) + (d.P ? 1 : 0); });
+    run(g, KK_COST, [&] { gpo::launch_cost(d, true, g->stream); return d.NCH ? 1 : 0; });
+    run(g, KK_DECIDE, [&] { gpo::launch_decide(d, g->prec, g->stream); return 1; });
+    run(g, KK_COMMIT, [&] { gpo::launch_commit(d, g->stream); return (d.C || d.P) ? 1 : 0; });
+    GPO_CUDA(g, cudaGetLastError());
+  }
+  g->cur_lm_iter = -1;
+  GPO_CUDA(g, cudaMemcpyAsync(g->h_sc, g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->stream));
+  const int nh = std::min(max_iters, gpo::kMaxHistory);
+  g->hist.resize(nh);
+  if (nh)
+    GPO_CUDA(g, cudaMemcpyAsync(g->hist.data(), g->dev.hist, nh * sizeof(gpo::IterRecord),
+                                cudaMemcpyDeviceToHost, g->stream));
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (g->prof.on) prof_resolve(g);
+  g->last_cost = g->h_sc->cost;
+  g->cost_valid = true;
+  if (out) {
+    out->initial_cost = F0;
+    out->final_cost = g->h_sc->cost;
+    out->final_lambda = g->h_sc->lambda;
+    out->iterations = g->h_sc->iter;
+    out->accepted = g->h_sc->n_accepted;
+    out->pcg_iters_total = g->h_sc->pcg_total;
+    out->reserved0 = 0;
+  }
+  return GPO_OK;
+}
+
+gpo_status gpo_get_cost(gpo_graph* g, double* cost) {
+  if (!g || !cost) return GPO_ERR_ARG;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  if (g->cost_valid) {
+    *cost = g->last_cost;
+    return GPO_OK;
+  }
+  gpo::launch_cam_prepare(g->dev, false, g->stream);
+  if ((s = compute_cost(g, cost)) != GPO_OK) return s;
+  g->last_cost = *cost;
+  g->cost_valid = true;
+  return GPO_OK;
+}
+
+gpo_status gpo_get_history(gpo_graph* g, gpo_iter_record* out, int32_t cap, int32_t* n_out) {
+  if (!g || (!out && cap > 0)) return GPO_ERR_ARG;
+  const int n = std::min<int>(cap, (int)g->hist.size());
+  for (int i = 0; i < n; ++i) {
+    const gpo::IterRecord& h = g->hist[i];
+    out[i].cost = h.cost;
+    out[i].cand_cost = h.cand_cost;
+    out[i].model_decrease = h.model_decrease;
+    out[i].rho = h.rho;
+    out[i].lambda = h.lambda;
+    out[i].pcg_residual = h.pcg_residual;
+    out[i].accepted = h.accepted;
+    out[i].pcg_iters = h.pcg_iters;
+  }
+  if (n_out) *n_out = n;
+  return GPO_OK;
+}
+
+gpo_status gpo_set_profiling(gpo_graph* g, int32_t enable) {
+  if (!g) return GPO_ERR_ARG;
+  if (g->stream) GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  Profiler& p = g->prof;
+  p.marks.clear();
+  p.pool_used = 0;
+  for (int k = 0; k < KK_COUNT; ++k) {
+    p.launches[k] = p.timed[k] = p.active[k] = 0;
+    p.ms[k] = p.active_ms[k] = 0.0;
+  }
+  p.on = enable != 0;
+  return GPO_OK;
+}
+
+gpo_status gpo_get_profile(gpo_graph* g, gpo_kernel_profile* out, int32_t cap, int32_t* n_out) {
+  if (!g || (!out && cap > 0)) return GPO_ERR_ARG;
+  if (g->stream) GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (!g->prof.marks.empty()) prof_resolve(g);
+  const int n = std::min<int>(cap, KK_COUNT);
+  for (int k = 0; k < n; ++k) {
+    std::memset(&out[k], 0, sizeof(out[k]));
+    std::snprintf(out[k].name, sizeof(out[k].name), "%s", kKernelNames[k]);
+    out[k].launches = g->prof.launches[k];
+    out[k].timed_launches = g->prof.timed[k];
+    out[k].active_launches = g->prof.active[k];
+    out[k].total_ms = g->prof.ms[k];
+    out[k].active_ms = g->prof.active_ms[k];
+  }
+  if (n_out) *n_out = n;
+  return GPO_OK;
+}
+
+gpo_status gpo_memory_footprint(gpo_graph* g, size_t* bytes) {
+  if (!g || !bytes) return GPO_ERR_ARG;
+  *bytes = g->arena_bytes;
+  return GPO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- diagnostics
+
+static double read_j(const std::vector<char>& raw, size_t i, Prec pr) {
+  if (pr == Prec::F64) return reinterpret_cast<const double*>(raw.data())[i];
+  if (pr == Prec::F32) return reinterpret_cast<const float*>(raw.data())[i];
+  const __nv_bfloat16 b = reinterpret_cast<const __nv_bfloat16*>(raw.data())[i];
+  uint16_t bits;
+  std::memcpy(&bits, &b, 2);
+  uint32_t f = (uint32_t)bits << 16;
+  float out;
+  std::memcpy(&out, &f, 4);
+  return out;
+}
+
+static double read_a(const std::vector<char>& raw, size_t i, Prec pr) {
+  return pr == Prec::F64 ? reinterpret_cast<const double*>(raw.data())[i]
+                         : (double)reinterpret_cast<const float*>(raw.data())[i];
+}
+
+template <class T>
+static gpo_status fetch(gpo_graph* g, std::vector<char>& dst, const T* src, size_t bytes) {
+  dst.resize(bytes);
+  if (bytes)
+    GPO_CUDA(g, cudaMemcpyAsync(dst.data(), src, bytes, cudaMemcpyDeviceToHost, g->stream));
+  return GPO_OK;
+}
+
+extern "C" {
+
+gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
+  if (!g) return GPO_ERR_ARG;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  const DevBA& d = g->dev;
+  double* dbg = nullptr;
+  GPO_CUDA(g, cudaMallocAsync(&dbg, std::max<size_t>(1, 2 * (size_t)d.E) * sizeof(double), g->stream));
+  DevBA dd = d;
+  dd.dbg_r = dbg;
+  Scalars sc;
+  gpo_lm_params prm;
+  gpo_lm_params_default(&prm);
+  fill_scalars(g, prm, prm.initial_damping, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
+  gpo::launch_cam_prepare(dd, false, g->stream);
+  gpo::launch_linearize(dd, g->prec, true, g->stream);
+  GPO_CUDA(g, cudaGetLastError());
+  std::vector<char> rraw, jraw;
+  if ((s = fetch(g, rraw, dbg, 2 * (size_t)d.E * sizeof(double))) != GPO_OK) return s;
+  if ((s = fetch(g, jraw, static_cast<const char*>(d.J), g->j_elems * jt_size(g->prec))) != GPO_OK) return s;
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  GPO_CUDA(g, cudaFreeAsync(dbg, g->stream));
+  const size_t Eall = g->e_cam.size();
+  if (r_out) std::fill(r_out, r_out + 2 * Eall, 0.0);
+  if (J_out) std::fill(J_out, J_out + 24 * Eall, 0.0);
+  const double* rv = reinterpret_cast<const double*>(rraw.data());
+  for (int k = 0; k < d.NCH; ++k) {
+    const int e0 = g->h_ch_e0[k], n = g->h_ch_e0[k + 1] - e0, ldt = gpo::pad8(n);
+    for (int i = 0; i < n; ++i) {
+      const int64_t id = g->sorted_edge[e0 + i];
+      if (r_out) {
+        r_out[2 * id] = rv[2 * (size_t)(e0 + i)];
+        r_out[2 * id + 1] = rv[2 * (size_t)(e0 + i) + 1];
+      }
+      if (J_out) {
+        const size_t b = (size_t)g->h_ch_j0[k];
+        for (int a = 0; a < 2; ++a) {
+          for (int j = 0; j < 9; ++j) J_out[24 * id + 12 * a + j] = read_j(jraw, b + (size_t)(9 * a + j) * ldt + i, g->prec);
+          for (int j = 0; j < 3; ++j) J_out[24 * id + 12 * a + 9 + j] = read_j(jraw, b + (size_t)(18 + 3 * a + j) * ldt + i, g->prec);
+        }
+      }
+    }
+  }
+  return GPO_OK;
+}
+
+gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* params, double* dx_out, int32_t* pcg_iters) {
+  if (!g || !dx_out) return GPO_ERR_ARG;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  const gpo_lm_params prm = params_or_default(params);
+  Scalars sc;
+  fill_scalars(g, prm, lambda, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
+  gpo::launch_cam_prepare(g->dev, false, g->stream);
+  if ((s = solve_system(g, sc.max_it, true)) != GPO_OK) return s;
+  const DevBA& d = g->dev;
+  const size_t sA = at_size(g->prec);
+  std::vector<char> sraw, xraw, xbraw, praw;
+  if ((s = fetch(g, sraw, reinterpret_cast<const char*>(d.sc), sizeof(Scalars))) != GPO_OK) return s;
+  if ((s = fetch(g, xraw, static_cast<const char*>(d.x), 9 * (size_t)d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, xbraw, static_cast<const char*>(d.xbest), 9 * (size_t)d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, praw, static_cast<const char*>(d.dp), 3 * (size_t)d.P * sA)) != GPO_OK) return s;
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  const Scalars* hs = reinterpret_cast<const Scalars*>(sraw.data());
+  const std::vector<char>& xs = hs->use_best ? xbraw : xraw;
+  if (pcg_iters) *pcg_iters = hs->pcg_it;
+  size_t off = 0;
+  for (size_t v = 0; v < g->v_kind.size(); ++v) {
+    const int64_t loc = g->v_local[v];
+    if (g->v_kind[v] == GPO_V_BA_CAMERA9) {
+      for (int k = 0; k < 9; ++k) dx_out[off + k] = g->cam_fixed[loc] ? 0.0 : read_a(xs, 9 * loc + k, g->prec);
+      off += 9;
+    } else {
+      const int np = g->pt_old2new[loc];
+      for (int k = 0; k < 3; ++k) dx_out[off + k] = g->pt_fixed[loc] ? 0.0 : read_a(praw, 3 * (size_t)np + k, g->prec);
+      off += 3;
+    }
+  }
+  return GPO_OK;
+}
+
+gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* params, double* S_out, double* g_out) {
+  if (!g) return GPO_ERR_ARG;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  const gpo_lm_params prm = params_or_default(params);
+  Scalars sc;
+  fill_scalars(g, prm, lambda, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
+  gpo::launch_cam_prepare(g->dev, false, g->stream);
+  gpo::launch_linearize(g->dev, g->prec, true, g->stream);
+  gpo::launch_schur_prepare(g->dev, g->prec, g->stream);
+  gpo::launch_cam_finalize(g->dev, g->prec, g->stream);
+  GPO_CUDA(g, cudaGetLastError());
+  const DevBA& d = g->dev;
+  const size_t sA = at_size(g->prec);
+  std::vector<char> Sraw, graw;
+  if ((s = fetch(g, Sraw, static_cast<const char*>(d.S), 45 * (size_t)d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, graw, static_cast<const char*>(d.g), 9 * (size_t)d.C * sA)) != GPO_OK) return s;
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  for (int c = 0; c < d.C; ++c) {
+    if (S_out)
+      for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+          const int t = i <= j ? i * 9 - (i * (i - 1)) / 2 + (j - i) : j * 9 - (j * (j - 1)) / 2 + (i - j);
+          S_out[81 * (size_t)c + 9 * i + j] = read_a(Sraw, 45 * (size_t)c + t, g->prec);
+        }
+    if (g_out)
+      for (int i = 0; i < 9; ++i) g_out[9 * (size_t)c + i] = read_a(graw, 9 * (size_t)c + i, g->prec);
+  }
+  return GPO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1311 @@
+// Bundle-adjustment hot path on sm_103a: edge linearisation, point and camera
+// accumulation, camera Schur complement, matrix-free block-Jacobi PCG, point
+// back-substitution, FP64 retraction, cost and the LM gain-ratio decision.
+//
+// Paper mapping: Eq. 1 and Eq. 7 (cost with Huber), Eq. 3-6 (LM normal equations),
+// Sec. IV-B (analytic Jacobians), Sec. IV-E (PCG on implicit products of the
+// Jacobians, block-Jacobi preconditioner kept at FP32 or higher, Hessian-diagonal
+// clamping, residual normalisation), Sec. IV-E last paragraph (kernels walk the
+// graph structure; no sparse-matrix format).  The PCG runs on the camera Schur
+// complement S = H_cc + lambda D_c - H_cp H_pp^-1 H_pc; its product with a vector is
+// formed from the stored Jacobians in one pass per chunk of point-major edges.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <type_traits>
+
+#include "gpo_internal.h"
+
+namespace gpo {
+
+// ---------------------------------------------------------------- numeric helpers
+
+template <class JT> struct AccOf { using T = float; };
+template <> struct AccOf<double> { using T = double; };
+
+__device__ __forceinline__ float ldj(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ldj(const float* p) { return *p; }
+__device__ __forceinline__ double ldj(const double* p) { return *p; }
+__device__ __forceinline__ __nv_bfloat16 cvj(float v, const __nv_bfloat16*) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float cvj(float v, const float*) { return v; }
+__device__ __forceinline__ double cvj(double v, const double*) { return v; }
+
+// Upper triangle of a 9x9 symmetric block, row-major: entry t is (c_ti[t], c_tj[t]).
+__constant__ unsigned char c_ti[kCamTri] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1,
+                                            2, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4,
+                                            4, 5, 5, 5, 5, 6, 6, 6, 7, 7, 8};
+__constant__ unsigned char c_tj[kCamTri] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 1, 2, 3, 4, 5, 6, 7, 8,
+                                            2, 3, 4, 5, 6, 7, 8, 3, 4, 5, 6, 7, 8, 4, 5, 6, 7,
+                                            8, 5, 6, 7, 8, 6, 7, 8, 7, 8, 8};
+__host__ __device__ __forceinline__ int tri9(int i, int j) {  // i <= j
+  return i * 9 - (i * (i - 1)) / 2 + (j - i);
+}
+__host__ __device__ __forceinline__ int sym9(int i, int j) { return i <= j ? tri9(i, j) : tri9(j, i); }
+
+// ---------------------------------------------------------------- SO(3) (FP64)
+
+// Rodrigues: R = I + a [w]_x + b [w]_x^2 with a = sin t / t, b = (1 - cos t)/t^2,
+// [w]_x^2 = w w^T - t^2 I; Taylor coefficients below t = 1e-4.
+__device__ void aa_to_R(const double* w, double* R) {
+  const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double a, b;
+  if (t2 < 1e-8) {
+    a = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+    b = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+  } else {
+    const double t = sqrt(t2);
+    double s, c;
+    sincos(t, &s, &c);
+    a = s / t;
+    b = (1.0 - c) / t2;
+  }
+  R[0] = 1.0 + b * (w[0] * w[0] - t2);
+  R[1] = -a * w[2] + b * w[0] * w[1];
+  R[2] = a * w[1] + b * w[0] * w[2];
+  R[3] = a * w[2] + b * w[1] * w[0];
+  R[4] = 1.0 + b * (w[1] * w[1] - t2);
+  R[5] = -a * w[0] + b * w[1] * w[2];
+  R[6] = -a * w[1] + b * w[2] * w[0];
+  R[7] = a * w[0] + b * w[2] * w[1];
+  R[8] = 1.0 + b * (w[2] * w[2] - t2);
+}
+
+// Unit quaternion (w, x, y, z) of an angle-axis vector.
+__device__ void aa_to_q(const double* w, double* q) {
+  const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double c, sdt;  // cos(t/2), sin(t/2)/t
+  if (t2 < 1e-8) {
+    c = 1.0 - t2 / 8.0 + t2 * t2 / 384.0;
+    sdt = 0.5 - t2 / 48.0 + t2 * t2 / 3840.0;
+  } else {
+    const double t = sqrt(t2);
+    double s;
+    sincos(0.5 * t, &s, &c);
+    sdt = s / t;
+  }
+  q[0] = c;
+  q[1] = sdt * w[0];
+  q[2] = sdt * w[1];
+  q[3] = sdt * w[2];
+}
+
+// Angle-axis of a unit quaternion, angle in [0, pi].
+__device__ void q_to_aa(const double* qin, double* w) {
+  double q0 = qin[0], q1 = qin[1], q2 = qin[2], q3 = qin[3];
+  if (q0 < 0) { q0 = -q0; q1 = -q1; q2 = -q2; q3 = -q3; }
+  const double s = sqrt(q1 * q1 + q2 * q2 + q3 * q3);
+  double k;
+  if (s < 1e-8) {
+    k = 2.0 / q0 * (1.0 - s * s / (3.0 * q0 * q0));   // 2 atan(s/q0)/s, series
+  } else {
+    k = 2.0 * atan2(s, q0) / s;
+  }
+  w[0] = k * q1;
+  w[1] = k * q2;
+  w[2] = k * q3;
+}
+
+// Left update w' = Log(Exp(dw) Exp(w)) via quaternion product.
+__device__ void aa_left_update(const double* dw, const double* w, double* out) {
+  double a[4], b[4], c[4];
+  aa_to_q(dw, a);
+  aa_to_q(w, b);
+  c[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  c[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  c[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  c[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+  const double n = 1.0 / sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + c[3] * c[3]);
+  c[0] *= n; c[1] *= n; c[2] *= n; c[3] *= n;
+  q_to_aa(c, out);
+}
+
+// ---------------------------------------------------------------- BA edge model
+
+// Camera render block rb[16]: R (row-major, 9), t (3), f, k1, k2, pad.
+struct Geom {
+  double y[3];   // R X
+  double P[3];   // R X + t
+  double p[2];   // -P_xy / P_z
+  double iz;     // 1 / P_z
+  double r2, d;  // |p|^2, 1 + k1 r2 + k2 r2^2
+  double u[2];   // f d p
+};
+
+__device__ __forceinline__ void load_rb(const double* __restrict__ src, double* rb) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const double2 v = __ldg(s2 + i);
+    rb[2 * i] = v.x;
+    rb[2 * i + 1] = v.y;
+  }
+}
+
+__device__ __forceinline__ void ba_geom(const double* rb, const double* X, Geom& g) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    g.y[i] = rb[3 * i] * X[0] + rb[3 * i + 1] * X[1] + rb[3 * i + 2] * X[2];
+    g.P[i] = g.y[i] + rb[9 + i];
+  }
+  g.iz = 1.0 / g.P[2];
+  g.p[0] = -g.P[0] * g.iz;
+  g.p[1] = -g.P[1] * g.iz;
+  g.r2 = g.p[0] * g.p[0] + g.p[1] * g.p[1];
+  g.d = 1.0 + rb[13] * g.r2 + rb[14] * g.r2 * g.r2;
+  const double fd = rb[12] * g.d;
+  g.u[0] = fd * g.p[0];
+  g.u[1] = fd * g.p[1];
+}
+
+// Whitened residual, squared norm, Huber value and sqrt of the first-order weight.
+struct Robust {
+  double r[2];   // whitened residual U (u - z)
+  double rho;    // rho(s)
+  double sw;     // sqrt(rho'(s))
+};
+
+__device__ __forceinline__ void ba_residual(const DevBA& d, int e, const Geom& g, Robust& o) {
+  const double2 z = __ldg(reinterpret_cast<const double2*>(d.obs) + e);
+  double r0 = g.u[0] - z.x, r1 = g.u[1] - z.y;
+  if (d.e_sqinfo) {
+    const double* U = d.e_sqinfo + 3 * (size_t)e;
+    const double a = U[0] * r0 + U[1] * r1;
+    r1 = U[2] * r1;
+    r0 = a;
+  }
+  o.r[0] = r0;
+  o.r[1] = r1;
+  const double s = r0 * r0 + r1 * r1;
+  const double delta = __ldg(d.e_delta + e);
+  if (delta > 0.0 && s > delta * delta) {
+    const double sq = sqrt(s);
+    o.rho = 2.0 * delta * sq - delta * delta;
+    o.sw = sqrt(delta / sq);
+  } else {
+    o.rho = s;
+    o.sw = 1.0;
+  }
+}
+
+// Jacobian rows of the residual on the chart (left rotation update, additive rest):
+// Jc (2x9) and Jp (2x3), whitened and scaled by sqrt(rho').  Computed in AT from
+// the FP64 geometry.
+template <class AT>
+__device__ __forceinline__ void ba_jacobian(const DevBA& d, int e, const double* rb, const Geom& g,
+                                            double sw, AT (&Jc)[2][9], AT (&Jp)[2][3]) {
+  const AT f = (AT)rb[12], k1 = (AT)rb[13], k2 = (AT)rb[14];
+  const AT p0 = (AT)g.p[0], p1 = (AT)g.p[1], r2 = (AT)g.r2, dd = (AT)g.d, iz = (AT)g.iz;
+  const AT c2 = (AT)2 * k1 + (AT)4 * k2 * r2;
+  // du/dp = f (d I + c2 p p^T)
+  const AT A00 = f * (dd + c2 * p0 * p0), A01 = f * c2 * p0 * p1, A11 = f * (dd + c2 * p1 * p1);
+  // dp/dP = [[-iz, 0, -p0 iz], [0, -iz, -p1 iz]]  (P_x / P_z^2 = -p0 / P_z)
+  const AT B02 = -p0 * iz, B12 = -p1 * iz;
+  AT D[2][3];
+  D[0][0] = -A00 * iz; D[0][1] = -A01 * iz; D[0][2] = A00 * B02 + A01 * B12;
+  D[1][0] = -A01 * iz; D[1][1] = -A11 * iz; D[1][2] = A01 * B02 + A11 * B12;
+  const AT y0 = (AT)g.y[0], y1 = (AT)g.y[1], y2 = (AT)g.y[2];
+  const AT pp[2] = {p0, p1};
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    // dP/d(dw) = -[y]_x : column k is e_k x y
+    Jc[a][0] = -D[a][1] * y2 + D[a][2] * y1;
+    Jc[a][1] = D[a][0] * y2 - D[a][2] * y0;
+    Jc[a][2] = -D[a][0] * y1 + D[a][1] * y0;
+    Jc[a][3] = D[a][0];
+    Jc[a][4] = D[a][1];
+    Jc[a][5] = D[a][2];
+    Jc[a][6] = dd * pp[a];
+    Jc[a][7] = f * r2 * pp[a];
+    Jc[a][8] = f * r2 * r2 * pp[a];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Jp[a][j] = D[a][0] * (AT)rb[j] + D[a][1] * (AT)rb[3 + j] + D[a][2] * (AT)rb[6 + j];
+  }
+  if (d.e_sqinfo) {
+    const double* U = d.e_sqinfo + 3 * (size_t)e;
+    const AT u00 = (AT)U[0], u01 = (AT)U[1], u11 = (AT)U[2];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const AT a = u00 * Jc[0][k] + u01 * Jc[1][k];
+      Jc[1][k] = u11 * Jc[1][k];
+      Jc[0][k] = a;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const AT a = u00 * Jp[0][k] + u01 * Jp[1][k];
+      Jp[1][k] = u11 * Jp[1][k];
+      Jp[0][k] = a;
+    }
+  }
+  const AT s = (AT)sw;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Jc[a][k] *= s;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Jp[a][k] *= s;
+  }
+}
+
+// Deterministic CTA sum of one double per thread (fixed tree).
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double out = red[0];
+  __syncthreads();
+  return out;
+}
+
+// Last-CTA detection for grid-wide reductions in a fixed order.
+__device__ bool last_cta(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+struct ChunkRange {
+  int e0, nE, p0, nP, s0, nS;
+};
+__device__ __forceinline__ ChunkRange chunk_range(const DevBA& d, int k) {
+  ChunkRange c;
+  c.e0 = d.ch_e0[k];
+  c.nE = d.ch_e0[k + 1] - c.e0;
+  c.p0 = d.ch_p0[k];
+  c.nP = d.ch_p0[k + 1] - c.p0;
+  c.s0 = d.ch_s0[k];
+  c.nS = d.ch_s0[k + 1] - c.s0;
+  return c;
+}
+
+// ---------------------------------------------------------------- camera render blocks
+
+__global__ void k_cam_prepare(DevBA d, int candidate) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const double* cam = (candidate ? d.cam_cand : d.cam) + 9 * (size_t)c;
+  double* rb = (candidate ? d.camrb_cand : d.camrb) + 16 * (size_t)c;
+  double R[9];
+  aa_to_R(cam, R);
+  for (int i = 0; i < 9; ++i) rb[i] = R[i];
+  for (int i = 0; i < 6; ++i) rb[9 + i] = cam[3 + i];
+  rb[15] = 0.0;
+}
+
+// ---------------------------------------------------------------- cost F(x)
+
+__global__ void __launch_bounds__(kThreads) k_cost(DevBA d, int candidate) {
+  __shared__ double red[kThreads];
+  const ChunkRange cr = chunk_range(d, blockIdx.x);
+  const double* rbs = candidate ? d.camrb_cand : d.camrb;
+  const double* pts = candidate ? d.pt_cand : d.pt;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int e = cr.e0 + i;
+    double rb[16];
+    load_rb(rbs + 16 * (size_t)__ldg(d.e_cam + e), rb);
+    const double* Xp = pts + 3 * (size_t)__ldg(d.e_pt + e);
+    const double X[3] = {Xp[0], Xp[1], Xp[2]};
+    Geom g;
+    ba_geom(rb, X, g);
+    Robust o;
+    ba_residual(d, e, g, o);
+    acc += 0.5 * o.rho;
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) d.cost_part[blockIdx.x] = s;
+}
+
+__global__ void k_cost_init(DevBA d) {
+  __shared__ double red[kThreads];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < d.NCH; k += kThreads) acc += d.cost_part[k];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) d.sc->cost = s;
+}
+
+// ---------------------------------------------------------------- linearisation
+
+// One CTA per chunk.  Writes the chunk's Jacobian tile, the undamped point blocks
+// H_pp = sum Jp^T Jp and gradients b_p, and per-slot camera partials
+// (H_cc = sum Jc^T Jc, b_c = sum Jc^T r).  H uses the stored (rounded) Jacobian; the
+// gradient uses the unrounded one, so BF16 storage leaves the LM fixed point intact.
+template <class JT>
+__global__ void __launch_bounds__(kThreads) k_linearize(DevBA d, int force) {
+  using AT = typename AccOf<JT>::T;
+  constexpr bool kSplit = !std::is_same<JT, AT>::value;
+  if (!force && !d.sc->need_lin) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  JT* Js = reinterpret_cast<JT*>(smem);               // [24][CH]
+  AT* rs = reinterpret_cast<AT*>(Js + kJComp * CH);   // [2][CH]
+  AT* bce = rs + 2 * CH;                              // [9][CH]  (kSplit only)
+  AT* bpe = bce + 9 * CH;                             // [3][CH]  (kSplit only)
+  const ChunkRange cr = chunk_range(d, blockIdx.x);
+  JT* Jg = reinterpret_cast<JT*>(d.J) + d.ch_j0[blockIdx.x];
+  const int ldt = pad8(cr.nE);
+
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int e = cr.e0 + i;
+    const int c = __ldg(d.e_cam + e), p = __ldg(d.e_pt + e);
+    double rb[16];
+    load_rb(d.camrb + 16 * (size_t)c, rb);
+    const double X[3] = {d.pt[3 * (size_t)p], d.pt[3 * (size_t)p + 1], d.pt[3 * (size_t)p + 2]};
+    Geom g;
+    ba_geom(rb, X, g);
+    Robust o;
+    ba_residual(d, e, g, o);
+    AT Jc[2][9], Jp[2][3];
+    ba_jacobian<AT>(d, e, rb, g, o.sw, Jc, Jp);
+    if (d.cam_fixed[c]) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Jc[0][k] = Jc[1][k] = (AT)0;
+    }
+    if (d.pt_fixed[p]) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Jp[0][k] = Jp[1][k] = (AT)0;
+    }
+    const AT rw0 = (AT)(o.sw * o.r[0]), rw1 = (AT)(o.sw * o.r[1]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const JT v0 = cvj(Jc[0][k], (const JT*)nullptr), v1 = cvj(Jc[1][k], (const JT*)nullptr);
+      Jg[k * ldt + i] = v0;
+      Jg[(9 + k) * ldt + i] = v1;
+      Js[k * CH + i] = v0;
+      Js[(9 + k) * CH + i] = v1;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const JT v0 = cvj(Jp[0][k], (const JT*)nullptr), v1 = cvj(Jp[1][k], (const JT*)nullptr);
+      Jg[(18 + k) * ldt + i] = v0;
+      Jg[(21 + k) * ldt + i] = v1;
+      Js[(18 + k) * CH + i] = v0;
+      Js[(21 + k) * CH + i] = v1;
+    }
+    rs[i] = rw0;
+    rs[CH + i] = rw1;
+    if constexpr (kSplit) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) bce[k * CH + i] = Jc[0][k] * rw0 + Jc[1][k] * rw1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) bpe[k * CH + i] = Jp[0][k] * rw0 + Jp[1][k] * rw1;
+    }
+    if (d.dbg_r) {
+      d.dbg_r[2 * (size_t)e] = o.sw * o.r[0];
+      d.dbg_r[2 * (size_t)e + 1] = o.sw * o.r[1];
+    }
+  }
+  for (int i = cr.nE + threadIdx.x; i < ldt; i += kThreads) {
+#pragma unroll
+    for (int k = 0; k < kJComp; ++k) Jg[k * ldt + i] = cvj((AT)0, (const JT*)nullptr);
+  }
+  __syncthreads();
+
+  // point blocks
+  AT* Hpp = reinterpret_cast<AT*>(d.Hpp);
+  AT* bp = reinterpret_cast<AT*>(d.bp);
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    const int a = d.pt_off[pj] - cr.e0, b = d.pt_off[pj + 1] - cr.e0;
+    AT h[6] = {0, 0, 0, 0, 0, 0}, bb[3] = {0, 0, 0};
+    for (int i = a; i < b; ++i) {
+      AT J0[3], J1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        J0[k] = ldj(Js + (18 + k) * CH + i);
+        J1[k] = ldj(Js + (21 + k) * CH + i);
+      }
+      h[0] += J0[0] * J0[0] + J1[0] * J1[0];
+      h[1] += J0[0] * J0[1] + J1[0] * J1[1];
+      h[2] += J0[0] * J0[2] + J1[0] * J1[2];
+      h[3] += J0[1] * J0[1] + J1[1] * J1[1];
+      h[4] += J0[1] * J0[2] + J1[1] * J1[2];
+      h[5] += J0[2] * J0[2] + J1[2] * J1[2];
+      if constexpr (kSplit) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) bb[k] += bpe[k * CH + i];
+      } else {
+        const AT r0 = rs[i], r1 = rs[CH + i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) bb[k] += J0[k] * r0 + J1[k] * r1;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Hpp[6 * (size_t)pj + k] = h[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bp[3 * (size_t)pj + k] = bb[k];
+  }
+
+  // camera slots: 6 groups of 9 outputs (5 groups of H_cc entries, 1 of b_c)
+  AT* partA = reinterpret_cast<AT*>(d.partA);
+  for (int w = threadIdx.x; w < cr.nS * 6; w += kThreads) {
+    const int sl = w / 6, grp = w - sl * 6;
+    const int a = d.slot_e0[cr.s0 + sl], b = d.slot_e0[cr.s0 + sl + 1];
+    AT acc[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
+    for (int q = a; q < b; ++q) {
+      const int i = d.ch_sorted[q];
+      if (grp < 5) {
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int ti = c_ti[9 * grp + o], tj = c_tj[9 * grp + o];
+          acc[o] += ldj(Js + ti * CH + i) * ldj(Js + tj * CH + i) +
+                    ldj(Js + (9 + ti) * CH + i) * ldj(Js + (9 + tj) * CH + i);
+        }
+      } else {
+        if constexpr (kSplit) {
+#pragma unroll
+          for (int o = 0; o < 9; ++o) acc[o] += bce[o * CH + i];
+        } else {
+          const AT r0 = rs[i], r1 = rs[CH + i];
+#pragma unroll
+          for (int o = 0; o < 9; ++o)
+            acc[o] += ldj(Js + o * CH + i) * r0 + ldj(Js + (9 + o) * CH + i) * r1;
+        }
+      }
+    }
+    AT* out = partA + (size_t)(cr.s0 + sl) * kPartA + 9 * grp;
+#pragma unroll
+    for (int o = 0; o < 9; ++o) out[o] = acc[o];
+  }
+}
+
+// ---------------------------------------------------------------- Schur preparation
+
+// 3x3 SPD inverse by cofactors; h = (a b c d e f) packed upper triangle.
+template <class AT>
+__device__ __forceinline__ void inv3(const AT* h, AT* o) {
+  const AT a = h[0], b = h[1], c = h[2], dd = h[3], e = h[4], f = h[5];
+  const AT A = dd * f - e * e, B = c * e - b * f, C = b * e - c * dd;
+  const AT D = a * f - c * c, E = b * c - a * e, F = a * dd - b * b;
+  const AT det = a * A + b * B + c * C;
+  if (det > (AT)0 && isfinite(det)) {
+    const AT id = (AT)1 / det;
+    o[0] = A * id; o[1] = B * id; o[2] = C * id; o[3] = D * id; o[4] = E * id; o[5] = F * id;
+  } else {  // not positive definite in this precision: Jacobi fallback
+    o[0] = a > (AT)0 ? (AT)1 / a : (AT)0;
+    o[3] = dd > (AT)0 ? (AT)1 / dd : (AT)0;
+    o[5] = f > (AT)0 ? (AT)1 / f : (AT)0;
+    o[1] = o[2] = o[4] = (AT)0;
+  }
+}
+
+template <class AT>
+__device__ __forceinline__ void mul3(const AT* h, const AT* v, AT* o) {
+  o[0] = h[0] * v[0] + h[1] * v[1] + h[2] * v[2];
+  o[1] = h[1] * v[0] + h[3] * v[1] + h[4] * v[2];
+  o[2] = h[2] * v[0] + h[4] * v[1] + h[5] * v[2];
+}
+
+template <class AT>
+__device__ __forceinline__ AT damp_diag(AT h, const Scalars* sc) {
+  if (sc->damping_mode == 1) return (AT)1;
+  return fmin(fmax(h, (AT)sc->diag_min), (AT)sc->diag_max);
+}
+
+// One CTA per chunk: damped point inverses H_pp^-1 and per-slot partials of
+// sum_e W_e H_pp^-1 W_e^T (= Jc^T (Jp Hinv Jp^T) Jc) and sum_e W_e H_pp^-1 b_p.
+template <class JT>
+__global__ void __launch_bounds__(kThreads) k_schur_prepare(DevBA d) {
+  using AT = typename AccOf<JT>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  JT* Jcs = reinterpret_cast<JT*>(smem);              // [18][CH]
+  AT* Ae = reinterpret_cast<AT*>(Jcs + 18 * CH);      // [3][CH]
+  AT* qe = Ae + 3 * CH;                               // [2][CH]
+  const ChunkRange cr = chunk_range(d, blockIdx.x);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + d.ch_j0[blockIdx.x];
+  const int ldt = pad8(cr.nE);
+  const Scalars* sc = d.sc;
+  const AT lam = (AT)sc->lambda;
+  const AT* Hpp = reinterpret_cast<const AT*>(d.Hpp);
+  const AT* bp = reinterpret_cast<const AT*>(d.bp);
+  AT* Hinv = reinterpret_cast<AT*>(d.Hinv);
+
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    AT h[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = Hpp[6 * (size_t)pj + k];
+    h[0] += lam * damp_diag(h[0], sc);
+    h[3] += lam * damp_diag(h[3], sc);
+    h[5] += lam * damp_diag(h[5], sc);
+    AT o[6];
+    inv3(h, o);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Hinv[6 * (size_t)pj + k] = o[k];
+  }
+  __syncthreads();
+
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int pj = __ldg(d.e_pt + cr.e0 + i);
+    AT hi[6], bb[3], hb[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bb[k] = bp[3 * (size_t)pj + k];
+    mul3(hi, bb, hb);
+    AT J0[3], J1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      J0[k] = ldj(Jg + (18 + k) * ldt + i);
+      J1[k] = ldj(Jg + (21 + k) * ldt + i);
+    }
+#pragma unroll
+    for (int k = 0; k < 18; ++k) Jcs[k * CH + i] = Jg[k * ldt + i];
+    AT t0[3], t1[3];
+    mul3(hi, J0, t0);
+    mul3(hi, J1, t1);
+    Ae[i] = J0[0] * t0[0] + J0[1] * t0[1] + J0[2] * t0[2];
+    Ae[CH + i] = J0[0] * t1[0] + J0[1] * t1[1] + J0[2] * t1[2];
+    Ae[2 * CH + i] = J1[0] * t1[0] + J1[1] * t1[1] + J1[2] * t1[2];
+    qe[i] = J0[0] * hb[0] + J0[1] * hb[1] + J0[2] * hb[2];
+    qe[CH + i] = J1[0] * hb[0] + J1[1] * hb[1] + J1[2] * hb[2];
+  }
+  __syncthreads();
+
+  AT* partB = reinterpret_cast<AT*>(d.partB);
+  for (int w = threadIdx.x; w < cr.nS * 6; w += kThreads) {
+    const int sl = w / 6, grp = w - sl * 6;
+    const int a = d.slot_e0[cr.s0 + sl], b = d.slot_e0[cr.s0 + sl + 1];
+    AT acc[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
+    for (int q = a; q < b; ++q) {
+      const int i = d.ch_sorted[q];
+      if (grp < 5) {
+        const AT a00 = Ae[i], a01 = Ae[CH + i], a11 = Ae[2 * CH + i];
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int ti = c_ti[9 * grp + o], tj = c_tj[9 * grp + o];
+          const AT c0i = ldj(Jcs + ti * CH + i), c1i = ldj(Jcs + (9 + ti) * CH + i);
+          const AT c0j = ldj(Jcs + tj * CH + i), c1j = ldj(Jcs + (9 + tj) * CH + i);
+          acc[o] += c0i * (a00 * c0j + a01 * c1j) + c1i * (a01 * c0j + a11 * c1j);
+        }
+      } else {
+        const AT q0 = qe[i], q1 = qe[CH + i];
+#pragma unroll
+        for (int o = 0; o < 9; ++o)
+          acc[o] += ldj(Jcs + o * CH + i) * q0 + ldj(Jcs + (9 + o) * CH + i) * q1;
+      }
+    }
+    AT* out = partB + (size_t)(cr.s0 + sl) * kPartA + 9 * grp;
+#pragma unroll
+    for (int o = 0; o < 9; ++o) out[o] = acc[o];
+  }
+}
+
+// ---------------------------------------------------------------- camera blocks + PCG start
+
+// 9x9 SPD inverse via Cholesky: S (packed upper) -> M = S^-1 (packed upper).
+// If S is not positive definite in this precision, M = diag(1 / S_ii) (Jacobi).
+template <class AT>
+__device__ void spd_inverse9(const AT* S, AT* M) {
+  AT L[9][9];
+  bool ok = true;
+  for (int j = 0; j < 9 && ok; ++j) {
+    AT s = S[tri9(j, j)];
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > (AT)0)) { ok = false; break; }
+    const AT ljj = sqrt(s);
+    L[j][j] = ljj;
+    for (int i = j + 1; i < 9; ++i) {
+      AT t = S[tri9(j, i)];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / ljj;
+    }
+  }
+  if (!ok) {
+    for (int t = 0; t < kCamTri; ++t) M[t] = (AT)0;
+    for (int i = 0; i < 9; ++i) {
+      const AT v = S[tri9(i, i)];
+      M[tri9(i, i)] = v > (AT)0 ? (AT)1 / v : (AT)1;
+    }
+    return;
+  }
+  // W = L^-1 (lower triangular)
+  AT W[9][9];
+  for (int i = 0; i < 9; ++i) {
+    W[i][i] = (AT)1 / L[i][i];
+    for (int j = 0; j < i; ++j) {
+      AT s = (AT)0;
+      for (int k = j; k < i; ++k) s += L[i][k] * W[k][j];
+      W[i][j] = -s / L[i][i];
+    }
+  }
+  // M = W^T W
+  for (int i = 0; i < 9; ++i)
+    for (int j = i; j < 9; ++j) {
+      AT s = (AT)0;
+      for (int k = j; k < 9; ++k) s += W[k][i] * W[k][j];
+      M[tri9(i, j)] = s;
+    }
+}
+
+// One warp per camera: reduces the slot partials into H_cc, b_c and the Schur
+// terms, forms H_cc + lambda D_c, S_cc, g_c and M_c = S_cc^-1, and starts the PCG
+// (x = 0, r = g, z = M g, p = z).  The last CTA reduces r^T z and |r|^2.
+template <class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(DevBA d) {
+  __shared__ AT vals[kCamPerBlock][2 * kPartA];
+  __shared__ double red[kCamPerBlock][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kCamPerBlock + warp;
+  Scalars* sc = d.sc;
+  const AT lam = (AT)sc->lambda;
+  const AT* partA = reinterpret_cast<const AT*>(d.partA);
+  const AT* partB = reinterpret_cast<const AT*>(d.partB);
+  double rz_c = 0.0, rr_c = 0.0;
+  if (c < d.C) {
+    const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
+    for (int o = lane; o < 2 * kPartA; o += 32) {
+      AT acc = (AT)0;
+      for (int s = sa; s < sb; ++s) {
+        const int slot = d.cam_s_list[s];
+        acc += o < kPartA ? partA[(size_t)slot * kPartA + o] : partB[(size_t)slot * kPartA + o - kPartA];
+      }
+      vals[warp][o] = acc;
+    }
+    __syncwarp();
+    AT* Hcl = reinterpret_cast<AT*>(d.Hcl) + (size_t)c * kCamTri;
+    AT* S = reinterpret_cast<AT*>(d.S) + (size_t)c * kCamTri;
+    AT* M = reinterpret_cast<AT*>(d.Minv) + (size_t)c * kCamTri;
+    if (lane == 0) {
+      AT Sl[kCamTri], Ml[kCamTri];
+      for (int t = 0; t < kCamTri; ++t) Sl[t] = vals[warp][t];
+      for (int i = 0; i < 9; ++i) Sl[tri9(i, i)] += lam * damp_diag(vals[warp][tri9(i, i)], sc);
+      for (int t = 0; t < kCamTri; ++t) {
+        Hcl[t] = Sl[t];
+        Sl[t] -= vals[warp][kPartA + t];
+        S[t] = Sl[t];
+      }
+      spd_inverse9(Sl, Ml);
+      for (int t = 0; t < kCamTri; ++t) M[t] = Ml[t];
+    }
+    __syncwarp();
+    AT* g = reinterpret_cast<AT*>(d.g) + 9 * (size_t)c;
+    AT* bc = reinterpret_cast<AT*>(d.bc) + 9 * (size_t)c;
+    if (lane < 9) {
+      const AT gi = -vals[warp][45 + lane] + vals[warp][kPartA + 45 + lane];
+      g[lane] = gi;
+      bc[lane] = vals[warp][45 + lane];
+      reinterpret_cast<AT*>(d.x)[9 * (size_t)c + lane] = (AT)0;
+      reinterpret_cast<AT*>(d.xbest)[9 * (size_t)c + lane] = (AT)0;
+      reinterpret_cast<AT*>(d.r)[9 * (size_t)c + lane] = gi;
+    }
+    __syncwarp();
+    if (lane < 9) {
+      AT zi = (AT)0;
+      for (int j = 0; j < 9; ++j) zi += M[sym9(lane, j)] * g[j];
+      reinterpret_cast<AT*>(d.z)[9 * (size_t)c + lane] = zi;
+      reinterpret_cast<AT*>(d.p)[9 * (size_t)c + lane] = zi;
+      const AT gi = g[lane];
+      rz_c = (double)gi * (double)zi;
+      rr_c = (double)gi * (double)gi;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rz_c += __shfl_down_sync(0xffffffffu, rz_c, o);
+    rr_c += __shfl_down_sync(0xffffffffu, rr_c, o);
+  }
+  if (lane == 0) {
+    red[warp][0] = rz_c;
+    red[warp][1] = rr_c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kCamPerBlock; ++w) { a += red[w][0]; b += red[w][1]; }
+    d.cblk_part[2 * blockIdx.x] = a;
+    d.cblk_part[2 * blockIdx.x + 1] = b;
+  }
+  if (last_cta(&sc->ticket) && threadIdx.x == 0) {
+    double rz = 0.0, rr = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
+    const double gn = sqrt(rr);
+    sc->rz = rz;
+    sc->gnorm = gn;
+    sc->rnorm = gn;
+    sc->rmin = gn;
+    sc->sigma = 1.0;
+    sc->inv_n = 1.0;
+    sc->beta = 0.0;
+    sc->pcg_it = 0;
+    sc->use_best = 0;
+    sc->save_best = 0;
+    sc->tol_abs = sc->pcg_rel ? sc->pcg_tol * gn : sc->pcg_tol;
+    sc->pcg_done = (rr == 0.0 || !(rz > 0.0) || !isfinite(rz)) ? 1 : 0;
+    sc->ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- PCG
+
+// Matrix-free Schur product, one CTA per chunk (the hot loop).  With t_p =
+// H_pp^-1 sum_e Jp_e^T Jc_e x_c(e), each edge contributes v_e = Jc_e^T Jp_e t_p(e) to
+// its camera; v is reduced per slot in a fixed order.  The chunk's Jacobian tile is
+// read from HBM once; the second pass over it hits L2.
+template <class JT>
+__global__ void __launch_bounds__(kThreads) k_spmv(DevBA d) {
+  using AT = typename AccOf<JT>::T;
+  if (d.sc->pcg_done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  AT* vv = reinterpret_cast<AT*>(smem);    // [9][CH]; first [3][CH] hold a_e in pass 1
+  AT* tp = vv + 9 * CH;                    // [3][CH] per point of the chunk
+  const ChunkRange cr = chunk_range(d, blockIdx.x);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + d.ch_j0[blockIdx.x];
+  const int ldt = pad8(cr.nE);
+  const AT* xv = reinterpret_cast<const AT*>(d.p);
+
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int c = __ldg(d.e_cam + cr.e0 + i);
+    const AT* xc = xv + 9 * (size_t)c;
+    AT q0 = (AT)0, q1 = (AT)0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const AT xk = xc[k];
+      q0 += ldj(Jg + k * ldt + i) * xk;
+      q1 += ldj(Jg + (9 + k) * ldt + i) * xk;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      vv[k * CH + i] = ldj(Jg + (18 + k) * ldt + i) * q0 + ldj(Jg + (21 + k) * ldt + i) * q1;
+  }
+  __syncthreads();
+  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    const int a = d.pt_off[pj] - cr.e0, b = d.pt_off[pj + 1] - cr.e0;
+    AT u[3] = {0, 0, 0};
+    for (int i = a; i < b; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += vv[k * CH + i];
+    }
+    AT hi[6], t[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+    mul3(hi, u, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tp[k * CH + j] = t[k];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int pl = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
+    const AT t0 = tp[pl], t1 = tp[CH + pl], t2 = tp[2 * CH + pl];
+    const AT s0 = ldj(Jg + 18 * ldt + i) * t0 + ldj(Jg + 19 * ldt + i) * t1 + ldj(Jg + 20 * ldt + i) * t2;
+    const AT s1 = ldj(Jg + 21 * ldt + i) * t0 + ldj(Jg + 22 * ldt + i) * t1 + ldj(Jg + 23 * ldt + i) * t2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      vv[k * CH + i] = ldj(Jg + k * ldt + i) * s0 + ldj(Jg + (9 + k) * ldt + i) * s1;
+  }
+  __syncthreads();
+  AT* partV = reinterpret_cast<AT*>(d.partV);
+  for (int w = threadIdx.x; w < cr.nS * 9; w += kThreads) {
+    const int sl = w / 9, comp = w - sl * 9;
+    const int a = d.slot_e0[cr.s0 + sl], b = d.slot_e0[cr.s0 + sl + 1];
+    AT acc = (AT)0;
+    for (int q = a; q < b; ++q) acc += vv[comp * CH + d.ch_sorted[q]];
+    partV[(size_t)(cr.s0 + sl) * 9 + comp] = acc;
+  }
+}
+
+// One warp per camera: y_c = (H_cc + lambda D_c) p_c - sum_slots v; the last CTA
+// reduces p^T y and sets alpha = r^T z / p^T y.
+template <class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(DevBA d) {
+  __shared__ double red[kCamPerBlock];
+  Scalars* sc = d.sc;
+  if (sc->pcg_done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kCamPerBlock + warp;
+  double dot = 0.0;
+  if (c < d.C && lane < 9) {
+    const AT* partV = reinterpret_cast<const AT*>(d.partV);
+    const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
+    AT sv = (AT)0;
+    for (int s = sa; s < sb; ++s) sv += partV[(size_t)d.cam_s_list[s] * 9 + lane];
+    const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * kCamTri;
+    const AT* pc = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
+    AT yi = (AT)0;
+    for (int j = 0; j < 9; ++j) yi += H[sym9(lane, j)] * pc[j];
+    yi -= sv;
+    reinterpret_cast<AT*>(d.y)[9 * (size_t)c + lane] = yi;
+    dot = (double)pc[lane] * (double)yi;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+  if (lane == 0) red[warp] = dot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < kCamPerBlock; ++w) a += red[w];
+    d.cblk_part[2 * blockIdx.x] = a;
+  }
+  if (last_cta(&sc->ticket) && threadIdx.x == 0) {
+    double pAp = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) pAp += d.cblk_part[2 * b];
+    sc->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      sc->alpha = 0.0;
+      sc->pcg_done = 1;
+    } else {
+      sc->alpha = sc->rz / pAp;
+    }
+    sc->ticket = 0u;
+  }
+}
+
+// One thread per camera: x += sigma alpha p, r -= alpha y, z = M r; the last CTA
+// reduces r^T z and |r|^2, applies the stopping rules (tolerance, rejection ratio,
+// iteration cap) and computes beta and the normalisation factor.
+template <class AT>
+__global__ void __launch_bounds__(256) k_pcg_update(DevBA d) {
+  __shared__ double red[2][256];
+  Scalars* sc = d.sc;
+  if (sc->pcg_done) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double rz_c = 0.0, rr_c = 0.0;
+  if (c < d.C) {
+    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha);
+    AT* x = reinterpret_cast<AT*>(d.x) + 9 * (size_t)c;
+    AT* r = reinterpret_cast<AT*>(d.r) + 9 * (size_t)c;
+    AT* z = reinterpret_cast<AT*>(d.z) + 9 * (size_t)c;
+    const AT* p = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
+    const AT* y = reinterpret_cast<const AT*>(d.y) + 9 * (size_t)c;
+    const AT* M = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * kCamTri;
+    AT rl[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      x[i] += sa * p[i];
+      rl[i] = r[i] - alpha * y[i];
+      r[i] = rl[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      AT zi = (AT)0;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) zi += M[sym9(i, j)] * rl[j];
+      z[i] = zi;
+      rz_c += (double)rl[i] * (double)zi;
+      rr_c += (double)rl[i] * (double)rl[i];
+    }
+  }
+  red[0][threadIdx.x] = rz_c;
+  red[1][threadIdx.x] = rr_c;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d.cblk_part[2 * blockIdx.x] = red[0][0];
+    d.cblk_part[2 * blockIdx.x + 1] = red[1][0];
+  }
+  if (last_cta(&sc->ticket) && threadIdx.x == 0) {
+    double rz = 0.0, rr = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
+    const double n = sqrt(rr);
+    const double rtrue = sc->sigma * n;
+    sc->pcg_it += 1;
+    sc->pcg_total += 1;
+    sc->rnorm = rtrue;
+    int done = 0;
+    sc->save_best = 0;
+    if (sc->ratio > 0.0) {
+      if (rtrue < sc->rmin) {
+        sc->rmin = rtrue;
+        sc->save_best = 1;
+      } else if (rtrue > sc->ratio * sc->rmin) {
+        done = 1;
+        sc->use_best = 1;
+      }
+    }
+    if (rtrue <= sc->tol_abs || sc->pcg_it >= sc->max_it || !isfinite(rtrue) || !(rz > 0.0)) {
+      done = 1;
+      if (!isfinite(rtrue)) sc->use_best = 1;
+    }
+    sc->beta = rz / sc->rz;
+    if (sc->normalize && n > 0.0) {
+      sc->inv_n = 1.0 / n;
+      sc->sigma *= n;
+      sc->rz = rz / (n * n);
+    } else {
+      sc->inv_n = 1.0;
+      sc->rz = rz;
+    }
+    sc->pcg_done = done;
+    sc->ticket = 0u;
+  }
+}
+
+// One thread per camera: keep the best iterate, then p = (z + beta p) / n and
+// r, z scaled by 1/n (n = 1 without normalisation).
+template <class AT>
+__global__ void k_pcg_direction(DevBA d) {
+  const Scalars* sc = d.sc;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  if (sc->save_best) {
+    const AT* x = reinterpret_cast<const AT*>(d.x) + 9 * (size_t)c;
+    AT* xb = reinterpret_cast<AT*>(d.xbest) + 9 * (size_t)c;
+    for (int i = 0; i < 9; ++i) xb[i] = x[i];
+  }
+  if (sc->pcg_done) return;
+  const AT beta = (AT)sc->beta, s = (AT)sc->inv_n;
+  AT* p = reinterpret_cast<AT*>(d.p) + 9 * (size_t)c;
+  AT* r = reinterpret_cast<AT*>(d.r) + 9 * (size_t)c;
+  AT* z = reinterpret_cast<AT*>(d.z) + 9 * (size_t)c;
+  for (int i = 0; i < 9; ++i) {
+    p[i] = (z[i] + beta * p[i]) * s;
+    r[i] *= s;
+    z[i] *= s;
+  }
+}
+
+// ---------------------------------------------------------------- back-substitution
+
+// One CTA per chunk: dp = H_pp^-1 (-b_p - sum_e Jp^T Jc dc) and the chunk's share of
+// the model decrease -b_p^T dp - 1/2 sum_e |Jc dc + Jp dp|^2 (FP64 accumulation).
+template <class JT>
+__global__ void __launch_bounds__(kThreads) k_backsub(DevBA d) {
+  using AT = typename AccOf<JT>::T;
+  __shared__ double red[kThreads];
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  AT* qv = reinterpret_cast<AT*>(smem);   // [2][CH]
+  AT* av = qv + 2 * CH;                   // [3][CH]
+  const ChunkRange cr = chunk_range(d, blockIdx.x);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + d.ch_j0[blockIdx.x];
+  const int ldt = pad8(cr.nE);
+  const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x);
+  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
+  const AT* bp = reinterpret_cast<const AT*>(d.bp);
+  AT* dp = reinterpret_cast<AT*>(d.dp);
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int c = __ldg(d.e_cam + cr.e0 + i);
+    AT q0 = (AT)0, q1 = (AT)0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const AT xk = xs[9 * (size_t)c + k];
+      q0 += ldj(Jg + k * ldt + i) * xk;
+      q1 += ldj(Jg + (9 + k) * ldt + i) * xk;
+    }
+    qv[i] = q0;
+    qv[CH + i] = q1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      av[k * CH + i] = ldj(Jg + (18 + k) * ldt + i) * q0 + ldj(Jg + (21 + k) * ldt + i) * q1;
+  }
+  __syncthreads();
+  double md = 0.0;
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    const int a = d.pt_off[pj] - cr.e0, b = d.pt_off[pj + 1] - cr.e0;
+    AT u[3] = {0, 0, 0};
+    for (int i = a; i < b; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += av[k * CH + i];
+    }
+    AT hi[6], rhs[3], t[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rhs[k] = -bp[3 * (size_t)pj + k] - u[k];
+    mul3(hi, rhs, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dp[3 * (size_t)pj + k] = t[k];
+      md -= (double)bp[3 * (size_t)pj + k] * (double)t[k];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int pj = __ldg(d.e_pt + cr.e0 + i);
+    const AT t0 = dp[3 * (size_t)pj], t1 = dp[3 * (size_t)pj + 1], t2 = dp[3 * (size_t)pj + 2];
+    const double j0 = (double)(qv[i] + ldj(Jg + 18 * ldt + i) * t0 + ldj(Jg + 19 * ldt + i) * t1 +
+                               ldj(Jg + 20 * ldt + i) * t2);
+    const double j1 = (double)(qv[CH + i] + ldj(Jg + 21 * ldt + i) * t0 + ldj(Jg + 22 * ldt + i) * t1 +
+                               ldj(Jg + 23 * ldt + i) * t2);
+    md -= 0.5 * (j0 * j0 + j1 * j1);
+  }
+  const double s = block_sum(md, red);
+  if (threadIdx.x == 0) d.md_part[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------- retraction (FP64)
+
+template <class AT>
+__global__ void k_retract_cams(DevBA d) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const double* cur = d.cam + 9 * (size_t)c;
+  double* nxt = d.cam_cand + 9 * (size_t)c;
+  double* rb = d.camrb_cand + 16 * (size_t)c;
+  if (d.cam_fixed[c]) {
+    for (int i = 0; i < 9; ++i) nxt[i] = cur[i];
+    for (int i = 0; i < 16; ++i) rb[i] = d.camrb[16 * (size_t)c + i];
+    return;
+  }
+  const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x) + 9 * (size_t)c;
+  double dl[9];
+  for (int i = 0; i < 9; ++i) dl[i] = (double)xs[i];
+  double w[3];
+  aa_left_update(dl, cur, w);
+  nxt[0] = w[0];
+  nxt[1] = w[1];
+  nxt[2] = w[2];
+  for (int i = 3; i < 9; ++i) nxt[i] = cur[i] + dl[i];
+  double R[9];
+  aa_to_R(w, R);
+  for (int i = 0; i < 9; ++i) rb[i] = R[i];
+  for (int i = 0; i < 6; ++i) rb[9 + i] = nxt[3 + i];
+  rb[15] = 0.0;
+}
+
+template <class AT>
+__global__ void k_retract_pts(DevBA d) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.P) return;
+  const AT* dp = reinterpret_cast<const AT*>(d.dp) + 3 * (size_t)p;
+  for (int i = 0; i < 3; ++i)
+    d.pt_cand[3 * (size_t)p + i] = d.pt[3 * (size_t)p + i] + (d.pt_fixed[p] ? 0.0 : (double)dp[i]);
+}
+
+// ---------------------------------------------------------------- LM decision (FP64)
+
+template <class AT>
+__global__ void __launch_bounds__(kThreads) k_decide(DevBA d) {
+  __shared__ double red[kThreads];
+  Scalars* sc = d.sc;
+  double fc = 0.0, md = 0.0;
+  for (int k = threadIdx.x; k < d.NCH; k += kThreads) {
+    fc += d.cost_part[k];
+    md += d.md_part[k];
+  }
+  const AT* xs = reinterpret_cast<const AT*>(sc->use_best ? d.xbest : d.x);
+  const AT* bc = reinterpret_cast<const AT*>(d.bc);
+  for (int i = threadIdx.x; i < 9 * d.C; i += kThreads) md -= (double)bc[i] * (double)xs[i];
+  const double Fc = block_sum(fc, red);
+  const double L = block_sum(md, red);
+  if (threadIdx.x != 0) return;
+  const double F = sc->cost;
+  const bool acc = L > 0.0 && isfinite(Fc) && Fc < F;
+  const double rho = L != 0.0 ? (F - Fc) / L : 0.0;
+  const int it = sc->iter;
+  if (it < kMaxHistory) {
+    IterRecord& h = d.hist[it];
+    h.cost = F;
+    h.cand_cost = Fc;
+    h.model_decrease = L;
+    h.rho = rho;
+    h.lambda = sc->lambda;
+    h.pcg_residual = sc->gnorm > 0.0 ? sc->rnorm / sc->gnorm : 0.0;
+    h.accepted = acc ? 1 : 0;
+    h.pcg_iters = sc->pcg_it;
+  }
+  double lam = sc->lambda, nu = sc->nu;
+  if (acc) {
+    const double t = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - t * t * t);
+    nu = 2.0;
+    sc->cost = Fc;
+    sc->n_accepted += 1;
+  } else {
+    lam *= nu;
+    nu *= 2.0;
+  }
+  sc->lambda = fmin(fmax(lam, sc->lambda_min), sc->lambda_max);
+  sc->nu = nu;
+  sc->cand_cost = Fc;
+  sc->model_dec = L;
+  sc->rho = rho;
+  sc->accepted = acc ? 1 : 0;
+  sc->need_lin = acc ? 1 : 0;
+  sc->iter = it + 1;
+}
+
+__global__ void k_commit(DevBA d) {
+  if (!d.sc->accepted) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.C) {
+    for (int k = 0; k < 9; ++k) d.cam[9 * (size_t)i + k] = d.cam_cand[9 * (size_t)i + k];
+    for (int k = 0; k < 16; ++k) d.camrb[16 * (size_t)i + k] = d.camrb_cand[16 * (size_t)i + k];
+  }
+  if (i < d.P) {
+    for (int k = 0; k < 3; ++k) d.pt[3 * (size_t)i + k] = d.pt_cand[3 * (size_t)i + k];
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline int blocks_for(int n, int t) { return n > 0 ? (n + t - 1) / t : 1; }
+
+int default_ch_max(Prec pr) { return pr == Prec::F64 ? 512 : 1024; }
+
+static size_t lin_smem(Prec pr, int ch) {
+  const size_t sJ = pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2);
+  const size_t sA = pr == Prec::F64 ? 8 : 4;
+  const size_t per = kJComp * sJ + 2 * sA + (pr == Prec::BF16 ? 12 * sA : 0);
+  return per * (size_t)ch;
+}
+static size_t schur_smem(Prec pr, int ch) {
+  const size_t sJ = pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2);
+  const size_t sA = pr == Prec::F64 ? 8 : 4;
+  return (18 * sJ + 5 * sA) * (size_t)ch;
+}
+static size_t spmv_smem(Prec pr, int ch) {
+  const size_t sA = pr == Prec::F64 ? 8 : 4;
+  return 12 * sA * (size_t)ch;
+}
+static size_t backsub_smem(Prec pr, int ch) {
+  const size_t sA = pr == Prec::F64 ? 8 : 4;
+  return 5 * sA * (size_t)ch;
+}
+size_t smem_bytes_linearize(Prec pr, int ch) { return lin_smem(pr, ch); }
+
+int max_supported_ch(Prec pr) {
+  // largest chunk whose linearisation tile fits the 227 KB opt-in shared memory
+  const size_t limit = 227 * 1024;
+  int ch = 64;
+  while (lin_smem(pr, ch * 2) <= limit && schur_smem(pr, ch * 2) <= limit) ch *= 2;
+  return ch;
+}
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, size).
+static void set_smem(const void* kernel, size_t bytes) {
+  static const void* keys[32];
+  static size_t vals[32];
+  static int n = 0;
+  for (int i = 0; i < n; ++i)
+    if (keys[i] == kernel) {
+      if (vals[i] >= bytes) return;
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      vals[i] = bytes;
+      return;
+    }
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (n < 32) { keys[n] = kernel; vals[n] = bytes; ++n; }
+}
+
+void launch_cam_prepare(const DevBA& d, bool candidate, cudaStream_t st) {
+  if (d.C == 0) return;
+  k_cam_prepare<<<blocks_for(d.C, 128), 128, 0, st>>>(d, candidate ? 1 : 0);
+}
+
+void launch_cost(const DevBA& d, bool candidate, cudaStream_t st) {
+  if (d.NCH == 0) return;
+  k_cost<<<d.NCH, kThreads, 0, st>>>(d, candidate ? 1 : 0);
+}
+
+void launch_cost_init(const DevBA& d, cudaStream_t st) { k_cost_init<<<1, kThreads, 0, st>>>(d); }
+
+template <class JT>
+static void lin_t(const DevBA& d, Prec pr, bool force, cudaStream_t st) {
+  const size_t sm = lin_smem(pr, d.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_linearize<JT>), sm);
+  k_linearize<JT><<<d.NCH, kThreads, sm, st>>>(d, force ? 1 : 0);
+}
+void launch_linearize(const DevBA& d, Prec pr, bool force, cudaStream_t st) {
+  if (d.NCH == 0) return;
+  if (pr == Prec::F64) lin_t<double>(d, pr, force, st);
+  else if (pr == Prec::F32) lin_t<float>(d, pr, force, st);
+  else lin_t<__nv_bfloat16>(d, pr, force, st);
+}
+
+template <class JT>
+static void schur_t(const DevBA& d, Prec pr, cudaStream_t st) {
+  const size_t sm = schur_smem(pr, d.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_schur_prepare<JT>), sm);
+  k_schur_prepare<JT><<<d.NCH, kThreads, sm, st>>>(d);
+}
+void launch_schur_prepare(const DevBA& d, Prec pr, cudaStream_t st) {
+  if (d.NCH == 0) return;
+  if (pr == Prec::F64) schur_t<double>(d, pr, st);
+  else if (pr == Prec::F32) schur_t<float>(d, pr, st);
+  else schur_t<__nv_bfloat16>(d, pr, st);
+}
+
+void launch_cam_finalize(const DevBA& d, Prec pr, cudaStream_t st) {
+  if (pr == Prec::F64) k_cam_finalize<double><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
+  else k_cam_finalize<float><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
+}
+
+template <class JT>
+static void spmv_t(const DevBA& d, Prec pr, cudaStream_t st) {
+  const size_t sm = spmv_smem(pr, d.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_spmv<JT>), sm);
+  k_spmv<JT><<<d.NCH, kThreads, sm, st>>>(d);
+}
+int launch_pcg_spmv(const DevBA& d, Prec pr, cudaStream_t st) {
+  if (d.NCH == 0) return 0;
+  if (pr == Prec::F64) spmv_t<double>(d, pr, st);
+  else if (pr == Prec::F32) spmv_t<float>(d, pr, st);
+  else spmv_t<__nv_bfloat16>(d, pr, st);
+  return 1;
+}
+int launch_pcg_vector(const DevBA& d, Prec pr, cudaStream_t st) {
+  const int nb = blocks_for(d.C, 256);
+  if (pr == Prec::F64) {
+    k_cam_apply<double><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
+    k_pcg_update<double><<<nb, 256, 0, st>>>(d);
+    k_pcg_direction<double><<<nb, 256, 0, st>>>(d);
+  } else {
+    k_cam_apply<float><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
+    k_pcg_update<float><<<nb, 256, 0, st>>>(d);
+    k_pcg_direction<float><<<nb, 256, 0, st>>>(d);
+  }
+  return 3;
+}
+
+template <class JT>
+static void backsub_t(const DevBA& d, Prec pr, cudaStream_t st) {
+  const size_t sm = backsub_smem(pr, d.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_backsub<JT>), sm);
+  k_backsub<JT><<<d.NCH, kThreads, sm, st>>>(d);
+}
+void launch_backsub(const DevBA& d, Prec pr, cudaStream_t st) {
+  if (d.NCH == 0) return;
+  if (pr == Prec::F64) backsub_t<double>(d, pr, st);
+  else if (pr == Prec::F32) backsub_t<float>(d, pr, st);
+  else backsub_t<__nv_bfloat16>(d, pr, st);
+}
+
+void launch_retract(const DevBA& d, Prec pr, cudaStream_t st) {
+  if (pr == Prec::F64) {
+    if (d.C) k_retract_cams<double><<<blocks_for(d.C, 128), 128, 0, st>>>(d);
+    if (d.P) k_retract_pts<double><<<blocks_for(d.P, 256), 256, 0, st>>>(d);
+  } else {
+    if (d.C) k_retract_cams<float><<<blocks_for(d.C, 128), 128, 0, st>>>(d);
+    if (d.P) k_retract_pts<float><<<blocks_for(d.P, 256), 256, 0, st>>>(d);
+  }
+}
+
+void launch_decide(const DevBA& d, Prec pr, cudaStream_t st) {
+  if (pr == Prec::F64) k_decide<double><<<1, kThreads, 0, st>>>(d);
+  else k_decide<float><<<1, kThreads, 0, st>>>(d);
+}
+
+void launch_commit(const DevBA& d, cudaStream_t st) {
+  const int n = d.C > d.P ? d.C : d.P;
+  if (n) k_commit<<<blocks_for(n, 256), 256, 0, st>>>(d);
+}
+
+}  // namespace gpo

@@ -1,0 +1,278 @@
+"""ctypes binding of libgpo (include/gpo.h): same names as the C ABI, argument
+marshalling only.  Every step of the optimiser runs in the library's CUDA kernels;
+this module never computes any part of it.
+
+`Graph` is a thin convenience wrapper over the C calls for numpy / torch arrays.
+Importing this module loads libgpo.so (building it first if needed) and raises
+if the library cannot be loaded; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GPO_OK = 0
+GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_STATE, GPO_ERR_NUMERIC = -1, -2, -3, -4
+GPO_ERR_CUDA, GPO_ERR_TIMEOUT, GPO_ERR_UNSUPPORTED = -5, -6, -7
+GPO_FP64, GPO_FP32, GPO_FP32_BF16 = 0, 1, 2
+GPO_V_BA_CAMERA9, GPO_V_POINT3 = 0, 1
+GPO_E_BA_REPROJ = 0
+GPO_LOSS_NONE, GPO_LOSS_HUBER = 0, 1
+PRECISIONS = {"fp64": GPO_FP64, "fp32": GPO_FP32, "bf16": GPO_FP32_BF16}
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class gpo_graph_desc(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32),
+                ("reserve_vertices", C.c_int64), ("reserve_edges", C.c_int64),
+                ("cuda_stream", C.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
+                ("alloc_ctx", C.c_void_p), ("memory_budget", C.c_size_t)]
+
+
+class gpo_lm_params(C.Structure):
+    _fields_ = [("initial_damping", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double), ("diag_min", C.c_double), ("diag_max", C.c_double),
+                ("damping_mode", C.c_int32), ("pcg_max_iters", C.c_int32),
+                ("pcg_tol", C.c_double), ("pcg_tol_relative", C.c_int32),
+                ("pcg_rejection_ratio", C.c_double), ("pcg_normalize", C.c_int32),
+                ("reserved0", C.c_int32)]
+
+
+class gpo_report(C.Structure):
+    _fields_ = [("initial_cost", C.c_double), ("final_cost", C.c_double),
+                ("final_lambda", C.c_double), ("iterations", C.c_int32),
+                ("accepted", C.c_int32), ("pcg_iters_total", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class gpo_iter_record(C.Structure):
+    _fields_ = [("cost", C.c_double), ("cand_cost", C.c_double), ("model_decrease", C.c_double),
+                ("rho", C.c_double), ("lambda_", C.c_double), ("pcg_residual", C.c_double),
+                ("accepted", C.c_int32), ("pcg_iters", C.c_int32)]
+
+
+class gpo_kernel_profile(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("timed_launches", C.c_int64),
+                ("active_launches", C.c_int64), ("total_ms", C.c_double), ("active_ms", C.c_double)]
+
+
+_P = C.c_void_p
+_PD = C.POINTER(C.c_double)
+_PI64 = C.POINTER(C.c_int64)
+_SIGS = {
+    "gpo_graph_desc_default": (C.c_int, [C.POINTER(gpo_graph_desc)]),
+    "gpo_lm_params_default": (C.c_int, [C.POINTER(gpo_lm_params)]),
+    "gpo_graph_create": (C.c_int, [C.POINTER(gpo_graph_desc), C.POINTER(_P)]),
+    "gpo_graph_destroy": (C.c_int, [_P]),
+    "gpo_add_vertices": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int64, _PI64]),
+    "gpo_add_edges": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, _P, C.c_int32, C.c_double, _PI64]),
+    "gpo_set_fixed": (C.c_int, [_P, C.c_int64, C.c_int32]),
+    "gpo_set_edge_active": (C.c_int, [_P, C.c_int64, C.c_int32]),
+    "gpo_set_initial": (C.c_int, [_P, C.c_int64, C.c_int64, _P, C.c_int32]),
+    "gpo_optimize": (C.c_int, [_P, C.c_int32, C.POINTER(gpo_lm_params), C.POINTER(gpo_report)]),
+    "gpo_get_cost": (C.c_int, [_P, _PD]),
+    "gpo_get_state": (C.c_int, [_P, C.c_int64, C.c_int64, _P, C.c_int32]),
+    "gpo_get_history": (C.c_int, [_P, C.POINTER(gpo_iter_record), C.c_int32, C.POINTER(C.c_int32)]),
+    "gpo_memory_footprint": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "gpo_set_profiling": (C.c_int, [_P, C.c_int32]),
+    "gpo_get_profile": (C.c_int, [_P, C.POINTER(gpo_kernel_profile), C.c_int32, C.POINTER(C.c_int32)]),
+    "gpo_last_error": (C.c_char_p, [_P]),
+    "gpo_version": (C.c_char_p, []),
+    "gpo_debug_linearize": (C.c_int, [_P, _P, _P]),
+    "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
+    "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
+}
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    path = path or os.environ.get("GPO_LIBRARY") or _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load_library()
+
+
+class GpoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gpo status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, g=None):
+    if st != GPO_OK:
+        msg = lib.gpo_last_error(g)
+        raise GpoError(st, msg.decode() if msg else "")
+
+
+def default_params(**kw) -> gpo_lm_params:
+    p = gpo_lm_params()
+    _check(lib.gpo_lm_params_default(C.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Graph:
+    """Owns one gpo_graph handle."""
+
+    def __init__(self, precision="fp64", device: int = 0, stream=None, memory_budget: int = 0,
+                 reserve_vertices: int = 0, reserve_edges: int = 0):
+        d = gpo_graph_desc()
+        _check(lib.gpo_graph_desc_default(C.byref(d)))
+        d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d.device = device
+        d.cuda_stream = stream
+        d.memory_budget = memory_budget
+        d.reserve_vertices = reserve_vertices
+        d.reserve_edges = reserve_edges
+        h = C.c_void_p()
+        _check(lib.gpo_graph_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gpo_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def add_vertices(self, kind: int, block_size: int, n: int) -> int:
+        first = C.c_int64()
+        _check(lib.gpo_add_vertices(self.h, kind, block_size, n, C.byref(first)), self.h)
+        return first.value
+
+    def add_edges(self, kind: int, vertex_ids: np.ndarray, meas: np.ndarray, info=None,
+                  loss_kind: int = GPO_LOSS_NONE, loss_delta: float = 0.0) -> int:
+        ids = np.ascontiguousarray(vertex_ids, dtype=np.int64)
+        m = np.ascontiguousarray(meas, dtype=np.float64)
+        inf = None if info is None else np.ascontiguousarray(info, dtype=np.float64)
+        first = C.c_int64()
+        _check(lib.gpo_add_edges(self.h, kind, ids.shape[0], _ptr(ids), _ptr(m),
+                                 None if inf is None else _ptr(inf), loss_kind, loss_delta,
+                                 C.byref(first)), self.h)
+        return first.value
+
+    def set_fixed(self, vid: int, fixed: bool = True):
+        _check(lib.gpo_set_fixed(self.h, vid, int(fixed)), self.h)
+
+    def set_edge_active(self, eid: int, active: bool):
+        _check(lib.gpo_set_edge_active(self.h, eid, int(active)), self.h)
+
+    def set_initial(self, first: int, state) -> None:
+        """state: numpy array (host) or torch CUDA tensor (device), float64 rows."""
+        if hasattr(state, "data_ptr"):
+            n = state.shape[0]
+            _check(lib.gpo_set_initial(self.h, first, n, C.c_void_p(state.data_ptr()), 1), self.h)
+        else:
+            a = np.ascontiguousarray(state, dtype=np.float64)
+            _check(lib.gpo_set_initial(self.h, first, a.shape[0], _ptr(a), 0), self.h)
+
+    def get_state(self, first: int, n: int, width: int, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            _check(lib.gpo_get_state(self.h, first, n, C.c_void_p(out.data_ptr()), 1), self.h)
+            return out
+        a = np.empty((n, width), dtype=np.float64)
+        _check(lib.gpo_get_state(self.h, first, n, _ptr(a), 0), self.h)
+        return a
+
+    def optimize(self, max_iters: int, params: gpo_lm_params | None = None) -> gpo_report:
+        rep = gpo_report()
+        _check(lib.gpo_optimize(self.h, max_iters, None if params is None else C.byref(params),
+                                C.byref(rep)), self.h)
+        return rep
+
+    def cost(self) -> float:
+        v = C.c_double()
+        _check(lib.gpo_get_cost(self.h, C.byref(v)), self.h)
+        return v.value
+
+    def history(self, cap: int = 4096) -> list[dict]:
+        buf = (gpo_iter_record * cap)()
+        n = C.c_int32()
+        _check(lib.gpo_get_history(self.h, buf, cap, C.byref(n)), self.h)
+        return [dict(cost=r.cost, cand_cost=r.cand_cost, model_decrease=r.model_decrease,
+                     rho=r.rho, lam=r.lambda_, pcg_residual=r.pcg_residual,
+                     accepted=bool(r.accepted), pcg_iters=r.pcg_iters) for r in buf[:n.value]]
+
+    def set_profiling(self, on: bool = True):
+        _check(lib.gpo_set_profiling(self.h, int(on)), self.h)
+
+    def profile(self) -> dict:
+        buf = (gpo_kernel_profile * 32)()
+        n = C.c_int32()
+        _check(lib.gpo_get_profile(self.h, buf, 32, C.byref(n)), self.h)
+        return {r.name.decode(): dict(launches=r.launches, timed=r.timed_launches,
+                                      active=r.active_launches, total_ms=r.total_ms,
+                                      active_ms=r.active_ms) for r in buf[:n.value]}
+
+    def footprint(self) -> int:
+        v = C.c_size_t()
+        _check(lib.gpo_memory_footprint(self.h, C.byref(v)), self.h)
+        return v.value
+
+    # diagnostics -----------------------------------------------------------
+    def debug_linearize(self, n_edges: int):
+        r = np.zeros((n_edges, 2))
+        J = np.zeros((n_edges, 2, 12))
+        _check(lib.gpo_debug_linearize(self.h, _ptr(r), _ptr(J)), self.h)
+        return r, J
+
+    def debug_step(self, lam: float, n_dof: int, params: gpo_lm_params | None = None):
+        dx = np.zeros(n_dof)
+        it = C.c_int32()
+        _check(lib.gpo_debug_step(self.h, lam, None if params is None else C.byref(params),
+                                  _ptr(dx), C.byref(it)), self.h)
+        return dx, it.value
+
+    def debug_schur(self, lam: float, n_cams: int, params: gpo_lm_params | None = None):
+        S = np.zeros((n_cams, 9, 9))
+        g = np.zeros((n_cams, 9))
+        _check(lib.gpo_debug_schur(self.h, lam, None if params is None else C.byref(params),
+                                   _ptr(S), _ptr(g)), self.h)
+        return S, g
+
+
+def ba_graph(cams, pts, cam_idx, pt_idx, obs, huber_delta=None, precision="fp64",
+             cam_fixed=None, pt_fixed=None, active=None, info=None, **kw) -> tuple[Graph, int, int]:
+    """Builds a BA graph: cameras get ids [0, C), points [C, C + P).  Returns
+    (graph, first camera id, first point id)."""
+    g = Graph(precision, **kw)
+    C_ = cams.shape[0]
+    P_ = pts.shape[0]
+    c0 = g.add_vertices(GPO_V_BA_CAMERA9, 9, C_)
+    p0 = g.add_vertices(GPO_V_POINT3, 3, P_)
+    ids = np.stack([np.asarray(cam_idx, np.int64) + c0, np.asarray(pt_idx, np.int64) + p0], axis=1)
+    if huber_delta is None:
+        g.add_edges(GPO_E_BA_REPROJ, ids, obs, info)
+    else:
+        g.add_edges(GPO_E_BA_REPROJ, ids, obs, info, GPO_LOSS_HUBER, float(huber_delta))
+    g.set_initial(c0, cams)
+    g.set_initial(p0, pts)
+    if cam_fixed is not None:
+        for c in np.nonzero(cam_fixed)[0]:
+            g.set_fixed(c0 + int(c))
+    if pt_fixed is not None:
+        for p in np.nonzero(pt_fixed)[0]:
+            g.set_fixed(p0 + int(p))
+    if active is not None:
+        for e in np.nonzero(~np.asarray(active, bool))[0]:
+            g.set_edge_active(int(e), False)
+    return g, c0, p0

@@ -1,0 +1,220 @@
+"""GPU parity of the BA path against the FP64 oracle, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic):
+  * per-edge residual and Jacobian, FP64: 1e-12 relative to the edge's largest entry
+    (the two sides differ only in rounding order, FMA contraction and libm);
+  * Schur blocks and reduced right-hand side, FP64: 1e-10 relative to the block norm
+    (sums of ~300 products with cancellation);
+  * one LM step solved by PCG to 1e-14 relative residual vs the oracle's dense
+    Cholesky step: 1e-8 relative (PCG stopping error times condition number);
+  * final cost after 20 LM iterations on the 10-camera problem: 1e-9 relative;
+  * mixed precision (FP32, BF16 storage) vs FP64 on the GPU: final cost 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import ba as oba
+from oracle import lm as olm
+from paper_2509_26581_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpo():
+    from paper_2509_26581_gb300 import gpo as m
+    return m
+
+
+def _oracle_problem(p, **kw):
+    return olm.ba_problem(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, huber_delta=p.huber_delta, **kw)
+
+
+def _edge_rel(a, b, floor):
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    scale = np.maximum(np.abs(b).max(axis=1), floor)
+    return (np.abs(a - b).max(axis=1) / scale).max()
+
+
+def _oracle_weighted_rows(p, active=None, sqrt_info=None, cam_fixed=None, pt_fixed=None):
+    cams, X = p.cams0[p.cam_idx], p.pts0[p.pt_idx]
+    r = oba.residual(cams, X, p.obs)
+    Jc, Jp = oba.jacobians(cams, X)
+    if sqrt_info is not None:
+        r = np.einsum("nij,nj->ni", sqrt_info, r)
+        Jc, Jp = sqrt_info @ Jc, sqrt_info @ Jp
+    s = np.sum(r * r, axis=1)
+    from oracle import robust
+    loss = None if p.huber_delta is None else ("huber", p.huber_delta)
+    w = np.sqrt(robust.weight(s, loss))
+    r, Jc, Jp = r * w[:, None], Jc * w[:, None, None], Jp * w[:, None, None]
+    if cam_fixed is not None:
+        Jc[cam_fixed[p.cam_idx]] = 0
+    if pt_fixed is not None:
+        Jp[pt_fixed[p.pt_idx]] = 0
+    J = np.concatenate([Jc, Jp], axis=2)
+    if active is not None:
+        r[~active] = 0
+        J[~active] = 0
+    return r, J
+
+
+@pytest.mark.parametrize("case", ["tiny", "huber_outliers", "info", "fixed_inactive"])
+def test_edge_residuals_and_jacobians_fp64(gpo, case):
+    kw = {}
+    if case == "tiny":
+        p = synth.ba_tiny(0)
+    else:
+        p = synth.ba_ring(11, 12, 400, 5, outlier_frac=0.05, huber_delta=2.0)
+    info = sqrt_info = active = cam_fixed = pt_fixed = None
+    if case == "info":
+        rng = np.random.default_rng(0)
+        A = rng.normal(size=(p.n_edges, 2, 2))
+        info = A @ np.transpose(A, (0, 2, 1)) + 0.5 * np.eye(2)
+        sqrt_info = np.transpose(np.linalg.cholesky(info), (0, 2, 1))   # U with U^T U = Omega
+    if case == "fixed_inactive":
+        cam_fixed = np.zeros(p.n_cams, bool)
+        cam_fixed[[0, 3]] = True
+        pt_fixed = np.zeros(p.n_pts, bool)
+        pt_fixed[::17] = True
+        active = np.ones(p.n_edges, bool)
+        active[::7] = False
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp64",
+                           cam_fixed=cam_fixed, pt_fixed=pt_fixed, active=active, info=info)
+    r, J = g.debug_linearize(p.n_edges)
+    ro, Jo = _oracle_weighted_rows(p, active, sqrt_info, cam_fixed, pt_fixed)
+    assert _edge_rel(r, ro, 1e-9) < 1e-12
+    assert _edge_rel(J, Jo, 1e-9) < 1e-12
+    # the oracle's cost agrees with the library's
+    prob = _oracle_problem(p, cam_fixed=cam_fixed, pt_fixed=pt_fixed, active=active,
+                           sqrt_info=sqrt_info)
+    F = olm.total_cost(prob)
+    assert abs(g.cost() - F) <= 1e-12 * F
+
+
+def _oracle_schur(p, lam, **kw):
+    prob = _oracle_problem(p, **kw)
+    layout = olm.make_layout(prob)
+    lin = olm.linearize(prob, layout)
+    H, b = olm.normal_equations(lin)
+    D = olm.damping_diagonal(H, olm.LMParams())
+    Hl = H + sp.diags(lam * D)
+    dx, S, gvec = olm.schur_solve(Hl, b, layout)
+    return dx, S, gvec, layout
+
+
+@pytest.mark.parametrize("lam", [1e-4, 1.0])
+def test_schur_blocks_and_rhs_fp64(gpo, lam):
+    p = synth.ba_ring(5, 8, 300, 5, outlier_frac=0.03, huber_delta=2.0)
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp64")
+    S, gv = g.debug_schur(lam, p.n_cams)
+    _, So, go, _ = _oracle_schur(p, lam)
+    for c in range(p.n_cams):
+        blk = So[9 * c:9 * c + 9, 9 * c:9 * c + 9]
+        assert np.abs(S[c] - blk).max() <= 1e-10 * np.abs(blk).max()
+    assert np.abs(gv.reshape(-1) - go).max() <= 1e-10 * np.abs(go).max()
+
+
+def _parity_params(gpo, **kw):
+    return gpo.default_params(pcg_max_iters=400, pcg_tol=1e-14, pcg_tol_relative=1,
+                              pcg_rejection_ratio=0.0, **kw)
+
+
+@pytest.mark.parametrize("lam", [1e-4, 1e-1])
+def test_one_step_pcg_matches_dense_cholesky(gpo, lam):
+    p = synth.ba_tiny(0)
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64")
+    dx, iters = g.debug_step(lam, 9 * p.n_cams + 3 * p.n_pts, _parity_params(gpo))
+    dxo, _, _, _ = _oracle_schur(p, lam)
+    assert np.abs(dx - dxo).max() <= 1e-8 * np.abs(dxo).max()
+    assert 0 < iters <= 400
+
+
+def test_lm_tiny_final_cost_matches_oracle(gpo):
+    p = synth.ba_tiny(0)
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64")
+    rep = g.optimize(20, _parity_params(gpo))
+    _, orep = olm.levenberg_marquardt(_oracle_problem(p), 20)
+    assert abs(rep.initial_cost - orep.initial_cost) <= 1e-12 * orep.initial_cost
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
+    hist = g.history()
+    assert len(hist) == 20
+    ohist = orep.history
+    # the accept/reject sequence agrees while steps are well above rounding
+    for h, o in zip(hist[:8], ohist[:8]):
+        assert h["accepted"] == o["accepted"]
+        assert abs(h["cost"] - o["cost"]) <= 1e-9 * o["cost"]
+
+
+def test_deterministic_bitwise(gpo):
+    p = synth.ba_path(3, 40, 6000, "pareto")
+    out = []
+    for _ in range(2):
+        g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp32")
+        rep = g.optimize(5)
+        out.append((rep.final_cost, g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_fixed_and_disabled_vertices_unchanged(gpo):
+    p = synth.ba_ring(4, 8, 200, 5)
+    cam_fixed = np.zeros(p.n_cams, bool)
+    cam_fixed[0] = True
+    pt_fixed = np.zeros(p.n_pts, bool)
+    pt_fixed[5] = True
+    active = np.ones(p.n_edges, bool)
+    active[p.pt_idx == 9] = False          # point 9 loses every observation
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64",
+                             cam_fixed=cam_fixed, pt_fixed=pt_fixed, active=active)
+    rep = g.optimize(10)
+    cams = g.get_state(c0, p.n_cams, 9)
+    pts = g.get_state(p0, p.n_pts, 3)
+    assert np.array_equal(cams[0], p.cams0[0])
+    assert np.array_equal(pts[5], p.pts0[5]) and np.array_equal(pts[9], p.pts0[9])
+    assert rep.final_cost < rep.initial_cost
+    prob = _oracle_problem(p, cam_fixed=cam_fixed, pt_fixed=pt_fixed, active=active)
+    _, orep = olm.levenberg_marquardt(prob, 10)
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-6 * orep.final_cost
+
+
+def test_empty_and_isolated(gpo):
+    g = gpo.Graph("fp64")
+    c0 = g.add_vertices(gpo.GPO_V_BA_CAMERA9, 9, 2)
+    p0 = g.add_vertices(gpo.GPO_V_POINT3, 3, 3)
+    cams = np.zeros((2, 9))
+    cams[:, 5] = -10.0
+    cams[:, 6] = 500.0
+    g.set_initial(c0, cams)
+    g.set_initial(p0, np.ones((3, 3)))
+    rep = g.optimize(3)
+    assert rep.initial_cost == 0.0 and rep.final_cost == 0.0
+    assert np.array_equal(g.get_state(p0, 3, 3), np.ones((3, 3)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_precision_final_cost_close_to_fp64(gpo, prec):
+    p = synth.ba_path(5, 120, 30000, "pareto")
+    costs = {}
+    for pr in ("fp64", prec):
+        g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, pr)
+        costs[pr] = g.optimize(30).final_cost
+    assert abs(costs[prec] - costs["fp64"]) <= 1e-6 * costs["fp64"]
+
+
+def test_sampled_edges_at_medium_size(gpo):
+    """Full 1,000-camera / 500,000-point workload (the benchmark's): a random sample
+    of edges is checked against the oracle one edge at a time."""
+    p = synth.ba_medium(1)
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp64")
+    r, J = g.debug_linearize(p.n_edges)
+    idx = np.random.default_rng(0).choice(p.n_edges, 3000, replace=False)
+    sub = synth.BAProblem("s", 0, p.cams_gt, p.pts_gt, p.cams0, p.pts0, p.cam_idx[idx],
+                          p.pt_idx[idx], p.obs[idx], p.is_outlier[idx], p.huber_delta)
+    ro, Jo = _oracle_weighted_rows(sub)
+    assert _edge_rel(r[idx], ro, 1e-9) < 1e-12
+    assert _edge_rel(J[idx], Jo, 1e-9) < 1e-12
+    rep = g.optimize(3)
+    assert rep.final_cost < rep.initial_cost
