@@ -147,7 +147,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
 
     from paper_2509_26581_gb300 import gpo, synth
 
-    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local % max(1, torch.cuda.device_count()))
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     p = synth.ba_medium(args.seed)
@@ -187,7 +188,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     out_p = torch.empty_like(pts_h).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    n_e2e = 0 if args.no_e2e else args.steps
+    for _ in range(n_e2e):
         g.set_initial(c0, cams_h.numpy())
         g.set_initial(p0, pts_h.numpy())
         g.optimize(1, params)
@@ -218,8 +220,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                     edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, seed=args.seed,
                     l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
                     parallelism=f"replicas x{world}"),
-        e2e=dict(value=world * args.steps / e2e_s, unit="LM iter/s", h2d_bytes_per_step=state_bytes,
-                 d2h_bytes_per_step=state_bytes),
+        e2e=None if args.no_e2e else dict(value=world * args.steps / e2e_s, unit="LM iter/s",
+                                          h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes),
         gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
                       traffic=None, kernel="k_spmv (PCG Schur product)", peak_source=peak_kind,
@@ -264,6 +266,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -15,7 +15,9 @@ with these readings where the paper is silent:
   * gain ratio rho = (F(x) - F(x + dx)) / (L(0) - L(dx)) with the model decrease
     L(0) - L(dx) = -b^T dx - 1/2 sum_e |J_e dx|^2_W;
   * acceptance and damping follow Nielsen's rule: accept iff L(0) - L(dx) > 0,
-    F(x + dx) is finite and F(x + dx) < F(x); then lambda *= max(1/3, 1 - (2 rho - 1)^3),
+    F(x + dx) is finite and F(x + dx) < F(x) (a reduced system that the Cholesky factorisation
+    finds not positive definite counts as a rejected step, as in Ceres);
+    then lambda *= max(1/3, 1 - (2 rho - 1)^3),
     nu = 2; otherwise lambda *= nu, nu *= 2; lambda is then clamped to
     [lambda_min, lambda_max] (1e-16, 1e32 by default, the inverse trust-region radius
     bounds of Ceres, which Sec. IV-E follows for its clamping).  Exactly max_iters iterations run
@@ -310,10 +312,16 @@ def levenberg_marquardt(problem: Problem, max_iters: int, params: LMParams | Non
         H, b = normal_equations(lin)
         D = damping_diagonal(H, params)
         Hl = H + sp.diags(lam * D)
-        dx, _, _ = schur_solve(Hl, b, layout)
-        L = model_decrease(lin, b, dx)
-        cand = apply_step(prob, layout, dx)
-        Fc = total_cost(prob, cand)
+        try:
+            dx, _, _ = schur_solve(Hl, b, layout)
+        except np.linalg.LinAlgError:
+            dx = None                    # reduced system not positive definite at this damping
+        if dx is None:
+            L, Fc, cand = 0.0, np.inf, None
+        else:
+            L = model_decrease(lin, b, dx)
+            cand = apply_step(prob, layout, dx)
+            Fc = total_cost(prob, cand)
         accepted = bool(L > 0 and np.isfinite(Fc) and Fc < F)
         rho = (F - Fc) / L if L != 0 else 0.0
         rep.history.append(dict(iter=it, cost=F, cand_cost=Fc, model_decrease=L, rho=rho,

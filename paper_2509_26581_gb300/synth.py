@@ -284,7 +284,8 @@ def track_lengths(rng: Stream, n: int, law: str) -> np.ndarray:
     raise ValueError(law)
 
 
-def ba_path(seed: int, n_cams: int, n_pts: int, law: str = "pareto", spacing: float = 0.1,
+def ba_path(seed: int, n_cams: int, n_pts: int, law: str = "pareto", spacing: float = 0.3,
+            depth_lo: float = 2.0, depth_hi: float = 20.0,
             pixel_sigma: float = 1.0, rot_noise: float = 0.02, trans_noise: float = 0.05,
             point_noise: float = 0.1, k_sigma: float = 1e-3, outlier_frac: float = 0.01,
             huber_delta: float | None = 2.0, name: str = "ba_path") -> BAProblem:
@@ -308,7 +309,9 @@ def ba_path(seed: int, n_cams: int, n_pts: int, law: str = "pareto", spacing: fl
 
     anchor = rng_vis.integers(n_pts, 0, n_cams)
     L = np.minimum(track_lengths(rng_vis, n_pts, law), n_cams)
-    depth = rng_vis.uniform(n_pts, 2.0, 20.0)
+    # depth U[depth_lo, depth_hi], raised so that the whole window of observing cameras
+    # sees the point within a +-35 degree cone (half window <= 0.7 depth)
+    depth = np.maximum(rng_vis.uniform(n_pts, depth_lo, depth_hi), 0.5 * L * spacing / 0.7)
     lat = rng_vis.uniform(n_pts, -0.4, 0.4) * depth
     up = rng_vis.uniform(n_pts, -0.3, 0.3) * depth
     X = centers[anchor] + depth[:, None] * fwd[anchor] + lat[:, None] * tang[anchor]
@@ -319,7 +322,14 @@ def ba_path(seed: int, n_cams: int, n_pts: int, law: str = "pareto", spacing: fl
     pt_e = np.repeat(np.arange(n_pts, dtype=np.int64), L)
     first = np.repeat(np.cumsum(L) - L, L)
     cam_e = np.repeat(start, L) + (np.arange(E0, dtype=np.int64) - first)
-    keep = np.einsum("ni,ni->n", X[pt_e] - centers[cam_e], fwd[cam_e]) >= 0.5
+    # an observer keeps the observation only if the point lies in front (depth >= 0.5)
+    # and inside a +-45 degree field of view about the viewing direction
+    rel = X[pt_e] - centers[cam_e]
+    dep = np.einsum("ni,ni->n", rel, fwd[cam_e])
+    lat_x = np.abs(np.einsum("ni,ni->n", rel, R[cam_e, 0]))
+    lat_y = np.abs(np.einsum("ni,ni->n", rel, R[cam_e, 1]))
+    keep = (dep >= 0.5) & (lat_x <= dep) & (lat_y <= dep)
+    del rel, dep, lat_x, lat_y
     pt_e, cam_e = pt_e[keep], cam_e[keep]
     cnt = np.bincount(pt_e, minlength=n_pts)
     good = cnt >= 2

