@@ -207,8 +207,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     sp = prof["spmv"]
     peak, peak_kind = load_peaks()
     alg = spmv_algorithmic_bytes(p.n_edges, p.n_pts, args.precision)
-    spmv_ms = sp["active_ms"] / max(1, sp["active"])
-    achieved = alg / (spmv_ms * 1e-3) / 1e9
+    spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
+    achieved = alg / (spmv_ms * 1e-3) / 1e9 if sp["active"] else 0.0
     state_bytes = (p.n_cams * 9 + p.n_pts * 3) * 8
     pcg_iters = [h["pcg_iters"] for h in hist]
     line = dict(

@@ -75,13 +75,14 @@ struct gpo_graph {
   std::vector<int64_t> sorted_edge;   // sorted position -> edge id
   std::vector<int32_t> pt_new2old, pt_old2new;
   std::vector<int32_t> h_ch_e0;
-  std::vector<long long> h_ch_j0;
   size_t j_elems = 0;
 
   // device
   void* arena = nullptr;
   size_t arena_bytes = 0;
   DevBA dev{};
+  gpo::LaunchSet ls{};             // one-problem launch set over `dev`
+  DevBA* dev_desc = nullptr;       // device copy of `dev` (ls.probs)
   Scalars* h_sc = nullptr;         // pinned
   int* h_flag = nullptr;           // pinned [2]
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -253,10 +254,9 @@ static gpo_status finalize(gpo_graph* g) {
     e_cam_s[i] = g->e_cam[e];
     e_pt_s[i] = g->pt_old2new[g->e_pt[e]];
   }
-  std::vector<uint16_t> e_slot(E), ch_sorted(E);
+  std::vector<uint16_t> e_pos(E), ch_sorted(E);
   std::vector<int32_t> ch_s0{0}, slot_e0, slot_cam;
-  std::vector<long long> ch_j0(NCH);
-  size_t jpos = 0;
+  const size_t jpos = (size_t)E * gpo::kJComp;
   {
     std::vector<std::pair<int32_t, int32_t>> tmp;
     for (int k = 0; k < NCH; ++k) {
@@ -272,12 +272,10 @@ static gpo_status finalize(gpo_graph* g) {
           slot_e0.push_back(e0 + q);
           slot_cam.push_back(prev);
         }
-        e_slot[e0 + tmp[q].second] = (uint16_t)slot;
+        e_pos[e0 + tmp[q].second] = (uint16_t)q;
         ch_sorted[e0 + q] = (uint16_t)tmp[q].second;
       }
       ch_s0.push_back((int)slot_cam.size());
-      ch_j0[k] = (long long)jpos;
-      jpos += (size_t)gpo::kJComp * gpo::pad8(n);
     }
     slot_e0.push_back(E);
   }
@@ -313,18 +311,15 @@ static gpo_status finalize(gpo_graph* g) {
   DevBA d{};
   d.C = C; d.P = P; d.E = E; d.NCH = NCH; d.NS = NS; d.ch_max = ch;
   d.ncblk = std::max(1, (C + gpo::kCamPerBlock - 1) / gpo::kCamPerBlock);
-  const int nb_upd = std::max(1, (C + 255) / 256);
-  const int ncblk_max = std::max(d.ncblk, nb_upd);
   Plan pl;
   int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d;
-  long long* ch_j0_d;
-  uint16_t *e_slot_d, *ch_sorted_d;
+  uint16_t *e_pos_d, *ch_sorted_d;
   uint8_t *cam_fixed_d, *pt_fixed_d;
   double *obs_d, *delta_d, *info_d = nullptr;
   pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, 2 * (size_t)E); pl.add(&delta_d, E);
   if (g->any_info) pl.add(&info_d, 3 * (size_t)E);
   pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
-  pl.add(&ch_s0_d, NCH + 1); pl.add(&ch_j0_d, std::max(NCH, 1)); pl.add(&e_slot_d, E);
+  pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E);
   pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
   pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1));
   pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
@@ -343,9 +338,15 @@ static gpo_status finalize(gpo_graph* g) {
   pl.add_raw(&d.z, 9 * (size_t)C * sA); pl.add_raw(&d.p, 9 * (size_t)C * sA);
   pl.add_raw(&d.y, 9 * (size_t)C * sA); pl.add_raw(&d.xbest, 9 * (size_t)C * sA);
   pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
-  pl.add(&d.cblk_part, 2 * (size_t)ncblk_max);
+  pl.add(&d.cblk_part, 2 * (size_t)d.ncblk);
   pl.add(&d.sc, 1);
   pl.add(&d.hist, gpo::kMaxHistory);
+  const int npb = std::max(1, (P + 255) / 256);
+  DevBA* desc_d;
+  int *ch_prob_d, *cb_prob_d, *pb_prob_d, *base_d, *running_d;
+  pl.add(&desc_d, 1);
+  pl.add(&ch_prob_d, std::max(NCH, 1)); pl.add(&cb_prob_d, d.ncblk); pl.add(&pb_prob_d, npb);
+  pl.add(&base_d, 1); pl.add(&running_d, 1);
   const size_t bytes = pl.total();
   if (g->desc.memory_budget && bytes > g->desc.memory_budget)
     return fail(g, GPO_ERR_OOM, "graph needs %zu bytes of device memory, budget is %zu", bytes,
@@ -365,8 +366,8 @@ static gpo_status finalize(gpo_graph* g) {
   g->arena_bytes = bytes;
   pl.assign(static_cast<char*>(base));
   d.e_cam = e_cam; d.e_pt = e_pt; d.obs = obs_d; d.e_delta = delta_d; d.e_sqinfo = info_d;
-  d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d; d.ch_j0 = ch_j0_d;
-  d.e_slot = e_slot_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
+  d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d;
+  d.e_pos = e_pos_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
   d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
   d.dbg_r = nullptr;
   cudaStream_t st = g->stream;
@@ -379,8 +380,7 @@ static gpo_status finalize(gpo_graph* g) {
   GPO_CUDA(g, up(ch_e0_d, ch_e0, st));
   GPO_CUDA(g, up(ch_p0_d, ch_p0, st));
   GPO_CUDA(g, up(ch_s0_d, ch_s0, st));
-  GPO_CUDA(g, up(ch_j0_d, ch_j0, st));
-  GPO_CUDA(g, up(e_slot_d, e_slot, st));
+  GPO_CUDA(g, up(e_pos_d, e_pos, st));
   GPO_CUDA(g, up(ch_sorted_d, ch_sorted, st));
   GPO_CUDA(g, up(slot_e0_d, slot_e0, st));
   GPO_CUDA(g, up(slot_cam_d, slot_cam, st));
@@ -398,12 +398,26 @@ static gpo_status finalize(gpo_graph* g) {
   GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(jpos, 8) * sJ, st));
   GPO_CUDA(g, cudaMemsetAsync(d.sc, 0, sizeof(Scalars), st));
   GPO_CUDA(g, cudaMemsetAsync(d.dp, 0, 3 * (size_t)P * sA, st));
+  GPO_CUDA(g, cudaMemsetAsync(ch_prob_d, 0, std::max(NCH, 1) * sizeof(int), st));
+  GPO_CUDA(g, cudaMemsetAsync(cb_prob_d, 0, d.ncblk * sizeof(int), st));
+  GPO_CUDA(g, cudaMemsetAsync(pb_prob_d, 0, npb * sizeof(int), st));
+  GPO_CUDA(g, cudaMemsetAsync(base_d, 0, sizeof(int), st));
+  GPO_CUDA(g, cudaMemsetAsync(running_d, 0, sizeof(int), st));
+  GPO_CUDA(g, cudaMemcpyAsync(desc_d, &d, sizeof(DevBA), cudaMemcpyHostToDevice, st));
   GPO_CUDA(g, cudaStreamSynchronize(st));
+  gpo::LaunchSet ls{};
+  ls.probs = desc_d;
+  ls.ch_prob = ch_prob_d; ls.ch_base = base_d;
+  ls.cb_prob = cb_prob_d; ls.cb_base = base_d;
+  ls.pb_prob = pb_prob_d; ls.pb_base = base_d;
+  ls.running = running_d;
+  ls.nprob = 1; ls.n_ch = NCH; ls.n_cb = C > 0 ? d.ncblk : 0; ls.n_pb = P > 0 ? npb : 0;
+  ls.ch_max = ch;
+  g->ls = ls;
+  g->dev_desc = desc_d;
   g->h_ch_e0 = ch_e0;
-  g->h_ch_j0 = ch_j0;
   g->dev = d;
   g->finalized = true;
-  gpo::launch_cam_prepare(g->dev, false, st);
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
@@ -477,6 +491,8 @@ static void fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Sc
   s.normalize = p.pcg_normalize < 0 ? (g->prec != Prec::F64 ? 1 : 0) : (p.pcg_normalize ? 1 : 0);
   s.sigma = 1.0;
   s.inv_n = 1.0;
+  s.active = 1;
+  s.pcg_done = 1;   // until the camera blocks start a PCG solve
 }
 
 static gpo_status upload_scalars(gpo_graph* g, const Scalars& s) {
@@ -497,16 +513,16 @@ static gpo_status pcg_solve(gpo_graph* g, int max_it) {
     const int n = std::min(kGroup, max_it - launched);
     for (int i = 0; i < n; ++i) {
       g->cur_pcg_k = launched + i + 1;
-      run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(g->dev, g->prec, g->stream); });
-      run(g, KK_PCG_VECTOR, [&] { return gpo::launch_pcg_vector(g->dev, g->prec, g->stream); });
+      run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(g->ls, g->prec, g->stream); });
+      run(g, KK_PCG_VECTOR, [&] { return gpo::launch_pcg_vector(g->ls, g->prec, g->stream); });
     }
     launched += n;
-    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], &g->dev.sc->pcg_done, sizeof(int),
+    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], g->ls.running, sizeof(int),
                                 cudaMemcpyDeviceToHost, g->stream));
     GPO_CUDA(g, cudaEventRecord(g->ev[slot], g->stream));
     if (pending >= 0) {
       GPO_CUDA(g, cudaEventSynchronize(g->ev[pending]));
-      if (g->h_flag[pending]) break;
+      if (g->h_flag[pending] == 0) break;   // no problem is still iterating
     }
     pending = slot;
     slot ^= 1;
@@ -516,23 +532,25 @@ static gpo_status pcg_solve(gpo_graph* g, int max_it) {
 }
 
 static gpo_status solve_system(gpo_graph* g, int max_it, bool force_lin) {
-  const DevBA& d = g->dev;
-  run(g, KK_LINEARIZE, [&] { gpo::launch_linearize(d, g->prec, force_lin, g->stream); return d.NCH ? 1 : 0; });
-  run(g, KK_SCHUR, [&] { gpo::launch_schur_prepare(d, g->prec, g->stream); return d.NCH ? 1 : 0; });
-  run(g, KK_CAM_FINALIZE, [&] { gpo::launch_cam_finalize(d, g->prec, g->stream); return 1; });
+  const gpo::LaunchSet& ls = g->ls;
+  run(g, KK_LINEARIZE, [&] { return gpo::launch_linearize(ls, g->prec, force_lin, g->stream); });
+  run(g, KK_SCHUR, [&] { return gpo::launch_schur_prepare(ls, g->prec, g->stream); });
+  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, sizeof(int), g->stream));
+  run(g, KK_CAM_FINALIZE, [&] { return gpo::launch_cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   gpo_status s = pcg_solve(g, max_it);
   if (s != GPO_OK) return s;
   g->cur_pcg_k = 0;
-  run(g, KK_BACKSUB, [&] { gpo::launch_backsub(d, g->prec, g->stream); return d.NCH ? 1 : 0; });
+  run(g, KK_BACKSUB, [&] { return gpo::launch_backsub(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
 
 static gpo_status compute_cost(gpo_graph* g, double* out) {
-  const DevBA& d = g->dev;
-  run(g, KK_COST, [&] { gpo::launch_cost(d, false, g->stream); return d.NCH ? 1 : 0; });
-  run(g, KK_COST_REDUCE, [&] { gpo::launch_cost_init(d, g->stream); return 1; });
+  const gpo::LaunchSet& ls = g->ls;
+  run(g, KK_CAM_PREPARE, [&] { return gpo::launch_cam_prepare(ls, false, g->stream); });
+  run(g, KK_COST, [&] { return gpo::launch_cost(ls, false, g->stream); });
+  run(g, KK_COST_REDUCE, [&] { return gpo::launch_cost_init(ls, g->stream); });
   GPO_CUDA(g, cudaMemcpyAsync(g->h_sc, g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->stream));
   GPO_CUDA(g, cudaStreamSynchronize(g->stream));
   *out = g->h_sc->cost;
@@ -760,7 +778,6 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
   if (kind == GPO_V_BA_CAMERA9) {
     GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * 9, state, n * 9 * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    gpo::launch_cam_prepare(g->dev, false, st);
   } else {
     // points live on the device in sorted order
     int32_t* idx = nullptr;
@@ -826,14 +843,14 @@ gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* pa
   double F0;
   if ((s = compute_cost(g, &F0)) != GPO_OK) return s;
   if (!std::isfinite(F0)) return fail(g, GPO_ERR_NUMERIC, "initial cost is not finite (%g)", F0);
-  const DevBA& d = g->dev;
+  const gpo::LaunchSet& ls = g->ls;
   for (int it = 0; it < max_iters; ++it) {
     g->cur_lm_iter = it;
     if ((s = solve_system(g, sc.max_it, false)) != GPO_OK) return s;
-    run(g, KK_RETRACT, [&] { gpo::launch_retract(d, g->prec, g->stream); return (d.C ? 1 : 0) + (d.P ? 1 : 0); });
-    run(g, KK_COST, [&] { gpo::launch_cost(d, true, g->stream); return d.NCH ? 1 : 0; });
-    run(g, KK_DECIDE, [&] { gpo::launch_decide(d, g->prec, g->stream); return 1; });
-    run(g, KK_COMMIT, [&] { gpo::launch_commit(d, g->stream); return (d.C || d.P) ? 1 : 0; });
+    run(g, KK_RETRACT, [&] { return gpo::launch_retract(ls, g->prec, g->stream); });
+    run(g, KK_COST, [&] { return gpo::launch_cost(ls, true, g->stream); });
+    run(g, KK_DECIDE, [&] { return gpo::launch_decide(ls, g->prec, g->stream); });
+    run(g, KK_COMMIT, [&] { return gpo::launch_commit(ls, g->stream); });
     GPO_CUDA(g, cudaGetLastError());
   }
   g->cur_lm_iter = -1;
@@ -868,7 +885,11 @@ gpo_status gpo_get_cost(gpo_graph* g, double* cost) {
     *cost = g->last_cost;
     return GPO_OK;
   }
-  gpo::launch_cam_prepare(g->dev, false, g->stream);
+  Scalars sc;
+  gpo_lm_params prm;
+  gpo_lm_params_default(&prm);
+  fill_scalars(g, prm, prm.initial_damping, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
   if ((s = compute_cost(g, cost)) != GPO_OK) return s;
   g->last_cost = *cost;
   g->cost_valid = true;
@@ -977,8 +998,10 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
   gpo_lm_params_default(&prm);
   fill_scalars(g, prm, prm.initial_damping, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
-  gpo::launch_cam_prepare(dd, false, g->stream);
-  gpo::launch_linearize(dd, g->prec, true, g->stream);
+  GPO_CUDA(g, cudaMemcpyAsync(g->dev_desc, &dd, sizeof(DevBA), cudaMemcpyHostToDevice, g->stream));
+  gpo::launch_cam_prepare(g->ls, false, g->stream);
+  gpo::launch_linearize(g->ls, g->prec, true, g->stream);
+  GPO_CUDA(g, cudaMemcpyAsync(g->dev_desc, &g->dev, sizeof(DevBA), cudaMemcpyHostToDevice, g->stream));
   GPO_CUDA(g, cudaGetLastError());
   std::vector<char> rraw, jraw;
   if ((s = fetch(g, rraw, dbg, 2 * (size_t)d.E * sizeof(double))) != GPO_OK) return s;
@@ -990,7 +1013,7 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
   if (J_out) std::fill(J_out, J_out + 24 * Eall, 0.0);
   const double* rv = reinterpret_cast<const double*>(rraw.data());
   for (int k = 0; k < d.NCH; ++k) {
-    const int e0 = g->h_ch_e0[k], n = g->h_ch_e0[k + 1] - e0, ldt = gpo::pad8(n);
+    const int e0 = g->h_ch_e0[k], n = g->h_ch_e0[k + 1] - e0;
     for (int i = 0; i < n; ++i) {
       const int64_t id = g->sorted_edge[e0 + i];
       if (r_out) {
@@ -998,10 +1021,10 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
         r_out[2 * id + 1] = rv[2 * (size_t)(e0 + i) + 1];
       }
       if (J_out) {
-        const size_t b = (size_t)g->h_ch_j0[k];
+        const size_t b = (size_t)(e0 + i) * gpo::kJComp;
         for (int a = 0; a < 2; ++a) {
-          for (int j = 0; j < 9; ++j) J_out[24 * id + 12 * a + j] = read_j(jraw, b + (size_t)(9 * a + j) * ldt + i, g->prec);
-          for (int j = 0; j < 3; ++j) J_out[24 * id + 12 * a + 9 + j] = read_j(jraw, b + (size_t)(18 + 3 * a + j) * ldt + i, g->prec);
+          for (int j = 0; j < 9; ++j) J_out[24 * id + 12 * a + j] = read_j(jraw, b + 9 * a + j, g->prec);
+          for (int j = 0; j < 3; ++j) J_out[24 * id + 12 * a + 9 + j] = read_j(jraw, b + 18 + 3 * a + j, g->prec);
         }
       }
     }
@@ -1018,7 +1041,7 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
   Scalars sc;
   fill_scalars(g, prm, lambda, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
-  gpo::launch_cam_prepare(g->dev, false, g->stream);
+  gpo::launch_cam_prepare(g->ls, false, g->stream);
   if ((s = solve_system(g, sc.max_it, true)) != GPO_OK) return s;
   const DevBA& d = g->dev;
   const size_t sA = at_size(g->prec);
@@ -1055,10 +1078,11 @@ gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* par
   Scalars sc;
   fill_scalars(g, prm, lambda, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
-  gpo::launch_cam_prepare(g->dev, false, g->stream);
-  gpo::launch_linearize(g->dev, g->prec, true, g->stream);
-  gpo::launch_schur_prepare(g->dev, g->prec, g->stream);
-  gpo::launch_cam_finalize(g->dev, g->prec, g->stream);
+  gpo::launch_cam_prepare(g->ls, false, g->stream);
+  gpo::launch_linearize(g->ls, g->prec, true, g->stream);
+  gpo::launch_schur_prepare(g->ls, g->prec, g->stream);
+  GPO_CUDA(g, cudaMemsetAsync(g->ls.running, 0, sizeof(int), g->stream));
+  gpo::launch_cam_finalize(g->ls, g->prec, g->stream);
   GPO_CUDA(g, cudaGetLastError());
   const DevBA& d = g->dev;
   const size_t sA = at_size(g->prec);

@@ -31,6 +31,59 @@ __device__ __forceinline__ __nv_bfloat16 cvj(float v, const __nv_bfloat16*) { re
 __device__ __forceinline__ float cvj(float v, const float*) { return v; }
 __device__ __forceinline__ double cvj(double v, const double*) { return v; }
 
+// Edge-major Jacobian rows: 24 values per edge, [Jc row 0 (9), Jc row 1 (9),
+// Jp row 0 (3), Jp row 1 (3)], contiguous in point-major edge order.  A row is 48,
+// 96 or 192 bytes (BF16 / FP32 / FP64): three, six or twelve 16-byte accesses.
+template <class AT>
+__device__ __forceinline__ void load_row(const __nv_bfloat16* src, AT (&v)[kJComp]) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const uint4 w = __ldg(s4 + i);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(h[j]);
+      v[8 * i + 2 * j] = (AT)f.x;
+      v[8 * i + 2 * j + 1] = (AT)f.y;
+    }
+  }
+}
+template <class AT>
+__device__ __forceinline__ void load_row(const float* src, AT (&v)[kJComp]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float4 w = __ldg(s4 + i);
+    v[4 * i] = (AT)w.x; v[4 * i + 1] = (AT)w.y; v[4 * i + 2] = (AT)w.z; v[4 * i + 3] = (AT)w.w;
+  }
+}
+template <class AT>
+__device__ __forceinline__ void load_row(const double* src, AT (&v)[kJComp]) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const double2 w = __ldg(s2 + i);
+    v[2 * i] = (AT)w.x; v[2 * i + 1] = (AT)w.y;
+  }
+}
+__device__ __forceinline__ void store_row(__nv_bfloat16* dst, const __nv_bfloat16 (&v)[kJComp]) {
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  const uint4* s4 = reinterpret_cast<const uint4*>(v);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d4[i] = s4[i];
+}
+__device__ __forceinline__ void store_row(float* dst, const float (&v)[kJComp]) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+__device__ __forceinline__ void store_row(double* dst, const double (&v)[kJComp]) {
+  double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) d2[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
 // Upper triangle of a 9x9 symmetric block, row-major: entry t is (c_ti[t], c_tj[t]).
 __constant__ unsigned char c_ti[kCamTri] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1,
                                             2, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4,
@@ -263,13 +316,13 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // Last-CTA detection for grid-wide reductions in a fixed order.
-__device__ bool last_cta(unsigned int* ticket) {
+__device__ bool last_cta(unsigned int* ticket, int ctas) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int t = atomicAdd(ticket, 1u);
-    is_last = (t == gridDim.x - 1);
+    is_last = (t == (unsigned int)ctas - 1u);
   }
   __syncthreads();
   if (is_last) __threadfence();
@@ -290,11 +343,30 @@ __device__ __forceinline__ ChunkRange chunk_range(const DevBA& d, int k) {
   return c;
 }
 
+// ---------------------------------------------------------------- problem binding
+
+// Copies problem q's descriptor into shared memory (all threads cooperate).
+__device__ __forceinline__ void bind_problem(DevBA& dst, const DevBA* src) {
+  static_assert(sizeof(DevBA) % 4 == 0, "DevBA must be a whole number of words");
+  const int* s4 = reinterpret_cast<const int*>(src);
+  int* d4 = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevBA) / 4); i += blockDim.x) d4[i] = s4[i];
+  __syncthreads();
+}
+
+#define GPO_BIND(KIND, LOCAL)                              \
+  __shared__ DevBA d;                                      \
+  const int prob_ = ls.KIND##_prob[blockIdx.x];            \
+  const int LOCAL = blockIdx.x - ls.KIND##_base[prob_];    \
+  bind_problem(d, ls.probs + prob_);
+
 // ---------------------------------------------------------------- camera render blocks
 
-__global__ void k_cam_prepare(DevBA d, int candidate) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C) return;
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_prepare(LaunchSet ls, int candidate) {
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active) return;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C || (threadIdx.x & 31) != 0) return;
   const double* cam = (candidate ? d.cam_cand : d.cam) + 9 * (size_t)c;
   double* rb = (candidate ? d.camrb_cand : d.camrb) + 16 * (size_t)c;
   double R[9];
@@ -306,9 +378,11 @@ __global__ void k_cam_prepare(DevBA d, int candidate) {
 
 // ---------------------------------------------------------------- cost F(x)
 
-__global__ void __launch_bounds__(kThreads) k_cost(DevBA d, int candidate) {
+__global__ void __launch_bounds__(kThreads) k_cost(LaunchSet ls, int candidate) {
   __shared__ double red[kThreads];
-  const ChunkRange cr = chunk_range(d, blockIdx.x);
+  GPO_BIND(ch, kl)
+  if (!d.sc->active) return;
+  const ChunkRange cr = chunk_range(d, kl);
   const double* rbs = candidate ? d.camrb_cand : d.camrb;
   const double* pts = candidate ? d.pt_cand : d.pt;
   double acc = 0.0;
@@ -325,11 +399,14 @@ __global__ void __launch_bounds__(kThreads) k_cost(DevBA d, int candidate) {
     acc += 0.5 * o.rho;
   }
   const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) d.cost_part[blockIdx.x] = s;
+  if (threadIdx.x == 0) d.cost_part[kl] = s;
 }
 
-__global__ void k_cost_init(DevBA d) {
+__global__ void k_cost_init(LaunchSet ls) {
   __shared__ double red[kThreads];
+  __shared__ DevBA d;
+  bind_problem(d, ls.probs + blockIdx.x);
+  if (!d.sc->active) return;
   double acc = 0.0;
   for (int k = threadIdx.x; k < d.NCH; k += kThreads) acc += d.cost_part[k];
   const double s = block_sum(acc, red);
@@ -343,19 +420,20 @@ __global__ void k_cost_init(DevBA d) {
 // (H_cc = sum Jc^T Jc, b_c = sum Jc^T r).  H uses the stored (rounded) Jacobian; the
 // gradient uses the unrounded one, so BF16 storage leaves the LM fixed point intact.
 template <class JT>
-__global__ void __launch_bounds__(kThreads) k_linearize(DevBA d, int force) {
+__global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force) {
   using AT = typename AccOf<JT>::T;
   constexpr bool kSplit = !std::is_same<JT, AT>::value;
-  if (!force && !d.sc->need_lin) return;
+  GPO_BIND(ch, kl)
+  if (!d.sc->active || (!force && !d.sc->need_lin)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max;
   JT* Js = reinterpret_cast<JT*>(smem);               // [24][CH]
   AT* rs = reinterpret_cast<AT*>(Js + kJComp * CH);   // [2][CH]
   AT* bce = rs + 2 * CH;                              // [9][CH]  (kSplit only)
   AT* bpe = bce + 9 * CH;                             // [3][CH]  (kSplit only)
-  const ChunkRange cr = chunk_range(d, blockIdx.x);
-  JT* Jg = reinterpret_cast<JT*>(d.J) + d.ch_j0[blockIdx.x];
-  const int ldt = pad8(cr.nE);
+  uint16_t* srt = reinterpret_cast<uint16_t*>(kSplit ? bpe + 3 * CH : bce);   // [CH]
+  const ChunkRange cr = chunk_range(d, kl);
+  JT* Jg = reinterpret_cast<JT*>(d.J) + (size_t)cr.e0 * kJComp;
 
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
     const int e = cr.e0 + i;
@@ -378,22 +456,21 @@ __global__ void __launch_bounds__(kThreads) k_linearize(DevBA d, int force) {
       for (int k = 0; k < 3; ++k) Jp[0][k] = Jp[1][k] = (AT)0;
     }
     const AT rw0 = (AT)(o.sw * o.r[0]), rw1 = (AT)(o.sw * o.r[1]);
+    __align__(16) JT row[kJComp];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const JT v0 = cvj(Jc[0][k], (const JT*)nullptr), v1 = cvj(Jc[1][k], (const JT*)nullptr);
-      Jg[k * ldt + i] = v0;
-      Jg[(9 + k) * ldt + i] = v1;
-      Js[k * CH + i] = v0;
-      Js[(9 + k) * CH + i] = v1;
+      row[k] = cvj(Jc[0][k], (const JT*)nullptr);
+      row[9 + k] = cvj(Jc[1][k], (const JT*)nullptr);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const JT v0 = cvj(Jp[0][k], (const JT*)nullptr), v1 = cvj(Jp[1][k], (const JT*)nullptr);
-      Jg[(18 + k) * ldt + i] = v0;
-      Jg[(21 + k) * ldt + i] = v1;
-      Js[(18 + k) * CH + i] = v0;
-      Js[(21 + k) * CH + i] = v1;
+      row[18 + k] = cvj(Jp[0][k], (const JT*)nullptr);
+      row[21 + k] = cvj(Jp[1][k], (const JT*)nullptr);
     }
+    store_row(Jg + (size_t)i * kJComp, row);
+#pragma unroll
+    for (int k = 0; k < kJComp; ++k) Js[k * CH + i] = row[k];
+    srt[i] = d.ch_sorted[e];
     rs[i] = rw0;
     rs[CH + i] = rw1;
     if constexpr (kSplit) {
@@ -406,10 +483,6 @@ __global__ void __launch_bounds__(kThreads) k_linearize(DevBA d, int force) {
       d.dbg_r[2 * (size_t)e] = o.sw * o.r[0];
       d.dbg_r[2 * (size_t)e + 1] = o.sw * o.r[1];
     }
-  }
-  for (int i = cr.nE + threadIdx.x; i < ldt; i += kThreads) {
-#pragma unroll
-    for (int k = 0; k < kJComp; ++k) Jg[k * ldt + i] = cvj((AT)0, (const JT*)nullptr);
   }
   __syncthreads();
 
@@ -457,7 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(DevBA d, int force) {
 #pragma unroll
     for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
     for (int q = a; q < b; ++q) {
-      const int i = d.ch_sorted[q];
+      const int i = srt[q - cr.e0];
       if (grp < 5) {
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
@@ -519,16 +592,18 @@ __device__ __forceinline__ AT damp_diag(AT h, const Scalars* sc) {
 // One CTA per chunk: damped point inverses H_pp^-1 and per-slot partials of
 // sum_e W_e H_pp^-1 W_e^T (= Jc^T (Jp Hinv Jp^T) Jc) and sum_e W_e H_pp^-1 b_p.
 template <class JT>
-__global__ void __launch_bounds__(kThreads) k_schur_prepare(DevBA d) {
+__global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
+  GPO_BIND(ch, kl)
+  if (!d.sc->active) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max;
   JT* Jcs = reinterpret_cast<JT*>(smem);              // [18][CH]
   AT* Ae = reinterpret_cast<AT*>(Jcs + 18 * CH);      // [3][CH]
   AT* qe = Ae + 3 * CH;                               // [2][CH]
-  const ChunkRange cr = chunk_range(d, blockIdx.x);
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + d.ch_j0[blockIdx.x];
-  const int ldt = pad8(cr.nE);
+  uint16_t* srt = reinterpret_cast<uint16_t*>(qe + 2 * CH);   // [CH]
+  const ChunkRange cr = chunk_range(d, kl);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * kJComp;
   const Scalars* sc = d.sc;
   const AT lam = (AT)sc->lambda;
   const AT* Hpp = reinterpret_cast<const AT*>(d.Hpp);
@@ -558,14 +633,17 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(DevBA d) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) bb[k] = bp[3 * (size_t)pj + k];
     mul3(hi, bb, hb);
+    AT row[kJComp];
+    load_row(Jg + (size_t)i * kJComp, row);
     AT J0[3], J1[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      J0[k] = ldj(Jg + (18 + k) * ldt + i);
-      J1[k] = ldj(Jg + (21 + k) * ldt + i);
+      J0[k] = row[18 + k];
+      J1[k] = row[21 + k];
     }
 #pragma unroll
-    for (int k = 0; k < 18; ++k) Jcs[k * CH + i] = Jg[k * ldt + i];
+    for (int k = 0; k < 18; ++k) Jcs[k * CH + i] = cvj(row[k], (const JT*)nullptr);
+    srt[i] = d.ch_sorted[cr.e0 + i];
     AT t0[3], t1[3];
     mul3(hi, J0, t0);
     mul3(hi, J1, t1);
@@ -585,7 +663,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(DevBA d) {
 #pragma unroll
     for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
     for (int q = a; q < b; ++q) {
-      const int i = d.ch_sorted[q];
+      const int i = srt[q - cr.e0];
       if (grp < 5) {
         const AT a00 = Ae[i], a01 = Ae[CH + i], a11 = Ae[2 * CH + i];
 #pragma unroll
@@ -659,11 +737,13 @@ __device__ void spd_inverse9(const AT* S, AT* M) {
 // terms, forms H_cc + lambda D_c, S_cc, g_c and M_c = S_cc^-1, and starts the PCG
 // (x = 0, r = g, z = M g, p = z).  The last CTA reduces r^T z and |r|^2.
 template <class AT>
-__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(DevBA d) {
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls) {
   __shared__ AT vals[kCamPerBlock][2 * kPartA];
   __shared__ double red[kCamPerBlock][2];
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kCamPerBlock + warp;
+  const int c = cbl * kCamPerBlock + warp;
   Scalars* sc = d.sc;
   const AT lam = (AT)sc->lambda;
   const AT* partA = reinterpret_cast<const AT*>(d.partA);
@@ -671,13 +751,27 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(DevBA d) {
   double rz_c = 0.0, rr_c = 0.0;
   if (c < d.C) {
     const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
-    for (int o = lane; o < 2 * kPartA; o += 32) {
-      AT acc = (AT)0;
-      for (int s = sa; s < sb; ++s) {
-        const int slot = d.cam_s_list[s];
-        acc += o < kPartA ? partA[(size_t)slot * kPartA + o] : partB[(size_t)slot * kPartA + o - kPartA];
+    // 12 groups of 9 outputs; lanes stride over the camera's slots, then a fixed
+    // shuffle tree sums the lanes
+    for (int grp = 0; grp < 12; ++grp) {
+      const AT* base = (grp < 6 ? partA : partB) + 9 * (grp % 6);
+      AT acc[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] = (AT)0;
+      for (int s = sa + lane; s < sb; s += 32) {
+        const AT* src = base + (size_t)d.cam_s_list[s] * kPartA;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] += src[k];
       }
-      vals[warp][o] = acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) vals[warp][9 * grp + k] = acc[k];
+      }
     }
     __syncwarp();
     AT* Hcl = reinterpret_cast<AT*>(d.Hcl) + (size_t)c * kCamTri;
@@ -730,12 +824,12 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(DevBA d) {
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < kCamPerBlock; ++w) { a += red[w][0]; b += red[w][1]; }
-    d.cblk_part[2 * blockIdx.x] = a;
-    d.cblk_part[2 * blockIdx.x + 1] = b;
+    d.cblk_part[2 * cbl] = a;
+    d.cblk_part[2 * cbl + 1] = b;
   }
-  if (last_cta(&sc->ticket) && threadIdx.x == 0) {
+  if (last_cta(&sc->ticket, d.ncblk) && threadIdx.x == 0) {
     double rz = 0.0, rr = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
+    for (int b = 0; b < d.ncblk; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
     const double gn = sqrt(rr);
     sc->rz = rz;
     sc->gnorm = gn;
@@ -749,6 +843,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(DevBA d) {
     sc->save_best = 0;
     sc->tol_abs = sc->pcg_rel ? sc->pcg_tol * gn : sc->pcg_tol;
     sc->pcg_done = (rr == 0.0 || !(rz > 0.0) || !isfinite(rz)) ? 1 : 0;
+    if (!sc->pcg_done) atomicAdd(ls.running, 1);
     sc->ticket = 0u;
   }
 }
@@ -757,34 +852,43 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(DevBA d) {
 
 // Matrix-free Schur product, one CTA per chunk (the hot loop).  With t_p =
 // H_pp^-1 sum_e Jp_e^T Jc_e x_c(e), each edge contributes v_e = Jc_e^T Jp_e t_p(e) to
-// its camera; v is reduced per slot in a fixed order.  The chunk's Jacobian tile is
-// read from HBM once; the second pass over it hits L2.
+// its camera.  v_e is written to shared memory at the edge's slot-sorted position,
+// so each slot's sum is a contiguous range.  The chunk's Jacobian rows are read from
+// HBM once; the second pass over them hits L1/L2.
+constexpr int kMaxEdgesPerThread = 8;   // ch_max <= 2048 with 256 threads
+
 template <class JT>
-__global__ void __launch_bounds__(kThreads) k_spmv(DevBA d) {
+__global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
-  if (d.sc->pcg_done) return;
+  GPO_BIND(ch, kl)
+  if (!d.sc->active || d.sc->pcg_done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max;
   AT* vv = reinterpret_cast<AT*>(smem);    // [9][CH]; first [3][CH] hold a_e in pass 1
   AT* tp = vv + 9 * CH;                    // [3][CH] per point of the chunk
-  const ChunkRange cr = chunk_range(d, blockIdx.x);
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + d.ch_j0[blockIdx.x];
-  const int ldt = pad8(cr.nE);
+  const ChunkRange cr = chunk_range(d, kl);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * kJComp;
   const AT* xv = reinterpret_cast<const AT*>(d.p);
+  uint16_t mypos[kMaxEdgesPerThread];
 
-  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+#pragma unroll
+  for (int m = 0; m < kMaxEdgesPerThread; ++m) {
+    const int i = threadIdx.x + m * kThreads;
+    if (i >= cr.nE) break;
     const int c = __ldg(d.e_cam + cr.e0 + i);
+    mypos[m] = __ldg(d.e_pos + cr.e0 + i);
+    AT row[kJComp];
+    load_row(Jg + (size_t)i * kJComp, row);
     const AT* xc = xv + 9 * (size_t)c;
     AT q0 = (AT)0, q1 = (AT)0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const AT xk = xc[k];
-      q0 += ldj(Jg + k * ldt + i) * xk;
-      q1 += ldj(Jg + (9 + k) * ldt + i) * xk;
+      q0 += row[k] * xk;
+      q1 += row[9 + k] * xk;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      vv[k * CH + i] = ldj(Jg + (18 + k) * ldt + i) * q0 + ldj(Jg + (21 + k) * ldt + i) * q1;
+    for (int k = 0; k < 3; ++k) vv[k * CH + i] = row[18 + k] * q0 + row[21 + k] * q1;
   }
   __syncthreads();
   const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
@@ -804,22 +908,28 @@ __global__ void __launch_bounds__(kThreads) k_spmv(DevBA d) {
     for (int k = 0; k < 3; ++k) tp[k * CH + j] = t[k];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+#pragma unroll
+  for (int m = 0; m < kMaxEdgesPerThread; ++m) {
+    const int i = threadIdx.x + m * kThreads;
+    if (i >= cr.nE) break;
     const int pl = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
     const AT t0 = tp[pl], t1 = tp[CH + pl], t2 = tp[2 * CH + pl];
-    const AT s0 = ldj(Jg + 18 * ldt + i) * t0 + ldj(Jg + 19 * ldt + i) * t1 + ldj(Jg + 20 * ldt + i) * t2;
-    const AT s1 = ldj(Jg + 21 * ldt + i) * t0 + ldj(Jg + 22 * ldt + i) * t1 + ldj(Jg + 23 * ldt + i) * t2;
+    AT row[kJComp];
+    load_row(Jg + (size_t)i * kJComp, row);
+    const AT s0 = row[18] * t0 + row[19] * t1 + row[20] * t2;
+    const AT s1 = row[21] * t0 + row[22] * t1 + row[23] * t2;
+    const int pos = mypos[m];
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-      vv[k * CH + i] = ldj(Jg + k * ldt + i) * s0 + ldj(Jg + (9 + k) * ldt + i) * s1;
+    for (int k = 0; k < 9; ++k) vv[k * CH + pos] = row[k] * s0 + row[9 + k] * s1;
   }
   __syncthreads();
   AT* partV = reinterpret_cast<AT*>(d.partV);
   for (int w = threadIdx.x; w < cr.nS * 9; w += kThreads) {
     const int sl = w / 9, comp = w - sl * 9;
-    const int a = d.slot_e0[cr.s0 + sl], b = d.slot_e0[cr.s0 + sl + 1];
+    const int a = d.slot_e0[cr.s0 + sl] - cr.e0, b = d.slot_e0[cr.s0 + sl + 1] - cr.e0;
+    const AT* src = vv + comp * CH;
     AT acc = (AT)0;
-    for (int q = a; q < b; ++q) acc += vv[comp * CH + d.ch_sorted[q]];
+    for (int q = a; q < b; ++q) acc += src[q];
     partV[(size_t)(cr.s0 + sl) * 9 + comp] = acc;
   }
 }
@@ -827,25 +937,45 @@ __global__ void __launch_bounds__(kThreads) k_spmv(DevBA d) {
 // One warp per camera: y_c = (H_cc + lambda D_c) p_c - sum_slots v; the last CTA
 // reduces p^T y and sets alpha = r^T z / p^T y.
 template <class AT>
-__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(DevBA d) {
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   __shared__ double red[kCamPerBlock];
+  GPO_BIND(cb, cbl)
   Scalars* sc = d.sc;
-  if (sc->pcg_done) return;
+  if (!sc->active || sc->pcg_done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kCamPerBlock + warp;
+  const int c = cbl * kCamPerBlock + warp;
   double dot = 0.0;
-  if (c < d.C && lane < 9) {
+  if (c < d.C) {   // warp-uniform
     const AT* partV = reinterpret_cast<const AT*>(d.partV);
     const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
+    AT acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = (AT)0;
+    for (int s = sa + lane; s < sb; s += 32) {
+      const AT* src = partV + (size_t)d.cam_s_list[s] * 9;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] += src[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    }
     AT sv = (AT)0;
-    for (int s = sa; s < sb; ++s) sv += partV[(size_t)d.cam_s_list[s] * 9 + lane];
-    const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * kCamTri;
-    const AT* pc = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
-    AT yi = (AT)0;
-    for (int j = 0; j < 9; ++j) yi += H[sym9(lane, j)] * pc[j];
-    yi -= sv;
-    reinterpret_cast<AT*>(d.y)[9 * (size_t)c + lane] = yi;
-    dot = (double)pc[lane] * (double)yi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const AT v = __shfl_sync(0xffffffffu, acc[k], 0);
+      if (lane == k) sv = v;
+    }
+    if (lane < 9) {
+      const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * kCamTri;
+      const AT* pc = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
+      AT yi = (AT)0;
+      for (int j = 0; j < 9; ++j) yi += H[sym9(lane, j)] * pc[j];
+      yi -= sv;
+      reinterpret_cast<AT*>(d.y)[9 * (size_t)c + lane] = yi;
+      dot = (double)pc[lane] * (double)yi;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
@@ -854,15 +984,16 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(DevBA d) {
   if (threadIdx.x == 0) {
     double a = 0.0;
     for (int w = 0; w < kCamPerBlock; ++w) a += red[w];
-    d.cblk_part[2 * blockIdx.x] = a;
+    d.cblk_part[2 * cbl] = a;
   }
-  if (last_cta(&sc->ticket) && threadIdx.x == 0) {
+  if (last_cta(&sc->ticket, d.ncblk) && threadIdx.x == 0) {
     double pAp = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) pAp += d.cblk_part[2 * b];
+    for (int b = 0; b < d.ncblk; ++b) pAp += d.cblk_part[2 * b];
     sc->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       sc->alpha = 0.0;
       sc->pcg_done = 1;
+      atomicSub(ls.running, 1);
     } else {
       sc->alpha = sc->rz / pAp;
     }
@@ -870,58 +1001,63 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(DevBA d) {
   }
 }
 
-// One thread per camera: x += sigma alpha p, r -= alpha y, z = M r; the last CTA
-// reduces r^T z and |r|^2, applies the stopping rules (tolerance, rejection ratio,
-// iteration cap) and computes beta and the normalisation factor.
+// One warp per camera: x += sigma alpha p, r -= alpha y, z = M r; the last CTA of
+// the problem reduces r^T z and |r|^2, applies the stopping rules (tolerance,
+// rejection ratio, iteration cap) and computes beta and the normalisation factor.
 template <class AT>
-__global__ void __launch_bounds__(256) k_pcg_update(DevBA d) {
-  __shared__ double red[2][256];
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) {
+  __shared__ double red[kCamPerBlock][2];
+  GPO_BIND(cb, cbl)
   Scalars* sc = d.sc;
-  if (sc->pcg_done) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!sc->active || sc->pcg_done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + warp;
   double rz_c = 0.0, rr_c = 0.0;
-  if (c < d.C) {
+  if (c < d.C) {   // warp-uniform
     const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha);
     AT* x = reinterpret_cast<AT*>(d.x) + 9 * (size_t)c;
     AT* r = reinterpret_cast<AT*>(d.r) + 9 * (size_t)c;
     AT* z = reinterpret_cast<AT*>(d.z) + 9 * (size_t)c;
-    const AT* p = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
-    const AT* y = reinterpret_cast<const AT*>(d.y) + 9 * (size_t)c;
+    const AT* pv = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
+    const AT* yv = reinterpret_cast<const AT*>(d.y) + 9 * (size_t)c;
     const AT* M = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * kCamTri;
-    AT rl[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      x[i] += sa * p[i];
-      rl[i] = r[i] - alpha * y[i];
-      r[i] = rl[i];
+    AT ri = (AT)0;
+    if (lane < 9) {
+      x[lane] += sa * pv[lane];
+      ri = r[lane] - alpha * yv[lane];
+      r[lane] = ri;
     }
+    AT zi = (AT)0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      AT zi = (AT)0;
-#pragma unroll
-      for (int j = 0; j < 9; ++j) zi += M[sym9(i, j)] * rl[j];
-      z[i] = zi;
-      rz_c += (double)rl[i] * (double)zi;
-      rr_c += (double)rl[i] * (double)rl[i];
+    for (int j = 0; j < 9; ++j) {
+      const AT rj = __shfl_sync(0xffffffffu, ri, j);
+      if (lane < 9) zi += M[sym9(lane, j)] * rj;
+    }
+    if (lane < 9) {
+      z[lane] = zi;
+      rz_c = (double)ri * (double)zi;
+      rr_c = (double)ri * (double)ri;
     }
   }
-  red[0][threadIdx.x] = rz_c;
-  red[1][threadIdx.x] = rr_c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rz_c += __shfl_down_sync(0xffffffffu, rz_c, o);
+    rr_c += __shfl_down_sync(0xffffffffu, rr_c, o);
+  }
+  if (lane == 0) {
+    red[warp][0] = rz_c;
+    red[warp][1] = rr_c;
+  }
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + s];
-      red[1][threadIdx.x] += red[1][threadIdx.x + s];
-    }
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    d.cblk_part[2 * blockIdx.x] = red[0][0];
-    d.cblk_part[2 * blockIdx.x + 1] = red[1][0];
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kCamPerBlock; ++w) { a += red[w][0]; b += red[w][1]; }
+    d.cblk_part[2 * cbl] = a;
+    d.cblk_part[2 * cbl + 1] = b;
   }
-  if (last_cta(&sc->ticket) && threadIdx.x == 0) {
+  if (last_cta(&sc->ticket, d.ncblk) && threadIdx.x == 0) {
     double rz = 0.0, rr = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
+    for (int b = 0; b < d.ncblk; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
     const double n = sqrt(rr);
     const double rtrue = sc->sigma * n;
     sc->pcg_it += 1;
@@ -952,32 +1088,31 @@ __global__ void __launch_bounds__(256) k_pcg_update(DevBA d) {
       sc->rz = rz;
     }
     sc->pcg_done = done;
+    if (done) atomicSub(ls.running, 1);
     sc->ticket = 0u;
   }
 }
 
-// One thread per camera: keep the best iterate, then p = (z + beta p) / n and
-// r, z scaled by 1/n (n = 1 without normalisation).
+// One warp per camera: keep the best iterate, then p = (z + beta p) / n and r, z
+// scaled by 1/n (n = 1 without normalisation).
 template <class AT>
-__global__ void k_pcg_direction(DevBA d) {
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_direction(LaunchSet ls) {
+  GPO_BIND(cb, cbl)
   const Scalars* sc = d.sc;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C) return;
-  if (sc->save_best) {
-    const AT* x = reinterpret_cast<const AT*>(d.x) + 9 * (size_t)c;
-    AT* xb = reinterpret_cast<AT*>(d.xbest) + 9 * (size_t)c;
-    for (int i = 0; i < 9; ++i) xb[i] = x[i];
-  }
+  if (!sc->active) return;
+  const int lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C || lane >= 9) return;
+  const size_t o = 9 * (size_t)c + lane;
+  if (sc->save_best) reinterpret_cast<AT*>(d.xbest)[o] = reinterpret_cast<const AT*>(d.x)[o];
   if (sc->pcg_done) return;
-  const AT beta = (AT)sc->beta, s = (AT)sc->inv_n;
-  AT* p = reinterpret_cast<AT*>(d.p) + 9 * (size_t)c;
-  AT* r = reinterpret_cast<AT*>(d.r) + 9 * (size_t)c;
-  AT* z = reinterpret_cast<AT*>(d.z) + 9 * (size_t)c;
-  for (int i = 0; i < 9; ++i) {
-    p[i] = (z[i] + beta * p[i]) * s;
-    r[i] *= s;
-    z[i] *= s;
-  }
+  const AT beta = (AT)sc->beta, sn = (AT)sc->inv_n;
+  AT* p = reinterpret_cast<AT*>(d.p);
+  AT* r = reinterpret_cast<AT*>(d.r);
+  AT* z = reinterpret_cast<AT*>(d.z);
+  p[o] = (z[o] + beta * p[o]) * sn;
+  r[o] *= sn;
+  z[o] *= sn;
 }
 
 // ---------------------------------------------------------------- back-substitution
@@ -985,34 +1120,36 @@ __global__ void k_pcg_direction(DevBA d) {
 // One CTA per chunk: dp = H_pp^-1 (-b_p - sum_e Jp^T Jc dc) and the chunk's share of
 // the model decrease -b_p^T dp - 1/2 sum_e |Jc dc + Jp dp|^2 (FP64 accumulation).
 template <class JT>
-__global__ void __launch_bounds__(kThreads) k_backsub(DevBA d) {
+__global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   __shared__ double red[kThreads];
+  GPO_BIND(ch, kl)
+  if (!d.sc->active) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max;
   AT* qv = reinterpret_cast<AT*>(smem);   // [2][CH]
   AT* av = qv + 2 * CH;                   // [3][CH]
-  const ChunkRange cr = chunk_range(d, blockIdx.x);
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + d.ch_j0[blockIdx.x];
-  const int ldt = pad8(cr.nE);
+  const ChunkRange cr = chunk_range(d, kl);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * kJComp;
   const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x);
   const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
   const AT* bp = reinterpret_cast<const AT*>(d.bp);
   AT* dp = reinterpret_cast<AT*>(d.dp);
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
     const int c = __ldg(d.e_cam + cr.e0 + i);
+    AT row[kJComp];
+    load_row(Jg + (size_t)i * kJComp, row);
     AT q0 = (AT)0, q1 = (AT)0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const AT xk = xs[9 * (size_t)c + k];
-      q0 += ldj(Jg + k * ldt + i) * xk;
-      q1 += ldj(Jg + (9 + k) * ldt + i) * xk;
+      q0 += row[k] * xk;
+      q1 += row[9 + k] * xk;
     }
     qv[i] = q0;
     qv[CH + i] = q1;
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      av[k * CH + i] = ldj(Jg + (18 + k) * ldt + i) * q0 + ldj(Jg + (21 + k) * ldt + i) * q1;
+    for (int k = 0; k < 3; ++k) av[k * CH + i] = row[18 + k] * q0 + row[21 + k] * q1;
   }
   __syncthreads();
   double md = 0.0;
@@ -1040,22 +1177,24 @@ __global__ void __launch_bounds__(kThreads) k_backsub(DevBA d) {
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
     const int pj = __ldg(d.e_pt + cr.e0 + i);
     const AT t0 = dp[3 * (size_t)pj], t1 = dp[3 * (size_t)pj + 1], t2 = dp[3 * (size_t)pj + 2];
-    const double j0 = (double)(qv[i] + ldj(Jg + 18 * ldt + i) * t0 + ldj(Jg + 19 * ldt + i) * t1 +
-                               ldj(Jg + 20 * ldt + i) * t2);
-    const double j1 = (double)(qv[CH + i] + ldj(Jg + 21 * ldt + i) * t0 + ldj(Jg + 22 * ldt + i) * t1 +
-                               ldj(Jg + 23 * ldt + i) * t2);
+    AT row[kJComp];
+    load_row(Jg + (size_t)i * kJComp, row);
+    const double j0 = (double)(qv[i] + row[18] * t0 + row[19] * t1 + row[20] * t2);
+    const double j1 = (double)(qv[CH + i] + row[21] * t0 + row[22] * t1 + row[23] * t2);
     md -= 0.5 * (j0 * j0 + j1 * j1);
   }
   const double s = block_sum(md, red);
-  if (threadIdx.x == 0) d.md_part[blockIdx.x] = s;
+  if (threadIdx.x == 0) d.md_part[kl] = s;
 }
 
 // ---------------------------------------------------------------- retraction (FP64)
 
 template <class AT>
-__global__ void k_retract_cams(DevBA d) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C) return;
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_retract_cams(LaunchSet ls) {
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active) return;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C || (threadIdx.x & 31) != 0) return;
   const double* cur = d.cam + 9 * (size_t)c;
   double* nxt = d.cam_cand + 9 * (size_t)c;
   double* rb = d.camrb_cand + 16 * (size_t)c;
@@ -1081,8 +1220,10 @@ __global__ void k_retract_cams(DevBA d) {
 }
 
 template <class AT>
-__global__ void k_retract_pts(DevBA d) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_retract_pts(LaunchSet ls) {
+  GPO_BIND(pb, pbl)
+  if (!d.sc->active) return;
+  const int p = pbl * 256 + threadIdx.x;
   if (p >= d.P) return;
   const AT* dp = reinterpret_cast<const AT*>(d.dp) + 3 * (size_t)p;
   for (int i = 0; i < 3; ++i)
@@ -1092,9 +1233,12 @@ __global__ void k_retract_pts(DevBA d) {
 // ---------------------------------------------------------------- LM decision (FP64)
 
 template <class AT>
-__global__ void __launch_bounds__(kThreads) k_decide(DevBA d) {
+__global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
   __shared__ double red[kThreads];
+  __shared__ DevBA d;
+  bind_problem(d, ls.probs + blockIdx.x);
   Scalars* sc = d.sc;
+  if (!sc->active) return;
   double fc = 0.0, md = 0.0;
   for (int k = threadIdx.x; k < d.NCH; k += kThreads) {
     fc += d.cost_part[k];
@@ -1142,34 +1286,39 @@ __global__ void __launch_bounds__(kThreads) k_decide(DevBA d) {
   sc->iter = it + 1;
 }
 
-__global__ void k_commit(DevBA d) {
-  if (!d.sc->accepted) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < d.C) {
-    for (int k = 0; k < 9; ++k) d.cam[9 * (size_t)i + k] = d.cam_cand[9 * (size_t)i + k];
-    for (int k = 0; k < 16; ++k) d.camrb[16 * (size_t)i + k] = d.camrb_cand[16 * (size_t)i + k];
-  }
-  if (i < d.P) {
-    for (int k = 0; k < 3; ++k) d.pt[3 * (size_t)i + k] = d.pt_cand[3 * (size_t)i + k];
-  }
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_commit_cams(LaunchSet ls) {
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active || !d.sc->accepted) return;
+  const int lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C) return;
+  if (lane < 9) d.cam[9 * (size_t)c + lane] = d.cam_cand[9 * (size_t)c + lane];
+  if (lane < 16) d.camrb[16 * (size_t)c + lane] = d.camrb_cand[16 * (size_t)c + lane];
+}
+
+__global__ void __launch_bounds__(256) k_commit_pts(LaunchSet ls) {
+  GPO_BIND(pb, pbl)
+  if (!d.sc->active || !d.sc->accepted) return;
+  const int p = pbl * 256 + threadIdx.x;
+  if (p >= d.P) return;
+  for (int k = 0; k < 3; ++k) d.pt[3 * (size_t)p + k] = d.pt_cand[3 * (size_t)p + k];
 }
 
 // ---------------------------------------------------------------- launchers
 
-static inline int blocks_for(int n, int t) { return n > 0 ? (n + t - 1) / t : 1; }
 
 int default_ch_max(Prec pr) { return pr == Prec::F64 ? 512 : 1024; }
 
 static size_t lin_smem(Prec pr, int ch) {
   const size_t sJ = pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2);
   const size_t sA = pr == Prec::F64 ? 8 : 4;
-  const size_t per = kJComp * sJ + 2 * sA + (pr == Prec::BF16 ? 12 * sA : 0);
+  const size_t per = kJComp * sJ + 2 * sA + (pr == Prec::BF16 ? 12 * sA : 0) + 2;
   return per * (size_t)ch;
 }
 static size_t schur_smem(Prec pr, int ch) {
   const size_t sJ = pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2);
   const size_t sA = pr == Prec::F64 ? 8 : 4;
-  return (18 * sJ + 5 * sA) * (size_t)ch;
+  return (18 * sJ + 5 * sA + 2) * (size_t)ch;
 }
 static size_t spmv_smem(Prec pr, int ch) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
@@ -1205,107 +1354,123 @@ static void set_smem(const void* kernel, size_t bytes) {
   if (n < 32) { keys[n] = kernel; vals[n] = bytes; ++n; }
 }
 
-void launch_cam_prepare(const DevBA& d, bool candidate, cudaStream_t st) {
-  if (d.C == 0) return;
-  k_cam_prepare<<<blocks_for(d.C, 128), 128, 0, st>>>(d, candidate ? 1 : 0);
-}
-
-void launch_cost(const DevBA& d, bool candidate, cudaStream_t st) {
-  if (d.NCH == 0) return;
-  k_cost<<<d.NCH, kThreads, 0, st>>>(d, candidate ? 1 : 0);
-}
-
-void launch_cost_init(const DevBA& d, cudaStream_t st) { k_cost_init<<<1, kThreads, 0, st>>>(d); }
-
-template <class JT>
-static void lin_t(const DevBA& d, Prec pr, bool force, cudaStream_t st) {
-  const size_t sm = lin_smem(pr, d.ch_max);
-  set_smem(reinterpret_cast<const void*>(k_linearize<JT>), sm);
-  k_linearize<JT><<<d.NCH, kThreads, sm, st>>>(d, force ? 1 : 0);
-}
-void launch_linearize(const DevBA& d, Prec pr, bool force, cudaStream_t st) {
-  if (d.NCH == 0) return;
-  if (pr == Prec::F64) lin_t<double>(d, pr, force, st);
-  else if (pr == Prec::F32) lin_t<float>(d, pr, force, st);
-  else lin_t<__nv_bfloat16>(d, pr, force, st);
-}
-
-template <class JT>
-static void schur_t(const DevBA& d, Prec pr, cudaStream_t st) {
-  const size_t sm = schur_smem(pr, d.ch_max);
-  set_smem(reinterpret_cast<const void*>(k_schur_prepare<JT>), sm);
-  k_schur_prepare<JT><<<d.NCH, kThreads, sm, st>>>(d);
-}
-void launch_schur_prepare(const DevBA& d, Prec pr, cudaStream_t st) {
-  if (d.NCH == 0) return;
-  if (pr == Prec::F64) schur_t<double>(d, pr, st);
-  else if (pr == Prec::F32) schur_t<float>(d, pr, st);
-  else schur_t<__nv_bfloat16>(d, pr, st);
-}
-
-void launch_cam_finalize(const DevBA& d, Prec pr, cudaStream_t st) {
-  if (pr == Prec::F64) k_cam_finalize<double><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
-  else k_cam_finalize<float><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
-}
-
-template <class JT>
-static void spmv_t(const DevBA& d, Prec pr, cudaStream_t st) {
-  const size_t sm = spmv_smem(pr, d.ch_max);
-  set_smem(reinterpret_cast<const void*>(k_spmv<JT>), sm);
-  k_spmv<JT><<<d.NCH, kThreads, sm, st>>>(d);
-}
-int launch_pcg_spmv(const DevBA& d, Prec pr, cudaStream_t st) {
-  if (d.NCH == 0) return 0;
-  if (pr == Prec::F64) spmv_t<double>(d, pr, st);
-  else if (pr == Prec::F32) spmv_t<float>(d, pr, st);
-  else spmv_t<__nv_bfloat16>(d, pr, st);
+int launch_cam_prepare(const LaunchSet& ls, bool candidate, cudaStream_t st) {
+  if (ls.n_cb == 0) return 0;
+  k_cam_prepare<<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls, candidate ? 1 : 0);
   return 1;
 }
-int launch_pcg_vector(const DevBA& d, Prec pr, cudaStream_t st) {
-  const int nb = blocks_for(d.C, 256);
+
+int launch_cost(const LaunchSet& ls, bool candidate, cudaStream_t st) {
+  if (ls.n_ch == 0) return 0;
+  k_cost<<<ls.n_ch, kThreads, 0, st>>>(ls, candidate ? 1 : 0);
+  return 1;
+}
+
+int launch_cost_init(const LaunchSet& ls, cudaStream_t st) {
+  k_cost_init<<<ls.nprob, kThreads, 0, st>>>(ls);
+  return 1;
+}
+
+template <class JT>
+static void lin_t(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st) {
+  const size_t sm = lin_smem(pr, ls.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_linearize<JT>), sm);
+  k_linearize<JT><<<ls.n_ch, kThreads, sm, st>>>(ls, force ? 1 : 0);
+}
+int launch_linearize(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st) {
+  if (ls.n_ch == 0) return 0;
+  if (pr == Prec::F64) lin_t<double>(ls, pr, force, st);
+  else if (pr == Prec::F32) lin_t<float>(ls, pr, force, st);
+  else lin_t<__nv_bfloat16>(ls, pr, force, st);
+  return 1;
+}
+
+template <class JT>
+static void schur_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  const size_t sm = schur_smem(pr, ls.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_schur_prepare<JT>), sm);
+  k_schur_prepare<JT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+}
+int launch_schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_ch == 0) return 0;
+  if (pr == Prec::F64) schur_t<double>(ls, pr, st);
+  else if (pr == Prec::F32) schur_t<float>(ls, pr, st);
+  else schur_t<__nv_bfloat16>(ls, pr, st);
+  return 1;
+}
+
+int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_cb == 0) return 0;
+  if (pr == Prec::F64) k_cam_finalize<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  else k_cam_finalize<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  return 1;
+}
+
+template <class JT>
+static void spmv_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  const size_t sm = spmv_smem(pr, ls.ch_max);
+  set_smem(reinterpret_cast<const void*>(k_spmv<JT>), sm);
+  k_spmv<JT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+}
+int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_ch == 0) return 0;
+  if (pr == Prec::F64) spmv_t<double>(ls, pr, st);
+  else if (pr == Prec::F32) spmv_t<float>(ls, pr, st);
+  else spmv_t<__nv_bfloat16>(ls, pr, st);
+  return 1;
+}
+int launch_pcg_vector(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_cb == 0) return 0;
+  const int nb = ls.n_cb, nt = kCamPerBlock * 32;
   if (pr == Prec::F64) {
-    k_cam_apply<double><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
-    k_pcg_update<double><<<nb, 256, 0, st>>>(d);
-    k_pcg_direction<double><<<nb, 256, 0, st>>>(d);
+    k_cam_apply<double><<<nb, nt, 0, st>>>(ls);
+    k_pcg_update<double><<<nb, nt, 0, st>>>(ls);
+    k_pcg_direction<double><<<nb, nt, 0, st>>>(ls);
   } else {
-    k_cam_apply<float><<<d.ncblk, kCamPerBlock * 32, 0, st>>>(d);
-    k_pcg_update<float><<<nb, 256, 0, st>>>(d);
-    k_pcg_direction<float><<<nb, 256, 0, st>>>(d);
+    k_cam_apply<float><<<nb, nt, 0, st>>>(ls);
+    k_pcg_update<float><<<nb, nt, 0, st>>>(ls);
+    k_pcg_direction<float><<<nb, nt, 0, st>>>(ls);
   }
   return 3;
 }
 
 template <class JT>
-static void backsub_t(const DevBA& d, Prec pr, cudaStream_t st) {
-  const size_t sm = backsub_smem(pr, d.ch_max);
+static void backsub_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  const size_t sm = backsub_smem(pr, ls.ch_max);
   set_smem(reinterpret_cast<const void*>(k_backsub<JT>), sm);
-  k_backsub<JT><<<d.NCH, kThreads, sm, st>>>(d);
+  k_backsub<JT><<<ls.n_ch, kThreads, sm, st>>>(ls);
 }
-void launch_backsub(const DevBA& d, Prec pr, cudaStream_t st) {
-  if (d.NCH == 0) return;
-  if (pr == Prec::F64) backsub_t<double>(d, pr, st);
-  else if (pr == Prec::F32) backsub_t<float>(d, pr, st);
-  else backsub_t<__nv_bfloat16>(d, pr, st);
+int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_ch == 0) return 0;
+  if (pr == Prec::F64) backsub_t<double>(ls, pr, st);
+  else if (pr == Prec::F32) backsub_t<float>(ls, pr, st);
+  else backsub_t<__nv_bfloat16>(ls, pr, st);
+  return 1;
 }
 
-void launch_retract(const DevBA& d, Prec pr, cudaStream_t st) {
+int launch_retract(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  int n = 0;
   if (pr == Prec::F64) {
-    if (d.C) k_retract_cams<double><<<blocks_for(d.C, 128), 128, 0, st>>>(d);
-    if (d.P) k_retract_pts<double><<<blocks_for(d.P, 256), 256, 0, st>>>(d);
+    if (ls.n_cb) { k_retract_cams<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls); ++n; }
+    if (ls.n_pb) { k_retract_pts<double><<<ls.n_pb, 256, 0, st>>>(ls); ++n; }
   } else {
-    if (d.C) k_retract_cams<float><<<blocks_for(d.C, 128), 128, 0, st>>>(d);
-    if (d.P) k_retract_pts<float><<<blocks_for(d.P, 256), 256, 0, st>>>(d);
+    if (ls.n_cb) { k_retract_cams<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls); ++n; }
+    if (ls.n_pb) { k_retract_pts<float><<<ls.n_pb, 256, 0, st>>>(ls); ++n; }
   }
+  return n;
 }
 
-void launch_decide(const DevBA& d, Prec pr, cudaStream_t st) {
-  if (pr == Prec::F64) k_decide<double><<<1, kThreads, 0, st>>>(d);
-  else k_decide<float><<<1, kThreads, 0, st>>>(d);
+int launch_decide(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (pr == Prec::F64) k_decide<double><<<ls.nprob, kThreads, 0, st>>>(ls);
+  else k_decide<float><<<ls.nprob, kThreads, 0, st>>>(ls);
+  return 1;
 }
 
-void launch_commit(const DevBA& d, cudaStream_t st) {
-  const int n = d.C > d.P ? d.C : d.P;
-  if (n) k_commit<<<blocks_for(n, 256), 256, 0, st>>>(d);
+int launch_commit(const LaunchSet& ls, cudaStream_t st) {
+  int n = 0;
+  if (ls.n_cb) { k_commit_cams<<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls); ++n; }
+  if (ls.n_pb) { k_commit_pts<<<ls.n_pb, 256, 0, st>>>(ls); ++n; }
+  return n;
 }
 
 }  // namespace gpo

@@ -9,8 +9,8 @@
 //    camera contributions per slot in a fixed order (edges pre-sorted by slot) and
 //    writes one partial per slot; a camera sums its slots' partials in chunk order.
 //    Every reduction therefore has a fixed order: runs are bit-reproducible;
-//  * Jacobians are stored per chunk as a tile [24][pad8(n_edges)] (component-major),
-//    so a chunk's Jacobian is one contiguous, 16-byte aligned range.
+//  * Jacobians are stored edge-major, one 24-value row per edge in point-major edge
+//    order (48 / 96 / 192 bytes in BF16 / FP32 / FP64: 16-byte vector accesses).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -48,6 +48,8 @@ struct Scalars {
   int pcg_rel;
   int pcg_it, pcg_done, use_best, save_best, normalize, max_it;
   unsigned int ticket;   // last-CTA counter of the reductions
+  int active;            // the problem takes part in the current launches
+  int lm_max;            // LM iterations to run (the problem deactivates after them)
   int pad_;
 };
 
@@ -71,8 +73,7 @@ struct DevBA {
   const int* ch_e0;          // [NCH+1]
   const int* ch_p0;          // [NCH+1]
   const int* ch_s0;          // [NCH+1]
-  const long long* ch_j0;    // [NCH] element offset of the chunk's Jacobian tile
-  const uint16_t* e_slot;    // [E] slot of the edge inside its chunk
+  const uint16_t* e_pos;     // [E] position of the edge in its chunk's slot-sorted order
   const uint16_t* ch_sorted; // [E] per chunk: local edge ids sorted by (slot, id)
   const int* slot_e0;        // [NS+1] range of a slot in ch_sorted (global positions)
   const int* slot_cam;       // [NS]
@@ -88,7 +89,7 @@ struct DevBA {
   double* pt;                // [P][3]
   double* pt_cand;           // [P][3]
   // linear system
-  void* J;                   // JT tiles
+  void* J;                   // JT [E][24] edge-major rows
   void* Hpp;                 // AT [P][6] undamped point blocks
   void* bp;                  // AT [P][3]
   void* Hinv;                // AT [P][6] damped inverses
@@ -114,19 +115,36 @@ struct DevBA {
 
 enum class Prec { F64 = 0, F32 = 1, BF16 = 2 };
 
+// A launch over several independent problems (one problem for a plain graph).
+// Every CTA finds its problem through a schedule table and binds that problem's
+// DevBA (device copy) in shared memory:
+//  * chunk CTAs (per-edge kernels): ch_prob[b], local chunk b - ch_base[problem];
+//  * camera CTAs (8 cameras, one warp each): cb_prob[b], local block b - cb_base[..];
+//  * point CTAs (256 points): pb_prob[b], local block b - pb_base[..];
+//  * problem CTAs (decisions, reductions): CTA b is problem b.
+struct LaunchSet {
+  const DevBA* probs;
+  const int* ch_prob; const int* ch_base;
+  const int* cb_prob; const int* cb_base;
+  const int* pb_prob; const int* pb_base;
+  int* running;          // problems whose PCG is still iterating
+  int nprob, n_ch, n_cb, n_pb;
+  int ch_max;            // largest chunk over the problems (shared-memory sizing)
+};
+
 // Kernel launchers (ba_kernels.cu).  All are asynchronous on `st`.
-void launch_cam_prepare(const DevBA& d, bool candidate, cudaStream_t st);
-void launch_cost(const DevBA& d, bool candidate, cudaStream_t st);
-void launch_cost_init(const DevBA& d, cudaStream_t st);
-void launch_linearize(const DevBA& d, Prec pr, bool force, cudaStream_t st);
-void launch_schur_prepare(const DevBA& d, Prec pr, cudaStream_t st);
-void launch_cam_finalize(const DevBA& d, Prec pr, cudaStream_t st);
-int launch_pcg_spmv(const DevBA& d, Prec pr, cudaStream_t st);      // the Schur product (hot loop)
-int launch_pcg_vector(const DevBA& d, Prec pr, cudaStream_t st);    // camera apply, update, direction
-void launch_backsub(const DevBA& d, Prec pr, cudaStream_t st);
-void launch_retract(const DevBA& d, Prec pr, cudaStream_t st);
-void launch_decide(const DevBA& d, Prec pr, cudaStream_t st);
-void launch_commit(const DevBA& d, cudaStream_t st);
+int launch_cam_prepare(const LaunchSet& ls, bool candidate, cudaStream_t st);
+int launch_cost(const LaunchSet& ls, bool candidate, cudaStream_t st);
+int launch_cost_init(const LaunchSet& ls, cudaStream_t st);
+int launch_linearize(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st);
+int launch_schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st);
+int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st);
+int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st);      // the Schur product (hot loop)
+int launch_pcg_vector(const LaunchSet& ls, Prec pr, cudaStream_t st);    // camera apply, update, direction
+int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st);
+int launch_retract(const LaunchSet& ls, Prec pr, cudaStream_t st);
+int launch_decide(const LaunchSet& ls, Prec pr, cudaStream_t st);
+int launch_commit(const LaunchSet& ls, cudaStream_t st);
 size_t smem_bytes_linearize(Prec pr, int ch_max);
 int default_ch_max(Prec pr);
 int max_supported_ch(Prec pr);

@@ -132,6 +132,30 @@ def _angle_axis_from_quat(q: np.ndarray) -> np.ndarray:
     return v * scale[:, None]
 
 
+def _quat_from_angle_axis(w: np.ndarray) -> np.ndarray:
+    th = np.linalg.norm(w, axis=1)
+    half = 0.5 * th
+    k = np.where(th > 1e-12, np.sin(half) / np.where(th > 1e-12, th, 1.0), 0.5)
+    return np.concatenate([np.cos(half)[:, None], w * k[:, None]], axis=1)
+
+
+def _quat_mul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    aw, ax, ay, az = a.T
+    bw, bx, by, bz = b.T
+    return np.stack([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw], axis=1)
+
+
+def _matrix_from_quat(q: np.ndarray) -> np.ndarray:
+    w, x, y, z = q.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], axis=1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], axis=1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], axis=1)], axis=1)
+
+
 def _look_frames(forward: np.ndarray) -> np.ndarray:
     """World-to-camera rotations whose camera -z axis points along `forward` (n,3)."""
     z = -forward / np.linalg.norm(forward, axis=1, keepdims=True)
@@ -209,13 +233,18 @@ def _observe(rng_noise: Stream, R, t, f, k1, k2, X, cam_idx, pt_idx, pixel_sigma
     return obs + noise, is_out
 
 
-def _perturb(rng: Stream, cams_gt, pts_gt, rot_noise, trans_noise, point_noise):
+def _perturb(rng: Stream, cams_gt, R_gt, pts_gt, rot_noise, trans_noise, point_noise):
+    """Initial state: each camera is turned by rot_noise radians about a uniformly random
+    axis through its own centre (the centre stays put), then t gets N(0, trans_noise^2)
+    per axis; points get N(0, point_noise^2) per axis."""
     C, P = cams_gt.shape[0], pts_gt.shape[0]
     cams0 = cams_gt.copy()
-    # rotation noise of magnitude rot_noise about a uniformly random axis, added in the
-    # angle-axis chart; translation and point noise are isotropic Gaussians
-    cams0[:, 0:3] += rot_noise * rng.unit_vectors(C)
-    cams0[:, 3:6] += rng.normal(3 * C, trans_noise).reshape(C, 3)
+    centers = -np.einsum("nji,nj->ni", R_gt, cams_gt[:, 3:6])        # c = -R^T t
+    dq = _quat_from_angle_axis(rot_noise * rng.unit_vectors(C))
+    q0 = _quat_mul(dq, _quat_from_matrix(R_gt))
+    R0 = _matrix_from_quat(q0)
+    cams0[:, 0:3] = _angle_axis_from_quat(q0 / np.linalg.norm(q0, axis=1, keepdims=True))
+    cams0[:, 3:6] = -np.einsum("nij,nj->ni", R0, centers) + rng.normal(3 * C, trans_noise).reshape(C, 3)
     pts0 = pts_gt + rng.normal(3 * P, point_noise).reshape(P, 3)
     return cams0, pts0
 
@@ -247,7 +276,7 @@ def ba_ring(seed: int, n_cams: int = 10, n_pts: int = 500, views: int = 6, radiu
                            outlier_frac, 50.0)
     w = _angle_axis_from_quat(_quat_from_matrix(R))
     cams_gt = np.concatenate([w, t, f[:, None], k1[:, None], k2[:, None]], axis=1)
-    cams0, pts0 = _perturb(rng_init, cams_gt, X, rot_noise, trans_noise, point_noise)
+    cams0, pts0 = _perturb(rng_init, cams_gt, R, X, rot_noise, trans_noise, point_noise)
     return BAProblem(name, seed, cams_gt, X, cams0, pts0, cam_idx, pt_idx, obs, is_out,
                      huber_delta, dict(kind="ring", views=views, pixel_sigma=pixel_sigma))
 
@@ -344,7 +373,7 @@ def ba_path(seed: int, n_cams: int, n_pts: int, law: str = "pareto", spacing: fl
                            outlier_frac, 50.0)
     w = _angle_axis_from_quat(_quat_from_matrix(R))
     cams_gt = np.concatenate([w, t, f[:, None], k1[:, None], k2[:, None]], axis=1)
-    cams0, pts0 = _perturb(rng_init, cams_gt, X, rot_noise, trans_noise, point_noise)
+    cams0, pts0 = _perturb(rng_init, cams_gt, R, X, rot_noise, trans_noise, point_noise)
     return BAProblem(name, seed, cams_gt, X, cams0, pts0, cam_idx, pt_idx, obs, is_out,
                      huber_delta, dict(kind="path", law=law, pixel_sigma=pixel_sigma))
 
