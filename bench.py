@@ -154,7 +154,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     p = synth.ba_medium(args.seed)
     params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
     g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
-                             args.precision, device=dev, stream=stream.cuda_stream)
+                             args.precision, device=dev, stream=stream.cuda_stream,
+                             chunk_edges=args.chunk)
     g.optimize(args.warmup, params)               # also freezes the topology and plans memory
     torch.cuda.synchronize()
     g.set_profiling(True)
@@ -218,6 +219,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         data="synthetic",
         config=dict(workload=WORKLOAD, precision=args.precision, cameras=p.n_cams, points=p.n_pts,
                     edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, seed=args.seed,
+                    chunk_edges=args.chunk or "default",
                     l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
                     parallelism=f"replicas x{world}"),
         e2e=None if args.no_e2e else dict(value=world * args.steps / e2e_s, unit="LM iter/s",
@@ -265,6 +267,7 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--chunk", type=int, default=0, help="edges per chunk (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     args = ap.parse_args()

@@ -84,6 +84,10 @@ typedef struct {
   void (*free)(void* ptr, void* ctx);
   void* alloc_ctx;
   size_t memory_budget;       /* bytes; 0 = unlimited.  Exceeding it gives GPO_ERR_OOM. */
+  int32_t chunk_edges;        /* edges per CTA chunk of the per-edge kernels (32..2048;
+                                 0 = default: 1024, 512 in FP64); raised to the longest
+                                 track.  A tuning knob: results do not depend on it. */
+  int32_t reserved0;
 } gpo_graph_desc;
 
 /* Levenberg-Marquardt and PCG options (Listing 5: LevenbergMarquardtOptions and

@@ -28,11 +28,12 @@ using gpo::Scalars;
 // kernels the library launches on the graph's stream.
 enum KernelKind {
   KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
-  KK_PCG_VECTOR, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT, KK_COUNT
+  KK_CAM_APPLY, KK_PCG_UPDATE, KK_PCG_DIRECTION, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT,
+  KK_COUNT
 };
 static const char* const kKernelNames[KK_COUNT] = {
     "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
-    "pcg_vector", "backsub", "retract", "decide", "commit"};
+    "cam_apply", "pcg_update", "pcg_direction", "backsub", "retract", "decide", "commit"};
 
 struct Profiler {
   bool on = false;
@@ -219,7 +220,8 @@ static gpo_status finalize(gpo_graph* g) {
       if (g->e_active[e]) g->sorted_edge[fill[g->pt_old2new[g->e_pt[e]]]++] = e;
   }
   // chunk size
-  int ch = gpo::default_ch_max(g->prec);
+  int ch = g->desc.chunk_edges > 0 ? g->desc.chunk_edges : gpo::default_ch_max(g->prec);
+  if (ch < 32) ch = 32;
   while (ch < maxdeg) ch *= 2;
   if (ch > gpo::max_supported_ch(g->prec))
     return fail(g, GPO_ERR_UNSUPPORTED,
@@ -514,7 +516,9 @@ static gpo_status pcg_solve(gpo_graph* g, int max_it) {
     for (int i = 0; i < n; ++i) {
       g->cur_pcg_k = launched + i + 1;
       run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(g->ls, g->prec, g->stream); });
-      run(g, KK_PCG_VECTOR, [&] { return gpo::launch_pcg_vector(g->ls, g->prec, g->stream); });
+      run(g, KK_CAM_APPLY, [&] { return gpo::launch_cam_apply(g->ls, g->prec, g->stream); });
+      run(g, KK_PCG_UPDATE, [&] { return gpo::launch_pcg_update(g->ls, g->prec, g->stream); });
+      run(g, KK_PCG_DIRECTION, [&] { return gpo::launch_pcg_direction(g->ls, g->prec, g->stream); });
     }
     launched += n;
     GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], g->ls.running, sizeof(int),

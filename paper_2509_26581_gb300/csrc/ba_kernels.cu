@@ -316,17 +316,40 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // Last-CTA detection for grid-wide reductions in a fixed order.
+// Call after thread 0 has written the CTA's partial; true in the CTA that finishes last.
 __device__ bool last_cta(unsigned int* ticket, int ctas) {
   __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
     is_last = (t == (unsigned int)ctas - 1u);
   }
   __syncthreads();
   if (is_last) __threadfence();
   return is_last;
+}
+
+// Sums the n per-CTA partial pairs (stride 2) with all threads of the CTA in a fixed
+// order (strided per thread, then a fixed tree); the result is valid in thread 0.
+__device__ void sum_partials(const double* part, int n, double& a, double& b) {
+  __shared__ double ra[256], rb[256];
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    x += part[2 * i];
+    y += part[2 * i + 1];
+  }
+  ra[threadIdx.x] = x;
+  rb[threadIdx.x] = y;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) {
+      ra[threadIdx.x] += ra[threadIdx.x + s2];
+      rb[threadIdx.x] += rb[threadIdx.x + s2];
+    }
+    __syncthreads();
+  }
+  a = ra[0];
+  b = rb[0];
 }
 
 struct ChunkRange {
@@ -827,9 +850,10 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     d.cblk_part[2 * cbl] = a;
     d.cblk_part[2 * cbl + 1] = b;
   }
-  if (last_cta(&sc->ticket, d.ncblk) && threadIdx.x == 0) {
-    double rz = 0.0, rr = 0.0;
-    for (int b = 0; b < d.ncblk; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
+  if (!last_cta(&sc->ticket, d.ncblk)) return;
+  double rz, rr;
+  sum_partials(d.cblk_part, d.ncblk, rz, rr);
+  if (threadIdx.x == 0) {
     const double gn = sqrt(rr);
     sc->rz = rz;
     sc->gnorm = gn;
@@ -864,8 +888,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   if (!d.sc->active || d.sc->pcg_done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max;
-  AT* vv = reinterpret_cast<AT*>(smem);    // [9][CH]; first [3][CH] hold a_e in pass 1
-  AT* tp = vv + 9 * CH;                    // [3][CH] per point of the chunk
+  const int LD = CH + 1;                   // odd stride: the 9 components of one
+                                           // position fall in different banks
+  AT* vv = reinterpret_cast<AT*>(smem);    // [9][LD]; first [3][LD] hold a_e in pass 1
+  AT* tp = vv + 9 * LD;                    // [3][LD] per point of the chunk
   const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * kJComp;
   const AT* xv = reinterpret_cast<const AT*>(d.p);
@@ -888,7 +914,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
       q1 += row[9 + k] * xk;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) vv[k * CH + i] = row[18 + k] * q0 + row[21 + k] * q1;
+    for (int k = 0; k < 3; ++k) vv[k * LD + i] = row[18 + k] * q0 + row[21 + k] * q1;
   }
   __syncthreads();
   const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
@@ -898,14 +924,14 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     AT u[3] = {0, 0, 0};
     for (int i = a; i < b; ++i) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) u[k] += vv[k * CH + i];
+      for (int k = 0; k < 3; ++k) u[k] += vv[k * LD + i];
     }
     AT hi[6], t[3];
 #pragma unroll
     for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
     mul3(hi, u, t);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) tp[k * CH + j] = t[k];
+    for (int k = 0; k < 3; ++k) tp[k * LD + j] = t[k];
   }
   __syncthreads();
 #pragma unroll
@@ -913,21 +939,21 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
     const int pl = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
-    const AT t0 = tp[pl], t1 = tp[CH + pl], t2 = tp[2 * CH + pl];
+    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
     AT row[kJComp];
     load_row(Jg + (size_t)i * kJComp, row);
     const AT s0 = row[18] * t0 + row[19] * t1 + row[20] * t2;
     const AT s1 = row[21] * t0 + row[22] * t1 + row[23] * t2;
     const int pos = mypos[m];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) vv[k * CH + pos] = row[k] * s0 + row[9 + k] * s1;
+    for (int k = 0; k < 9; ++k) vv[k * LD + pos] = row[k] * s0 + row[9 + k] * s1;
   }
   __syncthreads();
   AT* partV = reinterpret_cast<AT*>(d.partV);
   for (int w = threadIdx.x; w < cr.nS * 9; w += kThreads) {
     const int sl = w / 9, comp = w - sl * 9;
     const int a = d.slot_e0[cr.s0 + sl] - cr.e0, b = d.slot_e0[cr.s0 + sl + 1] - cr.e0;
-    const AT* src = vv + comp * CH;
+    const AT* src = vv + comp * LD;
     AT acc = (AT)0;
     for (int q = a; q < b; ++q) acc += src[q];
     partV[(size_t)(cr.s0 + sl) * 9 + comp] = acc;
@@ -985,10 +1011,12 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
     double a = 0.0;
     for (int w = 0; w < kCamPerBlock; ++w) a += red[w];
     d.cblk_part[2 * cbl] = a;
+    d.cblk_part[2 * cbl + 1] = 0.0;
   }
-  if (last_cta(&sc->ticket, d.ncblk) && threadIdx.x == 0) {
-    double pAp = 0.0;
-    for (int b = 0; b < d.ncblk; ++b) pAp += d.cblk_part[2 * b];
+  if (!last_cta(&sc->ticket, d.ncblk)) return;
+  double pAp, unused;
+  sum_partials(d.cblk_part, d.ncblk, pAp, unused);
+  if (threadIdx.x == 0) {
     sc->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       sc->alpha = 0.0;
@@ -1055,9 +1083,10 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
     d.cblk_part[2 * cbl] = a;
     d.cblk_part[2 * cbl + 1] = b;
   }
-  if (last_cta(&sc->ticket, d.ncblk) && threadIdx.x == 0) {
-    double rz = 0.0, rr = 0.0;
-    for (int b = 0; b < d.ncblk; ++b) { rz += d.cblk_part[2 * b]; rr += d.cblk_part[2 * b + 1]; }
+  if (!last_cta(&sc->ticket, d.ncblk)) return;
+  double rz, rr;
+  sum_partials(d.cblk_part, d.ncblk, rz, rr);
+  if (threadIdx.x == 0) {
     const double n = sqrt(rr);
     const double rtrue = sc->sigma * n;
     sc->pcg_it += 1;
@@ -1322,7 +1351,7 @@ static size_t schur_smem(Prec pr, int ch) {
 }
 static size_t spmv_smem(Prec pr, int ch) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
-  return 12 * sA * (size_t)ch;
+  return 12 * sA * (size_t)(ch + 1);
 }
 static size_t backsub_smem(Prec pr, int ch) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
@@ -1419,19 +1448,23 @@ int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   else spmv_t<__nv_bfloat16>(ls, pr, st);
   return 1;
 }
-int launch_pcg_vector(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+int launch_cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_cb == 0) return 0;
-  const int nb = ls.n_cb, nt = kCamPerBlock * 32;
-  if (pr == Prec::F64) {
-    k_cam_apply<double><<<nb, nt, 0, st>>>(ls);
-    k_pcg_update<double><<<nb, nt, 0, st>>>(ls);
-    k_pcg_direction<double><<<nb, nt, 0, st>>>(ls);
-  } else {
-    k_cam_apply<float><<<nb, nt, 0, st>>>(ls);
-    k_pcg_update<float><<<nb, nt, 0, st>>>(ls);
-    k_pcg_direction<float><<<nb, nt, 0, st>>>(ls);
-  }
-  return 3;
+  if (pr == Prec::F64) k_cam_apply<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  else k_cam_apply<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  return 1;
+}
+int launch_pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_cb == 0) return 0;
+  if (pr == Prec::F64) k_pcg_update<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  else k_pcg_update<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  return 1;
+}
+int launch_pcg_direction(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  if (ls.n_cb == 0) return 0;
+  if (pr == Prec::F64) k_pcg_direction<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  else k_pcg_direction<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  return 1;
 }
 
 template <class JT>

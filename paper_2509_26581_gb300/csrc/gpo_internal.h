@@ -140,7 +140,9 @@ int launch_linearize(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st);
 int launch_schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st);      // the Schur product (hot loop)
-int launch_pcg_vector(const LaunchSet& ls, Prec pr, cudaStream_t st);    // camera apply, update, direction
+int launch_cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st);     // y = S p camera side, alpha
+int launch_pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st);    // x, r, z; stopping rules, beta
+int launch_pcg_direction(const LaunchSet& ls, Prec pr, cudaStream_t st); // p = z + beta p
 int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_retract(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_decide(const LaunchSet& ls, Prec pr, cudaStream_t st);

@@ -32,7 +32,8 @@ class gpo_graph_desc(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32),
                 ("reserve_vertices", C.c_int64), ("reserve_edges", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
-                ("alloc_ctx", C.c_void_p), ("memory_budget", C.c_size_t)]
+                ("alloc_ctx", C.c_void_p), ("memory_budget", C.c_size_t),
+                ("chunk_edges", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class gpo_lm_params(C.Structure):
@@ -132,7 +133,7 @@ class Graph:
     """Owns one gpo_graph handle."""
 
     def __init__(self, precision="fp64", device: int = 0, stream=None, memory_budget: int = 0,
-                 reserve_vertices: int = 0, reserve_edges: int = 0):
+                 reserve_vertices: int = 0, reserve_edges: int = 0, chunk_edges: int = 0):
         d = gpo_graph_desc()
         _check(lib.gpo_graph_desc_default(C.byref(d)))
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -141,6 +142,7 @@ class Graph:
         d.memory_budget = memory_budget
         d.reserve_vertices = reserve_vertices
         d.reserve_edges = reserve_edges
+        d.chunk_edges = chunk_edges
         h = C.c_void_p()
         _check(lib.gpo_graph_create(C.byref(d), C.byref(h)))
         self.h = h

@@ -233,9 +233,14 @@ def test_sampled_edges_at_medium_size(gpo):
     kappa = (np.linalg.norm(X, axis=1) + np.linalg.norm(cams[:, 3:6], axis=1)) / np.abs(Pc[:, 2])
     dr = np.abs(r[idx] - ro).max(axis=1)
     assert np.all(dr <= 32 * eps * cams[:, 6] * kappa + 1e-12 * np.abs(ro).max(axis=1))
+    # An edge under an active Huber weight sqrt(delta / |r|) also carries the residual's
+    # rounding relative to |r| in every Jacobian entry.
     dJ = np.abs(J[idx] - Jo).reshape(len(idx), -1).max(axis=1)
     Js = np.abs(Jo).reshape(len(idx), -1).max(axis=1)
-    assert np.all(dJ <= (32 * eps * kappa + 1e-12) * Js)
+    rn = np.linalg.norm(oba.residual(cams, X, p.obs[idx]), axis=1)
+    huber = rn > p.huber_delta
+    rel = 32 * eps * kappa + 1e-12 + np.where(huber, 32 * eps * cams[:, 6] * kappa / np.maximum(rn, 1.0), 0.0)
+    assert np.all(dJ <= rel * Js)
     assert np.median(dr / np.maximum(np.abs(ro).max(axis=1), 1.0)) < 1e-12
     rep = g.optimize(3)
     assert rep.final_cost < rep.initial_cost
