@@ -233,6 +233,60 @@ const char* gpo_last_error(const gpo_graph* g);
 const char* gpo_version(void);
 
 /* ---------------------------------------------------------------------------
+ * Batched solves and serving.  Many small independent problems (e.g. the local
+ * bundle-adjustment windows of a SLAM back end) share every kernel launch: each
+ * launch covers the chunks and camera blocks of all graphs in the set, and each graph
+ * keeps its own LM and PCG state, so its result is the same as when it is solved
+ * alone with gpo_optimize (bit for bit: the reductions of a graph never mix with
+ * another graph's).  The paper has no batched mode; this is the library's extension.
+ * ------------------------------------------------------------------------ */
+
+/* Solves n graphs together for max_iters LM iterations.  The graphs must share
+ * precision and device and be distinct; they are finalized if needed and keep their
+ * device state (as after gpo_optimize).  Work runs on graphs[0]'s stream; reports
+ * (optional) receives n reports in graph order.  Errors as gpo_optimize; on error
+ * the message is on graphs[0]. */
+gpo_status gpo_optimize_batch(gpo_graph* const* graphs, int32_t n, int32_t max_iters,
+                              const gpo_lm_params* params, gpo_report* reports);
+
+typedef struct gpo_server gpo_server;
+
+typedef struct {
+  int32_t precision;          /* of every graph it serves */
+  int32_t device;
+  void* cuda_stream;          /* NULL = the server creates one */
+  size_t memory_budget;       /* device bytes of resident graphs; 0 = unlimited */
+  int32_t max_resident;       /* slots: graphs solved concurrently (default 1024) */
+  int32_t reserved0;
+} gpo_server_desc;
+
+/* Serving loop (continuous batching).  Requests are queued by gpo_server_submit;
+ * each gpo_server_step admits queued graphs in arrival order while a slot is free
+ * and their planned device memory fits the budget, runs ONE LM iteration for every
+ * resident graph in shared launches, and retires graphs that have run their
+ * iterations: their final state is copied back into the graph (host side; read it
+ * with gpo_get_state) and their device memory is released.  A graph is owned by the
+ * server from submit until its ticket is reported done; the caller destroys it. */
+gpo_status gpo_server_desc_default(gpo_server_desc* out);
+gpo_status gpo_server_create(const gpo_server_desc* desc, gpo_server** out);
+gpo_status gpo_server_destroy(gpo_server* sv);
+/* Queues g (not yet optimized) for max_iters iterations; *ticket identifies it.
+ * Errors: GPO_ERR_ARG (precision or device mismatch), GPO_ERR_STATE (g already on the
+ * device), GPO_ERR_OOM (g alone exceeds the budget), GPO_ERR_UNSUPPORTED. */
+gpo_status gpo_server_submit(gpo_server* sv, gpo_graph* g, int32_t max_iters,
+                             const gpo_lm_params* params, int64_t* ticket);
+/* Admission, one LM iteration of the resident graphs, retirement.  Outputs (optional):
+ * graphs resident after the step, still queued, and retired by this step. */
+gpo_status gpo_server_step(gpo_server* sv, int32_t* n_resident, int32_t* n_queued,
+                           int32_t* n_finished);
+/* *done = 1 and the report once the ticket's graph has been retired (each ticket is
+ * reported once). */
+gpo_status gpo_server_poll(gpo_server* sv, int64_t ticket, int32_t* done, gpo_report* report);
+/* Device bytes held by resident graphs. */
+gpo_status gpo_server_memory(gpo_server* sv, size_t* used_bytes);
+const char* gpo_server_last_error(const gpo_server* sv);
+
+/* ---------------------------------------------------------------------------
  * Diagnostic entry points (used by the parity tests; same kernels as optimize).
  * ------------------------------------------------------------------------ */
 

@@ -17,89 +17,13 @@
 #include <string>
 #include <vector>
 
-#include "gpo.h"
-#include "gpo_internal.h"
-
-using gpo::DevBA;
-using gpo::Prec;
-using gpo::Scalars;
-
-// Per-kernel launch counts (always) and CUDA-event timings (when enabled) of the
-// kernels the library launches on the graph's stream.
-enum KernelKind {
-  KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
-  KK_CAM_APPLY, KK_PCG_UPDATE, KK_PCG_DIRECTION, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT,
-  KK_COUNT
-};
-static const char* const kKernelNames[KK_COUNT] = {
-    "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
-    "cam_apply", "pcg_update", "pcg_direction", "backsub", "retract", "decide", "commit"};
-
-struct Profiler {
-  bool on = false;
-  int64_t launches[KK_COUNT] = {};
-  int64_t timed[KK_COUNT] = {};
-  int64_t active[KK_COUNT] = {};
-  double ms[KK_COUNT] = {};
-  double active_ms[KK_COUNT] = {};
-  struct Mark { int kind, lm_iter, pcg_k; cudaEvent_t a, b; };
-  std::vector<Mark> marks;
-  std::vector<cudaEvent_t> pool;
-  size_t pool_used = 0;
-};
-
-struct gpo_graph {
-  gpo_graph_desc desc{};
-  Prec prec = Prec::F64;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::string err;
-
-  // vertices: global id -> (kind, index within kind)
-  std::vector<int8_t> v_kind;
-  std::vector<int64_t> v_local;
-  std::vector<double> cam_state;   // [C][9] (host copy until finalize)
-  std::vector<double> pt_state;    // [P][3]
-  std::vector<uint8_t> cam_fixed, pt_fixed;
-
-  // BA edges (global edge id = index)
-  std::vector<int32_t> e_cam, e_pt;
-  std::vector<double> e_obs;       // [E][2]
-  std::vector<double> e_sqinfo;    // [E][3] upper Cholesky factor, identity if no info
-  std::vector<double> e_delta;     // [E]
-  std::vector<uint8_t> e_active;
-  bool any_info = false;
-
-  // finalized topology
-  bool finalized = false;
-  int ch_max = 0;
-  std::vector<int64_t> sorted_edge;   // sorted position -> edge id
-  std::vector<int32_t> pt_new2old, pt_old2new;
-  std::vector<int32_t> h_ch_e0;
-  size_t j_elems = 0;
-
-  // device
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  DevBA dev{};
-  gpo::LaunchSet ls{};             // one-problem launch set over `dev`
-  DevBA* dev_desc = nullptr;       // device copy of `dev` (ls.probs)
-  Scalars* h_sc = nullptr;         // pinned
-  int* h_flag = nullptr;           // pinned [2]
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  std::vector<gpo::IterRecord> hist;
-  double last_cost = NAN;
-  bool cost_valid = false;
-  Profiler prof;
-  int cur_lm_iter = -1;
-  int cur_pcg_k = 0;
-};
+#include "graph.h"
 
 namespace {
-
 thread_local std::string g_create_err;
+}
 
-gpo_status fail(gpo_graph* g, gpo_status st, const char* fmt, ...) {
+gpo_status gpo_host::fail(gpo_graph* g, gpo_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -110,12 +34,9 @@ gpo_status fail(gpo_graph* g, gpo_status st, const char* fmt, ...) {
   return st;
 }
 
-#define GPO_CUDA(g, call)                                                                    \
-  do {                                                                                       \
-    cudaError_t e_ = (call);                                                                 \
-    if (e_ != cudaSuccess)                                                                   \
-      return fail((g), GPO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
-  } while (0)
+using gpo_host::fail;
+
+namespace {
 
 int tangent_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : 3; }
 int state_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : 3; }
@@ -146,15 +67,6 @@ struct Plan {
 size_t at_size(Prec p) { return p == Prec::F64 ? 8 : 4; }
 size_t jt_size(Prec p) { return p == Prec::F64 ? 8 : (p == Prec::F32 ? 4 : 2); }
 
-void release_device(gpo_graph* g) {
-  if (g->arena) {
-    if (g->desc.alloc && g->desc.free) g->desc.free(g->arena, g->desc.alloc_ctx);
-    else cudaFree(g->arena);
-  }
-  g->arena = nullptr;
-  g->arena_bytes = 0;
-}
-
 template <class T>
 cudaError_t up(T* dst, const std::vector<T>& src, cudaStream_t st) {
   if (src.empty()) return cudaSuccess;
@@ -176,10 +88,26 @@ __global__ void k_gather_rows(double* dst, const double* src, const int32_t* idx
 
 }  // namespace
 
+void gpo_host::release_device(gpo_graph* g) {
+  if (g->arena) {
+    if (g->desc.alloc && g->desc.free) g->desc.free(g->arena, g->desc.alloc_ctx);
+    else cudaFree(g->arena);
+  }
+  g->arena = nullptr;
+  g->arena_bytes = 0;
+  g->finalized = false;
+}
+
 // ============================================================== topology
 
-static gpo_status finalize(gpo_graph* g) {
-  if (g->finalized) return GPO_OK;
+// Sorts the edges point-major, cuts chunks and slots, plans device memory and (unless
+// plan_bytes is given, in which case only the planned size is returned) allocates
+// and uploads everything.
+gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
+  if (g->finalized) {
+    if (plan_bytes) *plan_bytes = g->arena_bytes;
+    return GPO_OK;
+  }
   const int C = (int)g->cam_fixed.size();
   const int P = (int)g->pt_fixed.size();
   const int64_t Eall = (int64_t)g->e_cam.size();
@@ -256,7 +184,7 @@ static gpo_status finalize(gpo_graph* g) {
     e_cam_s[i] = g->e_cam[e];
     e_pt_s[i] = g->pt_old2new[g->e_pt[e]];
   }
-  std::vector<uint16_t> e_pos(E), ch_sorted(E);
+  std::vector<uint16_t> e_pos(E), e_slot(E), ch_sorted(E);
   std::vector<int32_t> ch_s0{0}, slot_e0, slot_cam;
   const size_t jpos = (size_t)E * gpo::kJComp;
   {
@@ -275,6 +203,7 @@ static gpo_status finalize(gpo_graph* g) {
           slot_cam.push_back(prev);
         }
         e_pos[e0 + tmp[q].second] = (uint16_t)q;
+        e_slot[e0 + tmp[q].second] = (uint16_t)slot;
         ch_sorted[e0 + q] = (uint16_t)tmp[q].second;
       }
       ch_s0.push_back((int)slot_cam.size());
@@ -282,6 +211,11 @@ static gpo_status finalize(gpo_graph* g) {
     slot_e0.push_back(E);
   }
   const int NS = (int)slot_cam.size();
+  int ns_max = 1, np_max = 1;
+  for (int k = 0; k < NCH; ++k) {
+    ns_max = std::max(ns_max, ch_s0[k + 1] - ch_s0[k]);
+    np_max = std::max(np_max, ch_p0[k + 1] - ch_p0[k]);
+  }
   g->j_elems = jpos;
   // per camera: its slots in chunk order
   std::vector<int32_t> cam_s_off(C + 1, 0), cam_s_list(NS);
@@ -312,16 +246,17 @@ static gpo_status finalize(gpo_graph* g) {
   const size_t sA = at_size(pr), sJ = jt_size(pr);
   DevBA d{};
   d.C = C; d.P = P; d.E = E; d.NCH = NCH; d.NS = NS; d.ch_max = ch;
+  d.ns_max = ns_max; d.np_max = np_max;
   d.ncblk = std::max(1, (C + gpo::kCamPerBlock - 1) / gpo::kCamPerBlock);
   Plan pl;
   int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d;
-  uint16_t *e_pos_d, *ch_sorted_d;
+  uint16_t *e_pos_d, *e_slot_d, *ch_sorted_d;
   uint8_t *cam_fixed_d, *pt_fixed_d;
   double *obs_d, *delta_d, *info_d = nullptr;
   pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, 2 * (size_t)E); pl.add(&delta_d, E);
   if (g->any_info) pl.add(&info_d, 3 * (size_t)E);
   pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
-  pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E);
+  pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E); pl.add(&e_slot_d, E);
   pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
   pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1));
   pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
@@ -350,6 +285,10 @@ static gpo_status finalize(gpo_graph* g) {
   pl.add(&ch_prob_d, std::max(NCH, 1)); pl.add(&cb_prob_d, d.ncblk); pl.add(&pb_prob_d, npb);
   pl.add(&base_d, 1); pl.add(&running_d, 1);
   const size_t bytes = pl.total();
+  if (plan_bytes) {
+    *plan_bytes = bytes;
+    return GPO_OK;
+  }
   if (g->desc.memory_budget && bytes > g->desc.memory_budget)
     return fail(g, GPO_ERR_OOM, "graph needs %zu bytes of device memory, budget is %zu", bytes,
                 (size_t)g->desc.memory_budget);
@@ -369,7 +308,7 @@ static gpo_status finalize(gpo_graph* g) {
   pl.assign(static_cast<char*>(base));
   d.e_cam = e_cam; d.e_pt = e_pt; d.obs = obs_d; d.e_delta = delta_d; d.e_sqinfo = info_d;
   d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d;
-  d.e_pos = e_pos_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
+  d.e_pos = e_pos_d; d.e_slot = e_slot_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
   d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
   d.dbg_r = nullptr;
   cudaStream_t st = g->stream;
@@ -383,6 +322,7 @@ static gpo_status finalize(gpo_graph* g) {
   GPO_CUDA(g, up(ch_p0_d, ch_p0, st));
   GPO_CUDA(g, up(ch_s0_d, ch_s0, st));
   GPO_CUDA(g, up(e_pos_d, e_pos, st));
+  GPO_CUDA(g, up(e_slot_d, e_slot, st));
   GPO_CUDA(g, up(ch_sorted_d, ch_sorted, st));
   GPO_CUDA(g, up(slot_e0_d, slot_e0, st));
   GPO_CUDA(g, up(slot_cam_d, slot_cam, st));
@@ -415,6 +355,8 @@ static gpo_status finalize(gpo_graph* g) {
   ls.running = running_d;
   ls.nprob = 1; ls.n_ch = NCH; ls.n_cb = C > 0 ? d.ncblk : 0; ls.n_pb = P > 0 ? npb : 0;
   ls.ch_max = ch;
+  ls.ns_max = ns_max;
+  ls.np_max = np_max;
   g->ls = ls;
   g->dev_desc = desc_d;
   g->h_ch_e0 = ch_e0;
@@ -455,7 +397,7 @@ static void run(gpo_graph* g, int kind, F&& f) {
 // Resolves the recorded events (after a stream sync).  A Schur-product launch is
 // active when its PCG iteration ran (iteration index <= that LM iteration's PCG
 // count); later launches of the look-ahead group return at once.
-static void prof_resolve(gpo_graph* g) {
+void gpo_host::prof_resolve(gpo_graph* g) {
   Profiler& p = g->prof;
   for (const auto& m : p.marks) {
     float el = 0.f;
@@ -476,7 +418,7 @@ static void prof_resolve(gpo_graph* g) {
 
 // ============================================================== LM driver
 
-static void fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Scalars& s) {
+void gpo_host::fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Scalars& s) {
   std::memset(&s, 0, sizeof(s));
   s.lambda = lambda;
   s.nu = 2.0;
@@ -497,7 +439,7 @@ static void fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Sc
   s.pcg_done = 1;   // until the camera blocks start a PCG solve
 }
 
-static gpo_status upload_scalars(gpo_graph* g, const Scalars& s) {
+gpo_status gpo_host::upload_scalars(gpo_graph* g, const Scalars& s) {
   *g->h_sc = s;
   GPO_CUDA(g, cudaMemcpyAsync(g->dev.sc, g->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, g->stream));
   // the pinned staging buffer is reused: make sure the copy has been consumed
@@ -508,20 +450,20 @@ static gpo_status upload_scalars(gpo_graph* g, const Scalars& s) {
 // PCG iterations with early exit: iterations are launched in groups; after each
 // group the done flag is copied back, and the flag of the previous group decides
 // whether to launch more (one group of look-ahead keeps the GPU busy).
-static gpo_status pcg_solve(gpo_graph* g, int max_it) {
+static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) {
   const int kGroup = 8;
   int launched = 0, slot = 0, pending = -1;
   while (launched < max_it) {
     const int n = std::min(kGroup, max_it - launched);
     for (int i = 0; i < n; ++i) {
       g->cur_pcg_k = launched + i + 1;
-      run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(g->ls, g->prec, g->stream); });
-      run(g, KK_CAM_APPLY, [&] { return gpo::launch_cam_apply(g->ls, g->prec, g->stream); });
-      run(g, KK_PCG_UPDATE, [&] { return gpo::launch_pcg_update(g->ls, g->prec, g->stream); });
-      run(g, KK_PCG_DIRECTION, [&] { return gpo::launch_pcg_direction(g->ls, g->prec, g->stream); });
+      run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(ls, g->prec, g->stream); });
+      run(g, KK_CAM_APPLY, [&] { return gpo::launch_cam_apply(ls, g->prec, g->stream); });
+      run(g, KK_PCG_UPDATE, [&] { return gpo::launch_pcg_update(ls, g->prec, g->stream); });
+      run(g, KK_PCG_DIRECTION, [&] { return gpo::launch_pcg_direction(ls, g->prec, g->stream); });
     }
     launched += n;
-    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], g->ls.running, sizeof(int),
+    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], ls.running, sizeof(int),
                                 cudaMemcpyDeviceToHost, g->stream));
     GPO_CUDA(g, cudaEventRecord(g->ev[slot], g->stream));
     if (pending >= 0) {
@@ -535,14 +477,13 @@ static gpo_status pcg_solve(gpo_graph* g, int max_it) {
   return GPO_OK;
 }
 
-static gpo_status solve_system(gpo_graph* g, int max_it, bool force_lin) {
-  const gpo::LaunchSet& ls = g->ls;
+gpo_status gpo_host::solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin) {
   run(g, KK_LINEARIZE, [&] { return gpo::launch_linearize(ls, g->prec, force_lin, g->stream); });
   run(g, KK_SCHUR, [&] { return gpo::launch_schur_prepare(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, sizeof(int), g->stream));
   run(g, KK_CAM_FINALIZE, [&] { return gpo::launch_cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
-  gpo_status s = pcg_solve(g, max_it);
+  gpo_status s = pcg_solve(g, ls, max_it);
   if (s != GPO_OK) return s;
   g->cur_pcg_k = 0;
   run(g, KK_BACKSUB, [&] { return gpo::launch_backsub(ls, g->prec, g->stream); });
@@ -550,22 +491,53 @@ static gpo_status solve_system(gpo_graph* g, int max_it, bool force_lin) {
   return GPO_OK;
 }
 
-static gpo_status compute_cost(gpo_graph* g, double* out) {
-  const gpo::LaunchSet& ls = g->ls;
+gpo_status gpo_host::finish_iteration(gpo_graph* g, const gpo::LaunchSet& ls) {
+  run(g, KK_RETRACT, [&] { return gpo::launch_retract(ls, g->prec, g->stream); });
+  run(g, KK_COST, [&] { return gpo::launch_cost(ls, true, g->stream); });
+  run(g, KK_DECIDE, [&] { return gpo::launch_decide(ls, g->prec, g->stream); });
+  run(g, KK_COMMIT, [&] { return gpo::launch_commit(ls, g->stream); });
+  GPO_CUDA(g, cudaGetLastError());
+  return GPO_OK;
+}
+
+gpo_status gpo_host::launch_initial_cost(gpo_graph* g, const gpo::LaunchSet& ls) {
   run(g, KK_CAM_PREPARE, [&] { return gpo::launch_cam_prepare(ls, false, g->stream); });
   run(g, KK_COST, [&] { return gpo::launch_cost(ls, false, g->stream); });
   run(g, KK_COST_REDUCE, [&] { return gpo::launch_cost_init(ls, g->stream); });
+  GPO_CUDA(g, cudaGetLastError());
+  return GPO_OK;
+}
+
+static gpo_status compute_cost(gpo_graph* g, double* out) {
+  gpo_status s = gpo_host::launch_initial_cost(g, g->ls);
+  if (s != GPO_OK) return s;
   GPO_CUDA(g, cudaMemcpyAsync(g->h_sc, g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->stream));
   GPO_CUDA(g, cudaStreamSynchronize(g->stream));
   *out = g->h_sc->cost;
   return GPO_OK;
 }
 
-static gpo_lm_params params_or_default(const gpo_lm_params* p) {
+gpo_lm_params gpo_host::params_or_default(const gpo_lm_params* p) {
   gpo_lm_params d;
   gpo_lm_params_default(&d);
   return p ? *p : d;
 }
+
+gpo_status gpo_host::download_state(gpo_graph* g) {
+  if (!g->finalized) return GPO_OK;
+  const DevBA& d = g->dev;
+  std::vector<double> pts(3 * (size_t)d.P);
+  if (d.C) GPO_CUDA(g, cudaMemcpyAsync(g->cam_state.data(), d.cam, 9 * (size_t)d.C * sizeof(double),
+                                      cudaMemcpyDeviceToHost, g->stream));
+  if (d.P) GPO_CUDA(g, cudaMemcpyAsync(pts.data(), d.pt, 3 * (size_t)d.P * sizeof(double),
+                                      cudaMemcpyDeviceToHost, g->stream));
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  for (int p = 0; p < d.P; ++p)
+    for (int k = 0; k < 3; ++k) g->pt_state[3 * (size_t)p + k] = pts[3 * (size_t)g->pt_old2new[p] + k];
+  return GPO_OK;
+}
+
+using namespace gpo_host;
 
 // ============================================================== C ABI
 
@@ -847,15 +819,10 @@ gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* pa
   double F0;
   if ((s = compute_cost(g, &F0)) != GPO_OK) return s;
   if (!std::isfinite(F0)) return fail(g, GPO_ERR_NUMERIC, "initial cost is not finite (%g)", F0);
-  const gpo::LaunchSet& ls = g->ls;
   for (int it = 0; it < max_iters; ++it) {
     g->cur_lm_iter = it;
-    if ((s = solve_system(g, sc.max_it, false)) != GPO_OK) return s;
-    run(g, KK_RETRACT, [&] { return gpo::launch_retract(ls, g->prec, g->stream); });
-    run(g, KK_COST, [&] { return gpo::launch_cost(ls, true, g->stream); });
-    run(g, KK_DECIDE, [&] { return gpo::launch_decide(ls, g->prec, g->stream); });
-    run(g, KK_COMMIT, [&] { return gpo::launch_commit(ls, g->stream); });
-    GPO_CUDA(g, cudaGetLastError());
+    if ((s = solve_system(g, g->ls, sc.max_it, false)) != GPO_OK) return s;
+    if ((s = finish_iteration(g, g->ls)) != GPO_OK) return s;
   }
   g->cur_lm_iter = -1;
   GPO_CUDA(g, cudaMemcpyAsync(g->h_sc, g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->stream));
@@ -1046,7 +1013,7 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
   fill_scalars(g, prm, lambda, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
   gpo::launch_cam_prepare(g->ls, false, g->stream);
-  if ((s = solve_system(g, sc.max_it, true)) != GPO_OK) return s;
+  if ((s = solve_system(g, g->ls, sc.max_it, true)) != GPO_OK) return s;
   const DevBA& d = g->dev;
   const size_t sA = at_size(g->prec);
   std::vector<char> sraw, xraw, xbraw, praw;

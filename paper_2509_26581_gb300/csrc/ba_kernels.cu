@@ -39,7 +39,7 @@ __device__ __forceinline__ void load_row(const __nv_bfloat16* src, AT (&v)[kJCom
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const uint4 w = __ldg(s4 + i);
+    const uint4 w = s4[i];
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -54,7 +54,7 @@ __device__ __forceinline__ void load_row(const float* src, AT (&v)[kJComp]) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    const float4 w = __ldg(s4 + i);
+    const float4 w = s4[i];
     v[4 * i] = (AT)w.x; v[4 * i + 1] = (AT)w.y; v[4 * i + 2] = (AT)w.z; v[4 * i + 3] = (AT)w.w;
   }
 }
@@ -63,7 +63,7 @@ __device__ __forceinline__ void load_row(const double* src, AT (&v)[kJComp]) {
   const double2* s2 = reinterpret_cast<const double2*>(src);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    const double2 w = __ldg(s2 + i);
+    const double2 w = s2[i];
     v[2 * i] = (AT)w.x; v[2 * i + 1] = (AT)w.y;
   }
 }
@@ -876,86 +876,113 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
 
 // Matrix-free Schur product, one CTA per chunk (the hot loop).  With t_p =
 // H_pp^-1 sum_e Jp_e^T Jc_e x_c(e), each edge contributes v_e = Jc_e^T Jp_e t_p(e) to
-// its camera.  v_e is written to shared memory at the edge's slot-sorted position,
-// so each slot's sum is a contiguous range.  The chunk's Jacobian rows are read from
-// HBM once; the second pass over them hits L1/L2.
-constexpr int kMaxEdgesPerThread = 8;   // ch_max <= 2048 with 256 threads
-
-template <class JT>
+// its camera.  The CTA first issues every load it needs at once (its edges'
+// Jacobian rows, kept in registers when they fit; the camera vector of each slot,
+// staged once per slot instead of once per edge; point offsets, point inverses and
+// slot ranges), then runs three barrier-separated passes in shared memory: point
+// sums, per-edge camera terms scattered to slot-sorted positions, and contiguous
+// per-slot sums.  Each chunk's Jacobian bytes are read from HBM once.
+template <class JT, int EPT>
 __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
+  constexpr int RV = (int)(sizeof(JT) * kJComp / 16);          // 16-byte vectors per row
+  constexpr bool kKeep = sizeof(JT) * kJComp * EPT <= 96;       // rows stay in registers
   GPO_BIND(ch, kl)
   if (!d.sc->active || d.sc->pcg_done) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int CH = d.ch_max;
-  const int LD = CH + 1;                   // odd stride: the 9 components of one
-                                           // position fall in different banks
-  AT* vv = reinterpret_cast<AT*>(smem);    // [9][LD]; first [3][LD] hold a_e in pass 1
-  AT* tp = vv + 9 * LD;                    // [3][LD] per point of the chunk
+  const int CH = d.ch_max, LD = CH + 1;
+  AT* vv = reinterpret_cast<AT*>(smem);        // [9][LD]; [0..2] hold a_e in pass 1
+  AT* tp = vv + 9 * LD;                        // [3][LD] point solutions
+  AT* xs = tp + 3 * LD;                        // [ls.ns_max][9] slot camera vectors
+  AT* hv = xs + 9 * ls.ns_max;                 // [ls.np_max][6] point inverses
+  int* po = reinterpret_cast<int*>(hv + 6 * ls.np_max);   // [np + 1] local point offsets
+  int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
   const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * kJComp;
-  const AT* xv = reinterpret_cast<const AT*>(d.p);
-  uint16_t mypos[kMaxEdgesPerThread];
 
+  // ---- prefetch
+  uint4 raw[kKeep ? EPT : 1][kKeep ? RV : 1];
+  int pos[EPT], slot[EPT], ptl[EPT];
 #pragma unroll
-  for (int m = 0; m < kMaxEdgesPerThread; ++m) {
+  for (int m = 0; m < EPT; ++m) {
+    const int i = threadIdx.x + m * kThreads;
+    if (i < cr.nE) {
+      if constexpr (kKeep) {
+        const uint4* src = reinterpret_cast<const uint4*>(Jg + (size_t)i * kJComp);
+#pragma unroll
+        for (int v = 0; v < RV; ++v) raw[m][v] = __ldg(src + v);
+      }
+      pos[m] = __ldg(d.e_pos + cr.e0 + i);
+      slot[m] = __ldg(d.e_slot + cr.e0 + i);
+      ptl[m] = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
+    }
+  }
+  const AT* xv = reinterpret_cast<const AT*>(d.p);
+  for (int w = threadIdx.x; w < cr.nS * 9; w += kThreads) {
+    const int sl = w / 9, k = w - sl * 9;
+    xs[w] = xv[9 * (size_t)__ldg(d.slot_cam + cr.s0 + sl) + k];
+  }
+  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv) + 6 * (size_t)cr.p0;
+  for (int w = threadIdx.x; w < cr.nP * 6; w += kThreads) hv[w] = Hinv[w];
+  for (int j = threadIdx.x; j <= cr.nP; j += kThreads) po[j] = __ldg(d.pt_off + cr.p0 + j) - cr.e0;
+  for (int t = threadIdx.x; t <= cr.nS; t += kThreads) so[t] = __ldg(d.slot_e0 + cr.s0 + t) - cr.e0;
+  __syncthreads();
+
+  // ---- pass 1: a_e = Jp^T (Jc x_c)
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
-    const int c = __ldg(d.e_cam + cr.e0 + i);
-    mypos[m] = __ldg(d.e_pos + cr.e0 + i);
     AT row[kJComp];
-    load_row(Jg + (size_t)i * kJComp, row);
-    const AT* xc = xv + 9 * (size_t)c;
+    if constexpr (kKeep) load_row(reinterpret_cast<const JT*>(raw[m]), row);
+    else load_row(Jg + (size_t)i * kJComp, row);
+    const AT* xc = xs + 9 * slot[m];
     AT q0 = (AT)0, q1 = (AT)0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const AT xk = xc[k];
-      q0 += row[k] * xk;
-      q1 += row[9 + k] * xk;
+      q0 += row[k] * xc[k];
+      q1 += row[9 + k] * xc[k];
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) vv[k * LD + i] = row[18 + k] * q0 + row[21 + k] * q1;
   }
   __syncthreads();
-  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
+  // ---- pass 2: t_p = H_pp^-1 sum_e a_e
   for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
-    const int pj = cr.p0 + j;
-    const int a = d.pt_off[pj] - cr.e0, b = d.pt_off[pj + 1] - cr.e0;
     AT u[3] = {0, 0, 0};
-    for (int i = a; i < b; ++i) {
+    for (int i = po[j]; i < po[j + 1]; ++i) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) u[k] += vv[k * LD + i];
     }
-    AT hi[6], t[3];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
-    mul3(hi, u, t);
+    AT t[3];
+    mul3(hv + 6 * j, u, t);
 #pragma unroll
     for (int k = 0; k < 3; ++k) tp[k * LD + j] = t[k];
   }
   __syncthreads();
+  // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
 #pragma unroll
-  for (int m = 0; m < kMaxEdgesPerThread; ++m) {
+  for (int m = 0; m < EPT; ++m) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
-    const int pl = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
-    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
     AT row[kJComp];
-    load_row(Jg + (size_t)i * kJComp, row);
+    if constexpr (kKeep) load_row(reinterpret_cast<const JT*>(raw[m]), row);
+    else load_row(Jg + (size_t)i * kJComp, row);
+    const int pl = ptl[m];
+    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
     const AT s0 = row[18] * t0 + row[19] * t1 + row[20] * t2;
     const AT s1 = row[21] * t0 + row[22] * t1 + row[23] * t2;
-    const int pos = mypos[m];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) vv[k * LD + pos] = row[k] * s0 + row[9 + k] * s1;
+    for (int k = 0; k < 9; ++k) vv[k * LD + pos[m]] = row[k] * s0 + row[9 + k] * s1;
   }
   __syncthreads();
+  // ---- pass 4: per-slot sums over contiguous positions
   AT* partV = reinterpret_cast<AT*>(d.partV);
   for (int w = threadIdx.x; w < cr.nS * 9; w += kThreads) {
     const int sl = w / 9, comp = w - sl * 9;
-    const int a = d.slot_e0[cr.s0 + sl] - cr.e0, b = d.slot_e0[cr.s0 + sl + 1] - cr.e0;
     const AT* src = vv + comp * LD;
     AT acc = (AT)0;
-    for (int q = a; q < b; ++q) acc += src[q];
+    for (int q = so[sl]; q < so[sl + 1]; ++q) acc += src[q];
     partV[(size_t)(cr.s0 + sl) * 9 + comp] = acc;
   }
 }
@@ -1336,7 +1363,7 @@ __global__ void __launch_bounds__(256) k_commit_pts(LaunchSet ls) {
 // ---------------------------------------------------------------- launchers
 
 
-int default_ch_max(Prec pr) { return pr == Prec::F64 ? 512 : 1024; }
+int default_ch_max(Prec) { return 512; }
 
 static size_t lin_smem(Prec pr, int ch) {
   const size_t sJ = pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2);
@@ -1349,9 +1376,10 @@ static size_t schur_smem(Prec pr, int ch) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
   return (18 * sJ + 5 * sA + 2) * (size_t)ch;
 }
-static size_t spmv_smem(Prec pr, int ch) {
+static size_t spmv_smem(Prec pr, const LaunchSet& ls) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
-  return 12 * sA * (size_t)(ch + 1);
+  return sA * (12 * (size_t)(ls.ch_max + 1) + 9 * (size_t)ls.ns_max + 6 * (size_t)ls.np_max) +
+         4 * (size_t)(ls.np_max + ls.ns_max + 2);
 }
 static size_t backsub_smem(Prec pr, int ch) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
@@ -1435,11 +1463,19 @@ int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   return 1;
 }
 
+template <class JT, int EPT>
+static void spmv_e(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+  const size_t sm = spmv_smem(pr, ls);
+  set_smem(reinterpret_cast<const void*>(k_spmv<JT, EPT>), sm);
+  k_spmv<JT, EPT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+}
 template <class JT>
 static void spmv_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-  const size_t sm = spmv_smem(pr, ls.ch_max);
-  set_smem(reinterpret_cast<const void*>(k_spmv<JT>), sm);
-  k_spmv<JT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+  const int ept = (ls.ch_max + kThreads - 1) / kThreads;
+  if (ept <= 1) spmv_e<JT, 1>(ls, pr, st);
+  else if (ept <= 2) spmv_e<JT, 2>(ls, pr, st);
+  else if (ept <= 4) spmv_e<JT, 4>(ls, pr, st);
+  else spmv_e<JT, 8>(ls, pr, st);
 }
 int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_ch == 0) return 0;

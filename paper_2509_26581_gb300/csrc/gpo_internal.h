@@ -74,6 +74,7 @@ struct DevBA {
   const int* ch_p0;          // [NCH+1]
   const int* ch_s0;          // [NCH+1]
   const uint16_t* e_pos;     // [E] position of the edge in its chunk's slot-sorted order
+  const uint16_t* e_slot;    // [E] slot of the edge inside its chunk
   const uint16_t* ch_sorted; // [E] per chunk: local edge ids sorted by (slot, id)
   const int* slot_e0;        // [NS+1] range of a slot in ch_sorted (global positions)
   const int* slot_cam;       // [NS]
@@ -110,6 +111,7 @@ struct DevBA {
   IterRecord* hist;          // [kMaxHistory]
   double* dbg_r;             // optional [E][2] weighted residual output
   int ch_max;                // max edges per chunk
+  int ns_max, np_max;        // max slots / points of a chunk
   int ncblk;                 // CTAs of the camera kernels
 };
 
@@ -130,6 +132,7 @@ struct LaunchSet {
   int* running;          // problems whose PCG is still iterating
   int nprob, n_ch, n_cb, n_pb;
   int ch_max;            // largest chunk over the problems (shared-memory sizing)
+  int ns_max, np_max;    // most slots / points in one chunk over the problems
 };
 
 // Kernel launchers (ba_kernels.cu).  All are asynchronous on `st`.

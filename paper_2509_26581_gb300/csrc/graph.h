@@ -1,0 +1,115 @@
+// Host-side graph object and LM driver helpers shared by the C-ABI translation
+// units (api.cu: single graphs; batch.cu: batched solves and the serving loop).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "gpo.h"
+#include "gpo_internal.h"
+
+using gpo::DevBA;
+using gpo::Prec;
+using gpo::Scalars;
+
+// Per-kernel launch counts (always) and CUDA-event timings (when enabled) of the
+// kernels the library launches on the graph's stream.
+enum KernelKind {
+  KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
+  KK_CAM_APPLY, KK_PCG_UPDATE, KK_PCG_DIRECTION, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT,
+  KK_COUNT
+};
+inline const char* const kKernelNames[KK_COUNT] = {
+    "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
+    "cam_apply", "pcg_update", "pcg_direction", "backsub", "retract", "decide", "commit"};
+
+struct Profiler {
+  bool on = false;
+  int64_t launches[KK_COUNT] = {};
+  int64_t timed[KK_COUNT] = {};
+  int64_t active[KK_COUNT] = {};
+  double ms[KK_COUNT] = {};
+  double active_ms[KK_COUNT] = {};
+  struct Mark { int kind, lm_iter, pcg_k; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+struct gpo_graph {
+  gpo_graph_desc desc{};
+  Prec prec = Prec::F64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // vertices: global id -> (kind, index within kind)
+  std::vector<int8_t> v_kind;
+  std::vector<int64_t> v_local;
+  std::vector<double> cam_state;   // [C][9] (host copy until finalize)
+  std::vector<double> pt_state;    // [P][3]
+  std::vector<uint8_t> cam_fixed, pt_fixed;
+
+  // BA edges (global edge id = index)
+  std::vector<int32_t> e_cam, e_pt;
+  std::vector<double> e_obs;       // [E][2]
+  std::vector<double> e_sqinfo;    // [E][3] upper Cholesky factor, identity if no info
+  std::vector<double> e_delta;     // [E]
+  std::vector<uint8_t> e_active;
+  bool any_info = false;
+
+  // finalized topology
+  bool finalized = false;
+  int ch_max = 0;
+  std::vector<int64_t> sorted_edge;   // sorted position -> edge id
+  std::vector<int32_t> pt_new2old, pt_old2new;
+  std::vector<int32_t> h_ch_e0;
+  size_t j_elems = 0;
+
+  // device
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  DevBA dev{};
+  gpo::LaunchSet ls{};             // one-problem launch set over `dev`
+  DevBA* dev_desc = nullptr;       // device copy of `dev` (ls.probs)
+  Scalars* h_sc = nullptr;         // pinned
+  int* h_flag = nullptr;           // pinned [2]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<gpo::IterRecord> hist;
+  double last_cost = NAN;
+  bool cost_valid = false;
+  Profiler prof;
+  int cur_lm_iter = -1;
+  int cur_pcg_k = 0;
+};
+
+
+namespace gpo_host {
+
+gpo_status fail(gpo_graph* g, gpo_status st, const char* fmt, ...);
+gpo_status finalize(gpo_graph* g, size_t* plan_bytes = nullptr);
+void release_device(gpo_graph* g);
+void fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Scalars& s);
+gpo_status upload_scalars(gpo_graph* g, const Scalars& s);
+gpo_lm_params params_or_default(const gpo_lm_params* p);
+// One LM iteration's solve (linearise, Schur, PCG, back-substitution) over `ls`
+// on g's stream, counting launches in g's profiler.
+gpo_status solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin);
+// Retraction, candidate cost, decision and commit over `ls`.
+gpo_status finish_iteration(gpo_graph* g, const gpo::LaunchSet& ls);
+// Camera render blocks, F(x) and its per-problem reduction over `ls` (no sync).
+gpo_status launch_initial_cost(gpo_graph* g, const gpo::LaunchSet& ls);
+void prof_resolve(gpo_graph* g);
+// Copies the final device state back into the graph's host arrays (user order).
+gpo_status download_state(gpo_graph* g);
+
+}  // namespace gpo_host
+
+#define GPO_CUDA(g, call)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return gpo_host::fail((g), GPO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)

@@ -62,6 +62,11 @@ class gpo_kernel_profile(C.Structure):
                 ("active_launches", C.c_int64), ("total_ms", C.c_double), ("active_ms", C.c_double)]
 
 
+class gpo_server_desc(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("memory_budget", C.c_size_t), ("max_resident", C.c_int32), ("reserved0", C.c_int32)]
+
+
 _P = C.c_void_p
 _PD = C.POINTER(C.c_double)
 _PI64 = C.POINTER(C.c_int64)
@@ -84,6 +89,16 @@ _SIGS = {
     "gpo_get_profile": (C.c_int, [_P, C.POINTER(gpo_kernel_profile), C.c_int32, C.POINTER(C.c_int32)]),
     "gpo_last_error": (C.c_char_p, [_P]),
     "gpo_version": (C.c_char_p, []),
+    "gpo_optimize_batch": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(gpo_lm_params),
+                                     C.POINTER(gpo_report)]),
+    "gpo_server_desc_default": (C.c_int, [C.POINTER(gpo_server_desc)]),
+    "gpo_server_create": (C.c_int, [C.POINTER(gpo_server_desc), C.POINTER(_P)]),
+    "gpo_server_destroy": (C.c_int, [_P]),
+    "gpo_server_submit": (C.c_int, [_P, _P, C.c_int32, C.POINTER(gpo_lm_params), _PI64]),
+    "gpo_server_step": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "gpo_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(gpo_report)]),
+    "gpo_server_memory": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "gpo_server_last_error": (C.c_char_p, [_P]),
     "gpo_debug_linearize": (C.c_int, [_P, _P, _P]),
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
@@ -250,6 +265,70 @@ class Graph:
         _check(lib.gpo_debug_schur(self.h, lam, None if params is None else C.byref(params),
                                    _ptr(S), _ptr(g)), self.h)
         return S, g
+
+
+def optimize_batch(graphs: list, max_iters: int, params: gpo_lm_params | None = None) -> list:
+    """Solves the graphs together (one launch per phase for all of them)."""
+    n = len(graphs)
+    arr = (_P * n)(*[g.h for g in graphs])
+    reps = (gpo_report * n)()
+    st = lib.gpo_optimize_batch(arr, n, max_iters, None if params is None else C.byref(params), reps)
+    _check(st, graphs[0].h)
+    return list(reps)
+
+
+class Server:
+    """Continuous-batching serving loop over the C ABI (gpo_server_*)."""
+
+    def __init__(self, precision="bf16", device: int = 0, stream=None, memory_budget: int = 0,
+                 max_resident: int = 1024):
+        d = gpo_server_desc()
+        _check(lib.gpo_server_desc_default(C.byref(d)))
+        d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d.device = device
+        d.cuda_stream = stream
+        d.memory_budget = memory_budget
+        d.max_resident = max_resident
+        h = C.c_void_p()
+        _check(lib.gpo_server_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.graphs = {}
+
+    def _check(self, st):
+        if st != GPO_OK:
+            msg = lib.gpo_server_last_error(self.h)
+            raise GpoError(st, msg.decode() if msg else "")
+
+    def submit(self, graph: "Graph", max_iters: int, params: gpo_lm_params | None = None) -> int:
+        t = C.c_int64()
+        self._check(lib.gpo_server_submit(self.h, graph.h, max_iters,
+                                          None if params is None else C.byref(params), C.byref(t)))
+        self.graphs[t.value] = graph
+        return t.value
+
+    def step(self) -> tuple[int, int, int]:
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(lib.gpo_server_step(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def poll(self, ticket: int):
+        done = C.c_int32()
+        rep = gpo_report()
+        self._check(lib.gpo_server_poll(self.h, ticket, C.byref(done), C.byref(rep)))
+        return rep if done.value else None
+
+    def memory(self) -> int:
+        v = C.c_size_t()
+        self._check(lib.gpo_server_memory(self.h, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gpo_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 def ba_graph(cams, pts, cam_idx, pt_idx, obs, huber_delta=None, precision="fp64",

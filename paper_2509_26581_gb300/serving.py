@@ -1,0 +1,83 @@
+"""Serving driver over the C ABI's continuous-batching loop (gpo_server_*).
+
+Requests (local bundle-adjustment windows) arrive at given times; the driver submits
+every request whose arrival time has passed, advances the server by one step (admit,
+one LM iteration for every resident window, retire), and records each request's
+latency from arrival to retirement.  Every solve runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import gpo
+
+
+def window_graph(p, precision: str, fix_first: bool = True, **kw) -> tuple:
+    """Graph of a window (first keyframe fixed, as local BA fixes its oldest pose)."""
+    cam_fixed = np.zeros(p.n_cams, bool)
+    if fix_first:
+        cam_fixed[0] = True
+    return gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, precision,
+                        cam_fixed=cam_fixed, **kw)
+
+
+def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str = "bf16",
+          lm_iters: int = 10, params=None, memory_budget: int = 40 << 30,
+          max_resident: int = 1024, stream=None) -> dict:
+    """Runs the request stream; request i is a fresh graph of windows[pick[i]] that
+    arrives at arrivals[i] seconds.  Returns latencies, throughput and final costs."""
+    sv = gpo.Server(precision, stream=stream, memory_budget=memory_budget, max_resident=max_resident)
+    n = len(arrivals)
+    lat = np.full(n, np.nan)
+    cost = np.full(n, np.nan)
+    tickets = {}
+    graphs = {}
+    nxt = 0
+    done = 0
+    steps = 0
+    max_res = 0
+    t0 = time.perf_counter()
+    while done < n:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            g, _, _ = window_graph(windows[pick[nxt]], precision)
+            tickets[sv.submit(g, lm_iters, params)] = nxt
+            graphs[nxt] = g
+            nxt += 1
+        res, queued, fin = sv.step()
+        steps += 1
+        max_res = max(max_res, res)
+        if fin:
+            tnow = time.perf_counter() - t0
+            for t in list(tickets):
+                rep = sv.poll(t)
+                if rep is not None:
+                    i = tickets.pop(t)
+                    lat[i] = tnow - arrivals[i]
+                    cost[i] = rep.final_cost
+                    graphs.pop(i).close()
+                    done += 1
+        if res == 0 and queued == 0 and nxt < n:
+            wait = arrivals[nxt] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+    total = time.perf_counter() - t0
+    sv.close()
+    return dict(latency=lat, final_cost=cost, seconds=total, steps=steps, max_resident=max_res,
+                solves_per_s=n / total, p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)))
+
+
+def one_by_one(windows: list, pick: np.ndarray, precision: str = "fp64", lm_iters: int = 10,
+               params=None) -> dict:
+    """Baseline: the same requests solved one after another with gpo_optimize."""
+    n = len(pick)
+    cost = np.empty(n)
+    t0 = time.perf_counter()
+    for i in range(n):
+        g, _, _ = window_graph(windows[pick[i]], precision)
+        cost[i] = g.optimize(lm_iters, params).final_cost
+        g.close()
+    total = time.perf_counter() - t0
+    return dict(final_cost=cost, seconds=total, solves_per_s=n / total)

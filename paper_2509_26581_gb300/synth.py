@@ -394,3 +394,27 @@ def ba_large(seed: int = 2, **kw) -> BAProblem:
     """13,000 cameras, 4.5M points, geometric tracks (mean 6.5, max 200, ~29M observations),
     1% outliers, Huber delta 2."""
     return ba_path(seed, 13_000, 4_500_000, "geom", name="ba_large_c13000_p4500k", **kw)
+
+
+def ba_window(seed: int, n_kf: int, n_pts: int, **kw) -> BAProblem:
+    """A local bundle-adjustment window: n_kf keyframes along a path and n_pts landmarks
+    (tracks of 2-40 views, 1% outliers, Huber delta 2), generated as the medium problem."""
+    return ba_path(seed, n_kf, n_pts, "pareto", name=f"ba_window_k{n_kf}_p{n_pts}", **kw)
+
+
+def window_pool(seed: int, n: int, kf=(5, 40), pts=(300, 8000)) -> list:
+    """n windows with keyframes ~ U{kf} and landmarks ~ U{pts} (edges follow from the
+    track lengths: about 6 per landmark, 2k-60k per window)."""
+    rng = Stream(seed, 21)
+    k = rng.integers(n, kf[0], kf[1] + 1)
+    m = rng.integers(n, pts[0], pts[1] + 1)
+    return [ba_window(seed * 1000003 + i, int(k[i]), int(m[i])) for i in range(n)]
+
+
+def poisson_arrivals(seed: int, rate: float, duration: float) -> np.ndarray:
+    """Arrival times of a Poisson process of `rate` per second over [0, duration)."""
+    rng = Stream(seed, 22)
+    n_max = int(rate * duration * 1.5 + 100)
+    gaps = -np.log1p(-rng.uniform(n_max)) / rate
+    t = np.cumsum(gaps)
+    return t[t < duration]
