@@ -218,12 +218,15 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   }
   g->j_elems = jpos;
   // per camera: its slots in chunk order
-  std::vector<int32_t> cam_s_off(C + 1, 0), cam_s_list(NS);
+  std::vector<int32_t> cam_s_off(C + 1, 0), cam_s_list(NS), slot_pos(std::max(NS, 1));
   for (int s = 0; s < NS; ++s) cam_s_off[slot_cam[s] + 1]++;
   for (int c = 0; c < C; ++c) cam_s_off[c + 1] += cam_s_off[c];
   {
     std::vector<int32_t> fill(cam_s_off.begin(), cam_s_off.end() - 1);
-    for (int s = 0; s < NS; ++s) cam_s_list[fill[slot_cam[s]]++] = s;
+    for (int s = 0; s < NS; ++s) {
+      slot_pos[s] = fill[slot_cam[s]];
+      cam_s_list[fill[slot_cam[s]]++] = s;
+    }
   }
   // per-edge data in sorted order
   std::vector<double> obs_s(2 * (size_t)E), delta_s(E), info_s;
@@ -249,7 +252,8 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   d.ns_max = ns_max; d.np_max = np_max;
   d.ncblk = std::max(1, (C + gpo::kCamPerBlock - 1) / gpo::kCamPerBlock);
   Plan pl;
-  int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d;
+  int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d,
+      *slot_pos_d;
   uint16_t *e_pos_d, *e_slot_d, *ch_sorted_d;
   uint8_t *cam_fixed_d, *pt_fixed_d;
   double *obs_d, *delta_d, *info_d = nullptr;
@@ -258,7 +262,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
   pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E); pl.add(&e_slot_d, E);
   pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
-  pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1));
+  pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1)); pl.add(&slot_pos_d, std::max(NS, 1));
   pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
   pl.add(&d.cam, 9 * (size_t)C); pl.add(&d.cam_cand, 9 * (size_t)C);
   pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
@@ -274,6 +278,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add_raw(&d.x, 9 * (size_t)C * sA); pl.add_raw(&d.r, 9 * (size_t)C * sA);
   pl.add_raw(&d.z, 9 * (size_t)C * sA); pl.add_raw(&d.p, 9 * (size_t)C * sA);
   pl.add_raw(&d.y, 9 * (size_t)C * sA); pl.add_raw(&d.xbest, 9 * (size_t)C * sA);
+  pl.add_raw(&d.p2, 9 * (size_t)C * sA);
   pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
   pl.add(&d.cblk_part, 2 * (size_t)d.ncblk);
   pl.add(&d.sc, 1);
@@ -309,7 +314,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   d.e_cam = e_cam; d.e_pt = e_pt; d.obs = obs_d; d.e_delta = delta_d; d.e_sqinfo = info_d;
   d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d;
   d.e_pos = e_pos_d; d.e_slot = e_slot_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
-  d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
+  d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.slot_pos = slot_pos_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
   d.dbg_r = nullptr;
   cudaStream_t st = g->stream;
   GPO_CUDA(g, up(e_cam, e_cam_s, st));
@@ -328,6 +333,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   GPO_CUDA(g, up(slot_cam_d, slot_cam, st));
   GPO_CUDA(g, up(cam_s_off_d, cam_s_off, st));
   GPO_CUDA(g, up(cam_s_list_d, cam_s_list, st));
+  GPO_CUDA(g, up(slot_pos_d, slot_pos, st));
   GPO_CUDA(g, up(cam_fixed_d, g->cam_fixed, st));
   GPO_CUDA(g, up(pt_fixed_d, pt_fixed_s, st));
   GPO_CUDA(g, up(d.cam, g->cam_state, st));
@@ -460,7 +466,6 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
       run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(ls, g->prec, g->stream); });
       run(g, KK_CAM_APPLY, [&] { return gpo::launch_cam_apply(ls, g->prec, g->stream); });
       run(g, KK_PCG_UPDATE, [&] { return gpo::launch_pcg_update(ls, g->prec, g->stream); });
-      run(g, KK_PCG_DIRECTION, [&] { return gpo::launch_pcg_direction(ls, g->prec, g->stream); });
     }
     launched += n;
     GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], ls.running, sizeof(int),

@@ -377,11 +377,20 @@ __device__ __forceinline__ void bind_problem(DevBA& dst, const DevBA* src) {
   __syncthreads();
 }
 
+// Programmatic dependent launch: every kernel lets the next one in the stream start
+// its prologue early (launch_dependents) and waits for its predecessor to complete
+// before touching anything the predecessor writes (wait).  The problem descriptor and
+// the schedule tables are written by the host before the launches.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 #define GPO_BIND(KIND, LOCAL)                              \
   __shared__ DevBA d;                                      \
+  pdl_trigger();                                           \
   const int prob_ = ls.KIND##_prob[blockIdx.x];            \
   const int LOCAL = blockIdx.x - ls.KIND##_base[prob_];    \
-  bind_problem(d, ls.probs + prob_);
+  bind_problem(d, ls.probs + prob_);                       \
+  pdl_wait();
 
 // ---------------------------------------------------------------- camera render blocks
 
@@ -428,7 +437,9 @@ __global__ void __launch_bounds__(kThreads) k_cost(LaunchSet ls, int candidate) 
 __global__ void k_cost_init(LaunchSet ls) {
   __shared__ double red[kThreads];
   __shared__ DevBA d;
+  pdl_trigger();
   bind_problem(d, ls.probs + blockIdx.x);
+  pdl_wait();
   if (!d.sc->active) return;
   double acc = 0.0;
   for (int k = threadIdx.x; k < d.NCH; k += kThreads) acc += d.cost_part[k];
@@ -573,7 +584,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
         }
       }
     }
-    AT* out = partA + (size_t)(cr.s0 + sl) * kPartA + 9 * grp;
+    AT* out = partA + (size_t)d.slot_pos[cr.s0 + sl] * kPartA + 9 * grp;
 #pragma unroll
     for (int o = 0; o < 9; ++o) out[o] = acc[o];
   }
@@ -703,7 +714,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
           acc[o] += ldj(Jcs + o * CH + i) * q0 + ldj(Jcs + (9 + o) * CH + i) * q1;
       }
     }
-    AT* out = partB + (size_t)(cr.s0 + sl) * kPartA + 9 * grp;
+    AT* out = partB + (size_t)d.slot_pos[cr.s0 + sl] * kPartA + 9 * grp;
 #pragma unroll
     for (int o = 0; o < 9; ++o) out[o] = acc[o];
   }
@@ -782,7 +793,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[k] = (AT)0;
       for (int s = sa + lane; s < sb; s += 32) {
-        const AT* src = base + (size_t)d.cam_s_list[s] * kPartA;
+        const AT* src = base + (size_t)s * kPartA;   // camera-major rows
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc[k] += src[k];
       }
@@ -828,7 +839,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
       AT zi = (AT)0;
       for (int j = 0; j < 9; ++j) zi += M[sym9(lane, j)] * g[j];
       reinterpret_cast<AT*>(d.z)[9 * (size_t)c + lane] = zi;
-      reinterpret_cast<AT*>(d.p)[9 * (size_t)c + lane] = zi;
+      reinterpret_cast<AT*>(d.p)[9 * (size_t)c + lane] = (AT)0;   // p_{-1}: p_0 = z_0
       const AT gi = g[lane];
       rz_c = (double)gi * (double)zi;
       rr_c = (double)gi * (double)gi;
@@ -862,6 +873,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     sc->sigma = 1.0;
     sc->inv_n = 1.0;
     sc->beta = 0.0;
+    sc->pidx = 0;
     sc->pcg_it = 0;
     sc->use_best = 0;
     sc->save_best = 0;
@@ -886,7 +898,7 @@ template <class JT, int EPT>
 __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   constexpr int RV = (int)(sizeof(JT) * kJComp / 16);          // 16-byte vectors per row
-  constexpr bool kKeep = sizeof(JT) * kJComp * EPT <= 96;       // rows stay in registers
+  constexpr bool kKeep = false;                                 // re-read rows (L1/L2) in pass 3
   GPO_BIND(ch, kl)
   if (!d.sc->active || d.sc->pcg_done) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -897,6 +909,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   AT* hv = xs + 9 * ls.ns_max;                 // [ls.np_max][6] point inverses
   int* po = reinterpret_cast<int*>(hv + 6 * ls.np_max);   // [np + 1] local point offsets
   int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
+  int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
   const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * kJComp;
 
@@ -917,11 +930,16 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
       ptl[m] = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
     }
   }
-  const AT* xv = reinterpret_cast<const AT*>(d.p);
+  // the search direction p_k = (z_k + beta_k p_{k-1}) / n_k, formed per slot camera
+  const AT* zv = reinterpret_cast<const AT*>(d.z);
+  const AT* pold = reinterpret_cast<const AT*>(d.sc->pidx ? d.p2 : d.p);
+  const AT beta = (AT)d.sc->beta, inv_n = (AT)d.sc->inv_n;
   for (int w = threadIdx.x; w < cr.nS * 9; w += kThreads) {
     const int sl = w / 9, k = w - sl * 9;
-    xs[w] = xv[9 * (size_t)__ldg(d.slot_cam + cr.s0 + sl) + k];
+    const size_t o = 9 * (size_t)__ldg(d.slot_cam + cr.s0 + sl) + k;
+    xs[w] = (zv[o] + beta * pold[o]) * inv_n;
   }
+  for (int t = threadIdx.x; t < cr.nS; t += kThreads) sp[t] = __ldg(d.slot_pos + cr.s0 + t);
   const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv) + 6 * (size_t)cr.p0;
   for (int w = threadIdx.x; w < cr.nP * 6; w += kThreads) hv[w] = Hinv[w];
   for (int j = threadIdx.x; j <= cr.nP; j += kThreads) po[j] = __ldg(d.pt_off + cr.p0 + j) - cr.e0;
@@ -983,7 +1001,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     const AT* src = vv + comp * LD;
     AT acc = (AT)0;
     for (int q = so[sl]; q < so[sl + 1]; ++q) acc += src[q];
-    partV[(size_t)(cr.s0 + sl) * 9 + comp] = acc;
+    partV[(size_t)sp[sl] * 9 + comp] = acc;
   }
 }
 
@@ -1005,7 +1023,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = (AT)0;
     for (int s = sa + lane; s < sb; s += 32) {
-      const AT* src = partV + (size_t)d.cam_s_list[s] * 9;
+      const AT* src = partV + (size_t)s * 9;   // camera-major rows
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[k] += src[k];
     }
@@ -1020,14 +1038,28 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
       const AT v = __shfl_sync(0xffffffffu, acc[k], 0);
       if (lane == k) sv = v;
     }
+    // p_k = (z_k + beta_k p_{k-1}) / n_k for this camera (the same values the Schur
+    // product gathered), written to the other direction buffer
+    const AT* pold = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p) + 9 * (size_t)c;
+    AT* pnew = reinterpret_cast<AT*>(sc->pidx ? d.p : d.p2) + 9 * (size_t)c;
+    const AT* zc = reinterpret_cast<const AT*>(d.z) + 9 * (size_t)c;
+    const AT pi = lane < 9 ? (zc[lane] + (AT)sc->beta * pold[lane]) * (AT)sc->inv_n : (AT)0;
     if (lane < 9) {
-      const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * kCamTri;
-      const AT* pc = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
-      AT yi = (AT)0;
-      for (int j = 0; j < 9; ++j) yi += H[sym9(lane, j)] * pc[j];
+      pnew[lane] = pi;
+      if (sc->save_best)
+        reinterpret_cast<AT*>(d.xbest)[9 * (size_t)c + lane] = reinterpret_cast<const AT*>(d.x)[9 * (size_t)c + lane];
+    }
+    const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * kCamTri;
+    AT yi = (AT)0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const AT pj = __shfl_sync(0xffffffffu, pi, j);
+      if (lane < 9) yi += H[sym9(lane, j)] * pj;
+    }
+    if (lane < 9) {
       yi -= sv;
       reinterpret_cast<AT*>(d.y)[9 * (size_t)c + lane] = yi;
-      dot = (double)pc[lane] * (double)yi;
+      dot = (double)pi * (double)yi;
     }
   }
 #pragma unroll
@@ -1069,17 +1101,17 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
   const int c = cbl * kCamPerBlock + warp;
   double rz_c = 0.0, rr_c = 0.0;
   if (c < d.C) {   // warp-uniform
-    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha);
+    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
     AT* x = reinterpret_cast<AT*>(d.x) + 9 * (size_t)c;
     AT* r = reinterpret_cast<AT*>(d.r) + 9 * (size_t)c;
     AT* z = reinterpret_cast<AT*>(d.z) + 9 * (size_t)c;
-    const AT* pv = reinterpret_cast<const AT*>(d.p) + 9 * (size_t)c;
+    const AT* pv = reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2) + 9 * (size_t)c;
     const AT* yv = reinterpret_cast<const AT*>(d.y) + 9 * (size_t)c;
     const AT* M = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * kCamTri;
     AT ri = (AT)0;
     if (lane < 9) {
       x[lane] += sa * pv[lane];
-      ri = r[lane] - alpha * yv[lane];
+      ri = r[lane] * sn - alpha * yv[lane];
       r[lane] = ri;
     }
     AT zi = (AT)0;
@@ -1143,32 +1175,11 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
       sc->inv_n = 1.0;
       sc->rz = rz;
     }
+    sc->pidx ^= 1;
     sc->pcg_done = done;
     if (done) atomicSub(ls.running, 1);
     sc->ticket = 0u;
   }
-}
-
-// One warp per camera: keep the best iterate, then p = (z + beta p) / n and r, z
-// scaled by 1/n (n = 1 without normalisation).
-template <class AT>
-__global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_direction(LaunchSet ls) {
-  GPO_BIND(cb, cbl)
-  const Scalars* sc = d.sc;
-  if (!sc->active) return;
-  const int lane = threadIdx.x & 31;
-  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
-  if (c >= d.C || lane >= 9) return;
-  const size_t o = 9 * (size_t)c + lane;
-  if (sc->save_best) reinterpret_cast<AT*>(d.xbest)[o] = reinterpret_cast<const AT*>(d.x)[o];
-  if (sc->pcg_done) return;
-  const AT beta = (AT)sc->beta, sn = (AT)sc->inv_n;
-  AT* p = reinterpret_cast<AT*>(d.p);
-  AT* r = reinterpret_cast<AT*>(d.r);
-  AT* z = reinterpret_cast<AT*>(d.z);
-  p[o] = (z[o] + beta * p[o]) * sn;
-  r[o] *= sn;
-  z[o] *= sn;
 }
 
 // ---------------------------------------------------------------- back-substitution
@@ -1292,7 +1303,9 @@ template <class AT>
 __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
   __shared__ double red[kThreads];
   __shared__ DevBA d;
+  pdl_trigger();
   bind_problem(d, ls.probs + blockIdx.x);
+  pdl_wait();
   Scalars* sc = d.sc;
   if (!sc->active) return;
   double fc = 0.0, md = 0.0;
@@ -1379,7 +1392,7 @@ static size_t schur_smem(Prec pr, int ch) {
 static size_t spmv_smem(Prec pr, const LaunchSet& ls) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
   return sA * (12 * (size_t)(ls.ch_max + 1) + 9 * (size_t)ls.ns_max + 6 * (size_t)ls.np_max) +
-         4 * (size_t)(ls.np_max + ls.ns_max + 2);
+         4 * (size_t)(ls.np_max + 2 * ls.ns_max + 2);
 }
 static size_t backsub_smem(Prec pr, int ch) {
   const size_t sA = pr == Prec::F64 ? 8 : 4;
@@ -1393,6 +1406,25 @@ int max_supported_ch(Prec pr) {
   int ch = 64;
   while (lin_smem(pr, ch * 2) <= limit && schur_smem(pr, ch * 2) <= limit) ch *= 2;
   return ch;
+}
+
+// Launches with programmatic stream serialization, so the kernel may begin while
+// its predecessor in the stream finishes (the kernels order themselves with
+// griddepcontrol).
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per (kernel, size).
@@ -1413,18 +1445,18 @@ static void set_smem(const void* kernel, size_t bytes) {
 
 int launch_cam_prepare(const LaunchSet& ls, bool candidate, cudaStream_t st) {
   if (ls.n_cb == 0) return 0;
-  k_cam_prepare<<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls, candidate ? 1 : 0);
+  launch_pdl(k_cam_prepare, ls.n_cb, kCamPerBlock * 32, 0, st, ls, candidate ? 1 : 0);
   return 1;
 }
 
 int launch_cost(const LaunchSet& ls, bool candidate, cudaStream_t st) {
   if (ls.n_ch == 0) return 0;
-  k_cost<<<ls.n_ch, kThreads, 0, st>>>(ls, candidate ? 1 : 0);
+  launch_pdl(k_cost, ls.n_ch, kThreads, 0, st, ls, candidate ? 1 : 0);
   return 1;
 }
 
 int launch_cost_init(const LaunchSet& ls, cudaStream_t st) {
-  k_cost_init<<<ls.nprob, kThreads, 0, st>>>(ls);
+  launch_pdl(k_cost_init, ls.nprob, kThreads, 0, st, ls);
   return 1;
 }
 
@@ -1432,7 +1464,7 @@ template <class JT>
 static void lin_t(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st) {
   const size_t sm = lin_smem(pr, ls.ch_max);
   set_smem(reinterpret_cast<const void*>(k_linearize<JT>), sm);
-  k_linearize<JT><<<ls.n_ch, kThreads, sm, st>>>(ls, force ? 1 : 0);
+  launch_pdl(k_linearize<JT>, ls.n_ch, kThreads, sm, st, ls, force ? 1 : 0);
 }
 int launch_linearize(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st) {
   if (ls.n_ch == 0) return 0;
@@ -1446,7 +1478,7 @@ template <class JT>
 static void schur_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   const size_t sm = schur_smem(pr, ls.ch_max);
   set_smem(reinterpret_cast<const void*>(k_schur_prepare<JT>), sm);
-  k_schur_prepare<JT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+  launch_pdl(k_schur_prepare<JT>, ls.n_ch, kThreads, sm, st, ls);
 }
 int launch_schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_ch == 0) return 0;
@@ -1458,8 +1490,8 @@ int launch_schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st) {
 
 int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_cb == 0) return 0;
-  if (pr == Prec::F64) k_cam_finalize<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
-  else k_cam_finalize<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  if (pr == Prec::F64) launch_pdl(k_cam_finalize<double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+  else launch_pdl(k_cam_finalize<float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
   return 1;
 }
 
@@ -1467,7 +1499,7 @@ template <class JT, int EPT>
 static void spmv_e(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   const size_t sm = spmv_smem(pr, ls);
   set_smem(reinterpret_cast<const void*>(k_spmv<JT, EPT>), sm);
-  k_spmv<JT, EPT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+  launch_pdl(k_spmv<JT, EPT>, ls.n_ch, kThreads, sm, st, ls);
 }
 template <class JT>
 static void spmv_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
@@ -1486,20 +1518,14 @@ int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
 }
 int launch_cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_cb == 0) return 0;
-  if (pr == Prec::F64) k_cam_apply<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
-  else k_cam_apply<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  if (pr == Prec::F64) launch_pdl(k_cam_apply<double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+  else launch_pdl(k_cam_apply<float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
   return 1;
 }
 int launch_pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_cb == 0) return 0;
-  if (pr == Prec::F64) k_pcg_update<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
-  else k_pcg_update<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
-  return 1;
-}
-int launch_pcg_direction(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-  if (ls.n_cb == 0) return 0;
-  if (pr == Prec::F64) k_pcg_direction<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
-  else k_pcg_direction<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls);
+  if (pr == Prec::F64) launch_pdl(k_pcg_update<double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+  else launch_pdl(k_pcg_update<float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
   return 1;
 }
 
@@ -1507,7 +1533,7 @@ template <class JT>
 static void backsub_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   const size_t sm = backsub_smem(pr, ls.ch_max);
   set_smem(reinterpret_cast<const void*>(k_backsub<JT>), sm);
-  k_backsub<JT><<<ls.n_ch, kThreads, sm, st>>>(ls);
+  launch_pdl(k_backsub<JT>, ls.n_ch, kThreads, sm, st, ls);
 }
 int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_ch == 0) return 0;
@@ -1520,25 +1546,25 @@ int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st) {
 int launch_retract(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   int n = 0;
   if (pr == Prec::F64) {
-    if (ls.n_cb) { k_retract_cams<double><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls); ++n; }
-    if (ls.n_pb) { k_retract_pts<double><<<ls.n_pb, 256, 0, st>>>(ls); ++n; }
+    if (ls.n_cb) { launch_pdl(k_retract_cams<double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls); ++n; }
+    if (ls.n_pb) { launch_pdl(k_retract_pts<double>, ls.n_pb, 256, 0, st, ls); ++n; }
   } else {
-    if (ls.n_cb) { k_retract_cams<float><<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls); ++n; }
-    if (ls.n_pb) { k_retract_pts<float><<<ls.n_pb, 256, 0, st>>>(ls); ++n; }
+    if (ls.n_cb) { launch_pdl(k_retract_cams<float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls); ++n; }
+    if (ls.n_pb) { launch_pdl(k_retract_pts<float>, ls.n_pb, 256, 0, st, ls); ++n; }
   }
   return n;
 }
 
 int launch_decide(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-  if (pr == Prec::F64) k_decide<double><<<ls.nprob, kThreads, 0, st>>>(ls);
-  else k_decide<float><<<ls.nprob, kThreads, 0, st>>>(ls);
+  if (pr == Prec::F64) launch_pdl(k_decide<double>, ls.nprob, kThreads, 0, st, ls);
+  else launch_pdl(k_decide<float>, ls.nprob, kThreads, 0, st, ls);
   return 1;
 }
 
 int launch_commit(const LaunchSet& ls, cudaStream_t st) {
   int n = 0;
-  if (ls.n_cb) { k_commit_cams<<<ls.n_cb, kCamPerBlock * 32, 0, st>>>(ls); ++n; }
-  if (ls.n_pb) { k_commit_pts<<<ls.n_pb, 256, 0, st>>>(ls); ++n; }
+  if (ls.n_cb) { launch_pdl(k_commit_cams, ls.n_cb, kCamPerBlock * 32, 0, st, ls); ++n; }
+  if (ls.n_pb) { launch_pdl(k_commit_pts, ls.n_pb, 256, 0, st, ls); ++n; }
   return n;
 }
 

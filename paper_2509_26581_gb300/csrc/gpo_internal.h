@@ -47,6 +47,7 @@ struct Scalars {
   double pcg_tol;        // PCG tolerance (relative to |g| if pcg_rel)
   int pcg_rel;
   int pcg_it, pcg_done, use_best, save_best, normalize, max_it;
+  int pidx;              // which direction buffer holds p_{k-1} (0: p, 1: p2)
   unsigned int ticket;   // last-CTA counter of the reductions
   int active;            // the problem takes part in the current launches
   int lm_max;            // LM iterations to run (the problem deactivates after them)
@@ -78,6 +79,7 @@ struct DevBA {
   const uint16_t* ch_sorted; // [E] per chunk: local edge ids sorted by (slot, id)
   const int* slot_e0;        // [NS+1] range of a slot in ch_sorted (global positions)
   const int* slot_cam;       // [NS]
+  const int* slot_pos;       // [NS] row of the slot's partial in camera-major order
   const int* cam_s_off;      // [C+1]
   const int* cam_s_list;     // [NS] slots of each camera, chunk order
   const uint8_t* cam_fixed;  // [C]
@@ -103,7 +105,7 @@ struct DevBA {
   void* S;                   // AT [C][45] Schur diagonal blocks
   void* Minv;                // AT [C][45] block-Jacobi preconditioner S_cc^-1
   void* g;                   // AT [C][9] reduced right-hand side
-  void* x; void* r; void* z; void* p; void* y; void* xbest;   // AT [C][9]
+  void* x; void* r; void* z; void* p; void* p2; void* y; void* xbest;   // AT [C][9]
   double* cost_part;         // [NCH]
   double* md_part;           // [NCH]
   double* cblk_part;         // [ncblk][2]
@@ -145,7 +147,6 @@ int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st);      // the Schur product (hot loop)
 int launch_cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st);     // y = S p camera side, alpha
 int launch_pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st);    // x, r, z; stopping rules, beta
-int launch_pcg_direction(const LaunchSet& ls, Prec pr, cudaStream_t st); // p = z + beta p
 int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_retract(const LaunchSet& ls, Prec pr, cudaStream_t st);
 int launch_decide(const LaunchSet& ls, Prec pr, cudaStream_t st);

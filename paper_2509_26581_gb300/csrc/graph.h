@@ -18,12 +18,12 @@ using gpo::Scalars;
 // kernels the library launches on the graph's stream.
 enum KernelKind {
   KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
-  KK_CAM_APPLY, KK_PCG_UPDATE, KK_PCG_DIRECTION, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT,
+  KK_CAM_APPLY, KK_PCG_UPDATE, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT,
   KK_COUNT
 };
 inline const char* const kKernelNames[KK_COUNT] = {
     "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
-    "cam_apply", "pcg_update", "pcg_direction", "backsub", "retract", "decide", "commit"};
+    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit"};
 
 struct Profiler {
   bool on = false;

@@ -242,5 +242,5 @@ def test_sampled_edges_at_medium_size(gpo):
     rel = 32 * eps * kappa + 1e-12 + np.where(huber, 32 * eps * cams[:, 6] * kappa / np.maximum(rn, 1.0), 0.0)
     assert np.all(dJ <= rel * Js)
     assert np.median(dr / np.maximum(np.abs(ro).max(axis=1), 1.0)) < 1e-12
-    rep = g.optimize(3)
-    assert rep.final_cost < rep.initial_cost
+    rep = g.optimize(10)
+    assert rep.final_cost < rep.initial_cost and rep.accepted >= 1
