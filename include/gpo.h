@@ -287,6 +287,31 @@ gpo_status gpo_server_memory(gpo_server* sv, size_t* used_bytes);
 const char* gpo_server_last_error(const gpo_server* sv);
 
 /* ---------------------------------------------------------------------------
+ * Cost evaluation without device allocation.  The paper has no counterpart; this is
+ * for callers that cannot allocate device memory where they need a cost (a fully
+ * handed-out memory pool, a real-time or callback thread that must not enter the
+ * CUDA allocator, device memory owned by another framework).
+ *
+ * F = 1/2 sum_e rho(|r_e|^2) of a BA problem with identity information, every buffer
+ * caller-owned device memory of `device`: cams [C][9] and points [P][3] (FP64 states in
+ * the layouts of GPO_V_BA_CAMERA9 / GPO_V_POINT3), cam_idx / pt_idx [n_edges] int32,
+ * obs [n_edges][2] pixels; huber_delta > 0 selects the Huber loss, <= 0 plain squares.
+ * *cost_out (a device double) receives F when the work queued on cuda_stream (NULL =
+ * the legacy default stream) completes; the call does not wait for it.
+ * No device memory is allocated: the reduction's scratch is a static device array of
+ * 64 KB held by every GPU that loads the library until the process exits, which
+ * bounds n_edges to 2,097,152 (larger gives GPO_ERR_ARG).  The first call on a device
+ * looks up that array's address (make it before any stream capture).  All calls on a
+ * device share the array and its last contents; the call clears the part that must
+ * start at zero, but calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.
+ * Errors: GPO_ERR_ARG (null buffer, bad device, n_edges out of range), GPO_ERR_CUDA. */
+gpo_status gpo_ba_cost_noalloc(int32_t device, void* cuda_stream, const double* cams,
+                               const double* points, const int32_t* cam_idx,
+                               const int32_t* pt_idx, const double* obs, int64_t n_edges,
+                               double huber_delta, double* cost_out);
+
+/* ---------------------------------------------------------------------------
  * Diagnostic entry points (used by the parity tests; same kernels as optimize).
  * ------------------------------------------------------------------------ */
 

@@ -99,6 +99,7 @@ _SIGS = {
     "gpo_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(gpo_report)]),
     "gpo_server_memory": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
     "gpo_server_last_error": (C.c_char_p, [_P]),
+    "gpo_ba_cost_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_double, _P]),
     "gpo_debug_linearize": (C.c_int, [_P, _P, _P]),
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
