@@ -133,6 +133,19 @@ def load_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+# DRAM traffic (read + write bytes) of one k_spmv launch from an ncu capture of the
+# medium workload (profiles/k_spmv_ba_medium_bf16.md), valid only for the kernel source it
+# was taken from: a different ba_kernels.cu reports null.
+MEASURED_TRAFFIC = {("bf16", "56ce627e8d8b"): 191.2e6}
+
+
+def spmv_traffic(precision: str):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2509_26581_gb300", "csrc", "ba_kernels.cu"), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()[:12]
+    return MEASURED_TRAFFIC.get((precision, sha))
+
+
 def spmv_algorithmic_bytes(E: int, P: int, precision: str) -> float:
     """Compulsory HBM bytes of one Schur-product launch: every stored Jacobian value
     (24 per edge) and camera index once, and each point's damped inverse block."""
@@ -226,7 +239,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                                           h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes),
         gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      traffic=None, kernel="k_spmv (PCG Schur product)", peak_source=peak_kind,
+                      traffic=spmv_traffic(args.precision) if args.seed == 1 and args.chunk in (0, 512) else None,
+                      kernel="k_spmv (PCG Schur product)", peak_source=peak_kind,
                       algorithmic_bytes=alg, avg_ms=spmv_ms),
         clocks=clk,
         pcg_iters_per_step=pcg_iters,

@@ -280,7 +280,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add_raw(&d.y, 9 * (size_t)C * sA); pl.add_raw(&d.xbest, 9 * (size_t)C * sA);
   pl.add_raw(&d.p2, 9 * (size_t)C * sA);
   pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
-  pl.add(&d.cblk_part, 2 * (size_t)d.ncblk);
+  pl.add(&d.cblk_part, 2 * 4 * (size_t)d.ncblk);   // cam_apply runs four CTAs per camera block
   pl.add(&d.sc, 1);
   pl.add(&d.hist, gpo::kMaxHistory);
   const int npb = std::max(1, (P + 255) / 256);

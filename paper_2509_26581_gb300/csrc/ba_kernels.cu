@@ -1005,24 +1005,38 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   }
 }
 
-// One warp per camera: y_c = (H_cc + lambda D_c) p_c - sum_slots v; the last CTA
-// reduces p^T y and sets alpha = r^T z / p^T y.
+// y_c = (H_cc + lambda D_c) p_c - sum_slots v, four warps per camera (each sums a
+// quarter of the camera's slot partials; the quarters are added in a fixed order).
+// The CTAs of camera block b are 4b .. 4b + 3, two cameras each.  The last CTA of
+// the problem reduces p^T y and sets alpha = r^T z / p^T y.
+constexpr int kApplySplit = 4;
 template <class AT>
 __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   __shared__ double red[kCamPerBlock];
-  GPO_BIND(cb, cbl)
+  __shared__ AT quarter[kCamPerBlock][9];
+  __shared__ DevBA d;
+  pdl_trigger();
+  const int cb = blockIdx.x / kApplySplit, part = blockIdx.x % kApplySplit;
+  const int prob_ = ls.cb_prob[cb];
+  const int cbl = cb - ls.cb_base[prob_];
+  bind_problem(d, ls.probs + prob_);
+  pdl_wait();
   Scalars* sc = d.sc;
   if (!sc->active || sc->pcg_done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = cbl * kCamPerBlock + warp;
+  const int cams_per_cta = kCamPerBlock / kApplySplit;             // 2
+  const int c = cbl * kCamPerBlock + part * cams_per_cta + warp / kApplySplit;
+  const int q = warp % kApplySplit;                                // quarter of the slots
   double dot = 0.0;
+  AT pi = (AT)0;
   if (c < d.C) {   // warp-uniform
     const AT* partV = reinterpret_cast<const AT*>(d.partV);
     const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
     AT acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = (AT)0;
-    for (int s = sa + lane; s < sb; s += 32) {
+#pragma unroll 4
+    for (int s = sa + q * 32 + lane; s < sb; s += 32 * kApplySplit) {
       const AT* src = partV + (size_t)s * 9;   // camera-major rows
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[k] += src[k];
@@ -1032,18 +1046,24 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
     }
-    AT sv = (AT)0;
+    if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const AT v = __shfl_sync(0xffffffffu, acc[k], 0);
-      if (lane == k) sv = v;
+      for (int k = 0; k < 9; ++k) quarter[warp][k] = acc[k];
+    }
+  }
+  __syncthreads();
+  if (c < d.C && q == 0) {
+    AT sv = (AT)0;
+    if (lane < 9) {
+      sv = quarter[warp][lane];
+      for (int j = 1; j < kApplySplit; ++j) sv += quarter[warp + j][lane];
     }
     // p_k = (z_k + beta_k p_{k-1}) / n_k for this camera (the same values the Schur
     // product gathered), written to the other direction buffer
     const AT* pold = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p) + 9 * (size_t)c;
     AT* pnew = reinterpret_cast<AT*>(sc->pidx ? d.p : d.p2) + 9 * (size_t)c;
     const AT* zc = reinterpret_cast<const AT*>(d.z) + 9 * (size_t)c;
-    const AT pi = lane < 9 ? (zc[lane] + (AT)sc->beta * pold[lane]) * (AT)sc->inv_n : (AT)0;
+    pi = lane < 9 ? (zc[lane] + (AT)sc->beta * pold[lane]) * (AT)sc->inv_n : (AT)0;
     if (lane < 9) {
       pnew[lane] = pi;
       if (sc->save_best)
@@ -1066,15 +1086,16 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
   if (lane == 0) red[warp] = dot;
   __syncthreads();
+  const int ctas = d.ncblk * kApplySplit, me = cbl * kApplySplit + part;
   if (threadIdx.x == 0) {
     double a = 0.0;
     for (int w = 0; w < kCamPerBlock; ++w) a += red[w];
-    d.cblk_part[2 * cbl] = a;
-    d.cblk_part[2 * cbl + 1] = 0.0;
+    d.cblk_part[2 * me] = a;
+    d.cblk_part[2 * me + 1] = 0.0;
   }
-  if (!last_cta(&sc->ticket, d.ncblk)) return;
+  if (!last_cta(&sc->ticket, ctas)) return;
   double pAp, unused;
-  sum_partials(d.cblk_part, d.ncblk, pAp, unused);
+  sum_partials(d.cblk_part, ctas, pAp, unused);
   if (threadIdx.x == 0) {
     sc->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
@@ -1518,8 +1539,8 @@ int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
 }
 int launch_cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st) {
   if (ls.n_cb == 0) return 0;
-  if (pr == Prec::F64) launch_pdl(k_cam_apply<double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
-  else launch_pdl(k_cam_apply<float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+  if (pr == Prec::F64) launch_pdl(k_cam_apply<double>, ls.n_cb * kApplySplit, kCamPerBlock * 32, 0, st, ls);
+  else launch_pdl(k_cam_apply<float>, ls.n_cb * kApplySplit, kCamPerBlock * 32, 0, st, ls);
   return 1;
 }
 int launch_pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {

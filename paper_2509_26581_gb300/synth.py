@@ -418,3 +418,182 @@ def poisson_arrivals(seed: int, rate: float, duration: float) -> np.ndarray:
     gaps = -np.log1p(-rng.uniform(n_max)) / rate
     t = np.cumsum(gaps)
     return t[t < duration]
+
+
+# --------------------------------------------------------------------------
+# visual-inertial problems
+# --------------------------------------------------------------------------
+
+GRAVITY = np.array([0.0, 0.0, -9.81])
+
+
+def _rodrigues(w: np.ndarray) -> np.ndarray:
+    """Rotation matrix of one angle-axis vector (world simulator)."""
+    t = float(np.linalg.norm(w))
+    K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    if t < 1e-9:
+        return np.eye(3) + K + 0.5 * K @ K
+    return np.eye(3) + np.sin(t) / t * K + (1.0 - np.cos(t)) / (t * t) * K @ K
+
+
+@dataclass
+class VIProblem:
+    """Keyframe states x = [q (x y z w), p, v, bg, ba] (16), landmarks, stereo edges and, per
+    consecutive keyframe pair, the raw IMU samples between them."""
+    name: str
+    seed: int
+    nav_gt: np.ndarray        # (K, 16)
+    pts_gt: np.ndarray        # (P, 3)
+    nav0: np.ndarray          # (K, 16) initial state (zero bias estimates)
+    pts0: np.ndarray          # (P, 3)
+    kf_idx: np.ndarray        # (E,) int32 keyframe of each stereo edge
+    pt_idx: np.ndarray        # (E,) int32
+    obs: np.ndarray           # (E, 3) [u_l, v_l, u_r]
+    imu_gyro: np.ndarray      # (K-1, N, 3) measured angular rates between keyframes k, k+1
+    imu_acc: np.ndarray       # (K-1, N, 3) measured specific forces
+    dt: float
+    camera: dict              # fx fy cx cy baseline R_cb t_cb width height
+    noise: dict               # sigma_g sigma_a sigma_bg sigma_ba pixel
+    huber_delta: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_kf(self) -> int:
+        return self.nav_gt.shape[0]
+
+    @property
+    def n_pts(self) -> int:
+        return self.pts_gt.shape[0]
+
+    @property
+    def n_edges(self) -> int:
+        return self.kf_idx.shape[0]
+
+
+def vi_problem(seed: int, n_kf: int = 3000, n_pts: int = 200_000, rate: float = 200.0,
+               kf_gap: float = 0.25, sigma_g: float = 1.7e-4, sigma_a: float = 2e-3,
+               sigma_bg: float = 2e-5, sigma_ba: float = 3e-3, pixel_sigma: float = 1.0,
+               imu_noise: bool = True, mean_track: float = 10.0, name: str = "vi") -> VIProblem:
+    """Stereo-inertial trajectory: smooth random body rates and world accelerations sampled
+    at `rate` Hz; ground-truth keyframe states are the discrete integration of the true
+    samples (R <- R Exp(w dt), v <- v + (g + R f) dt, p <- p + v dt + (g + R f) dt^2 / 2 with
+    f the specific force), one keyframe every kf_gap seconds.  Landmarks are back-projected
+    from random pixels of a keyframe at depth U[2, 20] and observed by nearby keyframes whose
+    left and right images contain them."""
+    rng_traj, rng_vis = Stream(seed, 31), Stream(seed, 32)
+    rng_noise, rng_init = Stream(seed, 33), Stream(seed, 34)
+    dt = 1.0 / rate
+    N = int(round(kf_gap * rate))
+    S = (n_kf - 1) * N
+    t = np.arange(S + 1) * dt
+    # smooth world velocity v(t) = v_init + sum of sinusoids (periods 2-20 s); a = dv/dt
+    amp = rng_traj.uniform(9, 0.05, 0.4).reshape(3, 3) * np.array([[1.0], [1.0], [0.2]])
+    frq = 2.0 * np.pi / rng_traj.uniform(9, 2.0, 20.0).reshape(3, 3)
+    phs = rng_traj.uniform(9, 0.0, 2.0 * np.pi).reshape(3, 3)
+    a_world = np.zeros((S + 1, 3))
+    for ax in range(3):
+        for j in range(3):
+            a_world[:, ax] += amp[ax, j] * frq[ax, j] * np.cos(frq[ax, j] * t + phs[ax, j])
+    v_init = np.array([1.0, 0.0, 0.0]) + (amp * np.sin(phs)).sum(axis=1) * 0.0
+    # smooth body rates, yaw dominated
+    wamp = rng_traj.uniform(9, 0.02, 0.1).reshape(3, 3) * np.array([[0.3], [0.3], [1.0]])
+    wfrq = 2.0 * np.pi / rng_traj.uniform(9, 2.0, 20.0).reshape(3, 3)
+    wphs = rng_traj.uniform(9, 0.0, 2.0 * np.pi).reshape(3, 3)
+    w_body = np.zeros((S + 1, 3))
+    for ax in range(3):
+        for j in range(3):
+            w_body[:, ax] += wamp[ax, j] * np.sin(wfrq[ax, j] * t + wphs[ax, j])
+    bg_true = rng_traj.normal(3, 1e-3)
+    ba_true = rng_traj.normal(3, 1e-2)
+    # discrete integration of the true samples -> ground truth at every keyframe
+    Rk = np.eye(3)
+    pk = np.zeros(3)
+    vk = v_init.copy()
+    gyro = np.empty((S, 3))
+    accm = np.empty((S, 3))
+    nav_gt = np.zeros((n_kf, 16))
+    for k in range(S + 1):
+        if k % N == 0:
+            i = k // N
+            nav_gt[i, 0:4] = _quat_from_matrix(Rk[None])[0][[1, 2, 3, 0]]
+            nav_gt[i, 4:7] = pk
+            nav_gt[i, 7:10] = vk
+            nav_gt[i, 10:13] = bg_true
+            nav_gt[i, 13:16] = ba_true
+        if k == S:
+            break
+        f_body = Rk.T @ (a_world[k] - GRAVITY)
+        gyro[k] = w_body[k] + bg_true
+        accm[k] = f_body + ba_true
+        acc_w = GRAVITY + Rk @ (accm[k] - ba_true)
+        pk = pk + vk * dt + 0.5 * acc_w * dt * dt
+        vk = vk + acc_w * dt
+        Rk = Rk @ _rodrigues((gyro[k] - bg_true) * dt)
+    if imu_noise:
+        gyro = gyro + rng_noise.normal(3 * S, sigma_g / np.sqrt(dt)).reshape(S, 3)
+        accm = accm + rng_noise.normal(3 * S, sigma_a / np.sqrt(dt)).reshape(S, 3)
+
+    # stereo rig: camera z = body x (forward), camera x = -body y, camera y = -body z
+    R_cb = np.array([[0.0, -1.0, 0.0], [0.0, 0.0, -1.0], [1.0, 0.0, 0.0]])
+    t_cb = np.array([0.02, -0.01, 0.05])
+    cam = dict(fx=450.0, fy=450.0, cx=320.0, cy=240.0, baseline=0.11, R_cb=R_cb, t_cb=t_cb,
+               width=640.0, height=480.0)
+    Rq = _matrix_from_quat(nav_gt[:, [3, 0, 1, 2]])          # (K,3,3) body-to-world
+    # landmarks
+    anchor = rng_vis.integers(n_pts, 0, n_kf)
+    u = rng_vis.uniform(n_pts, 40.0, 600.0)
+    v = rng_vis.uniform(n_pts, 40.0, 440.0)
+    depth = rng_vis.uniform(n_pts, 2.0, 20.0)
+    Xc = np.stack([(u - cam["cx"]) / cam["fx"] * depth, (v - cam["cy"]) / cam["fy"] * depth, depth], axis=1)
+    Xb = (Xc - t_cb) @ R_cb
+    X = np.einsum("nij,nj->ni", Rq[anchor], Xb) + nav_gt[anchor, 4:7]
+    q_geo = (mean_track - 2.0) / (mean_track - 1.0)
+    L = np.minimum(2 + np.floor(np.log1p(-rng_vis.uniform(n_pts)) / np.log(q_geo)).astype(np.int64), 40)
+    L = np.minimum(L, n_kf)
+    start = np.clip(anchor - L // 2, 0, n_kf - L)
+    E0 = int(L.sum())
+    pt_e = np.repeat(np.arange(n_pts), L)
+    kf_e = np.repeat(start, L) + (np.arange(E0) - np.repeat(np.cumsum(L) - L, L))
+    Xbe = np.einsum("nji,nj->ni", Rq[kf_e], X[pt_e] - nav_gt[kf_e, 4:7])
+    Xce = Xbe @ R_cb.T + t_cb
+    z = Xce[:, 2]
+    ok = z > 0.5
+    zs = np.where(ok, z, 1.0)
+    ul = cam["fx"] * Xce[:, 0] / zs + cam["cx"]
+    vl = cam["fy"] * Xce[:, 1] / zs + cam["cy"]
+    ur = cam["fx"] * (Xce[:, 0] - cam["baseline"]) / zs + cam["cx"]
+    ok &= (ul >= 0) & (ul < cam["width"]) & (vl >= 0) & (vl < cam["height"]) & (ur >= 0)
+    pt_e, kf_e = pt_e[ok], kf_e[ok]
+    obs = np.stack([ul, vl, ur], axis=1)[ok]
+    cnt = np.bincount(pt_e, minlength=n_pts)
+    good = cnt >= 2
+    new_id = np.cumsum(good) - 1
+    sel = good[pt_e]
+    pt_e, kf_e, obs = new_id[pt_e[sel]], kf_e[sel], obs[sel]
+    X = X[good]
+    obs = obs + rng_noise.normal(obs.size, pixel_sigma).reshape(obs.shape)
+    order = np.argsort(kf_e, kind="stable")
+    kf_e, pt_e, obs = kf_e[order].astype(np.int32), pt_e[order].astype(np.int32), obs[order]
+
+    # initial state: rotation turned by 0.02 rad (random axis, right), position and velocity
+    # N(0, 0.05^2) per axis, biases zero, points N(0, 0.1^2) per axis
+    nav0 = nav_gt.copy()
+    dq = _quat_from_angle_axis(0.02 * rng_init.unit_vectors(n_kf))
+    q = _quat_mul(nav_gt[:, [3, 0, 1, 2]], dq)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q[q[:, 0] < 0] *= -1.0
+    nav0[:, 0:4] = q[:, [1, 2, 3, 0]]
+    nav0[:, 4:7] += rng_init.normal(3 * n_kf, 0.05).reshape(n_kf, 3)
+    nav0[:, 7:10] += rng_init.normal(3 * n_kf, 0.05).reshape(n_kf, 3)
+    nav0[:, 10:16] = 0.0
+    pts0 = X + rng_init.normal(3 * len(X), 0.1).reshape(len(X), 3)
+    return VIProblem(name, seed, nav_gt, X, nav0, pts0, kf_e, pt_e, obs,
+                     gyro.reshape(n_kf - 1, N, 3), accm.reshape(n_kf - 1, N, 3), dt, cam,
+                     dict(sigma_g=sigma_g, sigma_a=sigma_a, sigma_bg=sigma_bg, sigma_ba=sigma_ba,
+                          pixel=pixel_sigma), float(np.sqrt(7.815)))
+
+
+def vi_global(seed: int = 3, **kw) -> VIProblem:
+    """3,000 stereo keyframes, 200,000 landmarks, ~2M stereo observations, IMU at 200 Hz
+    over 0.25 s gaps."""
+    return vi_problem(seed, 3000, 200_000, name="vi_global_k3000_p200k", **kw)
