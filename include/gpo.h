@@ -60,14 +60,39 @@ typedef enum {
 /* Vertex kinds (Listing 1's dimension = tangent block size; state size in brackets).
  *  GPO_V_BA_CAMERA9: BAL camera [wx wy wz tx ty tz f k1 k2], tangent 9;
  *                    rotation updated as w <- Log(Exp(dw) Exp(w)), rest additive.
- *  GPO_V_POINT3:     3-D point [X Y Z], tangent 3, additive; eliminated by Schur. */
-enum { GPO_V_BA_CAMERA9 = 0, GPO_V_POINT3 = 1 };
+ *  GPO_V_POINT3:     3-D point [X Y Z], tangent 3, additive; eliminated by Schur.
+ *  GPO_V_NAV15:      keyframe navigation state [qx qy qz qw px py pz vx vy vz
+ *                    bgx bgy bgz bax bay baz] (16 doubles; q a unit quaternion of the
+ *                    body-to-world rotation R, p and v in the world frame, gyroscope and
+ *                    accelerometer biases), tangent 15 [dtheta dp dv dbg dba]:
+ *                    R <- R Exp(dtheta), p <- p + R dp, the rest additive (Sec. V-C's
+ *                    IMU-camera pose, velocity and bias vertices as one block).
+ * A graph holds points and ONE camera kind (GPO_V_BA_CAMERA9 or GPO_V_NAV15). */
+enum { GPO_V_BA_CAMERA9 = 0, GPO_V_POINT3 = 1, GPO_V_NAV15 = 2 };
 
-/* Edge kinds.
- *  GPO_E_BA_REPROJ: 2-D reprojection (Eq. 7, Sec. V BAL problems).  Vertex ids per
- *    edge: {camera, point}.  meas: 2 doubles [u v] (pixels).  Residual
- *    r = f (1 + k1 |p|^2 + k2 |p|^4) p - meas with P = R(w) X + t, p = -P_xy / P_z. */
-enum { GPO_E_BA_REPROJ = 0 };
+/* Edge kinds (vertex ids per edge in brackets; meas length; residual size m).
+ *  GPO_E_BA_REPROJ  {camera9, point}; meas 2 [u v] pixels; m = 2 (Eq. 7, Sec. V BAL).
+ *    r = f (1 + k1 |p|^2 + k2 |p|^4) p - meas with P = R(w) X + t, p = -P_xy / P_z.
+ *  GPO_E_STEREO     {nav15, point}; meas 3 [u_l v_l u_r] pixels; m = 3 (Sec. V-C).
+ *    X_b = R^T (X - p), X_c = R_cb X_b + t_cb (rig of gpo_set_stereo_camera),
+ *    r = [fx X_c/Z_c + cx, fy Y_c/Z_c + cy, fx (X_c - b)/Z_c + cx] - meas.
+ *  GPO_E_IMU        {nav15 i, nav15 j}; meas = a preintegrated IMU record of
+ *    GPO_IMU_MEAS_LEN doubles (gpo_imu_preintegrate); m = 9 (Eq. 8 r_I):
+ *      r_R = Log((dR Exp(JRg dbg))^T R_i^T R_j),
+ *      r_v = R_i^T (v_j - v_i - g T) - (dv + Jvg dbg + Jva dba),
+ *      r_p = R_i^T (p_j - p_i - v_i T - g T^2 / 2) - (dp + Jpg dbg + Jpa dba),
+ *    dbg = bg_i - bg0, dba = ba_i - ba0, g = (0, 0, -9.81).
+ *  GPO_E_BIAS_RW    {nav15 i, nav15 j}; meas unused (may be NULL); m = 6 (Eq. 8 r_b):
+ *    r = [bg_j - bg_i, ba_j - ba_i].
+ *  GPO_E_BIAS_PRIOR {nav15}; meas 6 [bg ba] prior; m = 6: r = [bg, ba] - meas.
+ * GPO_E_IMU, GPO_E_BIAS_RW and GPO_E_BIAS_PRIOR take no robust loss. */
+enum { GPO_E_BA_REPROJ = 0, GPO_E_STEREO = 1, GPO_E_IMU = 2, GPO_E_BIAS_RW = 3,
+       GPO_E_BIAS_PRIOR = 4 };
+
+/* Preintegrated IMU record (doubles, matrices row-major):
+ *   [0..9)  dR   [9..12) dv   [12..15) dp   [15..24) JRg  [24..33) Jvg  [33..42) Jva
+ *   [42..51) Jpg [51..60) Jpa [60] T        [61..64) bg0  [64..67) ba0 */
+enum { GPO_IMU_MEAS_LEN = 67 };
 
 enum { GPO_LOSS_NONE = 0, GPO_LOSS_HUBER = 1 };
 
@@ -143,15 +168,16 @@ gpo_status gpo_graph_create(const gpo_graph_desc* desc, gpo_graph** out);
 gpo_status gpo_graph_destroy(gpo_graph* g);
 
 /* Adds n vertices of `kind` (Listing 4: add_vertex).  block_size must equal the
- * kind's tangent dimension (9 camera, 3 point).  *first_id (optional) receives the
- * id of the first new vertex; the others follow consecutively.  Initial state is
- * zero until gpo_set_initial.  Errors: GPO_ERR_ARG, GPO_ERR_STATE (after optimize). */
+ * kind's tangent dimension (9 camera, 3 point, 15 navigation).  *first_id (optional)
+ * receives the id of the first new vertex; the others follow consecutively.  Initial
+ * state is zero (navigation states: identity rotation) until gpo_set_initial.
+ * Errors: GPO_ERR_ARG (also for a second camera kind), GPO_ERR_STATE (after optimize). */
 gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int64_t n,
                             int64_t* first_id);
 
 /* Adds n edges of `kind` (Listing 4: add_factor(ids, obs, precision, data, loss)).
  *  vertex_ids: n * arity int64 ids, row-major, in the kind's slot order.
- *  meas:       n * meas_len doubles (2 for GPO_E_BA_REPROJ).
+ *  meas:       n * meas_len doubles (see the edge kinds).
  *  info:       n * m * m doubles, row-major symmetric positive definite information
  *              matrices Omega (m = residual size), or NULL for identity (Sec. IV-A:
  *              a null precision matrix means identity).
@@ -163,6 +189,28 @@ gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int6
 gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* vertex_ids,
                          const double* meas, const double* info, int32_t loss_kind,
                          double loss_delta, int64_t* first_id);
+
+/* Intrinsics and extrinsics of the stereo rig shared by the graph's GPO_E_STEREO
+ * edges: rig[17] = [fx fy cx cy baseline, R_cb (9, row-major, body-to-camera
+ * rotation), t_cb (3)].  Required before the first optimize of a graph with stereo
+ * edges.  Errors: GPO_ERR_ARG (null), GPO_ERR_STATE (after the first optimize). */
+gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig);
+
+/* On-manifold IMU preintegration (Forster et al., T-RO 2017) of n gyroscope and
+ * accelerometer samples gyro[n][3] (rad/s), acc[n][3] (m/s^2) taken every dt seconds,
+ * at bias estimates bg0[3], ba0[3], with white-noise densities sigma_g, sigma_a:
+ *   dR_{k+1} = dR_k Exp((w_k - bg0) dt), dv_{k+1} = dv_k + dR_k (a_k - ba0) dt,
+ *   dp_{k+1} = dp_k + dv_k dt + dR_k (a_k - ba0) dt^2 / 2,
+ * with first-order bias Jacobians and the covariance of (dphi, dv, dp) propagated from
+ * the discrete noise sigma / sqrt(dt).  meas_out receives the GPO_IMU_MEAS_LEN record
+ * for GPO_E_IMU; cov_out (9x9, optional) the covariance; info_out (9x9, optional) its
+ * inverse, the information matrix to pass to gpo_add_edges.  Host only: needs no GPU.
+ * Errors: GPO_ERR_ARG (null input, n < 1, dt <= 0, sigma <= 0),
+ *         GPO_ERR_NUMERIC (covariance not positive definite). */
+gpo_status gpo_imu_preintegrate(const double* gyro, const double* acc, int64_t n, double dt,
+                                const double* bg0, const double* ba0, double sigma_g,
+                                double sigma_a, double* meas_out, double* cov_out,
+                                double* info_out);
 
 /* Fixes or frees a vertex (Listing 5: set_fixed).  A fixed vertex keeps its state
  * bit for bit; its edges still constrain the other vertices.
@@ -316,11 +364,17 @@ gpo_status gpo_ba_cost_noalloc(int32_t device, void* cuda_stream, const double* 
  * ------------------------------------------------------------------------ */
 
 /* Linearises every edge at the current state in the graph's precision.
- * r_out: n_edges * m doubles (whitened, Huber-weighted residual sqrt(rho') U r);
- * J_out: n_edges * m * (sum of the edge's vertex tangent sizes) doubles, row-major
- *        per residual row, vertex blocks in slot order, same weighting, as stored
- *        (rounded to the storage precision).  Edge order = edge ids; disabled edges
- *        are written as zeros.  Either pointer may be NULL. */
+ * Layout per edge id, (R, K) = (2, 12) for graphs of BA cameras, (9, 30) for graphs of
+ * navigation states:
+ * r_out: n_edges * R doubles: the whitened residual (observation edges:
+ *        Huber-weighted, sqrt(rho') U r), rows beyond the edge's m are zero;
+ * J_out: n_edges * R * K doubles, row-major per residual row, with the same
+ *        weighting: observation edges have the camera block in columns [0, DB)
+ *        (DB = 9 or 15; a stereo edge fills the first 6, the pose) and the point in
+ *        [DB, DB + 3); camera-side edges have keyframe i in [0, 15) and j in [15, 30).
+ *        Observation-edge values are as stored (rounded to the storage precision);
+ *        camera-side edges are FP64.  Disabled edges are written as zeros.
+ * Either pointer may be NULL. */
 gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out);
 
 /* Solves one damped system (H + lambda D^T D) dx = -b at the current state with
@@ -330,9 +384,10 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out);
 gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* params,
                           double* dx_out, int32_t* pcg_iters);
 
-/* Camera Schur blocks at damping lambda: S_out[C][9][9] the diagonal blocks
- * S_cc = H_cc + lambda D_c - sum_p W H_pp^-1 W^T, g_out[C][9] the reduced right-hand
- * side -b_c + sum_p W H_pp^-1 b_p, cameras in id order.  Either may be NULL. */
+/* Camera Schur blocks at damping lambda: S_out[C][DB][DB] the diagonal blocks
+ * S_cc = H_cc + lambda D_c - sum_p W H_pp^-1 W^T, g_out[C][DB] the reduced right-hand
+ * side -b_c + sum_p W H_pp^-1 b_p, cameras in id order (DB = 9 for BA cameras, 15 for
+ * navigation states; H_cc includes the camera-side edges).  Either may be NULL. */
 gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* params,
                            double* S_out, double* g_out);
 

@@ -38,8 +38,34 @@ using gpo_host::fail;
 
 namespace {
 
-int tangent_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : 3; }
-int state_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : 3; }
+int tangent_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : (kind == GPO_V_NAV15 ? 15 : 3); }
+int state_dim(int kind) { return kind == GPO_V_BA_CAMERA9 ? 9 : (kind == GPO_V_NAV15 ? 16 : 3); }
+bool is_camera(int kind) { return kind == GPO_V_BA_CAMERA9 || kind == GPO_V_NAV15; }
+int tri(int n) { return n * (n + 1) / 2; }
+
+// Upper-triangular U with Omega = U^T U (U = L^T of the Cholesky factor L of Omega),
+// row-major m x m.  False if Omega is not symmetric positive definite.
+bool sqrt_info(const double* Om, int m, double* U) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(Om[i * m + j] - Om[j * m + i]) > 1e-12 * (std::fabs(Om[i * m + i]) + std::fabs(Om[j * m + j])))
+        return false;
+  std::vector<double> L(m * m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    double s = Om[j * m + j];
+    for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
+    if (!(s > 0.0) || !std::isfinite(s)) return false;
+    L[j * m + j] = std::sqrt(s);
+    for (int i = j + 1; i < m; ++i) {
+      double t = Om[i * m + j];
+      for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+      L[i * m + j] = t / L[j * m + j];
+    }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) U[i * m + j] = L[j * m + i];
+  return true;
+}
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -108,10 +134,15 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
     if (plan_bytes) *plan_bytes = g->arena_bytes;
     return GPO_OK;
   }
+  const gpo::KernelSet& ks = kernels_of(g);
+  const int SS = ks.SS, DB = ks.DB, M = ks.M, NJ = ks.NJ, NPA = ks.NPA, DC = ks.DC;
+  const int TB = tri(DB), NQ = tri(M);
   const int C = (int)g->cam_fixed.size();
   const int P = (int)g->pt_fixed.size();
   const int64_t Eall = (int64_t)g->e_cam.size();
   if (Eall > INT32_MAX / 2) return fail(g, GPO_ERR_UNSUPPORTED, "too many edges (%lld)", (long long)Eall);
+  if (ks.model == gpo::ModelKind::STEREO && Eall > 0 && !g->camk_set)
+    return fail(g, GPO_ERR_STATE, "stereo edges need the rig: call gpo_set_stereo_camera first");
 
   // point order: by the smallest camera index among the point's active edges
   // (points without active edges last), ties by point index.  Consecutive points
@@ -151,10 +182,10 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   int ch = g->desc.chunk_edges > 0 ? g->desc.chunk_edges : gpo::default_ch_max(g->prec);
   if (ch < 32) ch = 32;
   while (ch < maxdeg) ch *= 2;
-  if (ch > gpo::max_supported_ch(g->prec))
+  if (ch > ks.max_supported_ch(g->prec))
     return fail(g, GPO_ERR_UNSUPPORTED,
                 "a point has %d observations; this precision supports at most %d per point", maxdeg,
-                gpo::max_supported_ch(g->prec));
+                ks.max_supported_ch(g->prec));
   g->ch_max = ch;
   // chunks of whole points, at most ch edges and ch points each
   std::vector<int32_t> ch_e0{0}, ch_p0{0};
@@ -186,7 +217,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   }
   std::vector<uint16_t> e_pos(E), e_slot(E), ch_sorted(E);
   std::vector<int32_t> ch_s0{0}, slot_e0, slot_cam;
-  const size_t jpos = (size_t)E * gpo::kJComp;
+  const size_t jpos = (size_t)E * NJ;
   {
     std::vector<std::pair<int32_t, int32_t>> tmp;
     for (int k = 0; k < NCH; ++k) {
@@ -229,56 +260,95 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
     }
   }
   // per-edge data in sorted order
-  std::vector<double> obs_s(2 * (size_t)E), delta_s(E), info_s;
+  std::vector<double> obs_s((size_t)M * E), delta_s(E), info_s;
   for (int i = 0; i < E; ++i) {
     const int64_t e = g->sorted_edge[i];
-    obs_s[2 * i] = g->e_obs[2 * e];
-    obs_s[2 * i + 1] = g->e_obs[2 * e + 1];
+    for (int k = 0; k < M; ++k) obs_s[(size_t)M * i + k] = g->e_obs[(size_t)M * e + k];
     delta_s[i] = g->e_delta[e];
   }
   if (g->any_info) {
-    info_s.resize(3 * (size_t)E);
+    info_s.resize((size_t)NQ * E);
     for (int i = 0; i < E; ++i)
-      for (int k = 0; k < 3; ++k) info_s[3 * i + k] = g->e_sqinfo[3 * g->sorted_edge[i] + k];
+      for (int k = 0; k < NQ; ++k) info_s[(size_t)NQ * i + k] = g->e_sqinfo[(size_t)NQ * g->sorted_edge[i] + k];
   }
   std::vector<uint8_t> pt_fixed_s(P);
   for (int p = 0; p < P; ++p) pt_fixed_s[g->pt_old2new[p]] = g->pt_fixed[p];
+
+  // camera-side edges: active ones, sorted by (first camera, index)
+  g->x_sorted.clear();
+  for (size_t x = 0; x < g->x_kind.size(); ++x)
+    if (g->x_active[x]) g->x_sorted.push_back((int32_t)x);
+  std::stable_sort(g->x_sorted.begin(), g->x_sorted.end(),
+                   [&](int32_t a, int32_t b) { return g->x_i[a] < g->x_i[b]; });
+  const int NX = (int)g->x_sorted.size();
+  std::vector<int32_t> xi_s(NX), xj_s(NX), xk_s(NX), xo_off(C + 1, 0), xk_off(C + 1, 0), xk_list(2 * (size_t)NX);
+  std::vector<double> xrec_s((size_t)NX * gpo::kXRec);
+  for (int t = 0; t < NX; ++t) {
+    const int x = g->x_sorted[t];
+    xi_s[t] = g->x_i[x];
+    xj_s[t] = g->x_j[x];
+    xk_s[t] = g->x_kind[x];
+    std::memcpy(&xrec_s[(size_t)t * gpo::kXRec], &g->x_rec[(size_t)x * gpo::kXRec], gpo::kXRec * sizeof(double));
+    xo_off[xi_s[t] + 1]++;
+    xk_off[xi_s[t] + 1]++;
+    if (xj_s[t] >= 0) xk_off[xj_s[t] + 1]++;
+  }
+  for (int c = 0; c < C; ++c) {
+    xo_off[c + 1] += xo_off[c];
+    xk_off[c + 1] += xk_off[c];
+  }
+  {
+    std::vector<int32_t> fill(xk_off.begin(), xk_off.end() - 1);
+    for (int t = 0; t < NX; ++t) {
+      xk_list[fill[xi_s[t]]++] = 2 * t;
+      if (xj_s[t] >= 0) xk_list[fill[xj_s[t]]++] = 2 * t + 1;
+    }
+  }
 
   // ---- memory plan
   const Prec pr = g->prec;
   const size_t sA = at_size(pr), sJ = jt_size(pr);
   DevBA d{};
-  d.C = C; d.P = P; d.E = E; d.NCH = NCH; d.NS = NS; d.ch_max = ch;
+  d.C = C; d.P = P; d.E = E; d.NCH = NCH; d.NS = NS; d.NX = NX; d.ch_max = ch;
+  d.model = (int)ks.model;
+  std::memcpy(d.camk, g->camk, sizeof(d.camk));
   d.ns_max = ns_max; d.np_max = np_max;
   d.ncblk = std::max(1, (C + gpo::kCamPerBlock - 1) / gpo::kCamPerBlock);
   Plan pl;
   int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d,
       *slot_pos_d;
+  int *xe_i_d, *xe_j_d, *xe_kind_d, *xo_off_d, *xk_off_d, *xk_list_d;
+  double* xe_rec_d;
   uint16_t *e_pos_d, *e_slot_d, *ch_sorted_d;
   uint8_t *cam_fixed_d, *pt_fixed_d;
   double *obs_d, *delta_d, *info_d = nullptr;
-  pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, 2 * (size_t)E); pl.add(&delta_d, E);
-  if (g->any_info) pl.add(&info_d, 3 * (size_t)E);
+  pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, (size_t)M * E); pl.add(&delta_d, E);
+  if (g->any_info) pl.add(&info_d, (size_t)NQ * E);
   pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
   pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E); pl.add(&e_slot_d, E);
   pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
   pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1)); pl.add(&slot_pos_d, std::max(NS, 1));
   pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
-  pl.add(&d.cam, 9 * (size_t)C); pl.add(&d.cam_cand, 9 * (size_t)C);
+  pl.add(&xe_i_d, std::max(NX, 1)); pl.add(&xe_j_d, std::max(NX, 1)); pl.add(&xe_kind_d, std::max(NX, 1));
+  pl.add(&xe_rec_d, (size_t)std::max(NX, 1) * gpo::kXRec);
+  pl.add(&xo_off_d, C + 1); pl.add(&xk_off_d, C + 1); pl.add(&xk_list_d, std::max(2 * NX, 1));
+  pl.add(&d.xe_J, (size_t)std::max(NX, 1) * gpo::kXJ); pl.add(&d.xe_r, (size_t)std::max(NX, 1) * gpo::kXRows);
+  pl.add(&d.xe_cost, std::max(NX, 1)); pl.add(&d.xe_md, std::max(NX, 1));
+  pl.add(&d.cam, (size_t)SS * C); pl.add(&d.cam_cand, (size_t)SS * C);
   pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
   pl.add(&d.pt, 3 * (size_t)P); pl.add(&d.pt_cand, 3 * (size_t)P);
   pl.add_raw(&d.J, std::max<size_t>(jpos, 8) * sJ);
   pl.add_raw(&d.Hpp, 6 * (size_t)P * sA); pl.add_raw(&d.bp, 3 * (size_t)P * sA);
   pl.add_raw(&d.Hinv, 6 * (size_t)P * sA); pl.add_raw(&d.dp, 3 * (size_t)P * sA);
-  pl.add_raw(&d.partA, (size_t)gpo::kPartA * NS * sA); pl.add_raw(&d.partB, (size_t)gpo::kPartA * NS * sA);
-  pl.add_raw(&d.partV, 9 * (size_t)NS * sA);
-  pl.add_raw(&d.Hcl, 45 * (size_t)C * sA); pl.add_raw(&d.bc, 9 * (size_t)C * sA);
-  pl.add_raw(&d.S, 45 * (size_t)C * sA); pl.add_raw(&d.Minv, 45 * (size_t)C * sA);
-  pl.add_raw(&d.g, 9 * (size_t)C * sA);
-  pl.add_raw(&d.x, 9 * (size_t)C * sA); pl.add_raw(&d.r, 9 * (size_t)C * sA);
-  pl.add_raw(&d.z, 9 * (size_t)C * sA); pl.add_raw(&d.p, 9 * (size_t)C * sA);
-  pl.add_raw(&d.y, 9 * (size_t)C * sA); pl.add_raw(&d.xbest, 9 * (size_t)C * sA);
-  pl.add_raw(&d.p2, 9 * (size_t)C * sA);
+  pl.add_raw(&d.partA, (size_t)NPA * NS * sA); pl.add_raw(&d.partB, (size_t)NPA * NS * sA);
+  pl.add_raw(&d.partV, (size_t)DC * NS * sA);
+  pl.add_raw(&d.Hcl, (size_t)TB * C * sA); pl.add_raw(&d.bc, (size_t)DB * C * sA);
+  pl.add_raw(&d.S, (size_t)TB * C * sA); pl.add_raw(&d.Minv, (size_t)TB * C * sA);
+  pl.add_raw(&d.g, (size_t)DB * C * sA);
+  pl.add_raw(&d.x, (size_t)DB * C * sA); pl.add_raw(&d.r, (size_t)DB * C * sA);
+  pl.add_raw(&d.z, (size_t)DB * C * sA); pl.add_raw(&d.p, (size_t)DB * C * sA);
+  pl.add_raw(&d.y, (size_t)DB * C * sA); pl.add_raw(&d.xbest, (size_t)DB * C * sA);
+  pl.add_raw(&d.p2, (size_t)DB * C * sA);
   pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
   pl.add(&d.cblk_part, 2 * 4 * (size_t)d.ncblk);   // cam_apply runs four CTAs per camera block
   pl.add(&d.sc, 1);
@@ -315,6 +385,8 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d;
   d.e_pos = e_pos_d; d.e_slot = e_slot_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
   d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.slot_pos = slot_pos_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
+  d.xe_i = xe_i_d; d.xe_j = xe_j_d; d.xe_kind = xe_kind_d; d.xe_rec = xe_rec_d;
+  d.xo_off = xo_off_d; d.xk_off = xk_off_d; d.xk_list = xk_list_d;
   d.dbg_r = nullptr;
   cudaStream_t st = g->stream;
   GPO_CUDA(g, up(e_cam, e_cam_s, st));
@@ -336,6 +408,13 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   GPO_CUDA(g, up(slot_pos_d, slot_pos, st));
   GPO_CUDA(g, up(cam_fixed_d, g->cam_fixed, st));
   GPO_CUDA(g, up(pt_fixed_d, pt_fixed_s, st));
+  GPO_CUDA(g, up(xe_i_d, xi_s, st));
+  GPO_CUDA(g, up(xe_j_d, xj_s, st));
+  GPO_CUDA(g, up(xe_kind_d, xk_s, st));
+  GPO_CUDA(g, up(xe_rec_d, xrec_s, st));
+  GPO_CUDA(g, up(xo_off_d, xo_off, st));
+  GPO_CUDA(g, up(xk_off_d, xk_off, st));
+  if (NX) GPO_CUDA(g, up(xk_list_d, xk_list, st));
   GPO_CUDA(g, up(d.cam, g->cam_state, st));
   {
     std::vector<double> pts(3 * (size_t)P);
@@ -346,6 +425,8 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(jpos, 8) * sJ, st));
   GPO_CUDA(g, cudaMemsetAsync(d.sc, 0, sizeof(Scalars), st));
   GPO_CUDA(g, cudaMemsetAsync(d.dp, 0, 3 * (size_t)P * sA, st));
+  GPO_CUDA(g, cudaMemsetAsync(d.xe_cost, 0, std::max(NX, 1) * sizeof(double), st));
+  GPO_CUDA(g, cudaMemsetAsync(d.xe_md, 0, std::max(NX, 1) * sizeof(double), st));
   GPO_CUDA(g, cudaMemsetAsync(ch_prob_d, 0, std::max(NCH, 1) * sizeof(int), st));
   GPO_CUDA(g, cudaMemsetAsync(cb_prob_d, 0, d.ncblk * sizeof(int), st));
   GPO_CUDA(g, cudaMemsetAsync(pb_prob_d, 0, npb * sizeof(int), st));
@@ -364,6 +445,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   ls.ns_max = ns_max;
   ls.np_max = np_max;
   g->ls = ls;
+  g->ks = &ks;
   g->dev_desc = desc_d;
   g->h_ch_e0 = ch_e0;
   g->dev = d;
@@ -463,9 +545,9 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
     const int n = std::min(kGroup, max_it - launched);
     for (int i = 0; i < n; ++i) {
       g->cur_pcg_k = launched + i + 1;
-      run(g, KK_SPMV, [&] { return gpo::launch_pcg_spmv(ls, g->prec, g->stream); });
-      run(g, KK_CAM_APPLY, [&] { return gpo::launch_cam_apply(ls, g->prec, g->stream); });
-      run(g, KK_PCG_UPDATE, [&] { return gpo::launch_pcg_update(ls, g->prec, g->stream); });
+      run(g, KK_SPMV, [&] { return g->ks->pcg_spmv(ls, g->prec, g->stream); });
+      run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
+      run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
     }
     launched += n;
     GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], ls.running, sizeof(int),
@@ -483,32 +565,32 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
 }
 
 gpo_status gpo_host::solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin) {
-  run(g, KK_LINEARIZE, [&] { return gpo::launch_linearize(ls, g->prec, force_lin, g->stream); });
-  run(g, KK_SCHUR, [&] { return gpo::launch_schur_prepare(ls, g->prec, g->stream); });
+  run(g, KK_LINEARIZE, [&] { return g->ks->linearize(ls, g->prec, force_lin, g->stream); });
+  run(g, KK_SCHUR, [&] { return g->ks->schur_prepare(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, sizeof(int), g->stream));
-  run(g, KK_CAM_FINALIZE, [&] { return gpo::launch_cam_finalize(ls, g->prec, g->stream); });
+  run(g, KK_CAM_FINALIZE, [&] { return g->ks->cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   gpo_status s = pcg_solve(g, ls, max_it);
   if (s != GPO_OK) return s;
   g->cur_pcg_k = 0;
-  run(g, KK_BACKSUB, [&] { return gpo::launch_backsub(ls, g->prec, g->stream); });
+  run(g, KK_BACKSUB, [&] { return g->ks->backsub(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
 
 gpo_status gpo_host::finish_iteration(gpo_graph* g, const gpo::LaunchSet& ls) {
-  run(g, KK_RETRACT, [&] { return gpo::launch_retract(ls, g->prec, g->stream); });
-  run(g, KK_COST, [&] { return gpo::launch_cost(ls, true, g->stream); });
-  run(g, KK_DECIDE, [&] { return gpo::launch_decide(ls, g->prec, g->stream); });
-  run(g, KK_COMMIT, [&] { return gpo::launch_commit(ls, g->stream); });
+  run(g, KK_RETRACT, [&] { return g->ks->retract(ls, g->prec, g->stream); });
+  run(g, KK_COST, [&] { return g->ks->cost(ls, true, g->stream); });
+  run(g, KK_DECIDE, [&] { return g->ks->decide(ls, g->prec, g->stream); });
+  run(g, KK_COMMIT, [&] { return g->ks->commit(ls, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
 
 gpo_status gpo_host::launch_initial_cost(gpo_graph* g, const gpo::LaunchSet& ls) {
-  run(g, KK_CAM_PREPARE, [&] { return gpo::launch_cam_prepare(ls, false, g->stream); });
-  run(g, KK_COST, [&] { return gpo::launch_cost(ls, false, g->stream); });
-  run(g, KK_COST_REDUCE, [&] { return gpo::launch_cost_init(ls, g->stream); });
+  run(g, KK_CAM_PREPARE, [&] { return g->ks->cam_prepare(ls, false, g->stream); });
+  run(g, KK_COST, [&] { return g->ks->cost(ls, false, g->stream); });
+  run(g, KK_COST_REDUCE, [&] { return g->ks->cost_init(ls, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
@@ -532,7 +614,7 @@ gpo_status gpo_host::download_state(gpo_graph* g) {
   if (!g->finalized) return GPO_OK;
   const DevBA& d = g->dev;
   std::vector<double> pts(3 * (size_t)d.P);
-  if (d.C) GPO_CUDA(g, cudaMemcpyAsync(g->cam_state.data(), d.cam, 9 * (size_t)d.C * sizeof(double),
+  if (d.C) GPO_CUDA(g, cudaMemcpyAsync(g->cam_state.data(), d.cam, (size_t)cam_ss(g) * d.C * sizeof(double),
                                       cudaMemcpyDeviceToHost, g->stream));
   if (d.P) GPO_CUDA(g, cudaMemcpyAsync(pts.data(), d.pt, 3 * (size_t)d.P * sizeof(double),
                                       cudaMemcpyDeviceToHost, g->stream));
@@ -639,18 +721,26 @@ gpo_status gpo_graph_destroy(gpo_graph* g) {
 gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int64_t n, int64_t* first_id) {
   if (!g) return GPO_ERR_ARG;
   if (g->finalized) return fail(g, GPO_ERR_STATE, "topology is frozen after the first optimize");
-  if (kind != GPO_V_BA_CAMERA9 && kind != GPO_V_POINT3) return fail(g, GPO_ERR_ARG, "unknown vertex kind %d", kind);
+  if (kind != GPO_V_BA_CAMERA9 && kind != GPO_V_POINT3 && kind != GPO_V_NAV15)
+    return fail(g, GPO_ERR_ARG, "unknown vertex kind %d", kind);
   if (block_size != tangent_dim(kind))
     return fail(g, GPO_ERR_ARG, "block size %d does not match kind %d (%d)", block_size, kind, tangent_dim(kind));
   if (n < 0) return fail(g, GPO_ERR_ARG, "negative count");
+  if (is_camera(kind) && g->cam_kind >= 0 && g->cam_kind != kind)
+    return fail(g, GPO_ERR_ARG, "a graph holds one camera kind (it already has kind %d)", g->cam_kind);
   const int64_t id0 = (int64_t)g->v_kind.size();
-  const int64_t loc0 = kind == GPO_V_BA_CAMERA9 ? (int64_t)g->cam_fixed.size() : (int64_t)g->pt_fixed.size();
+  const int64_t loc0 = is_camera(kind) ? (int64_t)g->cam_fixed.size() : (int64_t)g->pt_fixed.size();
   if (loc0 + n > INT32_MAX / 16) return fail(g, GPO_ERR_UNSUPPORTED, "too many vertices of kind %d", kind);
   g->v_kind.insert(g->v_kind.end(), n, (int8_t)kind);
   for (int64_t i = 0; i < n; ++i) g->v_local.push_back(loc0 + i);
-  if (kind == GPO_V_BA_CAMERA9) {
+  if (is_camera(kind)) {
+    if (n > 0) g->cam_kind = kind;
     g->cam_fixed.insert(g->cam_fixed.end(), n, 0);
-    g->cam_state.insert(g->cam_state.end(), 9 * n, 0.0);
+    const int w = state_dim(kind);
+    const size_t at = g->cam_state.size();
+    g->cam_state.insert(g->cam_state.end(), (size_t)w * n, 0.0);
+    if (kind == GPO_V_NAV15)
+      for (int64_t i = 0; i < n; ++i) g->cam_state[at + (size_t)w * i + 3] = 1.0;   // qw
   } else {
     g->pt_fixed.insert(g->pt_fixed.end(), n, 0);
     g->pt_state.insert(g->pt_state.end(), 3 * n, 0.0);
@@ -659,58 +749,143 @@ gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int6
   return GPO_OK;
 }
 
+gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig) {
+  if (!g) return GPO_ERR_ARG;
+  if (!rig) return fail(g, GPO_ERR_ARG, "null rig");
+  if (g->finalized) return fail(g, GPO_ERR_STATE, "the rig is frozen after the first optimize");
+  for (int k = 0; k < 17; ++k)
+    if (!std::isfinite(rig[k])) return fail(g, GPO_ERR_ARG, "rig value %d is not finite", k);
+  std::memset(g->camk, 0, sizeof(g->camk));
+  std::memcpy(g->camk, rig, 17 * sizeof(double));
+  g->camk_set = true;
+  return GPO_OK;
+}
+
+// Observation edges (camera, point) of the graph's camera kind.
+static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* ids, const double* meas,
+                                const double* info, int32_t loss_kind, double loss_delta) {
+  const int ck = kind == GPO_E_BA_REPROJ ? GPO_V_BA_CAMERA9 : GPO_V_NAV15;
+  const int m = kind == GPO_E_BA_REPROJ ? 2 : 3, nq = tri(m);
+  if (g->cam_kind >= 0 && g->cam_kind != ck)
+    return fail(g, GPO_ERR_ARG, "edge kind %d does not fit the graph's camera kind %d", kind, g->cam_kind);
+  if (n > 0 && !meas) return fail(g, GPO_ERR_ARG, "null measurements");
+  const int64_t V = (int64_t)g->v_kind.size();
+  const size_t base = g->e_cam.size();
+  auto undo = [&] {
+    g->e_cam.resize(base); g->e_pt.resize(base); g->e_eid.resize(base); g->e_obs.resize((size_t)m * base);
+    g->e_delta.resize(base); g->e_active.resize(base); g->e_sqinfo.resize((size_t)nq * base);
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t c = ids[2 * i], p = ids[2 * i + 1];
+    if (c < 0 || c >= V || p < 0 || p >= V || g->v_kind[c] != ck || g->v_kind[p] != GPO_V_POINT3) {
+      undo();
+      return fail(g, GPO_ERR_ARG, "edge %lld: ids must be (%s, point)", (long long)i,
+                  ck == GPO_V_NAV15 ? "navigation state" : "camera");
+    }
+    double U[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (info) {
+      if (!sqrt_info(info + (size_t)m * m * i, m, U)) {
+        undo();
+        return fail(g, GPO_ERR_ARG, "edge %lld: information matrix is not symmetric positive definite", (long long)i);
+      }
+    }
+    g->e_cam.push_back((int32_t)g->v_local[c]);
+    g->e_pt.push_back((int32_t)g->v_local[p]);
+    g->e_eid.push_back((int64_t)g->ed_kind.size() + i);
+    for (int k = 0; k < m; ++k) g->e_obs.push_back(meas[(size_t)m * i + k]);
+    for (int a = 0; a < m; ++a)
+      for (int b = a; b < m; ++b) {
+        const double u = U[a * m + b];
+        if (u != (a == b ? 1.0 : 0.0)) g->any_info = true;
+        g->e_sqinfo.push_back(u);
+      }
+    g->e_delta.push_back(loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0);
+    g->e_active.push_back(1);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    g->ed_kind.push_back((int8_t)kind);
+    g->ed_local.push_back((int64_t)base + i);
+  }
+  if (n > 0) g->cam_kind = ck;
+  return GPO_OK;
+}
+
+// Camera-side edges between navigation states.
+static gpo_status add_nav_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* ids, const double* meas,
+                                const double* info, int32_t loss_kind) {
+  if (loss_kind != GPO_LOSS_NONE) return fail(g, GPO_ERR_UNSUPPORTED, "edge kind %d takes no robust loss", kind);
+  if (g->cam_kind >= 0 && g->cam_kind != GPO_V_NAV15)
+    return fail(g, GPO_ERR_ARG, "edge kind %d needs navigation states", kind);
+  const int arity = kind == GPO_E_BIAS_PRIOR ? 1 : 2;
+  const int m = kind == GPO_E_IMU ? 9 : 6;
+  const int mlen = kind == GPO_E_IMU ? gpo::kImuMeas : (kind == GPO_E_BIAS_PRIOR ? 6 : 0);
+  if (n > 0 && mlen > 0 && !meas) return fail(g, GPO_ERR_ARG, "null measurements");
+  const int64_t V = (int64_t)g->v_kind.size();
+  const size_t base = g->x_kind.size();
+  auto undo = [&] {
+    g->x_i.resize(base); g->x_j.resize(base); g->x_kind.resize(base); g->x_eid.resize(base);
+    g->x_rec.resize(base * gpo::kXRec); g->x_active.resize(base);
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t a = ids[arity * i], b = arity == 2 ? ids[arity * i + 1] : -1;
+    const bool ok = a >= 0 && a < V && g->v_kind[a] == GPO_V_NAV15 &&
+                    (arity == 1 || (b >= 0 && b < V && b != a && g->v_kind[b] == GPO_V_NAV15));
+    if (!ok) {
+      undo();
+      return fail(g, GPO_ERR_ARG, "edge %lld: ids must be %s navigation state%s", (long long)i,
+                  arity == 2 ? "two distinct" : "one", arity == 2 ? "s" : "");
+    }
+    double U[81];
+    for (int k = 0; k < m * m; ++k) U[k] = (k % (m + 1)) == 0 ? 1.0 : 0.0;
+    if (info && !sqrt_info(info + (size_t)m * m * i, m, U)) {
+      undo();
+      return fail(g, GPO_ERR_ARG, "edge %lld: information matrix is not symmetric positive definite", (long long)i);
+    }
+    if (kind == GPO_E_IMU && !(meas[(size_t)mlen * i + 60] > 0.0)) {
+      undo();
+      return fail(g, GPO_ERR_ARG, "edge %lld: preintegration time must be positive", (long long)i);
+    }
+    const size_t r0 = g->x_rec.size();
+    g->x_rec.resize(r0 + gpo::kXRec, 0.0);
+    for (int k = 0; k < mlen; ++k) g->x_rec[r0 + k] = meas[(size_t)mlen * i + k];
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < m; ++q) g->x_rec[r0 + gpo::kXU + p * gpo::kXRows + q] = U[p * m + q];
+    g->x_i.push_back((int32_t)g->v_local[a]);
+    g->x_j.push_back(b >= 0 ? (int32_t)g->v_local[b] : -1);
+    g->x_kind.push_back((int8_t)(kind == GPO_E_IMU ? gpo::XK_IMU : (kind == GPO_E_BIAS_RW ? gpo::XK_BIAS_RW
+                                                                                           : gpo::XK_BIAS_PRIOR)));
+    g->x_eid.push_back((int64_t)g->ed_kind.size() + i);
+    g->x_active.push_back(1);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    g->ed_kind.push_back((int8_t)kind);
+    g->ed_local.push_back((int64_t)base + i);
+  }
+  return GPO_OK;
+}
+
 gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* vertex_ids, const double* meas,
                          const double* info, int32_t loss_kind, double loss_delta, int64_t* first_id) {
   if (!g) return GPO_ERR_ARG;
   if (g->finalized) return fail(g, GPO_ERR_STATE, "topology is frozen after the first optimize");
-  if (kind != GPO_E_BA_REPROJ) return fail(g, GPO_ERR_ARG, "unknown edge kind %d", kind);
-  if (n < 0 || (n > 0 && (!vertex_ids || !meas))) return fail(g, GPO_ERR_ARG, "null ids or measurements");
+  if (kind < GPO_E_BA_REPROJ || kind > GPO_E_BIAS_PRIOR) return fail(g, GPO_ERR_ARG, "unknown edge kind %d", kind);
+  if (n < 0 || (n > 0 && !vertex_ids)) return fail(g, GPO_ERR_ARG, "null ids or negative count");
   if (loss_kind != GPO_LOSS_NONE && loss_kind != GPO_LOSS_HUBER) return fail(g, GPO_ERR_ARG, "unknown loss %d", loss_kind);
   if (loss_kind == GPO_LOSS_HUBER && !(loss_delta > 0.0 && std::isfinite(loss_delta)))
     return fail(g, GPO_ERR_ARG, "Huber threshold must be positive and finite");
-  const int64_t V = (int64_t)g->v_kind.size();
-  const size_t base = g->e_cam.size();
-  for (int64_t i = 0; i < n; ++i) {
-    const int64_t c = vertex_ids[2 * i], p = vertex_ids[2 * i + 1];
-    if (c < 0 || c >= V || p < 0 || p >= V || g->v_kind[c] != GPO_V_BA_CAMERA9 || g->v_kind[p] != GPO_V_POINT3) {
-      g->e_cam.resize(base); g->e_pt.resize(base); g->e_obs.resize(2 * base);
-      g->e_delta.resize(base); g->e_active.resize(base); g->e_sqinfo.resize(3 * base);
-      return fail(g, GPO_ERR_ARG, "edge %lld: ids must be (camera, point)", (long long)i);
-    }
-    double u00 = 1.0, u01 = 0.0, u11 = 1.0;
-    if (info) {
-      // Omega = U^T U with U upper triangular: u00 = sqrt(a), u01 = b / u00, u11 = sqrt(d - u01^2)
-      const double a = info[4 * i], b = info[4 * i + 1], b2 = info[4 * i + 2], dd = info[4 * i + 3];
-      const double t = dd - (b / std::sqrt(a)) * (b / std::sqrt(a));
-      if (!(a > 0.0) || !(t > 0.0) || std::fabs(b - b2) > 1e-12 * (std::fabs(a) + std::fabs(dd))) {
-        g->e_cam.resize(base); g->e_pt.resize(base); g->e_obs.resize(2 * base);
-        g->e_delta.resize(base); g->e_active.resize(base); g->e_sqinfo.resize(3 * base);
-        return fail(g, GPO_ERR_ARG, "edge %lld: information matrix is not symmetric positive definite", (long long)i);
-      }
-      u00 = std::sqrt(a);
-      u01 = b / u00;
-      u11 = std::sqrt(t);
-      if (u00 != 1.0 || u01 != 0.0 || u11 != 1.0) g->any_info = true;
-    }
-    g->e_cam.push_back((int32_t)g->v_local[c]);
-    g->e_pt.push_back((int32_t)g->v_local[p]);
-    g->e_obs.push_back(meas[2 * i]);
-    g->e_obs.push_back(meas[2 * i + 1]);
-    g->e_sqinfo.push_back(u00);
-    g->e_sqinfo.push_back(u01);
-    g->e_sqinfo.push_back(u11);
-    g->e_delta.push_back(loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0);
-    g->e_active.push_back(1);
-  }
-  if (first_id) *first_id = (int64_t)base;
-  return GPO_OK;
+  const int64_t first = (int64_t)g->ed_kind.size();
+  const gpo_status s = (kind == GPO_E_BA_REPROJ || kind == GPO_E_STEREO)
+                           ? add_obs_edges(g, kind, n, vertex_ids, meas, info, loss_kind, loss_delta)
+                           : add_nav_edges(g, kind, n, vertex_ids, meas, info, loss_kind);
+  if (s == GPO_OK && first_id) *first_id = first;
+  return s;
 }
 
 gpo_status gpo_set_fixed(gpo_graph* g, int64_t vid, int32_t fixed) {
   if (!g) return GPO_ERR_ARG;
   if (g->finalized) return fail(g, GPO_ERR_STATE, "fixed flags are frozen after the first optimize");
   if (vid < 0 || vid >= (int64_t)g->v_kind.size()) return fail(g, GPO_ERR_ARG, "no vertex %lld", (long long)vid);
-  if (g->v_kind[vid] == GPO_V_BA_CAMERA9) g->cam_fixed[g->v_local[vid]] = fixed ? 1 : 0;
+  if (is_camera(g->v_kind[vid])) g->cam_fixed[g->v_local[vid]] = fixed ? 1 : 0;
   else g->pt_fixed[g->v_local[vid]] = fixed ? 1 : 0;
   return GPO_OK;
 }
@@ -718,8 +893,10 @@ gpo_status gpo_set_fixed(gpo_graph* g, int64_t vid, int32_t fixed) {
 gpo_status gpo_set_edge_active(gpo_graph* g, int64_t eid, int32_t active) {
   if (!g) return GPO_ERR_ARG;
   if (g->finalized) return fail(g, GPO_ERR_STATE, "edge activity is frozen after the first optimize");
-  if (eid < 0 || eid >= (int64_t)g->e_cam.size()) return fail(g, GPO_ERR_ARG, "no edge %lld", (long long)eid);
-  g->e_active[eid] = active ? 1 : 0;
+  if (eid < 0 || eid >= (int64_t)g->ed_kind.size()) return fail(g, GPO_ERR_ARG, "no edge %lld", (long long)eid);
+  const int k = g->ed_kind[eid];
+  if (k == GPO_E_BA_REPROJ || k == GPO_E_STEREO) g->e_active[g->ed_local[eid]] = active ? 1 : 0;
+  else g->x_active[g->ed_local[eid]] = active ? 1 : 0;
   return GPO_OK;
 }
 
@@ -747,7 +924,7 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
   const int64_t loc = g->v_local[first];
   g->cost_valid = false;
   if (!g->finalized) {
-    std::vector<double>& dst = kind == GPO_V_BA_CAMERA9 ? g->cam_state : g->pt_state;
+    std::vector<double>& dst = is_camera(kind) ? g->cam_state : g->pt_state;
     if (on_device) {
       GPO_CUDA(g, cudaMemcpy(dst.data() + loc * w, state, n * w * sizeof(double), cudaMemcpyDeviceToHost));
     } else {
@@ -756,8 +933,8 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
     return GPO_OK;
   }
   cudaStream_t st = g->stream;
-  if (kind == GPO_V_BA_CAMERA9) {
-    GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * 9, state, n * 9 * sizeof(double),
+  if (is_camera(kind)) {
+    GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * w, state, n * w * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else {
     // points live on the device in sorted order
@@ -785,14 +962,14 @@ gpo_status gpo_get_state(gpo_graph* g, int64_t first, int64_t n, double* out, in
   const int w = state_dim(kind);
   const int64_t loc = g->v_local[first];
   if (!g->finalized) {
-    const std::vector<double>& src = kind == GPO_V_BA_CAMERA9 ? g->cam_state : g->pt_state;
+    const std::vector<double>& src = is_camera(kind) ? g->cam_state : g->pt_state;
     if (on_device) GPO_CUDA(g, cudaMemcpy(out, src.data() + loc * w, n * w * sizeof(double), cudaMemcpyHostToDevice));
     else std::memcpy(out, src.data() + loc * w, n * w * sizeof(double));
     return GPO_OK;
   }
   cudaStream_t st = g->stream;
-  if (kind == GPO_V_BA_CAMERA9) {
-    GPO_CUDA(g, cudaMemcpyAsync(out, g->dev.cam + loc * 9, n * 9 * sizeof(double),
+  if (is_camera(kind)) {
+    GPO_CUDA(g, cudaMemcpyAsync(out, g->dev.cam + loc * w, n * w * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   } else {
     int32_t* idx = nullptr;
@@ -964,9 +1141,13 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);
   if (s != GPO_OK) return s;
+  const gpo::KernelSet& ks = *g->ks;
+  const int M = ks.M, DC = ks.DC, DB = ks.DB, NJ = ks.NJ;
+  const bool nav = ks.model == gpo::ModelKind::STEREO;
+  const int R = nav ? gpo::kXRows : 2, K = nav ? gpo::kXCols : 12;
   const DevBA& d = g->dev;
   double* dbg = nullptr;
-  GPO_CUDA(g, cudaMallocAsync(&dbg, std::max<size_t>(1, 2 * (size_t)d.E) * sizeof(double), g->stream));
+  GPO_CUDA(g, cudaMallocAsync(&dbg, std::max<size_t>(1, (size_t)M * d.E) * sizeof(double), g->stream));
   DevBA dd = d;
   dd.dbg_r = dbg;
   Scalars sc;
@@ -975,35 +1156,45 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
   fill_scalars(g, prm, prm.initial_damping, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
   GPO_CUDA(g, cudaMemcpyAsync(g->dev_desc, &dd, sizeof(DevBA), cudaMemcpyHostToDevice, g->stream));
-  gpo::launch_cam_prepare(g->ls, false, g->stream);
-  gpo::launch_linearize(g->ls, g->prec, true, g->stream);
+  ks.cam_prepare(g->ls, false, g->stream);
+  ks.linearize(g->ls, g->prec, true, g->stream);
   GPO_CUDA(g, cudaMemcpyAsync(g->dev_desc, &g->dev, sizeof(DevBA), cudaMemcpyHostToDevice, g->stream));
   GPO_CUDA(g, cudaGetLastError());
-  std::vector<char> rraw, jraw;
-  if ((s = fetch(g, rraw, dbg, 2 * (size_t)d.E * sizeof(double))) != GPO_OK) return s;
+  std::vector<char> rraw, jraw, xjraw, xrraw;
+  if ((s = fetch(g, rraw, dbg, (size_t)M * d.E * sizeof(double))) != GPO_OK) return s;
   if ((s = fetch(g, jraw, static_cast<const char*>(d.J), g->j_elems * jt_size(g->prec))) != GPO_OK) return s;
+  if ((s = fetch(g, xjraw, d.xe_J, (size_t)d.NX * gpo::kXJ * sizeof(double))) != GPO_OK) return s;
+  if ((s = fetch(g, xrraw, d.xe_r, (size_t)d.NX * gpo::kXRows * sizeof(double))) != GPO_OK) return s;
   GPO_CUDA(g, cudaStreamSynchronize(g->stream));
   GPO_CUDA(g, cudaFreeAsync(dbg, g->stream));
-  const size_t Eall = g->e_cam.size();
-  if (r_out) std::fill(r_out, r_out + 2 * Eall, 0.0);
-  if (J_out) std::fill(J_out, J_out + 24 * Eall, 0.0);
+  const size_t n_ids = g->ed_kind.size();
+  if (r_out) std::fill(r_out, r_out + (size_t)R * n_ids, 0.0);
+  if (J_out) std::fill(J_out, J_out + (size_t)R * K * n_ids, 0.0);
   const double* rv = reinterpret_cast<const double*>(rraw.data());
   for (int k = 0; k < d.NCH; ++k) {
     const int e0 = g->h_ch_e0[k], n = g->h_ch_e0[k + 1] - e0;
     for (int i = 0; i < n; ++i) {
-      const int64_t id = g->sorted_edge[e0 + i];
-      if (r_out) {
-        r_out[2 * id] = rv[2 * (size_t)(e0 + i)];
-        r_out[2 * id + 1] = rv[2 * (size_t)(e0 + i) + 1];
-      }
+      const int64_t id = g->e_eid[g->sorted_edge[e0 + i]];
+      if (r_out)
+        for (int a = 0; a < M; ++a) r_out[(size_t)R * id + a] = rv[(size_t)M * (e0 + i) + a];
       if (J_out) {
-        const size_t b = (size_t)(e0 + i) * gpo::kJComp;
-        for (int a = 0; a < 2; ++a) {
-          for (int j = 0; j < 9; ++j) J_out[24 * id + 12 * a + j] = read_j(jraw, b + 9 * a + j, g->prec);
-          for (int j = 0; j < 3; ++j) J_out[24 * id + 12 * a + 9 + j] = read_j(jraw, b + 18 + 3 * a + j, g->prec);
+        const size_t b = (size_t)(e0 + i) * NJ;
+        for (int a = 0; a < M; ++a) {
+          double* row = J_out + ((size_t)R * id + a) * K;
+          for (int j = 0; j < DC; ++j) row[j] = read_j(jraw, b + (size_t)DC * a + j, g->prec);
+          for (int j = 0; j < 3; ++j) row[DB + j] = read_j(jraw, b + (size_t)M * DC + 3 * a + j, g->prec);
         }
       }
     }
+  }
+  const double* xj = reinterpret_cast<const double*>(xjraw.data());
+  const double* xr = reinterpret_cast<const double*>(xrraw.data());
+  for (int t = 0; t < d.NX; ++t) {
+    const int64_t id = g->x_eid[g->x_sorted[t]];
+    if (r_out)
+      for (int a = 0; a < gpo::kXRows; ++a) r_out[(size_t)R * id + a] = xr[(size_t)gpo::kXRows * t + a];
+    if (J_out)
+      for (int k = 0; k < gpo::kXJ; ++k) J_out[(size_t)R * K * id + k] = xj[(size_t)gpo::kXJ * t + k];
   }
   return GPO_OK;
 }
@@ -1017,14 +1208,15 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
   Scalars sc;
   fill_scalars(g, prm, lambda, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
-  gpo::launch_cam_prepare(g->ls, false, g->stream);
+  g->ks->cam_prepare(g->ls, false, g->stream);
   if ((s = solve_system(g, g->ls, sc.max_it, true)) != GPO_OK) return s;
   const DevBA& d = g->dev;
+  const int DB = g->ks->DB;
   const size_t sA = at_size(g->prec);
   std::vector<char> sraw, xraw, xbraw, praw;
   if ((s = fetch(g, sraw, reinterpret_cast<const char*>(d.sc), sizeof(Scalars))) != GPO_OK) return s;
-  if ((s = fetch(g, xraw, static_cast<const char*>(d.x), 9 * (size_t)d.C * sA)) != GPO_OK) return s;
-  if ((s = fetch(g, xbraw, static_cast<const char*>(d.xbest), 9 * (size_t)d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, xraw, static_cast<const char*>(d.x), (size_t)DB * d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, xbraw, static_cast<const char*>(d.xbest), (size_t)DB * d.C * sA)) != GPO_OK) return s;
   if ((s = fetch(g, praw, static_cast<const char*>(d.dp), 3 * (size_t)d.P * sA)) != GPO_OK) return s;
   GPO_CUDA(g, cudaStreamSynchronize(g->stream));
   const Scalars* hs = reinterpret_cast<const Scalars*>(sraw.data());
@@ -1033,9 +1225,10 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
   size_t off = 0;
   for (size_t v = 0; v < g->v_kind.size(); ++v) {
     const int64_t loc = g->v_local[v];
-    if (g->v_kind[v] == GPO_V_BA_CAMERA9) {
-      for (int k = 0; k < 9; ++k) dx_out[off + k] = g->cam_fixed[loc] ? 0.0 : read_a(xs, 9 * loc + k, g->prec);
-      off += 9;
+    if (is_camera(g->v_kind[v])) {
+      for (int k = 0; k < DB; ++k)
+        dx_out[off + k] = g->cam_fixed[loc] ? 0.0 : read_a(xs, (size_t)DB * loc + k, g->prec);
+      off += DB;
     } else {
       const int np = g->pt_old2new[loc];
       for (int k = 0; k < 3; ++k) dx_out[off + k] = g->pt_fixed[loc] ? 0.0 : read_a(praw, 3 * (size_t)np + k, g->prec);
@@ -1054,27 +1247,30 @@ gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* par
   Scalars sc;
   fill_scalars(g, prm, lambda, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
-  gpo::launch_cam_prepare(g->ls, false, g->stream);
-  gpo::launch_linearize(g->ls, g->prec, true, g->stream);
-  gpo::launch_schur_prepare(g->ls, g->prec, g->stream);
+  const gpo::KernelSet& ks = *g->ks;
+  ks.cam_prepare(g->ls, false, g->stream);
+  ks.linearize(g->ls, g->prec, true, g->stream);
+  ks.schur_prepare(g->ls, g->prec, g->stream);
   GPO_CUDA(g, cudaMemsetAsync(g->ls.running, 0, sizeof(int), g->stream));
-  gpo::launch_cam_finalize(g->ls, g->prec, g->stream);
+  ks.cam_finalize(g->ls, g->prec, g->stream);
   GPO_CUDA(g, cudaGetLastError());
   const DevBA& d = g->dev;
+  const int DB = ks.DB, TB = tri(DB);
   const size_t sA = at_size(g->prec);
   std::vector<char> Sraw, graw;
-  if ((s = fetch(g, Sraw, static_cast<const char*>(d.S), 45 * (size_t)d.C * sA)) != GPO_OK) return s;
-  if ((s = fetch(g, graw, static_cast<const char*>(d.g), 9 * (size_t)d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, Sraw, static_cast<const char*>(d.S), (size_t)TB * d.C * sA)) != GPO_OK) return s;
+  if ((s = fetch(g, graw, static_cast<const char*>(d.g), (size_t)DB * d.C * sA)) != GPO_OK) return s;
   GPO_CUDA(g, cudaStreamSynchronize(g->stream));
   for (int c = 0; c < d.C; ++c) {
     if (S_out)
-      for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) {
-          const int t = i <= j ? i * 9 - (i * (i - 1)) / 2 + (j - i) : j * 9 - (j * (j - 1)) / 2 + (i - j);
-          S_out[81 * (size_t)c + 9 * i + j] = read_a(Sraw, 45 * (size_t)c + t, g->prec);
+      for (int i = 0; i < DB; ++i)
+        for (int j = 0; j < DB; ++j) {
+          const int a = std::min(i, j), b = std::max(i, j);
+          const int t = a * DB - (a * (a - 1)) / 2 + (b - a);
+          S_out[(size_t)DB * DB * c + DB * i + j] = read_a(Sraw, (size_t)TB * c + t, g->prec);
         }
     if (g_out)
-      for (int i = 0; i < 9; ++i) g_out[9 * (size_t)c + i] = read_a(graw, 9 * (size_t)c + i, g->prec);
+      for (int i = 0; i < DB; ++i) g_out[(size_t)DB * c + i] = read_a(graw, (size_t)DB * c + i, g->prec);
   }
   return GPO_OK;
 }

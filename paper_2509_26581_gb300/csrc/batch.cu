@@ -185,6 +185,8 @@ gpo_status gpo_optimize_batch(gpo_graph* const* graphs, int32_t n, int32_t max_i
       if (graphs[i] != owner) owner->err = graphs[i]->err;
       return s;
     }
+    if (graphs[i]->ks != owner->ks)
+      return fail(owner, GPO_ERR_ARG, "graphs of a batch must share the camera kind");
   }
   const gpo_lm_params prm = params_or_default(params);
   if (!(prm.initial_damping > 0.0)) return fail(owner, GPO_ERR_ARG, "initial damping must be positive");
@@ -275,6 +277,9 @@ gpo_status gpo_server_submit(gpo_server* sv, gpo_graph* g, int32_t max_iters, co
   if (g->prec != sv->owner->prec || g->desc.device != sv->owner->desc.device)
     return fail(sv->owner, GPO_ERR_ARG, "graph precision or device differs from the server's");
   if (g->finalized) return fail(sv->owner, GPO_ERR_STATE, "graph is already resident on the device");
+  const gpo::KernelSet* k = &kernels_of(g);
+  if (sv->owner->ks && sv->owner->ks != k)
+    return fail(sv->owner, GPO_ERR_ARG, "graph camera kind differs from the server's earlier graphs");
   size_t bytes = 0;
   gpo_status s = finalize(g, &bytes);
   if (s != GPO_OK) {
@@ -284,6 +289,7 @@ gpo_status gpo_server_submit(gpo_server* sv, gpo_graph* g, int32_t max_iters, co
   if (sv->desc.memory_budget && bytes > sv->desc.memory_budget)
     return fail(sv->owner, GPO_ERR_OOM, "graph needs %zu bytes, more than the server budget %zu", bytes,
                 (size_t)sv->desc.memory_budget);
+  sv->owner->ks = k;
   gpo_server::Req r{g, max_iters, params_or_default(params), sv->next_ticket++, 0, bytes, 0.0};
   sv->queue.push_back(r);
   if (ticket) *ticket = r.ticket;

@@ -9,8 +9,12 @@
 //    camera contributions per slot in a fixed order (edges pre-sorted by slot) and
 //    writes one partial per slot; a camera sums its slots' partials in chunk order.
 //    Every reduction therefore has a fixed order: runs are bit-reproducible;
-//  * Jacobians are stored edge-major, one 24-value row per edge in point-major edge
-//    order (48 / 96 / 192 bytes in BF16 / FP32 / FP64: 16-byte vector accesses).
+//  * Jacobians are stored edge-major, one row per edge in point-major edge order
+//    (BA: 24 values, 48 / 96 / 192 bytes in BF16 / FP32 / FP64; stereo: 27 values
+//    padded to 32): 16-byte vector accesses;
+//  * the edge model (BAL reprojection on 9-dim cameras, or stereo reprojection on
+//    15-dim navigation states plus inertial / bias edges between them) is a
+//    compile-time parameter of the kernels; a graph picks its kernel set at finalize.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -19,13 +23,26 @@
 namespace gpo {
 
 constexpr int kThreads = 256;       // CTA size of the chunk kernels
-constexpr int kCamDim = 9;          // BA camera tangent size
 constexpr int kPtDim = 3;
-constexpr int kJComp = 24;          // 2 x (9 + 3) Jacobian values per edge
-constexpr int kCamTri = 45;         // packed upper triangle of a 9x9 block
-constexpr int kPartA = 54;          // H_cc (45) + b_c (9)
 constexpr int kCamPerBlock = 8;     // cameras (warps) per CTA in camera kernels
 constexpr int kMaxHistory = 4096;
+
+// Edge models (the kernel set a graph runs).
+enum class ModelKind { BA = 0, STEREO = 1 };
+
+// Camera-side ("extra") edges of the navigation model: inertial (9 rows), bias random
+// walk (6 rows) between keyframes i and j, bias prior (6 rows) on keyframe i.
+enum XKind { XK_IMU = 0, XK_BIAS_RW = 1, XK_BIAS_PRIOR = 2 };
+constexpr int kXRows = 9;           // largest residual of an extra edge
+constexpr int kXCols = 30;          // two 15-dim navigation blocks
+constexpr int kXJ = kXRows * kXCols;
+// Record of an extra edge (doubles): the measurement, then the upper-triangular
+// square root U of the information matrix (Omega = U^T U), row-major kXRows x kXRows.
+//  IMU:   dR (9, row-major), dv (3), dp (3), JRg, Jvg, Jva, Jpg, Jpa (9 each), T, bg0 (3), ba0 (3)
+//  prior: bg_prior (3), ba_prior (3)
+constexpr int kImuMeas = 67;
+constexpr int kXU = 72;             // offset of U in the record
+constexpr int kXRec = kXU + kXRows * kXRows;   // 153
 
 __host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }
 
@@ -59,17 +76,23 @@ struct IterRecord {       // mirrors gpo_iter_record
   int accepted, pcg_iters;
 };
 
-// Raw device pointers of one (possibly batched) BA problem set.  Arrays marked AT
-// are of the accumulation type (double in FP64 mode, float otherwise); J is of the
-// storage type (double, float or __nv_bfloat16).
+// Raw device pointers of one problem.  Arrays marked AT are of the accumulation type
+// (double in FP64 mode, float otherwise); J is of the storage type (double, float or
+// __nv_bfloat16).  Sizes by model: SS = camera state (9 BA, 16 navigation), DB =
+// camera tangent block (9 / 15), DC = camera columns of an observation's Jacobian
+// (9 / 6), M = observation rows (2 / 3), NJ = Jacobian row (24 / 32), NPA = slot
+// partial row (54 / 27), TB = packed camera block (45 / 120).
 struct DevBA {
   int C, P, E, NCH, NS;
+  int NX;                    // extra (camera-side) edges
+  int model;                 // ModelKind
+  double camk[20];           // stereo rig: fx fy cx cy baseline, R_cb (9, row-major), t_cb (3)
   // topology (point-major edge order)
   const int* e_cam;          // [E]
   const int* e_pt;           // [E]
-  const double* obs;         // [E][2]
+  const double* obs;         // [E][M]
   const double* e_delta;     // [E] Huber threshold, <= 0: plain squares
-  const double* e_sqinfo;    // [E][3] upper Cholesky factor of Omega (u00 u01 u11) or null
+  const double* e_sqinfo;    // [E][tri(M)] packed upper Cholesky factor of Omega, or null
   const int* pt_off;         // [P+1]
   const int* ch_e0;          // [NCH+1]
   const int* ch_p0;          // [NCH+1]
@@ -84,34 +107,46 @@ struct DevBA {
   const int* cam_s_list;     // [NS] slots of each camera, chunk order
   const uint8_t* cam_fixed;  // [C]
   const uint8_t* pt_fixed;   // [P]
+  // extra edges, sorted by (first vertex, id)
+  const int* xe_i;           // [NX] first camera
+  const int* xe_j;           // [NX] second camera, -1 for a unary edge
+  const int* xe_kind;        // [NX] XKind
+  const double* xe_rec;      // [NX][kXRec]
+  const int* xo_off;         // [C+1] extra edges whose first camera is c
+  const int* xk_off;         // [C+1] extra edges touching camera c ...
+  const int* xk_list;        // [2 NX] ... as 2 x + side (side 1: c is the second camera)
+  double* xe_J;              // [NX][kXRows][kXCols] whitened Jacobian (FP64)
+  double* xe_r;              // [NX][kXRows] whitened residual
+  double* xe_cost;           // [NX] 1/2 |r|^2 at the last evaluated state
+  double* xe_md;             // [NX] -1/2 |J dx|^2
   // FP64 state
-  double* cam;               // [C][9]
-  double* cam_cand;          // [C][9]
-  double* camrb;             // [C][16] R (9) t (3) f k1 k2 pad
+  double* cam;               // [C][SS]
+  double* cam_cand;          // [C][SS]
+  double* camrb;             // [C][16] render block (BA: R t f k1 k2 pad; nav: R p pad)
   double* camrb_cand;        // [C][16]
   double* pt;                // [P][3]
   double* pt_cand;           // [P][3]
   // linear system
-  void* J;                   // JT [E][24] edge-major rows
+  void* J;                   // JT [E][NJ] edge-major rows
   void* Hpp;                 // AT [P][6] undamped point blocks
   void* bp;                  // AT [P][3]
   void* Hinv;                // AT [P][6] damped inverses
   void* dp;                  // AT [P][3] point step
-  void* partA;               // AT [NS][54]
-  void* partB;               // AT [NS][54]
-  void* partV;               // AT [NS][9]
-  void* Hcl;                 // AT [C][45] H_cc + lambda D_c
-  void* bc;                  // AT [C][9]
-  void* S;                   // AT [C][45] Schur diagonal blocks
-  void* Minv;                // AT [C][45] block-Jacobi preconditioner S_cc^-1
-  void* g;                   // AT [C][9] reduced right-hand side
-  void* x; void* r; void* z; void* p; void* p2; void* y; void* xbest;   // AT [C][9]
+  void* partA;               // AT [NS][NPA]
+  void* partB;               // AT [NS][NPA]
+  void* partV;               // AT [NS][DC]
+  void* Hcl;                 // AT [C][TB] H_cc + lambda D_c
+  void* bc;                  // AT [C][DB]
+  void* S;                   // AT [C][TB] Schur diagonal blocks
+  void* Minv;                // AT [C][TB] block-Jacobi preconditioner S_cc^-1
+  void* g;                   // AT [C][DB] reduced right-hand side
+  void* x; void* r; void* z; void* p; void* p2; void* y; void* xbest;   // AT [C][DB]
   double* cost_part;         // [NCH]
   double* md_part;           // [NCH]
   double* cblk_part;         // [ncblk][2]
   Scalars* sc;               // [1]
   IterRecord* hist;          // [kMaxHistory]
-  double* dbg_r;             // optional [E][2] weighted residual output
+  double* dbg_r;             // optional [E][M] weighted residual output
   int ch_max;                // max edges per chunk
   int ns_max, np_max;        // max slots / points of a chunk
   int ncblk;                 // CTAs of the camera kernels
@@ -137,22 +172,29 @@ struct LaunchSet {
   int ns_max, np_max;    // most slots / points in one chunk over the problems
 };
 
-// Kernel launchers (ba_kernels.cu).  All are asynchronous on `st`.
-int launch_cam_prepare(const LaunchSet& ls, bool candidate, cudaStream_t st);
-int launch_cost(const LaunchSet& ls, bool candidate, cudaStream_t st);
-int launch_cost_init(const LaunchSet& ls, cudaStream_t st);
-int launch_linearize(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st);
-int launch_schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st);
-int launch_cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st);
-int launch_pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st);      // the Schur product (hot loop)
-int launch_cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st);     // y = S p camera side, alpha
-int launch_pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st);    // x, r, z; stopping rules, beta
-int launch_backsub(const LaunchSet& ls, Prec pr, cudaStream_t st);
-int launch_retract(const LaunchSet& ls, Prec pr, cudaStream_t st);
-int launch_decide(const LaunchSet& ls, Prec pr, cudaStream_t st);
-int launch_commit(const LaunchSet& ls, cudaStream_t st);
-size_t smem_bytes_linearize(Prec pr, int ch_max);
-int default_ch_max(Prec pr);
-int max_supported_ch(Prec pr);
+// Kernel set of one edge model.  Every launcher is asynchronous on `st` and returns
+// the number of kernels it launched.
+struct KernelSet {
+  ModelKind model;
+  int SS, DB, DC, M, NJ, NPA;     // sizes (see DevBA)
+  int (*cam_prepare)(const LaunchSet& ls, bool candidate, cudaStream_t st);
+  int (*cost)(const LaunchSet& ls, bool candidate, cudaStream_t st);
+  int (*cost_init)(const LaunchSet& ls, cudaStream_t st);
+  int (*linearize)(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st);
+  int (*schur_prepare)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*cam_finalize)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*pcg_spmv)(const LaunchSet& ls, Prec pr, cudaStream_t st);     // the Schur product (hot loop)
+  int (*cam_apply)(const LaunchSet& ls, Prec pr, cudaStream_t st);    // y = S p camera side, alpha
+  int (*pcg_update)(const LaunchSet& ls, Prec pr, cudaStream_t st);   // x, r, z; stopping rules, beta
+  int (*backsub)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*retract)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*decide)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*commit)(const LaunchSet& ls, cudaStream_t st);
+  int (*max_supported_ch)(Prec pr);
+};
+const KernelSet& kernels_ba();       // ba_kernels.cu
+const KernelSet& kernels_stereo();   // vi_kernels.cu
+inline const KernelSet& kernels_for(ModelKind m) { return m == ModelKind::STEREO ? kernels_stereo() : kernels_ba(); }
+inline int default_ch_max(Prec) { return 512; }
 
 }  // namespace gpo

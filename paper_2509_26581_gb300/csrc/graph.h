@@ -45,25 +45,41 @@ struct gpo_graph {
   bool own_stream = false;
   std::string err;
 
-  // vertices: global id -> (kind, index within kind)
+  // vertices: global id -> (kind, index within kind).  A graph holds one camera kind
+  // (BA cameras or navigation states) besides points.
+  int cam_kind = -1;
   std::vector<int8_t> v_kind;
   std::vector<int64_t> v_local;
-  std::vector<double> cam_state;   // [C][9] (host copy until finalize)
+  std::vector<double> cam_state;   // [C][SS] (host copy until finalize)
   std::vector<double> pt_state;    // [P][3]
   std::vector<uint8_t> cam_fixed, pt_fixed;
 
-  // BA edges (global edge id = index)
+  // edges: global id -> (kind, index within the kind's table)
+  std::vector<int8_t> ed_kind;
+  std::vector<int64_t> ed_local;
+  // observation edges (BA reprojection or stereo reprojection), M rows each
   std::vector<int32_t> e_cam, e_pt;
-  std::vector<double> e_obs;       // [E][2]
-  std::vector<double> e_sqinfo;    // [E][3] upper Cholesky factor, identity if no info
+  std::vector<int64_t> e_eid;      // edge id
+  std::vector<double> e_obs;       // [E][M]
+  std::vector<double> e_sqinfo;    // [E][tri(M)] packed upper Cholesky factor (identity if no info)
   std::vector<double> e_delta;     // [E]
   std::vector<uint8_t> e_active;
   bool any_info = false;
+  // camera-side edges (inertial, bias random walk, bias prior)
+  std::vector<int32_t> x_i, x_j;
+  std::vector<int8_t> x_kind;
+  std::vector<int64_t> x_eid;
+  std::vector<double> x_rec;       // [NX][kXRec]
+  std::vector<uint8_t> x_active;
+  double camk[20] = {};            // stereo rig
+  bool camk_set = false;
 
   // finalized topology
   bool finalized = false;
+  const gpo::KernelSet* ks = nullptr;
   int ch_max = 0;
-  std::vector<int64_t> sorted_edge;   // sorted position -> edge id
+  std::vector<int64_t> sorted_edge;   // sorted position -> observation edge index
+  std::vector<int32_t> x_sorted;      // sorted position -> camera-side edge index
   std::vector<int32_t> pt_new2old, pt_old2new;
   std::vector<int32_t> h_ch_e0;
   size_t j_elems = 0;
@@ -87,6 +103,13 @@ struct gpo_graph {
 
 
 namespace gpo_host {
+
+// Camera state and tangent sizes of the graph's camera kind.
+inline int cam_ss(const gpo_graph* g) { return g->cam_kind == GPO_V_NAV15 ? 16 : 9; }
+inline int cam_db(const gpo_graph* g) { return g->cam_kind == GPO_V_NAV15 ? 15 : 9; }
+inline const gpo::KernelSet& kernels_of(const gpo_graph* g) {
+  return gpo::kernels_for(g->cam_kind == GPO_V_NAV15 ? gpo::ModelKind::STEREO : gpo::ModelKind::BA);
+}
 
 gpo_status fail(gpo_graph* g, gpo_status st, const char* fmt, ...);
 gpo_status finalize(gpo_graph* g, size_t* plan_bytes = nullptr);

@@ -1,0 +1,1425 @@
+// Schur-complement Levenberg-Marquardt kernels on sm_103a, generic over the edge
+// model: observation-edge linearisation, point and camera accumulation, the camera
+// Schur complement, matrix-free block-Jacobi PCG, point back-substitution, FP64
+// retraction, cost and the LM gain-ratio decision.
+//
+// Paper mapping: Eq. 1 and Eq. 7 (cost with Huber), Eq. 3-6 (LM normal equations),
+// Sec. IV-B (analytic Jacobians), Sec. IV-E (PCG on implicit products of the
+// Jacobians, block-Jacobi preconditioner kept at FP32 or higher, Hessian-diagonal
+// clamping, residual normalisation), Sec. IV-E last paragraph (kernels walk the
+// graph structure; no sparse-matrix format).  The PCG runs on the camera Schur
+// complement S = H_cc + lambda D_c - H_cp H_pp^-1 H_pc; its product with a vector is
+// formed from the stored Jacobians in one pass per chunk of point-major edges.
+//
+// A model (schur_common.cuh) fixes M observation rows, DC camera columns of an
+// observation's Jacobian (the first DC dimensions of the DB-dimensional camera
+// block) and NJ stored values per edge.  Models with camera-side edges (kExtra:
+// inertial and bias edges of the navigation model) add their diagonal blocks and
+// gradients in the camera finalisation and their off-diagonal products in the
+// camera half of the Schur product; their linearisation, cost and model-decrease
+// kernels live with the model (vi_kernels.cu).
+#pragma once
+#include "schur_common.cuh"
+
+namespace gpo {
+
+// Packed upper triangles of 9x9 and 6x6 blocks: entry t is (row[t], col[t]).
+static __constant__ unsigned char c_t9i[45] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1,
+                                               2, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4,
+                                               4, 5, 5, 5, 5, 6, 6, 6, 7, 7, 8};
+static __constant__ unsigned char c_t9j[45] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 1, 2, 3, 4, 5, 6, 7, 8,
+                                               2, 3, 4, 5, 6, 7, 8, 3, 4, 5, 6, 7, 8, 4, 5, 6, 7,
+                                               8, 5, 6, 7, 8, 6, 7, 8, 7, 8, 8};
+static __constant__ unsigned char c_t6i[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+static __constant__ unsigned char c_t6j[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+
+template <int N>
+__device__ __forceinline__ int tri_row(int t) {
+  static_assert(N == 9 || N == 6, "no table for this block size");
+  if constexpr (N == 9) return c_t9i[t];
+  else return c_t6i[t];
+}
+template <int N>
+__device__ __forceinline__ int tri_col(int t) {
+  if constexpr (N == 9) return c_t9j[t];
+  else return c_t6j[t];
+}
+
+template <class Mo>
+struct Dims {
+  static constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, SS = Mo::SS, NJ = Mo::NJ;
+  static constexpr int JP0 = M * DC;            // first point-row value of a Jacobian row
+  static constexpr int NJU = JP0 + 3 * M;       // values in use (the rest is padding)
+  static constexpr int TC = tri_n(DC);          // H entries of a slot partial
+  static constexpr int NA = TC + DC;            // H + b entries of a slot partial
+  static constexpr int NG = (NA + 8) / 9;       // groups of nine
+  static constexpr int NPA = 9 * NG;            // slot partial row
+  static constexpr int TB = tri_n(DB);          // packed camera block
+  static constexpr int TM = tri_n(M);           // packed M x M point-side weights
+  static constexpr int VW = DC > 3 ? DC : 3;    // rows of the Schur-product scratch
+  static_assert(NJ % 8 == 0 && NJU <= NJ, "Jacobian rows are whole 16-byte vectors");
+  static_assert(DB <= 32, "one lane per camera-block component");
+};
+
+// ---------------------------------------------------------------- small dense helpers
+
+// 3x3 SPD inverse by cofactors; h = (a b c d e f) packed upper triangle.
+template <class AT>
+__device__ __forceinline__ void inv3(const AT* h, AT* o) {
+  const AT a = h[0], b = h[1], c = h[2], dd = h[3], e = h[4], f = h[5];
+  const AT A = dd * f - e * e, B = c * e - b * f, C = b * e - c * dd;
+  const AT D = a * f - c * c, E = b * c - a * e, F = a * dd - b * b;
+  const AT det = a * A + b * B + c * C;
+  if (det > (AT)0 && isfinite(det)) {
+    const AT id = (AT)1 / det;
+    o[0] = A * id; o[1] = B * id; o[2] = C * id; o[3] = D * id; o[4] = E * id; o[5] = F * id;
+  } else {  // not positive definite in this precision: Jacobi fallback
+    o[0] = a > (AT)0 ? (AT)1 / a : (AT)0;
+    o[3] = dd > (AT)0 ? (AT)1 / dd : (AT)0;
+    o[5] = f > (AT)0 ? (AT)1 / f : (AT)0;
+    o[1] = o[2] = o[4] = (AT)0;
+  }
+}
+
+template <class AT>
+__device__ __forceinline__ void mul3(const AT* h, const AT* v, AT* o) {
+  o[0] = h[0] * v[0] + h[1] * v[1] + h[2] * v[2];
+  o[1] = h[1] * v[0] + h[3] * v[1] + h[4] * v[2];
+  o[2] = h[2] * v[0] + h[4] * v[1] + h[5] * v[2];
+}
+
+template <class AT>
+__device__ __forceinline__ AT damp_diag(AT h, const Scalars* sc) {
+  if (sc->damping_mode == 1) return (AT)1;
+  return fmin(fmax(h, (AT)sc->diag_min), (AT)sc->diag_max);
+}
+
+// Inverse of an N x N SPD block by one warp, lane i holding row i (N <= 32): the block
+// is first scaled to unit diagonal (A' = D^-1/2 A D^-1/2, which removes the spread of
+// scales between rotation, translation, intrinsics or bias coordinates), then
+// Gauss-Jordan elimination without pivoting runs on [A' | I] (stable for SPD matrices:
+// each pivot is a Schur-complement diagonal, positive exactly when A is positive
+// definite).  M = D^-1/2 A'^-1 D^-1/2, written as the packed upper triangle.  If A is
+// not positive definite in this precision, M = diag(1 / A_ii) (Jacobi; 1 where
+// A_ii <= 0).  A is a full row-major N x N block in shared memory; every lane calls.
+template <int N, class AT>
+__device__ void warp_spd_inverse(const AT* A, AT* M, int lane) {
+  const unsigned full = 0xffffffffu;
+  const AT dii = lane < N ? A[lane * N + lane] : (AT)1;
+  const bool pos = __all_sync(full, dii > (AT)0);
+  const AT sc = pos ? (AT)1 / sqrt(dii) : (AT)0;
+  AT a[N], b[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const AT sj = __shfl_sync(full, sc, j);
+    a[j] = lane < N ? A[lane * N + j] * sc * sj : (AT)0;
+    b[j] = lane == j ? (AT)1 : (AT)0;
+  }
+  bool ok = pos;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const AT pk = __shfl_sync(full, a[k], k);
+    ok = ok && pk > (AT)0;
+    const AT inv = ok ? (AT)1 / pk : (AT)0;
+    const AT f = a[k];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const AT akj = __shfl_sync(full, a[j], k) * inv;
+      const AT bkj = __shfl_sync(full, b[j], k) * inv;
+      if (lane == k) {
+        a[j] = akj;
+        b[j] = bkj;
+      } else {
+        a[j] -= f * akj;
+        b[j] -= f * bkj;
+      }
+    }
+  }
+  if (ok) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const AT sj = __shfl_sync(full, sc, j);
+      if (lane < N && j >= lane) M[tri_idx(N, lane, j)] = sc * b[j] * sj;
+    }
+  } else if (lane < N) {
+    for (int j = lane; j < N; ++j) M[tri_idx(N, lane, j)] = (AT)0;
+    M[tri_idx(N, lane, lane)] = dii > (AT)0 ? (AT)1 / dii : (AT)1;
+  }
+}
+
+__device__ __forceinline__ int xrows(int kind) { return kind == XK_IMU ? 9 : 6; }
+
+// ---------------------------------------------------------------- camera render blocks
+
+template <class Mo>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_prepare(LaunchSet ls, int candidate) {
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active) return;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C || (threadIdx.x & 31) != 0) return;
+  const double* cam = (candidate ? d.cam_cand : d.cam) + Mo::SS * (size_t)c;
+  double* rb = (candidate ? d.camrb_cand : d.camrb) + 16 * (size_t)c;
+  Mo::render(d, cam, rb);
+}
+
+// ---------------------------------------------------------------- cost F(x)
+
+template <class Mo>
+__global__ void __launch_bounds__(kThreads) k_cost(LaunchSet ls, int candidate) {
+  __shared__ double red[kThreads];
+  GPO_BIND(ch, kl)
+  if (!d.sc->active) return;
+  const ChunkRange cr = chunk_range(d, kl);
+  const double* rbs = candidate ? d.camrb_cand : d.camrb;
+  const double* pts = candidate ? d.pt_cand : d.pt;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int e = cr.e0 + i;
+    double rb[16];
+    load_rb(rbs + 16 * (size_t)__ldg(d.e_cam + e), rb);
+    const double* Xp = pts + 3 * (size_t)__ldg(d.e_pt + e);
+    const double X[3] = {Xp[0], Xp[1], Xp[2]};
+    acc += Mo::cost(d, e, rb, X);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) d.cost_part[kl] = s;
+}
+
+template <class Mo>
+__global__ void k_cost_init(LaunchSet ls) {
+  __shared__ double red[kThreads];
+  __shared__ DevBA d;
+  pdl_trigger();
+  bind_problem(d, ls.probs + blockIdx.x);
+  pdl_wait();
+  if (!d.sc->active) return;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < d.NCH; k += kThreads) acc += d.cost_part[k];
+  if constexpr (Mo::kExtra)
+    for (int x = threadIdx.x; x < d.NX; x += kThreads) acc += d.xe_cost[x];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) d.sc->cost = s;
+}
+
+// ---------------------------------------------------------------- linearisation
+
+// One CTA per chunk.  Writes the chunk's Jacobian rows, the undamped point blocks
+// H_pp = sum Jp^T Jp and gradients b_p, and per-slot camera partials
+// (H_cc = sum Jc^T Jc, b_c = sum Jc^T r).  H uses the stored (rounded) Jacobian; the
+// gradient uses the unrounded one, so BF16 storage leaves the LM fixed point intact.
+template <class Mo, class JT>
+__global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force) {
+  using AT = typename AccOf<JT>::T;
+  using Dm = Dims<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, NJU = Dm::NJU;
+  constexpr int TC = Dm::TC, NG = Dm::NG, NPA = Dm::NPA;
+  constexpr bool kSplit = !std::is_same<JT, AT>::value;
+  GPO_BIND(ch, kl)
+  if (!d.sc->active || (!force && !d.sc->need_lin)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  JT* Js = reinterpret_cast<JT*>(smem);               // [NJU][CH]
+  AT* rs = reinterpret_cast<AT*>(Js + NJU * CH);      // [M][CH]
+  AT* bce = rs + M * CH;                              // [DC][CH]  (kSplit only)
+  AT* bpe = bce + DC * CH;                            // [3][CH]   (kSplit only)
+  uint16_t* srt = reinterpret_cast<uint16_t*>(kSplit ? bpe + 3 * CH : bce);   // [CH]
+  const ChunkRange cr = chunk_range(d, kl);
+  JT* Jg = reinterpret_cast<JT*>(d.J) + (size_t)cr.e0 * NJ;
+
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int e = cr.e0 + i;
+    const int c = __ldg(d.e_cam + e), p = __ldg(d.e_pt + e);
+    double rb[16];
+    load_rb(d.camrb + 16 * (size_t)c, rb);
+    const double X[3] = {d.pt[3 * (size_t)p], d.pt[3 * (size_t)p + 1], d.pt[3 * (size_t)p + 2]};
+    double r[M], rho, sw;
+    AT Jc[M][DC], Jp[M][3];
+    Mo::template eval<AT>(d, e, rb, X, r, rho, sw, Jc, Jp);
+    if (d.cam_fixed[c]) {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int k = 0; k < DC; ++k) Jc[a][k] = (AT)0;
+    }
+    if (d.pt_fixed[p]) {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Jp[a][k] = (AT)0;
+    }
+    AT rw[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) rw[a] = (AT)(sw * r[a]);
+    __align__(16) JT row[NJ];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+#pragma unroll
+      for (int k = 0; k < DC; ++k) row[a * DC + k] = cvj(Jc[a][k], (const JT*)nullptr);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) row[JP0 + 3 * a + k] = cvj(Jp[a][k], (const JT*)nullptr);
+    }
+#pragma unroll
+    for (int k = NJU; k < NJ; ++k) row[k] = cvj((AT)0, (const JT*)nullptr);
+    store_row<NJ>(Jg + (size_t)i * NJ, row);
+#pragma unroll
+    for (int k = 0; k < NJU; ++k) Js[k * CH + i] = row[k];
+    srt[i] = d.ch_sorted[e];
+#pragma unroll
+    for (int a = 0; a < M; ++a) rs[a * CH + i] = rw[a];
+    if constexpr (kSplit) {
+#pragma unroll
+      for (int k = 0; k < DC; ++k) {
+        AT s = Jc[0][k] * rw[0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) s += Jc[a][k] * rw[a];
+        bce[k * CH + i] = s;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        AT s = Jp[0][k] * rw[0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) s += Jp[a][k] * rw[a];
+        bpe[k * CH + i] = s;
+      }
+    }
+    if (d.dbg_r) {
+#pragma unroll
+      for (int a = 0; a < M; ++a) d.dbg_r[M * (size_t)e + a] = sw * r[a];
+    }
+  }
+  __syncthreads();
+
+  // point blocks
+  AT* Hpp = reinterpret_cast<AT*>(d.Hpp);
+  AT* bp = reinterpret_cast<AT*>(d.bp);
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    const int a0 = d.pt_off[pj] - cr.e0, b0 = d.pt_off[pj + 1] - cr.e0;
+    AT h[6] = {0, 0, 0, 0, 0, 0}, bb[3] = {0, 0, 0};
+    for (int i = a0; i < b0; ++i) {
+      AT Jq[M][3];
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Jq[a][k] = ldj(Js + (JP0 + 3 * a + k) * CH + i);
+      AT hs[6];
+      hs[0] = Jq[0][0] * Jq[0][0]; hs[1] = Jq[0][0] * Jq[0][1]; hs[2] = Jq[0][0] * Jq[0][2];
+      hs[3] = Jq[0][1] * Jq[0][1]; hs[4] = Jq[0][1] * Jq[0][2]; hs[5] = Jq[0][2] * Jq[0][2];
+#pragma unroll
+      for (int a = 1; a < M; ++a) {
+        hs[0] += Jq[a][0] * Jq[a][0]; hs[1] += Jq[a][0] * Jq[a][1]; hs[2] += Jq[a][0] * Jq[a][2];
+        hs[3] += Jq[a][1] * Jq[a][1]; hs[4] += Jq[a][1] * Jq[a][2]; hs[5] += Jq[a][2] * Jq[a][2];
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) h[k] += hs[k];
+      if constexpr (kSplit) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) bb[k] += bpe[k * CH + i];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          AT s = Jq[0][k] * rs[i];
+#pragma unroll
+          for (int a = 1; a < M; ++a) s += Jq[a][k] * rs[a * CH + i];
+          bb[k] += s;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Hpp[6 * (size_t)pj + k] = h[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bp[3 * (size_t)pj + k] = bb[k];
+  }
+
+  // camera slots: NG groups of nine outputs (H_cc entries, then b_c)
+  AT* partA = reinterpret_cast<AT*>(d.partA);
+  for (int w = threadIdx.x; w < cr.nS * NG; w += kThreads) {
+    const int sl = w / NG, grp = w - sl * NG;
+    const int qa = d.slot_e0[cr.s0 + sl], qb = d.slot_e0[cr.s0 + sl + 1];
+    const int t0 = 9 * grp;
+    AT acc[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
+    int ti[9], tj[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) {
+      const int t = t0 + o;
+      ti[o] = t < TC ? tri_row<DC>(t) : 0;
+      tj[o] = t < TC ? tri_col<DC>(t) : 0;
+    }
+    for (int q = qa; q < qb; ++q) {
+      const int i = srt[q - cr.e0];
+#pragma unroll
+      for (int o = 0; o < 9; ++o) {
+        const int t = t0 + o;
+        if (t < TC) {
+          AT s = ldj(Js + ti[o] * CH + i) * ldj(Js + tj[o] * CH + i);
+#pragma unroll
+          for (int a = 1; a < M; ++a) s += ldj(Js + (a * DC + ti[o]) * CH + i) * ldj(Js + (a * DC + tj[o]) * CH + i);
+          acc[o] += s;
+        } else if (t < TC + DC) {
+          const int k = t - TC;
+          if constexpr (kSplit) {
+            acc[o] += bce[k * CH + i];
+          } else {
+            AT s = ldj(Js + k * CH + i) * rs[i];
+#pragma unroll
+            for (int a = 1; a < M; ++a) s += ldj(Js + (a * DC + k) * CH + i) * rs[a * CH + i];
+            acc[o] += s;
+          }
+        }
+      }
+    }
+    AT* out = partA + (size_t)d.slot_pos[cr.s0 + sl] * NPA + t0;
+#pragma unroll
+    for (int o = 0; o < 9; ++o) out[o] = acc[o];
+  }
+}
+
+// ---------------------------------------------------------------- Schur preparation
+
+// One CTA per chunk: damped point inverses H_pp^-1 and per-slot partials of
+// sum_e W_e H_pp^-1 W_e^T (= Jc^T (Jp Hinv Jp^T) Jc) and sum_e W_e H_pp^-1 b_p.
+template <class Mo, class JT>
+__global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
+  using AT = typename AccOf<JT>::T;
+  using Dm = Dims<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0;
+  constexpr int TC = Dm::TC, NG = Dm::NG, NPA = Dm::NPA, TM = Dm::TM;
+  GPO_BIND(ch, kl)
+  if (!d.sc->active) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  JT* Jcs = reinterpret_cast<JT*>(smem);              // [M DC][CH]
+  AT* Ae = reinterpret_cast<AT*>(Jcs + JP0 * CH);     // [TM][CH]  Jp H_pp^-1 Jp^T (packed)
+  AT* qe = Ae + TM * CH;                              // [M][CH]   Jp H_pp^-1 b_p
+  uint16_t* srt = reinterpret_cast<uint16_t*>(qe + M * CH);   // [CH]
+  const ChunkRange cr = chunk_range(d, kl);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
+  const Scalars* sc = d.sc;
+  const AT lam = (AT)sc->lambda;
+  const AT* Hpp = reinterpret_cast<const AT*>(d.Hpp);
+  const AT* bp = reinterpret_cast<const AT*>(d.bp);
+  AT* Hinv = reinterpret_cast<AT*>(d.Hinv);
+
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    AT h[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = Hpp[6 * (size_t)pj + k];
+    h[0] += lam * damp_diag(h[0], sc);
+    h[3] += lam * damp_diag(h[3], sc);
+    h[5] += lam * damp_diag(h[5], sc);
+    AT o[6];
+    inv3(h, o);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Hinv[6 * (size_t)pj + k] = o[k];
+  }
+  __syncthreads();
+
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int pj = __ldg(d.e_pt + cr.e0 + i);
+    AT hi[6], bb[3], hb[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bb[k] = bp[3 * (size_t)pj + k];
+    mul3(hi, bb, hb);
+    AT row[NJ];
+    load_row<NJ>(Jg + (size_t)i * NJ, row);
+#pragma unroll
+    for (int k = 0; k < JP0; ++k) Jcs[k * CH + i] = cvj(row[k], (const JT*)nullptr);
+    srt[i] = d.ch_sorted[cr.e0 + i];
+    AT t[M][3];
+#pragma unroll
+    for (int a = 0; a < M; ++a) mul3(hi, row + JP0 + 3 * a, t[a]);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const AT* Ja = row + JP0 + 3 * a;
+#pragma unroll
+      for (int b = a; b < M; ++b) Ae[tri_idx(M, a, b) * CH + i] = Ja[0] * t[b][0] + Ja[1] * t[b][1] + Ja[2] * t[b][2];
+      qe[a * CH + i] = Ja[0] * hb[0] + Ja[1] * hb[1] + Ja[2] * hb[2];
+    }
+  }
+  __syncthreads();
+
+  AT* partB = reinterpret_cast<AT*>(d.partB);
+  for (int w = threadIdx.x; w < cr.nS * NG; w += kThreads) {
+    const int sl = w / NG, grp = w - sl * NG;
+    const int qa = d.slot_e0[cr.s0 + sl], qb = d.slot_e0[cr.s0 + sl + 1];
+    const int t0 = 9 * grp;
+    AT acc[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
+    int ti[9], tj[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) {
+      const int t = t0 + o;
+      ti[o] = t < TC ? tri_row<DC>(t) : 0;
+      tj[o] = t < TC ? tri_col<DC>(t) : 0;
+    }
+    for (int q = qa; q < qb; ++q) {
+      const int i = srt[q - cr.e0];
+      AT A[M][M];
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = a; b < M; ++b) A[a][b] = A[b][a] = Ae[tri_idx(M, a, b) * CH + i];
+#pragma unroll
+      for (int o = 0; o < 9; ++o) {
+        const int t = t0 + o;
+        if (t < TC) {
+          AT ci[M], cj[M];
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            ci[a] = ldj(Jcs + (a * DC + ti[o]) * CH + i);
+            cj[a] = ldj(Jcs + (a * DC + tj[o]) * CH + i);
+          }
+          AT s = (AT)0;
+#pragma unroll
+          for (int a = 0; a < M; ++a) {
+            AT u = A[a][0] * cj[0];
+#pragma unroll
+            for (int b = 1; b < M; ++b) u += A[a][b] * cj[b];
+            s += ci[a] * u;
+          }
+          acc[o] += s;
+        } else if (t < TC + DC) {
+          const int k = t - TC;
+          AT s = ldj(Jcs + k * CH + i) * qe[i];
+#pragma unroll
+          for (int a = 1; a < M; ++a) s += ldj(Jcs + (a * DC + k) * CH + i) * qe[a * CH + i];
+          acc[o] += s;
+        }
+      }
+    }
+    AT* out = partB + (size_t)d.slot_pos[cr.s0 + sl] * NPA + t0;
+#pragma unroll
+    for (int o = 0; o < 9; ++o) out[o] = acc[o];
+  }
+}
+
+// ---------------------------------------------------------------- camera blocks + PCG start
+
+// One warp per camera: reduces the slot partials into H_cc, b_c and the Schur
+// terms, adds the camera-side edges' blocks, forms H_cc + lambda D_c, S_cc, g_c and
+// M_c = S_cc^-1, and starts the PCG (x = 0, r = g, z = M g, p = z).  The last CTA
+// reduces r^T z and |r|^2.
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls) {
+  using Dm = Dims<Mo>;
+  constexpr int DB = Mo::DB, DC = Mo::DC, TC = Dm::TC, TB = Dm::TB, NG = Dm::NG, NPA = Dm::NPA;
+  constexpr int NHX = Mo::kExtra ? TB + DB : 1;
+  __shared__ AT vals[kCamPerBlock][2 * NPA];
+  __shared__ AT hx[kCamPerBlock][NHX];
+  __shared__ AT Sf[kCamPerBlock][DB * DB];
+  __shared__ double red[kCamPerBlock][2];
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + warp;
+  Scalars* sc = d.sc;
+  const AT lam = (AT)sc->lambda;
+  const AT* partA = reinterpret_cast<const AT*>(d.partA);
+  const AT* partB = reinterpret_cast<const AT*>(d.partB);
+  double rz_c = 0.0, rr_c = 0.0;
+  if (c < d.C) {
+    const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
+    // 2 NG groups of nine outputs; lanes stride over the camera's slots, then a fixed
+    // shuffle tree sums the lanes
+    for (int grp = 0; grp < 2 * NG; ++grp) {
+      const AT* base = (grp < NG ? partA : partB) + 9 * (grp % NG);
+      AT acc[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] = (AT)0;
+      for (int s = sa + lane; s < sb; s += 32) {
+        const AT* src = base + (size_t)s * NPA;   // camera-major rows
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] += src[k];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) vals[warp][9 * grp + k] = acc[k];
+      }
+    }
+    if constexpr (Mo::kExtra) {
+      // diagonal blocks J_c^T J_c and gradients J_c^T r of the camera-side edges
+      // touching c, in edge order (FP64 products, one rounding per edge)
+      const int xa = d.xk_off[c], xb = d.xk_off[c + 1];
+      for (int t = lane; t < TB + DB; t += 32) {
+        int ti = 0, tj = 0;
+        if (t < TB) tri_ij(DB, t, ti, tj);
+        AT acc = (AT)0;
+        for (int u = xa; u < xb; ++u) {
+          const int code = d.xk_list[u], x = code >> 1, off = (code & 1) * DB;
+          const double* J = d.xe_J + (size_t)x * kXJ;
+          const int m = xrows(d.xe_kind[x]);
+          double s = 0.0;
+          if (t < TB) {
+            for (int a = 0; a < m; ++a) s += J[a * kXCols + off + ti] * J[a * kXCols + off + tj];
+          } else {
+            const double* rx = d.xe_r + (size_t)x * kXRows;
+            for (int a = 0; a < m; ++a) s += J[a * kXCols + off + (t - TB)] * rx[a];
+          }
+          acc += (AT)s;
+        }
+        hx[warp][t] = acc;
+      }
+    }
+    __syncwarp();
+    AT* Hcl = reinterpret_cast<AT*>(d.Hcl) + (size_t)c * TB;
+    AT* S = reinterpret_cast<AT*>(d.S) + (size_t)c * TB;
+    AT* Mi = reinterpret_cast<AT*>(d.Minv) + (size_t)c * TB;
+    // H_cc + lambda D_c and S_cc, entry by entry: the slot partials fill the first DC
+    // coordinates of the block, the camera-side edges all of it
+    for (int t = lane; t < TB; t += 32) {
+      int ti, tj;
+      tri_ij(DB, t, ti, tj);
+      const bool obs = ti < DC && tj < DC;
+      const int tc = obs ? tri_idx(DC, ti, tj) : 0;
+      AT h = (AT)0;
+      if constexpr (Mo::kExtra) h = hx[warp][t];
+      if (obs) h += vals[warp][tc];
+      if (ti == tj) h += lam * damp_diag(h, sc);
+      Hcl[t] = h;
+      if (obs) h -= vals[warp][NPA + tc];
+      S[t] = h;
+      Sf[warp][ti * DB + tj] = h;
+      Sf[warp][tj * DB + ti] = h;
+    }
+    __syncwarp();
+    warp_spd_inverse<DB>(Sf[warp], Mi, lane);
+    __syncwarp();
+    AT* g = reinterpret_cast<AT*>(d.g) + DB * (size_t)c;
+    AT* bc = reinterpret_cast<AT*>(d.bc) + DB * (size_t)c;
+    if (lane < DB) {
+      AT bi = (AT)0, si = (AT)0;
+      if (lane < DC) {
+        bi = vals[warp][TC + lane];
+        si = vals[warp][NPA + TC + lane];
+      }
+      if constexpr (Mo::kExtra) bi += hx[warp][TB + lane];
+      const AT gi = -bi + si;
+      g[lane] = gi;
+      bc[lane] = bi;
+      reinterpret_cast<AT*>(d.x)[DB * (size_t)c + lane] = (AT)0;
+      reinterpret_cast<AT*>(d.xbest)[DB * (size_t)c + lane] = (AT)0;
+      reinterpret_cast<AT*>(d.r)[DB * (size_t)c + lane] = gi;
+    }
+    __syncwarp();
+    if (lane < DB) {
+      AT zi = (AT)0;
+      for (int j = 0; j < DB; ++j) zi += Mi[sym_idx(DB, lane, j)] * g[j];
+      reinterpret_cast<AT*>(d.z)[DB * (size_t)c + lane] = zi;
+      reinterpret_cast<AT*>(d.p)[DB * (size_t)c + lane] = (AT)0;   // p_{-1}: p_0 = z_0
+      const AT gi = g[lane];
+      rz_c = (double)gi * (double)zi;
+      rr_c = (double)gi * (double)gi;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rz_c += __shfl_down_sync(0xffffffffu, rz_c, o);
+    rr_c += __shfl_down_sync(0xffffffffu, rr_c, o);
+  }
+  if (lane == 0) {
+    red[warp][0] = rz_c;
+    red[warp][1] = rr_c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kCamPerBlock; ++w) { a += red[w][0]; b += red[w][1]; }
+    d.cblk_part[2 * cbl] = a;
+    d.cblk_part[2 * cbl + 1] = b;
+  }
+  if (!last_cta(&sc->ticket, d.ncblk)) return;
+  double rz, rr;
+  sum_partials(d.cblk_part, d.ncblk, rz, rr);
+  if (threadIdx.x == 0) {
+    const double gn = sqrt(rr);
+    sc->rz = rz;
+    sc->gnorm = gn;
+    sc->rnorm = gn;
+    sc->rmin = gn;
+    sc->sigma = 1.0;
+    sc->inv_n = 1.0;
+    sc->beta = 0.0;
+    sc->pidx = 0;
+    sc->pcg_it = 0;
+    sc->use_best = 0;
+    sc->save_best = 0;
+    sc->tol_abs = sc->pcg_rel ? sc->pcg_tol * gn : sc->pcg_tol;
+    sc->pcg_done = (rr == 0.0 || !(rz > 0.0) || !isfinite(rz)) ? 1 : 0;
+    if (!sc->pcg_done) atomicAdd(ls.running, 1);
+    sc->ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- PCG
+
+// Matrix-free Schur product, one CTA per chunk (the hot loop).  With t_p =
+// H_pp^-1 sum_e Jp_e^T Jc_e x_c(e), each edge contributes v_e = Jc_e^T Jp_e t_p(e) to
+// its camera.  The CTA first issues its index loads, stages the camera vector of
+// each slot once (instead of once per edge), the point inverses, point offsets and
+// slot ranges, then runs barrier-separated passes in shared memory: per-edge point
+// terms, point sums, per-edge camera terms scattered to slot-sorted positions, and
+// contiguous per-slot sums.  Each chunk's Jacobian rows are read twice, the second
+// time mostly from L1/L2.
+template <class Mo, class JT, int EPT>
+__global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
+  using AT = typename AccOf<JT>::T;
+  using Dm = Dims<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
+  GPO_BIND(ch, kl)
+  if (!d.sc->active || d.sc->pcg_done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max, LD = CH + 1;
+  AT* vv = reinterpret_cast<AT*>(smem);        // [VW][LD]; rows 0..2 hold a_e in pass 1
+  AT* tp = vv + VW * LD;                       // [3][LD] point solutions
+  AT* xs = tp + 3 * LD;                        // [ls.ns_max][DC] slot camera vectors
+  AT* hv = xs + DC * ls.ns_max;                // [ls.np_max][6] point inverses
+  int* po = reinterpret_cast<int*>(hv + 6 * ls.np_max);   // [np + 1] local point offsets
+  int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
+  int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
+  const ChunkRange cr = chunk_range(d, kl);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
+
+  int pos[EPT], slot[EPT], ptl[EPT];
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const int i = threadIdx.x + m * kThreads;
+    if (i < cr.nE) {
+      pos[m] = __ldg(d.e_pos + cr.e0 + i);
+      slot[m] = __ldg(d.e_slot + cr.e0 + i);
+      ptl[m] = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
+    }
+  }
+  // the search direction p_k = (z_k + beta_k p_{k-1}) / n_k, formed per slot camera
+  const AT* zv = reinterpret_cast<const AT*>(d.z);
+  const AT* pold = reinterpret_cast<const AT*>(d.sc->pidx ? d.p2 : d.p);
+  const AT beta = (AT)d.sc->beta, inv_n = (AT)d.sc->inv_n;
+  for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
+    const int sl = w / DC, k = w - sl * DC;
+    const size_t o = DB * (size_t)__ldg(d.slot_cam + cr.s0 + sl) + k;
+    xs[w] = (zv[o] + beta * pold[o]) * inv_n;
+  }
+  for (int t = threadIdx.x; t < cr.nS; t += kThreads) sp[t] = __ldg(d.slot_pos + cr.s0 + t);
+  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv) + 6 * (size_t)cr.p0;
+  for (int w = threadIdx.x; w < cr.nP * 6; w += kThreads) hv[w] = Hinv[w];
+  for (int j = threadIdx.x; j <= cr.nP; j += kThreads) po[j] = __ldg(d.pt_off + cr.p0 + j) - cr.e0;
+  for (int t = threadIdx.x; t <= cr.nS; t += kThreads) so[t] = __ldg(d.slot_e0 + cr.s0 + t) - cr.e0;
+  __syncthreads();
+
+  // ---- pass 1: a_e = Jp^T (Jc x_c)
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const int i = threadIdx.x + m * kThreads;
+    if (i >= cr.nE) break;
+    AT row[NJ];
+    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    const AT* xc = xs + DC * slot[m];
+    AT q[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) q[a] = (AT)0;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+      const AT xk = xc[k];
+#pragma unroll
+      for (int a = 0; a < M; ++a) q[a] += row[a * DC + k] * xk;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      AT s = row[JP0 + k] * q[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) s += row[JP0 + 3 * a + k] * q[a];
+      vv[k * LD + i] = s;
+    }
+  }
+  __syncthreads();
+  // ---- pass 2: t_p = H_pp^-1 sum_e a_e
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    AT u[3] = {0, 0, 0};
+    for (int i = po[j]; i < po[j + 1]; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += vv[k * LD + i];
+    }
+    AT t[3];
+    mul3(hv + 6 * j, u, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tp[k * LD + j] = t[k];
+  }
+  __syncthreads();
+  // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const int i = threadIdx.x + m * kThreads;
+    if (i >= cr.nE) break;
+    AT row[NJ];
+    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    const int pl = ptl[m];
+    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
+    AT s[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) s[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+      AT v = row[k] * s[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) v += row[a * DC + k] * s[a];
+      vv[k * LD + pos[m]] = v;
+    }
+  }
+  __syncthreads();
+  // ---- pass 4: per-slot sums over contiguous positions
+  AT* partV = reinterpret_cast<AT*>(d.partV);
+  for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
+    const int sl = w / DC, comp = w - sl * DC;
+    const AT* src = vv + comp * LD;
+    AT acc = (AT)0;
+    for (int q = so[sl]; q < so[sl + 1]; ++q) acc += src[q];
+    partV[(size_t)sp[sl] * DC + comp] = acc;
+  }
+}
+
+// y_c = (H_cc + lambda D_c) p_c - sum_slots v (+ the camera-side edges' off-diagonal
+// products), four warps per camera (each sums a quarter of the camera's slot
+// partials; the quarters are added in a fixed order).  The CTAs of camera block b
+// are 4b .. 4b + 3, two cameras each.  The last CTA of the problem reduces p^T y and
+// sets alpha = r^T z / p^T y.
+constexpr int kApplySplit = 4;
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
+  constexpr int DB = Mo::DB, DC = Mo::DC, TB = Dims<Mo>::TB;
+  __shared__ double red[kCamPerBlock];
+  __shared__ AT quarter[kCamPerBlock][DC];
+  __shared__ DevBA d;
+  pdl_trigger();
+  const int cb = blockIdx.x / kApplySplit, part = blockIdx.x % kApplySplit;
+  const int prob_ = ls.cb_prob[cb];
+  const int cbl = cb - ls.cb_base[prob_];
+  bind_problem(d, ls.probs + prob_);
+  pdl_wait();
+  Scalars* sc = d.sc;
+  if (!sc->active || sc->pcg_done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cams_per_cta = kCamPerBlock / kApplySplit;             // 2
+  const int c = cbl * kCamPerBlock + part * cams_per_cta + warp / kApplySplit;
+  const int q = warp % kApplySplit;                                // quarter of the slots
+  double dot = 0.0;
+  AT pi = (AT)0;
+  if (c < d.C) {   // warp-uniform
+    const AT* partV = reinterpret_cast<const AT*>(d.partV);
+    const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
+    AT acc[DC];
+#pragma unroll
+    for (int k = 0; k < DC; ++k) acc[k] = (AT)0;
+#pragma unroll 4
+    for (int s = sa + q * 32 + lane; s < sb; s += 32 * kApplySplit) {
+      const AT* src = partV + (size_t)s * DC;   // camera-major rows
+#pragma unroll
+      for (int k = 0; k < DC; ++k) acc[k] += src[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < DC; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < DC; ++k) quarter[warp][k] = acc[k];
+    }
+  }
+  __syncthreads();
+  if (c < d.C && q == 0) {
+    AT sv = (AT)0;
+    if (lane < DC) {
+      sv = quarter[warp][lane];
+      for (int j = 1; j < kApplySplit; ++j) sv += quarter[warp + j][lane];
+    }
+    // p_k = (z_k + beta_k p_{k-1}) / n_k for this camera (the same values the Schur
+    // product gathered), written to the other direction buffer
+    const AT* pold_all = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
+    const AT* z_all = reinterpret_cast<const AT*>(d.z);
+    const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
+    AT* pnew = reinterpret_cast<AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
+    pi = lane < DB ? (z_all[DB * (size_t)c + lane] + beta * pold_all[DB * (size_t)c + lane]) * inv_n : (AT)0;
+    if (lane < DB) {
+      pnew[lane] = pi;
+      if (sc->save_best)
+        reinterpret_cast<AT*>(d.xbest)[DB * (size_t)c + lane] = reinterpret_cast<const AT*>(d.x)[DB * (size_t)c + lane];
+    }
+    const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * TB;
+    AT yi = (AT)0;
+#pragma unroll
+    for (int j = 0; j < DB; ++j) {
+      const AT pj = __shfl_sync(0xffffffffu, pi, j);
+      if (lane < DB) yi += H[sym_idx(DB, lane, j)] * pj;
+    }
+    if constexpr (Mo::kExtra) {
+      // J_c^T (J_o p_o) of every camera-side edge joining c to another camera o
+      for (int u = d.xk_off[c]; u < d.xk_off[c + 1]; ++u) {
+        const int code = d.xk_list[u], x = code >> 1, side = code & 1;
+        const int o = side ? d.xe_i[x] : d.xe_j[x];
+        if (o < 0) continue;   // unary edge: diagonal only
+        const double* J = d.xe_J + (size_t)x * kXJ;
+        const int m = xrows(d.xe_kind[x]);
+        const int own = side * DB, oth = (1 - side) * DB;
+        const AT po = lane < DB ? (z_all[DB * (size_t)o + lane] + beta * pold_all[DB * (size_t)o + lane]) * inv_n : (AT)0;
+        AT ua = (AT)0;
+        for (int k = 0; k < DB; ++k) {
+          const AT pk = __shfl_sync(0xffffffffu, po, k);
+          if (lane < m) ua += (AT)J[lane * kXCols + oth + k] * pk;
+        }
+        for (int a = 0; a < m; ++a) {
+          const AT va = __shfl_sync(0xffffffffu, ua, a);
+          if (lane < DB) yi += (AT)J[a * kXCols + own + lane] * va;
+        }
+      }
+    }
+    if (lane < DB) {
+      yi -= sv;
+      reinterpret_cast<AT*>(d.y)[DB * (size_t)c + lane] = yi;
+      dot = (double)pi * (double)yi;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+  if (lane == 0) red[warp] = dot;
+  __syncthreads();
+  const int ctas = d.ncblk * kApplySplit, me = cbl * kApplySplit + part;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < kCamPerBlock; ++w) a += red[w];
+    d.cblk_part[2 * me] = a;
+    d.cblk_part[2 * me + 1] = 0.0;
+  }
+  if (!last_cta(&sc->ticket, ctas)) return;
+  double pAp, unused;
+  sum_partials(d.cblk_part, ctas, pAp, unused);
+  if (threadIdx.x == 0) {
+    sc->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      sc->alpha = 0.0;
+      sc->pcg_done = 1;
+      atomicSub(ls.running, 1);
+    } else {
+      sc->alpha = sc->rz / pAp;
+    }
+    sc->ticket = 0u;
+  }
+}
+
+// One warp per camera: x += sigma alpha p, r -= alpha y, z = M r; the last CTA of
+// the problem reduces r^T z and |r|^2, applies the stopping rules (tolerance,
+// rejection ratio, iteration cap) and computes beta and the normalisation factor.
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) {
+  constexpr int DB = Mo::DB, TB = Dims<Mo>::TB;
+  __shared__ double red[kCamPerBlock][2];
+  GPO_BIND(cb, cbl)
+  Scalars* sc = d.sc;
+  if (!sc->active || sc->pcg_done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + warp;
+  double rz_c = 0.0, rr_c = 0.0;
+  if (c < d.C) {   // warp-uniform
+    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
+    AT* x = reinterpret_cast<AT*>(d.x) + DB * (size_t)c;
+    AT* r = reinterpret_cast<AT*>(d.r) + DB * (size_t)c;
+    AT* z = reinterpret_cast<AT*>(d.z) + DB * (size_t)c;
+    const AT* pv = reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
+    const AT* yv = reinterpret_cast<const AT*>(d.y) + DB * (size_t)c;
+    const AT* Mi = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * TB;
+    AT ri = (AT)0;
+    if (lane < DB) {
+      x[lane] += sa * pv[lane];
+      ri = r[lane] * sn - alpha * yv[lane];
+      r[lane] = ri;
+    }
+    AT zi = (AT)0;
+#pragma unroll
+    for (int j = 0; j < DB; ++j) {
+      const AT rj = __shfl_sync(0xffffffffu, ri, j);
+      if (lane < DB) zi += Mi[sym_idx(DB, lane, j)] * rj;
+    }
+    if (lane < DB) {
+      z[lane] = zi;
+      rz_c = (double)ri * (double)zi;
+      rr_c = (double)ri * (double)ri;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rz_c += __shfl_down_sync(0xffffffffu, rz_c, o);
+    rr_c += __shfl_down_sync(0xffffffffu, rr_c, o);
+  }
+  if (lane == 0) {
+    red[warp][0] = rz_c;
+    red[warp][1] = rr_c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kCamPerBlock; ++w) { a += red[w][0]; b += red[w][1]; }
+    d.cblk_part[2 * cbl] = a;
+    d.cblk_part[2 * cbl + 1] = b;
+  }
+  if (!last_cta(&sc->ticket, d.ncblk)) return;
+  double rz, rr;
+  sum_partials(d.cblk_part, d.ncblk, rz, rr);
+  if (threadIdx.x == 0) {
+    const double n = sqrt(rr);
+    const double rtrue = sc->sigma * n;
+    sc->pcg_it += 1;
+    sc->pcg_total += 1;
+    sc->rnorm = rtrue;
+    int done = 0;
+    sc->save_best = 0;
+    if (sc->ratio > 0.0) {
+      if (rtrue < sc->rmin) {
+        sc->rmin = rtrue;
+        sc->save_best = 1;
+      } else if (rtrue > sc->ratio * sc->rmin) {
+        done = 1;
+        sc->use_best = 1;
+      }
+    }
+    if (rtrue <= sc->tol_abs || sc->pcg_it >= sc->max_it || !isfinite(rtrue) || !(rz > 0.0)) {
+      done = 1;
+      if (!isfinite(rtrue)) sc->use_best = 1;
+    }
+    sc->beta = rz / sc->rz;
+    if (sc->normalize && n > 0.0) {
+      sc->inv_n = 1.0 / n;
+      sc->sigma *= n;
+      sc->rz = rz / (n * n);
+    } else {
+      sc->inv_n = 1.0;
+      sc->rz = rz;
+    }
+    sc->pidx ^= 1;
+    sc->pcg_done = done;
+    if (done) atomicSub(ls.running, 1);
+    sc->ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- back-substitution
+
+// One CTA per chunk: dp = H_pp^-1 (-b_p - sum_e Jp^T Jc dc) and the chunk's share of
+// the model decrease -b_p^T dp - 1/2 sum_e |Jc dc + Jp dp|^2 (FP64 accumulation).
+template <class Mo, class JT>
+__global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
+  using AT = typename AccOf<JT>::T;
+  using Dm = Dims<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0;
+  __shared__ double red[kThreads];
+  GPO_BIND(ch, kl)
+  if (!d.sc->active) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int CH = d.ch_max;
+  AT* qv = reinterpret_cast<AT*>(smem);   // [M][CH]
+  AT* av = qv + M * CH;                   // [3][CH]
+  const ChunkRange cr = chunk_range(d, kl);
+  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
+  const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x);
+  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
+  const AT* bp = reinterpret_cast<const AT*>(d.bp);
+  AT* dp = reinterpret_cast<AT*>(d.dp);
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int c = __ldg(d.e_cam + cr.e0 + i);
+    AT row[NJ];
+    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    AT q[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) q[a] = (AT)0;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+      const AT xk = xs[DB * (size_t)c + k];
+#pragma unroll
+      for (int a = 0; a < M; ++a) q[a] += row[a * DC + k] * xk;
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) qv[a * CH + i] = q[a];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      AT s = row[JP0 + k] * q[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) s += row[JP0 + 3 * a + k] * q[a];
+      av[k * CH + i] = s;
+    }
+  }
+  __syncthreads();
+  double md = 0.0;
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const int pj = cr.p0 + j;
+    const int a0 = d.pt_off[pj] - cr.e0, b0 = d.pt_off[pj + 1] - cr.e0;
+    AT u[3] = {0, 0, 0};
+    for (int i = a0; i < b0; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += av[k * CH + i];
+    }
+    AT hi[6], rhs[3], t[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rhs[k] = -bp[3 * (size_t)pj + k] - u[k];
+    mul3(hi, rhs, t);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dp[3 * (size_t)pj + k] = t[k];
+      md -= (double)bp[3 * (size_t)pj + k] * (double)t[k];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
+    const int pj = __ldg(d.e_pt + cr.e0 + i);
+    const AT t0 = dp[3 * (size_t)pj], t1 = dp[3 * (size_t)pj + 1], t2 = dp[3 * (size_t)pj + 2];
+    AT row[NJ];
+    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    double sq = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      const double ja = (double)(qv[a * CH + i] + row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 +
+                                 row[JP0 + 3 * a + 2] * t2);
+      sq += ja * ja;
+    }
+    md -= 0.5 * sq;
+  }
+  const double s = block_sum(md, red);
+  if (threadIdx.x == 0) d.md_part[kl] = s;
+}
+
+// ---------------------------------------------------------------- retraction (FP64)
+
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_retract_cams(LaunchSet ls) {
+  constexpr int SS = Mo::SS, DB = Mo::DB;
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active) return;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C || (threadIdx.x & 31) != 0) return;
+  const double* cur = d.cam + SS * (size_t)c;
+  double* nxt = d.cam_cand + SS * (size_t)c;
+  double* rb = d.camrb_cand + 16 * (size_t)c;
+  if (d.cam_fixed[c]) {
+    for (int i = 0; i < SS; ++i) nxt[i] = cur[i];
+    for (int i = 0; i < 16; ++i) rb[i] = d.camrb[16 * (size_t)c + i];
+    return;
+  }
+  const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x) + DB * (size_t)c;
+  double dl[DB];
+  for (int i = 0; i < DB; ++i) dl[i] = (double)xs[i];
+  double cu[SS], nx[SS];
+  for (int i = 0; i < SS; ++i) cu[i] = cur[i];
+  Mo::retract(cu, dl, nx);
+  for (int i = 0; i < SS; ++i) nxt[i] = nx[i];
+  double r16[16];
+  Mo::render(d, nx, r16);
+  for (int i = 0; i < 16; ++i) rb[i] = r16[i];
+}
+
+template <class Mo, class AT>
+__global__ void __launch_bounds__(256) k_retract_pts(LaunchSet ls) {
+  GPO_BIND(pb, pbl)
+  if (!d.sc->active) return;
+  const int p = pbl * 256 + threadIdx.x;
+  if (p >= d.P) return;
+  const AT* dp = reinterpret_cast<const AT*>(d.dp) + 3 * (size_t)p;
+  for (int i = 0; i < 3; ++i)
+    d.pt_cand[3 * (size_t)p + i] = d.pt[3 * (size_t)p + i] + (d.pt_fixed[p] ? 0.0 : (double)dp[i]);
+}
+
+// ---------------------------------------------------------------- LM decision (FP64)
+
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
+  __shared__ double red[kThreads];
+  __shared__ DevBA d;
+  pdl_trigger();
+  bind_problem(d, ls.probs + blockIdx.x);
+  pdl_wait();
+  Scalars* sc = d.sc;
+  if (!sc->active) return;
+  double fc = 0.0, md = 0.0;
+  for (int k = threadIdx.x; k < d.NCH; k += kThreads) {
+    fc += d.cost_part[k];
+    md += d.md_part[k];
+  }
+  if constexpr (Mo::kExtra) {
+    for (int x = threadIdx.x; x < d.NX; x += kThreads) {
+      fc += d.xe_cost[x];
+      md += d.xe_md[x];
+    }
+  }
+  const AT* xs = reinterpret_cast<const AT*>(sc->use_best ? d.xbest : d.x);
+  const AT* bc = reinterpret_cast<const AT*>(d.bc);
+  for (int i = threadIdx.x; i < Mo::DB * d.C; i += kThreads) md -= (double)bc[i] * (double)xs[i];
+  const double Fc = block_sum(fc, red);
+  const double L = block_sum(md, red);
+  if (threadIdx.x != 0) return;
+  const double F = sc->cost;
+  const bool acc = L > 0.0 && isfinite(Fc) && Fc < F;
+  const double rho = L != 0.0 ? (F - Fc) / L : 0.0;
+  const int it = sc->iter;
+  if (it < kMaxHistory) {
+    IterRecord& h = d.hist[it];
+    h.cost = F;
+    h.cand_cost = Fc;
+    h.model_decrease = L;
+    h.rho = rho;
+    h.lambda = sc->lambda;
+    h.pcg_residual = sc->gnorm > 0.0 ? sc->rnorm / sc->gnorm : 0.0;
+    h.accepted = acc ? 1 : 0;
+    h.pcg_iters = sc->pcg_it;
+  }
+  double lam = sc->lambda, nu = sc->nu;
+  if (acc) {
+    const double t = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - t * t * t);
+    nu = 2.0;
+    sc->cost = Fc;
+    sc->n_accepted += 1;
+  } else {
+    lam *= nu;
+    nu *= 2.0;
+  }
+  sc->lambda = fmin(fmax(lam, sc->lambda_min), sc->lambda_max);
+  sc->nu = nu;
+  sc->cand_cost = Fc;
+  sc->model_dec = L;
+  sc->rho = rho;
+  sc->accepted = acc ? 1 : 0;
+  sc->need_lin = acc ? 1 : 0;
+  sc->iter = it + 1;
+}
+
+template <class Mo>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_commit_cams(LaunchSet ls) {
+  GPO_BIND(cb, cbl)
+  if (!d.sc->active || !d.sc->accepted) return;
+  const int lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + (threadIdx.x >> 5);
+  if (c >= d.C) return;
+  if (lane < Mo::SS) d.cam[Mo::SS * (size_t)c + lane] = d.cam_cand[Mo::SS * (size_t)c + lane];
+  if (lane < 16) d.camrb[16 * (size_t)c + lane] = d.camrb_cand[16 * (size_t)c + lane];
+}
+
+template <class Mo>
+__global__ void __launch_bounds__(256) k_commit_pts(LaunchSet ls) {
+  GPO_BIND(pb, pbl)
+  if (!d.sc->active || !d.sc->accepted) return;
+  const int p = pbl * 256 + threadIdx.x;
+  if (p >= d.P) return;
+  for (int k = 0; k < 3; ++k) d.pt[3 * (size_t)p + k] = d.pt_cand[3 * (size_t)p + k];
+}
+
+// ---------------------------------------------------------------- launchers
+
+// Launches with programmatic stream serialization, so the kernel may begin while
+// its predecessor in the stream finishes (the kernels order themselves with
+// griddepcontrol).
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, size).
+static void set_smem(const void* kernel, size_t bytes) {
+  static const void* keys[64];
+  static size_t vals[64];
+  static int n = 0;
+  for (int i = 0; i < n; ++i)
+    if (keys[i] == kernel) {
+      if (vals[i] >= bytes) return;
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      vals[i] = bytes;
+      return;
+    }
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (n < 64) { keys[n] = kernel; vals[n] = bytes; ++n; }
+}
+
+// Shared-memory sizes and launchers of one model.
+template <class Mo>
+struct Launch {
+  using Dm = Dims<Mo>;
+  static size_t sJ(Prec pr) { return pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2); }
+  static size_t sA(Prec pr) { return pr == Prec::F64 ? 8 : 4; }
+  static size_t lin_smem(Prec pr, int ch) {
+    const size_t per = Dm::NJU * sJ(pr) + Mo::M * sA(pr) + (pr == Prec::BF16 ? (Mo::DC + 3) * sA(pr) : 0) + 2;
+    return per * (size_t)ch;
+  }
+  static size_t schur_smem(Prec pr, int ch) {
+    return (Dm::JP0 * sJ(pr) + (Dm::TM + Mo::M) * sA(pr) + 2) * (size_t)ch;
+  }
+  static size_t spmv_smem(Prec pr, const LaunchSet& ls) {
+    return sA(pr) * ((Dm::VW + 3) * (size_t)(ls.ch_max + 1) + Mo::DC * (size_t)ls.ns_max + 6 * (size_t)ls.np_max) +
+           4 * (size_t)(ls.np_max + 2 * ls.ns_max + 2);
+  }
+  static size_t backsub_smem(Prec pr, int ch) { return (Mo::M + 3) * sA(pr) * (size_t)ch; }
+  static int max_supported_ch(Prec pr) {
+    // largest chunk whose linearisation tile fits the 227 KB opt-in shared memory
+    const size_t limit = 227 * 1024;
+    int ch = 64;
+    while (lin_smem(pr, ch * 2) <= limit && schur_smem(pr, ch * 2) <= limit) ch *= 2;
+    return ch;
+  }
+
+  static int cam_prepare(const LaunchSet& ls, bool candidate, cudaStream_t st) {
+    if (ls.n_cb == 0) return 0;
+    launch_pdl(k_cam_prepare<Mo>, ls.n_cb, kCamPerBlock * 32, 0, st, ls, candidate ? 1 : 0);
+    return 1;
+  }
+  static int cost(const LaunchSet& ls, bool candidate, cudaStream_t st) {
+    if (ls.n_ch == 0) return 0;
+    launch_pdl(k_cost<Mo>, ls.n_ch, kThreads, 0, st, ls, candidate ? 1 : 0);
+    return 1;
+  }
+  static int cost_init(const LaunchSet& ls, cudaStream_t st) {
+    launch_pdl(k_cost_init<Mo>, ls.nprob, kThreads, 0, st, ls);
+    return 1;
+  }
+  template <class JT>
+  static void lin_t(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st) {
+    const size_t sm = lin_smem(pr, ls.ch_max);
+    set_smem(reinterpret_cast<const void*>(k_linearize<Mo, JT>), sm);
+    launch_pdl(k_linearize<Mo, JT>, ls.n_ch, kThreads, sm, st, ls, force ? 1 : 0);
+  }
+  static int linearize(const LaunchSet& ls, Prec pr, bool force, cudaStream_t st) {
+    if (ls.n_ch == 0) return 0;
+    if (pr == Prec::F64) lin_t<double>(ls, pr, force, st);
+    else if (pr == Prec::F32) lin_t<float>(ls, pr, force, st);
+    else lin_t<__nv_bfloat16>(ls, pr, force, st);
+    return 1;
+  }
+  template <class JT>
+  static void schur_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = schur_smem(pr, ls.ch_max);
+    set_smem(reinterpret_cast<const void*>(k_schur_prepare<Mo, JT>), sm);
+    launch_pdl(k_schur_prepare<Mo, JT>, ls.n_ch, kThreads, sm, st, ls);
+  }
+  static int schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_ch == 0) return 0;
+    if (pr == Prec::F64) schur_t<double>(ls, pr, st);
+    else if (pr == Prec::F32) schur_t<float>(ls, pr, st);
+    else schur_t<__nv_bfloat16>(ls, pr, st);
+    return 1;
+  }
+  static int cam_finalize(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_cb == 0) return 0;
+    if (pr == Prec::F64) launch_pdl(k_cam_finalize<Mo, double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+    else launch_pdl(k_cam_finalize<Mo, float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+    return 1;
+  }
+  template <class JT, int EPT>
+  static void spmv_e(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = spmv_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_spmv<Mo, JT, EPT>), sm);
+    launch_pdl(k_spmv<Mo, JT, EPT>, ls.n_ch, kThreads, sm, st, ls);
+  }
+  template <class JT>
+  static void spmv_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const int ept = (ls.ch_max + kThreads - 1) / kThreads;
+    if (ept <= 1) spmv_e<JT, 1>(ls, pr, st);
+    else if (ept <= 2) spmv_e<JT, 2>(ls, pr, st);
+    else if (ept <= 4) spmv_e<JT, 4>(ls, pr, st);
+    else spmv_e<JT, 8>(ls, pr, st);
+  }
+  static int pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_ch == 0) return 0;
+    if (pr == Prec::F64) spmv_t<double>(ls, pr, st);
+    else if (pr == Prec::F32) spmv_t<float>(ls, pr, st);
+    else spmv_t<__nv_bfloat16>(ls, pr, st);
+    return 1;
+  }
+  static int cam_apply(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_cb == 0) return 0;
+    if (pr == Prec::F64) launch_pdl(k_cam_apply<Mo, double>, ls.n_cb * kApplySplit, kCamPerBlock * 32, 0, st, ls);
+    else launch_pdl(k_cam_apply<Mo, float>, ls.n_cb * kApplySplit, kCamPerBlock * 32, 0, st, ls);
+    return 1;
+  }
+  static int pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_cb == 0) return 0;
+    if (pr == Prec::F64) launch_pdl(k_pcg_update<Mo, double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+    else launch_pdl(k_pcg_update<Mo, float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
+    return 1;
+  }
+  template <class JT>
+  static void backsub_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = backsub_smem(pr, ls.ch_max);
+    set_smem(reinterpret_cast<const void*>(k_backsub<Mo, JT>), sm);
+    launch_pdl(k_backsub<Mo, JT>, ls.n_ch, kThreads, sm, st, ls);
+  }
+  static int backsub(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_ch == 0) return 0;
+    if (pr == Prec::F64) backsub_t<double>(ls, pr, st);
+    else if (pr == Prec::F32) backsub_t<float>(ls, pr, st);
+    else backsub_t<__nv_bfloat16>(ls, pr, st);
+    return 1;
+  }
+  static int retract(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    int n = 0;
+    if (pr == Prec::F64) {
+      if (ls.n_cb) { launch_pdl(k_retract_cams<Mo, double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls); ++n; }
+      if (ls.n_pb) { launch_pdl(k_retract_pts<Mo, double>, ls.n_pb, 256, 0, st, ls); ++n; }
+    } else {
+      if (ls.n_cb) { launch_pdl(k_retract_cams<Mo, float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls); ++n; }
+      if (ls.n_pb) { launch_pdl(k_retract_pts<Mo, float>, ls.n_pb, 256, 0, st, ls); ++n; }
+    }
+    return n;
+  }
+  static int decide(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (pr == Prec::F64) launch_pdl(k_decide<Mo, double>, ls.nprob, kThreads, 0, st, ls);
+    else launch_pdl(k_decide<Mo, float>, ls.nprob, kThreads, 0, st, ls);
+    return 1;
+  }
+  static int commit(const LaunchSet& ls, cudaStream_t st) {
+    int n = 0;
+    if (ls.n_cb) { launch_pdl(k_commit_cams<Mo>, ls.n_cb, kCamPerBlock * 32, 0, st, ls); ++n; }
+    if (ls.n_pb) { launch_pdl(k_commit_pts<Mo>, ls.n_pb, 256, 0, st, ls); ++n; }
+    return n;
+  }
+};
+
+template <class Mo>
+KernelSet make_kernel_set(ModelKind kind) {
+  using L = Launch<Mo>;
+  KernelSet k{};
+  k.model = kind;
+  k.SS = Mo::SS; k.DB = Mo::DB; k.DC = Mo::DC; k.M = Mo::M; k.NJ = Mo::NJ; k.NPA = Dims<Mo>::NPA;
+  k.cam_prepare = &L::cam_prepare;
+  k.cost = &L::cost;
+  k.cost_init = &L::cost_init;
+  k.linearize = &L::linearize;
+  k.schur_prepare = &L::schur_prepare;
+  k.cam_finalize = &L::cam_finalize;
+  k.pcg_spmv = &L::pcg_spmv;
+  k.cam_apply = &L::cam_apply;
+  k.pcg_update = &L::pcg_update;
+  k.backsub = &L::backsub;
+  k.retract = &L::retract;
+  k.decide = &L::decide;
+  k.commit = &L::commit;
+  k.max_supported_ch = &L::max_supported_ch;
+  return k;
+}
+
+}  // namespace gpo

@@ -19,8 +19,9 @@ GPO_OK = 0
 GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_STATE, GPO_ERR_NUMERIC = -1, -2, -3, -4
 GPO_ERR_CUDA, GPO_ERR_TIMEOUT, GPO_ERR_UNSUPPORTED = -5, -6, -7
 GPO_FP64, GPO_FP32, GPO_FP32_BF16 = 0, 1, 2
-GPO_V_BA_CAMERA9, GPO_V_POINT3 = 0, 1
-GPO_E_BA_REPROJ = 0
+GPO_V_BA_CAMERA9, GPO_V_POINT3, GPO_V_NAV15 = 0, 1, 2
+GPO_E_BA_REPROJ, GPO_E_STEREO, GPO_E_IMU, GPO_E_BIAS_RW, GPO_E_BIAS_PRIOR = 0, 1, 2, 3, 4
+GPO_IMU_MEAS_LEN = 67
 GPO_LOSS_NONE, GPO_LOSS_HUBER = 0, 1
 PRECISIONS = {"fp64": GPO_FP64, "fp32": GPO_FP32, "bf16": GPO_FP32_BF16}
 
@@ -100,6 +101,9 @@ _SIGS = {
     "gpo_server_memory": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
     "gpo_server_last_error": (C.c_char_p, [_P]),
     "gpo_ba_cost_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_double, _P]),
+    "gpo_set_stereo_camera": (C.c_int, [_P, _P]),
+    "gpo_imu_preintegrate": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, _P, C.c_double, C.c_double,
+                                       _P, _P, _P]),
     "gpo_debug_linearize": (C.c_int, [_P, _P, _P]),
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
@@ -177,16 +181,23 @@ class Graph:
         _check(lib.gpo_add_vertices(self.h, kind, block_size, n, C.byref(first)), self.h)
         return first.value
 
-    def add_edges(self, kind: int, vertex_ids: np.ndarray, meas: np.ndarray, info=None,
+    def add_edges(self, kind: int, vertex_ids: np.ndarray, meas, info=None,
                   loss_kind: int = GPO_LOSS_NONE, loss_delta: float = 0.0) -> int:
         ids = np.ascontiguousarray(vertex_ids, dtype=np.int64)
-        m = np.ascontiguousarray(meas, dtype=np.float64)
+        m = None if meas is None else np.ascontiguousarray(meas, dtype=np.float64)
         inf = None if info is None else np.ascontiguousarray(info, dtype=np.float64)
         first = C.c_int64()
-        _check(lib.gpo_add_edges(self.h, kind, ids.shape[0], _ptr(ids), _ptr(m),
+        _check(lib.gpo_add_edges(self.h, kind, ids.shape[0], _ptr(ids), None if m is None else _ptr(m),
                                  None if inf is None else _ptr(inf), loss_kind, loss_delta,
                                  C.byref(first)), self.h)
         return first.value
+
+    def set_stereo_camera(self, rig) -> None:
+        """rig = [fx fy cx cy baseline, R_cb (9, row-major), t_cb (3)]."""
+        a = np.ascontiguousarray(rig, dtype=np.float64).reshape(-1)
+        if a.shape[0] != 17:
+            raise ValueError("the stereo rig has 17 values")
+        _check(lib.gpo_set_stereo_camera(self.h, _ptr(a)), self.h)
 
     def set_fixed(self, vid: int, fixed: bool = True):
         _check(lib.gpo_set_fixed(self.h, vid, int(fixed)), self.h)
@@ -247,9 +258,12 @@ class Graph:
         return v.value
 
     # diagnostics -----------------------------------------------------------
-    def debug_linearize(self, n_edges: int):
-        r = np.zeros((n_edges, 2))
-        J = np.zeros((n_edges, 2, 12))
+    def debug_linearize(self, n_edges: int, nav: bool = False):
+        """Per edge id: whitened residual rows and Jacobian rows ((2, 12) for BA graphs,
+        (9, 30) for graphs of navigation states; see gpo_debug_linearize)."""
+        R, K = (9, 30) if nav else (2, 12)
+        r = np.zeros((n_edges, R))
+        J = np.zeros((n_edges, R, K))
         _check(lib.gpo_debug_linearize(self.h, _ptr(r), _ptr(J)), self.h)
         return r, J
 
@@ -260,9 +274,9 @@ class Graph:
                                   _ptr(dx), C.byref(it)), self.h)
         return dx, it.value
 
-    def debug_schur(self, lam: float, n_cams: int, params: gpo_lm_params | None = None):
-        S = np.zeros((n_cams, 9, 9))
-        g = np.zeros((n_cams, 9))
+    def debug_schur(self, lam: float, n_cams: int, params: gpo_lm_params | None = None, db: int = 9):
+        S = np.zeros((n_cams, db, db))
+        g = np.zeros((n_cams, db))
         _check(lib.gpo_debug_schur(self.h, lam, None if params is None else C.byref(params),
                                    _ptr(S), _ptr(g)), self.h)
         return S, g
@@ -358,3 +372,72 @@ def ba_graph(cams, pts, cam_idx, pt_idx, obs, huber_delta=None, precision="fp64"
         for e in np.nonzero(~np.asarray(active, bool))[0]:
             g.set_edge_active(int(e), False)
     return g, c0, p0
+
+
+def imu_preintegrate(gyro, acc, dt: float, bg0, ba0, sigma_g: float, sigma_a: float, with_info: bool = True):
+    """Library preintegration of one keyframe interval (gpo_imu_preintegrate).
+    Returns (record of GPO_IMU_MEAS_LEN doubles, covariance 9x9, information 9x9 or None)."""
+    w = np.ascontiguousarray(gyro, dtype=np.float64).reshape(-1, 3)
+    a = np.ascontiguousarray(acc, dtype=np.float64).reshape(-1, 3)
+    if w.shape != a.shape:
+        raise ValueError("gyro and acc must have the same number of samples")
+    b_g = np.ascontiguousarray(bg0, dtype=np.float64).reshape(3)
+    b_a = np.ascontiguousarray(ba0, dtype=np.float64).reshape(3)
+    meas = np.zeros(GPO_IMU_MEAS_LEN)
+    cov = np.zeros((9, 9))
+    info = np.zeros((9, 9))
+    _check(lib.gpo_imu_preintegrate(_ptr(w), _ptr(a), w.shape[0], float(dt), _ptr(b_g), _ptr(b_a),
+                                    float(sigma_g), float(sigma_a), _ptr(meas), _ptr(cov),
+                                    _ptr(info) if with_info else None))
+    return meas, cov, (info if with_info else None)
+
+
+def stereo_rig(camera: dict) -> np.ndarray:
+    """[fx fy cx cy baseline, R_cb, t_cb] of a camera description."""
+    return np.r_[camera["fx"], camera["fy"], camera["cx"], camera["cy"], camera["baseline"],
+                 np.asarray(camera["R_cb"], float).reshape(9), np.asarray(camera["t_cb"], float).reshape(3)]
+
+
+def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), huber=True, imu=None, **kw):
+    """Builds the visual-inertial graph of a VIProblem-like record: navigation states get
+    ids [0, K), landmarks [K, K + P); edges in this order: stereo (Huber), inertial between
+    consecutive keyframes (preintegrated by the library at the initial biases of the first
+    keyframe of each pair), bias random walk (information diag 1 / (sigma^2 T)), and a
+    zero bias prior on keyframe 0 (information diag 1 / prior_sigma^2).  imu = (records
+    (K-1, GPO_IMU_MEAS_LEN), information (K-1, 9, 9)) supplies the inertial edges instead.
+    Returns (graph, first navigation id, first landmark id, edge-id ranges by kind)."""
+    nav = p.nav0 if nav is None else nav
+    pts = p.pts0 if pts is None else pts
+    g = Graph(precision, **kw)
+    K, P = nav.shape[0], pts.shape[0]
+    n0 = g.add_vertices(GPO_V_NAV15, 15, K)
+    p0 = g.add_vertices(GPO_V_POINT3, 3, P)
+    g.set_stereo_camera(stereo_rig(p.camera))
+    ids = np.stack([np.asarray(p.kf_idx, np.int64) + n0, np.asarray(p.pt_idx, np.int64) + p0], axis=1)
+    ranges = {}
+    e0 = g.add_edges(GPO_E_STEREO, ids, p.obs, None, GPO_LOSS_HUBER if huber else GPO_LOSS_NONE,
+                     float(p.huber_delta) if huber else 0.0)
+    ranges["stereo"] = (e0, e0 + ids.shape[0])
+    if K > 1:
+        if imu is not None:
+            meas, info = (np.asarray(a, np.float64) for a in imu)
+        else:
+            meas = np.zeros((K - 1, GPO_IMU_MEAS_LEN))
+            info = np.zeros((K - 1, 9, 9))
+            for k in range(K - 1):
+                meas[k], _, info[k] = imu_preintegrate(p.imu_gyro[k], p.imu_acc[k], p.dt, nav[k, 10:13],
+                                                       nav[k, 13:16], p.noise["sigma_g"], p.noise["sigma_a"])
+        ij = np.stack([np.arange(K - 1), np.arange(1, K)], axis=1).astype(np.int64) + n0
+        e0 = g.add_edges(GPO_E_IMU, ij, meas, info)
+        ranges["imu"] = (e0, e0 + K - 1)
+        T = meas[:, 60]
+        w2 = np.concatenate([np.tile((1.0 / (p.noise["sigma_bg"] ** 2 * T))[:, None], (1, 3)),
+                             np.tile((1.0 / (p.noise["sigma_ba"] ** 2 * T))[:, None], (1, 3))], axis=1)
+        e0 = g.add_edges(GPO_E_BIAS_RW, ij, None, np.stack([np.diag(x) for x in w2]))
+        ranges["bias_rw"] = (e0, e0 + K - 1)
+    pw = np.diag(np.r_[np.full(3, prior_sigma[0] ** -2.0), np.full(3, prior_sigma[1] ** -2.0)])
+    e0 = g.add_edges(GPO_E_BIAS_PRIOR, np.array([[n0]], np.int64), np.zeros((1, 6)), pw[None])
+    ranges["bias_prior"] = (e0, e0 + 1)
+    g.set_initial(n0, nav)
+    g.set_initial(p0, pts)
+    return g, n0, p0, ranges
