@@ -134,16 +134,23 @@ def load_peaks() -> tuple[float, str]:
 
 
 # DRAM traffic (read + write bytes) of one k_spmv launch from an ncu capture of the
-# medium workload (profiles/k_spmv_ba_medium_bf16.md), valid only for the kernel source it
-# was taken from: a different ba_kernels.cu reports null.
-MEASURED_TRAFFIC = {("bf16", "56ce627e8d8b"): 191.2e6}
+# medium workload (profiles/k_spmv_ba_medium_bf16.md), valid only for the kernel sources it
+# was taken from (keyed by a hash of them): changed kernels report null.
+MEASURED_TRAFFIC = {}
+KERNEL_SOURCES = ("schur_common.cuh", "schur_kernels.cuh", "ba_kernels.cu")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_26581_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def spmv_traffic(precision: str):
-    import hashlib
-    with open(os.path.join(ROOT, "paper_2509_26581_gb300", "csrc", "ba_kernels.cu"), "rb") as f:
-        sha = hashlib.sha1(f.read()).hexdigest()[:12]
-    return MEASURED_TRAFFIC.get((precision, sha))
+    return MEASURED_TRAFFIC.get((precision, kernel_source_hash()))
 
 
 def spmv_algorithmic_bytes(E: int, P: int, precision: str) -> float:

@@ -334,6 +334,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add(&xo_off_d, C + 1); pl.add(&xk_off_d, C + 1); pl.add(&xk_list_d, std::max(2 * NX, 1));
   pl.add(&d.xe_J, (size_t)std::max(NX, 1) * gpo::kXJ); pl.add(&d.xe_r, (size_t)std::max(NX, 1) * gpo::kXRows);
   pl.add(&d.xe_cost, std::max(NX, 1)); pl.add(&d.xe_md, std::max(NX, 1));
+  pl.add_raw(&d.xe_H, (size_t)std::max(NX, 1) * DB * DB * sA);
   pl.add(&d.cam, (size_t)SS * C); pl.add(&d.cam_cand, (size_t)SS * C);
   pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
   pl.add(&d.pt, 3 * (size_t)P); pl.add(&d.pt_cand, 3 * (size_t)P);
@@ -782,7 +783,8 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
       return fail(g, GPO_ERR_ARG, "edge %lld: ids must be (%s, point)", (long long)i,
                   ck == GPO_V_NAV15 ? "navigation state" : "camera");
     }
-    double U[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    double U[9];
+    for (int k = 0; k < m * m; ++k) U[k] = (k % (m + 1)) == 0 ? 1.0 : 0.0;   // m x m identity
     if (info) {
       if (!sqrt_info(info + (size_t)m * m * i, m, U)) {
         undo();

@@ -119,6 +119,7 @@ struct DevBA {
   double* xe_r;              // [NX][kXRows] whitened residual
   double* xe_cost;           // [NX] 1/2 |r|^2 at the last evaluated state
   double* xe_md;             // [NX] -1/2 |J dx|^2
+  void* xe_H;                // AT [NX][15][15] J_i^T J_j of two-keyframe edges (row-major)
   // FP64 state
   double* cam;               // [C][SS]
   double* cam_cand;          // [C][SS]

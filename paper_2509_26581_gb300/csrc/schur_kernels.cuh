@@ -570,6 +570,21 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
         }
         hx[warp][t] = acc;
       }
+      // off-diagonal blocks H_ij = J_i^T J_j of the two-keyframe edges whose first
+      // keyframe is c (read by the camera half of the Schur product)
+      AT* xH = reinterpret_cast<AT*>(d.xe_H);
+      for (int u = xa; u < xb; ++u) {
+        const int code = d.xk_list[u], x = code >> 1;
+        if ((code & 1) || d.xe_j[x] < 0) continue;
+        const double* J = d.xe_J + (size_t)x * kXJ;
+        const int m = xrows(d.xe_kind[x]);
+        for (int t = lane; t < DB * DB; t += 32) {
+          const int a = t / DB, b = t - a * DB;
+          double s = 0.0;
+          for (int r = 0; r < m; ++r) s += J[r * kXCols + a] * J[r * kXCols + DB + b];
+          xH[(size_t)x * DB * DB + t] = (AT)s;
+        }
+      }
     }
     __syncwarp();
     AT* Hcl = reinterpret_cast<AT*>(d.Hcl) + (size_t)c * TB;
@@ -789,7 +804,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
 
 // y_c = (H_cc + lambda D_c) p_c - sum_slots v (+ the camera-side edges' off-diagonal
 // products), four warps per camera (each sums a quarter of the camera's slot
-// partials; the quarters are added in a fixed order).  The CTAs of camera block b
+// partials and of its camera-side edges; the quarters are added in a fixed order).  The CTAs of camera block b
 // are 4b .. 4b + 3, two cameras each.  The last CTA of the problem reduces p^T y and
 // sets alpha = r^T z / p^T y.
 constexpr int kApplySplit = 4;
@@ -798,6 +813,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   constexpr int DB = Mo::DB, DC = Mo::DC, TB = Dims<Mo>::TB;
   __shared__ double red[kCamPerBlock];
   __shared__ AT quarter[kCamPerBlock][DC];
+  __shared__ AT qx[Mo::kExtra ? kCamPerBlock : 1][DB];
   __shared__ DevBA d;
   pdl_trigger();
   const int cb = blockIdx.x / kApplySplit, part = blockIdx.x % kApplySplit;
@@ -811,6 +827,9 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   const int cams_per_cta = kCamPerBlock / kApplySplit;             // 2
   const int c = cbl * kCamPerBlock + part * cams_per_cta + warp / kApplySplit;
   const int q = warp % kApplySplit;                                // quarter of the slots
+  const AT* pold_all = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
+  const AT* z_all = reinterpret_cast<const AT*>(d.z);
+  const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
   double dot = 0.0;
   AT pi = (AT)0;
   if (c < d.C) {   // warp-uniform
@@ -834,6 +853,25 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
 #pragma unroll
       for (int k = 0; k < DC; ++k) quarter[warp][k] = acc[k];
     }
+    if constexpr (Mo::kExtra) {
+      // H_co p_o of the two-keyframe edges joining c to another keyframe o, the
+      // camera's edges dealt round-robin to its four warps
+      const AT* xH = reinterpret_cast<const AT*>(d.xe_H);
+      AT ex = (AT)0;
+      for (int u = d.xk_off[c] + q; u < d.xk_off[c + 1]; u += kApplySplit) {
+        const int code = d.xk_list[u], x = code >> 1, side = code & 1;
+        const int o = side ? d.xe_i[x] : d.xe_j[x];
+        if (o < 0) continue;   // unary edge: diagonal only
+        const AT* H = xH + (size_t)x * DB * DB;
+        const AT po = lane < DB ? (z_all[DB * (size_t)o + lane] + beta * pold_all[DB * (size_t)o + lane]) * inv_n : (AT)0;
+#pragma unroll
+        for (int k = 0; k < DB; ++k) {
+          const AT pk = __shfl_sync(0xffffffffu, po, k);
+          if (lane < DB) ex += (side ? H[k * DB + lane] : H[lane * DB + k]) * pk;   // H_ij or H_ij^T
+        }
+      }
+      if (lane < DB) qx[warp][lane] = ex;
+    }
   }
   __syncthreads();
   if (c < d.C && q == 0) {
@@ -844,9 +882,6 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
     }
     // p_k = (z_k + beta_k p_{k-1}) / n_k for this camera (the same values the Schur
     // product gathered), written to the other direction buffer
-    const AT* pold_all = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
-    const AT* z_all = reinterpret_cast<const AT*>(d.z);
-    const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
     AT* pnew = reinterpret_cast<AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
     pi = lane < DB ? (z_all[DB * (size_t)c + lane] + beta * pold_all[DB * (size_t)c + lane]) * inv_n : (AT)0;
     if (lane < DB) {
@@ -862,25 +897,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
       if (lane < DB) yi += H[sym_idx(DB, lane, j)] * pj;
     }
     if constexpr (Mo::kExtra) {
-      // J_c^T (J_o p_o) of every camera-side edge joining c to another camera o
-      for (int u = d.xk_off[c]; u < d.xk_off[c + 1]; ++u) {
-        const int code = d.xk_list[u], x = code >> 1, side = code & 1;
-        const int o = side ? d.xe_i[x] : d.xe_j[x];
-        if (o < 0) continue;   // unary edge: diagonal only
-        const double* J = d.xe_J + (size_t)x * kXJ;
-        const int m = xrows(d.xe_kind[x]);
-        const int own = side * DB, oth = (1 - side) * DB;
-        const AT po = lane < DB ? (z_all[DB * (size_t)o + lane] + beta * pold_all[DB * (size_t)o + lane]) * inv_n : (AT)0;
-        AT ua = (AT)0;
-        for (int k = 0; k < DB; ++k) {
-          const AT pk = __shfl_sync(0xffffffffu, po, k);
-          if (lane < m) ua += (AT)J[lane * kXCols + oth + k] * pk;
-        }
-        for (int a = 0; a < m; ++a) {
-          const AT va = __shfl_sync(0xffffffffu, ua, a);
-          if (lane < DB) yi += (AT)J[a * kXCols + own + lane] * va;
-        }
-      }
+      if (lane < DB)
+        for (int j = 0; j < kApplySplit; ++j) yi += qx[warp + j][lane];
     }
     if (lane < DB) {
       yi -= sv;

@@ -17,7 +17,8 @@ arithmetic):
   * one LM step, PCG to 1e-14 relative residual vs dense Cholesky: 1e-7 relative (the
     reduced system's condition number is ~1e6 higher than in bundle adjustment);
   * final cost after 15 LM iterations: 1e-9 relative;
-  * mixed precision (FP32, BF16 storage) vs FP64 on the GPU: 1e-6 relative.
+  * mixed precision (FP32, BF16 storage) vs FP64 on the GPU: 1e-6 relative, once both
+    have converged (PCG run to 1e-10 relative, 30 LM iterations).
 """
 import numpy as np
 import pytest
@@ -191,12 +192,18 @@ def test_lm_final_cost_matches_oracle(gpo, small):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_mixed_precision_close_to_fp64(gpo, prec):
+    # The inertial chain couples neighbouring keyframes strongly, which block-Jacobi
+    # leaves to the PCG iterations: with enough of them every precision converges to
+    # the optimum within 30 LM iterations (the oracle reaches it to 1e-12).
     p = synth.vi_problem(6, n_kf=12, n_pts=400)
+    prm = gpo.default_params(pcg_max_iters=500, pcg_tol=1e-10)
     costs = {}
     for pr in ("fp64", prec):
         g, _, _, _ = gpo.vi_graph(p, precision=pr)
-        costs[pr] = g.optimize(20).final_cost
+        costs[pr] = g.optimize(30, prm).final_cost
     assert abs(costs[prec] - costs["fp64"]) <= 1e-6 * costs["fp64"]
+    _, orep = olm.levenberg_marquardt(ovi.problem(p, p.nav0, p.pts0, ovi.preintegrate_all(p)), 30)
+    assert abs(costs["fp64"] - orep.final_cost) <= 1e-9 * orep.final_cost
 
 
 def test_library_preintegration_graph_matches_oracle(gpo, small):
@@ -213,7 +220,7 @@ def test_fixed_keyframe_and_disabled_edges(gpo, small):
     g, n0, p0, rg = _graph(gpo, p, pims)
     g.set_fixed(n0)
     g.set_edge_active(rg["imu"][0] + 2, False)
-    rep = g.optimize(8)
+    rep = g.optimize(8, _parity_params(gpo))
     nav = g.get_state(n0, p.n_kf, 16)
     assert np.array_equal(nav[0], p.nav0[0])
     assert rep.final_cost < rep.initial_cost
@@ -222,7 +229,7 @@ def test_fixed_keyframe_and_disabled_edges(gpo, small):
     prob.edges[1].active = np.ones(p.n_kf - 1, bool)
     prob.edges[1].active[2] = False
     _, orep = olm.levenberg_marquardt(prob, 8)
-    assert abs(rep.final_cost - orep.final_cost) <= 1e-6 * orep.final_cost
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
 
 
 def test_kind_errors(gpo):
