@@ -137,6 +137,7 @@ def load_peaks() -> tuple[float, str]:
 # medium workload (profiles/k_spmv_ba_medium_bf16.md), valid only for the kernel sources it
 # was taken from (keyed by a hash of them): changed kernels report null.
 MEASURED_TRAFFIC = {}
+SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_kernels.cuh", "ba_kernels.cu")
 
 
@@ -175,7 +176,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
     g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
                              args.precision, device=dev, stream=stream.cuda_stream,
-                             chunk_edges=args.chunk)
+                             chunk_edges=args.chunk, spmv_variant=SPMV_VARIANTS[args.spmv])
     g.optimize(args.warmup, params)               # also freezes the topology and plans memory
     torch.cuda.synchronize()
     g.set_profiling(True)
@@ -239,7 +240,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         data="synthetic",
         config=dict(workload=WORKLOAD, precision=args.precision, cameras=p.n_cams, points=p.n_pts,
                     edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, seed=args.seed,
-                    chunk_edges=args.chunk or "default",
+                    chunk_edges=args.chunk or "default", spmv_kernel=args.spmv,
                     l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
                     parallelism=f"replicas x{world}"),
         e2e=None if args.no_e2e else dict(value=world * args.steps / e2e_s, unit="LM iter/s",
@@ -289,6 +290,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--chunk", type=int, default=0, help="edges per chunk (0 = library default)")
+    ap.add_argument("--spmv", default="auto", choices=sorted(SPMV_VARIANTS),
+                    help="Schur-product kernel (a tuning knob; results are bit-identical)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     args = ap.parse_args()

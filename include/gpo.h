@@ -110,9 +110,13 @@ typedef struct {
   void* alloc_ctx;
   size_t memory_budget;       /* bytes; 0 = unlimited.  Exceeding it gives GPO_ERR_OOM. */
   int32_t chunk_edges;        /* edges per CTA chunk of the per-edge kernels (32..2048;
-                                 0 = default: 1024, 512 in FP64); raised to the longest
-                                 track.  A tuning knob: results do not depend on it. */
-  int32_t reserved0;
+                                 0 = default: 512); raised to the longest track.  A
+                                 tuning knob: results do not depend on it. */
+  int32_t spmv_variant;       /* Schur-product kernel: 0 = automatic (classic), 1 = staged
+                                 (persistent CTAs streaming chunks into shared memory
+                                 with bulk copies; chunks of at most 1024 edges, else
+                                 classic), 2 = classic.  A tuning knob: both give
+                                 bit-identical results. */
 } gpo_graph_desc;
 
 /* Levenberg-Marquardt and PCG options (Listing 5: LevenbergMarquardtOptions and

@@ -273,6 +273,19 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   }
   std::vector<uint8_t> pt_fixed_s(P);
   for (int p = 0; p < P; ++p) pt_fixed_s[g->pt_old2new[p]] = g->pt_fixed[p];
+  // staged Schur-product inputs: packed per-edge positions and per-slot records
+  std::vector<uint32_t> e_meta((size_t)E + 4, 0u);
+  std::vector<int32_t> slot_rec(4 * (size_t)std::max(NS, 1), 0);
+  for (int k = 0; k < NCH; ++k) {
+    for (int i = ch_e0[k]; i < ch_e0[k + 1] && ch <= 1024; ++i)
+      e_meta[i] = (uint32_t)e_pos[i] | ((uint32_t)e_slot[i] << 10) | ((uint32_t)(e_pt_s[i] - ch_p0[k]) << 20);
+    for (int s = ch_s0[k]; s < ch_s0[k + 1]; ++s) {
+      slot_rec[4 * (size_t)s] = slot_e0[s] - ch_e0[k];
+      slot_rec[4 * (size_t)s + 1] = slot_e0[s + 1] - ch_e0[k];
+      slot_rec[4 * (size_t)s + 2] = slot_cam[s];
+      slot_rec[4 * (size_t)s + 3] = slot_pos[s];
+    }
+  }
 
   // camera-side edges: active ones, sorted by (first camera, index)
   g->x_sorted.clear();
@@ -320,6 +333,8 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   int *xe_i_d, *xe_j_d, *xe_kind_d, *xo_off_d, *xk_off_d, *xk_list_d;
   double* xe_rec_d;
   uint16_t *e_pos_d, *e_slot_d, *ch_sorted_d;
+  uint32_t* e_meta_d;
+  int32_t* slot_rec_d;
   uint8_t *cam_fixed_d, *pt_fixed_d;
   double *obs_d, *delta_d, *info_d = nullptr;
   pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, (size_t)M * E); pl.add(&delta_d, E);
@@ -327,6 +342,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
   pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E); pl.add(&e_slot_d, E);
   pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
+  pl.add(&e_meta_d, (size_t)E + 4); pl.add(&slot_rec_d, 4 * (size_t)std::max(NS, 1));
   pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1)); pl.add(&slot_pos_d, std::max(NS, 1));
   pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
   pl.add(&xe_i_d, std::max(NX, 1)); pl.add(&xe_j_d, std::max(NX, 1)); pl.add(&xe_kind_d, std::max(NX, 1));
@@ -341,6 +357,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add_raw(&d.J, std::max<size_t>(jpos, 8) * sJ);
   pl.add_raw(&d.Hpp, 6 * (size_t)P * sA); pl.add_raw(&d.bp, 3 * (size_t)P * sA);
   pl.add_raw(&d.Hinv, 6 * (size_t)P * sA); pl.add_raw(&d.dp, 3 * (size_t)P * sA);
+  pl.add_raw(&d.pt_rec, (size_t)std::max(P, 1) * (pr == Prec::F64 ? 64 : 32));
   pl.add_raw(&d.partA, (size_t)NPA * NS * sA); pl.add_raw(&d.partB, (size_t)NPA * NS * sA);
   pl.add_raw(&d.partV, (size_t)DC * NS * sA);
   pl.add_raw(&d.Hcl, (size_t)TB * C * sA); pl.add_raw(&d.bc, (size_t)DB * C * sA);
@@ -359,7 +376,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   int *ch_prob_d, *cb_prob_d, *pb_prob_d, *base_d, *running_d;
   pl.add(&desc_d, 1);
   pl.add(&ch_prob_d, std::max(NCH, 1)); pl.add(&cb_prob_d, d.ncblk); pl.add(&pb_prob_d, npb);
-  pl.add(&base_d, 1); pl.add(&running_d, 1);
+  pl.add(&base_d, 1); pl.add(&running_d, 2);
   const size_t bytes = pl.total();
   if (plan_bytes) {
     *plan_bytes = bytes;
@@ -388,6 +405,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.slot_pos = slot_pos_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
   d.xe_i = xe_i_d; d.xe_j = xe_j_d; d.xe_kind = xe_kind_d; d.xe_rec = xe_rec_d;
   d.xo_off = xo_off_d; d.xk_off = xk_off_d; d.xk_list = xk_list_d;
+  d.e_meta = e_meta_d; d.slot_rec = reinterpret_cast<const int4*>(slot_rec_d);
   d.dbg_r = nullptr;
   cudaStream_t st = g->stream;
   GPO_CUDA(g, up(e_cam, e_cam_s, st));
@@ -407,6 +425,8 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   GPO_CUDA(g, up(cam_s_off_d, cam_s_off, st));
   GPO_CUDA(g, up(cam_s_list_d, cam_s_list, st));
   GPO_CUDA(g, up(slot_pos_d, slot_pos, st));
+  GPO_CUDA(g, up(e_meta_d, e_meta, st));
+  GPO_CUDA(g, up(slot_rec_d, slot_rec, st));
   GPO_CUDA(g, up(cam_fixed_d, g->cam_fixed, st));
   GPO_CUDA(g, up(pt_fixed_d, pt_fixed_s, st));
   GPO_CUDA(g, up(xe_i_d, xi_s, st));
@@ -432,7 +452,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   GPO_CUDA(g, cudaMemsetAsync(cb_prob_d, 0, d.ncblk * sizeof(int), st));
   GPO_CUDA(g, cudaMemsetAsync(pb_prob_d, 0, npb * sizeof(int), st));
   GPO_CUDA(g, cudaMemsetAsync(base_d, 0, sizeof(int), st));
-  GPO_CUDA(g, cudaMemsetAsync(running_d, 0, sizeof(int), st));
+  GPO_CUDA(g, cudaMemsetAsync(running_d, 0, 2 * sizeof(int), st));
   GPO_CUDA(g, cudaMemcpyAsync(desc_d, &d, sizeof(DevBA), cudaMemcpyHostToDevice, st));
   GPO_CUDA(g, cudaStreamSynchronize(st));
   gpo::LaunchSet ls{};
@@ -441,6 +461,8 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   ls.cb_prob = cb_prob_d; ls.cb_base = base_d;
   ls.pb_prob = pb_prob_d; ls.pb_base = base_d;
   ls.running = running_d;
+  ls.err = running_d + 1;
+  ls.spmv_variant = g->desc.spmv_variant;
   ls.nprob = 1; ls.n_ch = NCH; ls.n_cb = C > 0 ? d.ncblk : 0; ls.n_pb = P > 0 ? npb : 0;
   ls.ch_max = ch;
   ls.ns_max = ns_max;
@@ -551,15 +573,22 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
       run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
     }
     launched += n;
-    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[slot], ls.running, sizeof(int),
+    GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[2 * slot], ls.running, 2 * sizeof(int),
                                 cudaMemcpyDeviceToHost, g->stream));
     GPO_CUDA(g, cudaEventRecord(g->ev[slot], g->stream));
     if (pending >= 0) {
       GPO_CUDA(g, cudaEventSynchronize(g->ev[pending]));
-      if (g->h_flag[pending] == 0) break;   // no problem is still iterating
+      if (g->h_flag[2 * pending + 1])
+        return fail(g, GPO_ERR_TIMEOUT, "a bounded device wait in the Schur product gave up");
+      if (g->h_flag[2 * pending] == 0) break;   // no problem is still iterating
     }
     pending = slot;
     slot ^= 1;
+  }
+  if (pending >= 0) {
+    GPO_CUDA(g, cudaEventSynchronize(g->ev[pending]));
+    if (g->h_flag[2 * pending + 1])
+      return fail(g, GPO_ERR_TIMEOUT, "a bounded device wait in the Schur product gave up");
   }
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
@@ -568,7 +597,7 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
 gpo_status gpo_host::solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin) {
   run(g, KK_LINEARIZE, [&] { return g->ks->linearize(ls, g->prec, force_lin, g->stream); });
   run(g, KK_SCHUR, [&] { return g->ks->schur_prepare(ls, g->prec, g->stream); });
-  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, sizeof(int), g->stream));
+  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, 2 * sizeof(int), g->stream));
   run(g, KK_CAM_FINALIZE, [&] { return g->ks->cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   gpo_status s = pcg_solve(g, ls, max_it);
@@ -684,7 +713,7 @@ gpo_status gpo_graph_create(const gpo_graph_desc* desc, gpo_graph** out) {
     }
   }
   if (e == cudaSuccess) e = cudaMallocHost(&g->h_sc, sizeof(Scalars));
-  if (e == cudaSuccess) e = cudaMallocHost(&g->h_flag, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_flag, 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming);
   if (e != cudaSuccess) {

@@ -100,6 +100,8 @@ struct DevBA {
   const uint16_t* e_pos;     // [E] position of the edge in its chunk's slot-sorted order
   const uint16_t* e_slot;    // [E] slot of the edge inside its chunk
   const uint16_t* ch_sorted; // [E] per chunk: local edge ids sorted by (slot, id)
+  const uint32_t* e_meta;    // [E + 4] packed pos | slot << 10 | local point << 20 (chunks <= 1024)
+  const int4* slot_rec;      // [NS] local edge range [x, y) in slot order, camera z, partial row w
   const int* slot_e0;        // [NS+1] range of a slot in ch_sorted (global positions)
   const int* slot_cam;       // [NS]
   const int* slot_pos;       // [NS] row of the slot's partial in camera-major order
@@ -132,6 +134,7 @@ struct DevBA {
   void* Hpp;                 // AT [P][6] undamped point blocks
   void* bp;                  // AT [P][3]
   void* Hinv;                // AT [P][6] damped inverses
+  void* pt_rec;              // [P] records of 32 (FP32) / 64 (FP64) bytes: H_pp^-1 (6 AT), local edge range (2 int)
   void* dp;                  // AT [P][3] point step
   void* partA;               // AT [NS][NPA]
   void* partB;               // AT [NS][NPA]
@@ -167,7 +170,10 @@ struct LaunchSet {
   const int* ch_prob; const int* ch_base;
   const int* cb_prob; const int* cb_base;
   const int* pb_prob; const int* pb_base;
-  int* running;          // problems whose PCG is still iterating
+  int* running;          // [2]: problems whose PCG is still iterating; [1] error flag (a
+                         // bounded device wait gave up)
+  int* err;              // = running + 1
+  int spmv_variant;      // Schur-product kernel: 0 auto, 1 staged (bulk copies), 2 classic
   int nprob, n_ch, n_cb, n_pb;
   int ch_max;            // largest chunk over the problems (shared-memory sizing)
   int ns_max, np_max;    // most slots / points in one chunk over the problems

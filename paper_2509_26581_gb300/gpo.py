@@ -34,7 +34,7 @@ class gpo_graph_desc(C.Structure):
                 ("reserve_vertices", C.c_int64), ("reserve_edges", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
                 ("alloc_ctx", C.c_void_p), ("memory_budget", C.c_size_t),
-                ("chunk_edges", C.c_int32), ("reserved0", C.c_int32)]
+                ("chunk_edges", C.c_int32), ("spmv_variant", C.c_int32)]
 
 
 class gpo_lm_params(C.Structure):
@@ -153,7 +153,8 @@ class Graph:
     """Owns one gpo_graph handle."""
 
     def __init__(self, precision="fp64", device: int = 0, stream=None, memory_budget: int = 0,
-                 reserve_vertices: int = 0, reserve_edges: int = 0, chunk_edges: int = 0):
+                 reserve_vertices: int = 0, reserve_edges: int = 0, chunk_edges: int = 0,
+                 spmv_variant: int = 0):
         d = gpo_graph_desc()
         _check(lib.gpo_graph_desc_default(C.byref(d)))
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -163,6 +164,7 @@ class Graph:
         d.reserve_vertices = reserve_vertices
         d.reserve_edges = reserve_edges
         d.chunk_edges = chunk_edges
+        d.spmv_variant = spmv_variant
         h = C.c_void_p()
         _check(lib.gpo_graph_create(C.byref(d), C.byref(h)))
         self.h = h
