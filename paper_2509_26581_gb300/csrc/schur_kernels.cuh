@@ -149,6 +149,40 @@ __device__ void warp_spd_inverse(const AT* A, AT* M, int lane) {
   }
 }
 
+// Sum of src[a .. b) with four interleaved partial sums (more loads in flight than a
+// single running sum), combined as (s0 + s1) + (s2 + s3).
+template <class AT>
+__device__ __forceinline__ AT seg_sum(const AT* src, int a, int b) {
+  AT s0 = (AT)0, s1 = (AT)0, s2 = (AT)0, s3 = (AT)0;
+  int q = a;
+  for (; q + 4 <= b; q += 4) {
+    s0 += src[q];
+    s1 += src[q + 1];
+    s2 += src[q + 2];
+    s3 += src[q + 3];
+  }
+  for (; q < b; ++q) s0 += src[q];
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Point sums of the Schur product's pass 2: u_k = sum_{i in [a, b)} v[k LD + i].  FP32
+// storage takes the interleaved sums (measured faster on the 1,000-camera BA workload);
+// BF16 and FP64 keep one running sum per component (the interleaved form raises their
+// register count past six resident CTAs per SM, which costs more than it gains).
+template <class JT, class AT>
+__device__ __forceinline__ void point_sum(const AT* v, int LD, int a, int b, AT (&u)[3]) {
+  if constexpr (std::is_same<JT, float>::value) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = seg_sum(v + k * LD, a, b);
+  } else {
+    u[0] = u[1] = u[2] = (AT)0;
+    for (int i = a; i < b; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += v[k * LD + i];
+    }
+  }
+}
+
 __device__ __forceinline__ int xrows(int kind) { return kind == XK_IMU ? 9 : 6; }
 
 // ---------------------------------------------------------------- camera render blocks
@@ -769,11 +803,8 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   __syncthreads();
   // ---- pass 2: t_p = H_pp^-1 sum_e a_e
   for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
-    AT u[3] = {0, 0, 0};
-    for (int i = po[j]; i < po[j + 1]; ++i) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) u[k] += vv[k * LD + i];
-    }
+    AT u[3];
+    point_sum<JT>(vv, LD, po[j], po[j + 1], u);
     AT t[3];
     mul3(hv + 6 * j, u, t);
 #pragma unroll
@@ -805,10 +836,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   AT* partV = reinterpret_cast<AT*>(d.partV);
   for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
     const int sl = w / DC, comp = w - sl * DC;
-    const AT* src = vv + comp * LD;
-    AT acc = (AT)0;
-    for (int q = so[sl]; q < so[sl + 1]; ++q) acc += src[q];
-    partV[(size_t)sp[sl] * DC + comp] = acc;
+    partV[(size_t)sp[sl] * DC + comp] = seg_sum(vv + comp * LD, so[sl], so[sl + 1]);
   }
 }
 
@@ -840,12 +868,35 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr unsigned kSpinLimit = 1u << 24;   // bounded waits: ~seconds at most
-constexpr int kStages = 2;                  // chunks in flight per CTA
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+constexpr unsigned kSpinLimit = 1u << 22;   // bounded waits: well under a second of polling
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned n = 0; n < kSpinLimit; ++n)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+constexpr int kStages = 3;                    // chunks in flight per CTA
+constexpr int kWsThreads = kThreads + 32;     // eight consumer warps and one producer warp
+
+// Named barrier of the consumer warps (the producer warp does not take part), and its
+// OR-reduction form.
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+__device__ __forceinline__ bool consumer_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kThreads)
+      : "memory");
+  return r != 0;
+}
 
 // Byte layout of one pipeline stage in shared memory (all offsets 16-byte aligned).
 struct StageLayout {
-  uint32_t j, meta, pt, slot, size;
+  uint32_t j, meta, pt, slot, xs, size;
 };
 template <class Mo>
 __host__ __device__ inline StageLayout stage_layout(size_t sJ, size_t sA, int ch_max, int np_max, int ns_max) {
@@ -856,219 +907,225 @@ __host__ __device__ inline StageLayout stage_layout(size_t sJ, size_t sA, int ch
   L.meta = al((uint32_t)(ch_max * Mo::NJ * sJ));
   L.pt = L.meta + al((uint32_t)(ch_max * 4 + 16));
   L.slot = L.pt + al((uint32_t)(np_max * prb));
-  L.size = L.slot + al((uint32_t)(ns_max * 16));
+  L.xs = L.slot + al((uint32_t)(ns_max * 16));
+  L.size = L.xs + al((uint32_t)(ns_max * Mo::DC * sA));
   return L;
 }
 
-// Persistent form of the Schur product: each CTA walks chunks blockIdx.x, + gridDim.x,
-// ... of the launch set, skipping problems whose PCG has stopped.  Thread 0 streams a
-// chunk's inputs -- its Jacobian rows, packed per-edge positions, point records
-// (H_pp^-1 and edge range) and slot records (edge range, camera, partial row) -- into
-// a shared-memory stage with 1-D bulk copies completing on the stage's mbarrier, one
-// chunk ahead of the one being computed; the compute passes are those of k_spmv and
-// give bit-identical results.  A wait that does not complete within kSpinLimit
-// polls raises *ls.err and ends the kernel after the copies in flight have landed
-// (bounded again).
+struct StageInfo {
+  int k, q, nE, nP, nS, skew;   // chunk (-1: no more chunks), problem, sizes, meta skew
+};
+
+// Warp-specialised persistent Schur product.  One producer warp walks the chunks
+// blockIdx.x, + gridDim.x, ... of the launch set (skipping problems whose PCG has
+// stopped) and, kStages chunks ahead of the consumers, streams each chunk's inputs
+// -- Jacobian rows, packed per-edge positions, point records (H_pp^-1 and edge range)
+// and slot records (edge range, camera, partial row) -- into a shared-memory stage
+// with 1-D bulk copies completing on the stage's "full" mbarrier, and gathers the
+// slot cameras' search-direction values p = (z + beta p_old) / n into the stage
+// itself.  Eight consumer warps run the passes of k_spmv on the stage (named barriers
+// among themselves) and release it on its "empty" mbarrier.  Results are bit-identical
+// to k_spmv.  Every wait is bounded: a wait that gives up raises *ls.err, and the
+// producer lets its copies in flight land (bounded again) before the CTA exits.
 template <class Mo, class JT>
-__global__ void __launch_bounds__(kThreads) k_spmv_bulk(LaunchSet ls) {
+__global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
   constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
   constexpr uint32_t RB = NJ * sizeof(JT);
   constexpr uint32_t PRB = (6 * sizeof(AT) + 8 + 15) & ~15u;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[kStages];
-  __shared__ int st_k[kStages], st_skew[kStages];
-  __shared__ DevBA d;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ StageInfo info[kStages];
+  __shared__ int s_fail;
   pdl_trigger();
   const StageLayout SL = stage_layout<Mo>(sizeof(JT), sizeof(AT), ls.ch_max, ls.np_max, ls.ns_max);
-  const int CH = ls.ch_max, LD = CH + 1;
-  AT* vv = reinterpret_cast<AT*>(smem + kStages * SL.size);   // [VW][LD]
+  const int LD = ls.ch_max + 1;
+  AT* vv = reinterpret_cast<AT*>(smem + kStages * SL.size);   // [VW][LD] consumer scratch
   AT* tp = vv + VW * LD;                                        // [3][LD]
-  AT* xs = tp + 3 * LD;                                         // [ns_max][DC]
   const int G = gridDim.x;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(smem_u32(&full[st]), 2);    // the producer's expect_tx arrival + its gather arrival
+      mbar_init(smem_u32(&empty[st]), 1);   // one consumer arrival
+    }
     mbar_fence_init();
+    s_fail = 0;
   }
   pdl_wait();
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // next chunk k' >= k in this CTA's sequence whose problem still iterates, or -1
-  // (thread 0 only; dead problems are skipped whole)
-  auto next_live = [&](int k) -> int {
-    while (k < ls.n_ch) {
+  if (warp == kThreads / 32) {
+    // ================================================================ producer warp
+    // next chunk k' >= k of this CTA whose problem still iterates, or -1
+    auto next_live = [&](int k) -> int {
+      while (k < ls.n_ch) {
+        const int q = ls.ch_prob[k];
+        const Scalars* sc = ls.probs[q].sc;
+        if (sc->active && !sc->pcg_done) return k;
+        const int nxt = q + 1 < ls.nprob ? ls.ch_base[q + 1] : ls.n_ch;
+        k += ((nxt - k) + G - 1) / G * G;
+      }
+      return -1;
+    };
+    int last_use[kStages];
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) last_use[st] = -1;
+    int k = __shfl_sync(0xffffffffu, lane == 0 ? next_live(blockIdx.x) : 0, 0);
+    int cq = -1;
+    const DevBA* P = nullptr;
+    const AT* zv = nullptr;
+    const AT* pold = nullptr;
+    AT beta = (AT)0, inv_n = (AT)1;
+    for (int n = 0;; ++n) {
+      const int st = n % kStages, use = n / kStages;
+      if (use > 0 && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(use - 1) & 1u)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      const uint32_t fb = smem_u32(&full[st]);
+      last_use[st] = use;
+      if (k < 0) {   // end of work: an empty stage with no transfer
+        if (lane == 0) {
+          info[st].k = -1;
+          mbar_arrive(fb, 2);
+        }
+        break;
+      }
       const int q = ls.ch_prob[k];
-      const Scalars* sc = ls.probs[q].sc;
-      if (sc->active && !sc->pcg_done) return k;
-      const int nxt = q + 1 < ls.nprob ? ls.ch_base[q + 1] : ls.n_ch;
-      k += ((nxt - k) + G - 1) / G * G;
-    }
-    return -1;
-  };
-  auto issue = [&](int k, int s) {
-    const int q = ls.ch_prob[k];
-    const DevBA& P = ls.probs[q];
-    const int kl = k - ls.ch_base[q];
-    const int e0 = P.ch_e0[kl], e1 = P.ch_e0[kl + 1];
-    const int p0 = P.ch_p0[kl], p1 = P.ch_p0[kl + 1];
-    const int s0 = P.ch_s0[kl], s1 = P.ch_s0[kl + 1];
-    const uint32_t bJ = (uint32_t)(e1 - e0) * RB;
-    const uintptr_t ms = reinterpret_cast<uintptr_t>(P.e_meta + e0);
-    const uintptr_t ma = ms & ~(uintptr_t)15;
-    const uint32_t skew = (uint32_t)(ms - ma);
-    const uint32_t bM = e1 > e0 ? (skew + 4u * (uint32_t)(e1 - e0) + 15u) & ~15u : 0u;
-    const uint32_t bP = (uint32_t)(p1 - p0) * PRB;
-    const uint32_t bS = (uint32_t)(s1 - s0) * 16u;
-    const uint32_t mb = smem_u32(&mbar[s]);
-    unsigned char* base = smem + s * SL.size;
-    st_k[s] = k;
-    st_skew[s] = (int)(skew / 4);
-    fence_proxy_async();
-    mbar_expect_tx(mb, bJ + bM + bP + bS);
-    if (bJ) bulk_g2s(smem_u32(base + SL.j), static_cast<const JT*>(P.J) + (size_t)e0 * NJ, bJ, mb);
-    if (bM) bulk_g2s(smem_u32(base + SL.meta), reinterpret_cast<const void*>(ma), bM, mb);
-    if (bP) bulk_g2s(smem_u32(base + SL.pt), static_cast<const unsigned char*>(P.pt_rec) + (size_t)p0 * PRB, bP, mb);
-    if (bS) bulk_g2s(smem_u32(base + SL.slot), P.slot_rec + s0, bS, mb);
-  };
-
-  if (threadIdx.x == 0) {
-    const int k0 = next_live(blockIdx.x);
-    st_k[0] = -1;
-    if (k0 >= 0) issue(k0, 0);
-  }
-  __syncthreads();
-  int cur_q = -1;
-  int fail_it = -1;
-  for (int it = 0;; ++it) {
-    const int s = it % kStages;
-    const int k = st_k[s];
-    if (k < 0) break;
-    if (threadIdx.x == 0) {
-      const int s2 = (it + 1) % kStages;
-      const int k1 = next_live(k + G);
-      st_k[s2] = -1;
-      if (k1 >= 0) issue(k1, s2);
-    }
-    const int q = ls.ch_prob[k];
-    if (q != cur_q) {
-      bind_problem(d, ls.probs + q);   // includes a barrier
-      cur_q = q;
-    }
-    const ChunkRange cr = chunk_range(d, k - ls.ch_base[q]);
-    // wait for the stage (every thread polls; bounded).  Use n of stage s completes
-    // the mbarrier phase of parity n & 1.
-    bool ok = false;
-    {
-      const uint32_t mb = smem_u32(&mbar[s]);
-      const uint32_t par = (uint32_t)(it / kStages) & 1u;
-      for (unsigned n = 0; n < kSpinLimit && !ok; ++n) ok = mbar_try_wait(mb, par);
-    }
-    const unsigned char* stg = smem + s * SL.size;
-    const JT* Js = reinterpret_cast<const JT*>(stg + SL.j);
-    const uint32_t* meta = reinterpret_cast<const uint32_t*>(stg + SL.meta) + st_skew[s];
-    const unsigned char* prec = stg + SL.pt;
-    const int4* srec = reinterpret_cast<const int4*>(stg + SL.slot);
-    // the search direction p_k = (z_k + beta_k p_{k-1}) / n_k, formed per slot camera
-    const AT* zv = reinterpret_cast<const AT*>(d.z);
-    const AT* pold = reinterpret_cast<const AT*>(d.sc->pidx ? d.p2 : d.p);
-    const AT beta = (AT)d.sc->beta, inv_n = (AT)d.sc->inv_n;
-    if (__syncthreads_or(!ok)) {
-      fail_it = it;
-      break;
-    }
-    for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
-      const int sl = w / DC, kk = w - sl * DC;
-      const size_t o = DB * (size_t)srec[sl].z + kk;
-      xs[w] = (zv[o] + beta * pold[o]) * inv_n;
-    }
-    __syncthreads();
-    // ---- pass 1: a_e = Jp^T (Jc x_c)
-    for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
-      AT row[NJ];
-      load_row<NJ>(Js + (size_t)i * NJ, row);
-      const AT* xc = xs + DC * (int)((meta[i] >> 10) & 1023u);
-      AT qv[M];
-#pragma unroll
-      for (int a = 0; a < M; ++a) qv[a] = (AT)0;
-#pragma unroll
-      for (int kk = 0; kk < DC; ++kk) {
-        const AT xk = xc[kk];
-#pragma unroll
-        for (int a = 0; a < M; ++a) qv[a] += row[a * DC + kk] * xk;
+      if (q != cq) {
+        cq = q;
+        P = ls.probs + q;
+        const Scalars* sc = P->sc;
+        zv = reinterpret_cast<const AT*>(P->z);
+        pold = reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
+        beta = (AT)sc->beta;
+        inv_n = (AT)sc->inv_n;
       }
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        AT sum = row[JP0 + kk] * qv[0];
-#pragma unroll
-        for (int a = 1; a < M; ++a) sum += row[JP0 + 3 * a + kk] * qv[a];
-        vv[kk * LD + i] = sum;
+      const int kl = k - ls.ch_base[q];
+      const int e0 = P->ch_e0[kl], e1 = P->ch_e0[kl + 1];
+      const int p0 = P->ch_p0[kl], p1 = P->ch_p0[kl + 1];
+      const int s0 = P->ch_s0[kl], s1 = P->ch_s0[kl + 1];
+      unsigned char* base = smem + st * SL.size;
+      if (lane == 0) {
+        const uint32_t bJ = (uint32_t)(e1 - e0) * RB;
+        const uintptr_t ms = reinterpret_cast<uintptr_t>(P->e_meta + e0);
+        const uintptr_t ma = ms & ~(uintptr_t)15;
+        const uint32_t skew = (uint32_t)(ms - ma);
+        const uint32_t bM = e1 > e0 ? (skew + 4u * (uint32_t)(e1 - e0) + 15u) & ~15u : 0u;
+        const uint32_t bP = (uint32_t)(p1 - p0) * PRB;
+        const uint32_t bS = (uint32_t)(s1 - s0) * 16u;
+        info[st] = StageInfo{k, q, e1 - e0, p1 - p0, s1 - s0, (int)(skew / 4)};
+        fence_proxy_async();
+        mbar_expect_tx(fb, bJ + bM + bP + bS);
+        if (bJ) bulk_g2s(smem_u32(base + SL.j), static_cast<const JT*>(P->J) + (size_t)e0 * NJ, bJ, fb);
+        if (bM) bulk_g2s(smem_u32(base + SL.meta), reinterpret_cast<const void*>(ma), bM, fb);
+        if (bP) bulk_g2s(smem_u32(base + SL.pt), static_cast<const unsigned char*>(P->pt_rec) + (size_t)p0 * PRB, bP, fb);
+        if (bS) bulk_g2s(smem_u32(base + SL.slot), P->slot_rec + s0, bS, fb);
       }
-    }
-    __syncthreads();
-    // ---- pass 2: t_p = H_pp^-1 sum_e a_e
-    for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
-      const unsigned char* pr = prec + (size_t)j * PRB;
-      const AT* hv = reinterpret_cast<const AT*>(pr);
-      const int* se = reinterpret_cast<const int*>(pr + 6 * sizeof(AT));
-      AT u[3] = {0, 0, 0};
-      for (int i = se[0]; i < se[1]; ++i) {
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) u[kk] += vv[kk * LD + i];
+      // the slot cameras' search-direction values, gathered by the whole warp
+      AT* xs = reinterpret_cast<AT*>(base + SL.xs);
+      for (int w = lane; w < (s1 - s0) * DC; w += 32) {
+        const int sl = w / DC, kk = w - sl * DC;
+        const size_t o = DB * (size_t)__ldg(&P->slot_rec[s0 + sl].z) + kk;
+        xs[w] = (zv[o] + beta * pold[o]) * inv_n;
       }
-      AT t[3];
-      mul3(hv, u, t);
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) tp[kk * LD + j] = t[kk];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(fb, 1);
+      k = __shfl_sync(0xffffffffu, lane == 0 ? next_live(k + G) : 0, 0);
     }
-    __syncthreads();
-    // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
-    for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
-      AT row[NJ];
-      load_row<NJ>(Js + (size_t)i * NJ, row);
-      const uint32_t m = meta[i];
-      const int pl = (int)(m >> 20), pos = (int)(m & 1023u);
-      const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
-      AT sv[M];
+    // let every copy issued into a stage land before the CTA can exit (already true
+    // unless a wait gave up); bounded
+    if (lane == 0) {
 #pragma unroll
-      for (int a = 0; a < M; ++a)
-        sv[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
-#pragma unroll
-      for (int kk = 0; kk < DC; ++kk) {
-        AT v = row[kk] * sv[0];
-#pragma unroll
-        for (int a = 1; a < M; ++a) v += row[a * DC + kk] * sv[a];
-        vv[kk * LD + pos] = v;
+      for (int st = 0; st < kStages; ++st)
+        if (last_use[st] >= 0) mbar_wait(smem_u32(&full[st]), (uint32_t)last_use[st] & 1u);
+      if (s_fail) atomicExch(ls.err, 1);
+    }
+  } else {
+    // ================================================================ consumer warps
+    for (int n = 0;; ++n) {
+      const int st = n % kStages;
+      const bool ok = mbar_wait(smem_u32(&full[st]), (uint32_t)(n / kStages) & 1u);
+      if (consumer_any(!ok)) {
+        if (threadIdx.x == 0) s_fail = 1;
+        break;
       }
-    }
-    __syncthreads();
-    // ---- pass 4: per-slot sums over contiguous positions
-    AT* partV = reinterpret_cast<AT*>(d.partV);
-    for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
-      const int sl = w / DC, comp = w - sl * DC;
-      const int4 r4 = srec[sl];
-      const AT* src = vv + comp * LD;
-      AT acc = (AT)0;
-      for (int qq = r4.x; qq < r4.y; ++qq) acc += src[qq];
-      partV[(size_t)r4.w * DC + comp] = acc;
-    }
-    __syncthreads();
-  }
-  if (fail_it >= 0) {
-    // let the copies already issued (the failed stage and the one after it) land
-    // before the CTA's shared memory goes away; bounded again
-    if (threadIdx.x == 0) {
-      atomicExch(ls.err, 1);
-      for (int u = fail_it; u <= fail_it + 1; ++u) {
-        const int s = u % kStages;
-        if (u > fail_it && st_k[s] < 0) break;
-        const uint32_t mb = smem_u32(&mbar[s]);
-        const uint32_t par = (uint32_t)(u / kStages) & 1u;
-        for (unsigned n = 0; n < kSpinLimit && !mbar_try_wait(mb, par); ++n) {
+      const StageInfo in = info[st];
+      if (in.k < 0) break;
+      const unsigned char* stg = smem + st * SL.size;
+      const JT* Js = reinterpret_cast<const JT*>(stg + SL.j);
+      const uint32_t* meta = reinterpret_cast<const uint32_t*>(stg + SL.meta) + in.skew;
+      const unsigned char* prec = stg + SL.pt;
+      const int4* srec = reinterpret_cast<const int4*>(stg + SL.slot);
+      const AT* xs = reinterpret_cast<const AT*>(stg + SL.xs);
+      // ---- pass 1: a_e = Jp^T (Jc x_c)
+      for (int i = threadIdx.x; i < in.nE; i += kThreads) {
+        AT row[NJ];
+        load_row<NJ>(Js + (size_t)i * NJ, row);
+        const AT* xc = xs + DC * (int)((meta[i] >> 10) & 1023u);
+        AT qv[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) qv[a] = (AT)0;
+#pragma unroll
+        for (int kk = 0; kk < DC; ++kk) {
+          const AT xk = xc[kk];
+#pragma unroll
+          for (int a = 0; a < M; ++a) qv[a] += row[a * DC + kk] * xk;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          AT sum = row[JP0 + kk] * qv[0];
+#pragma unroll
+          for (int a = 1; a < M; ++a) sum += row[JP0 + 3 * a + kk] * qv[a];
+          vv[kk * LD + i] = sum;
         }
       }
+      consumer_sync();
+      // ---- pass 2: t_p = H_pp^-1 sum_e a_e
+      for (int j = threadIdx.x; j < in.nP; j += kThreads) {
+        const unsigned char* pr = prec + (size_t)j * PRB;
+        const AT* hv = reinterpret_cast<const AT*>(pr);
+        const int* se = reinterpret_cast<const int*>(pr + 6 * sizeof(AT));
+        AT u[3];
+        point_sum<JT>(vv, LD, se[0], se[1], u);
+        AT t[3];
+        mul3(hv, u, t);
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) tp[kk * LD + j] = t[kk];
+      }
+      consumer_sync();
+      // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
+      for (int i = threadIdx.x; i < in.nE; i += kThreads) {
+        AT row[NJ];
+        load_row<NJ>(Js + (size_t)i * NJ, row);
+        const uint32_t m = meta[i];
+        const int pl = (int)(m >> 20), pos = (int)(m & 1023u);
+        const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
+        AT sv[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+          sv[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
+#pragma unroll
+        for (int kk = 0; kk < DC; ++kk) {
+          AT v = row[kk] * sv[0];
+#pragma unroll
+          for (int a = 1; a < M; ++a) v += row[a * DC + kk] * sv[a];
+          vv[kk * LD + pos] = v;
+        }
+      }
+      consumer_sync();
+      // ---- pass 4: per-slot sums over contiguous positions
+      AT* partV = reinterpret_cast<AT*>(ls.probs[in.q].partV);
+      for (int w = threadIdx.x; w < in.nS * DC; w += kThreads) {
+        const int sl = w / DC, comp = w - sl * DC;
+        const int4 r4 = srec[sl];
+        partV[(size_t)r4.w * DC + comp] = seg_sum(vv + comp * LD, r4.x, r4.y);
+      }
+      consumer_sync();
+      if (threadIdx.x == 0) mbar_arrive(smem_u32(&empty[st]), 1);
     }
-    __syncthreads();
   }
 }
 
@@ -1631,23 +1688,19 @@ struct Launch {
     else if (ept <= 4) spmv_e<JT, 4>(ls, pr, st);
     else spmv_e<JT, 8>(ls, pr, st);
   }
-  static size_t bulk_smem(Prec pr, const LaunchSet& ls) {
+  static size_t ws_smem(Prec pr, const LaunchSet& ls) {
     const StageLayout L = stage_layout<Mo>(sJ(pr), sA(pr), ls.ch_max, ls.np_max, ls.ns_max);
-    return kStages * (size_t)L.size +
-           sA(pr) * ((Dm::VW + 3) * (size_t)(ls.ch_max + 1) + Mo::DC * (size_t)ls.ns_max);
+    return kStages * (size_t)L.size + sA(pr) * (Dm::VW + 3) * (size_t)(ls.ch_max + 1);
   }
   // The staged kernel packs in-chunk positions in 10 bits and needs its stages to fit
-  // the opt-in shared memory.  It runs when asked for (variant 1): measured on the
-  // 1,000-camera BA workload it is not yet faster than the classic kernel, whose
-  // seven resident CTAs per SM hide latency better than two staged ones.
-  static bool bulk_ok(Prec pr, const LaunchSet& ls) {
-    return ls.spmv_variant == 1 && ls.ch_max <= 1024 && bulk_smem(pr, ls) <= 200 * 1024;
+  // the opt-in shared memory.
+  static bool ws_ok(Prec pr, const LaunchSet& ls) {
+    return ls.spmv_variant == 1 && ls.ch_max <= 1024 && ws_smem(pr, ls) <= 220 * 1024;
   }
   template <class JT>
-  static void bulk_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-    const size_t sm = bulk_smem(pr, ls);
-    const void* fn = reinterpret_cast<const void*>(k_spmv_bulk<Mo, JT>);
-    set_smem(fn, sm);
+  static void ws_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = ws_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_spmv_ws<Mo, JT>), sm);
     static int n_sm = 0;
     if (!n_sm) {
       int dev = 0;
@@ -1656,16 +1709,16 @@ struct Launch {
       if (n_sm <= 0) n_sm = 1;
     }
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_bulk<Mo, JT>, kThreads, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ws<Mo, JT>, kWsThreads, sm);
     const int grid = std::max(1, std::min(ls.n_ch, n_sm * std::max(occ, 1)));
-    launch_pdl(k_spmv_bulk<Mo, JT>, grid, kThreads, sm, st, ls);
+    launch_pdl(k_spmv_ws<Mo, JT>, grid, kWsThreads, sm, st, ls);
   }
   static int pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
-    if (bulk_ok(pr, ls)) {
-      if (pr == Prec::F64) bulk_t<double>(ls, pr, st);
-      else if (pr == Prec::F32) bulk_t<float>(ls, pr, st);
-      else bulk_t<__nv_bfloat16>(ls, pr, st);
+    if (ws_ok(pr, ls)) {
+      if (pr == Prec::F64) ws_t<double>(ls, pr, st);
+      else if (pr == Prec::F32) ws_t<float>(ls, pr, st);
+      else ws_t<__nv_bfloat16>(ls, pr, st);
       return 1;
     }
     if (pr == Prec::F64) spmv_t<double>(ls, pr, st);
