@@ -162,6 +162,120 @@ def spmv_algorithmic_bytes(E: int, P: int, precision: str) -> float:
     return E * (24 * sJ + 4) + P * 6 * sA
 
 
+def spmv_algorithmic_bytes_vi(E: int, P: int, precision: str) -> float:
+    """Same for the stereo model: 27 stored Jacobian values per edge (3 x 6 pose, 3 x 3
+    point; rows padded to 32 are padding, not algorithmic)."""
+    sJ = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    sA = 8 if precision == "fp64" else 4
+    return E * (27 * sJ + 4) + P * 6 * sA
+
+
+def extra_mixed_vs_fp64(args, p, params, dev, stream, main_cost: float) -> dict:
+    """The FP64 GPU path on the same workload and schedule (warm-up, then the timed
+    steps, each call starting from initial_damping): final-cost difference of the
+    benchmarked precision against it, and the FP64 rate."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp64",
+                           device=dev, stream=stream.cuda_stream)
+    g.optimize(args.warmup, params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = g.optimize(args.steps, params)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    g.close()
+    return dict(fp64_final_cost=rep.final_cost, final_cost=main_cost, precision=args.precision,
+                rel_diff=abs(main_cost - rep.final_cost) / rep.final_cost,
+                fp64_lm_iter_per_s=args.steps / dt)
+
+
+def extra_vi(dev, stream, iters: int = 10) -> dict:
+    """Global visual-inertial workload (3,000 stereo keyframes, 200,000 landmarks, ~1.9M
+    stereo edges, inertial + bias random-walk edges between consecutive keyframes, bias
+    prior): LM iterations per second in FP64, FP32 and BF16 storage, the Schur product's
+    achieved bandwidth, and the final-cost difference of each mixed form against FP64.
+    PCG <= 100 iterations at 1e-6 relative, rejection-ratio guard off (the inertial
+    chain makes the PCG residual rise before it falls)."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo, synth
+    p = synth.vi_global()
+    params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6, pcg_rejection_ratio=0.0)
+    peak, peak_kind = load_peaks()
+    out = dict(workload=p.name, keyframes=p.n_kf, landmarks=p.n_pts, stereo_edges=p.n_edges,
+               lm_iters=iters)
+    costs = {}
+    for prec in ("fp64", "fp32", "bf16"):
+        g, _, _, _ = gpo.vi_graph(p, precision=prec, device=dev, stream=stream.cuda_stream)
+        g.optimize(1, params)                     # finalize + warm
+        g.set_initial(0, p.nav0)
+        g.set_initial(p.n_kf, p.pts0)
+        g.set_profiling(True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        rep = g.optimize(iters, params)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        prof = g.profile()
+        sp = prof["spmv"]
+        spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
+        alg = spmv_algorithmic_bytes_vi(p.n_edges, p.n_pts, prec)
+        gbs = alg / (spmv_ms * 1e-3) / 1e9 if sp["active"] else 0.0
+        costs[prec] = rep.final_cost
+        out[prec] = dict(lm_iter_per_s=iters / (ms / 1e3), initial_cost=rep.initial_cost,
+                         final_cost=rep.final_cost, accepted=rep.accepted,
+                         pcg_iters=rep.pcg_iters_total, footprint_bytes=g.footprint(),
+                         spmv=dict(avg_ms=spmv_ms, achieved_gbs=gbs, frac=gbs / peak, peak=peak,
+                                   peak_source=peak_kind))
+        g.close()
+    for prec in ("fp32", "bf16"):
+        out[prec]["rel_diff_vs_fp64"] = abs(costs[prec] - costs["fp64"]) / costs["fp64"]
+        out[prec]["speedup_vs_fp64"] = out[prec]["lm_iter_per_s"] / out["fp64"]["lm_iter_per_s"]
+    return out
+
+
+def extra_served(stream, rate: float = 2000.0, duration: float = 1.0, pool: int = 48,
+                 sample: int = 48) -> dict:
+    """Served local-BA windows: a Poisson stream (rate per second over `duration`) of
+    requests, each a window of the pool (5-40 keyframes, 300-8,000 landmarks, 2k-60k
+    edges; first keyframe fixed), 10 LM iterations in BF16 storage under a 40 GB budget,
+    through the continuous-batching server; against the same windows solved one by one
+    with the plain FP64 path (a sample of the requests)."""
+    import numpy as np
+
+    from paper_2509_26581_gb300 import serving, synth
+    windows = synth.window_pool(7, pool)
+    arr = synth.poisson_arrivals(8, rate, duration)
+    pick = np.arange(len(arr)) % pool
+    edges = np.array([w.n_edges for w in windows])
+    r = serving.serve(windows, arr, pick, precision="bf16", lm_iters=10, stream=stream.cuda_stream)
+    b = serving.one_by_one(windows, pick[:sample], precision="fp64", lm_iters=10)
+    a = serving.one_by_one(windows, pick[:sample], precision="bf16", lm_iters=10)
+    rel = np.abs(r["final_cost"][:sample] - b["final_cost"]) / b["final_cost"]
+    same = np.abs(r["final_cost"][:sample] - a["final_cost"]) / a["final_cost"]
+    # the served FP64 form against the plain FP64 path (same windows)
+    r64 = serving.serve(windows[:sample], arr[:sample], np.arange(sample), precision="fp64", lm_iters=10,
+                        stream=stream.cuda_stream)
+    b64 = serving.one_by_one(windows[:sample], np.arange(sample), precision="fp64", lm_iters=10)
+    same64 = np.abs(r64["final_cost"] - b64["final_cost"]) / b64["final_cost"]
+    return dict(requests=int(len(arr)), rate_per_s=rate, window_edges=[int(edges.min()), int(edges.max())],
+                precision="bf16", lm_iters=10, budget_gb=40,
+                solves_per_s=r["solves_per_s"], p50_s=r["p50"], p99_s=r["p99"],
+                max_resident=r["max_resident"], seconds=r["seconds"],
+                one_by_one_fp64_solves_per_s=b["solves_per_s"],
+                speedup_vs_one_by_one_fp64=r["solves_per_s"] / b["solves_per_s"],
+                max_rel_cost_diff_served_vs_alone_same_precision=float(same.max()),
+                max_rel_cost_diff_served_fp64_vs_plain_fp64=float(same64.max()),
+                max_rel_cost_diff_vs_fp64=float(rel.max()), median_rel_cost_diff_vs_fp64=float(np.median(rel)),
+                note="after 10 LM iterations the windows are not converged, so BF16 and FP64 "
+                     "trajectories end at different costs; the served form equals the same "
+                     "precision solved alone")
+
+
 def run_ours(args, rank: int, world: int, dist) -> dict | None:
     import numpy as np
     import torch
@@ -256,6 +370,11 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items()},
         footprint_bytes=g.footprint(),
     )
+    if not args.no_extras and world == 1:
+        g.close()
+        line["mixed_vs_fp64"] = extra_mixed_vs_fp64(args, p, params, dev, stream, rep.final_cost)
+        line["vi"] = extra_vi(dev, stream)
+        line["served"] = extra_served(stream)
     return line
 
 
@@ -294,6 +413,8 @@ def main():
                     help="Schur-product kernel (a tuning knob; results are bit-identical)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 comparison, the visual-inertial and the served-windows measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

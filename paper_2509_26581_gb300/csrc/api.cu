@@ -382,6 +382,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
     *plan_bytes = bytes;
     return GPO_OK;
   }
+  if (gpo_status s = ensure_stream(g); s != GPO_OK) return s;
   if (g->desc.memory_budget && bytes > g->desc.memory_budget)
     return fail(g, GPO_ERR_OOM, "graph needs %zu bytes of device memory, budget is %zu", bytes,
                 (size_t)g->desc.memory_budget);
@@ -551,6 +552,7 @@ void gpo_host::fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda,
 }
 
 gpo_status gpo_host::upload_scalars(gpo_graph* g, const Scalars& s) {
+  if (gpo_status st = ensure_runtime(g); st != GPO_OK) return st;
   *g->h_sc = s;
   GPO_CUDA(g, cudaMemcpyAsync(g->dev.sc, g->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, g->stream));
   // the pinned staging buffer is reused: make sure the copy has been consumed
@@ -562,6 +564,7 @@ gpo_status gpo_host::upload_scalars(gpo_graph* g, const Scalars& s) {
 // group the done flag is copied back, and the flag of the previous group decides
 // whether to launch more (one group of look-ahead keeps the GPU busy).
 static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) {
+  if (gpo_status s = gpo_host::ensure_runtime(g); s != GPO_OK) return s;
   const int kGroup = 8;
   int launched = 0, slot = 0, pending = -1;
   while (launched < max_it) {
@@ -640,17 +643,47 @@ gpo_lm_params gpo_host::params_or_default(const gpo_lm_params* p) {
   return p ? *p : d;
 }
 
-gpo_status gpo_host::download_state(gpo_graph* g) {
+gpo_status gpo_host::download_begin(gpo_graph* g, std::vector<double>& pts) {
   if (!g->finalized) return GPO_OK;
   const DevBA& d = g->dev;
-  std::vector<double> pts(3 * (size_t)d.P);
+  pts.resize(3 * (size_t)d.P);
   if (d.C) GPO_CUDA(g, cudaMemcpyAsync(g->cam_state.data(), d.cam, (size_t)cam_ss(g) * d.C * sizeof(double),
                                       cudaMemcpyDeviceToHost, g->stream));
   if (d.P) GPO_CUDA(g, cudaMemcpyAsync(pts.data(), d.pt, 3 * (size_t)d.P * sizeof(double),
                                       cudaMemcpyDeviceToHost, g->stream));
-  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
-  for (int p = 0; p < d.P; ++p)
+  return GPO_OK;
+}
+
+void gpo_host::download_end(gpo_graph* g, const std::vector<double>& pts) {
+  if (!g->finalized) return;
+  for (int p = 0; p < g->dev.P; ++p)
     for (int k = 0; k < 3; ++k) g->pt_state[3 * (size_t)p + k] = pts[3 * (size_t)g->pt_old2new[p] + k];
+}
+
+gpo_status gpo_host::download_state(gpo_graph* g) {
+  std::vector<double> pts;
+  gpo_status s = download_begin(g, pts);
+  if (s != GPO_OK) return s;
+  if (g->finalized) GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  download_end(g, pts);
+  return GPO_OK;
+}
+
+gpo_status gpo_host::ensure_stream(gpo_graph* g) {
+  if (g->stream) return GPO_OK;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  GPO_CUDA(g, cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+  g->own_stream = true;
+  return GPO_OK;
+}
+
+gpo_status gpo_host::ensure_runtime(gpo_graph* g) {
+  if (g->h_sc) return GPO_OK;
+  if (gpo_status s = ensure_stream(g); s != GPO_OK) return s;
+  GPO_CUDA(g, cudaMallocHost(&g->h_flag, 4 * sizeof(int)));
+  GPO_CUDA(g, cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming));
+  GPO_CUDA(g, cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming));
+  GPO_CUDA(g, cudaMallocHost(&g->h_sc, sizeof(Scalars)));   // last: marks the runtime as ready
   return GPO_OK;
 }
 
@@ -703,23 +736,9 @@ gpo_status gpo_graph_create(const gpo_graph_desc* desc, gpo_graph** out) {
   if (!g) return fail(nullptr, GPO_ERR_OOM, "host allocation failed");
   g->desc = *desc;
   g->prec = static_cast<Prec>(desc->precision);
-  e = cudaSetDevice(desc->device);
-  if (e == cudaSuccess) {
-    if (desc->cuda_stream) {
-      g->stream = static_cast<cudaStream_t>(desc->cuda_stream);
-    } else {
-      e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
-      g->own_stream = true;
-    }
-  }
-  if (e == cudaSuccess) e = cudaMallocHost(&g->h_sc, sizeof(Scalars));
-  if (e == cudaSuccess) e = cudaMallocHost(&g->h_flag, 4 * sizeof(int));
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    gpo_graph_destroy(g);
-    return fail(nullptr, GPO_ERR_CUDA, "graph setup failed: %s", cudaGetErrorString(e));
-  }
+  // the stream, pinned staging and events are created at the first finalize (a graph
+  // handed to a server runs on the server's stream and never needs its own)
+  if (desc->cuda_stream) g->stream = static_cast<cudaStream_t>(desc->cuda_stream);
   if (desc->reserve_vertices > 0) {
     g->v_kind.reserve(desc->reserve_vertices);
     g->v_local.reserve(desc->reserve_vertices);

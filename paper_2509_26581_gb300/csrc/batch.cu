@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <new>
 #include <unordered_map>
 #include <vector>
@@ -140,6 +141,53 @@ void report_from(const Scalars& s, double initial_cost, gpo_report* r) {
   r->reserved0 = 0;
 }
 
+// Device-memory pool of a server: arenas of retired graphs are kept (keyed by size,
+// 1 MiB granularity) and handed to the next admitted graphs, so the serving loop does
+// not pay cudaMalloc / cudaFree (which synchronises the device) per request.
+struct DevPool {
+  std::multimap<size_t, void*> free_blocks;
+  std::unordered_map<void*, size_t> block_size;
+  size_t held = 0;   // bytes obtained from cudaMalloc and not yet returned
+
+  void trim() {
+    for (auto& kv : free_blocks) {
+      cudaFree(kv.second);
+      held -= kv.first;
+      block_size.erase(kv.second);
+    }
+    free_blocks.clear();
+  }
+};
+
+void* pool_alloc(size_t bytes, void* ctx) {
+  DevPool* pool = static_cast<DevPool*>(ctx);
+  const size_t b = (bytes + (size_t(1) << 20) - 1) & ~((size_t(1) << 20) - 1);
+  auto it = pool->free_blocks.lower_bound(b);
+  if (it != pool->free_blocks.end() && it->first <= 2 * b) {   // reuse a block at most twice as big
+    void* p = it->second;
+    pool->free_blocks.erase(it);
+    return p;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, b) != cudaSuccess) {
+    cudaGetLastError();
+    pool->trim();
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  pool->block_size[p] = b;
+  pool->held += b;
+  return p;
+}
+
+void pool_free(void* p, void* ctx) {
+  DevPool* pool = static_cast<DevPool*>(ctx);
+  auto it = pool->block_size.find(p);
+  if (it != pool->block_size.end()) pool->free_blocks.emplace(it->second, p);
+}
+
 }  // namespace
 
 // ============================================================== serving loop state
@@ -155,7 +203,10 @@ struct gpo_server {
     int done_iters;
     size_t bytes;
     double initial_cost;
+    gpo_graph_desc saved;   // the graph's own stream and allocator, restored at retirement
+    bool adopted_stream;
   };
+  DevPool pool;
   std::deque<Req> queue;
   std::vector<Req> resident;
   std::unordered_map<int64_t, gpo_report> finished;
@@ -252,6 +303,10 @@ gpo_status gpo_server_create(const gpo_server_desc* desc, gpo_server** out) {
   gpo_graph* owner = nullptr;
   gpo_status s = gpo_graph_create(&gd, &owner);
   if (s != GPO_OK) return s;
+  if ((s = ensure_runtime(owner)) != GPO_OK) {
+    gpo_graph_destroy(owner);
+    return s;
+  }
   gpo_server* sv = new (std::nothrow) gpo_server();
   if (!sv) {
     gpo_graph_destroy(owner);
@@ -263,11 +318,25 @@ gpo_status gpo_server_create(const gpo_server_desc* desc, gpo_server** out) {
   return GPO_OK;
 }
 
+// Gives a graph back its own stream and allocator after the server is done with it.
+static void restore_graph(gpo_server::Req& r) {
+  r.g->desc.alloc = r.saved.alloc;
+  r.g->desc.free = r.saved.free;
+  r.g->desc.alloc_ctx = r.saved.alloc_ctx;
+  if (r.adopted_stream) r.g->stream = nullptr;
+}
+
 gpo_status gpo_server_destroy(gpo_server* sv) {
   if (!sv) return GPO_OK;
   cudaStreamSynchronize(sv->owner->stream);
-  for (auto& r : sv->resident) release_device(r.g);
+  for (auto& r : sv->resident) {
+    release_device(r.g);
+    restore_graph(r);
+  }
+  for (auto& r : sv->queue) restore_graph(r);
   sv->set.release(sv->owner->stream);
+  cudaStreamSynchronize(sv->owner->stream);
+  sv->pool.trim();
   gpo_graph_destroy(sv->owner);
   delete sv;
   return GPO_OK;
@@ -292,7 +361,18 @@ gpo_status gpo_server_submit(gpo_server* sv, gpo_graph* g, int32_t max_iters, co
     return fail(sv->owner, GPO_ERR_OOM, "graph needs %zu bytes, more than the server budget %zu", bytes,
                 (size_t)sv->desc.memory_budget);
   sv->owner->ks = k;
-  gpo_server::Req r{g, max_iters, params_or_default(params), sv->next_ticket++, 0, bytes, 0.0};
+  gpo_server::Req r{g, max_iters, params_or_default(params), sv->next_ticket++, 0, bytes, 0.0, g->desc, false};
+  // a graph without a stream of its own runs on the server's; a graph without an
+  // allocator hook takes its arena from the server's pool
+  if (!g->stream) {
+    g->stream = sv->owner->stream;
+    r.adopted_stream = true;
+  }
+  if (!g->desc.alloc) {
+    g->desc.alloc = pool_alloc;
+    g->desc.free = pool_free;
+    g->desc.alloc_ctx = &sv->pool;
+  }
   sv->queue.push_back(r);
   if (ticket) *ticket = r.ticket;
   return GPO_OK;
@@ -303,8 +383,10 @@ gpo_status gpo_server_step(gpo_server* sv, int32_t* n_resident, int32_t* n_queue
   gpo_graph* owner = sv->owner;
   GPO_CUDA(owner, cudaSetDevice(owner->desc.device));
   int fin = 0;
-  // 1. admission: first come, first served, while slots and memory allow
-  while (!sv->queue.empty() && (int)sv->resident.size() < sv->desc.max_resident) {
+  // 1. admission: first come, first served, while slots and memory allow; the new
+  //    graphs' initial costs are computed together in shared launches
+  std::vector<gpo_server::Req> adm;
+  while (!sv->queue.empty() && (int)(sv->resident.size() + adm.size()) < sv->desc.max_resident) {
     gpo_server::Req r = sv->queue.front();
     if (sv->desc.memory_budget && sv->used + r.bytes > sv->desc.memory_budget) break;
     gpo_status s = finalize(r.g);
@@ -312,27 +394,35 @@ gpo_status gpo_server_step(gpo_server* sv, int32_t* n_resident, int32_t* n_queue
       owner->err = r.g->err;
       return s;
     }
-    Scalars sc;
-    fill_scalars(r.g, r.prm, r.prm.initial_damping, sc);
-    if ((s = upload_scalars(r.g, sc)) != GPO_OK) return s;
-    if ((s = launch_initial_cost(r.g, r.g->ls)) != GPO_OK) return s;
-    GPO_CUDA(owner, cudaMemcpyAsync(r.g->h_sc, r.g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, r.g->stream));
-    GPO_CUDA(owner, cudaStreamSynchronize(r.g->stream));
-    r.initial_cost = r.g->h_sc->cost;
     sv->used += r.g->arena_bytes;
     sv->queue.pop_front();
-    if (r.max_iters == 0 || !std::isfinite(r.initial_cost)) {
-      gpo_report rep;
-      report_from(*r.g->h_sc, r.initial_cost, &rep);
-      sv->finished[r.ticket] = rep;
-      download_state(r.g);
-      sv->used -= r.g->arena_bytes;
-      release_device(r.g);
-      ++fin;
-      continue;
+    adm.push_back(r);
+  }
+  std::vector<gpo_server::Req> retire;   // graphs leaving the device this step
+  if (!adm.empty()) {
+    std::vector<gpo_graph*> gs;
+    for (auto& r : adm) gs.push_back(r.g);
+    BatchSet bs;
+    gpo_status s = build_set(owner, gs, bs);
+    if (s != GPO_OK) return s;
+    std::vector<Scalars> sc(adm.size());
+    for (size_t i = 0; i < adm.size(); ++i) fill_scalars(adm[i].g, adm[i].prm, adm[i].prm.initial_damping, sc[i]);
+    if ((s = put_scalars(owner, bs, sc)) == GPO_OK && (s = launch_initial_cost(owner, bs.ls)) == GPO_OK)
+      s = get_scalars(owner, bs, sc);
+    bs.release(owner->stream);
+    if (s != GPO_OK) return s;
+    for (size_t i = 0; i < adm.size(); ++i) {
+      adm[i].initial_cost = sc[i].cost;
+      if (adm[i].max_iters == 0 || !std::isfinite(adm[i].initial_cost)) {
+        gpo_report rep;
+        report_from(sc[i], adm[i].initial_cost, &rep);
+        sv->finished[adm[i].ticket] = rep;
+        retire.push_back(adm[i]);
+      } else {
+        sv->resident.push_back(adm[i]);
+        sv->dirty = true;
+      }
     }
-    sv->resident.push_back(r);
-    sv->dirty = true;
   }
   if (!sv->resident.empty()) {
     // 2. one LM iteration for every resident graph, in shared launches
@@ -369,13 +459,28 @@ gpo_status gpo_server_step(gpo_server* sv, int32_t* n_resident, int32_t* n_queue
         sv->finished[r.ticket] = rep;
         r.g->last_cost = sc[i].cost;
         r.g->cost_valid = true;
-        if ((s = download_state(r.g)) != GPO_OK) return s;
-        sv->used -= r.g->arena_bytes;
-        release_device(r.g);
-        ++fin;
+        retire.push_back(r);
       }
       sv->resident.swap(keep);
       sv->dirty = true;
+    }
+  }
+  if (!retire.empty()) {
+    // final states back to the graphs' host arrays: all copies, then one wait
+    std::vector<std::vector<double>> pts(retire.size());
+    for (size_t i = 0; i < retire.size(); ++i) {
+      gpo_status s = download_begin(retire[i].g, pts[i]);
+      if (s != GPO_OK) return s;
+    }
+    GPO_CUDA(owner, cudaStreamSynchronize(owner->stream));
+    for (size_t i = 0; i < retire.size(); ++i) {
+      gpo_server::Req& r = retire[i];
+      if (r.g->stream != owner->stream) GPO_CUDA(owner, cudaStreamSynchronize(r.g->stream));
+      download_end(r.g, pts[i]);
+      sv->used -= r.g->arena_bytes;
+      release_device(r.g);
+      restore_graph(r);
+      ++fin;
     }
   }
   if (n_resident) *n_resident = (int32_t)sv->resident.size();

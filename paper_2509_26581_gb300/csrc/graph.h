@@ -127,6 +127,14 @@ gpo_status launch_initial_cost(gpo_graph* g, const gpo::LaunchSet& ls);
 void prof_resolve(gpo_graph* g);
 // Copies the final device state back into the graph's host arrays (user order).
 gpo_status download_state(gpo_graph* g);
+// The same in two halves: enqueue the copies (points into `pts`), then, after the
+// caller has synchronised the graph's stream, scatter the points to user order.
+gpo_status download_begin(gpo_graph* g, std::vector<double>& pts);
+void download_end(gpo_graph* g, const std::vector<double>& pts);
+// Creates the graph's stream unless one was given or adopted (done by the first full
+// finalize), and its pinned staging and events (done by the calls that need them).
+gpo_status ensure_stream(gpo_graph* g);
+gpo_status ensure_runtime(gpo_graph* g);
 
 }  // namespace gpo_host
 
