@@ -138,7 +138,7 @@ def load_peaks() -> tuple[float, str]:
 # was taken from (keyed by a hash of them): changed kernels report null.
 MEASURED_TRAFFIC = {}
 SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2}
-KERNEL_SOURCES = ("schur_common.cuh", "schur_kernels.cuh", "ba_kernels.cu")
+KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -276,6 +276,52 @@ def extra_served(stream, rate: float = 2000.0, duration: float = 1.0, pool: int 
                      "precision solved alone")
 
 
+def run_vi(args, dev, stream, world: int) -> dict:
+    """The global visual-inertial workload as the measured loop (--workload vi_global;
+    used for its own launch lists and profiles): K LM iterations after W warm-up ones."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo, synth
+    p = synth.vi_global()
+    params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6, pcg_rejection_ratio=0.0)
+    g, _, _, _ = gpo.vi_graph(p, precision=args.precision, device=dev, stream=stream.cuda_stream,
+                              chunk_edges=args.chunk, spmv_variant=SPMV_VARIANTS[args.spmv])
+    g.optimize(args.warmup, params)
+    torch.cuda.synchronize()
+    g.set_profiling(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rep = g.optimize(args.steps, params)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = g.profile()
+    sp = prof["spmv"]
+    peak, peak_kind = load_peaks()
+    alg = spmv_algorithmic_bytes_vi(p.n_edges, p.n_pts, args.precision)
+    spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
+    achieved = alg / (spmv_ms * 1e-3) / 1e9 if sp["active"] else 0.0
+    return dict(
+        metric=METRIC, value=world * args.steps / (ms / 1e3), unit="LM iter/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype={"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
+        data="synthetic",
+        config=dict(workload=p.name, precision=args.precision, keyframes=p.n_kf, landmarks=p.n_pts,
+                    stereo_edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, pcg_rejection_ratio="off",
+                    chunk_edges=args.chunk or "default", spmv_kernel=args.spmv,
+                    parallelism=f"replicas x{world}"),
+        gpu_launches=int(sum(v["launches"] for v in prof.values())),
+        roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
+                      kernel="k_spmv (PCG Schur product)", peak_source=peak_kind, algorithmic_bytes=alg,
+                      avg_ms=spmv_ms),
+        clocks=clk, final_cost=rep.final_cost,
+        kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items()},
+        footprint_bytes=g.footprint())
+
+
 def run_ours(args, rank: int, world: int, dist) -> dict | None:
     import numpy as np
     import torch
@@ -286,6 +332,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     torch.cuda.set_device(local % max(1, torch.cuda.device_count()))
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
+    if args.workload == "vi_global":
+        return run_vi(args, dev, stream, world)
     p = synth.ba_medium(args.seed)
     params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
     g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
@@ -413,6 +461,9 @@ def main():
                     help="Schur-product kernel (a tuning knob; results are bit-identical)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--workload", default="ba_medium", choices=["ba_medium", "vi_global"],
+                    help="the measured loop: the 1,000-camera BA workload (default) or the global "
+                         "visual-inertial one (for its profiles)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, the visual-inertial and the served-windows measurements")
     args = ap.parse_args()
@@ -424,7 +475,7 @@ def main():
             print(json.dumps(line))
         return
     base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "ba_medium":
         base = cpu_baseline(args.seed)          # before any GPU work in this process
     dist = None
     if world > 1:

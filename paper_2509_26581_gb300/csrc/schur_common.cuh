@@ -558,4 +558,63 @@ struct ModelStereo {
   }
 };
 
+// ---------------------------------------------------------------- model sizes and shared helpers
+
+template <class Mo>
+struct Dims {
+  static constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, SS = Mo::SS, NJ = Mo::NJ;
+  static constexpr int JP0 = M * DC;            // first point-row value of a Jacobian row
+  static constexpr int NJU = JP0 + 3 * M;       // values in use (the rest is padding)
+  static constexpr int TC = tri_n(DC);          // H entries of a slot partial
+  static constexpr int NA = TC + DC;            // H + b entries of a slot partial
+  static constexpr int NG = (NA + 8) / 9;       // groups of nine
+  static constexpr int NPA = 9 * NG;            // slot partial row
+  static constexpr int TB = tri_n(DB);          // packed camera block
+  static constexpr int TM = tri_n(M);           // packed M x M point-side weights
+  static constexpr int VW = DC > 3 ? DC : 3;    // rows of the Schur-product scratch
+  static_assert(NJ % 8 == 0 && NJU <= NJ, "Jacobian rows are whole 16-byte vectors");
+  static_assert(DB <= 32, "one lane per camera-block component");
+};
+
+template <class AT>
+__device__ __forceinline__ void mul3(const AT* h, const AT* v, AT* o) {
+  o[0] = h[0] * v[0] + h[1] * v[1] + h[2] * v[2];
+  o[1] = h[1] * v[0] + h[3] * v[1] + h[4] * v[2];
+  o[2] = h[2] * v[0] + h[4] * v[1] + h[5] * v[2];
+}
+
+// Sum of src[a .. b) with four interleaved partial sums (more loads in flight than a
+// single running sum), combined as (s0 + s1) + (s2 + s3).
+template <class AT>
+__device__ __forceinline__ AT seg_sum(const AT* src, int a, int b) {
+  AT s0 = (AT)0, s1 = (AT)0, s2 = (AT)0, s3 = (AT)0;
+  int q = a;
+  for (; q + 4 <= b; q += 4) {
+    s0 += src[q];
+    s1 += src[q + 1];
+    s2 += src[q + 2];
+    s3 += src[q + 3];
+  }
+  for (; q < b; ++q) s0 += src[q];
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Point sums of the Schur product's pass 2: u_k = sum_{i in [a, b)} v[k LD + i].  FP32
+// storage takes the interleaved sums (measured faster on the 1,000-camera BA workload);
+// BF16 and FP64 keep one running sum per component (the interleaved form raises their
+// register count past six resident CTAs per SM, which costs more than it gains).
+template <class JT, class AT>
+__device__ __forceinline__ void point_sum(const AT* v, int LD, int a, int b, AT (&u)[3]) {
+  if constexpr (std::is_same<JT, float>::value) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = seg_sum(v + k * LD, a, b);
+  } else {
+    u[0] = u[1] = u[2] = (AT)0;
+    for (int i = a; i < b; ++i) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] += v[k * LD + i];
+    }
+  }
+}
+
 }  // namespace gpo

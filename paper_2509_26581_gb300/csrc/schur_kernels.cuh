@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "schur_common.cuh"
+#include "schur_spmv.cuh"
 
 namespace gpo {
 
@@ -47,22 +48,6 @@ __device__ __forceinline__ int tri_col(int t) {
   else return c_t6j[t];
 }
 
-template <class Mo>
-struct Dims {
-  static constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, SS = Mo::SS, NJ = Mo::NJ;
-  static constexpr int JP0 = M * DC;            // first point-row value of a Jacobian row
-  static constexpr int NJU = JP0 + 3 * M;       // values in use (the rest is padding)
-  static constexpr int TC = tri_n(DC);          // H entries of a slot partial
-  static constexpr int NA = TC + DC;            // H + b entries of a slot partial
-  static constexpr int NG = (NA + 8) / 9;       // groups of nine
-  static constexpr int NPA = 9 * NG;            // slot partial row
-  static constexpr int TB = tri_n(DB);          // packed camera block
-  static constexpr int TM = tri_n(M);           // packed M x M point-side weights
-  static constexpr int VW = DC > 3 ? DC : 3;    // rows of the Schur-product scratch
-  static_assert(NJ % 8 == 0 && NJU <= NJ, "Jacobian rows are whole 16-byte vectors");
-  static_assert(DB <= 32, "one lane per camera-block component");
-};
-
 // ---------------------------------------------------------------- small dense helpers
 
 // 3x3 SPD inverse by cofactors; h = (a b c d e f) packed upper triangle.
@@ -81,13 +66,6 @@ __device__ __forceinline__ void inv3(const AT* h, AT* o) {
     o[5] = f > (AT)0 ? (AT)1 / f : (AT)0;
     o[1] = o[2] = o[4] = (AT)0;
   }
-}
-
-template <class AT>
-__device__ __forceinline__ void mul3(const AT* h, const AT* v, AT* o) {
-  o[0] = h[0] * v[0] + h[1] * v[1] + h[2] * v[2];
-  o[1] = h[1] * v[0] + h[3] * v[1] + h[4] * v[2];
-  o[2] = h[2] * v[0] + h[4] * v[1] + h[5] * v[2];
 }
 
 template <class AT>
@@ -146,40 +124,6 @@ __device__ void warp_spd_inverse(const AT* A, AT* M, int lane) {
   } else if (lane < N) {
     for (int j = lane; j < N; ++j) M[tri_idx(N, lane, j)] = (AT)0;
     M[tri_idx(N, lane, lane)] = dii > (AT)0 ? (AT)1 / dii : (AT)1;
-  }
-}
-
-// Sum of src[a .. b) with four interleaved partial sums (more loads in flight than a
-// single running sum), combined as (s0 + s1) + (s2 + s3).
-template <class AT>
-__device__ __forceinline__ AT seg_sum(const AT* src, int a, int b) {
-  AT s0 = (AT)0, s1 = (AT)0, s2 = (AT)0, s3 = (AT)0;
-  int q = a;
-  for (; q + 4 <= b; q += 4) {
-    s0 += src[q];
-    s1 += src[q + 1];
-    s2 += src[q + 2];
-    s3 += src[q + 3];
-  }
-  for (; q < b; ++q) s0 += src[q];
-  return (s0 + s1) + (s2 + s3);
-}
-
-// Point sums of the Schur product's pass 2: u_k = sum_{i in [a, b)} v[k LD + i].  FP32
-// storage takes the interleaved sums (measured faster on the 1,000-camera BA workload);
-// BF16 and FP64 keep one running sum per component (the interleaved form raises their
-// register count past six resident CTAs per SM, which costs more than it gains).
-template <class JT, class AT>
-__device__ __forceinline__ void point_sum(const AT* v, int LD, int a, int b, AT (&u)[3]) {
-  if constexpr (std::is_same<JT, float>::value) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) u[k] = seg_sum(v + k * LD, a, b);
-  } else {
-    u[0] = u[1] = u[2] = (AT)0;
-    for (int i = a; i < b; ++i) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) u[k] += v[k * LD + i];
-    }
   }
 }
 
@@ -566,7 +510,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
   const AT lam = (AT)sc->lambda;
   const AT* partA = reinterpret_cast<const AT*>(d.partA);
   const AT* partB = reinterpret_cast<const AT*>(d.partB);
-  double rz_c = 0.0, rr_c = 0.0;
+  AT rz_c = (AT)0, rr_c = (AT)0;   // per-warp partials in AT, accumulated across warps in FP64
   if (c < d.C) {
     const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
     // 2 NG groups of nine outputs; lanes stride over the camera's slots, then a fixed
@@ -677,8 +621,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
       reinterpret_cast<AT*>(d.z)[DB * (size_t)c + lane] = zi;
       reinterpret_cast<AT*>(d.p)[DB * (size_t)c + lane] = (AT)0;   // p_{-1}: p_0 = z_0
       const AT gi = g[lane];
-      rz_c = (double)gi * (double)zi;
-      rr_c = (double)gi * (double)gi;
+      rz_c = gi * zi;
+      rr_c = gi * gi;
     }
   }
 #pragma unroll
@@ -687,8 +631,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     rr_c += __shfl_down_sync(0xffffffffu, rr_c, o);
   }
   if (lane == 0) {
-    red[warp][0] = rz_c;
-    red[warp][1] = rr_c;
+    red[warp][0] = (double)rz_c;
+    red[warp][1] = (double)rr_c;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -722,413 +666,6 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
 
 // ---------------------------------------------------------------- PCG
 
-// Matrix-free Schur product, one CTA per chunk (the hot loop).  With t_p =
-// H_pp^-1 sum_e Jp_e^T Jc_e x_c(e), each edge contributes v_e = Jc_e^T Jp_e t_p(e) to
-// its camera.  The CTA first issues its index loads, stages the camera vector of
-// each slot once (instead of once per edge), the point inverses, point offsets and
-// slot ranges, then runs barrier-separated passes in shared memory: per-edge point
-// terms, point sums, per-edge camera terms scattered to slot-sorted positions, and
-// contiguous per-slot sums.  Each chunk's Jacobian rows are read twice, the second
-// time mostly from L1/L2.
-template <class Mo, class JT, int EPT>
-__global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
-  using AT = typename AccOf<JT>::T;
-  using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
-  GPO_BIND(ch, kl)
-  if (!d.sc->active || d.sc->pcg_done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int CH = d.ch_max, LD = CH + 1;
-  AT* vv = reinterpret_cast<AT*>(smem);        // [VW][LD]; rows 0..2 hold a_e in pass 1
-  AT* tp = vv + VW * LD;                       // [3][LD] point solutions
-  AT* xs = tp + 3 * LD;                        // [ls.ns_max][DC] slot camera vectors
-  AT* hv = xs + DC * ls.ns_max;                // [ls.np_max][6] point inverses
-  int* po = reinterpret_cast<int*>(hv + 6 * ls.np_max);   // [np + 1] local point offsets
-  int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
-  int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
-  const ChunkRange cr = chunk_range(d, kl);
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
-
-  int pos[EPT], slot[EPT], ptl[EPT];
-#pragma unroll
-  for (int m = 0; m < EPT; ++m) {
-    const int i = threadIdx.x + m * kThreads;
-    if (i < cr.nE) {
-      pos[m] = __ldg(d.e_pos + cr.e0 + i);
-      slot[m] = __ldg(d.e_slot + cr.e0 + i);
-      ptl[m] = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
-    }
-  }
-  // the search direction p_k = (z_k + beta_k p_{k-1}) / n_k, formed per slot camera
-  const AT* zv = reinterpret_cast<const AT*>(d.z);
-  const AT* pold = reinterpret_cast<const AT*>(d.sc->pidx ? d.p2 : d.p);
-  const AT beta = (AT)d.sc->beta, inv_n = (AT)d.sc->inv_n;
-  for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
-    const int sl = w / DC, k = w - sl * DC;
-    const size_t o = DB * (size_t)__ldg(d.slot_cam + cr.s0 + sl) + k;
-    xs[w] = (zv[o] + beta * pold[o]) * inv_n;
-  }
-  for (int t = threadIdx.x; t < cr.nS; t += kThreads) sp[t] = __ldg(d.slot_pos + cr.s0 + t);
-  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv) + 6 * (size_t)cr.p0;
-  for (int w = threadIdx.x; w < cr.nP * 6; w += kThreads) hv[w] = Hinv[w];
-  for (int j = threadIdx.x; j <= cr.nP; j += kThreads) po[j] = __ldg(d.pt_off + cr.p0 + j) - cr.e0;
-  for (int t = threadIdx.x; t <= cr.nS; t += kThreads) so[t] = __ldg(d.slot_e0 + cr.s0 + t) - cr.e0;
-  __syncthreads();
-
-  // ---- pass 1: a_e = Jp^T (Jc x_c)
-#pragma unroll
-  for (int m = 0; m < EPT; ++m) {
-    const int i = threadIdx.x + m * kThreads;
-    if (i >= cr.nE) break;
-    AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
-    const AT* xc = xs + DC * slot[m];
-    AT q[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) q[a] = (AT)0;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-      const AT xk = xc[k];
-#pragma unroll
-      for (int a = 0; a < M; ++a) q[a] += row[a * DC + k] * xk;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      AT s = row[JP0 + k] * q[0];
-#pragma unroll
-      for (int a = 1; a < M; ++a) s += row[JP0 + 3 * a + k] * q[a];
-      vv[k * LD + i] = s;
-    }
-  }
-  __syncthreads();
-  // ---- pass 2: t_p = H_pp^-1 sum_e a_e
-  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
-    AT u[3];
-    point_sum<JT>(vv, LD, po[j], po[j + 1], u);
-    AT t[3];
-    mul3(hv + 6 * j, u, t);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) tp[k * LD + j] = t[k];
-  }
-  __syncthreads();
-  // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
-#pragma unroll
-  for (int m = 0; m < EPT; ++m) {
-    const int i = threadIdx.x + m * kThreads;
-    if (i >= cr.nE) break;
-    AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
-    const int pl = ptl[m];
-    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
-    AT s[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) s[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-      AT v = row[k] * s[0];
-#pragma unroll
-      for (int a = 1; a < M; ++a) v += row[a * DC + k] * s[a];
-      vv[k * LD + pos[m]] = v;
-    }
-  }
-  __syncthreads();
-  // ---- pass 4: per-slot sums over contiguous positions
-  AT* partV = reinterpret_cast<AT*>(d.partV);
-  for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
-    const int sl = w / DC, comp = w - sl * DC;
-    partV[(size_t)sp[sl] * DC + comp] = seg_sum(vv + comp * LD, so[sl], so[sl + 1]);
-  }
-}
-
-// ---------------------------------------------------------------- Schur product, bulk-copy pipeline
-
-// Async-proxy helpers (sm_90+): mbarrier with transaction counts and 1-D bulk copies
-// from global to shared memory.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-constexpr unsigned kSpinLimit = 1u << 22;   // bounded waits: well under a second of polling
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (unsigned n = 0; n < kSpinLimit; ++n)
-    if (mbar_try_wait(mbar, parity)) return true;
-  return false;
-}
-
-constexpr int kStages = 3;                    // chunks in flight per CTA
-constexpr int kWsThreads = kThreads + 32;     // eight consumer warps and one producer warp
-
-// Named barrier of the consumer warps (the producer warp does not take part), and its
-// OR-reduction form.
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
-__device__ __forceinline__ bool consumer_any(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(kThreads)
-      : "memory");
-  return r != 0;
-}
-
-// Byte layout of one pipeline stage in shared memory (all offsets 16-byte aligned).
-struct StageLayout {
-  uint32_t j, meta, pt, slot, xs, size;
-};
-template <class Mo>
-__host__ __device__ inline StageLayout stage_layout(size_t sJ, size_t sA, int ch_max, int np_max, int ns_max) {
-  auto al = [](uint32_t v) { return (v + 15u) & ~15u; };
-  StageLayout L;
-  const uint32_t prb = (uint32_t)((6 * sA + 8 + 15) & ~(size_t)15);
-  L.j = 0;
-  L.meta = al((uint32_t)(ch_max * Mo::NJ * sJ));
-  L.pt = L.meta + al((uint32_t)(ch_max * 4 + 16));
-  L.slot = L.pt + al((uint32_t)(np_max * prb));
-  L.xs = L.slot + al((uint32_t)(ns_max * 16));
-  L.size = L.xs + al((uint32_t)(ns_max * Mo::DC * sA));
-  return L;
-}
-
-struct StageInfo {
-  int k, q, nE, nP, nS, skew;   // chunk (-1: no more chunks), problem, sizes, meta skew
-};
-
-// Warp-specialised persistent Schur product.  One producer warp walks the chunks
-// blockIdx.x, + gridDim.x, ... of the launch set (skipping problems whose PCG has
-// stopped) and, kStages chunks ahead of the consumers, streams each chunk's inputs
-// -- Jacobian rows, packed per-edge positions, point records (H_pp^-1 and edge range)
-// and slot records (edge range, camera, partial row) -- into a shared-memory stage
-// with 1-D bulk copies completing on the stage's "full" mbarrier, and gathers the
-// slot cameras' search-direction values p = (z + beta p_old) / n into the stage
-// itself.  Eight consumer warps run the passes of k_spmv on the stage (named barriers
-// among themselves) and release it on its "empty" mbarrier.  Results are bit-identical
-// to k_spmv.  Every wait is bounded: a wait that gives up raises *ls.err, and the
-// producer lets its copies in flight land (bounded again) before the CTA exits.
-template <class Mo, class JT>
-__global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
-  using AT = typename AccOf<JT>::T;
-  using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
-  constexpr uint32_t RB = NJ * sizeof(JT);
-  constexpr uint32_t PRB = (6 * sizeof(AT) + 8 + 15) & ~15u;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  __shared__ StageInfo info[kStages];
-  __shared__ int s_fail;
-  pdl_trigger();
-  const StageLayout SL = stage_layout<Mo>(sizeof(JT), sizeof(AT), ls.ch_max, ls.np_max, ls.ns_max);
-  const int LD = ls.ch_max + 1;
-  AT* vv = reinterpret_cast<AT*>(smem + kStages * SL.size);   // [VW][LD] consumer scratch
-  AT* tp = vv + VW * LD;                                        // [3][LD]
-  const int G = gridDim.x;
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) {
-      mbar_init(smem_u32(&full[st]), 2);    // the producer's expect_tx arrival + its gather arrival
-      mbar_init(smem_u32(&empty[st]), 1);   // one consumer arrival
-    }
-    mbar_fence_init();
-    s_fail = 0;
-  }
-  pdl_wait();
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (warp == kThreads / 32) {
-    // ================================================================ producer warp
-    // next chunk k' >= k of this CTA whose problem still iterates, or -1
-    auto next_live = [&](int k) -> int {
-      while (k < ls.n_ch) {
-        const int q = ls.ch_prob[k];
-        const Scalars* sc = ls.probs[q].sc;
-        if (sc->active && !sc->pcg_done) return k;
-        const int nxt = q + 1 < ls.nprob ? ls.ch_base[q + 1] : ls.n_ch;
-        k += ((nxt - k) + G - 1) / G * G;
-      }
-      return -1;
-    };
-    int last_use[kStages];
-#pragma unroll
-    for (int st = 0; st < kStages; ++st) last_use[st] = -1;
-    int k = __shfl_sync(0xffffffffu, lane == 0 ? next_live(blockIdx.x) : 0, 0);
-    int cq = -1;
-    const DevBA* P = nullptr;
-    const AT* zv = nullptr;
-    const AT* pold = nullptr;
-    AT beta = (AT)0, inv_n = (AT)1;
-    for (int n = 0;; ++n) {
-      const int st = n % kStages, use = n / kStages;
-      if (use > 0 && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(use - 1) & 1u)) {
-        if (lane == 0) s_fail = 1;
-        break;
-      }
-      const uint32_t fb = smem_u32(&full[st]);
-      last_use[st] = use;
-      if (k < 0) {   // end of work: an empty stage with no transfer
-        if (lane == 0) {
-          info[st].k = -1;
-          mbar_arrive(fb, 2);
-        }
-        break;
-      }
-      const int q = ls.ch_prob[k];
-      if (q != cq) {
-        cq = q;
-        P = ls.probs + q;
-        const Scalars* sc = P->sc;
-        zv = reinterpret_cast<const AT*>(P->z);
-        pold = reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-        beta = (AT)sc->beta;
-        inv_n = (AT)sc->inv_n;
-      }
-      const int kl = k - ls.ch_base[q];
-      const int e0 = P->ch_e0[kl], e1 = P->ch_e0[kl + 1];
-      const int p0 = P->ch_p0[kl], p1 = P->ch_p0[kl + 1];
-      const int s0 = P->ch_s0[kl], s1 = P->ch_s0[kl + 1];
-      unsigned char* base = smem + st * SL.size;
-      if (lane == 0) {
-        const uint32_t bJ = (uint32_t)(e1 - e0) * RB;
-        const uintptr_t ms = reinterpret_cast<uintptr_t>(P->e_meta + e0);
-        const uintptr_t ma = ms & ~(uintptr_t)15;
-        const uint32_t skew = (uint32_t)(ms - ma);
-        const uint32_t bM = e1 > e0 ? (skew + 4u * (uint32_t)(e1 - e0) + 15u) & ~15u : 0u;
-        const uint32_t bP = (uint32_t)(p1 - p0) * PRB;
-        const uint32_t bS = (uint32_t)(s1 - s0) * 16u;
-        info[st] = StageInfo{k, q, e1 - e0, p1 - p0, s1 - s0, (int)(skew / 4)};
-        fence_proxy_async();
-        mbar_expect_tx(fb, bJ + bM + bP + bS);
-        if (bJ) bulk_g2s(smem_u32(base + SL.j), static_cast<const JT*>(P->J) + (size_t)e0 * NJ, bJ, fb);
-        if (bM) bulk_g2s(smem_u32(base + SL.meta), reinterpret_cast<const void*>(ma), bM, fb);
-        if (bP) bulk_g2s(smem_u32(base + SL.pt), static_cast<const unsigned char*>(P->pt_rec) + (size_t)p0 * PRB, bP, fb);
-        if (bS) bulk_g2s(smem_u32(base + SL.slot), P->slot_rec + s0, bS, fb);
-      }
-      // the slot cameras' search-direction values, gathered by the whole warp
-      AT* xs = reinterpret_cast<AT*>(base + SL.xs);
-      for (int w = lane; w < (s1 - s0) * DC; w += 32) {
-        const int sl = w / DC, kk = w - sl * DC;
-        const size_t o = DB * (size_t)__ldg(&P->slot_rec[s0 + sl].z) + kk;
-        xs[w] = (zv[o] + beta * pold[o]) * inv_n;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(fb, 1);
-      k = __shfl_sync(0xffffffffu, lane == 0 ? next_live(k + G) : 0, 0);
-    }
-    // let every copy issued into a stage land before the CTA can exit (already true
-    // unless a wait gave up); bounded
-    if (lane == 0) {
-#pragma unroll
-      for (int st = 0; st < kStages; ++st)
-        if (last_use[st] >= 0) mbar_wait(smem_u32(&full[st]), (uint32_t)last_use[st] & 1u);
-      if (s_fail) atomicExch(ls.err, 1);
-    }
-  } else {
-    // ================================================================ consumer warps
-    for (int n = 0;; ++n) {
-      const int st = n % kStages;
-      const bool ok = mbar_wait(smem_u32(&full[st]), (uint32_t)(n / kStages) & 1u);
-      if (consumer_any(!ok)) {
-        if (threadIdx.x == 0) s_fail = 1;
-        break;
-      }
-      const StageInfo in = info[st];
-      if (in.k < 0) break;
-      const unsigned char* stg = smem + st * SL.size;
-      const JT* Js = reinterpret_cast<const JT*>(stg + SL.j);
-      const uint32_t* meta = reinterpret_cast<const uint32_t*>(stg + SL.meta) + in.skew;
-      const unsigned char* prec = stg + SL.pt;
-      const int4* srec = reinterpret_cast<const int4*>(stg + SL.slot);
-      const AT* xs = reinterpret_cast<const AT*>(stg + SL.xs);
-      // ---- pass 1: a_e = Jp^T (Jc x_c)
-      for (int i = threadIdx.x; i < in.nE; i += kThreads) {
-        AT row[NJ];
-        load_row<NJ>(Js + (size_t)i * NJ, row);
-        const AT* xc = xs + DC * (int)((meta[i] >> 10) & 1023u);
-        AT qv[M];
-#pragma unroll
-        for (int a = 0; a < M; ++a) qv[a] = (AT)0;
-#pragma unroll
-        for (int kk = 0; kk < DC; ++kk) {
-          const AT xk = xc[kk];
-#pragma unroll
-          for (int a = 0; a < M; ++a) qv[a] += row[a * DC + kk] * xk;
-        }
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-          AT sum = row[JP0 + kk] * qv[0];
-#pragma unroll
-          for (int a = 1; a < M; ++a) sum += row[JP0 + 3 * a + kk] * qv[a];
-          vv[kk * LD + i] = sum;
-        }
-      }
-      consumer_sync();
-      // ---- pass 2: t_p = H_pp^-1 sum_e a_e
-      for (int j = threadIdx.x; j < in.nP; j += kThreads) {
-        const unsigned char* pr = prec + (size_t)j * PRB;
-        const AT* hv = reinterpret_cast<const AT*>(pr);
-        const int* se = reinterpret_cast<const int*>(pr + 6 * sizeof(AT));
-        AT u[3];
-        point_sum<JT>(vv, LD, se[0], se[1], u);
-        AT t[3];
-        mul3(hv, u, t);
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) tp[kk * LD + j] = t[kk];
-      }
-      consumer_sync();
-      // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
-      for (int i = threadIdx.x; i < in.nE; i += kThreads) {
-        AT row[NJ];
-        load_row<NJ>(Js + (size_t)i * NJ, row);
-        const uint32_t m = meta[i];
-        const int pl = (int)(m >> 20), pos = (int)(m & 1023u);
-        const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
-        AT sv[M];
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-          sv[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
-#pragma unroll
-        for (int kk = 0; kk < DC; ++kk) {
-          AT v = row[kk] * sv[0];
-#pragma unroll
-          for (int a = 1; a < M; ++a) v += row[a * DC + kk] * sv[a];
-          vv[kk * LD + pos] = v;
-        }
-      }
-      consumer_sync();
-      // ---- pass 4: per-slot sums over contiguous positions
-      AT* partV = reinterpret_cast<AT*>(ls.probs[in.q].partV);
-      for (int w = threadIdx.x; w < in.nS * DC; w += kThreads) {
-        const int sl = w / DC, comp = w - sl * DC;
-        const int4 r4 = srec[sl];
-        partV[(size_t)r4.w * DC + comp] = seg_sum(vv + comp * LD, r4.x, r4.y);
-      }
-      consumer_sync();
-      if (threadIdx.x == 0) mbar_arrive(smem_u32(&empty[st]), 1);
-    }
-  }
-}
-
 // y_c = (H_cc + lambda D_c) p_c - sum_slots v (+ the camera-side edges' off-diagonal
 // products), four warps per camera (each sums a quarter of the camera's slot
 // partials and of its camera-side edges; the quarters are added in a fixed order).  The CTAs of camera block b
@@ -1157,7 +694,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   const AT* pold_all = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
   const AT* z_all = reinterpret_cast<const AT*>(d.z);
   const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
-  double dot = 0.0;
+  AT dot = (AT)0;   // per-warp partial in AT, accumulated across warps in FP64
   AT pi = (AT)0;
   if (c < d.C) {   // warp-uniform
     const AT* partV = reinterpret_cast<const AT*>(d.partV);
@@ -1230,12 +767,12 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
     if (lane < DB) {
       yi -= sv;
       reinterpret_cast<AT*>(d.y)[DB * (size_t)c + lane] = yi;
-      dot = (double)pi * (double)yi;
+      dot = pi * yi;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
-  if (lane == 0) red[warp] = dot;
+  if (lane == 0) red[warp] = (double)dot;
   __syncthreads();
   const int ctas = d.ncblk * kApplySplit, me = cbl * kApplySplit + part;
   if (threadIdx.x == 0) {
@@ -1272,7 +809,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
   if (!sc->active || sc->pcg_done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = cbl * kCamPerBlock + warp;
-  double rz_c = 0.0, rr_c = 0.0;
+  AT rz_c = (AT)0, rr_c = (AT)0;   // per-warp partials in AT, accumulated across warps in FP64
   if (c < d.C) {   // warp-uniform
     const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
     AT* x = reinterpret_cast<AT*>(d.x) + DB * (size_t)c;
@@ -1295,8 +832,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
     }
     if (lane < DB) {
       z[lane] = zi;
-      rz_c = (double)ri * (double)zi;
-      rr_c = (double)ri * (double)ri;
+      rz_c = ri * zi;
+      rr_c = ri * ri;
     }
   }
 #pragma unroll
@@ -1305,8 +842,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
     rr_c += __shfl_down_sync(0xffffffffu, rr_c, o);
   }
   if (lane == 0) {
-    red[warp][0] = rz_c;
-    red[warp][1] = rr_c;
+    red[warp][0] = (double)rz_c;
+    red[warp][1] = (double)rr_c;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
