@@ -162,6 +162,16 @@ def spmv_algorithmic_bytes(E: int, P: int, precision: str) -> float:
     return E * (24 * sJ + 4) + P * 6 * sA
 
 
+def knobs(args) -> dict:
+    """Schedule knobs given on the command line; none given = the autotuned table's."""
+    k = {}
+    if args.chunk:
+        k["chunk_edges"] = args.chunk
+    if args.spmv != "auto":
+        k["spmv_variant"] = SPMV_VARIANTS[args.spmv]
+    return k
+
+
 def spmv_algorithmic_bytes_vi(E: int, P: int, precision: str) -> float:
     """Same for the stereo model: 27 stored Jacobian values per edge (3 x 6 pose, 3 x 3
     point; rows padded to 32 are padding, not algorithmic)."""
@@ -285,7 +295,7 @@ def run_vi(args, dev, stream, world: int) -> dict:
     p = synth.vi_global()
     params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6, pcg_rejection_ratio=0.0)
     g, _, _, _ = gpo.vi_graph(p, precision=args.precision, device=dev, stream=stream.cuda_stream,
-                              chunk_edges=args.chunk, spmv_variant=SPMV_VARIANTS[args.spmv])
+                              **knobs(args))
     g.optimize(args.warmup, params)
     torch.cuda.synchronize()
     g.set_profiling(True)
@@ -311,7 +321,7 @@ def run_vi(args, dev, stream, world: int) -> dict:
         data="synthetic",
         config=dict(workload=p.name, precision=args.precision, keyframes=p.n_kf, landmarks=p.n_pts,
                     stereo_edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, pcg_rejection_ratio="off",
-                    chunk_edges=args.chunk or "default", spmv_kernel=args.spmv,
+                    schedule=g.knobs,
                     parallelism=f"replicas x{world}"),
         gpu_launches=int(sum(v["launches"] for v in prof.values())),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
@@ -337,8 +347,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     p = synth.ba_medium(args.seed)
     params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
     g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
-                             args.precision, device=dev, stream=stream.cuda_stream,
-                             chunk_edges=args.chunk, spmv_variant=SPMV_VARIANTS[args.spmv])
+                             args.precision, device=dev, stream=stream.cuda_stream, **knobs(args))
     g.optimize(args.warmup, params)               # also freezes the topology and plans memory
     torch.cuda.synchronize()
     g.set_profiling(True)
@@ -402,14 +411,15 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         data="synthetic",
         config=dict(workload=WORKLOAD, precision=args.precision, cameras=p.n_cams, points=p.n_pts,
                     edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, seed=args.seed,
-                    chunk_edges=args.chunk or "default", spmv_kernel=args.spmv,
+                    schedule=g.knobs,
                     l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
                     parallelism=f"replicas x{world}"),
         e2e=None if args.no_e2e else dict(value=world * args.steps / e2e_s, unit="LM iter/s",
                                           h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes),
         gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      traffic=spmv_traffic(args.precision) if args.seed == 1 and args.chunk in (0, 512) else None,
+                      traffic=spmv_traffic(args.precision) if args.seed == 1 and g.knobs["chunk_edges"] in (0, 512)
+                      and g.knobs["spmv_variant"] in (0, 2) else None,
                       kernel="k_spmv (PCG Schur product)", peak_source=peak_kind,
                       algorithmic_bytes=alg, avg_ms=spmv_ms),
         clocks=clk,

@@ -114,7 +114,13 @@ __global__ void k_gather_rows(double* dst, const double* src, const int32_t* idx
 
 }  // namespace
 
+void gpo_host::drop_pcg_graph(gpo_graph* g) {
+  if (g->pcg_exec) cudaGraphExecDestroy(g->pcg_exec);
+  g->pcg_exec = nullptr;
+}
+
 void gpo_host::release_device(gpo_graph* g) {
+  drop_pcg_graph(g);
   if (g->arena) {
     if (g->desc.alloc && g->desc.free) g->desc.free(g->arena, g->desc.alloc_ctx);
     else cudaFree(g->arena);
@@ -560,20 +566,62 @@ gpo_status gpo_host::upload_scalars(gpo_graph* g, const Scalars& s) {
   return GPO_OK;
 }
 
+constexpr int kPcgGroup = 8;
+
+// Captures kPcgGroup PCG iterations of `ls` as a CUDA graph on g's stream (the
+// kernels read every per-iteration value from device memory, so one graph serves
+// every group).  On any capture error the graph path is switched off for g.
+static void capture_pcg_group(gpo_graph* g, const gpo::LaunchSet& ls) {
+  gpo_host::drop_pcg_graph(g);
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    g->pcg_graph_off = true;
+    return;
+  }
+  int c[3] = {0, 0, 0};
+  for (int i = 0; i < kPcgGroup; ++i) {
+    c[0] += g->ks->pcg_spmv(ls, g->prec, g->stream);
+    c[1] += g->ks->cam_apply(ls, g->prec, g->stream);
+    c[2] += g->ks->pcg_update(ls, g->prec, g->stream);
+  }
+  const cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+  if (e != cudaSuccess || !graph || cudaGraphInstantiate(&g->pcg_exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    g->pcg_exec = nullptr;
+    g->pcg_graph_off = true;
+  } else {
+    g->pcg_ls = ls;
+    for (int k = 0; k < 3; ++k) g->pcg_counts[k] = c[k];
+  }
+  if (graph) cudaGraphDestroy(graph);
+}
+
 // PCG iterations with early exit: iterations are launched in groups; after each
 // group the done flag is copied back, and the flag of the previous group decides
-// whether to launch more (one group of look-ahead keeps the GPU busy).
+// whether to launch more (one group of look-ahead keeps the GPU busy).  Full groups
+// replay a captured CUDA graph unless profiling is on (which times every launch).
 static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) {
   if (gpo_status s = gpo_host::ensure_runtime(g); s != GPO_OK) return s;
-  const int kGroup = 8;
+  const int kGroup = kPcgGroup;
   int launched = 0, slot = 0, pending = -1;
   while (launched < max_it) {
     const int n = std::min(kGroup, max_it - launched);
-    for (int i = 0; i < n; ++i) {
-      g->cur_pcg_k = launched + i + 1;
-      run(g, KK_SPMV, [&] { return g->ks->pcg_spmv(ls, g->prec, g->stream); });
-      run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
-      run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
+    const bool graph_ok = !g->prof.on && !g->pcg_graph_off && n == kGroup;
+    if (graph_ok && (!g->pcg_exec || std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) != 0) && launched > 0)
+      capture_pcg_group(g, ls);   // after one direct group, so kernel attributes are set
+    if (graph_ok && g->pcg_exec && std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) == 0) {
+      GPO_CUDA(g, cudaGraphLaunch(g->pcg_exec, g->stream));
+      g->prof.launches[KK_SPMV] += g->pcg_counts[0];
+      g->prof.launches[KK_CAM_APPLY] += g->pcg_counts[1];
+      g->prof.launches[KK_PCG_UPDATE] += g->pcg_counts[2];
+    } else {
+      for (int i = 0; i < n; ++i) {
+        g->cur_pcg_k = launched + i + 1;
+        run(g, KK_SPMV, [&] { return g->ks->pcg_spmv(ls, g->prec, g->stream); });
+        run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
+        run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
+      }
     }
     launched += n;
     GPO_CUDA(g, cudaMemcpyAsync(&g->h_flag[2 * slot], ls.running, 2 * sizeof(int),

@@ -99,6 +99,12 @@ struct gpo_graph {
   Profiler prof;
   int cur_lm_iter = -1;
   int cur_pcg_k = 0;
+  // a group of PCG iterations captured as a CUDA graph, for the launch set it was
+  // captured with (replayed by the PCG loop while profiling is off)
+  cudaGraphExec_t pcg_exec = nullptr;
+  gpo::LaunchSet pcg_ls{};
+  int pcg_counts[3] = {0, 0, 0};   // kernels per group: Schur product, camera half, update
+  bool pcg_graph_off = false;      // capture failed once: launch directly
 };
 
 
@@ -125,6 +131,8 @@ gpo_status finish_iteration(gpo_graph* g, const gpo::LaunchSet& ls);
 // Camera render blocks, F(x) and its per-problem reduction over `ls` (no sync).
 gpo_status launch_initial_cost(gpo_graph* g, const gpo::LaunchSet& ls);
 void prof_resolve(gpo_graph* g);
+// Drops the captured PCG group (its launch set is gone).
+void drop_pcg_graph(gpo_graph* g);
 // Copies the final device state back into the graph's host arrays (user order).
 gpo_status download_state(gpo_graph* g);
 // The same in two halves: enqueue the copies (points into `pts`), then, after the

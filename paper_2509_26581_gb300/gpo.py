@@ -165,6 +165,7 @@ class Graph:
         d.reserve_edges = reserve_edges
         d.chunk_edges = chunk_edges
         d.spmv_variant = spmv_variant
+        self.knobs = dict(chunk_edges=chunk_edges, spmv_variant=spmv_variant)
         h = C.c_void_p()
         _check(lib.gpo_graph_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -348,10 +349,21 @@ class Server:
         self.close()
 
 
+def _tuned(kw: dict, n_edges: int, precision, model: str) -> dict:
+    """Adds the autotuned schedule knobs (chunk size, Schur-product kernel) for this size
+    class unless the caller set either of them."""
+    if "chunk_edges" in kw or "spmv_variant" in kw:
+        return kw
+    from . import autotune
+    name = precision if isinstance(precision, str) else {v: k for k, v in PRECISIONS.items()}[int(precision)]
+    return {**autotune.choose(int(n_edges), name, model), **kw}
+
+
 def ba_graph(cams, pts, cam_idx, pt_idx, obs, huber_delta=None, precision="fp64",
              cam_fixed=None, pt_fixed=None, active=None, info=None, **kw) -> tuple[Graph, int, int]:
     """Builds a BA graph: cameras get ids [0, C), points [C, C + P).  Returns
     (graph, first camera id, first point id)."""
+    kw = _tuned(kw, len(cam_idx), precision, "ba")
     g = Graph(precision, **kw)
     C_ = cams.shape[0]
     P_ = pts.shape[0]
@@ -410,6 +422,7 @@ def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), 
     Returns (graph, first navigation id, first landmark id, edge-id ranges by kind)."""
     nav = p.nav0 if nav is None else nav
     pts = p.pts0 if pts is None else pts
+    kw = _tuned(kw, len(p.kf_idx), precision, "vi")
     g = Graph(precision, **kw)
     K, P = nav.shape[0], pts.shape[0]
     n0 = g.add_vertices(GPO_V_NAV15, 15, K)

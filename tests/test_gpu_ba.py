@@ -259,3 +259,18 @@ def test_schur_product_variants_bitwise(gpo, prec):
         out.append((rep.final_cost, rep.pcg_iters_total, g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)))
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][3], out[1][3])
+
+
+def test_captured_pcg_groups_bitwise(gpo):
+    """Full groups of PCG iterations replay a captured CUDA graph unless profiling is on
+    (profiling times every launch directly): both give the same solve bit for bit."""
+    p = synth.ba_path(4, 40, 6000, "pareto")
+    out = []
+    for prof in (False, True):
+        g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp32")
+        g.set_profiling(prof)
+        rep = g.optimize(4, gpo.default_params(pcg_max_iters=60, pcg_tol=1e-12))
+        out.append((rep.final_cost, rep.pcg_iters_total, g.get_state(c0, p.n_cams, 9)))
+        assert rep.pcg_iters_total > 16       # several full groups ran
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
