@@ -37,14 +37,20 @@ def size_class(n_edges: int) -> str:
     return SIZE_CLASSES[-1][1]
 
 
+_CACHE: dict = {}
+
+
 def device_name() -> str:
-    try:
-        import torch
-        if torch.cuda.is_available():
-            return torch.cuda.get_device_name(0)
-    except Exception:   # no torch or no GPU: the table is not used
-        pass
-    return "none"
+    if "device" not in _CACHE:
+        name = "none"
+        try:
+            import torch
+            if torch.cuda.is_available():
+                name = torch.cuda.get_device_name(0)
+        except Exception:   # no torch or no GPU: the table is not used
+            pass
+        _CACHE["device"] = name
+    return _CACHE["device"]
 
 
 def load_table(path: str = TABLE) -> dict:
@@ -59,7 +65,10 @@ def choose(n_edges: int, precision: str, model: str = "ba", table: dict | None =
            device: str | None = None) -> dict:
     """Knobs for a graph of n_edges observation edges: the table's entry for this device,
     model, precision and size class, else the library defaults."""
-    table = load_table() if table is None else table
+    if table is None:
+        if "table" not in _CACHE:
+            _CACHE["table"] = load_table()
+        table = _CACHE["table"]
     key = f"{device or device_name()}|{model}|{precision}|{size_class(n_edges)}"
     entry = table.get(key)
     return dict(entry["best"]) if entry else dict(DEFAULT)
@@ -145,8 +154,8 @@ def tune_all(models=("ba", "vi"), precisions=("fp64", "fp32", "bf16"),
                 print(model, cls, prec, n_edges, res["best"],
                       {f"{t['knobs']['chunk_edges']}/{t['knobs']['spmv_variant']}": round(t['s_per_iter'] * 1e3, 3)
                        for t in res["timings"]}, flush=True)
-    with open(path, "w") as f:
-        json.dump(table, f, indent=1, sort_keys=True)
+                with open(path, "w") as f:      # after every entry: a partial run keeps its results
+                    json.dump(table, f, indent=1, sort_keys=True)
     return table
 
 

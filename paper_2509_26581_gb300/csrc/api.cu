@@ -187,6 +187,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   // chunk size
   int ch = g->desc.chunk_edges > 0 ? g->desc.chunk_edges : gpo::default_ch_max(g->prec);
   if (ch < 32) ch = 32;
+  ch = std::min(ch, ks.max_supported_ch(g->prec));   // a larger request is a hint only
   while (ch < maxdeg) ch *= 2;
   if (ch > ks.max_supported_ch(g->prec))
     return fail(g, GPO_ERR_UNSUPPORTED,
