@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <string>
@@ -50,7 +51,7 @@ bool sqrt_info(const double* Om, int m, double* U) {
     for (int j = 0; j < i; ++j)
       if (std::fabs(Om[i * m + j] - Om[j * m + i]) > 1e-12 * (std::fabs(Om[i * m + i]) + std::fabs(Om[j * m + j])))
         return false;
-  std::vector<double> L(m * m, 0.0);
+  double L[81] = {};
   for (int j = 0; j < m; ++j) {
     double s = Om[j * m + j];
     for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
@@ -69,16 +70,42 @@ bool sqrt_info(const double* Om, int m, double* U) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Device memory plan: requests are laid out in one arena (256-byte aligned).
+// Device memory plan: requests are laid out in one arena (256-byte aligned).  Requests
+// with a host source (`up`) come first, so the arena's prefix is one host image that a
+// single copy uploads.
 struct Plan {
-  struct Req { void** ptr; size_t bytes; };
+  struct Req { void** ptr; size_t bytes; const void* src; size_t src_bytes; };
   std::vector<Req> reqs;
-  template <class T> void add(T** p, size_t count) { reqs.push_back({reinterpret_cast<void**>(p), count * sizeof(T)}); }
-  void add_raw(void** p, size_t bytes) { reqs.push_back({p, bytes}); }
+  template <class T> void add(T** p, size_t count) {
+    reqs.push_back({reinterpret_cast<void**>(p), count * sizeof(T), nullptr, 0});
+  }
+  void add_raw(void** p, size_t bytes) { reqs.push_back({p, bytes, nullptr, 0}); }
+  // an array uploaded from `src` (count elements); the allocation may be larger
+  template <class T> void up(T** p, size_t count, const std::vector<T>& src) {
+    reqs.push_back({reinterpret_cast<void**>(p), std::max(count, src.size()) * sizeof(T), src.data(),
+                    src.size() * sizeof(T)});
+  }
   size_t total() const {
     size_t t = 0;
     for (auto& r : reqs) t = align_up(t, 256) + align_up(r.bytes, 256);
     return t;
+  }
+  // bytes of the uploaded prefix and its host image
+  size_t image(std::vector<char>& out) const {
+    size_t t = 0, end = 0;
+    for (auto& r : reqs) {
+      t = align_up(t, 256);
+      if (r.src) end = t + r.src_bytes;
+      t += align_up(r.bytes, 256);
+    }
+    out.assign(end, 0);
+    t = 0;
+    for (auto& r : reqs) {
+      t = align_up(t, 256);
+      if (r.src && r.src_bytes) std::memcpy(out.data() + t, r.src, r.src_bytes);
+      t += align_up(r.bytes, 256);
+    }
+    return end;
   }
   void assign(char* base) const {
     size_t t = 0;
@@ -132,15 +159,42 @@ void gpo_host::release_device(gpo_graph* g) {
 
 // ============================================================== topology
 
-// Sorts the edges point-major, cuts chunks and slots, plans device memory and (unless
-// plan_bytes is given, in which case only the planned size is returned) allocates
-// and uploads everything.
-gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
-  if (g->finalized) {
-    if (plan_bytes) *plan_bytes = g->arena_bytes;
-    return GPO_OK;
-  }
-  const gpo::KernelSet& ks = kernels_of(g);
+// Host-side preparation of a graph's device image: sorted topology, chunks, slots,
+// per-edge data in sorted order, the memory plan and the host sources of the uploaded
+// prefix of the arena.  Built once (a server plans at submit and uploads at admission)
+// and dropped after the upload or when the topology changes.
+struct Prepared {
+  DevBA d{};
+  int ch = 0, NCH = 0, npb = 0;
+  size_t jpos = 0, bytes = 0;
+  std::vector<int64_t> sorted_edge;
+  std::vector<int32_t> pt_new2old, pt_old2new, x_sorted;
+  // sources of the uploaded arrays
+  std::vector<int32_t> e_cam_s, e_pt_s, pt_off, ch_e0, ch_p0, ch_s0, slot_e0, slot_cam, cam_s_off, cam_s_list,
+      slot_pos, slot_rec, xi_s, xj_s, xk_s, xo_off, xk_off, xk_list, zeros_ch, zeros_cb, zeros_pb, zeros_small;
+  std::vector<uint16_t> e_pos, e_slot, ch_sorted;
+  std::vector<uint32_t> e_meta;
+  std::vector<uint8_t> cam_fixed, pt_fixed_s;
+  std::vector<double> obs_s, delta_s, info_s, xrec_s, cams, pts, xzeros;
+  std::vector<Scalars> sc0;
+  // device pointers assigned by the plan
+  int *e_cam_d = nullptr, *e_pt_d = nullptr, *pt_off_d = nullptr, *ch_e0_d = nullptr, *ch_p0_d = nullptr,
+      *ch_s0_d = nullptr, *slot_e0_d = nullptr, *slot_cam_d = nullptr, *cam_s_off_d = nullptr,
+      *cam_s_list_d = nullptr, *slot_pos_d = nullptr, *slot_rec_d = nullptr, *xe_i_d = nullptr, *xe_j_d = nullptr,
+      *xe_kind_d = nullptr, *xo_off_d = nullptr, *xk_off_d = nullptr, *xk_list_d = nullptr, *ch_prob_d = nullptr,
+      *cb_prob_d = nullptr, *pb_prob_d = nullptr, *base_d = nullptr, *running_d = nullptr;
+  uint16_t *e_pos_d = nullptr, *e_slot_d = nullptr, *ch_sorted_d = nullptr;
+  uint32_t* e_meta_d = nullptr;
+  uint8_t *cam_fixed_d = nullptr, *pt_fixed_d = nullptr;
+  double *obs_d = nullptr, *delta_d = nullptr, *info_d = nullptr, *xe_rec_d = nullptr;
+  DevBA* desc_d = nullptr;
+  Plan pl;
+};
+
+void PrepDeleter::operator()(Prepared* p) const { delete p; }
+
+static gpo_status prepare(gpo_graph* g) {
+  const gpo::KernelSet& ks = gpo_host::kernels_of(g);
   const int SS = ks.SS, DB = ks.DB, M = ks.M, NJ = ks.NJ, NPA = ks.NPA, DC = ks.DC;
   const int TB = tri(DB), NQ = tri(M);
   const int C = (int)g->cam_fixed.size();
@@ -149,6 +203,9 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   if (Eall > INT32_MAX / 2) return fail(g, GPO_ERR_UNSUPPORTED, "too many edges (%lld)", (long long)Eall);
   if (ks.model == gpo::ModelKind::STEREO && Eall > 0 && !g->camk_set)
     return fail(g, GPO_ERR_STATE, "stereo edges need the rig: call gpo_set_stereo_camera first");
+  std::unique_ptr<Prepared> pp(new (std::nothrow) Prepared());
+  if (!pp) return fail(g, GPO_ERR_OOM, "host allocation failed");
+  Prepared& R = *pp;
 
   // point order: by the smallest camera index among the point's active edges
   // (points without active edges last), ties by point index.  Consecutive points
@@ -164,25 +221,25 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   std::vector<int32_t> cnt(C + 2, 0);
   for (int p = 0; p < P; ++p) cnt[key[p] + 1]++;
   for (int k = 0; k <= C; ++k) cnt[k + 1] += cnt[k];
-  g->pt_new2old.assign(P, 0);
-  g->pt_old2new.assign(P, 0);
+  R.pt_new2old.assign(P, 0);
+  R.pt_old2new.assign(P, 0);
   for (int p = 0; p < P; ++p) {
     const int np = cnt[key[p]]++;
-    g->pt_new2old[np] = p;
-    g->pt_old2new[p] = np;
+    R.pt_new2old[np] = p;
+    R.pt_old2new[p] = np;
   }
   // edges: point-major (new point order), then edge id
-  std::vector<int32_t> pt_off(P + 1, 0);
-  for (int p = 0; p < P; ++p) pt_off[g->pt_old2new[p] + 1] = deg[p];
-  for (int p = 0; p < P; ++p) pt_off[p + 1] += pt_off[p];
-  const int E = pt_off[P];
+  R.pt_off.assign(P + 1, 0);
+  for (int p = 0; p < P; ++p) R.pt_off[R.pt_old2new[p] + 1] = deg[p];
+  for (int p = 0; p < P; ++p) R.pt_off[p + 1] += R.pt_off[p];
+  const int E = R.pt_off[P];
   int maxdeg = 0;
   for (int p = 0; p < P; ++p) maxdeg = std::max(maxdeg, deg[p]);
-  g->sorted_edge.assign(E, 0);
+  R.sorted_edge.assign(E, 0);
   {
-    std::vector<int32_t> fill(pt_off.begin(), pt_off.end() - 1);
+    std::vector<int32_t> fill(R.pt_off.begin(), R.pt_off.end() - 1);
     for (int64_t e = 0; e < Eall; ++e)
-      if (g->e_active[e]) g->sorted_edge[fill[g->pt_old2new[g->e_pt[e]]]++] = e;
+      if (g->e_active[e]) R.sorted_edge[fill[R.pt_old2new[g->e_pt[e]]]++] = e;
   }
   // chunk size
   int ch = g->desc.chunk_edges > 0 ? g->desc.chunk_edges : gpo::default_ch_max(g->prec);
@@ -193,16 +250,17 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
     return fail(g, GPO_ERR_UNSUPPORTED,
                 "a point has %d observations; this precision supports at most %d per point", maxdeg,
                 ks.max_supported_ch(g->prec));
-  g->ch_max = ch;
+  R.ch = ch;
   // chunks of whole points, at most ch edges and ch points each
-  std::vector<int32_t> ch_e0{0}, ch_p0{0};
+  R.ch_e0.assign(1, 0);
+  R.ch_p0.assign(1, 0);
   {
     int ne = 0, np = 0;
     for (int p = 0; p < P; ++p) {
-      const int L = pt_off[p + 1] - pt_off[p];
+      const int L = R.pt_off[p + 1] - R.pt_off[p];
       if (np > 0 && (ne + L > ch || np + 1 > ch)) {
-        ch_e0.push_back(pt_off[p]);
-        ch_p0.push_back(p);
+        R.ch_e0.push_back(R.pt_off[p]);
+        R.ch_p0.push_back(p);
         ne = 0;
         np = 0;
       }
@@ -210,158 +268,194 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
       np += 1;
     }
     if (np > 0) {
-      ch_e0.push_back(E);
-      ch_p0.push_back(P);
+      R.ch_e0.push_back(E);
+      R.ch_p0.push_back(P);
     }
   }
-  const int NCH = (int)ch_e0.size() - 1;
-  // slots: distinct cameras per chunk, edges sorted by slot
-  std::vector<int32_t> e_cam_s(E), e_pt_s(E);
+  const int NCH = (int)R.ch_e0.size() - 1;
+  R.NCH = NCH;
+  // slots: distinct cameras per chunk in ascending order; the chunk's edges bucketed by
+  // slot, stable in edge order
+  R.e_cam_s.resize(E);
+  R.e_pt_s.resize(E);
   for (int i = 0; i < E; ++i) {
-    const int64_t e = g->sorted_edge[i];
-    e_cam_s[i] = g->e_cam[e];
-    e_pt_s[i] = g->pt_old2new[g->e_pt[e]];
+    const int64_t e = R.sorted_edge[i];
+    R.e_cam_s[i] = g->e_cam[e];
+    R.e_pt_s[i] = R.pt_old2new[g->e_pt[e]];
   }
-  std::vector<uint16_t> e_pos(E), e_slot(E), ch_sorted(E);
-  std::vector<int32_t> ch_s0{0}, slot_e0, slot_cam;
-  const size_t jpos = (size_t)E * NJ;
+  R.e_pos.resize(E);
+  R.e_slot.resize(E);
+  R.ch_sorted.resize(E);
+  R.ch_s0.assign(1, 0);
   {
-    std::vector<std::pair<int32_t, int32_t>> tmp;
+    std::vector<int32_t> cam2slot(std::max(C, 1), -1), cams, fill;
     for (int k = 0; k < NCH; ++k) {
-      const int e0 = ch_e0[k], n = ch_e0[k + 1] - e0;
-      tmp.resize(n);
-      for (int i = 0; i < n; ++i) tmp[i] = {e_cam_s[e0 + i], i};
-      std::sort(tmp.begin(), tmp.end());
-      int slot = -1, prev = -1;
-      for (int q = 0; q < n; ++q) {
-        if (tmp[q].first != prev) {
-          ++slot;
-          prev = tmp[q].first;
-          slot_e0.push_back(e0 + q);
-          slot_cam.push_back(prev);
+      const int e0 = R.ch_e0[k], n = R.ch_e0[k + 1] - e0;
+      cams.clear();
+      for (int i = 0; i < n; ++i) {
+        const int c = R.e_cam_s[e0 + i];
+        if (cam2slot[c] == -1) {
+          cam2slot[c] = -2;
+          cams.push_back(c);
         }
-        e_pos[e0 + tmp[q].second] = (uint16_t)q;
-        e_slot[e0 + tmp[q].second] = (uint16_t)slot;
-        ch_sorted[e0 + q] = (uint16_t)tmp[q].second;
       }
-      ch_s0.push_back((int)slot_cam.size());
+      std::sort(cams.begin(), cams.end());
+      const int ns = (int)cams.size();
+      fill.assign(ns + 1, 0);
+      for (int s2 = 0; s2 < ns; ++s2) cam2slot[cams[s2]] = s2;
+      for (int i = 0; i < n; ++i) fill[cam2slot[R.e_cam_s[e0 + i]] + 1]++;
+      for (int s2 = 0; s2 < ns; ++s2) fill[s2 + 1] += fill[s2];
+      for (int s2 = 0; s2 < ns; ++s2) {
+        R.slot_e0.push_back(e0 + fill[s2]);
+        R.slot_cam.push_back(cams[s2]);
+      }
+      for (int i = 0; i < n; ++i) {
+        const int sl = cam2slot[R.e_cam_s[e0 + i]];
+        const int q = fill[sl]++;
+        R.e_pos[e0 + i] = (uint16_t)q;
+        R.e_slot[e0 + i] = (uint16_t)sl;
+        R.ch_sorted[e0 + q] = (uint16_t)i;
+      }
+      for (int c : cams) cam2slot[c] = -1;
+      R.ch_s0.push_back((int)R.slot_cam.size());
     }
-    slot_e0.push_back(E);
+    R.slot_e0.push_back(E);
   }
-  const int NS = (int)slot_cam.size();
+  const int NS = (int)R.slot_cam.size();
   int ns_max = 1, np_max = 1;
   for (int k = 0; k < NCH; ++k) {
-    ns_max = std::max(ns_max, ch_s0[k + 1] - ch_s0[k]);
-    np_max = std::max(np_max, ch_p0[k + 1] - ch_p0[k]);
+    ns_max = std::max(ns_max, R.ch_s0[k + 1] - R.ch_s0[k]);
+    np_max = std::max(np_max, R.ch_p0[k + 1] - R.ch_p0[k]);
   }
-  g->j_elems = jpos;
+  R.jpos = (size_t)E * NJ;
   // per camera: its slots in chunk order
-  std::vector<int32_t> cam_s_off(C + 1, 0), cam_s_list(NS), slot_pos(std::max(NS, 1));
-  for (int s = 0; s < NS; ++s) cam_s_off[slot_cam[s] + 1]++;
-  for (int c = 0; c < C; ++c) cam_s_off[c + 1] += cam_s_off[c];
+  R.cam_s_off.assign(C + 1, 0);
+  R.cam_s_list.resize(NS);
+  R.slot_pos.assign(std::max(NS, 1), 0);
+  for (int s2 = 0; s2 < NS; ++s2) R.cam_s_off[R.slot_cam[s2] + 1]++;
+  for (int c = 0; c < C; ++c) R.cam_s_off[c + 1] += R.cam_s_off[c];
   {
-    std::vector<int32_t> fill(cam_s_off.begin(), cam_s_off.end() - 1);
-    for (int s = 0; s < NS; ++s) {
-      slot_pos[s] = fill[slot_cam[s]];
-      cam_s_list[fill[slot_cam[s]]++] = s;
+    std::vector<int32_t> fill(R.cam_s_off.begin(), R.cam_s_off.end() - 1);
+    for (int s2 = 0; s2 < NS; ++s2) {
+      R.slot_pos[s2] = fill[R.slot_cam[s2]];
+      R.cam_s_list[fill[R.slot_cam[s2]]++] = s2;
     }
   }
   // per-edge data in sorted order
-  std::vector<double> obs_s((size_t)M * E), delta_s(E), info_s;
+  R.obs_s.resize((size_t)M * E);
+  R.delta_s.resize(E);
   for (int i = 0; i < E; ++i) {
-    const int64_t e = g->sorted_edge[i];
-    for (int k = 0; k < M; ++k) obs_s[(size_t)M * i + k] = g->e_obs[(size_t)M * e + k];
-    delta_s[i] = g->e_delta[e];
+    const int64_t e = R.sorted_edge[i];
+    for (int k = 0; k < M; ++k) R.obs_s[(size_t)M * i + k] = g->e_obs[(size_t)M * e + k];
+    R.delta_s[i] = g->e_delta[e];
   }
   if (g->any_info) {
-    info_s.resize((size_t)NQ * E);
+    R.info_s.resize((size_t)NQ * E);
     for (int i = 0; i < E; ++i)
-      for (int k = 0; k < NQ; ++k) info_s[(size_t)NQ * i + k] = g->e_sqinfo[(size_t)NQ * g->sorted_edge[i] + k];
+      for (int k = 0; k < NQ; ++k) R.info_s[(size_t)NQ * i + k] = g->e_sqinfo[(size_t)NQ * R.sorted_edge[i] + k];
   }
-  std::vector<uint8_t> pt_fixed_s(P);
-  for (int p = 0; p < P; ++p) pt_fixed_s[g->pt_old2new[p]] = g->pt_fixed[p];
+  R.pt_fixed_s.resize(P);
+  for (int p = 0; p < P; ++p) R.pt_fixed_s[R.pt_old2new[p]] = g->pt_fixed[p];
+  R.cam_fixed = g->cam_fixed;
   // staged Schur-product inputs: packed per-edge positions and per-slot records
-  std::vector<uint32_t> e_meta((size_t)E + 4, 0u);
-  std::vector<int32_t> slot_rec(4 * (size_t)std::max(NS, 1), 0);
+  R.e_meta.assign((size_t)E + 4, 0u);
+  R.slot_rec.assign(4 * (size_t)std::max(NS, 1), 0);
   for (int k = 0; k < NCH; ++k) {
-    for (int i = ch_e0[k]; i < ch_e0[k + 1] && ch <= 1024; ++i)
-      e_meta[i] = (uint32_t)e_pos[i] | ((uint32_t)e_slot[i] << 10) | ((uint32_t)(e_pt_s[i] - ch_p0[k]) << 20);
-    for (int s = ch_s0[k]; s < ch_s0[k + 1]; ++s) {
-      slot_rec[4 * (size_t)s] = slot_e0[s] - ch_e0[k];
-      slot_rec[4 * (size_t)s + 1] = slot_e0[s + 1] - ch_e0[k];
-      slot_rec[4 * (size_t)s + 2] = slot_cam[s];
-      slot_rec[4 * (size_t)s + 3] = slot_pos[s];
+    for (int i = R.ch_e0[k]; i < R.ch_e0[k + 1] && ch <= 1024; ++i)
+      R.e_meta[i] = (uint32_t)R.e_pos[i] | ((uint32_t)R.e_slot[i] << 10) | ((uint32_t)(R.e_pt_s[i] - R.ch_p0[k]) << 20);
+    for (int s2 = R.ch_s0[k]; s2 < R.ch_s0[k + 1]; ++s2) {
+      R.slot_rec[4 * (size_t)s2] = R.slot_e0[s2] - R.ch_e0[k];
+      R.slot_rec[4 * (size_t)s2 + 1] = R.slot_e0[s2 + 1] - R.ch_e0[k];
+      R.slot_rec[4 * (size_t)s2 + 2] = R.slot_cam[s2];
+      R.slot_rec[4 * (size_t)s2 + 3] = R.slot_pos[s2];
     }
   }
-
   // camera-side edges: active ones, sorted by (first camera, index)
-  g->x_sorted.clear();
   for (size_t x = 0; x < g->x_kind.size(); ++x)
-    if (g->x_active[x]) g->x_sorted.push_back((int32_t)x);
-  std::stable_sort(g->x_sorted.begin(), g->x_sorted.end(),
-                   [&](int32_t a, int32_t b) { return g->x_i[a] < g->x_i[b]; });
-  const int NX = (int)g->x_sorted.size();
-  std::vector<int32_t> xi_s(NX), xj_s(NX), xk_s(NX), xo_off(C + 1, 0), xk_off(C + 1, 0), xk_list(2 * (size_t)NX);
-  std::vector<double> xrec_s((size_t)NX * gpo::kXRec);
+    if (g->x_active[x]) R.x_sorted.push_back((int32_t)x);
+  std::stable_sort(R.x_sorted.begin(), R.x_sorted.end(), [&](int32_t a, int32_t b) { return g->x_i[a] < g->x_i[b]; });
+  const int NX = (int)R.x_sorted.size();
+  R.xi_s.resize(NX);
+  R.xj_s.resize(NX);
+  R.xk_s.resize(NX);
+  R.xo_off.assign(C + 1, 0);
+  R.xk_off.assign(C + 1, 0);
+  R.xk_list.resize(2 * (size_t)NX);
+  R.xrec_s.resize((size_t)NX * gpo::kXRec);
   for (int t = 0; t < NX; ++t) {
-    const int x = g->x_sorted[t];
-    xi_s[t] = g->x_i[x];
-    xj_s[t] = g->x_j[x];
-    xk_s[t] = g->x_kind[x];
-    std::memcpy(&xrec_s[(size_t)t * gpo::kXRec], &g->x_rec[(size_t)x * gpo::kXRec], gpo::kXRec * sizeof(double));
-    xo_off[xi_s[t] + 1]++;
-    xk_off[xi_s[t] + 1]++;
-    if (xj_s[t] >= 0) xk_off[xj_s[t] + 1]++;
+    const int x = R.x_sorted[t];
+    R.xi_s[t] = g->x_i[x];
+    R.xj_s[t] = g->x_j[x];
+    R.xk_s[t] = g->x_kind[x];
+    std::memcpy(&R.xrec_s[(size_t)t * gpo::kXRec], &g->x_rec[(size_t)x * gpo::kXRec], gpo::kXRec * sizeof(double));
+    R.xo_off[R.xi_s[t] + 1]++;
+    R.xk_off[R.xi_s[t] + 1]++;
+    if (R.xj_s[t] >= 0) R.xk_off[R.xj_s[t] + 1]++;
   }
   for (int c = 0; c < C; ++c) {
-    xo_off[c + 1] += xo_off[c];
-    xk_off[c + 1] += xk_off[c];
+    R.xo_off[c + 1] += R.xo_off[c];
+    R.xk_off[c + 1] += R.xk_off[c];
   }
   {
-    std::vector<int32_t> fill(xk_off.begin(), xk_off.end() - 1);
+    std::vector<int32_t> fill(R.xk_off.begin(), R.xk_off.end() - 1);
     for (int t = 0; t < NX; ++t) {
-      xk_list[fill[xi_s[t]]++] = 2 * t;
-      if (xj_s[t] >= 0) xk_list[fill[xj_s[t]]++] = 2 * t + 1;
+      R.xk_list[fill[R.xi_s[t]]++] = 2 * t;
+      if (R.xj_s[t] >= 0) R.xk_list[fill[R.xj_s[t]]++] = 2 * t + 1;
     }
   }
+  // FP64 state in device order
+  R.cams = g->cam_state;
+  R.pts.resize(3 * (size_t)P);
+  for (int p = 0; p < P; ++p)
+    for (int k = 0; k < 3; ++k) R.pts[3 * (size_t)R.pt_old2new[p] + k] = g->pt_state[3 * (size_t)p + k];
 
-  // ---- memory plan
+  // ---- memory plan (uploaded arrays first)
   const Prec pr = g->prec;
   const size_t sA = at_size(pr), sJ = jt_size(pr);
-  DevBA d{};
+  DevBA& d = R.d;
   d.C = C; d.P = P; d.E = E; d.NCH = NCH; d.NS = NS; d.NX = NX; d.ch_max = ch;
   d.model = (int)ks.model;
   std::memcpy(d.camk, g->camk, sizeof(d.camk));
   d.ns_max = ns_max; d.np_max = np_max;
   d.ncblk = std::max(1, (C + gpo::kCamPerBlock - 1) / gpo::kCamPerBlock);
-  Plan pl;
-  int *e_cam, *e_pt, *pt_off_d, *ch_e0_d, *ch_p0_d, *ch_s0_d, *slot_e0_d, *slot_cam_d, *cam_s_off_d, *cam_s_list_d,
-      *slot_pos_d;
-  int *xe_i_d, *xe_j_d, *xe_kind_d, *xo_off_d, *xk_off_d, *xk_list_d;
-  double* xe_rec_d;
-  uint16_t *e_pos_d, *e_slot_d, *ch_sorted_d;
-  uint32_t* e_meta_d;
-  int32_t* slot_rec_d;
-  uint8_t *cam_fixed_d, *pt_fixed_d;
-  double *obs_d, *delta_d, *info_d = nullptr;
-  pl.add(&e_cam, E); pl.add(&e_pt, E); pl.add(&obs_d, (size_t)M * E); pl.add(&delta_d, E);
-  if (g->any_info) pl.add(&info_d, (size_t)NQ * E);
-  pl.add(&pt_off_d, P + 1); pl.add(&ch_e0_d, NCH + 1); pl.add(&ch_p0_d, NCH + 1);
-  pl.add(&ch_s0_d, NCH + 1); pl.add(&e_pos_d, E); pl.add(&e_slot_d, E);
-  pl.add(&ch_sorted_d, E); pl.add(&slot_e0_d, NS + 1); pl.add(&slot_cam_d, std::max(NS, 1));
-  pl.add(&e_meta_d, (size_t)E + 4); pl.add(&slot_rec_d, 4 * (size_t)std::max(NS, 1));
-  pl.add(&cam_s_off_d, C + 1); pl.add(&cam_s_list_d, std::max(NS, 1)); pl.add(&slot_pos_d, std::max(NS, 1));
-  pl.add(&cam_fixed_d, std::max(C, 1)); pl.add(&pt_fixed_d, std::max(P, 1));
-  pl.add(&xe_i_d, std::max(NX, 1)); pl.add(&xe_j_d, std::max(NX, 1)); pl.add(&xe_kind_d, std::max(NX, 1));
-  pl.add(&xe_rec_d, (size_t)std::max(NX, 1) * gpo::kXRec);
-  pl.add(&xo_off_d, C + 1); pl.add(&xk_off_d, C + 1); pl.add(&xk_list_d, std::max(2 * NX, 1));
+  R.npb = std::max(1, (P + 255) / 256);
+  R.zeros_ch.assign(std::max(NCH, 1), 0);
+  R.zeros_cb.assign(d.ncblk, 0);
+  R.zeros_pb.assign(R.npb, 0);
+  R.zeros_small.assign(4, 0);
+  R.xzeros.assign(std::max(NX, 1), 0.0);
+  R.sc0.assign(1, Scalars{});
+  Plan& pl = R.pl;
+  pl.up(&R.e_cam_d, E, R.e_cam_s); pl.up(&R.e_pt_d, E, R.e_pt_s); pl.up(&R.obs_d, (size_t)M * E, R.obs_s);
+  pl.up(&R.delta_d, E, R.delta_s);
+  if (g->any_info) pl.up(&R.info_d, (size_t)NQ * E, R.info_s);
+  pl.up(&R.pt_off_d, P + 1, R.pt_off); pl.up(&R.ch_e0_d, NCH + 1, R.ch_e0); pl.up(&R.ch_p0_d, NCH + 1, R.ch_p0);
+  pl.up(&R.ch_s0_d, NCH + 1, R.ch_s0); pl.up(&R.e_pos_d, E, R.e_pos); pl.up(&R.e_slot_d, E, R.e_slot);
+  pl.up(&R.ch_sorted_d, E, R.ch_sorted); pl.up(&R.slot_e0_d, NS + 1, R.slot_e0);
+  pl.up(&R.slot_cam_d, std::max(NS, 1), R.slot_cam);
+  pl.up(&R.e_meta_d, (size_t)E + 4, R.e_meta); pl.up(&R.slot_rec_d, 4 * (size_t)std::max(NS, 1), R.slot_rec);
+  pl.up(&R.cam_s_off_d, C + 1, R.cam_s_off); pl.up(&R.cam_s_list_d, std::max(NS, 1), R.cam_s_list);
+  pl.up(&R.slot_pos_d, std::max(NS, 1), R.slot_pos);
+  pl.up(&R.cam_fixed_d, std::max(C, 1), R.cam_fixed); pl.up(&R.pt_fixed_d, std::max(P, 1), R.pt_fixed_s);
+  pl.up(&R.xe_i_d, std::max(NX, 1), R.xi_s); pl.up(&R.xe_j_d, std::max(NX, 1), R.xj_s);
+  pl.up(&R.xe_kind_d, std::max(NX, 1), R.xk_s);
+  pl.up(&R.xe_rec_d, (size_t)std::max(NX, 1) * gpo::kXRec, R.xrec_s);
+  pl.up(&R.xo_off_d, C + 1, R.xo_off); pl.up(&R.xk_off_d, C + 1, R.xk_off);
+  pl.up(&R.xk_list_d, std::max(2 * NX, 1), R.xk_list);
+  pl.up(&d.xe_cost, std::max(NX, 1), R.xzeros); pl.up(&d.xe_md, std::max(NX, 1), R.xzeros);
+  pl.up(&d.cam, (size_t)SS * C, R.cams);
+  pl.up(&d.pt, 3 * (size_t)P, R.pts);
+  pl.up(&d.sc, 1, R.sc0);
+  pl.up(&R.ch_prob_d, std::max(NCH, 1), R.zeros_ch); pl.up(&R.cb_prob_d, d.ncblk, R.zeros_cb);
+  pl.up(&R.pb_prob_d, R.npb, R.zeros_pb);
+  pl.up(&R.base_d, 1, R.zeros_small); pl.up(&R.running_d, 2, R.zeros_small);
+  // device-only arrays
   pl.add(&d.xe_J, (size_t)std::max(NX, 1) * gpo::kXJ); pl.add(&d.xe_r, (size_t)std::max(NX, 1) * gpo::kXRows);
-  pl.add(&d.xe_cost, std::max(NX, 1)); pl.add(&d.xe_md, std::max(NX, 1));
   pl.add_raw(&d.xe_H, (size_t)std::max(NX, 1) * DB * DB * sA);
-  pl.add(&d.cam, (size_t)SS * C); pl.add(&d.cam_cand, (size_t)SS * C);
+  pl.add(&d.cam_cand, (size_t)SS * C);
   pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
-  pl.add(&d.pt, 3 * (size_t)P); pl.add(&d.pt_cand, 3 * (size_t)P);
-  pl.add_raw(&d.J, std::max<size_t>(jpos, 8) * sJ);
+  pl.add(&d.pt_cand, 3 * (size_t)P);
+  pl.add_raw(&d.J, std::max<size_t>(R.jpos, 8) * sJ);
   pl.add_raw(&d.Hpp, 6 * (size_t)P * sA); pl.add_raw(&d.bp, 3 * (size_t)P * sA);
   pl.add_raw(&d.Hinv, 6 * (size_t)P * sA); pl.add_raw(&d.dp, 3 * (size_t)P * sA);
   pl.add_raw(&d.pt_rec, (size_t)std::max(P, 1) * (pr == Prec::F64 ? 64 : 32));
@@ -376,15 +470,28 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   pl.add_raw(&d.p2, (size_t)DB * C * sA);
   pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
   pl.add(&d.cblk_part, 2 * 4 * (size_t)d.ncblk);   // cam_apply runs four CTAs per camera block
-  pl.add(&d.sc, 1);
   pl.add(&d.hist, gpo::kMaxHistory);
-  const int npb = std::max(1, (P + 255) / 256);
-  DevBA* desc_d;
-  int *ch_prob_d, *cb_prob_d, *pb_prob_d, *base_d, *running_d;
-  pl.add(&desc_d, 1);
-  pl.add(&ch_prob_d, std::max(NCH, 1)); pl.add(&cb_prob_d, d.ncblk); pl.add(&pb_prob_d, npb);
-  pl.add(&base_d, 1); pl.add(&running_d, 2);
-  const size_t bytes = pl.total();
+  pl.add(&R.desc_d, 1);
+  R.bytes = pl.total();
+  g->prep.reset(pp.release());
+  return GPO_OK;
+}
+
+// Plans the graph (sorted topology, chunks, slots, memory plan; kept until the upload)
+// and, unless plan_bytes is given, in which case only the planned size is returned,
+// allocates the arena and uploads everything with one copy (no wait: the copy
+// from pageable host memory is staged before the call returns).
+gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
+  if (g->finalized) {
+    if (plan_bytes) *plan_bytes = g->arena_bytes;
+    return GPO_OK;
+  }
+  if (!g->prep) {
+    gpo_status s = prepare(g);
+    if (s != GPO_OK) return s;
+  }
+  Prepared& R = *g->prep;
+  const size_t bytes = R.bytes;
   if (plan_bytes) {
     *plan_bytes = bytes;
     return GPO_OK;
@@ -406,81 +513,51 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   }
   g->arena = base;
   g->arena_bytes = bytes;
-  pl.assign(static_cast<char*>(base));
-  d.e_cam = e_cam; d.e_pt = e_pt; d.obs = obs_d; d.e_delta = delta_d; d.e_sqinfo = info_d;
-  d.pt_off = pt_off_d; d.ch_e0 = ch_e0_d; d.ch_p0 = ch_p0_d; d.ch_s0 = ch_s0_d;
-  d.e_pos = e_pos_d; d.e_slot = e_slot_d; d.ch_sorted = ch_sorted_d; d.slot_e0 = slot_e0_d; d.slot_cam = slot_cam_d;
-  d.cam_s_off = cam_s_off_d; d.cam_s_list = cam_s_list_d; d.slot_pos = slot_pos_d; d.cam_fixed = cam_fixed_d; d.pt_fixed = pt_fixed_d;
-  d.xe_i = xe_i_d; d.xe_j = xe_j_d; d.xe_kind = xe_kind_d; d.xe_rec = xe_rec_d;
-  d.xo_off = xo_off_d; d.xk_off = xk_off_d; d.xk_list = xk_list_d;
-  d.e_meta = e_meta_d; d.slot_rec = reinterpret_cast<const int4*>(slot_rec_d);
+  R.pl.assign(static_cast<char*>(base));
+  DevBA& d = R.d;
+  d.e_cam = R.e_cam_d; d.e_pt = R.e_pt_d; d.obs = R.obs_d; d.e_delta = R.delta_d; d.e_sqinfo = R.info_d;
+  d.pt_off = R.pt_off_d; d.ch_e0 = R.ch_e0_d; d.ch_p0 = R.ch_p0_d; d.ch_s0 = R.ch_s0_d;
+  d.e_pos = R.e_pos_d; d.e_slot = R.e_slot_d; d.ch_sorted = R.ch_sorted_d; d.slot_e0 = R.slot_e0_d;
+  d.slot_cam = R.slot_cam_d; d.cam_s_off = R.cam_s_off_d; d.cam_s_list = R.cam_s_list_d; d.slot_pos = R.slot_pos_d;
+  d.cam_fixed = R.cam_fixed_d; d.pt_fixed = R.pt_fixed_d;
+  d.xe_i = R.xe_i_d; d.xe_j = R.xe_j_d; d.xe_kind = R.xe_kind_d; d.xe_rec = R.xe_rec_d;
+  d.xo_off = R.xo_off_d; d.xk_off = R.xk_off_d; d.xk_list = R.xk_list_d;
+  d.e_meta = R.e_meta_d; d.slot_rec = reinterpret_cast<const int4*>(R.slot_rec_d);
   d.dbg_r = nullptr;
-  cudaStream_t st = g->stream;
-  GPO_CUDA(g, up(e_cam, e_cam_s, st));
-  GPO_CUDA(g, up(e_pt, e_pt_s, st));
-  GPO_CUDA(g, up(obs_d, obs_s, st));
-  GPO_CUDA(g, up(delta_d, delta_s, st));
-  if (g->any_info) GPO_CUDA(g, up(info_d, info_s, st));
-  GPO_CUDA(g, up(pt_off_d, pt_off, st));
-  GPO_CUDA(g, up(ch_e0_d, ch_e0, st));
-  GPO_CUDA(g, up(ch_p0_d, ch_p0, st));
-  GPO_CUDA(g, up(ch_s0_d, ch_s0, st));
-  GPO_CUDA(g, up(e_pos_d, e_pos, st));
-  GPO_CUDA(g, up(e_slot_d, e_slot, st));
-  GPO_CUDA(g, up(ch_sorted_d, ch_sorted, st));
-  GPO_CUDA(g, up(slot_e0_d, slot_e0, st));
-  GPO_CUDA(g, up(slot_cam_d, slot_cam, st));
-  GPO_CUDA(g, up(cam_s_off_d, cam_s_off, st));
-  GPO_CUDA(g, up(cam_s_list_d, cam_s_list, st));
-  GPO_CUDA(g, up(slot_pos_d, slot_pos, st));
-  GPO_CUDA(g, up(e_meta_d, e_meta, st));
-  GPO_CUDA(g, up(slot_rec_d, slot_rec, st));
-  GPO_CUDA(g, up(cam_fixed_d, g->cam_fixed, st));
-  GPO_CUDA(g, up(pt_fixed_d, pt_fixed_s, st));
-  GPO_CUDA(g, up(xe_i_d, xi_s, st));
-  GPO_CUDA(g, up(xe_j_d, xj_s, st));
-  GPO_CUDA(g, up(xe_kind_d, xk_s, st));
-  GPO_CUDA(g, up(xe_rec_d, xrec_s, st));
-  GPO_CUDA(g, up(xo_off_d, xo_off, st));
-  GPO_CUDA(g, up(xk_off_d, xk_off, st));
-  if (NX) GPO_CUDA(g, up(xk_list_d, xk_list, st));
-  GPO_CUDA(g, up(d.cam, g->cam_state, st));
+  const cudaStream_t st = g->stream;
   {
-    std::vector<double> pts(3 * (size_t)P);
-    for (int p = 0; p < P; ++p)
-      for (int k = 0; k < 3; ++k) pts[3 * (size_t)g->pt_old2new[p] + k] = g->pt_state[3 * (size_t)p + k];
-    GPO_CUDA(g, up(d.pt, pts, st));
+    std::vector<char> img;
+    const size_t n = R.pl.image(img);
+    if (n) GPO_CUDA(g, cudaMemcpyAsync(base, img.data(), n, cudaMemcpyHostToDevice, st));
   }
-  GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(jpos, 8) * sJ, st));
-  GPO_CUDA(g, cudaMemsetAsync(d.sc, 0, sizeof(Scalars), st));
-  GPO_CUDA(g, cudaMemsetAsync(d.dp, 0, 3 * (size_t)P * sA, st));
-  GPO_CUDA(g, cudaMemsetAsync(d.xe_cost, 0, std::max(NX, 1) * sizeof(double), st));
-  GPO_CUDA(g, cudaMemsetAsync(d.xe_md, 0, std::max(NX, 1) * sizeof(double), st));
-  GPO_CUDA(g, cudaMemsetAsync(ch_prob_d, 0, std::max(NCH, 1) * sizeof(int), st));
-  GPO_CUDA(g, cudaMemsetAsync(cb_prob_d, 0, d.ncblk * sizeof(int), st));
-  GPO_CUDA(g, cudaMemsetAsync(pb_prob_d, 0, npb * sizeof(int), st));
-  GPO_CUDA(g, cudaMemsetAsync(base_d, 0, sizeof(int), st));
-  GPO_CUDA(g, cudaMemsetAsync(running_d, 0, 2 * sizeof(int), st));
-  GPO_CUDA(g, cudaMemcpyAsync(desc_d, &d, sizeof(DevBA), cudaMemcpyHostToDevice, st));
-  GPO_CUDA(g, cudaStreamSynchronize(st));
+  GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(R.jpos, 8) * jt_size(g->prec), st));
+  GPO_CUDA(g, cudaMemsetAsync(d.dp, 0, 3 * (size_t)d.P * at_size(g->prec), st));
+  GPO_CUDA(g, cudaMemcpyAsync(R.desc_d, &d, sizeof(DevBA), cudaMemcpyHostToDevice, st));
   gpo::LaunchSet ls{};
-  ls.probs = desc_d;
-  ls.ch_prob = ch_prob_d; ls.ch_base = base_d;
-  ls.cb_prob = cb_prob_d; ls.cb_base = base_d;
-  ls.pb_prob = pb_prob_d; ls.pb_base = base_d;
-  ls.running = running_d;
-  ls.err = running_d + 1;
+  ls.probs = R.desc_d;
+  ls.ch_prob = R.ch_prob_d; ls.ch_base = R.base_d;
+  ls.cb_prob = R.cb_prob_d; ls.cb_base = R.base_d;
+  ls.pb_prob = R.pb_prob_d; ls.pb_base = R.base_d;
+  ls.running = R.running_d;
+  ls.err = R.running_d + 1;
   ls.spmv_variant = g->desc.spmv_variant;
-  ls.nprob = 1; ls.n_ch = NCH; ls.n_cb = C > 0 ? d.ncblk : 0; ls.n_pb = P > 0 ? npb : 0;
-  ls.ch_max = ch;
-  ls.ns_max = ns_max;
-  ls.np_max = np_max;
+  ls.nprob = 1; ls.n_ch = R.NCH; ls.n_cb = d.C > 0 ? d.ncblk : 0; ls.n_pb = d.P > 0 ? R.npb : 0;
+  ls.ch_max = R.ch;
+  ls.ns_max = d.ns_max;
+  ls.np_max = d.np_max;
   g->ls = ls;
-  g->ks = &ks;
-  g->dev_desc = desc_d;
-  g->h_ch_e0 = ch_e0;
+  g->ks = &gpo_host::kernels_of(g);
+  g->dev_desc = R.desc_d;
+  g->ch_max = R.ch;
+  g->j_elems = R.jpos;
+  g->h_ch_e0 = std::move(R.ch_e0);
+  g->sorted_edge = std::move(R.sorted_edge);
+  g->pt_new2old = std::move(R.pt_new2old);
+  g->pt_old2new = std::move(R.pt_old2new);
+  g->x_sorted = std::move(R.x_sorted);
   g->dev = d;
   g->finalized = true;
+  g->prep.reset();
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
@@ -843,6 +920,7 @@ gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int6
     g->pt_fixed.insert(g->pt_fixed.end(), n, 0);
     g->pt_state.insert(g->pt_state.end(), 3 * n, 0.0);
   }
+  g->prep.reset();
   if (first_id) *first_id = id0;
   return GPO_OK;
 }
@@ -856,6 +934,7 @@ gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig) {
   std::memset(g->camk, 0, sizeof(g->camk));
   std::memcpy(g->camk, rig, 17 * sizeof(double));
   g->camk_set = true;
+  g->prep.reset();
   return GPO_OK;
 }
 
@@ -868,44 +947,64 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
     return fail(g, GPO_ERR_ARG, "edge kind %d does not fit the graph's camera kind %d", kind, g->cam_kind);
   if (n > 0 && !meas) return fail(g, GPO_ERR_ARG, "null measurements");
   const int64_t V = (int64_t)g->v_kind.size();
-  const size_t base = g->e_cam.size();
-  auto undo = [&] {
-    g->e_cam.resize(base); g->e_pt.resize(base); g->e_eid.resize(base); g->e_obs.resize((size_t)m * base);
-    g->e_delta.resize(base); g->e_active.resize(base); g->e_sqinfo.resize((size_t)nq * base);
-  };
+  // validate everything first: a failed call leaves the graph unchanged
   for (int64_t i = 0; i < n; ++i) {
     const int64_t c = ids[2 * i], p = ids[2 * i + 1];
-    if (c < 0 || c >= V || p < 0 || p >= V || g->v_kind[c] != ck || g->v_kind[p] != GPO_V_POINT3) {
-      undo();
+    if (c < 0 || c >= V || p < 0 || p >= V || g->v_kind[c] != ck || g->v_kind[p] != GPO_V_POINT3)
       return fail(g, GPO_ERR_ARG, "edge %lld: ids must be (%s, point)", (long long)i,
                   ck == GPO_V_NAV15 ? "navigation state" : "camera");
-    }
-    double U[9];
-    for (int k = 0; k < m * m; ++k) U[k] = (k % (m + 1)) == 0 ? 1.0 : 0.0;   // m x m identity
-    if (info) {
-      if (!sqrt_info(info + (size_t)m * m * i, m, U)) {
-        undo();
+  }
+  std::vector<double> packed;   // packed upper square roots of the information, if given
+  bool non_identity = false;
+  if (info) {
+    packed.resize((size_t)nq * n);
+    for (int64_t i = 0; i < n; ++i) {
+      double U[9];
+      if (!sqrt_info(info + (size_t)m * m * i, m, U))
         return fail(g, GPO_ERR_ARG, "edge %lld: information matrix is not symmetric positive definite", (long long)i);
-      }
+      int t = 0;
+      for (int a = 0; a < m; ++a)
+        for (int b = a; b < m; ++b, ++t) {
+          packed[(size_t)nq * i + t] = U[a * m + b];
+          if (U[a * m + b] != (a == b ? 1.0 : 0.0)) non_identity = true;
+        }
     }
-    g->e_cam.push_back((int32_t)g->v_local[c]);
-    g->e_pt.push_back((int32_t)g->v_local[p]);
-    g->e_eid.push_back((int64_t)g->ed_kind.size() + i);
-    for (int k = 0; k < m; ++k) g->e_obs.push_back(meas[(size_t)m * i + k]);
-    for (int a = 0; a < m; ++a)
-      for (int b = a; b < m; ++b) {
-        const double u = U[a * m + b];
-        if (u != (a == b ? 1.0 : 0.0)) g->any_info = true;
-        g->e_sqinfo.push_back(u);
-      }
-    g->e_delta.push_back(loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0);
-    g->e_active.push_back(1);
   }
+  const size_t base = g->e_cam.size();
+  const int64_t eid0 = (int64_t)g->ed_kind.size();
+  g->e_cam.resize(base + n);
+  g->e_pt.resize(base + n);
+  g->e_eid.resize(base + n);
+  g->e_delta.resize(base + n, loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0);
+  g->e_active.resize(base + n, 1);
+  g->e_obs.insert(g->e_obs.end(), meas, meas + (size_t)m * n);
   for (int64_t i = 0; i < n; ++i) {
-    g->ed_kind.push_back((int8_t)kind);
-    g->ed_local.push_back((int64_t)base + i);
+    g->e_cam[base + i] = (int32_t)g->v_local[ids[2 * i]];
+    g->e_pt[base + i] = (int32_t)g->v_local[ids[2 * i + 1]];
+    g->e_eid[base + i] = eid0 + i;
   }
+  // square roots of the information are stored once some edge has a non-identity one
+  if (non_identity && !g->any_info) {
+    g->any_info = true;
+    g->e_sqinfo.assign((size_t)nq * base, 0.0);
+    for (size_t e = 0; e < base; ++e)
+      for (int a = 0, t = 0; a < m; ++a)
+        for (int b = a; b < m; ++b, ++t) g->e_sqinfo[(size_t)nq * e + t] = a == b ? 1.0 : 0.0;
+  }
+  if (g->any_info) {
+    if (info) {
+      g->e_sqinfo.insert(g->e_sqinfo.end(), packed.begin(), packed.end());
+    } else {
+      for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < m; ++a)
+          for (int b = a; b < m; ++b) g->e_sqinfo.push_back(a == b ? 1.0 : 0.0);
+    }
+  }
+  g->ed_kind.resize(eid0 + n, (int8_t)kind);
+  g->ed_local.resize(eid0 + n);
+  for (int64_t i = 0; i < n; ++i) g->ed_local[eid0 + i] = (int64_t)base + i;
   if (n > 0) g->cam_kind = ck;
+  g->prep.reset();
   return GPO_OK;
 }
 
@@ -960,6 +1059,7 @@ static gpo_status add_nav_edges(gpo_graph* g, int32_t kind, int64_t n, const int
     g->ed_kind.push_back((int8_t)kind);
     g->ed_local.push_back((int64_t)base + i);
   }
+  g->prep.reset();
   return GPO_OK;
 }
 
@@ -986,6 +1086,7 @@ gpo_status gpo_set_fixed(gpo_graph* g, int64_t vid, int32_t fixed) {
   if (vid < 0 || vid >= (int64_t)g->v_kind.size()) return fail(g, GPO_ERR_ARG, "no vertex %lld", (long long)vid);
   if (is_camera(g->v_kind[vid])) g->cam_fixed[g->v_local[vid]] = fixed ? 1 : 0;
   else g->pt_fixed[g->v_local[vid]] = fixed ? 1 : 0;
+  g->prep.reset();
   return GPO_OK;
 }
 
@@ -996,6 +1097,7 @@ gpo_status gpo_set_edge_active(gpo_graph* g, int64_t eid, int32_t active) {
   const int k = g->ed_kind[eid];
   if (k == GPO_E_BA_REPROJ || k == GPO_E_STEREO) g->e_active[g->ed_local[eid]] = active ? 1 : 0;
   else g->x_active[g->ed_local[eid]] = active ? 1 : 0;
+  g->prep.reset();
   return GPO_OK;
 }
 
@@ -1023,6 +1125,7 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
   const int64_t loc = g->v_local[first];
   g->cost_valid = false;
   if (!g->finalized) {
+    g->prep.reset();
     std::vector<double>& dst = is_camera(kind) ? g->cam_state : g->pt_state;
     if (on_device) {
       GPO_CUDA(g, cudaMemcpy(dst.data() + loc * w, state, n * w * sizeof(double), cudaMemcpyDeviceToHost));

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -36,6 +37,11 @@ struct Profiler {
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+};
+
+struct Prepared;                       // host-side plan of a graph's device image (api.cu)
+struct PrepDeleter {
+  void operator()(Prepared* p) const;
 };
 
 struct gpo_graph {
@@ -75,6 +81,7 @@ struct gpo_graph {
   bool camk_set = false;
 
   // finalized topology
+  std::unique_ptr<Prepared, PrepDeleter> prep;   // planned, not yet uploaded
   bool finalized = false;
   const gpo::KernelSet* ks = nullptr;
   int ch_max = 0;
