@@ -39,30 +39,52 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
 
+  // per-edge positions: one packed word per edge when chunks fit 10-bit positions
   int pos[EPT], slot[EPT], ptl[EPT];
+  const bool packed = ls.ch_max <= 1024;
 #pragma unroll
   for (int m = 0; m < EPT; ++m) {
     const int i = threadIdx.x + m * kThreads;
     if (i < cr.nE) {
-      pos[m] = __ldg(d.e_pos + cr.e0 + i);
-      slot[m] = __ldg(d.e_slot + cr.e0 + i);
-      ptl[m] = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
+      if (packed) {
+        const uint32_t w = __ldg(d.e_meta + cr.e0 + i);
+        pos[m] = (int)(w & 1023u);
+        slot[m] = (int)((w >> 10) & 1023u);
+        ptl[m] = (int)(w >> 20);
+      } else {
+        pos[m] = __ldg(d.e_pos + cr.e0 + i);
+        slot[m] = __ldg(d.e_slot + cr.e0 + i);
+        ptl[m] = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
+      }
     }
   }
-  // the search direction p_k = (z_k + beta_k p_{k-1}) / n_k, formed per slot camera
+  // one thread per slot: its record (edge range, camera, partial row) and the search
+  // direction p_k = (z_k + beta_k p_{k-1}) / n_k of its camera
   const AT* zv = reinterpret_cast<const AT*>(d.z);
   const AT* pold = reinterpret_cast<const AT*>(d.sc->pidx ? d.p2 : d.p);
   const AT beta = (AT)d.sc->beta, inv_n = (AT)d.sc->inv_n;
-  for (int w = threadIdx.x; w < cr.nS * DC; w += kThreads) {
-    const int sl = w / DC, k = w - sl * DC;
-    const size_t o = DB * (size_t)__ldg(d.slot_cam + cr.s0 + sl) + k;
-    xs[w] = (zv[o] + beta * pold[o]) * inv_n;
+  for (int t = threadIdx.x; t < cr.nS; t += kThreads) {
+    const int4 r4 = __ldg(d.slot_rec + cr.s0 + t);
+    so[t] = r4.x;
+    so[t + 1] = r4.y;
+    sp[t] = r4.w;
+    const size_t o = DB * (size_t)r4.z;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) xs[DC * t + k] = (zv[o + k] + beta * pold[o + k]) * inv_n;
   }
-  for (int t = threadIdx.x; t < cr.nS; t += kThreads) sp[t] = __ldg(d.slot_pos + cr.s0 + t);
-  const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv) + 6 * (size_t)cr.p0;
-  for (int w = threadIdx.x; w < cr.nP * 6; w += kThreads) hv[w] = Hinv[w];
-  for (int j = threadIdx.x; j <= cr.nP; j += kThreads) po[j] = __ldg(d.pt_off + cr.p0 + j) - cr.e0;
-  for (int t = threadIdx.x; t <= cr.nS; t += kThreads) so[t] = __ldg(d.slot_e0 + cr.s0 + t) - cr.e0;
+  // one thread per point: its record (H_pp^-1 and edge range)
+  constexpr size_t PRB = (6 * sizeof(AT) + 8 + 15) & ~(size_t)15;
+  const unsigned char* prec = static_cast<const unsigned char*>(d.pt_rec) + (size_t)cr.p0 * PRB;
+  for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
+    const AT* h = reinterpret_cast<const AT*>(prec + (size_t)j * PRB);
+    const int* se = reinterpret_cast<const int*>(prec + (size_t)j * PRB + 6 * sizeof(AT));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hv[6 * j + k] = h[k];
+    po[j] = se[0];
+    po[j + 1] = se[1];
+  }
+  if (threadIdx.x == 0 && cr.nP == 0) po[0] = 0;
+  if (threadIdx.x == 0 && cr.nS == 0) so[0] = 0;
   __syncthreads();
 
   // ---- pass 1: a_e = Jp^T (Jc x_c)
