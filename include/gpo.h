@@ -257,6 +257,15 @@ gpo_status gpo_get_history(gpo_graph* g, gpo_iter_record* out, int32_t cap, int3
 /* Device bytes held by the graph (planned arena plus state buffers). */
 gpo_status gpo_memory_footprint(gpo_graph* g, size_t* bytes);
 
+/* Plans the graph on the host -- sorted topology, chunks, slots and the device memory
+ * plan -- without touching the device, and returns the bytes its device image will
+ * take.  Optional: gpo_optimize and gpo_server_submit plan when needed and reuse a plan
+ * made here (until the next add / set call on the graph).  Needs no GPU and may run
+ * concurrently for different graphs (e.g. on worker threads that build requests for a
+ * server).  Errors: GPO_ERR_ARG, GPO_ERR_STATE (missing stereo rig),
+ * GPO_ERR_UNSUPPORTED, GPO_ERR_OOM (host). */
+gpo_status gpo_graph_plan(gpo_graph* g, size_t* bytes);
+
 /* Per-kernel statistics of the kernels the library launches (gpo_get_profile). */
 typedef struct {
   char name[32];              /* kernel class, e.g. "spmv" (the PCG Schur product) */

@@ -1301,6 +1301,11 @@ gpo_status gpo_get_profile(gpo_graph* g, gpo_kernel_profile* out, int32_t cap, i
   return GPO_OK;
 }
 
+gpo_status gpo_graph_plan(gpo_graph* g, size_t* bytes) {
+  if (!g || !bytes) return GPO_ERR_ARG;
+  return finalize(g, bytes);
+}
+
 gpo_status gpo_memory_footprint(gpo_graph* g, size_t* bytes) {
   if (!g || !bytes) return GPO_ERR_ARG;
   *bytes = g->arena_bytes;

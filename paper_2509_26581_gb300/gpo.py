@@ -86,6 +86,7 @@ _SIGS = {
     "gpo_get_state": (C.c_int, [_P, C.c_int64, C.c_int64, _P, C.c_int32]),
     "gpo_get_history": (C.c_int, [_P, C.POINTER(gpo_iter_record), C.c_int32, C.POINTER(C.c_int32)]),
     "gpo_memory_footprint": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "gpo_graph_plan": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
     "gpo_set_profiling": (C.c_int, [_P, C.c_int32]),
     "gpo_get_profile": (C.c_int, [_P, C.POINTER(gpo_kernel_profile), C.c_int32, C.POINTER(C.c_int32)]),
     "gpo_last_error": (C.c_char_p, [_P]),
@@ -254,6 +255,12 @@ class Graph:
         return {r.name.decode(): dict(launches=r.launches, timed=r.timed_launches,
                                       active=r.active_launches, total_ms=r.total_ms,
                                       active_ms=r.active_ms) for r in buf[:n.value]}
+
+    def plan(self) -> int:
+        """Host-side planning (gpo_graph_plan); returns the planned device bytes."""
+        v = C.c_size_t()
+        _check(lib.gpo_graph_plan(self.h, C.byref(v)), self.h)
+        return v.value
 
     def footprint(self) -> int:
         v = C.c_size_t()

@@ -1,9 +1,10 @@
 """Serving driver over the C ABI's continuous-batching loop (gpo_server_*).
 
-Requests (local bundle-adjustment windows) arrive at given times; the driver submits
-every request whose arrival time has passed, advances the server by one step (admit,
-one LM iteration for every resident window, retire), and records each request's
-latency from arrival to retirement.  Every solve runs in the library's kernels.
+Requests (local bundle-adjustment windows) arrive at given times; the driver builds
+and plans every arrived request on worker threads, submits them in arrival order,
+advances the server by one step (admit, one LM iteration for every resident window,
+retire), and records each request's latency from arrival to retirement.  Every solve
+runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -25,44 +26,68 @@ def window_graph(p, precision: str, fix_first: bool = True, **kw) -> tuple:
 
 def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str = "bf16",
           lm_iters: int = 10, params=None, memory_budget: int = 40 << 30,
-          max_resident: int = 1024, stream=None) -> dict:
+          max_resident: int = 1024, stream=None, builders: int = 4) -> dict:
     """Runs the request stream; request i is a fresh graph of windows[pick[i]] that
-    arrives at arrivals[i] seconds.  Returns latencies, throughput and final costs."""
+    arrives at arrivals[i] seconds.  Arrived requests are built and planned on
+    `builders` worker threads (graph construction and host planning need no GPU and
+    release the interpreter inside the library), submitted in arrival order, and the
+    server is stepped on this thread.  Returns latencies (arrival to retirement),
+    throughput and final costs."""
+    from concurrent.futures import ThreadPoolExecutor
+
     sv = gpo.Server(precision, stream=stream, memory_budget=memory_budget, max_resident=max_resident)
     n = len(arrivals)
     lat = np.full(n, np.nan)
     cost = np.full(n, np.nan)
     tickets = {}
     graphs = {}
+    building = {}
+    nxt_build = 0
     nxt = 0
     done = 0
     steps = 0
     max_res = 0
+
+    def make(i):
+        g, _, _ = window_graph(windows[pick[i]], precision)
+        g.plan()
+        return g
+
+    pool = ThreadPoolExecutor(max_workers=max(1, builders))
     t0 = time.perf_counter()
-    while done < n:
-        now = time.perf_counter() - t0
-        while nxt < n and arrivals[nxt] <= now:
-            g, _, _ = window_graph(windows[pick[nxt]], precision)
-            tickets[sv.submit(g, lm_iters, params)] = nxt
-            graphs[nxt] = g
-            nxt += 1
-        res, queued, fin = sv.step()
-        steps += 1
-        max_res = max(max_res, res)
-        if fin:
-            tnow = time.perf_counter() - t0
-            for t in list(tickets):
-                rep = sv.poll(t)
-                if rep is not None:
-                    i = tickets.pop(t)
-                    lat[i] = tnow - arrivals[i]
-                    cost[i] = rep.final_cost
-                    graphs.pop(i).close()
-                    done += 1
-        if res == 0 and queued == 0 and nxt < n:
-            wait = arrivals[nxt] - (time.perf_counter() - t0)
-            if wait > 0:
-                time.sleep(min(wait, 0.01))
+    try:
+        while done < n:
+            now = time.perf_counter() - t0
+            while nxt_build < n and arrivals[nxt_build] <= now:
+                building[nxt_build] = pool.submit(make, nxt_build)
+                nxt_build += 1
+            while nxt < nxt_build and building[nxt].done():
+                g = building.pop(nxt).result()
+                tickets[sv.submit(g, lm_iters, params)] = nxt
+                graphs[nxt] = g
+                nxt += 1
+            res, queued, fin = sv.step()
+            steps += 1
+            max_res = max(max_res, res)
+            if fin:
+                tnow = time.perf_counter() - t0
+                for t in list(tickets):
+                    rep = sv.poll(t)
+                    if rep is not None:
+                        i = tickets.pop(t)
+                        lat[i] = tnow - arrivals[i]
+                        cost[i] = rep.final_cost
+                        graphs.pop(i).close()
+                        done += 1
+            if res == 0 and queued == 0:       # idle: wait for a build or the next arrival
+                if nxt < nxt_build:
+                    building[nxt].result()
+                elif nxt_build < n:
+                    wait = arrivals[nxt_build] - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+    finally:
+        pool.shutdown(wait=True)
     total = time.perf_counter() - t0
     sv.close()
     return dict(latency=lat, final_cost=cost, seconds=total, steps=steps, max_resident=max_res,
