@@ -248,6 +248,67 @@ def extra_vi(dev, stream, iters: int = 10) -> dict:
     return out
 
 
+def accumulation_bytes(E: int, P: int, NS: int, precision: str) -> float:
+    """Compulsory bytes of one linearisation + Schur preparation (the accumulation phase):
+    linearisation reads observations, indices, thresholds and point states and writes
+    the Jacobian rows, point blocks and camera slot partials; the Schur preparation
+    reads the rows and point blocks and writes the point inverses, point records and
+    Schur slot partials."""
+    sJ = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    sA = 8 if precision == "fp64" else 4
+    prb = 64 if precision == "fp64" else 32
+    lin = E * (16 + 8 + 8 + 2 + 24 * sJ) + P * (24 + 9 * sA) + NS * 54 * sA
+    schur = E * (24 * sJ + 4 + 2) + P * (9 * sA + 6 * sA + prb) + NS * 54 * sA
+    return lin + schur
+
+
+def extra_large(dev, stream, iters: int = 3) -> dict:
+    """Large BA workload (13,000 cameras, 4.5M points, ~29M observations, geometric tracks
+    of mean 6.5 capped at 200): LM iterations per second, the Schur product's and the
+    accumulation phase's achieved bandwidth, and the device footprint, in BF16 storage
+    (mixed precision with the FP64 gain ratio) against the FP64 path."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo, synth
+    p = synth.ba_large(2)
+    params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
+    peak, peak_kind = load_peaks()
+    out = dict(workload=p.name, cameras=p.n_cams, points=p.n_pts, edges=p.n_edges, lm_iters=iters,
+               peak=peak, peak_source=peak_kind)
+    for prec in ("bf16", "fp32", "fp64"):
+        g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec,
+                                 device=dev, stream=stream.cuda_stream)
+        g.optimize(1, params)
+        g.set_initial(c0, p.cams0)
+        g.set_initial(p0, p.pts0)
+        info = g.info()
+        g.set_profiling(True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        rep = g.optimize(iters, params)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        prof = g.profile()
+        sp = prof["spmv"]
+        spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
+        acc_ms = (prof["linearize"]["active_ms"] + prof["schur_prepare"]["active_ms"]) / max(1, prof["linearize"]["active"])
+        alg_s = spmv_algorithmic_bytes(p.n_edges, p.n_pts, prec)
+        alg_a = accumulation_bytes(p.n_edges, p.n_pts, info["slots"], prec)
+        out[prec] = dict(lm_iter_per_s=iters / (ms / 1e3), final_cost=rep.final_cost, pcg_iters=rep.pcg_iters_total,
+                         footprint_bytes=g.footprint(), schedule=g.knobs,
+                         spmv=dict(avg_ms=spmv_ms, achieved_gbs=alg_s / (spmv_ms * 1e-3) / 1e9,
+                                   frac=alg_s / (spmv_ms * 1e-3) / 1e9 / peak),
+                         accumulation=dict(avg_ms=acc_ms, achieved_gbs=alg_a / (acc_ms * 1e-3) / 1e9,
+                                           frac=alg_a / (acc_ms * 1e-3) / 1e9 / peak))
+        g.close()
+    for prec in ("bf16", "fp32"):
+        out[prec]["footprint_vs_fp64"] = out[prec]["footprint_bytes"] / out["fp64"]["footprint_bytes"]
+        out[prec]["speedup_vs_fp64"] = out[prec]["lm_iter_per_s"] / out["fp64"]["lm_iter_per_s"]
+    return out
+
+
 def extra_served(stream, rate: float = 2000.0, duration: float = 1.0, pool: int = 48,
                  sample: int = 48) -> dict:
     """Served local-BA windows: a Poisson stream (rate per second over `duration`) of
@@ -433,6 +494,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         line["mixed_vs_fp64"] = extra_mixed_vs_fp64(args, p, params, dev, stream, rep.final_cost)
         line["vi"] = extra_vi(dev, stream)
         line["served"] = extra_served(stream)
+        line["large"] = extra_large(dev, stream)
     return line
 
 

@@ -257,6 +257,22 @@ gpo_status gpo_get_history(gpo_graph* g, gpo_iter_record* out, int32_t cap, int3
 /* Device bytes held by the graph (planned arena plus state buffers). */
 gpo_status gpo_memory_footprint(gpo_graph* g, size_t* bytes);
 
+/* Sizes of a finalized graph (gpo_graph_info). */
+typedef struct {
+  int64_t cameras;            /* camera or navigation-state vertices */
+  int64_t points;
+  int64_t edges;              /* active observation edges */
+  int64_t extra_edges;        /* active inertial / bias edges */
+  int64_t chunks;             /* CTA chunks of the per-edge kernels */
+  int64_t slots;              /* (chunk, camera) pairs: rows of the camera-side partials */
+  int32_t chunk_edges;        /* edges per chunk in effect */
+  int32_t spmv_variant;       /* as requested in gpo_graph_desc */
+} gpo_graph_info_t;
+
+/* Fills *out for a graph that has been optimized (or otherwise finalized).
+ * Errors: GPO_ERR_ARG, GPO_ERR_STATE (not finalized). */
+gpo_status gpo_graph_info(gpo_graph* g, gpo_graph_info_t* out);
+
 /* Plans the graph on the host -- sorted topology, chunks, slots and the device memory
  * plan -- without touching the device, and returns the bytes its device image will
  * take.  Optional: gpo_optimize and gpo_server_submit plan when needed and reuse a plan
@@ -389,6 +405,11 @@ gpo_status gpo_ba_cost_noalloc(int32_t device, void* cuda_stream, const double* 
  *        camera-side edges are FP64.  Disabled edges are written as zeros.
  * Either pointer may be NULL. */
 gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out);
+
+/* The same for the n edges edge_ids[0..n) only: row k of r_out / J_out belongs to
+ * edge_ids[k] (for sampled checks of large graphs).  Errors: GPO_ERR_ARG (unknown id). */
+gpo_status gpo_debug_linearize_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
+                                     double* J_out);
 
 /* Solves one damped system (H + lambda D^T D) dx = -b at the current state with
  * the full path (Schur, PCG, back-substitution) and given PCG options, without

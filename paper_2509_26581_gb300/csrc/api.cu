@@ -1301,6 +1301,21 @@ gpo_status gpo_get_profile(gpo_graph* g, gpo_kernel_profile* out, int32_t cap, i
   return GPO_OK;
 }
 
+gpo_status gpo_graph_info(gpo_graph* g, gpo_graph_info_t* out) {
+  if (!g || !out) return GPO_ERR_ARG;
+  if (!g->finalized) return fail(g, GPO_ERR_STATE, "the graph is not on the device");
+  const DevBA& d = g->dev;
+  out->cameras = d.C;
+  out->points = d.P;
+  out->edges = d.E;
+  out->extra_edges = d.NX;
+  out->chunks = d.NCH;
+  out->slots = d.NS;
+  out->chunk_edges = g->ch_max;
+  out->spmv_variant = g->desc.spmv_variant;
+  return GPO_OK;
+}
+
 gpo_status gpo_graph_plan(gpo_graph* g, size_t* bytes) {
   if (!g || !bytes) return GPO_ERR_ARG;
   return finalize(g, bytes);
@@ -1343,7 +1358,10 @@ static gpo_status fetch(gpo_graph* g, std::vector<char>& dst, const T* src, size
 
 extern "C" {
 
-gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
+// Linearises every edge and writes the rows of the edges `sel[0..n_sel)` (all edges in
+// id order when sel is null) to r_out / J_out, one output row per selected edge.
+static gpo_status debug_linearize_rows(gpo_graph* g, const int64_t* sel, int64_t n_sel, double* r_out,
+                                       double* J_out) {
   if (!g) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);
@@ -1375,13 +1393,25 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
   GPO_CUDA(g, cudaStreamSynchronize(g->stream));
   GPO_CUDA(g, cudaFreeAsync(dbg, g->stream));
   const size_t n_ids = g->ed_kind.size();
-  if (r_out) std::fill(r_out, r_out + (size_t)R * n_ids, 0.0);
-  if (J_out) std::fill(J_out, J_out + (size_t)R * K * n_ids, 0.0);
+  // output row of each edge id (-1: not selected)
+  std::vector<int64_t> row_of;
+  size_t n_out = n_ids;
+  if (sel) {
+    row_of.assign(n_ids, -1);
+    for (int64_t k = 0; k < n_sel; ++k) {
+      if (sel[k] < 0 || sel[k] >= (int64_t)n_ids) return fail(g, GPO_ERR_ARG, "no edge %lld", (long long)sel[k]);
+      row_of[sel[k]] = k;
+    }
+    n_out = (size_t)n_sel;
+  }
+  if (r_out) std::fill(r_out, r_out + (size_t)R * n_out, 0.0);
+  if (J_out) std::fill(J_out, J_out + (size_t)R * K * n_out, 0.0);
   const double* rv = reinterpret_cast<const double*>(rraw.data());
   for (int k = 0; k < d.NCH; ++k) {
     const int e0 = g->h_ch_e0[k], n = g->h_ch_e0[k + 1] - e0;
     for (int i = 0; i < n; ++i) {
-      const int64_t id = g->e_eid[g->sorted_edge[e0 + i]];
+      int64_t id = g->e_eid[g->sorted_edge[e0 + i]];
+      if (sel && (id = row_of[id]) < 0) continue;
       if (r_out)
         for (int a = 0; a < M; ++a) r_out[(size_t)R * id + a] = rv[(size_t)M * (e0 + i) + a];
       if (J_out) {
@@ -1397,13 +1427,24 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
   const double* xj = reinterpret_cast<const double*>(xjraw.data());
   const double* xr = reinterpret_cast<const double*>(xrraw.data());
   for (int t = 0; t < d.NX; ++t) {
-    const int64_t id = g->x_eid[g->x_sorted[t]];
+    int64_t id = g->x_eid[g->x_sorted[t]];
+    if (sel && (id = row_of[id]) < 0) continue;
     if (r_out)
       for (int a = 0; a < gpo::kXRows; ++a) r_out[(size_t)R * id + a] = xr[(size_t)gpo::kXRows * t + a];
     if (J_out)
       for (int k = 0; k < gpo::kXJ; ++k) J_out[(size_t)R * K * id + k] = xj[(size_t)gpo::kXJ * t + k];
   }
   return GPO_OK;
+}
+
+gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
+  return debug_linearize_rows(g, nullptr, 0, r_out, J_out);
+}
+
+gpo_status gpo_debug_linearize_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
+                                     double* J_out) {
+  if (!g || n < 0 || (n > 0 && !edge_ids)) return GPO_ERR_ARG;
+  return debug_linearize_rows(g, edge_ids, n, r_out, J_out);
 }
 
 gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* params, double* dx_out, int32_t* pcg_iters) {

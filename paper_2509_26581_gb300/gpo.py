@@ -58,6 +58,12 @@ class gpo_iter_record(C.Structure):
                 ("accepted", C.c_int32), ("pcg_iters", C.c_int32)]
 
 
+class gpo_graph_info_t(C.Structure):
+    _fields_ = [("cameras", C.c_int64), ("points", C.c_int64), ("edges", C.c_int64),
+                ("extra_edges", C.c_int64), ("chunks", C.c_int64), ("slots", C.c_int64),
+                ("chunk_edges", C.c_int32), ("spmv_variant", C.c_int32)]
+
+
 class gpo_kernel_profile(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("timed_launches", C.c_int64),
                 ("active_launches", C.c_int64), ("total_ms", C.c_double), ("active_ms", C.c_double)]
@@ -87,6 +93,7 @@ _SIGS = {
     "gpo_get_history": (C.c_int, [_P, C.POINTER(gpo_iter_record), C.c_int32, C.POINTER(C.c_int32)]),
     "gpo_memory_footprint": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
     "gpo_graph_plan": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "gpo_graph_info": (C.c_int, [_P, C.POINTER(gpo_graph_info_t)]),
     "gpo_set_profiling": (C.c_int, [_P, C.c_int32]),
     "gpo_get_profile": (C.c_int, [_P, C.POINTER(gpo_kernel_profile), C.c_int32, C.POINTER(C.c_int32)]),
     "gpo_last_error": (C.c_char_p, [_P]),
@@ -106,6 +113,7 @@ _SIGS = {
     "gpo_imu_preintegrate": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, _P, C.c_double, C.c_double,
                                        _P, _P, _P]),
     "gpo_debug_linearize": (C.c_int, [_P, _P, _P]),
+    "gpo_debug_linearize_edges": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
 }
@@ -256,6 +264,12 @@ class Graph:
                                       active=r.active_launches, total_ms=r.total_ms,
                                       active_ms=r.active_ms) for r in buf[:n.value]}
 
+    def info(self) -> dict:
+        """Sizes of the finalized graph (gpo_graph_info)."""
+        v = gpo_graph_info_t()
+        _check(lib.gpo_graph_info(self.h, C.byref(v)), self.h)
+        return {k: getattr(v, k) for k, _ in gpo_graph_info_t._fields_}
+
     def plan(self) -> int:
         """Host-side planning (gpo_graph_plan); returns the planned device bytes."""
         v = C.c_size_t()
@@ -275,6 +289,15 @@ class Graph:
         r = np.zeros((n_edges, R))
         J = np.zeros((n_edges, R, K))
         _check(lib.gpo_debug_linearize(self.h, _ptr(r), _ptr(J)), self.h)
+        return r, J
+
+    def debug_linearize_edges(self, edge_ids, nav: bool = False):
+        """Rows of the given edges only (gpo_debug_linearize_edges)."""
+        ids = np.ascontiguousarray(edge_ids, dtype=np.int64)
+        R, K = (9, 30) if nav else (2, 12)
+        r = np.zeros((len(ids), R))
+        J = np.zeros((len(ids), R, K))
+        _check(lib.gpo_debug_linearize_edges(self.h, _ptr(ids), len(ids), _ptr(r), _ptr(J)), self.h)
         return r, J
 
     def debug_step(self, lam: float, n_dof: int, params: gpo_lm_params | None = None):

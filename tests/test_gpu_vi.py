@@ -261,3 +261,57 @@ def test_schur_product_variants_bitwise_vi(gpo, small):
         out.append((rep.final_cost, g.get_state(n0, p.n_kf, 16), g.get_state(p0, p.n_pts, 3)))
     assert out[0][0] == out[1][0]
     assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_sampled_edges_at_full_size(gpo):
+    """The full global workload (3,000 keyframes, 200,000 landmarks, ~1.9M stereo edges)
+    as the benchmark runs it (library preintegration): a random sample of stereo edges
+    and every inertial and bias edge are checked against the oracle one edge at a time.
+    The oracle evaluates the inertial edges with the library's own records (whose
+    agreement with the oracle's preintegration test_vi_host.py pins), so this checks the
+    GPU evaluation only.  Tolerances: stereo 1e-12 relative to the edge's largest entry
+    plus the cancellation in X - p (positions reach hundreds of metres): 64 eps |p| /
+    depth; inertial 1e-11 as in the small test, plus the same cancellation in
+    p_j - p_i - v_i T scaled by the whitening."""
+    p = synth.vi_global()
+    g, n0, p0, rg = gpo.vi_graph(p, precision="fp64")
+    rng = np.random.default_rng(0)
+    a, b = rg["stereo"]
+    sid = np.sort(rng.choice(b - a, 3000, replace=False)) + a
+    r, J = g.debug_linearize_edges(sid, nav=True)
+    cam = ovi.camera_of(p.camera)
+    k = sid - a
+    nav, X = p.nav0[p.kf_idx[k]], p.pts0[p.pt_idx[k]]
+    ro, (Jn, Jp) = cam.evaluate((nav, X), p.obs[k])
+    w = np.sqrt(robust.weight(np.sum(ro * ro, axis=1), ("huber", p.huber_delta)))
+    ro = ro * w[:, None]
+    Jo = np.concatenate([Jn, Jp], axis=2) * w[:, None, None]
+    _, Xc = cam.point_in_camera(nav, X)
+    eps = np.finfo(np.float64).eps
+    kappa = 64 * eps * (np.linalg.norm(nav[:, 4:7], axis=1) + np.linalg.norm(X, axis=1)) / np.abs(Xc[:, 2])
+    scale_r = np.maximum(np.abs(ro).max(axis=1), 1.0)
+    assert np.all(np.abs(r[:, :3] - ro).max(axis=1) <= (1e-12 + kappa * 450.0) * scale_r)
+    Jg = np.concatenate([J[:, :3, :15], J[:, :3, 15:18]], axis=2)
+    assert np.all(np.abs(Jg - Jo).reshape(len(sid), -1).max(axis=1)
+                  <= (1e-12 + kappa) * np.abs(Jo).reshape(len(sid), -1).max(axis=1) + 1e-300)
+    # every inertial edge, with the library's records
+    ia, ib = rg["imu"]
+    ids = np.arange(ia, ib)
+    ri, Ji = g.debug_linearize_edges(ids, nav=True)
+    meas = np.zeros((p.n_kf - 1, gpo.GPO_IMU_MEAS_LEN))
+    info = np.zeros((p.n_kf - 1, 9, 9))
+    worst_r = worst_J = 0.0
+    for q in range(p.n_kf - 1):
+        m, _, inf = gpo.imu_preintegrate(p.imu_gyro[q], p.imu_acc[q], p.dt, p.nav0[q, 10:13], p.nav0[q, 13:16],
+                                         p.noise["sigma_g"], p.noise["sigma_a"])
+        pm = dict(dR=m[0:9].reshape(3, 3), dv=m[9:12], dp=m[12:15], JRg=m[15:24].reshape(3, 3),
+                  Jvg=m[24:33].reshape(3, 3), Jva=m[33:42].reshape(3, 3), Jpg=m[42:51].reshape(3, 3),
+                  Jpa=m[51:60].reshape(3, 3), T=m[60], bg0=m[61:64], ba0=m[64:67])
+        U = np.linalg.cholesky(inf).T
+        rr = U @ ovi.imu_residual_one(pm, p.nav0[q:q + 1], p.nav0[q + 1:q + 2])
+        Jq = np.concatenate([U @ x for x in ovi.imu_jacobians_one(pm, p.nav0[q:q + 1], p.nav0[q + 1:q + 2])], axis=1)
+        # cancellation in p_j - p_i - v_i T at |p| of hundreds of metres, through U
+        cancel = 64 * eps * np.linalg.norm(p.nav0[q, 4:7]) * np.abs(U).max()
+        worst_r = max(worst_r, np.abs(ri[q] - rr).max() / (1e-11 * max(np.abs(rr).max(), 1.0) + cancel))
+        worst_J = max(worst_J, np.abs(Ji[q] - Jq).max() / (1e-11 * np.abs(Jq).max()))
+    assert worst_r <= 1.0 and worst_J <= 1.0
