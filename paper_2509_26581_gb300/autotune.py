@@ -1,10 +1,12 @@
 """Autotuner of the per-graph schedule knobs.
 
-Two knobs of `gpo_graph_desc` change how the kernels walk a problem but not what they
-compute (every candidate gives bit-identical results; see the variant tests):
-  * chunk_edges  -- edges per CTA chunk of the per-edge kernels (256, 512, 1024);
+Two knobs of `gpo_graph_desc` change how the kernels walk a problem, not the method:
+  * chunk_edges  -- edges per CTA chunk of the per-edge kernels (256, 512, 1024); the
+                    chunking groups the per-camera partial sums, so results agree up to
+                    rounding;
   * spmv_variant -- the PCG Schur-product kernel: 2 = classic (one CTA per chunk),
-                    1 = staged (persistent CTAs, warp-specialised bulk-copy pipeline).
+                    1 = staged (persistent CTAs, warp-specialised bulk-copy pipeline);
+                    both give bit-identical results (see the variant tests).
 The best choice depends on the problem's size (how many chunks fill the GPU, how many
 slots a chunk has) and on the storage precision.  `tune` times every candidate on a
 representative problem of a size class -- a few LM iterations after a warm-up, wall

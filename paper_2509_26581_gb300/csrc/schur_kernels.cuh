@@ -181,7 +181,80 @@ __global__ void k_cost_init(LaunchSet ls) {
   if (threadIdx.x == 0) d.sc->cost = s;
 }
 
+// ---------------------------------------------------------------- per-edge records and slot rows
+
+// Both accumulation kernels first turn each edge of the chunk into a record of AT
+// values in shared memory (one row per edge, an odd number of 4-byte words apart so
+// that the edge-per-thread stores do not collide in a bank), then reduce the records
+// of each camera slot into that slot's partial row.  A record starts with
+// Y[k * M + a] (k < DC camera coordinates, a < M rows), followed by the DC-vector g:
+// the slot row is the packed upper triangle of sum_e Y_e^T Y_e (TC entries), then
+// sum_e g_e (DC entries), then zero padding up to NPA.
+template <int N>
+struct OddStride {
+  static constexpr int value = N | 1;
+};
+
+// One warp per slot (slots handed out by a shared counter, so long slots do not hold
+// up a fixed set of warps); lane l owns outputs l, l + 32, ... of the row.  All lanes
+// read the same edge's record at a time (broadcasts or distinct banks).  Each output
+// is summed over the slot's edges in slot order: acc += (sum_a Y[i][a] Y[j][a]).
+template <class Mo, class AT, int RS>
+__device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, const AT* rec,
+                                          const uint16_t* srt, AT* part, int* next) {
+  using Dm = Dims<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, TC = Dm::TC, NPA = Dm::NPA;
+  constexpr int OPL = (NPA + 31) / 32;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int oi[OPL], oj[OPL], kind[OPL];    // kind: 0 H entry, 1 vector entry, 2 padding
+#pragma unroll
+  for (int u = 0; u < OPL; ++u) {
+    const int o = lane + 32 * u;
+    kind[u] = o < TC ? 0 : (o < TC + DC ? 1 : 2);
+    oi[u] = o < TC ? tri_row<DC>(o) * M : (o < TC + DC ? M * DC + (o - TC) : 0);
+    oj[u] = o < TC ? tri_col<DC>(o) * M : 0;
+  }
+  for (;;) {
+    int sl = 0;
+    if (lane == 0) sl = atomicAdd(next, 1);
+    sl = __shfl_sync(full, sl, 0);
+    if (sl >= cr.nS) break;
+    const int qa = d.slot_e0[cr.s0 + sl] - cr.e0, qb = d.slot_e0[cr.s0 + sl + 1] - cr.e0;
+    AT acc[OPL];
+#pragma unroll
+    for (int u = 0; u < OPL; ++u) acc[u] = (AT)0;
+    for (int q = qa; q < qb; ++q) {
+      const AT* r = rec + (size_t)srt[q] * RS;
+#pragma unroll
+      for (int u = 0; u < OPL; ++u) {
+        if (kind[u] == 0) {
+          AT s = r[oi[u]] * r[oj[u]];
+#pragma unroll
+          for (int a = 1; a < M; ++a) s += r[oi[u] + a] * r[oj[u] + a];
+          acc[u] += s;
+        } else if (kind[u] == 1) {
+          acc[u] += r[oi[u]];
+        }
+      }
+    }
+    AT* out = part + (size_t)d.slot_pos[cr.s0 + sl] * NPA;
+#pragma unroll
+    for (int u = 0; u < OPL; ++u)
+      if (lane + 32 * u < NPA) out[lane + 32 * u] = acc[u];
+  }
+}
+
 // ---------------------------------------------------------------- linearisation
+
+// Record layout of the linearisation: Y = the stored (rounded) camera rows, g = Jc^T r
+// from the unrounded rows, then the point terms: packed Jp^T Jp of the stored rows (6)
+// and Jp^T r from the unrounded rows (3).
+template <class Mo>
+struct LinRec {
+  static constexpr int G = Mo::M * Mo::DC, H = G + Mo::DC, B = H + 6;
+  static constexpr int RS = OddStride<B + 3>::value;
+};
 
 // One CTA per chunk.  Writes the chunk's Jacobian rows, the undamped point blocks
 // H_pp = sum Jp^T Jp and gradients b_p, and per-slot camera partials
@@ -191,20 +264,18 @@ template <class Mo, class JT>
 __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, NJU = Dm::NJU;
-  constexpr int TC = Dm::TC, NG = Dm::NG, NPA = Dm::NPA;
-  constexpr bool kSplit = !std::is_same<JT, AT>::value;
+  using R = LinRec<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, NJU = Dm::NJU, RS = R::RS;
   GPO_BIND(ch, kl)
   if (!d.sc->active || (!force && !d.sc->need_lin)) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int next_slot;
   const int CH = d.ch_max;
-  JT* Js = reinterpret_cast<JT*>(smem);               // [NJU][CH]
-  AT* rs = reinterpret_cast<AT*>(Js + NJU * CH);      // [M][CH]
-  AT* bce = rs + M * CH;                              // [DC][CH]  (kSplit only)
-  AT* bpe = bce + DC * CH;                            // [3][CH]   (kSplit only)
-  uint16_t* srt = reinterpret_cast<uint16_t*>(kSplit ? bpe + 3 * CH : bce);   // [CH]
+  AT* rec = reinterpret_cast<AT*>(smem);                      // [CH][RS]
+  uint16_t* srt = reinterpret_cast<uint16_t*>(rec + (size_t)RS * CH);   // [CH]
   const ChunkRange cr = chunk_range(d, kl);
   JT* Jg = reinterpret_cast<JT*>(d.J) + (size_t)cr.e0 * NJ;
+  if (threadIdx.x == 0) next_slot = 0;
 
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
     const int e = cr.e0 + i;
@@ -241,26 +312,38 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
 #pragma unroll
     for (int k = NJU; k < NJ; ++k) row[k] = cvj((AT)0, (const JT*)nullptr);
     store_row<NJ>(Jg + (size_t)i * NJ, row);
-#pragma unroll
-    for (int k = 0; k < NJU; ++k) Js[k * CH + i] = row[k];
     srt[i] = d.ch_sorted[e];
+    AT* re = rec + (size_t)i * RS;
 #pragma unroll
-    for (int a = 0; a < M; ++a) rs[a * CH + i] = rw[a];
-    if constexpr (kSplit) {
+    for (int k = 0; k < DC; ++k) {
 #pragma unroll
-      for (int k = 0; k < DC; ++k) {
-        AT s = Jc[0][k] * rw[0];
+      for (int a = 0; a < M; ++a) re[k * M + a] = ldj(&row[a * DC + k]);
+      AT s = Jc[0][k] * rw[0];
 #pragma unroll
-        for (int a = 1; a < M; ++a) s += Jc[a][k] * rw[a];
-        bce[k * CH + i] = s;
-      }
+      for (int a = 1; a < M; ++a) s += Jc[a][k] * rw[a];
+      re[R::G + k] = s;
+    }
+    AT Jq[M][3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        AT s = Jp[0][k] * rw[0];
+    for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int a = 1; a < M; ++a) s += Jp[a][k] * rw[a];
-        bpe[k * CH + i] = s;
-      }
+      for (int k = 0; k < 3; ++k) Jq[a][k] = ldj(&row[JP0 + 3 * a + k]);
+    AT hs[6];
+    hs[0] = Jq[0][0] * Jq[0][0]; hs[1] = Jq[0][0] * Jq[0][1]; hs[2] = Jq[0][0] * Jq[0][2];
+    hs[3] = Jq[0][1] * Jq[0][1]; hs[4] = Jq[0][1] * Jq[0][2]; hs[5] = Jq[0][2] * Jq[0][2];
+#pragma unroll
+    for (int a = 1; a < M; ++a) {
+      hs[0] += Jq[a][0] * Jq[a][0]; hs[1] += Jq[a][0] * Jq[a][1]; hs[2] += Jq[a][0] * Jq[a][2];
+      hs[3] += Jq[a][1] * Jq[a][1]; hs[4] += Jq[a][1] * Jq[a][2]; hs[5] += Jq[a][2] * Jq[a][2];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) re[R::H + k] = hs[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      AT s = Jp[0][k] * rw[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) s += Jp[a][k] * rw[a];
+      re[R::B + k] = s;
     }
     if (d.dbg_r) {
 #pragma unroll
@@ -269,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
   }
   __syncthreads();
 
-  // point blocks
+  // point blocks: the point's edges are contiguous in the chunk
   AT* Hpp = reinterpret_cast<AT*>(d.Hpp);
   AT* bp = reinterpret_cast<AT*>(d.bp);
   for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
@@ -277,33 +360,11 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     const int a0 = d.pt_off[pj] - cr.e0, b0 = d.pt_off[pj + 1] - cr.e0;
     AT h[6] = {0, 0, 0, 0, 0, 0}, bb[3] = {0, 0, 0};
     for (int i = a0; i < b0; ++i) {
-      AT Jq[M][3];
+      const AT* re = rec + (size_t)i * RS;
 #pragma unroll
-      for (int a = 0; a < M; ++a)
+      for (int k = 0; k < 6; ++k) h[k] += re[R::H + k];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Jq[a][k] = ldj(Js + (JP0 + 3 * a + k) * CH + i);
-      AT hs[6];
-      hs[0] = Jq[0][0] * Jq[0][0]; hs[1] = Jq[0][0] * Jq[0][1]; hs[2] = Jq[0][0] * Jq[0][2];
-      hs[3] = Jq[0][1] * Jq[0][1]; hs[4] = Jq[0][1] * Jq[0][2]; hs[5] = Jq[0][2] * Jq[0][2];
-#pragma unroll
-      for (int a = 1; a < M; ++a) {
-        hs[0] += Jq[a][0] * Jq[a][0]; hs[1] += Jq[a][0] * Jq[a][1]; hs[2] += Jq[a][0] * Jq[a][2];
-        hs[3] += Jq[a][1] * Jq[a][1]; hs[4] += Jq[a][1] * Jq[a][2]; hs[5] += Jq[a][2] * Jq[a][2];
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) h[k] += hs[k];
-      if constexpr (kSplit) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) bb[k] += bpe[k * CH + i];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          AT s = Jq[0][k] * rs[i];
-#pragma unroll
-          for (int a = 1; a < M; ++a) s += Jq[a][k] * rs[a * CH + i];
-          bb[k] += s;
-        }
-      }
+      for (int k = 0; k < 3; ++k) bb[k] += re[R::B + k];
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) Hpp[6 * (size_t)pj + k] = h[k];
@@ -311,69 +372,65 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     for (int k = 0; k < 3; ++k) bp[3 * (size_t)pj + k] = bb[k];
   }
 
-  // camera slots: NG groups of nine outputs (H_cc entries, then b_c)
-  AT* partA = reinterpret_cast<AT*>(d.partA);
-  for (int w = threadIdx.x; w < cr.nS * NG; w += kThreads) {
-    const int sl = w / NG, grp = w - sl * NG;
-    const int qa = d.slot_e0[cr.s0 + sl], qb = d.slot_e0[cr.s0 + sl + 1];
-    const int t0 = 9 * grp;
-    AT acc[9];
-#pragma unroll
-    for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
-    int ti[9], tj[9];
-#pragma unroll
-    for (int o = 0; o < 9; ++o) {
-      const int t = t0 + o;
-      ti[o] = t < TC ? tri_row<DC>(t) : 0;
-      tj[o] = t < TC ? tri_col<DC>(t) : 0;
-    }
-    for (int q = qa; q < qb; ++q) {
-      const int i = srt[q - cr.e0];
-#pragma unroll
-      for (int o = 0; o < 9; ++o) {
-        const int t = t0 + o;
-        if (t < TC) {
-          AT s = ldj(Js + ti[o] * CH + i) * ldj(Js + tj[o] * CH + i);
-#pragma unroll
-          for (int a = 1; a < M; ++a) s += ldj(Js + (a * DC + ti[o]) * CH + i) * ldj(Js + (a * DC + tj[o]) * CH + i);
-          acc[o] += s;
-        } else if (t < TC + DC) {
-          const int k = t - TC;
-          if constexpr (kSplit) {
-            acc[o] += bce[k * CH + i];
-          } else {
-            AT s = ldj(Js + k * CH + i) * rs[i];
-#pragma unroll
-            for (int a = 1; a < M; ++a) s += ldj(Js + (a * DC + k) * CH + i) * rs[a * CH + i];
-            acc[o] += s;
-          }
-        }
-      }
-    }
-    AT* out = partA + (size_t)d.slot_pos[cr.s0 + sl] * NPA + t0;
-#pragma unroll
-    for (int o = 0; o < 9; ++o) out[o] = acc[o];
-  }
+  // camera slots
+  slot_rows<Mo, AT, RS>(d, cr, rec, srt, reinterpret_cast<AT*>(d.partA), &next_slot);
 }
 
 // ---------------------------------------------------------------- Schur preparation
 
-// One CTA per chunk: damped point inverses H_pp^-1 and per-slot partials of
-// sum_e W_e H_pp^-1 W_e^T (= Jc^T (Jp Hinv Jp^T) Jc) and sum_e W_e H_pp^-1 b_p.
+// Upper Cholesky-style factor of an M x M positive semi-definite block: A = L L^T with L
+// lower triangular (a non-positive pivot, possible only through rounding of a singular
+// block, gives a zero column).
+template <int M, class AT>
+__device__ __forceinline__ void psd_cholesky(const AT (&A)[M][M], AT (&L)[M][M]) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) L[i][j] = (AT)0;
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    AT dj = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) dj -= L[j][k] * L[j][k];
+    const AT ljj = dj > (AT)0 ? sqrt(dj) : (AT)0;
+    const AT inv = ljj > (AT)0 ? (AT)1 / ljj : (AT)0;
+    L[j][j] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < M; ++i) {
+      AT v = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = v * inv;
+    }
+  }
+}
+
+// Record layout of the Schur preparation: Y = K = L^T Jc, where L L^T = Jp H_pp^-1 Jp^T,
+// so that sum_e K^T K = sum_e W_e H_pp^-1 W_e^T; g = Jc^T Jp H_pp^-1 b_p.
+template <class Mo>
+struct SchurRec {
+  static constexpr int G = Mo::M * Mo::DC;
+  static constexpr int RS = OddStride<G + Mo::DC>::value;
+};
+
+// One CTA per chunk: damped point inverses H_pp^-1 (and the point records of the Schur
+// product), then per-slot partials of sum_e W_e H_pp^-1 W_e^T and sum_e W_e H_pp^-1 b_p
+// (W_e = Jc^T Jp, from the stored Jacobian rows).
 template <class Mo, class JT>
 __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0;
-  constexpr int TC = Dm::TC, NG = Dm::NG, NPA = Dm::NPA, TM = Dm::TM;
+  using R = SchurRec<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, RS = R::RS;
   GPO_BIND(ch, kl)
   if (!d.sc->active) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int next_slot;
   const int CH = d.ch_max;
-  JT* Jcs = reinterpret_cast<JT*>(smem);              // [M DC][CH]
-  AT* Ae = reinterpret_cast<AT*>(Jcs + JP0 * CH);     // [TM][CH]  Jp H_pp^-1 Jp^T (packed)
-  AT* qe = Ae + TM * CH;                              // [M][CH]   Jp H_pp^-1 b_p
-  uint16_t* srt = reinterpret_cast<uint16_t*>(qe + M * CH);   // [CH]
+  AT* rec = reinterpret_cast<AT*>(smem);                   // [CH][RS]
+  AT* pv = rec + (size_t)RS * CH;                          // [CH][9]: H_pp^-1 (6), H_pp^-1 b_p (3)
+  uint16_t* srt = reinterpret_cast<uint16_t*>(pv + 9 * (size_t)CH);   // [CH]
   const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
   const Scalars* sc = d.sc;
@@ -382,6 +439,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
   const AT* bp = reinterpret_cast<const AT*>(d.bp);
   AT* Hinv = reinterpret_cast<AT*>(d.Hinv);
   constexpr size_t PRB = (6 * sizeof(AT) + 8 + 15) & ~(size_t)15;
+  if (threadIdx.x == 0) next_slot = 0;
 
   for (int j = threadIdx.x; j < cr.nP; j += kThreads) {
     const int pj = cr.p0 + j;
@@ -393,98 +451,63 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
     h[5] += lam * damp_diag(h[5], sc);
     AT o[6];
     inv3(h, o);
-    unsigned char* rec = static_cast<unsigned char*>(d.pt_rec) + (size_t)pj * PRB;
+    unsigned char* prec = static_cast<unsigned char*>(d.pt_rec) + (size_t)pj * PRB;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       Hinv[6 * (size_t)pj + k] = o[k];
-      reinterpret_cast<AT*>(rec)[k] = o[k];
+      reinterpret_cast<AT*>(prec)[k] = o[k];
+      pv[9 * j + k] = o[k];
     }
-    int* se = reinterpret_cast<int*>(rec + 6 * sizeof(AT));
+    int* se = reinterpret_cast<int*>(prec + 6 * sizeof(AT));
     se[0] = d.pt_off[pj] - cr.e0;
     se[1] = d.pt_off[pj + 1] - cr.e0;
+    AT bb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bb[k] = bp[3 * (size_t)pj + k];
+    mul3(o, bb, pv + 9 * j + 6);
   }
   __syncthreads();
 
+  const bool packed = ls.ch_max <= 1024;
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
-    const int pj = __ldg(d.e_pt + cr.e0 + i);
-    AT hi[6], bb[3], hb[3];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) bb[k] = bp[3 * (size_t)pj + k];
-    mul3(hi, bb, hb);
+    const int pl = packed ? (int)(__ldg(d.e_meta + cr.e0 + i) >> 20) : __ldg(d.e_pt + cr.e0 + i) - cr.p0;
+    const AT* hi = pv + 9 * pl;
+    const AT* hb = hi + 6;
     AT row[NJ];
     load_row<NJ>(Jg + (size_t)i * NJ, row);
-#pragma unroll
-    for (int k = 0; k < JP0; ++k) Jcs[k * CH + i] = cvj(row[k], (const JT*)nullptr);
     srt[i] = d.ch_sorted[cr.e0 + i];
     AT t[M][3];
 #pragma unroll
     for (int a = 0; a < M; ++a) mul3(hi, row + JP0 + 3 * a, t[a]);
+    AT A[M][M], qe[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       const AT* Ja = row + JP0 + 3 * a;
 #pragma unroll
-      for (int b = a; b < M; ++b) Ae[tri_idx(M, a, b) * CH + i] = Ja[0] * t[b][0] + Ja[1] * t[b][1] + Ja[2] * t[b][2];
-      qe[a * CH + i] = Ja[0] * hb[0] + Ja[1] * hb[1] + Ja[2] * hb[2];
+      for (int b = a; b < M; ++b) A[a][b] = A[b][a] = Ja[0] * t[b][0] + Ja[1] * t[b][1] + Ja[2] * t[b][2];
+      qe[a] = Ja[0] * hb[0] + Ja[1] * hb[1] + Ja[2] * hb[2];
+    }
+    AT L[M][M];
+    psd_cholesky<M>(A, L);
+    AT* re = rec + (size_t)i * RS;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+#pragma unroll
+      for (int a = 0; a < M; ++a) {           // K[a][k] = sum_{b >= a} L[b][a] Jc[b][k]
+        AT v = L[a][a] * row[a * DC + k];
+#pragma unroll
+        for (int b = a + 1; b < M; ++b) v += L[b][a] * row[b * DC + k];
+        re[k * M + a] = v;
+      }
+      AT s = row[k] * qe[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) s += row[a * DC + k] * qe[a];
+      re[R::G + k] = s;
     }
   }
   __syncthreads();
 
-  AT* partB = reinterpret_cast<AT*>(d.partB);
-  for (int w = threadIdx.x; w < cr.nS * NG; w += kThreads) {
-    const int sl = w / NG, grp = w - sl * NG;
-    const int qa = d.slot_e0[cr.s0 + sl], qb = d.slot_e0[cr.s0 + sl + 1];
-    const int t0 = 9 * grp;
-    AT acc[9];
-#pragma unroll
-    for (int o = 0; o < 9; ++o) acc[o] = (AT)0;
-    int ti[9], tj[9];
-#pragma unroll
-    for (int o = 0; o < 9; ++o) {
-      const int t = t0 + o;
-      ti[o] = t < TC ? tri_row<DC>(t) : 0;
-      tj[o] = t < TC ? tri_col<DC>(t) : 0;
-    }
-    for (int q = qa; q < qb; ++q) {
-      const int i = srt[q - cr.e0];
-      AT A[M][M];
-#pragma unroll
-      for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int b = a; b < M; ++b) A[a][b] = A[b][a] = Ae[tri_idx(M, a, b) * CH + i];
-#pragma unroll
-      for (int o = 0; o < 9; ++o) {
-        const int t = t0 + o;
-        if (t < TC) {
-          AT ci[M], cj[M];
-#pragma unroll
-          for (int a = 0; a < M; ++a) {
-            ci[a] = ldj(Jcs + (a * DC + ti[o]) * CH + i);
-            cj[a] = ldj(Jcs + (a * DC + tj[o]) * CH + i);
-          }
-          AT s = (AT)0;
-#pragma unroll
-          for (int a = 0; a < M; ++a) {
-            AT u = A[a][0] * cj[0];
-#pragma unroll
-            for (int b = 1; b < M; ++b) u += A[a][b] * cj[b];
-            s += ci[a] * u;
-          }
-          acc[o] += s;
-        } else if (t < TC + DC) {
-          const int k = t - TC;
-          AT s = ldj(Jcs + k * CH + i) * qe[i];
-#pragma unroll
-          for (int a = 1; a < M; ++a) s += ldj(Jcs + (a * DC + k) * CH + i) * qe[a * CH + i];
-          acc[o] += s;
-        }
-      }
-    }
-    AT* out = partB + (size_t)d.slot_pos[cr.s0 + sl] * NPA + t0;
-#pragma unroll
-    for (int o = 0; o < 9; ++o) out[o] = acc[o];
-  }
+  slot_rows<Mo, AT, RS>(d, cr, rec, srt, reinterpret_cast<AT*>(d.partB), &next_slot);
 }
 
 // ---------------------------------------------------------------- camera blocks + PCG start
@@ -1145,13 +1168,8 @@ struct Launch {
   using Dm = Dims<Mo>;
   static size_t sJ(Prec pr) { return pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2); }
   static size_t sA(Prec pr) { return pr == Prec::F64 ? 8 : 4; }
-  static size_t lin_smem(Prec pr, int ch) {
-    const size_t per = Dm::NJU * sJ(pr) + Mo::M * sA(pr) + (pr == Prec::BF16 ? (Mo::DC + 3) * sA(pr) : 0) + 2;
-    return per * (size_t)ch;
-  }
-  static size_t schur_smem(Prec pr, int ch) {
-    return (Dm::JP0 * sJ(pr) + (Dm::TM + Mo::M) * sA(pr) + 2) * (size_t)ch;
-  }
+  static size_t lin_smem(Prec pr, int ch) { return (LinRec<Mo>::RS * sA(pr) + 2) * (size_t)ch; }
+  static size_t schur_smem(Prec pr, int ch) { return ((SchurRec<Mo>::RS + 9) * sA(pr) + 2) * (size_t)ch; }
   static size_t spmv_smem(Prec pr, const LaunchSet& ls) {
     return sA(pr) * ((Dm::VW + 3) * (size_t)(ls.ch_max + 1) + Mo::DC * (size_t)ls.ns_max + 6 * (size_t)ls.np_max) +
            4 * (size_t)(ls.np_max + 2 * ls.ns_max + 2);
