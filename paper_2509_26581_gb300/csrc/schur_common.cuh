@@ -264,12 +264,15 @@ __device__ __forceinline__ void bind_problem(DevBA& dst, const DevBA* src) {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-#define GPO_BIND(KIND, LOCAL)                              \
-  __shared__ DevBA d;                                      \
-  pdl_trigger();                                           \
-  const int prob_ = ls.KIND##_prob[blockIdx.x];            \
-  const int LOCAL = blockIdx.x - ls.KIND##_base[prob_];    \
-  bind_problem(d, ls.probs + prob_);                       \
+// A launch over one problem needs no schedule lookup (CTA b is local block b), which
+// takes two dependent global loads off the start of every CTA.
+#define GPO_BIND(KIND, LOCAL)                                                    \
+  __shared__ DevBA d;                                                            \
+  pdl_trigger();                                                                 \
+  const int prob_ = ls.nprob == 1 ? 0 : ls.KIND##_prob[blockIdx.x];              \
+  const int LOCAL = ls.nprob == 1 ? (int)blockIdx.x                              \
+                                  : (int)blockIdx.x - ls.KIND##_base[prob_];     \
+  bind_problem(d, ls.probs + prob_);                                             \
   pdl_wait();
 
 __device__ __forceinline__ void load_rb(const double* __restrict__ src, double* rb) {

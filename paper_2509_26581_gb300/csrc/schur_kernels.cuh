@@ -704,16 +704,18 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   __shared__ DevBA d;
   pdl_trigger();
   const int cb = blockIdx.x / kApplySplit, part = blockIdx.x % kApplySplit;
-  const int prob_ = ls.cb_prob[cb];
-  const int cbl = cb - ls.cb_base[prob_];
+  const int prob_ = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
+  const int cbl = ls.nprob == 1 ? cb : cb - ls.cb_base[prob_];
   bind_problem(d, ls.probs + prob_);
   pdl_wait();
   Scalars* sc = d.sc;
-  if (!sc->active || sc->pcg_done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cams_per_cta = kCamPerBlock / kApplySplit;             // 2
   const int c = cbl * kCamPerBlock + part * cams_per_cta + warp / kApplySplit;
   const int q = warp % kApplySplit;                                // quarter of the slots
+  // the camera's slot range is loaded with the solve's flags (one round trip)
+  const int sa = c < d.C ? d.cam_s_off[c] : 0, sb = c < d.C ? d.cam_s_off[c + 1] : 0;
+  if (!sc->active || sc->pcg_done) return;
   const AT* pold_all = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
   const AT* z_all = reinterpret_cast<const AT*>(d.z);
   const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
@@ -721,7 +723,6 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   AT pi = (AT)0;
   if (c < d.C) {   // warp-uniform
     const AT* partV = reinterpret_cast<const AT*>(d.partV);
-    const int sa = d.cam_s_off[c], sb = d.cam_s_off[c + 1];
     AT acc[DC];
 #pragma unroll
     for (int k = 0; k < DC; ++k) acc[k] = (AT)0;
@@ -829,9 +830,22 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
   __shared__ double red[kCamPerBlock][2];
   GPO_BIND(cb, cbl)
   Scalars* sc = d.sc;
-  if (!sc->active || sc->pcg_done) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = cbl * kCamPerBlock + warp;
+  // the camera's inputs that do not depend on the solve's scalars are loaded together
+  // with them (one round trip before the arithmetic instead of two)
+  const bool mine = c < d.C && lane < DB;
+  AT r0 = (AT)0, y0 = (AT)0, mrow[DB];
+#pragma unroll
+  for (int j = 0; j < DB; ++j) mrow[j] = (AT)0;
+  if (mine) {
+    const AT* Mi = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * TB;
+    r0 = reinterpret_cast<const AT*>(d.r)[DB * (size_t)c + lane];
+    y0 = reinterpret_cast<const AT*>(d.y)[DB * (size_t)c + lane];
+#pragma unroll
+    for (int j = 0; j < DB; ++j) mrow[j] = Mi[sym_idx(DB, lane, j)];
+  }
+  if (!sc->active || sc->pcg_done) return;
   AT rz_c = (AT)0, rr_c = (AT)0;   // per-warp partials in AT, accumulated across warps in FP64
   if (c < d.C) {   // warp-uniform
     const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
@@ -839,19 +853,17 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
     AT* r = reinterpret_cast<AT*>(d.r) + DB * (size_t)c;
     AT* z = reinterpret_cast<AT*>(d.z) + DB * (size_t)c;
     const AT* pv = reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
-    const AT* yv = reinterpret_cast<const AT*>(d.y) + DB * (size_t)c;
-    const AT* Mi = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * TB;
     AT ri = (AT)0;
     if (lane < DB) {
       x[lane] += sa * pv[lane];
-      ri = r[lane] * sn - alpha * yv[lane];
+      ri = r0 * sn - alpha * y0;
       r[lane] = ri;
     }
     AT zi = (AT)0;
 #pragma unroll
     for (int j = 0; j < DB; ++j) {
       const AT rj = __shfl_sync(0xffffffffu, ri, j);
-      if (lane < DB) zi += Mi[sym_idx(DB, lane, j)] * rj;
+      if (lane < DB) zi += mrow[j] * rj;
     }
     if (lane < DB) {
       z[lane] = zi;

@@ -26,7 +26,13 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   using Dm = Dims<Mo>;
   constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
   GPO_BIND(ch, kl)
-  if (!d.sc->active || d.sc->pcg_done) return;
+  // the chunk's ranges and the solve's scalars are loaded together, ahead of the
+  // early exit, so that the index loads below start one round trip sooner
+  const Scalars* sc = d.sc;
+  const ChunkRange cr = chunk_range(d, kl);
+  const int act = sc->active, done = sc->pcg_done, pidx = sc->pidx;
+  const double beta_d = sc->beta, inv_n_d = sc->inv_n;
+  if (!act || done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max, LD = CH + 1;
   AT* vv = reinterpret_cast<AT*>(smem);        // [VW][LD]; rows 0..2 hold a_e in pass 1
@@ -36,7 +42,6 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   int* po = reinterpret_cast<int*>(hv + 6 * ls.np_max);   // [np + 1] local point offsets
   int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
   int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
-  const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
 
   // per-edge positions: one packed word per edge when chunks fit 10-bit positions
@@ -61,8 +66,8 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   // one thread per slot: its record (edge range, camera, partial row) and the search
   // direction p_k = (z_k + beta_k p_{k-1}) / n_k of its camera
   const AT* zv = reinterpret_cast<const AT*>(d.z);
-  const AT* pold = reinterpret_cast<const AT*>(d.sc->pidx ? d.p2 : d.p);
-  const AT beta = (AT)d.sc->beta, inv_n = (AT)d.sc->inv_n;
+  const AT* pold = reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
+  const AT beta = (AT)beta_d, inv_n = (AT)inv_n_d;
   for (int t = threadIdx.x; t < cr.nS; t += kThreads) {
     const int4 r4 = __ldg(d.slot_rec + cr.s0 + t);
     so[t] = r4.x;
