@@ -327,7 +327,7 @@ static gpo_status prepare(gpo_graph* g) {
     ns_max = std::max(ns_max, R.ch_s0[k + 1] - R.ch_s0[k]);
     np_max = std::max(np_max, R.ch_p0[k + 1] - R.ch_p0[k]);
   }
-  R.jpos = (size_t)E * NJ;
+  R.jpos = (size_t)std::max<int64_t>((E + gpo::kJTile - 1) / gpo::kJTile, 1) * gpo::kJTile * NJ;   // whole tiles
   // per camera: its slots in chunk order
   R.cam_s_off.assign(C + 1, 0);
   R.cam_s_list.resize(NS);
@@ -1415,11 +1415,16 @@ static gpo_status debug_linearize_rows(gpo_graph* g, const int64_t* sel, int64_t
       if (r_out)
         for (int a = 0; a < M; ++a) r_out[(size_t)R * id + a] = rv[(size_t)M * (e0 + i) + a];
       if (J_out) {
-        const size_t b = (size_t)(e0 + i) * NJ;
+        // element k of row e in the tiled layout (see kJTile)
+        const size_t e = (size_t)(e0 + i), sj = jt_size(g->prec), Q = (size_t)NJ * sj / 16;
+        auto at = [&](size_t k) {
+          const size_t unit = ((e / gpo::kJTile) * Q + k * sj / 16) * gpo::kJTile + e % gpo::kJTile;
+          return (unit * 16 + (k * sj) % 16) / sj;
+        };
         for (int a = 0; a < M; ++a) {
           double* row = J_out + ((size_t)R * id + a) * K;
-          for (int j = 0; j < DC; ++j) row[j] = read_j(jraw, b + (size_t)DC * a + j, g->prec);
-          for (int j = 0; j < 3; ++j) row[DB + j] = read_j(jraw, b + (size_t)M * DC + 3 * a + j, g->prec);
+          for (int j = 0; j < DC; ++j) row[j] = read_j(jraw, at((size_t)DC * a + j), g->prec);
+          for (int j = 0; j < 3; ++j) row[DB + j] = read_j(jraw, at((size_t)M * DC + 3 * a + j), g->prec);
         }
       }
     }

@@ -204,4 +204,9 @@ const KernelSet& kernels_stereo();   // vi_kernels.cu
 inline const KernelSet& kernels_for(ModelKind m) { return m == ModelKind::STEREO ? kernels_stereo() : kernels_ba(); }
 inline int default_ch_max(Prec) { return 512; }
 
+// Jacobian rows are stored in tiles of kJTile consecutive edges, each row cut into
+// 16-byte pieces and piece q of a tile's rows stored contiguously: piece q of row e is
+// 16-byte unit ((e / kJTile) * Q + q) * kJTile + e % kJTile, Q = row bytes / 16.
+constexpr int kJTile = 32;
+
 }  // namespace gpo

@@ -63,6 +63,38 @@ __device__ __forceinline__ void load_row(const double* src, AT (&v)[NJ]) {
     v[2 * i] = (AT)w.x; v[2 * i + 1] = (AT)w.y;
   }
 }
+// Jacobian rows live in tiles of 32 consecutive edges.  Inside a tile the rows are cut
+// into Q 16-byte pieces and piece q of the tile's rows is one contiguous 512-byte
+// block ([tile][q][e mod 32]): a warp that reads the rows of 32 consecutive edges
+// reads Q whole blocks, one per 16-byte vector access, instead of Q scattered 16-byte
+// pieces per 48-byte row.  J is allocated in whole tiles.
+template <class JT, int NJ>
+struct JTiles {
+  static constexpr int Q = NJ * (int)sizeof(JT) / 16;   // pieces per row
+  static_assert(NJ * sizeof(JT) % 16 == 0, "rows are whole 16-byte pieces");
+  // index (in 16-byte units) of piece q of row e
+  __host__ __device__ static __forceinline__ size_t piece(size_t e, int q) {
+    return ((e >> 5) * Q + q) * kJTile + (e & 31);
+  }
+};
+template <int NJ, class JT, class AT>
+__device__ __forceinline__ void load_row_t(const JT* J, size_t e, AT (&v)[NJ]) {
+  using T = JTiles<JT, NJ>;
+  const uint4* J4 = reinterpret_cast<const uint4*>(J);
+  uint4 w[T::Q];
+#pragma unroll
+  for (int q = 0; q < T::Q; ++q) w[q] = J4[T::piece(e, q)];
+  load_row<NJ>(reinterpret_cast<const JT*>(w), v);
+}
+template <int NJ, class JT>
+__device__ __forceinline__ void store_row_t(JT* J, size_t e, const JT (&v)[NJ]) {
+  using T = JTiles<JT, NJ>;
+  uint4* J4 = reinterpret_cast<uint4*>(J);
+  const uint4* s4 = reinterpret_cast<const uint4*>(v);
+#pragma unroll
+  for (int q = 0; q < T::Q; ++q) J4[T::piece(e, q)] = s4[q];
+}
+
 template <int NJ>
 __device__ __forceinline__ void store_row(__nv_bfloat16* dst, const __nv_bfloat16 (&v)[NJ]) {
   uint4* d4 = reinterpret_cast<uint4*>(dst);

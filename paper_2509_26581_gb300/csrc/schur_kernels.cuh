@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
   AT* rec = reinterpret_cast<AT*>(smem);                      // [CH][RS]
   uint16_t* srt = reinterpret_cast<uint16_t*>(rec + (size_t)RS * CH);   // [CH]
   const ChunkRange cr = chunk_range(d, kl);
-  JT* Jg = reinterpret_cast<JT*>(d.J) + (size_t)cr.e0 * NJ;
+  JT* Jg = reinterpret_cast<JT*>(d.J);
   if (threadIdx.x == 0) next_slot = 0;
 
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     }
 #pragma unroll
     for (int k = NJU; k < NJ; ++k) row[k] = cvj((AT)0, (const JT*)nullptr);
-    store_row<NJ>(Jg + (size_t)i * NJ, row);
+    store_row_t<NJ>(Jg, (size_t)e, row);
     srt[i] = d.ch_sorted[e];
     AT* re = rec + (size_t)i * RS;
 #pragma unroll
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
   AT* pv = rec + (size_t)RS * CH;                          // [CH][9]: H_pp^-1 (6), H_pp^-1 b_p (3)
   uint16_t* srt = reinterpret_cast<uint16_t*>(pv + 9 * (size_t)CH);   // [CH]
   const ChunkRange cr = chunk_range(d, kl);
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
+  const JT* Jg = reinterpret_cast<const JT*>(d.J);
   const Scalars* sc = d.sc;
   const AT lam = (AT)sc->lambda;
   const AT* Hpp = reinterpret_cast<const AT*>(d.Hpp);
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
     const AT* hi = pv + 9 * pl;
     const AT* hb = hi + 6;
     AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     srt[i] = d.ch_sorted[cr.e0 + i];
     AT t[M][3];
 #pragma unroll
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
   AT* qv = reinterpret_cast<AT*>(smem);   // [M][CH]
   AT* av = qv + M * CH;                   // [3][CH]
   const ChunkRange cr = chunk_range(d, kl);
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
+  const JT* Jg = reinterpret_cast<const JT*>(d.J);
   const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x);
   const AT* Hinv = reinterpret_cast<const AT*>(d.Hinv);
   const AT* bp = reinterpret_cast<const AT*>(d.bp);
@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
     const int c = __ldg(d.e_cam + cr.e0 + i);
     AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     AT q[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) q[a] = (AT)0;
@@ -999,7 +999,7 @@ __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
     const int pj = __ldg(d.e_pt + cr.e0 + i);
     const AT t0 = dp[3 * (size_t)pj], t1 = dp[3 * (size_t)pj + 1], t2 = dp[3 * (size_t)pj + 2];
     AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     double sq = 0.0;
 #pragma unroll
     for (int a = 0; a < M; ++a) {

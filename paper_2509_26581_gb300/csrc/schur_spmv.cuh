@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   int* po = reinterpret_cast<int*>(hv + 6 * ls.np_max);   // [np + 1] local point offsets
   int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
   int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
-  const JT* Jg = reinterpret_cast<const JT*>(d.J) + (size_t)cr.e0 * NJ;
+  const JT* Jg = reinterpret_cast<const JT*>(d.J);
 
   // per-edge positions: one packed word per edge when chunks fit 10-bit positions
   int pos[EPT], slot[EPT], ptl[EPT];
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
     AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     const AT* xc = xs + DC * slot[m];
     AT q[M];
 #pragma unroll
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
     AT row[NJ];
-    load_row<NJ>(Jg + (size_t)i * NJ, row);
+    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     const int pl = ptl[m];
     const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
     AT s[M];
@@ -220,8 +220,8 @@ __host__ __device__ inline StageLayout stage_layout(size_t sJ, size_t sA, int ch
   auto al = [](uint32_t v) { return (v + 15u) & ~15u; };
   StageLayout L;
   const uint32_t prb = (uint32_t)((6 * sA + 8 + 15) & ~(size_t)15);
-  L.j = 0;
-  L.meta = al((uint32_t)(ch_max * Mo::NJ * sJ));
+  L.j = 0;   // whole 32-edge tiles covering the chunk (a chunk may start inside a tile)
+  L.meta = al((uint32_t)((ch_max / kJTile + 2) * kJTile * Mo::NJ * sJ));
   L.pt = L.meta + al((uint32_t)(ch_max * 4 + 16));
   L.slot = L.pt + al((uint32_t)(np_max * prb));
   L.xs = L.slot + al((uint32_t)(ns_max * 16));
@@ -231,6 +231,7 @@ __host__ __device__ inline StageLayout stage_layout(size_t sJ, size_t sA, int ch
 
 struct StageInfo {
   int k, q, nE, nP, nS, skew;   // chunk (-1: no more chunks), problem, sizes, meta skew
+  int jskew;                    // position of the chunk's first row in its first tile
 };
 
 // Warp-specialised persistent Schur product.  One producer warp walks the chunks
@@ -326,17 +327,17 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
       const int s0 = P->ch_s0[kl], s1 = P->ch_s0[kl + 1];
       unsigned char* base = smem + st * SL.size;
       if (lane == 0) {
-        const uint32_t bJ = (uint32_t)(e1 - e0) * RB;
+        const uint32_t bJ = e1 > e0 ? (uint32_t)(((e1 - 1) >> 5) - (e0 >> 5) + 1) * kJTile * RB : 0u;
         const uintptr_t ms = reinterpret_cast<uintptr_t>(P->e_meta + e0);
         const uintptr_t ma = ms & ~(uintptr_t)15;
         const uint32_t skew = (uint32_t)(ms - ma);
         const uint32_t bM = e1 > e0 ? (skew + 4u * (uint32_t)(e1 - e0) + 15u) & ~15u : 0u;
         const uint32_t bP = (uint32_t)(p1 - p0) * PRB;
         const uint32_t bS = (uint32_t)(s1 - s0) * 16u;
-        info[st] = StageInfo{k, q, e1 - e0, p1 - p0, s1 - s0, (int)(skew / 4)};
+        info[st] = StageInfo{k, q, e1 - e0, p1 - p0, s1 - s0, (int)(skew / 4), e0 & (kJTile - 1)};
         fence_proxy_async();
         mbar_expect_tx(fb, bJ + bM + bP + bS);
-        if (bJ) bulk_g2s(smem_u32(base + SL.j), static_cast<const JT*>(P->J) + (size_t)e0 * NJ, bJ, fb);
+        if (bJ) bulk_g2s(smem_u32(base + SL.j), static_cast<const JT*>(P->J) + (size_t)(e0 >> 5) * kJTile * NJ, bJ, fb);
         if (bM) bulk_g2s(smem_u32(base + SL.meta), reinterpret_cast<const void*>(ma), bM, fb);
         if (bP) bulk_g2s(smem_u32(base + SL.pt), static_cast<const unsigned char*>(P->pt_rec) + (size_t)p0 * PRB, bP, fb);
         if (bS) bulk_g2s(smem_u32(base + SL.slot), P->slot_rec + s0, bS, fb);
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
       // ---- pass 1: a_e = Jp^T (Jc x_c)
       for (int i = threadIdx.x; i < in.nE; i += kThreads) {
         AT row[NJ];
-        load_row<NJ>(Js + (size_t)i * NJ, row);
+        load_row_t<NJ>(Js, (size_t)(i + in.jskew), row);
         const AT* xc = xs + DC * (int)((meta[i] >> 10) & 1023u);
         AT qv[M];
 #pragma unroll
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
       // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
       for (int i = threadIdx.x; i < in.nE; i += kThreads) {
         AT row[NJ];
-        load_row<NJ>(Js + (size_t)i * NJ, row);
+        load_row_t<NJ>(Js, (size_t)(i + in.jskew), row);
         const uint32_t m = meta[i];
         const int pl = (int)(m >> 20), pos = (int)(m & 1023u);
         const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
