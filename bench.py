@@ -137,7 +137,7 @@ def load_peaks() -> tuple[float, str]:
 # medium workload (profiles/k_spmv_ba_medium_bf16.md), valid only for the kernel sources it
 # was taken from (keyed by a hash of them): changed kernels report null.
 MEASURED_TRAFFIC = {("bf16", "020655f7e122"): 189.6e6}
-SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2}
+SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
 

@@ -111,12 +111,16 @@ typedef struct {
   size_t memory_budget;       /* bytes; 0 = unlimited.  Exceeding it gives GPO_ERR_OOM. */
   int32_t chunk_edges;        /* edges per CTA chunk of the per-edge kernels (32..2048;
                                  0 = default: 512); raised to the longest track.  A
-                                 tuning knob: results do not depend on it. */
-  int32_t spmv_variant;       /* Schur-product kernel: 0 = automatic (classic), 1 = staged
+                                 tuning knob: the chunking groups the per-camera partial
+                                 sums, so results agree up to rounding. */
+  int32_t spmv_variant;       /* Schur-product kernel: 0 = automatic (pipelined for BF16
+                                 and FP32 storage, classic for FP64), 1 = staged
                                  (persistent CTAs streaming chunks into shared memory
-                                 with bulk copies; chunks of at most 1024 edges, else
-                                 classic), 2 = classic.  A tuning knob: both give
-                                 bit-identical results. */
+                                 with bulk copies), 2 = classic (one CTA per chunk),
+                                 3 = pipelined (persistent CTAs prefetching the next
+                                 chunk's indices while the current one runs).  1 and 3
+                                 need chunks of at most 1024 edges, else classic runs.
+                                 A tuning knob: all give bit-identical results. */
 } gpo_graph_desc;
 
 /* Levenberg-Marquardt and PCG options (Listing 5: LevenbergMarquardtOptions and

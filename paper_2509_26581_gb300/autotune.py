@@ -5,8 +5,9 @@ Two knobs of `gpo_graph_desc` change how the kernels walk a problem, not the met
                     chunking groups the per-camera partial sums, so results agree up to
                     rounding;
   * spmv_variant -- the PCG Schur-product kernel: 2 = classic (one CTA per chunk),
-                    1 = staged (persistent CTAs, warp-specialised bulk-copy pipeline);
-                    both give bit-identical results (see the variant tests).
+                    1 = staged (persistent CTAs, warp-specialised bulk-copy pipeline),
+                    3 = pipelined (persistent CTAs prefetching the next chunk's
+                    indices); all give bit-identical results (see the variant tests).
 The best choice depends on the problem's size (how many chunks fill the GPU, how many
 slots a chunk has) and on the storage precision.  `tune` times every candidate on a
 representative problem of a size class -- a few LM iterations after a warm-up, wall
@@ -28,8 +29,8 @@ TABLE = os.path.join(HERE, "tuning.json")
 
 # (upper bound on observation edges, class name)
 SIZE_CLASSES = [(20_000, "window"), (300_000, "small"), (8_000_000, "medium"), (math.inf, "large")]
-CANDIDATES = [dict(chunk_edges=c, spmv_variant=v) for c in (256, 512, 1024) for v in (2, 1)]
-DEFAULT = dict(chunk_edges=512, spmv_variant=2)
+CANDIDATES = [dict(chunk_edges=c, spmv_variant=v) for c in (256, 512, 1024) for v in (2, 1, 3)]
+DEFAULT = dict(chunk_edges=512, spmv_variant=0)
 
 
 def size_class(n_edges: int) -> str:

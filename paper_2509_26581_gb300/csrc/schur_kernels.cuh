@@ -1280,8 +1280,47 @@ struct Launch {
     const int grid = std::max(1, std::min(ls.n_ch, n_sm * std::max(occ, 1)));
     launch_pdl(k_spmv_ws<Mo, JT>, grid, kWsThreads, sm, st, ls);
   }
+  static size_t pp_smem(Prec pr, const LaunchSet& ls) {
+    return pipe_layout<Mo>(sA(pr), ls.ch_max, ls.np_max, ls.ns_max).size;
+  }
+  // The pipelined kernel reads packed edge words (chunks of at most 1024 edges).  It is
+  // the automatic choice for BF16 and FP32 storage (measured faster there; FP64 keeps
+  // the classic kernel).
+  static bool pp_ok(Prec pr, const LaunchSet& ls) {
+    const bool want = ls.spmv_variant == 3 || (ls.spmv_variant == 0 && pr != Prec::F64);
+    return want && ls.ch_max <= 1024 && pp_smem(pr, ls) <= 220 * 1024;
+  }
+  template <class JT, int EPT>
+  static void pp_e(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = pp_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_spmv_pp<Mo, JT, EPT>), sm);
+    static int n_sm = 0;
+    if (!n_sm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      if (n_sm <= 0) n_sm = 1;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_pp<Mo, JT, EPT>, kThreads, sm);
+    const int grid = std::max(1, std::min(ls.n_ch, n_sm * std::max(occ, 1)));
+    launch_pdl(k_spmv_pp<Mo, JT, EPT>, grid, kThreads, sm, st, ls);
+  }
+  template <class JT>
+  static void pp_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const int ept = (ls.ch_max + kThreads - 1) / kThreads;
+    if (ept <= 1) pp_e<JT, 1>(ls, pr, st);
+    else if (ept <= 2) pp_e<JT, 2>(ls, pr, st);
+    else pp_e<JT, 4>(ls, pr, st);
+  }
   static int pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
+    if (pp_ok(pr, ls)) {
+      if (pr == Prec::F64) pp_t<double>(ls, pr, st);
+      else if (pr == Prec::F32) pp_t<float>(ls, pr, st);
+      else pp_t<__nv_bfloat16>(ls, pr, st);
+      return 1;
+    }
     if (ws_ok(pr, ls)) {
       if (pr == Prec::F64) ws_t<double>(ls, pr, st);
       else if (pr == Prec::F32) ws_t<float>(ls, pr, st);

@@ -447,4 +447,276 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
   }
 }
 
+
+// ---------------------------------------------------------------- Schur product, pipelined persistent form
+
+// Asynchronous global-to-shared copies of 4 and 16 bytes (the per-thread form; a
+// group is committed per chunk and waited for one chunk later).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Index buffers of one chunk in the pipelined kernel's shared memory.
+// Shared memory of the pipelined kernel: the passes' scratch (per-edge terms [VW][LD],
+// point solutions [3][np_max + 1]), the slot cameras' search direction, and two
+// buffers of one chunk's index copies.
+struct PipeLayout {
+  uint32_t tp, xs, buf;          // offsets
+  uint32_t meta, srec, prec;     // offsets inside a buffer
+  uint32_t bsize, size;
+};
+template <class Mo>
+__host__ __device__ inline PipeLayout pipe_layout(size_t sA, int ch_max, int np_max, int ns_max) {
+  auto al = [](uint32_t v) { return (v + 15u) & ~15u; };
+  const uint32_t prb = (uint32_t)((6 * sA + 8 + 15) & ~(size_t)15);
+  const int vw = Mo::DC > 3 ? Mo::DC : 3;
+  PipeLayout L;
+  L.tp = al((uint32_t)(vw * (size_t)(ch_max + 1) * sA));
+  L.xs = L.tp + al((uint32_t)(3 * (size_t)(np_max + 1) * sA));
+  L.buf = L.xs + al((uint32_t)(ns_max * Mo::DC * sA));
+  L.meta = 0;
+  L.srec = al((uint32_t)ch_max * 4u);
+  L.prec = L.srec + al((uint32_t)ns_max * 16u);
+  L.bsize = L.prec + al((uint32_t)np_max * prb);
+  L.size = L.buf + 2 * L.bsize;
+  return L;
+}
+
+struct PipeChunk {
+  int k, q, kl, e0, nE, p0, nP, s0, nS;   // k < 0: no more chunks
+};
+
+// The classic Schur product's passes as a persistent kernel: CTA b walks the chunks
+// b, b + G, ... of the launch set (skipping problems whose PCG has stopped).  While a
+// chunk's passes run, every thread has already issued its share of the next chunk's
+// index copies (packed edge words, slot records, point records) into the other of two
+// shared-memory buffers, the next chunk's Jacobian tiles are being prefetched into L2,
+// and the chunk after that is being located; only the slot cameras' search-direction
+// gather stays on a chunk's critical path.  The sums and their order are those of
+// k_spmv (bit-identical results).  Requires chunks of at most 1024 edges.
+// Resident CTAs per SM the register budget targets: BF16 rows are re-read from L2
+// anyway, so more CTAs win; FP32 rows are twice as long and their second read hits L1
+// only while fewer CTAs share it; FP64 is limited by shared memory.
+template <class JT> struct PipeOcc { static constexpr int value = sizeof(JT) == 2 ? 5 : (sizeof(JT) == 4 ? 4 : 2); };
+template <class Mo, class JT, int EPT>
+__global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(LaunchSet ls) {
+  using AT = typename AccOf<JT>::T;
+  using Dm = Dims<Mo>;
+  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
+  constexpr size_t PRB = (6 * sizeof(AT) + 8 + 15) & ~(size_t)15;
+  constexpr int kWords = (int)(sizeof(DevBA) / 4);
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ DevBA d;
+  __shared__ PipeChunk ck[3];
+  pdl_trigger();
+  const int LD = ls.ch_max + 1, LP = ls.np_max + 1;
+  const PipeLayout PL = pipe_layout<Mo>(sizeof(AT), ls.ch_max, ls.np_max, ls.ns_max);
+  AT* vv = reinterpret_cast<AT*>(smem);                 // [VW][LD]; rows 0..2 hold a_e in pass 1
+  AT* tp = reinterpret_cast<AT*>(smem + PL.tp);         // [3][LP] point solutions
+  AT* xs = reinterpret_cast<AT*>(smem + PL.xs);         // [ns_max][DC] slot cameras' direction
+  unsigned char* bufs = smem + PL.buf;
+  const int G = gridDim.x;
+  int bound_q = -1;              // problem whose descriptor is in d
+  pdl_wait();
+
+  // First chunk at or after k whose problem still iterates (-1: none).  The problems'
+  // scalars do not change during the launch; a one-problem launch checks them once.
+  auto next_live = [&](int k) -> int {
+    if (ls.nprob == 1) return k < ls.n_ch ? k : -1;
+    while (k < ls.n_ch) {
+      const int q = ls.ch_prob[k];
+      const Scalars* sc = ls.probs[q].sc;
+      if (sc->active && !sc->pcg_done) return k;
+      const int nxt = q + 1 < ls.nprob ? ls.ch_base[q + 1] : ls.n_ch;
+      k += ((nxt - k) + G - 1) / G * G;
+    }
+    return -1;
+  };
+  // a chunk's problem and ranges (thread 0)
+  auto plan = [&](int k) -> PipeChunk {
+    PipeChunk c;
+    c.k = k;
+    if (k < 0) return c;
+    const int q = ls.nprob == 1 ? 0 : ls.ch_prob[k];
+    const int kl = ls.nprob == 1 ? k : k - ls.ch_base[q];
+    const DevBA* P = q == bound_q ? &d : ls.probs + q;
+    const int* ce = P->ch_e0;
+    const int* cp = P->ch_p0;
+    const int* cs = P->ch_s0;
+    c.q = q; c.kl = kl;
+    c.e0 = ce[kl]; c.nE = ce[kl + 1] - c.e0;
+    c.p0 = cp[kl]; c.nP = cp[kl + 1] - c.p0;
+    c.s0 = cs[kl]; c.nS = cs[kl + 1] - c.s0;
+    return c;
+  };
+  // every thread's share of a chunk's index copies, and the L2 prefetch of its tiles
+  auto issue = [&](const PipeChunk& c, int b, int bound) {
+    if (c.k < 0) return;
+    const DevBA* P = c.q == bound ? &d : ls.probs + c.q;
+    unsigned char* B = bufs + b * PL.bsize;
+    const uint32_t* meta = P->e_meta + c.e0;
+    for (int i = threadIdx.x; i < c.nE; i += kThreads) cp_async4(B + PL.meta + 4 * i, meta + i);
+    const int4* sr = P->slot_rec + c.s0;
+    for (int t = threadIdx.x; t < c.nS; t += kThreads) cp_async16(B + PL.srec + 16 * t, sr + t);
+    const unsigned char* pr = static_cast<const unsigned char*>(P->pt_rec) + (size_t)c.p0 * PRB;
+    const int pieces = (int)(c.nP * (PRB / 16));
+    for (int u = threadIdx.x; u < pieces; u += kThreads) cp_async16(B + PL.prec + 16 * u, pr + 16 * u);
+    if (threadIdx.x == 0 && c.nE > 0) {
+      const size_t t0 = (size_t)c.e0 >> 5, t1 = (size_t)(c.e0 + c.nE - 1) >> 5;
+      prefetch_l2(static_cast<const JT*>(P->J) + t0 * kJTile * NJ,
+                  (uint32_t)((t1 - t0 + 1) * kJTile * NJ * sizeof(JT)));
+    }
+  };
+
+  // the slot cameras' search direction p = (z + beta p_old) / n of a chunk whose slot
+  // records are in buffer b
+  auto gather = [&](const PipeChunk& c, int b) {
+    if (c.k < 0) return;
+    const DevBA* P = c.q == bound_q ? &d : ls.probs + c.q;
+    const int4* srec = reinterpret_cast<const int4*>(bufs + b * PL.bsize + PL.srec);
+    const Scalars* sc = P->sc;
+    const AT* zv = reinterpret_cast<const AT*>(P->z);
+    const AT* pold = reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
+    const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
+    for (int w = threadIdx.x; w < c.nS * DC; w += kThreads) {
+      const int sl = w / DC, k = w - sl * DC;
+      const size_t o = DB * (size_t)srec[sl].z + k;
+      xs[w] = (zv[o] + beta * pold[o]) * inv_n;
+    }
+  };
+
+  if (ls.nprob == 1) {          // a one-problem launch stops at once if its PCG has
+    const Scalars* sc = ls.probs[0].sc;
+    if (!sc->active || sc->pcg_done) return;
+  }
+  if (threadIdx.x == 0) {
+    const int k0 = next_live(blockIdx.x);
+    ck[0] = plan(k0);
+    ck[1] = plan(k0 < 0 ? -1 : next_live(k0 + G));
+  }
+  __syncthreads();
+  if (ck[0].k < 0) return;
+  issue(ck[0], 0, -1);
+  cp_async_commit();
+  for (int n = 0;; ++n) {
+    const int b = n & 1;
+    const PipeChunk c = ck[n % 3];
+    if (c.k < 0) break;
+    const PipeChunk cn = ck[(n + 1) % 3];
+    if (c.q != bound_q) {        // CTA-uniform: bind the chunk's problem
+      __syncthreads();           // every thread is past the previous use of d
+      for (int i = threadIdx.x; i < kWords; i += kThreads)
+        reinterpret_cast<int*>(&d)[i] = reinterpret_cast<const int*>(ls.probs + c.q)[i];
+      bound_q = c.q;
+      __syncthreads();
+    }
+    issue(cn, b ^ 1, bound_q);
+    cp_async_commit();
+    cp_async_wait_prev();        // this thread's copies into buffer b have landed
+    __syncthreads();             // ... and everyone else's; d is bound
+
+    unsigned char* B = bufs + b * PL.bsize;
+    const uint32_t* meta = reinterpret_cast<const uint32_t*>(B + PL.meta);
+    const int4* srec = reinterpret_cast<const int4*>(B + PL.srec);
+    const unsigned char* prec = B + PL.prec;
+    if (n == 0) gather(c, b);    // later chunks' directions were gathered one chunk ahead
+    int pos[EPT], slot[EPT], ptl[EPT];
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+      const int i = threadIdx.x + m * kThreads;
+      if (i < c.nE) {
+        const uint32_t w = meta[i];
+        pos[m] = (int)(w & 1023u);
+        slot[m] = (int)((w >> 10) & 1023u);
+        ptl[m] = (int)(w >> 20);
+      }
+    }
+    __syncthreads();
+    const JT* Jg = reinterpret_cast<const JT*>(d.J);
+    // ---- pass 1: a_e = Jp^T (Jc x_c)
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+      const int i = threadIdx.x + m * kThreads;
+      if (i >= c.nE) break;
+      AT row[NJ];
+      load_row_t<NJ>(Jg, (size_t)(c.e0 + i), row);
+      const AT* xc = xs + DC * slot[m];
+      AT qv[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) qv[a] = (AT)0;
+#pragma unroll
+      for (int k = 0; k < DC; ++k) {
+        const AT xk = xc[k];
+#pragma unroll
+        for (int a = 0; a < M; ++a) qv[a] += row[a * DC + k] * xk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        AT s2 = row[JP0 + k] * qv[0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) s2 += row[JP0 + 3 * a + k] * qv[a];
+        vv[k * LD + i] = s2;
+      }
+    }
+    __syncthreads();
+    // ---- pass 2: t_p = H_pp^-1 sum_e a_e; meanwhile the last warp's first thread
+    // locates the chunk after next (its loads overlap the pass)
+    if (threadIdx.x == kThreads - 32) ck[(n + 2) % 3] = plan(cn.k < 0 ? -1 : next_live(cn.k + G));
+    cp_async_wait_all();         // the next chunk's copies (visible after the barrier)
+    for (int j = threadIdx.x; j < c.nP; j += kThreads) {
+      const AT* hv = reinterpret_cast<const AT*>(prec + (size_t)j * PRB);
+      const int* se = reinterpret_cast<const int*>(prec + (size_t)j * PRB + 6 * sizeof(AT));
+      AT u[3];
+      point_sum<JT>(vv, LD, se[0], se[1], u);
+      AT t[3];
+      mul3(hv, u, t);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) tp[k * LP + j] = t[k];
+    }
+    __syncthreads();
+    // the next chunk's search direction (its slot records have landed; this chunk's
+    // pass 1 was the last reader of xs), overlapping pass 3
+    gather(cn, b ^ 1);
+    // ---- pass 3: v_e = Jc^T (Jp t_p), scattered to the edge's slot-sorted position
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+      const int i = threadIdx.x + m * kThreads;
+      if (i >= c.nE) break;
+      AT row[NJ];
+      load_row_t<NJ>(Jg, (size_t)(c.e0 + i), row);
+      const int pl = ptl[m];
+      const AT t0 = tp[pl], t1 = tp[LP + pl], t2 = tp[2 * LP + pl];
+      AT sv[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) sv[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
+#pragma unroll
+      for (int k = 0; k < DC; ++k) {
+        AT v = row[k] * sv[0];
+#pragma unroll
+        for (int a = 1; a < M; ++a) v += row[a * DC + k] * sv[a];
+        vv[k * LD + pos[m]] = v;
+      }
+    }
+    __syncthreads();
+    // ---- pass 4: per-slot sums over contiguous positions
+    AT* partV = reinterpret_cast<AT*>(d.partV);
+    for (int w = threadIdx.x; w < c.nS * DC; w += kThreads) {
+      const int sl = w / DC, comp = w - sl * DC;
+      const int4 r4 = srec[sl];
+      partV[(size_t)r4.w * DC + comp] = seg_sum(vv + comp * LD, r4.x, r4.y);
+    }
+    __syncthreads();             // vv, xs and buffer b are free again
+  }
+  cp_async_wait_all();           // no copy may still be landing when the CTA exits
+}
+
 }  // namespace gpo

@@ -248,17 +248,18 @@ def test_sampled_edges_at_medium_size(gpo):
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
 def test_schur_product_variants_bitwise(gpo, prec):
-    """The staged (bulk-copy pipeline) and classic Schur-product kernels compute the
-    same sums in the same order: the solves agree bit for bit."""
+    """The staged (bulk-copy pipeline), classic and pipelined persistent Schur-product
+    kernels compute the same sums in the same order: the solves agree bit for bit."""
     p = synth.ba_path(3, 40, 6000, "pareto")
     out = []
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec,
                                  spmv_variant=variant)
         rep = g.optimize(4)
         out.append((rep.final_cost, rep.pcg_iters_total, g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)))
-    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
-    assert np.array_equal(out[0][2], out[1][2]) and np.array_equal(out[0][3], out[1][3])
+    for o in out[1:]:
+        assert out[0][0] == o[0] and out[0][1] == o[1]
+        assert np.array_equal(out[0][2], o[2]) and np.array_equal(out[0][3], o[3])
 
 
 def test_captured_pcg_groups_bitwise(gpo):

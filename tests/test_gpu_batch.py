@@ -22,17 +22,20 @@ def windows():
     return synth.window_pool(3, 12, kf=(5, 12), pts=(200, 1500))
 
 
-def _alone(gpo, serving, p, prec, iters):
-    g, c0, p0 = serving.window_graph(p, prec)
+def _alone(gpo, serving, p, prec, iters, **kw):
+    g, c0, p0 = serving.window_graph(p, prec, **kw)
     rep = g.optimize(iters)
     return rep, g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16"])
-def test_batch_equals_alone_bitwise(gpo, windows, prec):
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("bf16", 0), ("fp32", 1), ("fp32", 3)])
+def test_batch_equals_alone_bitwise(gpo, windows, prec, variant):
+    """Also with the staged and pipelined Schur products, whose persistent CTAs walk
+    chunks of several problems."""
     from paper_2509_26581_gb300 import serving
-    alone = [_alone(gpo, serving, p, prec, 6) for p in windows]
-    built = [serving.window_graph(p, prec) for p in windows]
+    kw = dict(spmv_variant=variant, chunk_edges=256)
+    alone = [_alone(gpo, serving, p, prec, 6, **kw) for p in windows]
+    built = [serving.window_graph(p, prec, **kw) for p in windows]
     reps = gpo.optimize_batch([b[0] for b in built], 6)
     for (rep, cams, pts), (g, c0, p0), r, p in zip(alone, built, reps, windows):
         assert r.final_cost == rep.final_cost and r.accepted == rep.accepted

@@ -255,12 +255,13 @@ def test_kind_errors(gpo):
 def test_schur_product_variants_bitwise_vi(gpo, small):
     p, pims = small
     out = []
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         g, n0, p0, _ = _graph(gpo, p, pims, precision="fp32", spmv_variant=variant)
         rep = g.optimize(4)
         out.append((rep.final_cost, g.get_state(n0, p.n_kf, 16), g.get_state(p0, p.n_pts, 3)))
-    assert out[0][0] == out[1][0]
-    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    for o in out[1:]:
+        assert out[0][0] == o[0]
+        assert np.array_equal(out[0][1], o[1]) and np.array_equal(out[0][2], o[2])
 
 
 def test_sampled_edges_at_full_size(gpo):
