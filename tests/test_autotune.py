@@ -19,7 +19,8 @@ def test_choose_reads_the_table_and_falls_back():
     assert autotune.choose(3_000_000, "bf16", "ba", table, device="GPU Y") == autotune.DEFAULT
 
 
-def test_candidates_cover_both_kernels_and_three_chunk_sizes():
-    assert {c["spmv_variant"] for c in autotune.CANDIDATES} == {1, 2}
+def test_candidates_cover_the_three_kernels_and_three_chunk_sizes():
+    assert {c["spmv_variant"] for c in autotune.CANDIDATES} == {1, 2, 3}
     assert {c["chunk_edges"] for c in autotune.CANDIDATES} == {256, 512, 1024}
-    assert autotune.DEFAULT in autotune.CANDIDATES
+    # the untuned default leaves the kernel choice to the library (automatic)
+    assert autotune.DEFAULT == {"chunk_edges": 512, "spmv_variant": 0}
