@@ -448,7 +448,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.up(&d.sc, 1, R.sc0);
   pl.up(&R.ch_prob_d, std::max(NCH, 1), R.zeros_ch); pl.up(&R.cb_prob_d, d.ncblk, R.zeros_cb);
   pl.up(&R.pb_prob_d, R.npb, R.zeros_pb);
-  pl.up(&R.base_d, 1, R.zeros_small); pl.up(&R.running_d, 2, R.zeros_small);
+  pl.up(&R.base_d, 1, R.zeros_small); pl.up(&R.running_d, 4, R.zeros_small);
   // device-only arrays
   pl.add(&d.xe_J, (size_t)std::max(NX, 1) * gpo::kXJ); pl.add(&d.xe_r, (size_t)std::max(NX, 1) * gpo::kXRows);
   pl.add_raw(&d.xe_H, (size_t)std::max(NX, 1) * DB * DB * sA);
@@ -540,6 +540,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   ls.pb_prob = R.pb_prob_d; ls.pb_base = R.base_d;
   ls.running = R.running_d;
   ls.err = R.running_d + 1;
+  ls.work = R.running_d + 2;
   ls.spmv_variant = g->desc.spmv_variant;
   ls.nprob = 1; ls.n_ch = R.NCH; ls.n_cb = d.C > 0 ? d.ncblk : 0; ls.n_pb = d.P > 0 ? R.npb : 0;
   ls.ch_max = R.ch;
@@ -726,7 +727,7 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
 gpo_status gpo_host::solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin) {
   run(g, KK_LINEARIZE, [&] { return g->ks->linearize(ls, g->prec, force_lin, g->stream); });
   run(g, KK_SCHUR, [&] { return g->ks->schur_prepare(ls, g->prec, g->stream); });
-  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, 2 * sizeof(int), g->stream));
+  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, 4 * sizeof(int), g->stream));   // flags and work counters
   run(g, KK_CAM_FINALIZE, [&] { return g->ks->cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   gpo_status s = pcg_solve(g, ls, max_it);

@@ -87,7 +87,7 @@ gpo_status build_set(gpo_graph* owner, const std::vector<gpo_graph*>& gs, BatchS
   GPO_CUDA(owner, cudaMemcpyAsync(chb_d, ch_base.data(), n * 4, cudaMemcpyHostToDevice, st));
   GPO_CUDA(owner, cudaMemcpyAsync(cbb_d, cb_base.data(), n * 4, cudaMemcpyHostToDevice, st));
   GPO_CUDA(owner, cudaMemcpyAsync(pbb_d, pb_base.data(), n * 4, cudaMemcpyHostToDevice, st));
-  GPO_CUDA(owner, cudaMemsetAsync(running_d, 0, 8, st));
+  GPO_CUDA(owner, cudaMemsetAsync(running_d, 0, 16, st));
   // the host vectors go out of scope: wait for the copies
   GPO_CUDA(owner, cudaStreamSynchronize(st));
   gpo::LaunchSet ls{};
@@ -97,6 +97,7 @@ gpo_status build_set(gpo_graph* owner, const std::vector<gpo_graph*>& gs, BatchS
   ls.pb_prob = pb_d; ls.pb_base = pbb_d;
   ls.running = running_d;
   ls.err = running_d + 1;
+  ls.work = running_d + 2;
   ls.spmv_variant = owner->desc.spmv_variant;
   ls.nprob = n;
   ls.n_ch = (int)ch_prob.size();

@@ -173,6 +173,9 @@ struct LaunchSet {
   int* running;          // [2]: problems whose PCG is still iterating; [1] error flag (a
                          // bounded device wait gave up)
   int* err;              // = running + 1
+  int* work;             // = running + 2: [0] next chunk handed out by the pipelined Schur
+                         // product, [1] its CTAs that have finished (both back to 0 at
+                         // the end of every launch)
   int spmv_variant;      // Schur-product kernel: 0 auto, 1 staged (bulk copies), 2 classic
   int nprob, n_ch, n_cb, n_pb;
   int ch_max;            // largest chunk over the problems (shared-memory sizing)

@@ -1275,8 +1275,13 @@ struct Launch {
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
       if (n_sm <= 0) n_sm = 1;
     }
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ws<Mo, JT>, kWsThreads, sm);
+    static size_t occ_sm = 0;   // occupancy for the last shared-memory size asked
+    static int occ = 0;
+    if (sm != occ_sm) {
+      occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_ws<Mo, JT>, kWsThreads, sm);
+      occ_sm = sm;
+    }
     const int grid = std::max(1, std::min(ls.n_ch, n_sm * std::max(occ, 1)));
     launch_pdl(k_spmv_ws<Mo, JT>, grid, kWsThreads, sm, st, ls);
   }
@@ -1301,8 +1306,13 @@ struct Launch {
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
       if (n_sm <= 0) n_sm = 1;
     }
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_pp<Mo, JT, EPT>, kThreads, sm);
+    static size_t occ_sm = 0;   // occupancy for the last shared-memory size asked
+    static int occ = 0;
+    if (sm != occ_sm) {
+      occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_pp<Mo, JT, EPT>, kThreads, sm);
+      occ_sm = sm;
+    }
     const int grid = std::max(1, std::min(ls.n_ch, n_sm * std::max(occ, 1)));
     launch_pdl(k_spmv_pp<Mo, JT, EPT>, grid, kThreads, sm, st, ls);
   }

@@ -495,14 +495,16 @@ struct PipeChunk {
   int k, q, kl, e0, nE, p0, nP, s0, nS;   // k < 0: no more chunks
 };
 
-// The classic Schur product's passes as a persistent kernel: CTA b walks the chunks
-// b, b + G, ... of the launch set (skipping problems whose PCG has stopped).  While a
-// chunk's passes run, every thread has already issued its share of the next chunk's
-// index copies (packed edge words, slot records, point records) into the other of two
-// shared-memory buffers, the next chunk's Jacobian tiles are being prefetched into L2,
-// and the chunk after that is being located; only the slot cameras' search-direction
-// gather stays on a chunk's critical path.  The sums and their order are those of
-// k_spmv (bit-identical results).  Requires chunks of at most 1024 edges.
+// The classic Schur product's passes as a persistent kernel.  CTAs take chunks from a
+// shared counter (skipping problems whose PCG has stopped), so a CTA that starts late
+// -- the launch overlaps its predecessor's tail -- simply takes fewer; which CTA sums
+// a chunk does not change any result.  While a chunk's passes run, every thread has
+// already issued its share of the next chunk's index copies (packed edge words, slot
+// records, point records) into the other of two shared-memory buffers, the next
+// chunk's Jacobian tiles are being prefetched into L2, the chunk after that is being
+// taken, and the next chunk's search-direction gather overlaps pass 3.  The sums and
+// their order are those of k_spmv (bit-identical results).  The last CTA to finish
+// puts the counters back to 0.  Requires chunks of at most 1024 edges.
 // Resident CTAs per SM the register budget targets: BF16 rows are re-read from L2
 // anyway, so more CTAs win; FP32 rows are twice as long and their second read hits L1
 // only while fewer CTAs share it; FP64 is limited by shared memory.
@@ -524,22 +526,31 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
   AT* tp = reinterpret_cast<AT*>(smem + PL.tp);         // [3][LP] point solutions
   AT* xs = reinterpret_cast<AT*>(smem + PL.xs);         // [ns_max][DC] slot cameras' direction
   unsigned char* bufs = smem + PL.buf;
-  const int G = gridDim.x;
   int bound_q = -1;              // problem whose descriptor is in d
   pdl_wait();
 
-  // First chunk at or after k whose problem still iterates (-1: none).  The problems'
-  // scalars do not change during the launch; a one-problem launch checks them once.
-  auto next_live = [&](int k) -> int {
-    if (ls.nprob == 1) return k < ls.n_ch ? k : -1;
-    while (k < ls.n_ch) {
+  // The next chunk from the shared counter whose problem still iterates (-1: none
+  // left).  The problems' scalars do not change during the launch; a one-problem
+  // launch checks them once, a batch skips a stopped problem's remaining chunks.
+  auto grab = [&]() -> int {
+    for (;;) {
+      const int k = atomicAdd(ls.work, 1);
+      if (k >= ls.n_ch) return -1;
+      if (ls.nprob == 1) return k;
       const int q = ls.ch_prob[k];
       const Scalars* sc = ls.probs[q].sc;
       if (sc->active && !sc->pcg_done) return k;
-      const int nxt = q + 1 < ls.nprob ? ls.ch_base[q + 1] : ls.n_ch;
-      k += ((nxt - k) + G - 1) / G * G;
     }
-    return -1;
+  };
+  // a CTA that has taken its last chunk; the last one resets the counters
+  auto finish = [&]() {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(ls.work + 1, 1) == (int)gridDim.x - 1) {
+        ls.work[0] = 0;
+        ls.work[1] = 0;
+      }
+    }
   };
   // a chunk's problem and ranges (thread 0)
   auto plan = [&](int k) -> PipeChunk {
@@ -599,12 +610,15 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     if (!sc->active || sc->pcg_done) return;
   }
   if (threadIdx.x == 0) {
-    const int k0 = next_live(blockIdx.x);
+    const int k0 = grab();
     ck[0] = plan(k0);
-    ck[1] = plan(k0 < 0 ? -1 : next_live(k0 + G));
+    ck[1] = plan(k0 < 0 ? -1 : grab());
   }
   __syncthreads();
-  if (ck[0].k < 0) return;
+  if (ck[0].k < 0) {
+    finish();
+    return;
+  }
   issue(ck[0], 0, -1);
   cp_async_commit();
   for (int n = 0;; ++n) {
@@ -670,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     __syncthreads();
     // ---- pass 2: t_p = H_pp^-1 sum_e a_e; meanwhile the last warp's first thread
     // locates the chunk after next (its loads overlap the pass)
-    if (threadIdx.x == kThreads - 32) ck[(n + 2) % 3] = plan(cn.k < 0 ? -1 : next_live(cn.k + G));
+    if (threadIdx.x == kThreads - 32) ck[(n + 2) % 3] = plan(cn.k < 0 ? -1 : grab());
     cp_async_wait_all();         // the next chunk's copies (visible after the barrier)
     for (int j = threadIdx.x; j < c.nP; j += kThreads) {
       const AT* hv = reinterpret_cast<const AT*>(prec + (size_t)j * PRB);
@@ -717,6 +731,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     __syncthreads();             // vv, xs and buffer b are free again
   }
   cp_async_wait_all();           // no copy may still be landing when the CTA exits
+  finish();
 }
 
 }  // namespace gpo
