@@ -136,7 +136,9 @@ def load_peaks() -> tuple[float, str]:
 # DRAM traffic (read + write bytes) of one k_spmv launch from an ncu capture of the
 # medium workload (profiles/k_spmv_ba_medium_bf16.md), valid only for the kernel sources it
 # was taken from (keyed by a hash of them): changed kernels report null.
-MEASURED_TRAFFIC = {("bf16", "020655f7e122"): 189.6e6}
+# DRAM bytes (read + write) per Schur-product launch from an ncu capture, keyed by
+# (precision, kernel, hash of the kernel sources): stale once the sources change.
+MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "8e9b5891fc1f"): 181.3e6}
 SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
@@ -150,8 +152,23 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def spmv_traffic(precision: str):
-    return MEASURED_TRAFFIC.get((precision, kernel_source_hash()))
+def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
+    """The Schur-product kernel the library runs for these knobs (gpo_graph_desc)."""
+    v = knobs.get("spmv_variant", 0)
+    if ch_max <= 1024 and (v == 3 or (v == 0 and precision != "fp64")):
+        return "k_spmv_pp"
+    if ch_max <= 1024 and v == 1:
+        return "k_spmv_ws"
+    return "k_spmv"
+
+
+KERNEL_LABEL = {"k_spmv_pp": "k_spmv_pp (PCG Schur product, pipelined persistent)",
+                "k_spmv_ws": "k_spmv_ws (PCG Schur product, staged)",
+                "k_spmv": "k_spmv (PCG Schur product, classic)"}
+
+
+def spmv_traffic(precision: str, kernel: str):
+    return MEASURED_TRAFFIC.get((precision, kernel, kernel_source_hash()))
 
 
 def spmv_algorithmic_bytes(E: int, P: int, precision: str) -> float:
@@ -386,8 +403,8 @@ def run_vi(args, dev, stream, world: int) -> dict:
                     parallelism=f"replicas x{world}"),
         gpu_launches=int(sum(v["launches"] for v in prof.values())),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
-                      kernel="k_spmv (PCG Schur product)", peak_source=peak_kind, algorithmic_bytes=alg,
-                      avg_ms=spmv_ms),
+                      kernel=KERNEL_LABEL[spmv_kernel(args.precision, g.knobs, g.info()["chunk_edges"])],
+                      peak_source=peak_kind, algorithmic_bytes=alg, avg_ms=spmv_ms),
         clocks=clk, final_cost=rep.final_cost,
         kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items()},
         footprint_bytes=g.footprint())
@@ -460,6 +477,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         return None
     sp = prof["spmv"]
     peak, peak_kind = load_peaks()
+    kern = spmv_kernel(args.precision, g.knobs, g.info()["chunk_edges"])
     alg = spmv_algorithmic_bytes(p.n_edges, p.n_pts, args.precision)
     spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
     achieved = alg / (spmv_ms * 1e-3) / 1e9 if sp["active"] else 0.0
@@ -479,9 +497,9 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                                           h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes),
         gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      traffic=spmv_traffic(args.precision) if args.seed == 1 and g.knobs["chunk_edges"] in (0, 512)
-                      and g.knobs["spmv_variant"] in (0, 2) else None,
-                      kernel="k_spmv (PCG Schur product)", peak_source=peak_kind,
+                      traffic=spmv_traffic(args.precision, kern) if args.seed == 1
+                      and g.knobs["chunk_edges"] in (0, 512) else None,
+                      kernel=KERNEL_LABEL[kern], peak_source=peak_kind,
                       algorithmic_bytes=alg, avg_ms=spmv_ms),
         clocks=clk,
         pcg_iters_per_step=pcg_iters,
