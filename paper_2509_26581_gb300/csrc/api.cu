@@ -422,7 +422,7 @@ static gpo_status prepare(gpo_graph* g) {
   R.zeros_ch.assign(std::max(NCH, 1), 0);
   R.zeros_cb.assign(d.ncblk, 0);
   R.zeros_pb.assign(R.npb, 0);
-  R.zeros_small.assign(4, 0);
+  R.zeros_small.assign(8, 0);
   R.xzeros.assign(std::max(NX, 1), 0.0);
   R.sc0.assign(1, Scalars{});
   Plan& pl = R.pl;
@@ -448,7 +448,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.up(&d.sc, 1, R.sc0);
   pl.up(&R.ch_prob_d, std::max(NCH, 1), R.zeros_ch); pl.up(&R.cb_prob_d, d.ncblk, R.zeros_cb);
   pl.up(&R.pb_prob_d, R.npb, R.zeros_pb);
-  pl.up(&R.base_d, 1, R.zeros_small); pl.up(&R.running_d, 4, R.zeros_small);
+  pl.up(&R.base_d, 1, R.zeros_small); pl.up(&R.running_d, 8, R.zeros_small);
   // device-only arrays
   pl.add(&d.xe_J, (size_t)std::max(NX, 1) * gpo::kXJ); pl.add(&d.xe_r, (size_t)std::max(NX, 1) * gpo::kXRows);
   pl.add_raw(&d.xe_H, (size_t)std::max(NX, 1) * DB * DB * sA);
@@ -661,8 +661,12 @@ static void capture_pcg_group(gpo_graph* g, const gpo::LaunchSet& ls) {
   int c[3] = {0, 0, 0};
   for (int i = 0; i < kPcgGroup; ++i) {
     c[0] += g->ks->pcg_spmv(ls, g->prec, g->stream);
-    c[1] += g->ks->cam_apply(ls, g->prec, g->stream);
-    c[2] += g->ks->pcg_update(ls, g->prec, g->stream);
+    const int fused = g->ks->pcg_camera(ls, g->prec, g->stream);
+    c[1] += fused;
+    if (!fused) {
+      c[2] += g->ks->cam_apply(ls, g->prec, g->stream);
+      c[2] += g->ks->pcg_update(ls, g->prec, g->stream);
+    }
   }
   const cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
   if (e != cudaSuccess || !graph || cudaGraphInstantiate(&g->pcg_exec, graph, 0) != cudaSuccess) {
@@ -692,14 +696,22 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
     if (graph_ok && g->pcg_exec && std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) == 0) {
       GPO_CUDA(g, cudaGraphLaunch(g->pcg_exec, g->stream));
       g->prof.launches[KK_SPMV] += g->pcg_counts[0];
-      g->prof.launches[KK_CAM_APPLY] += g->pcg_counts[1];
-      g->prof.launches[KK_PCG_UPDATE] += g->pcg_counts[2];
+      g->prof.launches[KK_PCG_CAMERA] += g->pcg_counts[1];
+      g->prof.launches[KK_CAM_APPLY] += g->pcg_counts[2] / 2;
+      g->prof.launches[KK_PCG_UPDATE] += g->pcg_counts[2] / 2;
     } else {
       for (int i = 0; i < n; ++i) {
         g->cur_pcg_k = launched + i + 1;
         run(g, KK_SPMV, [&] { return g->ks->pcg_spmv(ls, g->prec, g->stream); });
-        run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
-        run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
+        if (g->prof.on) {   // timed separately: the camera half and the update
+          run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
+          run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
+        } else if (!g->ks->pcg_camera(ls, g->prec, g->stream)) {
+          run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
+          run(g, KK_PCG_UPDATE, [&] { return g->ks->pcg_update(ls, g->prec, g->stream); });
+        } else {
+          g->prof.launches[KK_PCG_CAMERA] += 1;
+        }
       }
     }
     launched += n;
@@ -727,7 +739,7 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
 gpo_status gpo_host::solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin) {
   run(g, KK_LINEARIZE, [&] { return g->ks->linearize(ls, g->prec, force_lin, g->stream); });
   run(g, KK_SCHUR, [&] { return g->ks->schur_prepare(ls, g->prec, g->stream); });
-  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, 4 * sizeof(int), g->stream));   // flags and work counters
+  GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, 6 * sizeof(int), g->stream));   // flags and work counters
   run(g, KK_CAM_FINALIZE, [&] { return g->ks->cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   gpo_status s = pcg_solve(g, ls, max_it);

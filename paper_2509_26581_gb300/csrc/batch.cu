@@ -87,7 +87,7 @@ gpo_status build_set(gpo_graph* owner, const std::vector<gpo_graph*>& gs, BatchS
   GPO_CUDA(owner, cudaMemcpyAsync(chb_d, ch_base.data(), n * 4, cudaMemcpyHostToDevice, st));
   GPO_CUDA(owner, cudaMemcpyAsync(cbb_d, cb_base.data(), n * 4, cudaMemcpyHostToDevice, st));
   GPO_CUDA(owner, cudaMemcpyAsync(pbb_d, pb_base.data(), n * 4, cudaMemcpyHostToDevice, st));
-  GPO_CUDA(owner, cudaMemsetAsync(running_d, 0, 16, st));
+  GPO_CUDA(owner, cudaMemsetAsync(running_d, 0, 32, st));
   // the host vectors go out of scope: wait for the copies
   GPO_CUDA(owner, cudaStreamSynchronize(st));
   gpo::LaunchSet ls{};

@@ -175,7 +175,8 @@ struct LaunchSet {
   int* err;              // = running + 1
   int* work;             // = running + 2: [0] next chunk handed out by the pipelined Schur
                          // product, [1] its CTAs that have finished (both back to 0 at
-                         // the end of every launch)
+                         // the end of every launch); [2] arrivals at the camera kernel's
+                         // grid barrier (back to 0 at every barrier), [3] its generation
   int spmv_variant;      // Schur-product kernel: 0 auto, 1 staged (bulk copies), 2 classic
   int nprob, n_ch, n_cb, n_pb;
   int ch_max;            // largest chunk over the problems (shared-memory sizing)
@@ -196,6 +197,7 @@ struct KernelSet {
   int (*pcg_spmv)(const LaunchSet& ls, Prec pr, cudaStream_t st);     // the Schur product (hot loop)
   int (*cam_apply)(const LaunchSet& ls, Prec pr, cudaStream_t st);    // y = S p camera side, alpha
   int (*pcg_update)(const LaunchSet& ls, Prec pr, cudaStream_t st);   // x, r, z; stopping rules, beta
+  int (*pcg_camera)(const LaunchSet& ls, Prec pr, cudaStream_t st);   // cam_apply + pcg_update in one launch
   int (*backsub)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*retract)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*decide)(const LaunchSet& ls, Prec pr, cudaStream_t st);

@@ -19,12 +19,12 @@ using gpo::Scalars;
 // kernels the library launches on the graph's stream.
 enum KernelKind {
   KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
-  KK_CAM_APPLY, KK_PCG_UPDATE, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT,
+  KK_CAM_APPLY, KK_PCG_UPDATE, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT, KK_PCG_CAMERA,
   KK_COUNT
 };
 inline const char* const kKernelNames[KK_COUNT] = {
     "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
-    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit"};
+    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit", "pcg_camera"};
 
 struct Profiler {
   bool on = false;
@@ -110,7 +110,7 @@ struct gpo_graph {
   // captured with (replayed by the PCG loop while profiling is off)
   cudaGraphExec_t pcg_exec = nullptr;
   gpo::LaunchSet pcg_ls{};
-  int pcg_counts[3] = {0, 0, 0};   // kernels per group: Schur product, camera half, update
+  int pcg_counts[3] = {0, 0, 0};   // kernels per group: Schur product, fused camera kernel, separate camera kernels
   bool pcg_graph_off = false;      // capture failed once: launch directly
 };
 

@@ -696,18 +696,19 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
 // sets alpha = r^T z / p^T y.
 constexpr int kApplySplit = 4;
 template <class Mo, class AT>
-__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
+struct ApplyShared {
+  double red[kCamPerBlock];
+  AT quarter[kCamPerBlock][Mo::DC];
+  AT qx[Mo::kExtra ? kCamPerBlock : 1][Mo::DB];
+};
+// One unit of the camera half: CTA-part `part` of camera block cbl of the problem bound
+// in d (every thread calls; returns uniformly).
+template <class Mo, class AT>
+__device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int part, ApplyShared<Mo, AT>& S) {
   constexpr int DB = Mo::DB, DC = Mo::DC, TB = Dims<Mo>::TB;
-  __shared__ double red[kCamPerBlock];
-  __shared__ AT quarter[kCamPerBlock][DC];
-  __shared__ AT qx[Mo::kExtra ? kCamPerBlock : 1][DB];
-  __shared__ DevBA d;
-  pdl_trigger();
-  const int cb = blockIdx.x / kApplySplit, part = blockIdx.x % kApplySplit;
-  const int prob_ = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
-  const int cbl = ls.nprob == 1 ? cb : cb - ls.cb_base[prob_];
-  bind_problem(d, ls.probs + prob_);
-  pdl_wait();
+  double* red = S.red;
+  auto& quarter = S.quarter;
+  auto& qx = S.qx;
   Scalars* sc = d.sc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cams_per_cta = kCamPerBlock / kApplySplit;             // 2
@@ -821,14 +822,25 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   }
 }
 
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
+  __shared__ ApplyShared<Mo, AT> S;
+  __shared__ DevBA d;
+  pdl_trigger();
+  const int cb = blockIdx.x / kApplySplit, part = blockIdx.x % kApplySplit;
+  const int prob_ = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
+  const int cbl = ls.nprob == 1 ? cb : cb - ls.cb_base[prob_];
+  bind_problem(d, ls.probs + prob_);
+  pdl_wait();
+  cam_apply_body<Mo, AT>(ls, d, cbl, part, S);
+}
+
 // One warp per camera: x += sigma alpha p, r -= alpha y, z = M r; the last CTA of
 // the problem reduces r^T z and |r|^2, applies the stopping rules (tolerance,
 // rejection ratio, iteration cap) and computes beta and the normalisation factor.
 template <class Mo, class AT>
-__global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) {
+__device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, double (*red)[2]) {
   constexpr int DB = Mo::DB, TB = Dims<Mo>::TB;
-  __shared__ double red[kCamPerBlock][2];
-  GPO_BIND(cb, cbl)
   Scalars* sc = d.sc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = cbl * kCamPerBlock + warp;
@@ -924,6 +936,85 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
     sc->pcg_done = done;
     if (done) atomicSub(ls.running, 1);
     sc->ticket = 0u;
+  }
+}
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) {
+  __shared__ double red[kCamPerBlock][2];
+  GPO_BIND(cb, cbl)
+  pcg_update_body<Mo, AT>(ls, d, cbl, red);
+}
+
+// Grid-wide barrier of the persistent camera kernel (every CTA resident): the last
+// CTA to arrive resets the count and advances the generation the others wait on.  The
+// wait is bounded; false if it gave up (the caller raises *ls.err).
+__device__ __forceinline__ bool grid_sync(int* count, int* gen, int ctas) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile int* vg = gen;
+    const int g0 = *vg;
+    __threadfence();
+    if (atomicAdd(count, 1) == ctas - 1) {
+      atomicExch(count, 0);
+      __threadfence();
+      atomicAdd(gen, 1);
+    } else {
+      unsigned n = 0;
+      while (*vg == g0) {
+        if (++n > kSpinLimit) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// The camera half of the Schur product and the PCG update in one persistent launch
+// (the production path; profiling times the two separately): the CTAs first walk the
+// camera half's units (camera block, quarter) -- the last unit of a problem sets its
+// alpha -- meet at a grid barrier, then walk the update's camera blocks -- the last
+// block of a problem applies the stopping rules and sets beta.  The same bodies as
+// k_cam_apply and k_pcg_update: bit-identical results.  Launched only when the
+// camera half's units fit one wave of resident CTAs (one unit per CTA; the grid is
+// then resident when the barrier waits); larger problems keep the two launches, whose
+// many concurrent CTAs hide the units' latency better than a persistent loop.
+template <class Mo, class AT>
+__global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet ls) {
+  __shared__ ApplyShared<Mo, AT> S;
+  __shared__ double red[kCamPerBlock][2];
+  __shared__ DevBA d;
+  pdl_trigger();
+  pdl_wait();
+  const int G = gridDim.x;
+  int bound = -1;
+  auto bind = [&](int q) {
+    if (q != bound) {          // CTA-uniform
+      __syncthreads();         // no thread still reads the previous descriptor
+      bind_problem(d, ls.probs + q);
+      bound = q;
+    }
+  };
+  for (int u = blockIdx.x; u < ls.n_cb * kApplySplit; u += G) {
+    const int cb = u / kApplySplit, part = u % kApplySplit;
+    const int q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
+    bind(q);
+    cam_apply_body<Mo, AT>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], part, S);
+    __syncthreads();
+  }
+  if (!grid_sync(ls.work + 2, ls.work + 3, G)) {
+    if (threadIdx.x == 0) atomicExch(ls.err, 1);
+    return;
+  }
+  for (int cb = blockIdx.x; cb < ls.n_cb; cb += G) {
+    const int q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
+    bind(q);
+    pcg_update_body<Mo, AT>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], red);
+    __syncthreads();
   }
 }
 
@@ -1348,6 +1439,30 @@ struct Launch {
     else launch_pdl(k_cam_apply<Mo, float>, ls.n_cb * kApplySplit, kCamPerBlock * 32, 0, st, ls);
     return 1;
   }
+  template <class AT>
+  static int pcg_camera_cap() {
+    static int cap = 0;   // resident CTAs of the fused camera kernel
+    if (!cap) {
+      int dev = 0, n_sm = 0, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_camera<Mo, AT>, kCamPerBlock * 32, 0);
+      cap = std::max(1, n_sm) * std::max(1, occ);
+    }
+    return cap;
+  }
+  // Launches the fused camera kernel if the camera half's units fit one resident wave
+  // (returns 1); otherwise launches nothing and returns 0 (the caller launches
+  // cam_apply and pcg_update).
+  static int pcg_camera(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_cb == 0) return 0;
+    const int units = ls.n_cb * kApplySplit;
+    const int cap = pr == Prec::F64 ? pcg_camera_cap<double>() : pcg_camera_cap<float>();
+    if (units > cap) return 0;
+    if (pr == Prec::F64) launch_pdl(k_pcg_camera<Mo, double>, units, kCamPerBlock * 32, 0, st, ls);
+    else launch_pdl(k_pcg_camera<Mo, float>, units, kCamPerBlock * 32, 0, st, ls);
+    return 1;
+  }
   static int pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_cb == 0) return 0;
     if (pr == Prec::F64) launch_pdl(k_pcg_update<Mo, double>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
@@ -1406,6 +1521,7 @@ KernelSet make_kernel_set(ModelKind kind) {
   k.pcg_spmv = &L::pcg_spmv;
   k.cam_apply = &L::cam_apply;
   k.pcg_update = &L::pcg_update;
+  k.pcg_camera = &L::pcg_camera;
   k.backsub = &L::backsub;
   k.retract = &L::retract;
   k.decide = &L::decide;
