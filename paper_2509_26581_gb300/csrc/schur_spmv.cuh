@@ -635,8 +635,13 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     }
     issue(cn, b ^ 1, bound_q);
     cp_async_commit();
-    cp_async_wait_prev();        // this thread's copies into buffer b have landed
-    __syncthreads();             // ... and everyone else's; d is bound
+    // Buffer b: the first chunk's copies are waited for here; a later chunk's landed
+    // during the previous chunk's pass 2 (wait_all, then that pass's barrier), and its
+    // search direction was gathered in the previous pass 3 -- no barrier needed.
+    if (n == 0) {
+      cp_async_wait_prev();
+      __syncthreads();
+    }
 
     unsigned char* B = bufs + b * PL.bsize;
     const uint32_t* meta = reinterpret_cast<const uint32_t*>(B + PL.meta);
@@ -654,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
         ptl[m] = (int)(w >> 20);
       }
     }
-    __syncthreads();
+    if (n == 0) __syncthreads();   // the first chunk's direction gather
     const JT* Jg = reinterpret_cast<const JT*>(d.J);
     // ---- pass 1: a_e = Jp^T (Jc x_c)
 #pragma unroll
