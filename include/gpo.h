@@ -429,6 +429,17 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
 gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* params,
                            double* S_out, double* g_out);
 
+/* Failure-detection test of the bounded device waits: prepares one PCG solve and
+ * launches the fused camera kernel (camera half of the Schur product and PCG update)
+ * with its grid barrier waiting for one CTA more than the grid, so that nothing can
+ * complete it.  The barrier's bounded wait (1 s) gives up, the kernel raises the
+ * error flag and returns.  Returns GPO_ERR_TIMEOUT when that happened (the expected
+ * result), GPO_ERR_UNSUPPORTED when the graph's camera blocks do not fit one resident
+ * wave (the fused kernel is then not used), GPO_ERR_STATE otherwise.  The graph's
+ * device counters are left clean and the context usable: a later gpo_optimize runs
+ * as if this call had not been made. */
+gpo_status gpo_debug_wait_timeout(gpo_graph* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1504,6 +1504,35 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
   return GPO_OK;
 }
 
+gpo_status gpo_debug_wait_timeout(gpo_graph* g) {
+  if (!g) return GPO_ERR_ARG;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  gpo_lm_params prm;
+  gpo_lm_params_default(&prm);
+  Scalars sc;
+  fill_scalars(g, prm, prm.initial_damping, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
+  g->ks->cam_prepare(g->ls, false, g->stream);
+  g->ks->linearize(g->ls, g->prec, true, g->stream);
+  g->ks->schur_prepare(g->ls, g->prec, g->stream);
+  GPO_CUDA(g, cudaMemsetAsync(g->ls.running, 0, 6 * sizeof(int), g->stream));
+  g->ks->cam_finalize(g->ls, g->prec, g->stream);
+  gpo::LaunchSet ls = g->ls;
+  ls.debug_wait = 1;   // one CTA more than the grid: nothing completes the barrier
+  const int fused = g->ks->pcg_camera(ls, g->prec, g->stream);
+  GPO_CUDA(g, cudaGetLastError());
+  int flags[2] = {0, 0};
+  GPO_CUDA(g, cudaMemcpyAsync(flags, ls.running, sizeof(flags), cudaMemcpyDeviceToHost, g->stream));
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  GPO_CUDA(g, cudaMemsetAsync(g->ls.running, 0, 6 * sizeof(int), g->stream));   // leave clean counters
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (!fused) return fail(g, GPO_ERR_UNSUPPORTED, "the camera blocks do not fit one resident wave");
+  if (flags[1]) return fail(g, GPO_ERR_TIMEOUT, "the camera kernel's grid barrier gave up");
+  return fail(g, GPO_ERR_STATE, "the grid barrier did not give up");
+}
+
 gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* params, double* S_out, double* g_out) {
   if (!g) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));

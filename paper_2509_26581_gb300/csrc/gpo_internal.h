@@ -177,7 +177,11 @@ struct LaunchSet {
                          // product, [1] its CTAs that have finished (both back to 0 at
                          // the end of every launch); [2] arrivals at the camera kernel's
                          // grid barrier (back to 0 at every barrier), [3] its generation
-  int spmv_variant;      // Schur-product kernel: 0 auto, 1 staged (bulk copies), 2 classic
+  int spmv_variant;      // Schur-product kernel: 0 auto, 1 staged (bulk copies), 2 classic,
+                         // 3 pipelined
+  int debug_wait;        // test hook, 0 in production: the camera kernel's grid barrier
+                         // waits for this many CTAs more than the grid, so that its
+                         // bounded wait gives up
   int nprob, n_ch, n_cb, n_pb;
   int ch_max;            // largest chunk over the problems (shared-memory sizing)
   int ns_max, np_max;    // most slots / points in one chunk over the problems

@@ -945,9 +945,17 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) 
   pcg_update_body<Mo, AT>(ls, d, cbl, red);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr unsigned long long kWaitNs = 1000000000ull;   // bounded waits give up after 1 s
+
 // Grid-wide barrier of the persistent camera kernel (every CTA resident): the last
 // CTA to arrive resets the count and advances the generation the others wait on.  The
-// wait is bounded; false if it gave up (the caller raises *ls.err).
+// wait is bounded (kWaitNs of wall time); false if it gave up (the caller raises
+// *ls.err).
 __device__ __forceinline__ bool grid_sync(int* count, int* gen, int ctas) {
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -960,9 +968,9 @@ __device__ __forceinline__ bool grid_sync(int* count, int* gen, int ctas) {
       __threadfence();
       atomicAdd(gen, 1);
     } else {
-      unsigned n = 0;
+      const unsigned long long t0 = global_ns();
       while (*vg == g0) {
-        if (++n > kSpinLimit) {
+        if (global_ns() - t0 > kWaitNs) {
           ok = 0;
           break;
         }
@@ -1006,7 +1014,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
     cam_apply_body<Mo, AT>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], part, S);
     __syncthreads();
   }
-  if (!grid_sync(ls.work + 2, ls.work + 3, G)) {
+  if (!grid_sync(ls.work + 2, ls.work + 3, G + ls.debug_wait)) {
     if (threadIdx.x == 0) atomicExch(ls.err, 1);
     return;
   }

@@ -116,6 +116,7 @@ _SIGS = {
     "gpo_debug_linearize_edges": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
+    "gpo_debug_wait_timeout": (C.c_int, [_P]),
 }
 
 
@@ -306,6 +307,10 @@ class Graph:
         _check(lib.gpo_debug_step(self.h, lam, None if params is None else C.byref(params),
                                   _ptr(dx), C.byref(it)), self.h)
         return dx, it.value
+
+    def debug_wait_timeout(self) -> int:
+        """gpo_debug_wait_timeout: the status it returns (GPO_ERR_TIMEOUT expected)."""
+        return int(lib.gpo_debug_wait_timeout(self.h))
 
     def debug_schur(self, lam: float, n_cams: int, params: gpo_lm_params | None = None, db: int = 9):
         S = np.zeros((n_cams, db, db))

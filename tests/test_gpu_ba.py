@@ -262,6 +262,22 @@ def test_schur_product_variants_bitwise(gpo, prec):
         assert np.array_equal(out[0][2], o[2]) and np.array_equal(out[0][3], o[3])
 
 
+def test_bounded_wait_gives_up_and_the_context_survives(gpo):
+    """Failure detection without a GPU fault: the fused camera kernel's grid barrier is
+    made to wait for one CTA more than the grid, so nothing completes it; its bounded
+    wait gives up after a second, the kernel raises the error flag and returns, and the
+    call reports GPO_ERR_TIMEOUT.  The same graph then optimises bit for bit like a
+    fresh one."""
+    p = synth.ba_path(4, 40, 6000, "pareto")
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp32")
+    assert g.debug_wait_timeout() == gpo.GPO_ERR_TIMEOUT
+    rep = g.optimize(3)
+    h, d0, q0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp32")
+    ref = h.optimize(3)
+    assert rep.final_cost == ref.final_cost and rep.pcg_iters_total == ref.pcg_iters_total
+    assert np.array_equal(g.get_state(c0, p.n_cams, 9), h.get_state(d0, p.n_cams, 9))
+
+
 def test_captured_pcg_groups_bitwise(gpo):
     """Full groups of PCG iterations replay a captured CUDA graph unless profiling is on
     (profiling times every launch directly): both give the same solve bit for bit."""
