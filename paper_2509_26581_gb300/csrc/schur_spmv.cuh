@@ -505,9 +505,10 @@ struct PipeChunk {
 // taken, and the next chunk's search-direction gather overlaps pass 3.  The sums and
 // their order are those of k_spmv (bit-identical results).  The last CTA to finish
 // puts the counters back to 0.  Requires chunks of at most 1024 edges.
-// Resident CTAs per SM the register budget targets: BF16 rows are re-read from L2
-// anyway, so more CTAs win; FP32 rows are twice as long and their second read hits L1
-// only while fewer CTAs share it; FP64 is limited by shared memory.
+//
+// PipeOcc: resident CTAs per SM the register budget targets.  BF16 rows are re-read
+// from L2 anyway, so more CTAs win; FP32 rows are twice as long and their second read
+// hits L1 only while fewer CTAs share it; FP64 is limited by shared memory.
 template <class JT> struct PipeOcc { static constexpr int value = sizeof(JT) == 2 ? 5 : (sizeof(JT) == 4 ? 4 : 2); };
 template <class Mo, class JT, int EPT>
 __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(LaunchSet ls) {
