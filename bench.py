@@ -239,14 +239,17 @@ def extra_vi(dev, stream, iters: int = 10) -> dict:
         g.optimize(1, params)                     # finalize + warm
         g.set_initial(0, p.nav0)
         g.set_initial(p.n_kf, p.pts0)
-        g.set_profiling(True)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        rep = g.optimize(iters, params)
+        rep = g.optimize(iters, params)           # production path
         ev1.record(stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
+        g.set_initial(0, p.nav0)                  # per-kernel pass, same iterations
+        g.set_initial(p.n_kf, p.pts0)
+        g.set_profiling(True)
+        g.optimize(iters, params)
         prof = g.profile()
         sp = prof["spmv"]
         spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
@@ -299,14 +302,17 @@ def extra_large(dev, stream, iters: int = 3) -> dict:
         g.set_initial(c0, p.cams0)
         g.set_initial(p0, p.pts0)
         info = g.info()
-        g.set_profiling(True)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        rep = g.optimize(iters, params)
+        rep = g.optimize(iters, params)           # production path
         ev1.record(stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
+        g.set_initial(c0, p.cams0)                # per-kernel pass, same iterations
+        g.set_initial(p0, p.pts0)
+        g.set_profiling(True)
+        g.optimize(iters, params)
         prof = g.profile()
         sp = prof["spmv"]
         spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
@@ -375,8 +381,10 @@ def run_vi(args, dev, stream, world: int) -> dict:
     g, _, _, _ = gpo.vi_graph(p, precision=args.precision, device=dev, stream=stream.cuda_stream,
                               **knobs(args))
     g.optimize(args.warmup, params)
+    nav_w = g.get_state(0, p.n_kf, 16)
+    pts_w = g.get_state(p.n_kf, p.n_pts, 3)
     torch.cuda.synchronize()
-    g.set_profiling(True)
+    g.set_profiling(False)
     clocks = ClockSampler(dev)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -386,6 +394,11 @@ def run_vi(args, dev, stream, world: int) -> dict:
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    launches = int(sum(v["launches"] for v in g.profile().values()))
+    g.set_initial(0, nav_w)                       # per-kernel pass from the same state
+    g.set_initial(p.n_kf, pts_w)
+    g.set_profiling(True)
+    g.optimize(args.steps, params)
     prof = g.profile()
     sp = prof["spmv"]
     peak, peak_kind = load_peaks()
@@ -401,7 +414,7 @@ def run_vi(args, dev, stream, world: int) -> dict:
                     stereo_edges=p.n_edges, pcg_max_iters=100, pcg_tol=1e-6, pcg_rejection_ratio="off",
                     schedule=g.knobs,
                     parallelism=f"replicas x{world}"),
-        gpu_launches=int(sum(v["launches"] for v in prof.values())),
+        gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
                       kernel=KERNEL_LABEL[spmv_kernel(args.precision, g.knobs, g.info()["chunk_edges"])],
                       peak_source=peak_kind, algorithmic_bytes=alg, avg_ms=spmv_ms),
@@ -427,8 +440,10 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
                              args.precision, device=dev, stream=stream.cuda_stream, **knobs(args))
     g.optimize(args.warmup, params)               # also freezes the topology and plans memory
+    cams_w = g.get_state(c0, p.n_cams, 9)         # the state the timed iterations start from
+    pts_w = g.get_state(p0, p.n_pts, 3)
     torch.cuda.synchronize()
-    g.set_profiling(True)
+    g.set_profiling(False)                        # the production path; resets the launch counts
     clocks = ClockSampler(dev)
     if dist:
         dist.barrier()
@@ -441,14 +456,21 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    prof = g.profile()
+    launches = int(sum(v["launches"] for v in g.profile().values()))
     hist = g.history()
     if dist:
         import torch.distributed as tdist
         t = torch.tensor([ms], device="cuda")
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         ms = float(t.item())
-    launches = int(sum(v["launches"] for v in prof.values()))
+    # per-kernel times: the same iterations again from the same state (deterministic),
+    # every launch bracketed by CUDA events on the stream (direct launches, the camera
+    # half and the PCG update timed apart)
+    g.set_initial(c0, cams_w)
+    g.set_initial(p0, pts_w)
+    g.set_profiling(True)
+    g.optimize(args.steps, params)
+    prof = g.profile()
 
     # end to end through the public API with host buffers: every step copies the
     # state in from pinned host memory, runs one LM iteration and reads the state back

@@ -139,7 +139,15 @@ typedef struct {
                                  best iterate; <= 0 or inf disables; default 10 */
   int32_t pcg_normalize;      /* keep the PCG residual at unit norm each iteration
                                  (Sec. IV-E); -1 = on for FP32/BF16, off for FP64 */
-  int32_t reserved0;
+  int32_t pcg_restart_every;  /* residual restarts: after every this many PCG
+                                 iterations one extra Schur product recomputes the
+                                 true residual r = g - S x from the current solution
+                                 and the direction restarts from z = M r; the
+                                 recursively updated residual of FP32/BF16 arithmetic
+                                 drifts from the true one.  -1 (default) or 0 = off
+                                 (a restart discards the Krylov directions, which slows
+                                 convergence); otherwise >= 4 (smaller values are
+                                 raised to 4). */
 } gpo_lm_params;
 
 typedef struct {
@@ -162,6 +170,8 @@ typedef struct {
   double pcg_residual;        /* final |r| / |g| of the PCG solve */
   int32_t accepted;
   int32_t pcg_iters;
+  int32_t pcg_products;       /* Schur products run: PCG iterations plus residual restarts */
+  int32_t reserved0;
 } gpo_iter_record;
 
 /* Defaults for the two option structs.  Never fail for non-null pointers. */

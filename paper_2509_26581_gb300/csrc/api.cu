@@ -603,7 +603,7 @@ void gpo_host::prof_resolve(gpo_graph* g) {
     p.ms[m.kind] += el;
     bool act = true;
     if (m.kind == KK_SPMV && m.lm_iter >= 0 && m.lm_iter < (int)g->hist.size())
-      act = m.pcg_k <= g->hist[m.lm_iter].pcg_iters;
+      act = m.pcg_k <= g->hist[m.lm_iter].pcg_products;
     if (act) {
       p.active[m.kind]++;
       p.active_ms[m.kind] += el;
@@ -630,6 +630,8 @@ void gpo_host::fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda,
   s.pcg_rel = p.pcg_tol_relative ? 1 : 0;
   s.max_it = std::max(1, p.pcg_max_iters);
   s.normalize = p.pcg_normalize < 0 ? (g->prec != Prec::F64 ? 1 : 0) : (p.pcg_normalize ? 1 : 0);
+  s.restart_every = p.pcg_restart_every <= 0 ? 0 : std::max(4, p.pcg_restart_every);
+  s.restart = 0;
   s.sigma = 1.0;
   s.inv_n = 1.0;
   s.active = 1;
@@ -688,8 +690,11 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
   if (gpo_status s = gpo_host::ensure_runtime(g); s != GPO_OK) return s;
   const int kGroup = kPcgGroup;
   int launched = 0, slot = 0, pending = -1;
-  while (launched < max_it) {
-    const int n = std::min(kGroup, max_it - launched);
+  // restart iterations (at most one per four PCG iterations) are launched on top of
+  // max_it; the device stops at max_it counted PCG iterations
+  const int max_launch = max_it + max_it / 4 + 1;
+  while (launched < max_launch) {
+    const int n = std::min(kGroup, max_launch - launched);
     const bool graph_ok = !g->prof.on && !g->pcg_graph_off && n == kGroup;
     if (graph_ok && (!g->pcg_exec || std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) != 0) && launched > 0)
       capture_pcg_group(g, ls);   // after one direct group, so kernel attributes are set
@@ -853,6 +858,7 @@ gpo_status gpo_lm_params_default(gpo_lm_params* out) {
   out->pcg_tol_relative = 1;
   out->pcg_rejection_ratio = 10.0;
   out->pcg_normalize = -1;
+  out->pcg_restart_every = -1;
   return GPO_OK;
 }
 
@@ -1277,6 +1283,8 @@ gpo_status gpo_get_history(gpo_graph* g, gpo_iter_record* out, int32_t cap, int3
     out[i].pcg_residual = h.pcg_residual;
     out[i].accepted = h.accepted;
     out[i].pcg_iters = h.pcg_iters;
+    out[i].pcg_products = h.pcg_products;
+    out[i].reserved0 = 0;
   }
   if (n_out) *n_out = n;
   return GPO_OK;

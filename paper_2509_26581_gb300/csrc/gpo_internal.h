@@ -68,12 +68,16 @@ struct Scalars {
   unsigned int ticket;   // last-CTA counter of the reductions
   int active;            // the problem takes part in the current launches
   int lm_max;            // LM iterations to run (the problem deactivates after them)
-  int pad_;
+  int restart_every;     // true-residual restart period in PCG iterations (0: off)
+  int restart;           // the current PCG iteration is a restart: the product is S x,
+                         // the update sets r = g - S x and restarts the direction
+  int pcg_products;      // Schur products of the current solve (iterations + restarts)
+  int pad2_;
 };
 
 struct IterRecord {       // mirrors gpo_iter_record
   double cost, cand_cost, model_decrease, rho, lambda, pcg_residual;
-  int accepted, pcg_iters;
+  int accepted, pcg_iters, pcg_products, pad_;
 };
 
 // Raw device pointers of one problem.  Arrays marked AT are of the accumulation type

@@ -678,6 +678,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     sc->beta = 0.0;
     sc->pidx = 0;
     sc->pcg_it = 0;
+    sc->pcg_products = 0;
+    sc->restart = 0;
     sc->use_best = 0;
     sc->save_best = 0;
     sc->tol_abs = sc->pcg_rel ? sc->pcg_tol * gn : sc->pcg_tol;
@@ -717,9 +719,12 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
   // the camera's slot range is loaded with the solve's flags (one round trip)
   const int sa = c < d.C ? d.cam_s_off[c] : 0, sb = c < d.C ? d.cam_s_off[c + 1] : 0;
   if (!sc->active || sc->pcg_done) return;
-  const AT* pold_all = reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
-  const AT* z_all = reinterpret_cast<const AT*>(d.z);
-  const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
+  // the vector the product is taken of: the direction p = (z + beta p_old) / n, or in a
+  // restart iteration the current solution x (read as (x + 0 x) / 1, exactly x)
+  const int restart = sc->restart;
+  const AT* z_all = reinterpret_cast<const AT*>(restart ? d.x : d.z);
+  const AT* pold_all = restart ? z_all : reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
+  const AT beta = restart ? (AT)0 : (AT)sc->beta, inv_n = restart ? (AT)1 : (AT)sc->inv_n;
   AT dot = (AT)0;   // per-warp partial in AT, accumulated across warps in FP64
   AT pi = (AT)0;
   if (c < d.C) {   // warp-uniform
@@ -774,7 +779,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     AT* pnew = reinterpret_cast<AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
     pi = lane < DB ? (z_all[DB * (size_t)c + lane] + beta * pold_all[DB * (size_t)c + lane]) * inv_n : (AT)0;
     if (lane < DB) {
-      pnew[lane] = pi;
+      if (!restart) pnew[lane] = pi;
       if (sc->save_best)
         reinterpret_cast<AT*>(d.xbest)[DB * (size_t)c + lane] = reinterpret_cast<const AT*>(d.x)[DB * (size_t)c + lane];
     }
@@ -795,6 +800,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
       dot = pi * yi;
     }
   }
+  if (restart) return;   // S x needs no alpha (uniform for the CTA)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
   if (lane == 0) red[warp] = (double)dot;
@@ -847,17 +853,21 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
   // the camera's inputs that do not depend on the solve's scalars are loaded together
   // with them (one round trip before the arithmetic instead of two)
   const bool mine = c < d.C && lane < DB;
-  AT r0 = (AT)0, y0 = (AT)0, mrow[DB];
+  AT r0 = (AT)0, y0 = (AT)0, g0 = (AT)0, mrow[DB];
 #pragma unroll
   for (int j = 0; j < DB; ++j) mrow[j] = (AT)0;
   if (mine) {
     const AT* Mi = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * TB;
     r0 = reinterpret_cast<const AT*>(d.r)[DB * (size_t)c + lane];
     y0 = reinterpret_cast<const AT*>(d.y)[DB * (size_t)c + lane];
+    g0 = reinterpret_cast<const AT*>(d.g)[DB * (size_t)c + lane];
 #pragma unroll
     for (int j = 0; j < DB; ++j) mrow[j] = Mi[sym_idx(DB, lane, j)];
   }
   if (!sc->active || sc->pcg_done) return;
+  // a restart iteration: y = S x at the current solution, and the residual becomes the
+  // true one, g - S x (unit scale), with the direction restarted from z = M r
+  const int restart = sc->restart;
   AT rz_c = (AT)0, rr_c = (AT)0;   // per-warp partials in AT, accumulated across warps in FP64
   if (c < d.C) {   // warp-uniform
     const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
@@ -867,8 +877,12 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
     const AT* pv = reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
     AT ri = (AT)0;
     if (lane < DB) {
-      x[lane] += sa * pv[lane];
-      ri = r0 * sn - alpha * y0;
+      if (restart) {
+        ri = g0 - y0;
+      } else {
+        x[lane] += sa * pv[lane];
+        ri = r0 * sn - alpha * y0;
+      }
       r[lane] = ri;
     }
     AT zi = (AT)0;
@@ -904,9 +918,11 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
   sum_partials(d.cblk_part, d.ncblk, rz, rr);
   if (threadIdx.x == 0) {
     const double n = sqrt(rr);
+    if (restart) sc->sigma = 1.0;            // r is now the true residual
     const double rtrue = sc->sigma * n;
-    sc->pcg_it += 1;
+    if (!restart) sc->pcg_it += 1;           // a restart is an extra product, not an iteration
     sc->pcg_total += 1;
+    sc->pcg_products += 1;
     sc->rnorm = rtrue;
     int done = 0;
     sc->save_best = 0;
@@ -923,7 +939,7 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
       done = 1;
       if (!isfinite(rtrue)) sc->use_best = 1;
     }
-    sc->beta = rz / sc->rz;
+    sc->beta = restart ? 0.0 : rz / sc->rz;   // a restart starts the direction from z
     if (sc->normalize && n > 0.0) {
       sc->inv_n = 1.0 / n;
       sc->sigma *= n;
@@ -932,7 +948,8 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
       sc->inv_n = 1.0;
       sc->rz = rz;
     }
-    sc->pidx ^= 1;
+    if (!restart) sc->pidx ^= 1;            // a restart wrote no new direction
+    sc->restart = (!done && !restart && sc->restart_every > 0 && sc->pcg_it % sc->restart_every == 0) ? 1 : 0;
     sc->pcg_done = done;
     if (done) atomicSub(ls.running, 1);
     sc->ticket = 0u;
@@ -1194,6 +1211,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
     h.pcg_residual = sc->gnorm > 0.0 ? sc->rnorm / sc->gnorm : 0.0;
     h.accepted = acc ? 1 : 0;
     h.pcg_iters = sc->pcg_it;
+    h.pcg_products = sc->pcg_products;
   }
   double lam = sc->lambda, nu = sc->nu;
   if (acc) {

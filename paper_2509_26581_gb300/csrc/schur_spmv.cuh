@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   // early exit, so that the index loads below start one round trip sooner
   const Scalars* sc = d.sc;
   const ChunkRange cr = chunk_range(d, kl);
-  const int act = sc->active, done = sc->pcg_done, pidx = sc->pidx;
+  const int act = sc->active, done = sc->pcg_done, pidx = sc->pidx, restart = sc->restart;
   const double beta_d = sc->beta, inv_n_d = sc->inv_n;
   if (!act || done) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -65,9 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   }
   // one thread per slot: its record (edge range, camera, partial row) and the search
   // direction p_k = (z_k + beta_k p_{k-1}) / n_k of its camera
-  const AT* zv = reinterpret_cast<const AT*>(d.z);
-  const AT* pold = reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
-  const AT beta = (AT)beta_d, inv_n = (AT)inv_n_d;
+  // the direction p = (z + beta p_old) / n, or in a restart iteration the solution x
+  const AT* zv = reinterpret_cast<const AT*>(restart ? d.x : d.z);
+  const AT* pold = restart ? zv : reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
+  const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
   for (int t = threadIdx.x; t < cr.nS; t += kThreads) {
     const int4 r4 = __ldg(d.slot_rec + cr.s0 + t);
     so[t] = r4.x;
@@ -316,10 +317,11 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
         cq = q;
         P = ls.probs + q;
         const Scalars* sc = P->sc;
-        zv = reinterpret_cast<const AT*>(P->z);
-        pold = reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-        beta = (AT)sc->beta;
-        inv_n = (AT)sc->inv_n;
+        const int restart = sc->restart;   // a restart's product is taken of x
+        zv = reinterpret_cast<const AT*>(restart ? P->x : P->z);
+        pold = restart ? zv : reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
+        beta = restart ? (AT)0 : (AT)sc->beta;
+        inv_n = restart ? (AT)1 : (AT)sc->inv_n;
       }
       const int kl = k - ls.ch_base[q];
       const int e0 = P->ch_e0[kl], e1 = P->ch_e0[kl + 1];
@@ -596,9 +598,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     const DevBA* P = c.q == bound_q ? &d : ls.probs + c.q;
     const int4* srec = reinterpret_cast<const int4*>(bufs + b * PL.bsize + PL.srec);
     const Scalars* sc = P->sc;
-    const AT* zv = reinterpret_cast<const AT*>(P->z);
-    const AT* pold = reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-    const AT beta = (AT)sc->beta, inv_n = (AT)sc->inv_n;
+    const int restart = sc->restart;     // a restart's product is taken of x
+    const AT* zv = reinterpret_cast<const AT*>(restart ? P->x : P->z);
+    const AT* pold = restart ? zv : reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
+    const AT beta = restart ? (AT)0 : (AT)sc->beta, inv_n = restart ? (AT)1 : (AT)sc->inv_n;
     for (int w = threadIdx.x; w < c.nS * DC; w += kThreads) {
       const int sl = w / DC, k = w - sl * DC;
       const size_t o = DB * (size_t)srec[sl].z + k;

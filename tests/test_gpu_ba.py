@@ -262,6 +262,38 @@ def test_schur_product_variants_bitwise(gpo, prec):
         assert np.array_equal(out[0][2], o[2]) and np.array_equal(out[0][3], o[3])
 
 
+def test_residual_restarts_fp64_match_the_oracle(gpo):
+    """True-residual restarts (r = g - S x every 25 iterations, direction restarted) in
+    FP64: the restarted PCG still solves each LM system to tolerance, so the LM run
+    matches the oracle to 1e-9; the history counts one extra Schur product per
+    restart."""
+    p = synth.ba_ring(0, 10, 500, 6)
+    params = gpo.default_params(pcg_max_iters=500, pcg_tol=1e-14, pcg_rejection_ratio=0.0,
+                                pcg_restart_every=25)
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64")
+    rep = g.optimize(10, params)
+    _, orep = olm.levenberg_marquardt(_oracle_problem(p), 10)
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
+    hist = g.history()
+    assert any(h["pcg_iters"] > 25 for h in hist)
+    for h in hist:
+        restarts = h["pcg_products"] - h["pcg_iters"]
+        assert restarts == (h["pcg_iters"] - 1) // 25 or restarts == h["pcg_iters"] // 25
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_residual_restarts_mixed_precision(gpo, prec):
+    """Mixed precision with restarts every 20 iterations and without (the default):
+    both converge to the FP64 optimum within 1e-6."""
+    p = synth.ba_ring(7, 20, 4000, 6, outlier_frac=0.01, huber_delta=2.0)
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, "fp64")
+    ref = g.optimize(30).final_cost
+    for every in (20, 0):
+        h, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec)
+        cost = h.optimize(30, gpo.default_params(pcg_restart_every=every)).final_cost
+        assert abs(cost - ref) <= 1e-6 * ref
+
+
 def test_bounded_wait_gives_up_and_the_context_survives(gpo):
     """Failure detection without a GPU fault: the fused camera kernel's grid barrier is
     made to wait for one CTA more than the grid, so nothing completes it; its bounded
