@@ -183,24 +183,30 @@ __global__ void k_cost_init(LaunchSet ls) {
 
 // ---------------------------------------------------------------- per-edge records and slot rows
 
-// Both accumulation kernels first turn each edge of the chunk into a record of AT
-// values in shared memory (one row per edge, an odd number of 4-byte words apart so
-// that the edge-per-thread stores do not collide in a bank), then reduce the records
-// of each camera slot into that slot's partial row.  A record starts with
-// Y[k * M + a] (k < DC camera coordinates, a < M rows), followed by the DC-vector g:
-// the slot row is the packed upper triangle of sum_e Y_e^T Y_e (TC entries), then
-// sum_e g_e (DC entries), then zero padding up to NPA.
+// Both accumulation kernels first turn each edge of the chunk into records in shared
+// memory, then reduce the records of each camera slot into that slot's partial row.
+// Per edge: Y[k * M + a] (k < DC camera coordinates, a < M rows; type YT) and, in a
+// second array of AT values, the DC-vector g followed by kernel-specific terms.  Rows
+// are an odd number of 4-byte words apart (8-byte values: an odd number of values) so
+// that the edge-per-thread stores do not collide in a bank.  The slot row is the packed
+// upper triangle of sum_e Y_e^T Y_e (TC entries), then sum_e g_e (DC entries), then
+// zero padding up to NPA.
 template <int N>
 struct OddStride {
   static constexpr int value = N | 1;
 };
+template <class T, int N>
+struct OddRow {   // row length in values, N rounded up so the row spans an odd count of banks
+  static constexpr int value = sizeof(T) == 2 ? ((N / 2) % 2 == 1 ? N : N + 2) : (N | 1);
+  static_assert(sizeof(T) != 2 || N % 2 == 0, "two-byte rows hold whole words");
+};
 
 // One warp per slot (slots handed out by a shared counter, so long slots do not hold
 // up a fixed set of warps); lane l owns outputs l, l + 32, ... of the row.  All lanes
-// read the same edge's record at a time (broadcasts or distinct banks).  Each output
+// read the same edge's records at a time (broadcasts or distinct banks).  Each output
 // is summed over the slot's edges in slot order: acc += (sum_a Y[i][a] Y[j][a]).
-template <class Mo, class AT, int RS>
-__device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, const AT* rec,
+template <class Mo, class YT, class AT, int RSY, int RSG>
+__device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, const YT* Y, const AT* G,
                                           const uint16_t* srt, AT* part, int* next) {
   using Dm = Dims<Mo>;
   constexpr int M = Mo::M, DC = Mo::DC, TC = Dm::TC, NPA = Dm::NPA;
@@ -212,7 +218,7 @@ __device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, 
   for (int u = 0; u < OPL; ++u) {
     const int o = lane + 32 * u;
     kind[u] = o < TC ? 0 : (o < TC + DC ? 1 : 2);
-    oi[u] = o < TC ? tri_row<DC>(o) * M : (o < TC + DC ? M * DC + (o - TC) : 0);
+    oi[u] = o < TC ? tri_row<DC>(o) * M : (o < TC + DC ? o - TC : 0);
     oj[u] = o < TC ? tri_col<DC>(o) * M : 0;
   }
   for (;;) {
@@ -225,16 +231,18 @@ __device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, 
 #pragma unroll
     for (int u = 0; u < OPL; ++u) acc[u] = (AT)0;
     for (int q = qa; q < qb; ++q) {
-      const AT* r = rec + (size_t)srt[q] * RS;
+      const int e = srt[q];
+      const YT* y = Y + (size_t)e * RSY;
+      const AT* g = G + (size_t)e * RSG;
 #pragma unroll
       for (int u = 0; u < OPL; ++u) {
         if (kind[u] == 0) {
-          AT s = r[oi[u]] * r[oj[u]];
+          AT s = (AT)ldj(y + oi[u]) * (AT)ldj(y + oj[u]);
 #pragma unroll
-          for (int a = 1; a < M; ++a) s += r[oi[u] + a] * r[oj[u] + a];
+          for (int a = 1; a < M; ++a) s += (AT)ldj(y + oi[u] + a) * (AT)ldj(y + oj[u] + a);
           acc[u] += s;
         } else if (kind[u] == 1) {
-          acc[u] += r[oi[u]];
+          acc[u] += g[oi[u]];
         }
       }
     }
@@ -247,13 +255,15 @@ __device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, 
 
 // ---------------------------------------------------------------- linearisation
 
-// Record layout of the linearisation: Y = the stored (rounded) camera rows, g = Jc^T r
-// from the unrounded rows, then the point terms: packed Jp^T Jp of the stored rows (6)
-// and Jp^T r from the unrounded rows (3).
-template <class Mo>
+// Records of the linearisation: Y = the stored camera rows in the storage type (exact:
+// they are the rounded values), and in AT g = Jc^T r from the unrounded rows, then the
+// point terms: packed Jp^T Jp of the stored rows (6) and Jp^T r from the unrounded rows
+// (3).  BF16 rows keep the records at 112 bytes per edge (three CTAs per SM).
+template <class Mo, class JT>
 struct LinRec {
-  static constexpr int G = Mo::M * Mo::DC, H = G + Mo::DC, B = H + 6;
-  static constexpr int RS = OddStride<B + 3>::value;
+  static constexpr int RSY = OddRow<JT, Mo::M * Mo::DC>::value;
+  static constexpr int G = 0, H = Mo::DC, B = H + 6;
+  static constexpr int RSG = OddStride<B + 3>::value;
 };
 
 // One CTA per chunk.  Writes the chunk's Jacobian rows, the undamped point blocks
@@ -264,15 +274,17 @@ template <class Mo, class JT>
 __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  using R = LinRec<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, NJU = Dm::NJU, RS = R::RS;
+  using R = LinRec<Mo, JT>;
+  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, NJU = Dm::NJU;
+  constexpr int RSY = R::RSY, RSG = R::RSG;
   GPO_BIND(ch, kl)
   if (!d.sc->active || (!force && !d.sc->need_lin)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next_slot;
   const int CH = d.ch_max;
-  AT* rec = reinterpret_cast<AT*>(smem);                      // [CH][RS]
-  uint16_t* srt = reinterpret_cast<uint16_t*>(rec + (size_t)RS * CH);   // [CH]
+  AT* rec = reinterpret_cast<AT*>(smem);                       // [CH][RSG]
+  JT* yrec = reinterpret_cast<JT*>(rec + (size_t)RSG * CH);     // [CH][RSY]
+  uint16_t* srt = reinterpret_cast<uint16_t*>(yrec + (size_t)RSY * CH);   // [CH]
   const ChunkRange cr = chunk_range(d, kl);
   JT* Jg = reinterpret_cast<JT*>(d.J);
   if (threadIdx.x == 0) next_slot = 0;
@@ -313,11 +325,12 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     for (int k = NJU; k < NJ; ++k) row[k] = cvj((AT)0, (const JT*)nullptr);
     store_row_t<NJ>(Jg, (size_t)e, row);
     srt[i] = d.ch_sorted[e];
-    AT* re = rec + (size_t)i * RS;
+    AT* re = rec + (size_t)i * RSG;
+    JT* ye = yrec + (size_t)i * RSY;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
 #pragma unroll
-      for (int a = 0; a < M; ++a) re[k * M + a] = ldj(&row[a * DC + k]);
+      for (int a = 0; a < M; ++a) ye[k * M + a] = row[a * DC + k];
       AT s = Jc[0][k] * rw[0];
 #pragma unroll
       for (int a = 1; a < M; ++a) s += Jc[a][k] * rw[a];
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     const int a0 = d.pt_off[pj] - cr.e0, b0 = d.pt_off[pj + 1] - cr.e0;
     AT h[6] = {0, 0, 0, 0, 0, 0}, bb[3] = {0, 0, 0};
     for (int i = a0; i < b0; ++i) {
-      const AT* re = rec + (size_t)i * RS;
+      const AT* re = rec + (size_t)i * RSG;
 #pragma unroll
       for (int k = 0; k < 6; ++k) h[k] += re[R::H + k];
 #pragma unroll
@@ -373,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
   }
 
   // camera slots
-  slot_rows<Mo, AT, RS>(d, cr, rec, srt, reinterpret_cast<AT*>(d.partA), &next_slot);
+  slot_rows<Mo, JT, AT, RSY, RSG>(d, cr, yrec, rec, srt, reinterpret_cast<AT*>(d.partA), &next_slot);
 }
 
 // ---------------------------------------------------------------- Schur preparation
@@ -408,10 +421,10 @@ __device__ __forceinline__ void psd_cholesky(const AT (&A)[M][M], AT (&L)[M][M])
 
 // Record layout of the Schur preparation: Y = K = L^T Jc, where L L^T = Jp H_pp^-1 Jp^T,
 // so that sum_e K^T K = sum_e W_e H_pp^-1 W_e^T; g = Jc^T Jp H_pp^-1 b_p.
-template <class Mo>
+template <class Mo, class AT>
 struct SchurRec {
-  static constexpr int G = Mo::M * Mo::DC;
-  static constexpr int RS = OddStride<G + Mo::DC>::value;
+  static constexpr int RSY = OddRow<AT, Mo::M * Mo::DC>::value;
+  static constexpr int RSG = OddStride<Mo::DC>::value;
 };
 
 // One CTA per chunk: damped point inverses H_pp^-1 (and the point records of the Schur
@@ -421,16 +434,17 @@ template <class Mo, class JT>
 __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  using R = SchurRec<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, RS = R::RS;
+  using R = SchurRec<Mo, AT>;
+  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dm::JP0, RSY = R::RSY, RSG = R::RSG;
   GPO_BIND(ch, kl)
   if (!d.sc->active) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next_slot;
   const int CH = d.ch_max;
-  AT* rec = reinterpret_cast<AT*>(smem);                   // [CH][RS]
-  AT* pv = rec + (size_t)RS * CH;                          // [CH][9]: H_pp^-1 (6), H_pp^-1 b_p (3)
-  uint16_t* srt = reinterpret_cast<uint16_t*>(pv + 9 * (size_t)CH);   // [CH]
+  AT* rec = reinterpret_cast<AT*>(smem);                   // [CH][RSY]: K
+  AT* grec = rec + (size_t)RSY * CH;                       // [CH][RSG]: g
+  AT* pv = grec + (size_t)RSG * CH;                        // [np_max][9]: H_pp^-1 (6), H_pp^-1 b_p (3)
+  uint16_t* srt = reinterpret_cast<uint16_t*>(pv + 9 * (size_t)ls.np_max);   // [CH]
   const ChunkRange cr = chunk_range(d, kl);
   const JT* Jg = reinterpret_cast<const JT*>(d.J);
   const Scalars* sc = d.sc;
@@ -489,7 +503,8 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
     }
     AT L[M][M];
     psd_cholesky<M>(A, L);
-    AT* re = rec + (size_t)i * RS;
+    AT* re = rec + (size_t)i * RSY;
+    AT* ge = grec + (size_t)i * RSG;
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
 #pragma unroll
@@ -502,12 +517,12 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
       AT s = row[k] * qe[0];
 #pragma unroll
       for (int a = 1; a < M; ++a) s += row[a * DC + k] * qe[a];
-      re[R::G + k] = s;
+      ge[k] = s;
     }
   }
   __syncthreads();
 
-  slot_rows<Mo, AT, RS>(d, cr, rec, srt, reinterpret_cast<AT*>(d.partB), &next_slot);
+  slot_rows<Mo, AT, AT, RSY, RSG>(d, cr, rec, grec, srt, reinterpret_cast<AT*>(d.partB), &next_slot);
 }
 
 // ---------------------------------------------------------------- camera blocks + PCG start
@@ -1297,8 +1312,18 @@ struct Launch {
   using Dm = Dims<Mo>;
   static size_t sJ(Prec pr) { return pr == Prec::F64 ? 8 : (pr == Prec::F32 ? 4 : 2); }
   static size_t sA(Prec pr) { return pr == Prec::F64 ? 8 : 4; }
-  static size_t lin_smem(Prec pr, int ch) { return (LinRec<Mo>::RS * sA(pr) + 2) * (size_t)ch; }
-  static size_t schur_smem(Prec pr, int ch) { return ((SchurRec<Mo>::RS + 9) * sA(pr) + 2) * (size_t)ch; }
+  static size_t lin_rsy(Prec pr) {
+    return pr == Prec::F64 ? LinRec<Mo, double>::RSY * 8
+                           : (pr == Prec::F32 ? LinRec<Mo, float>::RSY * 4 : LinRec<Mo, __nv_bfloat16>::RSY * 2);
+  }
+  static size_t lin_smem(Prec pr, int ch) {
+    return (LinRec<Mo, float>::RSG * sA(pr) + lin_rsy(pr) + 2) * (size_t)ch;
+  }
+  // np = most points of a chunk (the point records); np = ch bounds any chunk
+  static size_t schur_smem(Prec pr, int ch, int np) {
+    const size_t rsy = pr == Prec::F64 ? SchurRec<Mo, double>::RSY : SchurRec<Mo, float>::RSY;
+    return ((rsy + SchurRec<Mo, float>::RSG) * sA(pr) + 2) * (size_t)ch + 9 * sA(pr) * (size_t)np;
+  }
   static size_t spmv_smem(Prec pr, const LaunchSet& ls) {
     return sA(pr) * ((Dm::VW + 3) * (size_t)(ls.ch_max + 1) + Mo::DC * (size_t)ls.ns_max + 6 * (size_t)ls.np_max) +
            4 * (size_t)(ls.np_max + 2 * ls.ns_max + 2);
@@ -1308,7 +1333,7 @@ struct Launch {
     // largest chunk whose linearisation tile fits the 227 KB opt-in shared memory
     const size_t limit = 227 * 1024;
     int ch = 64;
-    while (lin_smem(pr, ch * 2) <= limit && schur_smem(pr, ch * 2) <= limit) ch *= 2;
+    while (lin_smem(pr, ch * 2) <= limit && schur_smem(pr, ch * 2, ch * 2) <= limit) ch *= 2;
     return ch;
   }
 
@@ -1341,7 +1366,7 @@ struct Launch {
   }
   template <class JT>
   static void schur_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-    const size_t sm = schur_smem(pr, ls.ch_max);
+    const size_t sm = schur_smem(pr, ls.ch_max, ls.np_max);
     set_smem(reinterpret_cast<const void*>(k_schur_prepare<Mo, JT>), sm);
     launch_pdl(k_schur_prepare<Mo, JT>, ls.n_ch, kThreads, sm, st, ls);
   }
