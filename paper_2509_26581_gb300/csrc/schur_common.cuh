@@ -318,6 +318,17 @@ __device__ __forceinline__ void load_rb(const double* __restrict__ src, double* 
 }
 
 // Huber value and sqrt of the first-order weight of a whitened squared norm s.
+// IRLS weight sqrt(rho'(s)) = sqrt(delta / sqrt(s)) for s > delta^2 (1 inside), in the
+// accumulation type: FP32 for the mixed forms (the Jacobian it scales is FP32), FP64 else.
+template <class AT>
+__device__ __forceinline__ double huber_weight(double s, double delta) {
+  if (!(delta > 0.0 && s > delta * delta)) return 1.0;
+  if constexpr (std::is_same<AT, float>::value) {
+    return (double)sqrtf((float)delta * rsqrtf((float)s));
+  } else {
+    return sqrt(delta / sqrt(s));
+  }
+}
 __device__ __forceinline__ void huber(double s, double delta, double& rho, double& sw) {
   if (delta > 0.0 && s > delta * delta) {
     const double sq = sqrt(s);
@@ -402,7 +413,8 @@ struct ModelBA {
     Geom g;
     geom(rb, X, g);
     residual(d, e, g, r);
-    huber(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e), rho, sw);
+    rho = 0.0;
+    sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e));
     const AT f = (AT)rb[12], k1 = (AT)rb[13], k2 = (AT)rb[14];
     const AT p0 = (AT)g.p[0], p1 = (AT)g.p[1], r2 = (AT)g.r2, dd = (AT)g.d, iz = (AT)g.iz;
     const AT c2 = (AT)2 * k1 + (AT)4 * k2 * r2;
@@ -537,7 +549,8 @@ struct ModelStereo {
     Geom g;
     geom(d, rb, X, g);
     residual(d, e, g, r);
-    huber(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], __ldg(d.e_delta + e), rho, sw);
+    rho = 0.0;
+    sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], __ldg(d.e_delta + e));
     const AT fx = (AT)d.camk[0], fy = (AT)d.camk[1], b = (AT)d.camk[4];
     const AT iz = (AT)g.iz, x = (AT)g.Xc[0], y = (AT)g.Xc[1];
     AT D[3][3];
