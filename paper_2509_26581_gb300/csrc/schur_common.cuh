@@ -317,9 +317,9 @@ __device__ __forceinline__ void load_rb(const double* __restrict__ src, double* 
   }
 }
 
-// Huber value and sqrt of the first-order weight of a whitened squared norm s.
-// IRLS weight sqrt(rho'(s)) = sqrt(delta / sqrt(s)) for s > delta^2 (1 inside), in the
-// accumulation type: FP32 for the mixed forms (the Jacobian it scales is FP32), FP64 else.
+// IRLS weight sqrt(rho'(s)) = sqrt(delta / sqrt(s)) of a whitened squared norm s for
+// s > delta^2 (1 inside), in the accumulation type: FP32 for the mixed forms (the
+// Jacobian it scales is FP32), FP64 otherwise.
 template <class AT>
 __device__ __forceinline__ double huber_weight(double s, double delta) {
   if (!(delta > 0.0 && s > delta * delta)) return 1.0;
@@ -329,15 +329,10 @@ __device__ __forceinline__ double huber_weight(double s, double delta) {
     return sqrt(delta / sqrt(s));
   }
 }
-__device__ __forceinline__ void huber(double s, double delta, double& rho, double& sw) {
-  if (delta > 0.0 && s > delta * delta) {
-    const double sq = sqrt(s);
-    rho = 2.0 * delta * sq - delta * delta;
-    sw = sqrt(delta / sq);
-  } else {
-    rho = s;
-    sw = 1.0;
-  }
+// Huber value rho(s) (FP64): s inside delta^2, 2 delta sqrt(s) - delta^2 outside.
+__device__ __forceinline__ double huber_rho(double s, double delta) {
+  if (delta > 0.0 && s > delta * delta) return 2.0 * delta * sqrt(s) - delta * delta;
+  return s;
 }
 
 // ---------------------------------------------------------------- BA model
@@ -400,9 +395,7 @@ struct ModelBA {
     geom(rb, X, g);
     double r[M];
     residual(d, e, g, r);
-    double rho, sw;
-    huber(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e), rho, sw);
-    return 0.5 * rho;
+    return 0.5 * huber_rho(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e));
   }
 
   // Whitened residual, Huber, and the whitened, sqrt(rho')-scaled Jacobian rows on the
@@ -536,9 +529,7 @@ struct ModelStereo {
     geom(d, rb, X, g);
     double r[M];
     residual(d, e, g, r);
-    double rho, sw;
-    huber(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], __ldg(d.e_delta + e), rho, sw);
-    return 0.5 * rho;
+    return 0.5 * huber_rho(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], __ldg(d.e_delta + e));
   }
 
   // dr/dX_c rows: [fx/Z, 0, -fx X/Z^2], [0, fy/Z, -fy Y/Z^2], [fx/Z, 0, -fx (X-b)/Z^2];
