@@ -370,6 +370,23 @@ def extra_served(stream, rate: float = 2000.0, duration: float = 1.0, pool: int 
                      "precision solved alone")
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """The maximum of x over the ranks of the process group (x itself without a group):
+    the replicas' timed regions end when the slowest one does."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, steps: int, seconds: float) -> float:
+    """Whole-job LM iterations per second: each of the `world` replicas runs `steps`."""
+    return world * steps / seconds
+
+
 def run_vi(args, dev, stream, world: int) -> dict:
     """The global visual-inertial workload as the measured loop (--workload vi_global;
     used for its own launch lists and profiles): K LM iterations after W warm-up ones."""
@@ -458,11 +475,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     ms = ev0.elapsed_time(ev1)
     launches = int(sum(v["launches"] for v in g.profile().values()))
     hist = g.history()
-    if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     # per-kernel times: the same iterations again from the same state (deterministic),
     # every launch bracketed by CUDA events on the stream (direct launches, the camera
     # half and the PCG update timed apart)
@@ -490,11 +503,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         g.get_state(p0, p.n_pts, 3)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([e2e_s], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     if rank != 0:
         return None
     sp = prof["spmv"]
@@ -506,7 +515,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     state_bytes = (p.n_cams * 9 + p.n_pts * 3) * 8
     pcg_iters = [h["pcg_iters"] for h in hist]
     line = dict(
-        metric=METRIC, value=world * args.steps / (ms / 1e3), unit="LM iter/s", n_gpus=world,
+        metric=METRIC, value=replica_rate(world, args.steps, ms / 1e3), unit="LM iter/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype={"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
         data="synthetic",
@@ -515,7 +524,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                     schedule=g.knobs,
                     l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
                     parallelism=f"replicas x{world}"),
-        e2e=None if args.no_e2e else dict(value=world * args.steps / e2e_s, unit="LM iter/s",
+        e2e=None if args.no_e2e else dict(value=replica_rate(world, args.steps, e2e_s), unit="LM iter/s",
                                           h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes),
         gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
