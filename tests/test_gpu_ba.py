@@ -246,15 +246,16 @@ def test_sampled_edges_at_medium_size(gpo):
     assert rep.final_cost < rep.initial_cost and rep.accepted >= 1
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16"])
-def test_schur_product_variants_bitwise(gpo, prec):
+@pytest.mark.parametrize("prec,chunk", [("fp64", 512), ("bf16", 512), ("fp32", 256), ("bf16", 1024)])
+def test_schur_product_variants_bitwise(gpo, prec, chunk):
     """The staged (bulk-copy pipeline), classic and pipelined persistent Schur-product
-    kernels compute the same sums in the same order: the solves agree bit for bit."""
+    kernels compute the same sums in the same order: the solves agree bit for bit (one,
+    two and four edges per thread)."""
     p = synth.ba_path(3, 40, 6000, "pareto")
     out = []
     for variant in (1, 2, 3):
         g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec,
-                                 spmv_variant=variant)
+                                 spmv_variant=variant, chunk_edges=chunk)
         rep = g.optimize(4)
         out.append((rep.final_cost, rep.pcg_iters_total, g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)))
     for o in out[1:]:
