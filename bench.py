@@ -79,36 +79,51 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
+        self.window = (0.0, float("inf"))
 
     def start(self):
+        """Start sampling; returns once the first sample has arrived (at most 3 s), so
+        that the samples cover the whole timed region that begins on return."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        t0 = time.monotonic()
+        while not self.lines and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.window = (time.monotonic(), float("inf"))
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def stop(self) -> dict:
+        """Stop sampling; the summary covers the samples taken between start() returning
+        and this call (all samples if none fell inside)."""
         if self.proc is None:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.window = (self.window[0], time.monotonic())
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        lo, hi = self.window
+        inside = [ln for t, ln in self.lines if lo <= t <= hi]
+        used = inside if inside else [ln for _, ln in self.lines]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in used:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -122,7 +137,8 @@ class ClockSampler:
                     reasons.add(n)
         sm.sort()
         return dict(sm_mhz=sm[len(sm) // 2] if sm else None, sm_max_mhz=max(mx) if mx else None,
-                    reasons=sorted(reasons), samples=len(sm))
+                    reasons=sorted(reasons), samples=len(sm), samples_in_window=len(inside),
+                    interval_ms=self.interval_ms)
 
 
 def load_peaks() -> tuple[float, str]:
@@ -138,7 +154,7 @@ def load_peaks() -> tuple[float, str]:
 # was taken from (keyed by a hash of them): changed kernels report null.
 # DRAM bytes (read + write) per Schur-product launch from an ncu capture, keyed by
 # (precision, kernel, hash of the kernel sources): stale once the sources change.
-MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "c42d2a9fe2bf"): 179.2e6}
+MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "9beb5db0b9fc"): 179.2e6}
 SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
