@@ -141,6 +141,66 @@ class ClockSampler:
                     interval_ms=self.interval_ms)
 
 
+# HBM3e nominal bandwidth of the part (8 stacks at 3,996 MHz), reported beside the
+# measured copy rate.
+NOMINAL_HBM_GBS = 7900.0
+
+# FP64 thread instructions per edge (2 x DFMA + DADD + DMUL = FP64 flops) of one
+# launch of the BA linearisation and cost kernels, from an ncu capture of the medium
+# workload (profiles/k_linearize_k_cost_fp64_ba_medium.md); keyed by a hash of the
+# sources they were counted from, so changed kernels report null.
+FP64_SOURCES = ("schur_common.cuh", "schur_kernels.cuh")
+FP64_FLOPS_PER_EDGE = {
+    ("k_linearize", "bf16", "c17ffedc6d7e"): 49.0,
+    ("k_linearize", "fp64", "c17ffedc6d7e"): 449.29,
+    # one kernel for every precision (FP64 geometry and cost)
+    ("k_cost", "bf16", "c17ffedc6d7e"): 65.50,
+    ("k_cost", "fp32", "c17ffedc6d7e"): 65.50,
+    ("k_cost", "fp64", "c17ffedc6d7e"): 65.50,
+}
+
+
+def fp64_peak(stream) -> float:
+    """Measured FP64 FMA throughput of this GPU (TFLOP/s): gpo_fp64_fma_probe, eight
+    CTAs of 256 threads per SM, the median of ten launches timed with CUDA events."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo
+    n_ctas = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    iters = 400
+    out = torch.empty(n_ctas * 256, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        gpo.fp64_fma_probe(stream.cuda_stream, n_ctas, iters, out)
+    times = []
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gpo.fp64_fma_probe(stream.cuda_stream, n_ctas, iters, out)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times.sort()
+    ms = times[len(times) // 2]
+    flops = 2.0 * n_ctas * 256 * iters * 32
+    return flops / (ms * 1e-3) / 1e12
+
+
+def fp64_rooflines(prof: dict, n_edges: int, precision: str, peak_tflops: float) -> dict:
+    """FP64-pipe rooflines of the linearisation and cost kernels from their per-launch
+    times in a profiled pass and the counted FP64 flops per edge (null when the
+    counts are not for the current sources)."""
+    h = kernel_source_hash(FP64_SOURCES)
+    out = dict(peak_tflops=peak_tflops, peak_source="measured (gpo_fp64_fma_probe)")
+    for key, kern in (("linearize", "k_linearize"), ("cost", "k_cost")):
+        k = prof.get(key, {})
+        ms = k["active_ms"] / k["active"] if k.get("active") else None
+        fpe = FP64_FLOPS_PER_EDGE.get((kern, precision, h))
+        ach = fpe * n_edges / (ms * 1e-3) / 1e12 if (fpe and ms) else None
+        out[key] = dict(kernel=kern, avg_ms=ms, fp64_flops_per_edge=fpe, achieved_tflops=ach,
+                        frac=ach / peak_tflops if ach else None)
+    return out
+
+
 def load_peaks() -> tuple[float, str]:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -159,10 +219,10 @@ SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha1()
-    for name in KERNEL_SOURCES:
+    for name in sources:
         with open(os.path.join(ROOT, "paper_2509_26581_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -213,10 +273,12 @@ def spmv_algorithmic_bytes_vi(E: int, P: int, precision: str) -> float:
     return E * (27 * sJ + 4) + P * 6 * sA
 
 
-def extra_mixed_vs_fp64(args, p, params, dev, stream, main_cost: float) -> dict:
+def extra_mixed_vs_fp64(args, p, params, dev, stream, main_cost: float, fp64_peak_tflops: float) -> dict:
     """The FP64 GPU path on the same workload and schedule (warm-up, then the timed
     steps, each call starting from initial_damping): final-cost difference of the
-    benchmarked precision against it, and the FP64 rate."""
+    benchmarked precision against it, the FP64 rate, and the FP64-pipe rooflines of
+    the FP64 build's linearisation and cost kernels (a profiled pass of two more
+    iterations)."""
     import torch
 
     from paper_2509_26581_gb300 import gpo
@@ -228,10 +290,13 @@ def extra_mixed_vs_fp64(args, p, params, dev, stream, main_cost: float) -> dict:
     rep = g.optimize(args.steps, params)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    g.set_profiling(True)
+    g.optimize(2, params)
+    roof = fp64_rooflines(g.profile(), p.n_edges, "fp64", fp64_peak_tflops)
     g.close()
     return dict(fp64_final_cost=rep.final_cost, final_cost=main_cost, precision=args.precision,
                 rel_diff=abs(main_cost - rep.final_cost) / rep.final_cost,
-                fp64_lm_iter_per_s=args.steps / dt)
+                fp64_lm_iter_per_s=args.steps / dt, fp64_build_rooflines=roof)
 
 
 def extra_vi(dev, stream, iters: int = 10) -> dict:
@@ -332,7 +397,7 @@ def extra_large(dev, stream, iters: int = 3) -> dict:
         prof = g.profile()
         sp = prof["spmv"]
         spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
-        acc_ms = (prof["linearize"]["active_ms"] + prof["schur_prepare"]["active_ms"]) / max(1, prof["linearize"]["active"])
+        acc_ms = sum(prof[k]["active_ms"] / max(1, prof[k]["active"]) for k in ("linearize", "schur_prepare"))
         alg_s = spmv_algorithmic_bytes(p.n_edges, p.n_pts, prec)
         alg_a = accumulation_bytes(p.n_edges, p.n_pts, info["slots"], prec)
         out[prec] = dict(lm_iter_per_s=iters / (ms / 1e3), final_cost=rep.final_cost, pcg_iters=rep.pcg_iters_total,
@@ -547,16 +612,19 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                       traffic=spmv_traffic(args.precision, kern) if args.seed == 1
                       and g.knobs["chunk_edges"] in (0, 512) else None,
                       kernel=KERNEL_LABEL[kern], peak_source=peak_kind,
-                      algorithmic_bytes=alg, avg_ms=spmv_ms),
+                      algorithmic_bytes=alg, avg_ms=spmv_ms,
+                      peak_nominal=NOMINAL_HBM_GBS, frac_nominal=achieved / NOMINAL_HBM_GBS),
         clocks=clk,
         pcg_iters_per_step=pcg_iters,
         final_cost=rep.final_cost,
         kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items()},
         footprint_bytes=g.footprint(),
+        fp64=fp64_rooflines(prof, p.n_edges, args.precision, fp64_peak(stream)),
     )
     if not args.no_extras and world == 1:
         g.close()
-        line["mixed_vs_fp64"] = extra_mixed_vs_fp64(args, p, params, dev, stream, rep.final_cost)
+        line["mixed_vs_fp64"] = extra_mixed_vs_fp64(args, p, params, dev, stream, rep.final_cost,
+                                                    line["fp64"]["peak_tflops"])
         line["vi"] = extra_vi(dev, stream)
         line["served"] = extra_served(stream)
         line["large"] = extra_large(dev, stream)

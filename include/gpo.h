@@ -302,7 +302,8 @@ typedef struct {
   int64_t launches;           /* kernels launched since gpo_set_profiling (always counted) */
   int64_t timed_launches;     /* launches bracketed by CUDA events (profiling on) */
   int64_t active_launches;    /* timed launches that did work: a Schur-product launch after
-                                 its PCG solve stopped returns at once and is not active */
+                                 its PCG solve stopped returns at once, and so does the
+                                 linearisation after a rejected LM step; neither is active */
   double total_ms;            /* summed event time of the timed launches */
   double active_ms;           /* summed event time of the active launches */
 } gpo_kernel_profile;
@@ -401,6 +402,19 @@ gpo_status gpo_ba_cost_noalloc(int32_t device, void* cuda_stream, const double* 
                                const double* points, const int32_t* cam_idx,
                                const int32_t* pt_idx, const double* obs, int64_t n_edges,
                                double huber_delta, double* cost_out);
+
+/* ---------------------------------------------------------------------------
+ * FP64 throughput probe (measurement).  The linearisation and cost kernels evaluate
+ * the geometry, residuals and cost in FP64 (the state, retraction and cost are FP64 in
+ * every precision mode), so their roofline is the FP64 pipe, whose rate this measures.
+ *
+ * Launches n_ctas CTAs of 256 threads on cuda_stream (NULL = the legacy default
+ * stream); every thread runs iters x 32 FP64 fused multiply-adds in eight independent
+ * chains and writes one double to out[thread] (out: caller-owned device memory of
+ * n_ctas * 256 doubles).  One launch performs n_ctas * 256 * iters * 32 FMAs, i.e.
+ * twice that many FP64 flops; the caller times it on the stream.  The call does not
+ * wait.  Errors: GPO_ERR_ARG (n_ctas or iters <= 0, out NULL), GPO_ERR_CUDA. */
+gpo_status gpo_fp64_fma_probe(void* cuda_stream, int32_t n_ctas, int32_t iters, double* out);
 
 /* ---------------------------------------------------------------------------
  * Diagnostic entry points (used by the parity tests; same kernels as optimize).

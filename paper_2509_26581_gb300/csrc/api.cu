@@ -469,7 +469,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.add_raw(&d.y, (size_t)DB * C * sA); pl.add_raw(&d.xbest, (size_t)DB * C * sA);
   pl.add_raw(&d.p2, (size_t)DB * C * sA);
   pl.add(&d.cost_part, std::max(NCH, 1)); pl.add(&d.md_part, std::max(NCH, 1));
-  pl.add(&d.cblk_part, 2 * 4 * (size_t)d.ncblk);   // cam_apply runs four CTAs per camera block
+  pl.add(&d.cblk_part, 2 * 5 * (size_t)d.ncblk);   // four camera-half CTAs per camera block, then the update's
   pl.add(&d.hist, gpo::kMaxHistory);
   pl.add(&R.desc_d, 1);
   R.bytes = pl.total();
@@ -593,7 +593,8 @@ static void run(gpo_graph* g, int kind, F&& f) {
 
 // Resolves the recorded events (after a stream sync).  A Schur-product launch is
 // active when its PCG iteration ran (iteration index <= that LM iteration's PCG
-// count); later launches of the look-ahead group return at once.
+// count); later launches of the look-ahead group return at once.  A linearisation is
+// active when the LM iteration before it accepted its step.
 void gpo_host::prof_resolve(gpo_graph* g) {
   Profiler& p = g->prof;
   for (const auto& m : p.marks) {
@@ -604,6 +605,9 @@ void gpo_host::prof_resolve(gpo_graph* g) {
     bool act = true;
     if (m.kind == KK_SPMV && m.lm_iter >= 0 && m.lm_iter < (int)g->hist.size())
       act = m.pcg_k <= g->hist[m.lm_iter].pcg_products;
+    // the linearisation returns at once after a rejected step (the state is unchanged)
+    if (m.kind == KK_LINEARIZE && m.lm_iter >= 1 && m.lm_iter - 1 < (int)g->hist.size())
+      act = g->hist[m.lm_iter - 1].accepted != 0;
     if (act) {
       p.active[m.kind]++;
       p.active_ms[m.kind] += el;

@@ -719,8 +719,10 @@ struct ApplyShared {
   AT qx[Mo::kExtra ? kCamPerBlock : 1][Mo::DB];
 };
 // One unit of the camera half: CTA-part `part` of camera block cbl of the problem bound
-// in d (every thread calls; returns uniformly).
-template <class Mo, class AT>
+// in d (every thread calls; returns uniformly).  kFused: the unit stops after writing
+// its p^T y partial; alpha is formed after the fused kernel's grid barrier by every
+// CTA of the update (the same partials summed in the same order, so the same value).
+template <class Mo, class AT, bool kFused = false>
 __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int part, ApplyShared<Mo, AT>& S) {
   constexpr int DB = Mo::DB, DC = Mo::DC, TB = Dims<Mo>::TB;
   double* red = S.red;
@@ -827,6 +829,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     d.cblk_part[2 * me] = a;
     d.cblk_part[2 * me + 1] = 0.0;
   }
+  if constexpr (kFused) return;
   if (!last_cta(&sc->ticket, ctas)) return;
   double pAp, unused;
   sum_partials(d.cblk_part, ctas, pAp, unused);
@@ -856,47 +859,87 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   cam_apply_body<Mo, AT>(ls, d, cbl, part, S);
 }
 
+// The update's inputs that the camera half does not write (the fused kernel loads
+// them before its grid barrier): the camera's row of M, r, g and x.  (The direction p
+// and y = S p are the camera half's outputs.)
+template <class Mo, class AT>
+struct UpdateIn {
+  AT r0, g0, x0, mrow[Mo::DB];
+};
+template <class Mo, class AT>
+__device__ __forceinline__ void pcg_update_load(const DevBA& d, int cbl, UpdateIn<Mo, AT>& in) {
+  constexpr int DB = Mo::DB, TB = Dims<Mo>::TB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = cbl * kCamPerBlock + warp;
+  in.r0 = in.g0 = in.x0 = (AT)0;
+#pragma unroll
+  for (int j = 0; j < DB; ++j) in.mrow[j] = (AT)0;
+  if (c < d.C && lane < DB) {
+    const AT* Mi = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * TB;
+    const size_t o = DB * (size_t)c + lane;
+    in.r0 = reinterpret_cast<const AT*>(d.r)[o];
+    in.g0 = reinterpret_cast<const AT*>(d.g)[o];
+    in.x0 = reinterpret_cast<const AT*>(d.x)[o];
+#pragma unroll
+    for (int j = 0; j < DB; ++j) in.mrow[j] = Mi[sym_idx(DB, lane, j)];
+  }
+}
+
 // One warp per camera: x += sigma alpha p, r -= alpha y, z = M r; the last CTA of
 // the problem reduces r^T z and |r|^2, applies the stopping rules (tolerance,
 // rejection ratio, iteration cap) and computes beta and the normalisation factor.
-template <class Mo, class AT>
-__device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, double (*red)[2]) {
-  constexpr int DB = Mo::DB, TB = Dims<Mo>::TB;
+// Its partials sit after the camera half's (which the fused form still reads here).
+// kFused: alpha = r^T z / p^T y is formed here from the camera half's partials (every
+// CTA the same value; camera block 0 records it, or stops a solve whose p^T y is not
+// positive, as the camera half's last CTA does in the separate launches).
+template <class Mo, class AT, bool kFused = false>
+__device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, double (*red)[2],
+                                const UpdateIn<Mo, AT>& in) {
+  constexpr int DB = Mo::DB;
   Scalars* sc = d.sc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = cbl * kCamPerBlock + warp;
-  // the camera's inputs that do not depend on the solve's scalars are loaded together
-  // with them (one round trip before the arithmetic instead of two)
   const bool mine = c < d.C && lane < DB;
-  AT r0 = (AT)0, y0 = (AT)0, g0 = (AT)0, mrow[DB];
-#pragma unroll
-  for (int j = 0; j < DB; ++j) mrow[j] = (AT)0;
-  if (mine) {
-    const AT* Mi = reinterpret_cast<const AT*>(d.Minv) + (size_t)c * TB;
-    r0 = reinterpret_cast<const AT*>(d.r)[DB * (size_t)c + lane];
-    y0 = reinterpret_cast<const AT*>(d.y)[DB * (size_t)c + lane];
-    g0 = reinterpret_cast<const AT*>(d.g)[DB * (size_t)c + lane];
-#pragma unroll
-    for (int j = 0; j < DB; ++j) mrow[j] = Mi[sym_idx(DB, lane, j)];
-  }
+  const AT y0 = mine ? reinterpret_cast<const AT*>(d.y)[DB * (size_t)c + lane] : (AT)0;
+  const AT p0 = mine ? reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2)[DB * (size_t)c + lane] : (AT)0;
   if (!sc->active || sc->pcg_done) return;
   // a restart iteration: y = S x at the current solution, and the residual becomes the
   // true one, g - S x (unit scale), with the direction restarted from z = M r
   const int restart = sc->restart;
+  double alpha_d = 0.0;
+  if constexpr (kFused) {
+    if (!restart) {
+      double pAp, unused;
+      sum_partials(d.cblk_part, d.ncblk * kApplySplit, pAp, unused);
+      const bool bad = !(pAp > 0.0) || !isfinite(pAp);
+      alpha_d = bad ? 0.0 : sc->rz / pAp;
+      __syncthreads();   // every thread has read sc->rz before block 0 may stop the solve
+      if (cbl == 0 && threadIdx.x == 0) {
+        sc->pAp = pAp;
+        sc->alpha = alpha_d;
+        if (bad) {
+          sc->pcg_done = 1;
+          atomicSub(ls.running, 1);
+        }
+      }
+      if (bad) return;
+    }
+  } else {
+    alpha_d = sc->alpha;
+  }
   AT rz_c = (AT)0, rr_c = (AT)0;   // per-warp partials in AT, accumulated across warps in FP64
   if (c < d.C) {   // warp-uniform
-    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
+    const AT alpha = (AT)alpha_d, sa = (AT)(sc->sigma * alpha_d), sn = (AT)sc->inv_n;
     AT* x = reinterpret_cast<AT*>(d.x) + DB * (size_t)c;
     AT* r = reinterpret_cast<AT*>(d.r) + DB * (size_t)c;
     AT* z = reinterpret_cast<AT*>(d.z) + DB * (size_t)c;
-    const AT* pv = reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
     AT ri = (AT)0;
     if (lane < DB) {
       if (restart) {
-        ri = g0 - y0;
+        ri = in.g0 - y0;
       } else {
-        x[lane] += sa * pv[lane];
-        ri = r0 * sn - alpha * y0;
+        x[lane] = in.x0 + sa * p0;
+        ri = in.r0 * sn - alpha * y0;
       }
       r[lane] = ri;
     }
@@ -904,7 +947,7 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
 #pragma unroll
     for (int j = 0; j < DB; ++j) {
       const AT rj = __shfl_sync(0xffffffffu, ri, j);
-      if (lane < DB) zi += mrow[j] * rj;
+      if (lane < DB) zi += in.mrow[j] * rj;
     }
     if (lane < DB) {
       z[lane] = zi;
@@ -922,15 +965,16 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
     red[warp][1] = (double)rr_c;
   }
   __syncthreads();
+  double* upart = d.cblk_part + 2 * kApplySplit * (size_t)d.ncblk;
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int w = 0; w < kCamPerBlock; ++w) { a += red[w][0]; b += red[w][1]; }
-    d.cblk_part[2 * cbl] = a;
-    d.cblk_part[2 * cbl + 1] = b;
+    upart[2 * cbl] = a;
+    upart[2 * cbl + 1] = b;
   }
   if (!last_cta(&sc->ticket, d.ncblk)) return;
   double rz, rr;
-  sum_partials(d.cblk_part, d.ncblk, rz, rr);
+  sum_partials(upart, d.ncblk, rz, rr);
   if (threadIdx.x == 0) {
     const double n = sqrt(rr);
     if (restart) sc->sigma = 1.0;            // r is now the true residual
@@ -974,7 +1018,9 @@ template <class Mo, class AT>
 __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) {
   __shared__ double red[kCamPerBlock][2];
   GPO_BIND(cb, cbl)
-  pcg_update_body<Mo, AT>(ls, d, cbl, red);
+  UpdateIn<Mo, AT> in;
+  pcg_update_load<Mo, AT>(d, cbl, in);
+  pcg_update_body<Mo, AT>(ls, d, cbl, red, in);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1015,11 +1061,13 @@ __device__ __forceinline__ bool grid_sync(int* count, int* gen, int ctas) {
 }
 
 // The camera half of the Schur product and the PCG update in one persistent launch
-// (the production path; profiling times the two separately): the CTAs first walk the
-// camera half's units (camera block, quarter) -- the last unit of a problem sets its
-// alpha -- meet at a grid barrier, then walk the update's camera blocks -- the last
-// block of a problem applies the stopping rules and sets beta.  The same bodies as
-// k_cam_apply and k_pcg_update: bit-identical results.  Launched only when the
+// (the production path; profiling times the two separately): each CTA runs one unit
+// of the camera half (camera block, quarter), loads its update block's inputs that the
+// camera half does not write, and meets the others at a grid barrier; then CTA b
+// updates camera block b, every update CTA forming alpha from the camera half's
+// partials itself (no ticket between the halves), and the last block of a problem
+// applies the stopping rules and sets beta.  The same bodies and sums as k_cam_apply
+// and k_pcg_update: bit-identical results.  Launched only when the
 // camera half's units fit one wave of resident CTAs (one unit per CTA; the grid is
 // then resident when the barrier waits); larger problems keep the two launches, whose
 // many concurrent CTAs hide the units' latency better than a persistent loop.
@@ -1043,19 +1091,25 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
     const int cb = u / kApplySplit, part = u % kApplySplit;
     const int q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
     bind(q);
-    cam_apply_body<Mo, AT>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], part, S);
+    cam_apply_body<Mo, AT, true>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], part, S);
     __syncthreads();
+  }
+  // the grid has one CTA per unit (n_cb * kApplySplit >= n_cb), so CTA b < n_cb updates
+  // camera block b; its inputs that the camera half does not write are loaded first
+  const int ucb = blockIdx.x;
+  int ucbl = 0;
+  UpdateIn<Mo, AT> in;
+  if (ucb < ls.n_cb) {
+    const int q = ls.nprob == 1 ? 0 : ls.cb_prob[ucb];
+    bind(q);
+    ucbl = ls.nprob == 1 ? ucb : ucb - ls.cb_base[q];
+    pcg_update_load<Mo, AT>(d, ucbl, in);
   }
   if (!grid_sync(ls.work + 2, ls.work + 3, G + ls.debug_wait)) {
     if (threadIdx.x == 0) atomicExch(ls.err, 1);
     return;
   }
-  for (int cb = blockIdx.x; cb < ls.n_cb; cb += G) {
-    const int q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
-    bind(q);
-    pcg_update_body<Mo, AT>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], red);
-    __syncthreads();
-  }
+  if (ucb < ls.n_cb) pcg_update_body<Mo, AT, true>(ls, d, ucbl, red, in);
 }
 
 // ---------------------------------------------------------------- back-substitution

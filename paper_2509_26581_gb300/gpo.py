@@ -118,6 +118,7 @@ _SIGS = {
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
     "gpo_debug_wait_timeout": (C.c_int, [_P]),
+    "gpo_fp64_fma_probe": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
 }
 
 
@@ -330,6 +331,13 @@ def optimize_batch(graphs: list, max_iters: int, params: gpo_lm_params | None = 
     st = lib.gpo_optimize_batch(arr, n, max_iters, None if params is None else C.byref(params), reps)
     _check(st, graphs[0].h)
     return list(reps)
+
+
+def fp64_fma_probe(stream, n_ctas: int, iters: int, out) -> None:
+    """gpo_fp64_fma_probe: queues the FP64 FMA throughput kernel on `stream` (a CUDA
+    stream handle or 0) writing n_ctas * 256 doubles to the device tensor `out`; one
+    launch performs n_ctas * 256 * iters * 32 FMAs."""
+    _check(lib.gpo_fp64_fma_probe(stream, n_ctas, iters, out.data_ptr()))
 
 
 class Server:
