@@ -566,22 +566,32 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     g.optimize(args.steps, params)
     prof = g.profile()
 
-    # end to end through the public API with host buffers: every step copies the
-    # state in from pinned host memory, runs one LM iteration and reads the state back
+    # end to end through the public API with host buffers: the timed LM trajectory
+    # again (from the same post-warm-up state and initial damping), one call per
+    # iteration as a caller stepping the solver makes it: copy the state in from pinned
+    # host memory, run one LM iteration (continuing the damping from the previous
+    # call's final lambda), read the state back and feed it to the next step
     g.set_profiling(False)
-    cams_h = torch.from_numpy(np.ascontiguousarray(g.get_state(c0, p.n_cams, 9))).pin_memory()
-    pts_h = torch.from_numpy(np.ascontiguousarray(g.get_state(p0, p.n_pts, 3))).pin_memory()
-    out_c = torch.empty_like(cams_h).pin_memory()
-    out_p = torch.empty_like(pts_h).pin_memory()
+    bufs = [(torch.from_numpy(np.ascontiguousarray(cams_w)).pin_memory(),
+             torch.from_numpy(np.ascontiguousarray(pts_w)).pin_memory())]
+    bufs.append((torch.empty_like(bufs[0][0]).pin_memory(), torch.empty_like(bufs[0][1]).pin_memory()))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     n_e2e = 0 if args.no_e2e else args.steps
-    for _ in range(n_e2e):
-        g.set_initial(c0, cams_h.numpy())
-        g.set_initial(p0, pts_h.numpy())
-        g.optimize(1, params)
-        g.get_state(c0, p.n_cams, 9)
-        g.get_state(p0, p.n_pts, 3)
+    step_params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
+    lam = step_params.initial_damping
+    e2e_pcg = []
+    for k in range(n_e2e):
+        cin, pin = bufs[k % 2]
+        cout, pout = bufs[(k + 1) % 2]
+        g.set_initial(c0, cin.numpy())
+        g.set_initial(p0, pin.numpy())
+        step_params.initial_damping = lam
+        r = g.optimize(1, step_params)
+        lam = r.final_lambda
+        e2e_pcg.append(r.pcg_iters_total)
+        g.get_state(c0, p.n_cams, 9, out=cout.numpy())
+        g.get_state(p0, p.n_pts, 3, out=pout.numpy())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist)
@@ -606,7 +616,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                     l2="inputs larger than L2 (Jacobians + observations exceed 129 MB)",
                     parallelism=f"replicas x{world}"),
         e2e=None if args.no_e2e else dict(value=replica_rate(world, args.steps, e2e_s), unit="LM iter/s",
-                                          h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes),
+                                          h2d_bytes_per_step=state_bytes, d2h_bytes_per_step=state_bytes,
+                                          pcg_iters_per_step=e2e_pcg),
         gpu_launches=launches,
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
                       traffic=spmv_traffic(args.precision, kern) if args.seed == 1

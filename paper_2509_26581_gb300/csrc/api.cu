@@ -182,7 +182,8 @@ struct Prepared {
       *ch_s0_d = nullptr, *slot_e0_d = nullptr, *slot_cam_d = nullptr, *cam_s_off_d = nullptr,
       *cam_s_list_d = nullptr, *slot_pos_d = nullptr, *slot_rec_d = nullptr, *xe_i_d = nullptr, *xe_j_d = nullptr,
       *xe_kind_d = nullptr, *xo_off_d = nullptr, *xk_off_d = nullptr, *xk_list_d = nullptr, *ch_prob_d = nullptr,
-      *cb_prob_d = nullptr, *pb_prob_d = nullptr, *base_d = nullptr, *running_d = nullptr;
+      *cb_prob_d = nullptr, *pb_prob_d = nullptr, *base_d = nullptr, *running_d = nullptr,
+      *old2new_d = nullptr;
   uint16_t *e_pos_d = nullptr, *e_slot_d = nullptr, *ch_sorted_d = nullptr;
   uint32_t* e_meta_d = nullptr;
   uint8_t *cam_fixed_d = nullptr, *pt_fixed_d = nullptr;
@@ -449,6 +450,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.up(&R.ch_prob_d, std::max(NCH, 1), R.zeros_ch); pl.up(&R.cb_prob_d, d.ncblk, R.zeros_cb);
   pl.up(&R.pb_prob_d, R.npb, R.zeros_pb);
   pl.up(&R.base_d, 1, R.zeros_small); pl.up(&R.running_d, 8, R.zeros_small);
+  pl.up(&R.old2new_d, std::max(P, 1), R.pt_old2new);   // point id -> sorted row (state copies)
   // device-only arrays
   pl.add(&d.xe_J, (size_t)std::max(NX, 1) * gpo::kXJ); pl.add(&d.xe_r, (size_t)std::max(NX, 1) * gpo::kXRows);
   pl.add_raw(&d.xe_H, (size_t)std::max(NX, 1) * DB * DB * sA);
@@ -555,6 +557,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   g->sorted_edge = std::move(R.sorted_edge);
   g->pt_new2old = std::move(R.pt_new2old);
   g->pt_old2new = std::move(R.pt_old2new);
+  g->pt_old2new_d = R.old2new_d;
   g->x_sorted = std::move(R.x_sorted);
   g->dev = d;
   g->finalized = true;
@@ -1162,16 +1165,12 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
     GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * w, state, n * w * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else {
-    // points live on the device in sorted order
-    int32_t* idx = nullptr;
+    // points live on the device in sorted order (the id -> row map is resident)
     double* tmp = nullptr;
-    GPO_CUDA(g, cudaMallocAsync(&idx, n * sizeof(int32_t), st));
     GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
-    GPO_CUDA(g, cudaMemcpyAsync(idx, g->pt_old2new.data() + loc, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     GPO_CUDA(g, cudaMemcpyAsync(tmp, state, n * 3 * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    k_scatter_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(g->dev.pt, tmp, idx, (int)n, 3);
-    GPO_CUDA(g, cudaFreeAsync(idx, st));
+    k_scatter_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(g->dev.pt, tmp, g->pt_old2new_d + loc, (int)n, 3);
     GPO_CUDA(g, cudaFreeAsync(tmp, st));
   }
   GPO_CUDA(g, cudaStreamSynchronize(st));
@@ -1197,15 +1196,11 @@ gpo_status gpo_get_state(gpo_graph* g, int64_t first, int64_t n, double* out, in
     GPO_CUDA(g, cudaMemcpyAsync(out, g->dev.cam + loc * w, n * w * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   } else {
-    int32_t* idx = nullptr;
     double* tmp = nullptr;
-    GPO_CUDA(g, cudaMallocAsync(&idx, n * sizeof(int32_t), st));
     GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
-    GPO_CUDA(g, cudaMemcpyAsync(idx, g->pt_old2new.data() + loc, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    k_gather_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(tmp, g->dev.pt, idx, (int)n, 3);
+    k_gather_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(tmp, g->dev.pt, g->pt_old2new_d + loc, (int)n, 3);
     GPO_CUDA(g, cudaMemcpyAsync(out, tmp, n * 3 * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    GPO_CUDA(g, cudaFreeAsync(idx, st));
     GPO_CUDA(g, cudaFreeAsync(tmp, st));
   }
   GPO_CUDA(g, cudaStreamSynchronize(st));

@@ -88,6 +88,7 @@ struct gpo_graph {
   std::vector<int64_t> sorted_edge;   // sorted position -> observation edge index
   std::vector<int32_t> x_sorted;      // sorted position -> camera-side edge index
   std::vector<int32_t> pt_new2old, pt_old2new;
+  const int32_t* pt_old2new_d = nullptr;   // device copy of pt_old2new (in the arena)
   std::vector<int32_t> h_ch_e0;
   size_t j_elems = 0;
 

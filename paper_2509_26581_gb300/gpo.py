@@ -230,8 +230,17 @@ class Graph:
             _check(lib.gpo_set_initial(self.h, first, a.shape[0], _ptr(a), 0), self.h)
 
     def get_state(self, first: int, n: int, width: int, out=None):
+        """Copies n states out: into `out` when given (a CUDA tensor: device copy; a CPU
+        tensor or a C-contiguous float64 numpy array of n x width: host copy, fastest
+        from pinned memory), else into a new numpy array."""
         if out is not None and hasattr(out, "data_ptr"):
-            _check(lib.gpo_get_state(self.h, first, n, C.c_void_p(out.data_ptr()), 1), self.h)
+            on_dev = 1 if getattr(out, "is_cuda", True) else 0
+            _check(lib.gpo_get_state(self.h, first, n, C.c_void_p(out.data_ptr()), on_dev), self.h)
+            return out
+        if out is not None:
+            if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != n * width:
+                raise ValueError("out must be a C-contiguous float64 array of n x width")
+            _check(lib.gpo_get_state(self.h, first, n, _ptr(out), 0), self.h)
             return out
         a = np.empty((n, width), dtype=np.float64)
         _check(lib.gpo_get_state(self.h, first, n, _ptr(a), 0), self.h)
