@@ -123,6 +123,12 @@ typedef struct {
                                  A tuning knob: all give bit-identical results. */
 } gpo_graph_desc;
 
+/* Linear solver of the LM step (gpo_lm_params.solver). */
+enum {
+  GPO_SOLVER_SCHUR = 0,   /* PCG on the camera Schur complement, points by back-substitution */
+  GPO_SOLVER_FULL = 1     /* PCG on the full damped system of cameras and points (Sec. IV-E) */
+};
+
 /* Levenberg-Marquardt and PCG options (Listing 5: LevenbergMarquardtOptions and
  * PCGSolver(max_it, tol, rejection_ratio)). */
 typedef struct {
@@ -148,6 +154,17 @@ typedef struct {
                                  (a restart discards the Krylov directions, which slows
                                  convergence); otherwise >= 4 (smaller values are
                                  raised to 4). */
+  int32_t solver;             /* GPO_SOLVER_SCHUR (default) or GPO_SOLVER_FULL: the paper's
+                                 block-Jacobi PCG on all vertices at once (camera blocks
+                                 (H_cc + lambda D_c)^-1 and point blocks (H_pp +
+                                 lambda D_p)^-1 as preconditioner, products from the
+                                 stored Jacobians, one pass over them per iteration).
+                                 An exact solve of either gives the same step; the
+                                 tolerance and iteration cap apply to the solved system's
+                                 residual.  The full form allocates seven [P][3] vectors
+                                 on its first use (counted by gpo_memory_footprint).
+                                 Graphs without cameras, and graphs solved together
+                                 (gpo_optimize_batch, a server), use the Schur form. */
 } gpo_lm_params;
 
 typedef struct {

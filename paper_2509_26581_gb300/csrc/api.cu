@@ -148,10 +148,13 @@ void gpo_host::drop_pcg_graph(gpo_graph* g) {
 
 void gpo_host::release_device(gpo_graph* g) {
   drop_pcg_graph(g);
-  if (g->arena) {
-    if (g->desc.alloc && g->desc.free) g->desc.free(g->arena, g->desc.alloc_ctx);
-    else cudaFree(g->arena);
+  for (void* b : {g->arena, g->full_buf}) {
+    if (!b) continue;
+    if (g->desc.alloc && g->desc.free) g->desc.free(b, g->desc.alloc_ctx);
+    else cudaFree(b);
   }
+  g->full_buf = nullptr;
+  g->full_bytes = 0;
   g->arena = nullptr;
   g->arena_bytes = 0;
   g->finalized = false;
@@ -639,6 +642,8 @@ void gpo_host::fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda,
   s.normalize = p.pcg_normalize < 0 ? (g->prec != Prec::F64 ? 1 : 0) : (p.pcg_normalize ? 1 : 0);
   s.restart_every = p.pcg_restart_every <= 0 ? 0 : std::max(4, p.pcg_restart_every);
   s.restart = 0;
+  s.full = (p.solver == GPO_SOLVER_FULL && g->dev.C > 0) ? 1 : 0;
+  g->pcg_full = s.full;
   s.sigma = 1.0;
   s.inv_n = 1.0;
   s.active = 1;
@@ -669,6 +674,12 @@ static void capture_pcg_group(gpo_graph* g, const gpo::LaunchSet& ls) {
   }
   int c[3] = {0, 0, 0};
   for (int i = 0; i < kPcgGroup; ++i) {
+    if (g->pcg_full) {   // full system: product, camera half, update over cameras and points
+      c[0] += g->ks->full_spmv(ls, g->prec, g->stream);
+      c[2] += g->ks->cam_apply(ls, g->prec, g->stream);
+      c[2] += g->ks->full_update(ls, g->prec, g->stream);
+      continue;
+    }
     c[0] += g->ks->pcg_spmv(ls, g->prec, g->stream);
     const int fused = g->ks->pcg_camera(ls, g->prec, g->stream);
     c[1] += fused;
@@ -684,6 +695,7 @@ static void capture_pcg_group(gpo_graph* g, const gpo::LaunchSet& ls) {
     g->pcg_graph_off = true;
   } else {
     g->pcg_ls = ls;
+    g->pcg_exec_full = g->pcg_full;
     for (int k = 0; k < 3; ++k) g->pcg_counts[k] = c[k];
   }
   if (graph) cudaGraphDestroy(graph);
@@ -703,9 +715,12 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
   while (launched < max_launch) {
     const int n = std::min(kGroup, max_launch - launched);
     const bool graph_ok = !g->prof.on && !g->pcg_graph_off && n == kGroup;
-    if (graph_ok && (!g->pcg_exec || std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) != 0) && launched > 0)
+    auto same = [&] {   // the captured group is of this launch set and solver
+      return g->pcg_exec && g->pcg_exec_full == g->pcg_full && std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) == 0;
+    };
+    if (graph_ok && !same() && launched > 0)
       capture_pcg_group(g, ls);   // after one direct group, so kernel attributes are set
-    if (graph_ok && g->pcg_exec && std::memcmp(&g->pcg_ls, &ls, sizeof(ls)) == 0) {
+    if (graph_ok && same()) {
       GPO_CUDA(g, cudaGraphLaunch(g->pcg_exec, g->stream));
       g->prof.launches[KK_SPMV] += g->pcg_counts[0];
       g->prof.launches[KK_PCG_CAMERA] += g->pcg_counts[1];
@@ -714,6 +729,12 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
     } else {
       for (int i = 0; i < n; ++i) {
         g->cur_pcg_k = launched + i + 1;
+        if (g->pcg_full) {
+          run(g, KK_SPMV, [&] { return g->ks->full_spmv(ls, g->prec, g->stream); });
+          run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
+          run(g, KK_PCG_UPDATE, [&] { return g->ks->full_update(ls, g->prec, g->stream); });
+          continue;
+        }
         run(g, KK_SPMV, [&] { return g->ks->pcg_spmv(ls, g->prec, g->stream); });
         if (g->prof.on) {   // timed separately: the camera half and the update
           run(g, KK_CAM_APPLY, [&] { return g->ks->cam_apply(ls, g->prec, g->stream); });
@@ -748,10 +769,43 @@ static gpo_status pcg_solve(gpo_graph* g, const gpo::LaunchSet& ls, int max_it) 
   return GPO_OK;
 }
 
+// The point rows of the full-system PCG: seven [P][3] vectors of the accumulation type
+// and the point blocks' partial sums, allocated on the first full-system solve (with
+// the graph's allocator) and published in the graph's device descriptor.
+static gpo_status ensure_full(gpo_graph* g) {
+  if (g->full_buf) return GPO_OK;
+  const size_t P = (size_t)g->dev.P, sA = at_size(g->prec);
+  const size_t vec = (3 * std::max<size_t>(P, 1) * sA + 255) & ~(size_t)255;
+  const size_t npb = std::max<size_t>((P + 255) / 256, 1);
+  const size_t bytes = 7 * vec + 2 * npb * sizeof(double);
+  void* b = nullptr;
+  if (g->desc.alloc && g->desc.free) {
+    b = g->desc.alloc(bytes, g->desc.alloc_ctx);
+    if (!b) return fail(g, GPO_ERR_OOM, "allocator hook returned NULL for %zu bytes", bytes);
+  } else if (cudaMalloc(&b, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(g, GPO_ERR_OOM, "cudaMalloc(%zu) failed for the full-system solver", bytes);
+  }
+  g->full_buf = b;
+  g->full_bytes = bytes;
+  char* c = static_cast<char*>(b);
+  void** v[7] = {&g->dev.xq, &g->dev.rq, &g->dev.zq, &g->dev.pq, &g->dev.pq2, &g->dev.yq, &g->dev.xqbest};
+  for (int i = 0; i < 7; ++i) *v[i] = c + i * vec;
+  g->dev.pt_part = reinterpret_cast<double*>(c + 7 * vec);
+  GPO_CUDA(g, cudaMemsetAsync(b, 0, bytes, g->stream));
+  GPO_CUDA(g, cudaMemcpyAsync(g->dev_desc, &g->dev, sizeof(DevBA), cudaMemcpyHostToDevice, g->stream));
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));   // the host copy of the descriptor stays valid
+  return GPO_OK;
+}
+
 gpo_status gpo_host::solve_system(gpo_graph* g, const gpo::LaunchSet& ls, int max_it, bool force_lin) {
+  if (g->pcg_full) {
+    if (gpo_status s = ensure_full(g); s != GPO_OK) return s;
+  }
   run(g, KK_LINEARIZE, [&] { return g->ks->linearize(ls, g->prec, force_lin, g->stream); });
   run(g, KK_SCHUR, [&] { return g->ks->schur_prepare(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaMemsetAsync(ls.running, 0, 6 * sizeof(int), g->stream));   // flags and work counters
+  if (g->pcg_full) run(g, KK_FULL_INIT, [&] { return g->ks->full_init(ls, g->prec, g->stream); });
   run(g, KK_CAM_FINALIZE, [&] { return g->ks->cam_finalize(ls, g->prec, g->stream); });
   GPO_CUDA(g, cudaGetLastError());
   gpo_status s = pcg_solve(g, ls, max_it);
@@ -866,6 +920,7 @@ gpo_status gpo_lm_params_default(gpo_lm_params* out) {
   out->pcg_rejection_ratio = 10.0;
   out->pcg_normalize = -1;
   out->pcg_restart_every = -1;
+  out->solver = GPO_SOLVER_SCHUR;
   return GPO_OK;
 }
 
@@ -1343,7 +1398,7 @@ gpo_status gpo_graph_plan(gpo_graph* g, size_t* bytes) {
 
 gpo_status gpo_memory_footprint(gpo_graph* g, size_t* bytes) {
   if (!g || !bytes) return GPO_ERR_ARG;
-  *bytes = g->arena_bytes;
+  *bytes = g->arena_bytes + g->full_bytes;
   return GPO_OK;
 }
 

@@ -249,7 +249,11 @@ gpo_status gpo_optimize_batch(gpo_graph* const* graphs, int32_t n, int32_t max_i
   gpo_status s = build_set(owner, gs, bs);
   if (s != GPO_OK) return s;
   std::vector<Scalars> sc(n);
-  for (int i = 0; i < n; ++i) fill_scalars(graphs[i], prm, prm.initial_damping, sc[i]);
+  for (int i = 0; i < n; ++i) {
+    fill_scalars(graphs[i], prm, prm.initial_damping, sc[i]);
+    sc[i].full = 0;   // shared launches run the Schur form
+    graphs[i]->pcg_full = 0;
+  }
   int max_it = 1;
   for (auto& x : sc) max_it = std::max(max_it, x.max_it);
   if ((s = put_scalars(owner, bs, sc)) == GPO_OK && (s = launch_initial_cost(owner, bs.ls)) == GPO_OK &&
@@ -407,7 +411,11 @@ gpo_status gpo_server_step(gpo_server* sv, int32_t* n_resident, int32_t* n_queue
     gpo_status s = build_set(owner, gs, bs);
     if (s != GPO_OK) return s;
     std::vector<Scalars> sc(adm.size());
-    for (size_t i = 0; i < adm.size(); ++i) fill_scalars(adm[i].g, adm[i].prm, adm[i].prm.initial_damping, sc[i]);
+    for (size_t i = 0; i < adm.size(); ++i) {
+      fill_scalars(adm[i].g, adm[i].prm, adm[i].prm.initial_damping, sc[i]);
+      sc[i].full = 0;   // shared launches run the Schur form
+      adm[i].g->pcg_full = 0;
+    }
     if ((s = put_scalars(owner, bs, sc)) == GPO_OK && (s = launch_initial_cost(owner, bs.ls)) == GPO_OK)
       s = get_scalars(owner, bs, sc);
     bs.release(owner->stream);

@@ -72,7 +72,8 @@ struct Scalars {
   int restart;           // the current PCG iteration is a restart: the product is S x,
                          // the update sets r = g - S x and restarts the direction
   int pcg_products;      // Schur products of the current solve (iterations + restarts)
-  int pad2_;
+  int full;              // PCG on the full damped system (cameras and points) instead of
+                         // the camera Schur complement
 };
 
 struct IterRecord {       // mirrors gpo_iter_record
@@ -149,6 +150,9 @@ struct DevBA {
   void* Minv;                // AT [C][TB] block-Jacobi preconditioner S_cc^-1
   void* g;                   // AT [C][DB] reduced right-hand side
   void* x; void* r; void* z; void* p; void* p2; void* y; void* xbest;   // AT [C][DB]
+  // full-system PCG, point part (allocated on first use): AT [P][3] each
+  void* xq; void* rq; void* zq; void* pq; void* pq2; void* yq; void* xqbest;
+  double* pt_part;           // [npb][2] per-point-block partial sums (full-system PCG)
   double* cost_part;         // [NCH]
   double* md_part;           // [NCH]
   double* cblk_part;         // [ncblk][2]
@@ -206,6 +210,11 @@ struct KernelSet {
   int (*cam_apply)(const LaunchSet& ls, Prec pr, cudaStream_t st);    // y = S p camera side, alpha
   int (*pcg_update)(const LaunchSet& ls, Prec pr, cudaStream_t st);   // x, r, z; stopping rules, beta
   int (*pcg_camera)(const LaunchSet& ls, Prec pr, cudaStream_t st);   // cam_apply + pcg_update in one launch
+  // full-system PCG (cameras and points; the paper's form): point-side start, the
+  // product with the whole damped H, the update over camera and point blocks
+  int (*full_init)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*full_spmv)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  int (*full_update)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*backsub)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*retract)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*decide)(const LaunchSet& ls, Prec pr, cudaStream_t st);

@@ -20,11 +20,11 @@ using gpo::Scalars;
 enum KernelKind {
   KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
   KK_CAM_APPLY, KK_PCG_UPDATE, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT, KK_PCG_CAMERA,
-  KK_COUNT
+  KK_FULL_INIT, KK_COUNT
 };
 inline const char* const kKernelNames[KK_COUNT] = {
     "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
-    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit", "pcg_camera"};
+    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit", "pcg_camera", "full_init"};
 
 struct Profiler {
   bool on = false;
@@ -95,6 +95,8 @@ struct gpo_graph {
   // device
   void* arena = nullptr;
   size_t arena_bytes = 0;
+  void* full_buf = nullptr;        // point rows of the full-system PCG (allocated on first use)
+  size_t full_bytes = 0;
   DevBA dev{};
   gpo::LaunchSet ls{};             // one-problem launch set over `dev`
   DevBA* dev_desc = nullptr;       // device copy of `dev` (ls.probs)
@@ -113,6 +115,8 @@ struct gpo_graph {
   gpo::LaunchSet pcg_ls{};
   int pcg_counts[3] = {0, 0, 0};   // kernels per group: Schur product, fused camera kernel, separate camera kernels
   bool pcg_graph_off = false;      // capture failed once: launch directly
+  int pcg_full = 0;                // solver of the last scalars filled (1: full system)
+  int pcg_exec_full = -1;          // solver the captured group was recorded for
 };
 
 

@@ -266,6 +266,24 @@ __device__ __forceinline__ void sum_partials(const double* part, int n, double& 
   b = rb[0];
 }
 
+// Sums n single per-CTA partials with all threads in a fixed order (as sum_partials);
+// the result is valid in every thread.
+__device__ __forceinline__ double sum_singles(const double* part, int n) {
+  __shared__ double rs[256];
+  double x = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x += part[i];
+  rs[threadIdx.x] = x;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) rs[threadIdx.x] += rs[threadIdx.x + s2];
+    __syncthreads();
+  }
+  return rs[0];
+}
+
+// Point blocks of 256 points (the point kernels' CTAs) of a problem.
+__device__ __forceinline__ int point_blocks(const DevBA& d) { return (d.P + 255) / 256; }
+
 struct ChunkRange {
   int e0, nE, p0, nP, s0, nS;
 };

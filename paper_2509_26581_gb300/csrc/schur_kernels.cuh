@@ -628,10 +628,13 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
       if (obs) h += vals[warp][tc];
       if (ti == tj) h += lam * damp_diag(h, sc);
       Hcl[t] = h;
+      const AT hc = h;
       if (obs) h -= vals[warp][NPA + tc];
       S[t] = h;
-      Sf[warp][ti * DB + tj] = h;
-      Sf[warp][tj * DB + ti] = h;
+      // preconditioner block: S_cc^-1, or (H_cc + lambda D_c)^-1 for the full system
+      const AT hm = sc->full ? hc : h;
+      Sf[warp][ti * DB + tj] = hm;
+      Sf[warp][tj * DB + ti] = hm;
     }
     __syncwarp();
     warp_spd_inverse<DB>(Sf[warp], Mi, lane);
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
         si = vals[warp][NPA + TC + lane];
       }
       if constexpr (Mo::kExtra) bi += hx[warp][TB + lane];
-      const AT gi = -bi + si;
+      const AT gi = sc->full ? -bi : -bi + si;   // full system: the camera rows of -b
       g[lane] = gi;
       bc[lane] = bi;
       reinterpret_cast<AT*>(d.x)[DB * (size_t)c + lane] = (AT)0;
@@ -682,6 +685,13 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
   if (!last_cta(&sc->ticket, d.ncblk)) return;
   double rz, rr;
   sum_partials(d.cblk_part, d.ncblk, rz, rr);
+  if (sc->full) {   // the point rows, started by k_full_init
+    double rzq, rrq;
+    __syncthreads();
+    sum_partials(d.pt_part, point_blocks(d), rzq, rrq);
+    rz += rzq;
+    rr += rrq;
+  }
   if (threadIdx.x == 0) {
     const double gn = sqrt(rr);
     sc->rz = rz;
@@ -812,7 +822,10 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
         for (int j = 0; j < kApplySplit; ++j) yi += qx[warp + j][lane];
     }
     if (lane < DB) {
-      yi -= sv;
+      // the Schur complement subtracts the points' coupling; the full system's product
+      // adds the edges' coupling terms J_c^T J_p v_p
+      if (sc->full) yi += sv;
+      else yi -= sv;
       reinterpret_cast<AT*>(d.y)[DB * (size_t)c + lane] = yi;
       dot = pi * yi;
     }
@@ -833,6 +846,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
   if (!last_cta(&sc->ticket, ctas)) return;
   double pAp, unused;
   sum_partials(d.cblk_part, ctas, pAp, unused);
+  if (sc->full) pAp += sum_singles(d.md_part, d.NCH);   // the points' p^T H p, per chunk
   if (threadIdx.x == 0) {
     sc->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
@@ -882,6 +896,65 @@ __device__ __forceinline__ void pcg_update_load(const DevBA& d, int cbl, UpdateI
     in.x0 = reinterpret_cast<const AT*>(d.x)[o];
 #pragma unroll
     for (int j = 0; j < DB; ++j) in.mrow[j] = Mi[sym_idx(DB, lane, j)];
+  }
+}
+
+// The end of a PCG update, reached by every CTA of the update after writing its
+// partial (r^T z, |r|^2): the last one of the problem sums the camera blocks' partials
+// (and, in the full-system form, the point blocks' after them), applies the stopping
+// rules (tolerance, rejection ratio, iteration cap) and computes beta and the
+// normalisation factor.
+__device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, int restart) {
+  Scalars* sc = d.sc;
+  const int full = sc->full;
+  const int npb = full ? point_blocks(d) : 0;
+  if (!last_cta(&sc->ticket, d.ncblk + npb)) return;
+  double rz, rr;
+  sum_partials(d.cblk_part + 2 * kApplySplit * (size_t)d.ncblk, d.ncblk, rz, rr);
+  if (full) {
+    double rzq, rrq;
+    __syncthreads();   // every thread has read the first sums out of the shared tree
+    sum_partials(d.pt_part, npb, rzq, rrq);
+    rz += rzq;
+    rr += rrq;
+  }
+  if (threadIdx.x == 0) {
+    const double n = sqrt(rr);
+    if (restart) sc->sigma = 1.0;            // r is now the true residual
+    const double rtrue = sc->sigma * n;
+    if (!restart) sc->pcg_it += 1;           // a restart is an extra product, not an iteration
+    sc->pcg_total += 1;
+    sc->pcg_products += 1;
+    sc->rnorm = rtrue;
+    int done = 0;
+    sc->save_best = 0;
+    if (sc->ratio > 0.0) {
+      if (rtrue < sc->rmin) {
+        sc->rmin = rtrue;
+        sc->save_best = 1;
+      } else if (rtrue > sc->ratio * sc->rmin) {
+        done = 1;
+        sc->use_best = 1;
+      }
+    }
+    if (rtrue <= sc->tol_abs || sc->pcg_it >= sc->max_it || !isfinite(rtrue) || !(rz > 0.0)) {
+      done = 1;
+      if (!isfinite(rtrue)) sc->use_best = 1;
+    }
+    sc->beta = restart ? 0.0 : rz / sc->rz;   // a restart starts the direction from z
+    if (sc->normalize && n > 0.0) {
+      sc->inv_n = 1.0 / n;
+      sc->sigma *= n;
+      sc->rz = rz / (n * n);
+    } else {
+      sc->inv_n = 1.0;
+      sc->rz = rz;
+    }
+    if (!restart) sc->pidx ^= 1;            // a restart wrote no new direction
+    sc->restart = (!done && !restart && sc->restart_every > 0 && sc->pcg_it % sc->restart_every == 0) ? 1 : 0;
+    sc->pcg_done = done;
+    if (done) atomicSub(ls.running, 1);
+    sc->ticket = 0u;
   }
 }
 
@@ -972,47 +1045,7 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
     upart[2 * cbl] = a;
     upart[2 * cbl + 1] = b;
   }
-  if (!last_cta(&sc->ticket, d.ncblk)) return;
-  double rz, rr;
-  sum_partials(upart, d.ncblk, rz, rr);
-  if (threadIdx.x == 0) {
-    const double n = sqrt(rr);
-    if (restart) sc->sigma = 1.0;            // r is now the true residual
-    const double rtrue = sc->sigma * n;
-    if (!restart) sc->pcg_it += 1;           // a restart is an extra product, not an iteration
-    sc->pcg_total += 1;
-    sc->pcg_products += 1;
-    sc->rnorm = rtrue;
-    int done = 0;
-    sc->save_best = 0;
-    if (sc->ratio > 0.0) {
-      if (rtrue < sc->rmin) {
-        sc->rmin = rtrue;
-        sc->save_best = 1;
-      } else if (rtrue > sc->ratio * sc->rmin) {
-        done = 1;
-        sc->use_best = 1;
-      }
-    }
-    if (rtrue <= sc->tol_abs || sc->pcg_it >= sc->max_it || !isfinite(rtrue) || !(rz > 0.0)) {
-      done = 1;
-      if (!isfinite(rtrue)) sc->use_best = 1;
-    }
-    sc->beta = restart ? 0.0 : rz / sc->rz;   // a restart starts the direction from z
-    if (sc->normalize && n > 0.0) {
-      sc->inv_n = 1.0 / n;
-      sc->sigma *= n;
-      sc->rz = rz / (n * n);
-    } else {
-      sc->inv_n = 1.0;
-      sc->rz = rz;
-    }
-    if (!restart) sc->pidx ^= 1;            // a restart wrote no new direction
-    sc->restart = (!done && !restart && sc->restart_every > 0 && sc->pcg_it % sc->restart_every == 0) ? 1 : 0;
-    sc->pcg_done = done;
-    if (done) atomicSub(ls.running, 1);
-    sc->ticket = 0u;
-  }
+  pcg_update_finish(ls, d, restart);
 }
 template <class Mo, class AT>
 __global__ void __launch_bounds__(kCamPerBlock * 32) k_pcg_update(LaunchSet ls) {
@@ -1114,8 +1147,9 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
 
 // ---------------------------------------------------------------- back-substitution
 
-// One CTA per chunk: dp = H_pp^-1 (-b_p - sum_e Jp^T Jc dc) and the chunk's share of
-// the model decrease -b_p^T dp - 1/2 sum_e |Jc dc + Jp dp|^2 (FP64 accumulation).
+// One CTA per chunk: dp = H_pp^-1 (-b_p - sum_e Jp^T Jc dc) (the full-system PCG's
+// point rows instead when it solved them) and the chunk's share of the model decrease
+// -b_p^T dp - 1/2 sum_e |Jc dc + Jp dp|^2 (FP64 accumulation).
 template <class Mo, class JT>
 __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
@@ -1168,11 +1202,17 @@ __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
       for (int k = 0; k < 3; ++k) u[k] += av[k * CH + i];
     }
     AT hi[6], rhs[3], t[3];
+    if (d.sc->full) {   // the full-system PCG solved the point rows itself
+      const AT* xq = reinterpret_cast<const AT*>(d.sc->use_best ? d.xqbest : d.xq) + 3 * (size_t)pj;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+      for (int k = 0; k < 3; ++k) t[k] = xq[k];
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) rhs[k] = -bp[3 * (size_t)pj + k] - u[k];
-    mul3(hi, rhs, t);
+      for (int k = 0; k < 6; ++k) hi[k] = Hinv[6 * (size_t)pj + k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) rhs[k] = -bp[3 * (size_t)pj + k] - u[k];
+      mul3(hi, rhs, t);
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       dp[3 * (size_t)pj + k] = t[k];
@@ -1360,6 +1400,12 @@ static void set_smem(const void* kernel, size_t bytes) {
   if (n < 64) { keys[n] = kernel; vals[n] = bytes; ++n; }
 }
 
+}  // namespace gpo
+
+#include "schur_full.cuh"
+
+namespace gpo {
+
 // Shared-memory sizes and launchers of one model.
 template <class Mo>
 struct Launch {
@@ -1383,6 +1429,36 @@ struct Launch {
            4 * (size_t)(ls.np_max + 2 * ls.ns_max + 2);
   }
   static size_t backsub_smem(Prec pr, int ch) { return (Mo::M + 3) * sA(pr) * (size_t)ch; }
+  static size_t full_smem(Prec pr, const LaunchSet& ls) {
+    return sA(pr) * ((Mo::DC + 3) * (size_t)(ls.ch_max + 1) + Mo::DC * (size_t)ls.ns_max + 3 * (size_t)ls.np_max) +
+           4 * (size_t)(ls.np_max + 2 * ls.ns_max + 2);
+  }
+  static int full_init(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_pb == 0) return 0;
+    if (pr == Prec::F64) launch_pdl(k_full_init<Mo, double>, ls.n_pb, 256, 0, st, ls);
+    else launch_pdl(k_full_init<Mo, float>, ls.n_pb, 256, 0, st, ls);
+    return 1;
+  }
+  template <class JT>
+  static void full_spmv_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = full_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_full_spmv<Mo, JT>), sm);
+    launch_pdl(k_full_spmv<Mo, JT>, ls.n_ch, kThreads, sm, st, ls);
+  }
+  static int full_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.n_ch == 0) return 0;
+    if (pr == Prec::F64) full_spmv_t<double>(ls, pr, st);
+    else if (pr == Prec::F32) full_spmv_t<float>(ls, pr, st);
+    else full_spmv_t<__nv_bfloat16>(ls, pr, st);
+    return 1;
+  }
+  static int full_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const int n = ls.n_cb + ls.n_pb;
+    if (n == 0) return 0;
+    if (pr == Prec::F64) launch_pdl(k_full_update<Mo, double>, n, kCamPerBlock * 32, 0, st, ls);
+    else launch_pdl(k_full_update<Mo, float>, n, kCamPerBlock * 32, 0, st, ls);
+    return 1;
+  }
   static int max_supported_ch(Prec pr) {
     // largest chunk whose linearisation tile fits the 227 KB opt-in shared memory
     const size_t limit = 227 * 1024;
@@ -1627,6 +1703,9 @@ KernelSet make_kernel_set(ModelKind kind) {
   k.cam_apply = &L::cam_apply;
   k.pcg_update = &L::pcg_update;
   k.pcg_camera = &L::pcg_camera;
+  k.full_init = &L::full_init;
+  k.full_spmv = &L::full_spmv;
+  k.full_update = &L::full_update;
   k.backsub = &L::backsub;
   k.retract = &L::retract;
   k.decide = &L::decide;

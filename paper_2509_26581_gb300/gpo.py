@@ -18,6 +18,7 @@ from . import build as _build
 GPO_OK = 0
 GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_STATE, GPO_ERR_NUMERIC = -1, -2, -3, -4
 GPO_ERR_CUDA, GPO_ERR_TIMEOUT, GPO_ERR_UNSUPPORTED = -5, -6, -7
+GPO_SOLVER_SCHUR, GPO_SOLVER_FULL = 0, 1
 GPO_FP64, GPO_FP32, GPO_FP32_BF16 = 0, 1, 2
 GPO_V_BA_CAMERA9, GPO_V_POINT3, GPO_V_NAV15 = 0, 1, 2
 GPO_E_BA_REPROJ, GPO_E_STEREO, GPO_E_IMU, GPO_E_BIAS_RW, GPO_E_BIAS_PRIOR = 0, 1, 2, 3, 4
@@ -43,7 +44,7 @@ class gpo_lm_params(C.Structure):
                 ("damping_mode", C.c_int32), ("pcg_max_iters", C.c_int32),
                 ("pcg_tol", C.c_double), ("pcg_tol_relative", C.c_int32),
                 ("pcg_rejection_ratio", C.c_double), ("pcg_normalize", C.c_int32),
-                ("pcg_restart_every", C.c_int32)]
+                ("pcg_restart_every", C.c_int32), ("solver", C.c_int32)]
 
 
 class gpo_report(C.Structure):
