@@ -273,6 +273,60 @@ def spmv_algorithmic_bytes_vi(E: int, P: int, precision: str) -> float:
     return E * (27 * sJ + 4) + P * 6 * sA
 
 
+def full_algorithmic_bytes(E: int, P: int, precision: str) -> float:
+    """Compulsory HBM bytes of one full-system product (k_full_spmv): every stored
+    Jacobian value and camera index once, and per point its undamped block (6), the
+    direction's inputs z and p_old and outputs p and y (3 each) and its edge range."""
+    sJ = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    sA = 8 if precision == "fp64" else 4
+    return E * (24 * sJ + 4) + P * (6 * sA + 12 * sA + 8)
+
+
+def extra_full_system(args, p, dev, stream, schur_rate: float, schur_cost: float) -> dict:
+    """The paper's own form of the solve on the same workload and precision: block-
+    Jacobi PCG on the full damped system (GPO_SOLVER_FULL, same PCG cap and tolerance)
+    against the camera Schur complement: LM rate over the same warm-up and timed
+    steps, PCG iterations, final cost, the full-system product's time and achieved
+    bandwidth (profiled pass), and the device footprint."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo
+    prm = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6, solver=gpo.GPO_SOLVER_FULL)
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, args.precision,
+                             device=dev, stream=stream.cuda_stream, **knobs(args))
+    g.optimize(args.warmup, prm)
+    cams_w = g.get_state(c0, p.n_cams, 9)
+    pts_w = g.get_state(p0, p.n_pts, 3)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rep = g.optimize(args.steps, prm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    its = [h["pcg_iters"] for h in g.history()]
+    g.set_initial(c0, cams_w)
+    g.set_initial(p0, pts_w)
+    g.set_profiling(True)
+    g.optimize(args.steps, prm)
+    prof = g.profile()
+    sp = prof["spmv"]
+    spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
+    peak, peak_kind = load_peaks()
+    alg = full_algorithmic_bytes(p.n_edges, p.n_pts, args.precision)
+    out = dict(solver="full system (cameras and points), block-Jacobi PCG", precision=args.precision,
+               lm_iter_per_s=args.steps / (ms / 1e3), schur_lm_iter_per_s=schur_rate,
+               pcg_iters_per_step=its, final_cost=rep.final_cost,
+               rel_diff_vs_schur=abs(rep.final_cost - schur_cost) / schur_cost,
+               product=dict(kernel="k_full_spmv", avg_ms=spmv_ms, algorithmic_bytes=alg,
+                            achieved_gbs=alg / (spmv_ms * 1e-3) / 1e9,
+                            frac=alg / (spmv_ms * 1e-3) / 1e9 / peak, peak=peak, peak_source=peak_kind),
+               kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items() if v["launches"]},
+               footprint_bytes=g.footprint())
+    g.close()
+    return out
+
+
 def extra_mixed_vs_fp64(args, p, params, dev, stream, main_cost: float, fp64_peak_tflops: float) -> dict:
     """The FP64 GPU path on the same workload and schedule (warm-up, then the timed
     steps, each call starting from initial_damping): final-cost difference of the
@@ -636,6 +690,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         g.close()
         line["mixed_vs_fp64"] = extra_mixed_vs_fp64(args, p, params, dev, stream, rep.final_cost,
                                                     line["fp64"]["peak_tflops"])
+        line["full_system"] = extra_full_system(args, p, dev, stream, line["value"], rep.final_cost)
         line["vi"] = extra_vi(dev, stream)
         line["served"] = extra_served(stream)
         line["large"] = extra_large(dev, stream)
