@@ -42,7 +42,22 @@ def test_defaults_and_version(lib):
     p = gpo.default_params()
     assert p.initial_damping == 1e-4 and p.pcg_max_iters == 100 and p.pcg_tol == 1e-6
     assert p.diag_min == 1e-6 and p.diag_max == 1e32 and p.pcg_rejection_ratio == 10.0
+    # the last fields too: the binding's structure matches the header's layout
+    assert p.pcg_normalize == -1 and p.pcg_restart_every == -1 and p.solver == gpo.GPO_SOLVER_SCHUR
     assert gpo.lib.gpo_version().decode().startswith("gpo")
+
+
+def test_struct_sizes_match_the_header():
+    """Each parameter struct the binding mirrors has the size the header gives it
+    (C layout rules of the header's member types, computed here independently)."""
+    from paper_2509_26581_gb300 import gpo
+    # gpo_lm_params: 5 doubles, 2 int32, double, int32 (+4 pad), double, 3 int32 (+4 pad)
+    assert ctypes.sizeof(gpo.gpo_lm_params) == 5 * 8 + 2 * 4 + 8 + 8 + 8 + 16
+    src = open(os.path.join(ROOT, "include", "gpo.h")).read()
+    body = src[src.index("typedef struct {", src.index("PCGSolver(max_it")):src.index("} gpo_lm_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(double|int32_t)\s+(\w+);", body)
+    assert [f for _, f in fields] == [f for f, _ in gpo.gpo_lm_params._fields_]
 
 
 def test_null_arguments_are_rejected(lib):
