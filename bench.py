@@ -327,6 +327,32 @@ def extra_full_system(args, p, dev, stream, schur_rate: float, schur_cost: float
     return out
 
 
+def extra_autodiff(args, p, dev, stream) -> dict:
+    """The forward-mode automatic-differentiation checker on the whole workload: its
+    kernel time (every edge's FP64 dual-number residual and rows) against the analytic
+    linearisation kernel's, and the largest difference of their rows on 2,000 sampled
+    edges (relative to each edge's largest entry; the analytic rows stored in the
+    benchmarked precision)."""
+    import numpy as np
+
+    from paper_2509_26581_gb300 import gpo
+    g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, args.precision,
+                           device=dev, stream=stream.cuda_stream, **knobs(args))
+    ids = np.random.default_rng(0).choice(p.n_edges, 2000, replace=False)
+    _, J = g.debug_linearize_edges(ids)
+    g.set_profiling(True)
+    _, Ja = g.debug_autodiff_edges(ids)
+    g.optimize(1, gpo.default_params(pcg_max_iters=1))   # one profiled analytic linearisation
+    prof = g.profile()
+    lin, ad = prof["linearize"], prof["autodiff"]
+    scale = np.maximum(np.abs(Ja).reshape(len(ids), -1).max(axis=1), 1e-9)
+    rel = (np.abs(J - Ja).reshape(len(ids), -1).max(axis=1) / scale).max()
+    g.close()
+    return dict(edges=p.n_edges, autodiff_ms=ad["total_ms"] / max(1, ad["timed"]),
+                analytic_linearize_ms=lin["active_ms"] / max(1, lin["active"]),
+                sampled_edges=len(ids), max_rel_diff_sampled=float(rel), analytic_precision=args.precision)
+
+
 def extra_mixed_vs_fp64(args, p, params, dev, stream, main_cost: float, fp64_peak_tflops: float) -> dict:
     """The FP64 GPU path on the same workload and schedule (warm-up, then the timed
     steps, each call starting from initial_damping): final-cost difference of the
@@ -691,6 +717,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         line["mixed_vs_fp64"] = extra_mixed_vs_fp64(args, p, params, dev, stream, rep.final_cost,
                                                     line["fp64"]["peak_tflops"])
         line["full_system"] = extra_full_system(args, p, dev, stream, line["value"], rep.final_cost)
+        line["autodiff"] = extra_autodiff(args, p, dev, stream)
         line["vi"] = extra_vi(dev, stream)
         line["served"] = extra_served(stream)
         line["large"] = extra_large(dev, stream)

@@ -456,6 +456,18 @@ gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out);
 gpo_status gpo_debug_linearize_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
                                      double* J_out);
 
+/* Forward-mode automatic differentiation of the observation edges (Sec. IV-D: the
+ * paper's edges are differentiated by a forward-mode generator, with analytic
+ * Jacobians beside it): every edge's residual is evaluated on dual numbers at the
+ * current state in FP64, with the whitening, Huber IRLS weight and fixed-vertex zero
+ * columns of the analytic path, and returned in gpo_debug_linearize_edges' layout
+ * (edge_ids[k] -> row k; camera-side edges give zero rows).  Unlike
+ * gpo_debug_linearize_edges the rows are FP64 in every precision.  A checker of the
+ * analytic Jacobians and the prototyping path for new edge kinds; with profiling on its
+ * kernel is timed as "autodiff".  Errors: GPO_ERR_ARG (unknown id), GPO_ERR_CUDA. */
+gpo_status gpo_debug_autodiff_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
+                                    double* J_out);
+
 /* Solves one damped system (H + lambda D^T D) dx = -b at the current state with
  * the full path (Schur, PCG, back-substitution) and given PCG options, without
  * changing the state.  dx_out: one row per vertex in id order, each of the

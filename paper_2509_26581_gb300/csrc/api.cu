@@ -1527,6 +1527,67 @@ gpo_status gpo_debug_linearize_edges(gpo_graph* g, const int64_t* edge_ids, int6
   return debug_linearize_rows(g, edge_ids, n, r_out, J_out);
 }
 
+gpo_status gpo_debug_autodiff_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
+                                    double* J_out) {
+  if (!g || n < 0 || (n > 0 && !edge_ids)) return GPO_ERR_ARG;
+  GPO_CUDA(g, cudaSetDevice(g->desc.device));
+  gpo_status s = finalize(g);
+  if (s != GPO_OK) return s;
+  const gpo::KernelSet& ks = *g->ks;
+  const int M = ks.M, DC = ks.DC, DB = ks.DB, N = DC + 3;
+  const bool nav = ks.model == gpo::ModelKind::STEREO;
+  const int R = nav ? gpo::kXRows : 2, K = nav ? gpo::kXCols : 12;
+  const DevBA& d = g->dev;
+  Scalars sc;
+  gpo_lm_params prm;
+  gpo_lm_params_default(&prm);
+  fill_scalars(g, prm, prm.initial_damping, sc);
+  if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
+  double *rb = nullptr, *jb = nullptr;
+  GPO_CUDA(g, cudaMallocAsync(&rb, std::max<size_t>(1, (size_t)M * d.E) * sizeof(double), g->stream));
+  GPO_CUDA(g, cudaMallocAsync(&jb, std::max<size_t>(1, (size_t)M * N * d.E) * sizeof(double), g->stream));
+  ks.cam_prepare(g->ls, false, g->stream);
+  run(g, KK_AUTODIFF, [&] { return ks.autodiff(g->ls, d.E, rb, jb, g->stream); });
+  GPO_CUDA(g, cudaGetLastError());
+  std::vector<char> rraw, jraw;
+  if ((s = fetch(g, rraw, rb, (size_t)M * d.E * sizeof(double))) != GPO_OK) return s;
+  if ((s = fetch(g, jraw, jb, (size_t)M * N * d.E * sizeof(double))) != GPO_OK) return s;
+  GPO_CUDA(g, cudaStreamSynchronize(g->stream));
+  GPO_CUDA(g, cudaFreeAsync(rb, g->stream));
+  GPO_CUDA(g, cudaFreeAsync(jb, g->stream));
+  if (g->prof.on) prof_resolve(g);
+  const size_t n_ids = g->ed_kind.size();
+  std::vector<int64_t> row_of;
+  size_t n_out = n_ids;
+  if (edge_ids) {
+    row_of.assign(n_ids, -1);
+    for (int64_t k = 0; k < n; ++k) {
+      if (edge_ids[k] < 0 || edge_ids[k] >= (int64_t)n_ids)
+        return fail(g, GPO_ERR_ARG, "no edge %lld", (long long)edge_ids[k]);
+      row_of[edge_ids[k]] = k;
+    }
+    n_out = (size_t)n;
+  }
+  if (r_out) std::fill(r_out, r_out + (size_t)R * n_out, 0.0);
+  if (J_out) std::fill(J_out, J_out + (size_t)R * K * n_out, 0.0);
+  const double* rv = reinterpret_cast<const double*>(rraw.data());
+  const double* jv = reinterpret_cast<const double*>(jraw.data());
+  for (int e = 0; e < d.E; ++e) {   // sorted position
+    int64_t id = g->e_eid[g->sorted_edge[e]];
+    if (edge_ids && (id = row_of[id]) < 0) continue;
+    for (int a = 0; a < M; ++a) {
+      if (r_out) r_out[(size_t)R * id + a] = rv[(size_t)M * e + a];
+      if (J_out) {
+        double* row = J_out + ((size_t)R * id + a) * K;
+        const double* src = jv + ((size_t)M * e + a) * N;
+        for (int j = 0; j < DC; ++j) row[j] = src[j];
+        for (int j = 0; j < 3; ++j) row[DB + j] = src[DC + j];
+      }
+    }
+  }
+  return GPO_OK;
+}
+
 gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* params, double* dx_out, int32_t* pcg_iters) {
   if (!g || !dx_out) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));

@@ -215,6 +215,8 @@ struct KernelSet {
   int (*full_init)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*full_spmv)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*full_update)(const LaunchSet& ls, Prec pr, cudaStream_t st);
+  // forward-mode automatic differentiation of the observation edges (checker)
+  int (*autodiff)(const LaunchSet& ls, int n_edges, double* r, double* J, cudaStream_t st);
   int (*backsub)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*retract)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*decide)(const LaunchSet& ls, Prec pr, cudaStream_t st);

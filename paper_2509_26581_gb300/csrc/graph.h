@@ -20,11 +20,11 @@ using gpo::Scalars;
 enum KernelKind {
   KK_CAM_PREPARE, KK_COST, KK_COST_REDUCE, KK_LINEARIZE, KK_SCHUR, KK_CAM_FINALIZE, KK_SPMV,
   KK_CAM_APPLY, KK_PCG_UPDATE, KK_BACKSUB, KK_RETRACT, KK_DECIDE, KK_COMMIT, KK_PCG_CAMERA,
-  KK_FULL_INIT, KK_COUNT
+  KK_FULL_INIT, KK_AUTODIFF, KK_COUNT
 };
 inline const char* const kKernelNames[KK_COUNT] = {
     "cam_prepare", "cost", "cost_reduce", "linearize", "schur_prepare", "cam_finalize", "spmv",
-    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit", "pcg_camera", "full_init"};
+    "cam_apply", "pcg_update", "backsub", "retract", "decide", "commit", "pcg_camera", "full_init", "autodiff"};
 
 struct Profiler {
   bool on = false;

@@ -1403,6 +1403,7 @@ static void set_smem(const void* kernel, size_t bytes) {
 }  // namespace gpo
 
 #include "schur_full.cuh"
+#include "autodiff.cuh"
 
 namespace gpo {
 
@@ -1450,6 +1451,11 @@ struct Launch {
     if (pr == Prec::F64) full_spmv_t<double>(ls, pr, st);
     else if (pr == Prec::F32) full_spmv_t<float>(ls, pr, st);
     else full_spmv_t<__nv_bfloat16>(ls, pr, st);
+    return 1;
+  }
+  static int autodiff(const LaunchSet& ls, int n_edges, double* r, double* J, cudaStream_t st) {
+    if (n_edges <= 0) return 0;
+    launch_pdl(k_autodiff<Mo>, (n_edges + 255) / 256, 256, 0, st, ls, r, J);
     return 1;
   }
   static int full_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
@@ -1706,6 +1712,7 @@ KernelSet make_kernel_set(ModelKind kind) {
   k.full_init = &L::full_init;
   k.full_spmv = &L::full_spmv;
   k.full_update = &L::full_update;
+  k.autodiff = &L::autodiff;
   k.backsub = &L::backsub;
   k.retract = &L::retract;
   k.decide = &L::decide;

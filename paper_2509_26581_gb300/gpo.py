@@ -119,6 +119,7 @@ _SIGS = {
     "gpo_debug_step": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, C.POINTER(C.c_int32)]),
     "gpo_debug_schur": (C.c_int, [_P, C.c_double, C.POINTER(gpo_lm_params), _P, _P]),
     "gpo_debug_wait_timeout": (C.c_int, [_P]),
+    "gpo_debug_autodiff_edges": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "gpo_fp64_fma_probe": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
 }
 
@@ -312,6 +313,16 @@ class Graph:
         r = np.zeros((len(ids), R))
         J = np.zeros((len(ids), R, K))
         _check(lib.gpo_debug_linearize_edges(self.h, _ptr(ids), len(ids), _ptr(r), _ptr(J)), self.h)
+        return r, J
+
+    def debug_autodiff_edges(self, edge_ids, nav: bool = False):
+        """Rows of the given edges by forward-mode automatic differentiation, FP64
+        (gpo_debug_autodiff_edges; layout of debug_linearize_edges)."""
+        ids = np.ascontiguousarray(edge_ids, dtype=np.int64)
+        R, K = (9, 30) if nav else (2, 12)
+        r = np.zeros((len(ids), R))
+        J = np.zeros((len(ids), R, K))
+        _check(lib.gpo_debug_autodiff_edges(self.h, _ptr(ids), len(ids), _ptr(r), _ptr(J)), self.h)
         return r, J
 
     def debug_step(self, lam: float, n_dof: int, params: gpo_lm_params | None = None):
