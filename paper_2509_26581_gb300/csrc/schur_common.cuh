@@ -283,6 +283,9 @@ __device__ __forceinline__ double sum_singles(const double* part, int n) {
 
 // Point blocks of 256 points (the point kernels' CTAs) of a problem.
 __device__ __forceinline__ int point_blocks(const DevBA& d) { return (d.P + 255) / 256; }
+// Points per update CTA of the full-system PCG, and that update's point CTAs.
+constexpr int kUpdatePoints = 2048;
+__host__ __device__ inline int update_point_blocks(int P) { return (P + kUpdatePoints - 1) / kUpdatePoints; }
 
 struct ChunkRange {
   int e0, nE, p0, nP, s0, nS;

@@ -216,9 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
 }
 
 // Update of a full-system PCG iteration: CTAs 0 .. ncblk-1 are the camera blocks
-// (pcg_update_body: x, r, z = M r over the camera rows), the rest point blocks of 256
-// points (x += sigma alpha p, r <- r / n - alpha y, or the true residual g - y in a
-// restart iteration, z = (H_pp + lambda D_p)^-1 r).  Every CTA writes its (r^T z,
+// (pcg_update_body: x, r, z = M r over the camera rows), the rest point blocks of
+// kUpdatePoints points, eight per thread (x += sigma alpha p, r <- r / n - alpha y, or
+// the true residual g - y in a restart iteration, z = (H_pp + lambda D_p)^-1 r); large
+// point blocks keep the last-CTA ticket and the final sum short.  Every CTA writes its (r^T z,
 // |r|^2); the last one of the grid sums camera then point partials and applies the
 // stopping rules (pcg_update_finish).
 template <class Mo, class AT>
@@ -240,10 +241,9 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_full_update(LaunchSet ls)
   Scalars* sc = d.sc;
   if (!sc->active || sc->pcg_done) return;
   const int pbl = b - d.ncblk;
-  const int p = pbl * 256 + threadIdx.x;
   const int restart = sc->restart;
   double rz = 0.0, rr = 0.0;
-  if (p < d.P) {
+  for (int p = pbl * kUpdatePoints + threadIdx.x; p < min(d.P, (pbl + 1) * kUpdatePoints); p += kThreads) {
     const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
     const size_t o = 3 * (size_t)p;
     AT* x = reinterpret_cast<AT*>(d.xq) + o;
@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_full_update(LaunchSet ls)
       rz_a += ri[k] * zi[k];
       rr_a += ri[k] * ri[k];
     }
-    rz = (double)rz_a;
-    rr = (double)rr_a;
+    rz += (double)rz_a;
+    rr += (double)rr_a;
   }
   const double a = block_sum(rz, redp);
   const double c = block_sum(rr, redp);

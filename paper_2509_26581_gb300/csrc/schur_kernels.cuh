@@ -907,7 +907,7 @@ __device__ __forceinline__ void pcg_update_load(const DevBA& d, int cbl, UpdateI
 __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, int restart) {
   Scalars* sc = d.sc;
   const int full = sc->full;
-  const int npb = full ? point_blocks(d) : 0;
+  const int npb = full ? update_point_blocks(d.P) : 0;   // the update's point CTAs
   if (!last_cta(&sc->ticket, d.ncblk + npb)) return;
   double rz, rr;
   sum_partials(d.cblk_part + 2 * kApplySplit * (size_t)d.ncblk, d.ncblk, rz, rr);
@@ -1459,7 +1459,7 @@ struct Launch {
     return 1;
   }
   static int full_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-    const int n = ls.n_cb + ls.n_pb;
+    const int n = ls.n_cb + (ls.n_pb > 0 ? update_point_blocks(ls.n_pb * 256) : 0);
     if (n == 0) return 0;
     if (pr == Prec::F64) launch_pdl(k_full_update<Mo, double>, n, kCamPerBlock * 32, 0, st, ls);
     else launch_pdl(k_full_update<Mo, float>, n, kCamPerBlock * 32, 0, st, ls);
