@@ -240,7 +240,8 @@ def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
 
 KERNEL_LABEL = {"k_spmv_pp": "k_spmv_pp (PCG Schur product, pipelined persistent)",
                 "k_spmv_ws": "k_spmv_ws (PCG Schur product, staged)",
-                "k_spmv": "k_spmv (PCG Schur product, classic)"}
+                "k_spmv": "k_spmv (PCG Schur product, classic)",
+                "k_full_spmv": "k_full_spmv (PCG product with the full damped system)"}
 
 
 def spmv_traffic(precision: str, kernel: str):
@@ -614,7 +615,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     if args.workload == "vi_global":
         return run_vi(args, dev, stream, world)
     p = synth.ba_medium(args.seed)
-    params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
+    solver = gpo.GPO_SOLVER_FULL if args.solver == "full" else gpo.GPO_SOLVER_SCHUR
+    params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6, solver=solver)
     g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta,
                              args.precision, device=dev, stream=stream.cuda_stream, **knobs(args))
     g.optimize(args.warmup, params)               # also freezes the topology and plans memory
@@ -658,7 +660,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     n_e2e = 0 if args.no_e2e else args.steps
-    step_params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
+    step_params = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6, solver=solver)
     lam = step_params.initial_damping
     e2e_pcg = []
     for k in range(n_e2e):
@@ -681,6 +683,9 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     peak, peak_kind = load_peaks()
     kern = spmv_kernel(args.precision, g.knobs, g.info()["chunk_edges"])
     alg = spmv_algorithmic_bytes(p.n_edges, p.n_pts, args.precision)
+    if args.solver == "full":   # the full-system product instead of the Schur product
+        kern = "k_full_spmv"
+        alg = full_algorithmic_bytes(p.n_edges, p.n_pts, args.precision)
     spmv_ms = sp["active_ms"] / sp["active"] if sp["active"] else float("nan")
     achieved = alg / (spmv_ms * 1e-3) / 1e9 if sp["active"] else 0.0
     state_bytes = (p.n_cams * 9 + p.n_pts * 3) * 8
@@ -757,6 +762,9 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="edges per chunk (0 = library default)")
     ap.add_argument("--spmv", default="auto", choices=sorted(SPMV_VARIANTS),
                     help="Schur-product kernel (a tuning knob; results are bit-identical)")
+    ap.add_argument("--solver", default="schur", choices=["schur", "full"],
+                    help="linear solver of the LM step: camera Schur complement (default) or the "
+                         "full-system PCG")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--workload", default="ba_medium", choices=["ba_medium", "vi_global"],
