@@ -295,9 +295,10 @@ def preintegrate_all(p, bg0=None, ba0=None):
     return out
 
 
-def problem(p, nav, pts, pims, prior_sigma=(1e-2, 1e-1), huber=True):
-    """Generic-LM problem of the VI objective: stereo reprojection (Huber), inertial,
-    bias random walk between consecutive keyframes, bias prior on keyframe 0."""
+def problem(p, nav, pts, pims, prior_sigma=(1e-2, 1e-1), huber=True, imu_huber=None):
+    """Generic-LM problem of the VI objective: stereo reprojection (Huber), inertial
+    (optionally Huber on its whitened residual, threshold imu_huber), bias random walk
+    between consecutive keyframes, bias prior on keyframe 0."""
     from . import lm
     K = nav.shape[0]
     vs = {"nav": lm.VertexSet("nav", 15, nav, retract_nav, False),
@@ -307,7 +308,8 @@ def problem(p, nav, pts, pims, prior_sigma=(1e-2, 1e-1), huber=True):
                     np.asarray(p.obs, float), None, ("huber", p.huber_delta) if huber else None)
     ij = np.stack([np.arange(K - 1), np.arange(1, K)], axis=1)
     U = np.stack([np.linalg.cholesky(np.linalg.inv(pm["cov"])).T for pm in pims])
-    imu = lm.EdgeSet("imu", ["nav", "nav"], ij, imu_evaluate(pims), np.arange(K - 1), U, None)
+    imu = lm.EdgeSet("imu", ["nav", "nav"], ij, imu_evaluate(pims), np.arange(K - 1), U,
+                     None if imu_huber is None else ("huber", float(imu_huber)))
     T = np.array([pm["T"] for pm in pims])
     w = np.concatenate([np.tile(1.0 / np.sqrt(p.noise["sigma_bg"] ** 2 * T)[:, None], (1, 3)),
                         np.tile(1.0 / np.sqrt(p.noise["sigma_ba"] ** 2 * T)[:, None], (1, 3))], axis=1)

@@ -1091,8 +1091,9 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
 
 // Camera-side edges between navigation states.
 static gpo_status add_nav_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* ids, const double* meas,
-                                const double* info, int32_t loss_kind) {
-  if (loss_kind != GPO_LOSS_NONE) return fail(g, GPO_ERR_UNSUPPORTED, "edge kind %d takes no robust loss", kind);
+                                const double* info, int32_t loss_kind, double loss_delta) {
+  if (loss_kind != GPO_LOSS_NONE && kind != GPO_E_IMU)
+    return fail(g, GPO_ERR_UNSUPPORTED, "edge kind %d takes no robust loss", kind);
   if (g->cam_kind >= 0 && g->cam_kind != GPO_V_NAV15)
     return fail(g, GPO_ERR_ARG, "edge kind %d needs navigation states", kind);
   const int arity = kind == GPO_E_BIAS_PRIOR ? 1 : 2;
@@ -1129,6 +1130,7 @@ static gpo_status add_nav_edges(gpo_graph* g, int32_t kind, int64_t n, const int
     for (int k = 0; k < mlen; ++k) g->x_rec[r0 + k] = meas[(size_t)mlen * i + k];
     for (int p = 0; p < m; ++p)
       for (int q = 0; q < m; ++q) g->x_rec[r0 + gpo::kXU + p * gpo::kXRows + q] = U[p * m + q];
+    g->x_rec[r0 + gpo::kXDelta] = loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0;
     g->x_i.push_back((int32_t)g->v_local[a]);
     g->x_j.push_back(b >= 0 ? (int32_t)g->v_local[b] : -1);
     g->x_kind.push_back((int8_t)(kind == GPO_E_IMU ? gpo::XK_IMU : (kind == GPO_E_BIAS_RW ? gpo::XK_BIAS_RW
@@ -1156,7 +1158,7 @@ gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* v
   const int64_t first = (int64_t)g->ed_kind.size();
   const gpo_status s = (kind == GPO_E_BA_REPROJ || kind == GPO_E_STEREO)
                            ? add_obs_edges(g, kind, n, vertex_ids, meas, info, loss_kind, loss_delta)
-                           : add_nav_edges(g, kind, n, vertex_ids, meas, info, loss_kind);
+                           : add_nav_edges(g, kind, n, vertex_ids, meas, info, loss_kind, loss_delta);
   if (s == GPO_OK && first_id) *first_id = first;
   return s;
 }

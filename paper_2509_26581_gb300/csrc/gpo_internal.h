@@ -42,6 +42,7 @@ constexpr int kXJ = kXRows * kXCols;
 //  prior: bg_prior (3), ba_prior (3)
 constexpr int kImuMeas = 67;
 constexpr int kXU = 72;             // offset of U in the record
+constexpr int kXDelta = kXU - 1;    // Huber threshold of the whitened residual (0: no loss)
 constexpr int kXRec = kXU + kXRows * kXRows;   // 153
 
 __host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }

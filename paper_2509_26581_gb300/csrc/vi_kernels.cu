@@ -304,12 +304,20 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_extra_eval(LaunchSet ls, 
     double r[kXRows];
     double* J = mode == 0 ? d.xe_J + (size_t)x * kXJ : nullptr;
     const int m = xedge_eval(d, x, cams, rbs, r, J);
-    double cost = 0.0;
-    for (int p = 0; p < m; ++p) cost += r[p] * r[p];
+    double s = 0.0;
+    for (int p = 0; p < m; ++p) s += r[p] * r[p];
+    // Huber loss on the whitened residual (inertial edges): IRLS rows scaled by
+    // sqrt(rho'), cost 1/2 rho(s), as for the observation edges
+    const double delta = d.xe_rec[(size_t)x * kXRec + kXDelta];
     if (mode == 0) {
+      const double sw = huber_weight<double>(s, delta);
+      if (sw != 1.0) {
+        for (int p = 0; p < m; ++p) r[p] *= sw;
+        for (int k = 0; k < m * kXCols; ++k) J[k] *= sw;
+      }
       for (int p = 0; p < kXRows; ++p) d.xe_r[(size_t)x * kXRows + p] = r[p];
     } else {
-      d.xe_cost[x] = 0.5 * cost;
+      d.xe_cost[x] = 0.5 * huber_rho(s, delta);
     }
   }
 }

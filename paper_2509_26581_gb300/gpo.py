@@ -478,7 +478,8 @@ def stereo_rig(camera: dict) -> np.ndarray:
                  np.asarray(camera["R_cb"], float).reshape(9), np.asarray(camera["t_cb"], float).reshape(3)]
 
 
-def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), huber=True, imu=None, **kw):
+def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), huber=True, imu=None,
+             imu_huber=None, **kw):
     """Builds the visual-inertial graph of a VIProblem-like record: navigation states get
     ids [0, K), landmarks [K, K + P); edges in this order: stereo (Huber), inertial between
     consecutive keyframes (preintegrated by the library at the initial biases of the first
@@ -509,7 +510,10 @@ def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), 
                 meas[k], _, info[k] = imu_preintegrate(p.imu_gyro[k], p.imu_acc[k], p.dt, nav[k, 10:13],
                                                        nav[k, 13:16], p.noise["sigma_g"], p.noise["sigma_a"])
         ij = np.stack([np.arange(K - 1), np.arange(1, K)], axis=1).astype(np.int64) + n0
-        e0 = g.add_edges(GPO_E_IMU, ij, meas, info)
+        if imu_huber is None:
+            e0 = g.add_edges(GPO_E_IMU, ij, meas, info)
+        else:   # Huber on the inertial edges' whitened residual
+            e0 = g.add_edges(GPO_E_IMU, ij, meas, info, GPO_LOSS_HUBER, float(imu_huber))
         ranges["imu"] = (e0, e0 + K - 1)
         T = meas[:, 60]
         w2 = np.concatenate([np.tile((1.0 / (p.noise["sigma_bg"] ** 2 * T))[:, None], (1, 3)),

@@ -216,6 +216,22 @@ def test_library_preintegration_graph_matches_oracle(gpo, small):
     assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
 
 
+def test_huber_inertial_edges_match_the_oracle(gpo, small):
+    """Huber loss on the inertial edges (threshold: the median whitened residual at the
+    start, so about half the edges are beyond it): the initial cost to 1e-12 and the
+    LM run to the oracle's final cost to 1e-9, FP64."""
+    p, pims = small
+    c0 = olm.edge_costs(ovi.problem(p, p.nav0, p.pts0, pims))
+    delta = float(np.median(np.sqrt(2.0 * c0[1])))
+    g, _, _, _ = gpo.vi_graph(p, precision="fp64", imu=_records(pims), imu_huber=delta)
+    rep = g.optimize(15, _parity_params(gpo))
+    _, orep = olm.levenberg_marquardt(ovi.problem(p, p.nav0, p.pts0, pims, imu_huber=delta), 15)
+    assert abs(rep.initial_cost - orep.initial_cost) <= 1e-12 * orep.initial_cost
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
+    plain, _, _, _ = gpo.vi_graph(p, precision="fp64", imu=_records(pims))
+    assert plain.cost() > rep.initial_cost   # rho(s) < s beyond the threshold
+
+
 def test_fixed_keyframe_and_disabled_edges(gpo, small):
     p, pims = small
     g, n0, p0, rg = _graph(gpo, p, pims)

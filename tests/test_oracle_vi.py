@@ -142,3 +142,23 @@ def test_vi_lm_decreases_cost(small):
     prob = vi.problem(p, p.nav0, p.pts0, vi.preintegrate_all(p))
     _, rep = lm.levenberg_marquardt(prob, 8)
     assert rep.final_cost < 0.2 * rep.initial_cost
+
+
+def test_huber_inertial_edges_reduce_to_the_plain_and_the_huber_forms(small):
+    """Huber on the inertial edges: a threshold above every whitened residual leaves the
+    objective unchanged; a finite one replaces each large edge's s by 2 delta sqrt(s) -
+    delta^2 (Eq. 7) and leaves the other edge sets as they were."""
+    p = small
+    pims = vi.preintegrate_all(p)
+    plain = vi.problem(p, p.nav0, p.pts0, pims)
+    c0 = lm.edge_costs(plain)
+    s = 2.0 * c0[1]                                   # whitened squared norms of the inertial edges
+    big = vi.problem(p, p.nav0, p.pts0, pims, imu_huber=10.0 * np.sqrt(s.max()))
+    assert np.array_equal(lm.edge_costs(big)[1], c0[1])
+    delta = float(np.median(np.sqrt(s)))
+    hub = lm.edge_costs(vi.problem(p, p.nav0, p.pts0, pims, imu_huber=delta))
+    want = np.where(s > delta ** 2, 2.0 * delta * np.sqrt(s) - delta ** 2, s) / 2.0
+    assert np.allclose(hub[1], want, rtol=1e-15, atol=0.0)
+    assert (s > delta ** 2).any() and (s <= delta ** 2).any()
+    for k in (0, 2, 3):
+        assert np.array_equal(hub[k], c0[k])
