@@ -85,11 +85,15 @@ enum { GPO_V_BA_CAMERA9 = 0, GPO_V_POINT3 = 1, GPO_V_NAV15 = 2 };
  *  GPO_E_BIAS_RW    {nav15 i, nav15 j}; meas unused (may be NULL); m = 6 (Eq. 8 r_b):
  *    r = [bg_j - bg_i, ba_j - ba_i].
  *  GPO_E_BIAS_PRIOR {nav15}; meas 6 [bg ba] prior; m = 6: r = [bg, ba] - meas.
+ *  GPO_E_MONO       {nav15, point3}; meas 2 pixels [u v] in the left camera of the
+ *    stereo rig; m = 2: the first two rows of GPO_E_STEREO's residual.  Info is 2 x 2.
+ *    Stored as a stereo edge whose third row is whitened to zero (edges of both kinds
+ *    share the graph and its kernels).
  * GPO_E_IMU may take the Huber loss on its whitened 9-dim residual (the robust inertial
  * edge of the paper's VI descriptors); GPO_E_BIAS_RW and GPO_E_BIAS_PRIOR take no
  * robust loss (GPO_ERR_UNSUPPORTED). */
 enum { GPO_E_BA_REPROJ = 0, GPO_E_STEREO = 1, GPO_E_IMU = 2, GPO_E_BIAS_RW = 3,
-       GPO_E_BIAS_PRIOR = 4 };
+       GPO_E_BIAS_PRIOR = 4, GPO_E_MONO = 5 };
 
 /* Preintegrated IMU record (doubles, matrices row-major):
  *   [0..9)  dR   [9..12) dv   [12..15) dp   [15..24) JRg  [24..33) Jvg  [33..42) Jva

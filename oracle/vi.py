@@ -278,6 +278,16 @@ def bias_prior_evaluate(states, data):
 
 # ---------------------------------------------------------------- problem builder
 
+def mono_evaluate(cam: StereoCamera):
+    """Monocular reprojection in the rig's left camera: the first two rows of the stereo
+    residual and its Jacobians (obs: n x 2 pixels)."""
+    def ev(states, obs):
+        o3 = np.concatenate([np.asarray(obs, float), np.zeros((len(obs), 1))], axis=1)
+        r, (Jn, Jp) = cam.evaluate(states, o3)
+        return r[:, :2], [Jn[:, :2], Jp[:, :2]]
+    return ev
+
+
 def camera_of(cam: dict) -> StereoCamera:
     return StereoCamera(cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["baseline"], cam["R_cb"],
                         cam["t_cb"])
@@ -295,17 +305,25 @@ def preintegrate_all(p, bg0=None, ba0=None):
     return out
 
 
-def problem(p, nav, pts, pims, prior_sigma=(1e-2, 1e-1), huber=True, imu_huber=None):
+def problem(p, nav, pts, pims, prior_sigma=(1e-2, 1e-1), huber=True, imu_huber=None, mono=None):
     """Generic-LM problem of the VI objective: stereo reprojection (Huber), inertial
     (optionally Huber on its whitened residual, threshold imu_huber), bias random walk
-    between consecutive keyframes, bias prior on keyframe 0."""
+    between consecutive keyframes, bias prior on keyframe 0.  mono: boolean mask of the
+    observations kept as monocular (left-camera) edges instead of stereo ones."""
     from . import lm
     K = nav.shape[0]
     vs = {"nav": lm.VertexSet("nav", 15, nav, retract_nav, False),
           "pt": lm.VertexSet("pt", 3, pts, lambda s, d: s + d, True)}
     cam = camera_of(p.camera)
-    st = lm.EdgeSet("stereo", ["nav", "pt"], np.stack([p.kf_idx, p.pt_idx], axis=1), cam.evaluate,
-                    np.asarray(p.obs, float), None, ("huber", p.huber_delta) if huber else None)
+    loss = ("huber", p.huber_delta) if huber else None
+    keep = np.ones(len(p.kf_idx), bool) if mono is None else ~np.asarray(mono, bool)
+    ids = np.stack([p.kf_idx, p.pt_idx], axis=1)
+    obs = np.asarray(p.obs, float)
+    sets = []
+    if keep.any():
+        sets.append(lm.EdgeSet("stereo", ["nav", "pt"], ids[keep], cam.evaluate, obs[keep], None, loss))
+    if mono is not None and (~keep).any():
+        sets.append(lm.EdgeSet("mono", ["nav", "pt"], ids[~keep], mono_evaluate(cam), obs[~keep, :2], None, loss))
     ij = np.stack([np.arange(K - 1), np.arange(1, K)], axis=1)
     U = np.stack([np.linalg.cholesky(np.linalg.inv(pm["cov"])).T for pm in pims])
     imu = lm.EdgeSet("imu", ["nav", "nav"], ij, imu_evaluate(pims), np.arange(K - 1), U,
@@ -318,4 +336,4 @@ def problem(p, nav, pts, pims, prior_sigma=(1e-2, 1e-1), huber=True, imu_huber=N
     pw = np.diag(np.r_[np.full(3, 1.0 / prior_sigma[0]), np.full(3, 1.0 / prior_sigma[1])])
     prior = lm.EdgeSet("bias_prior", ["nav"], np.array([[0]]), bias_prior_evaluate,
                        np.zeros((1, 6)), pw[None], None)
-    return lm.Problem(vs, [st, imu, rw, prior])
+    return lm.Problem(vs, sets + [imu, rw, prior])

@@ -1019,11 +1019,16 @@ gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig) {
   return GPO_OK;
 }
 
-// Observation edges (camera, point) of the graph's camera kind.
+// Observation edges (camera, point) of the graph's camera kind.  A monocular edge is
+// stored as a stereo edge whose third residual row is whitened to zero: observation
+// (u, v, 0) and the square root of its 2 x 2 information embedded with a zero third
+// row, so the stereo kernels evaluate it unchanged.
 static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* ids, const double* meas,
                                 const double* info, int32_t loss_kind, double loss_delta) {
+  const bool mono = kind == GPO_E_MONO;
   const int ck = kind == GPO_E_BA_REPROJ ? GPO_V_BA_CAMERA9 : GPO_V_NAV15;
   const int m = kind == GPO_E_BA_REPROJ ? 2 : 3, nq = tri(m);
+  const int mu = mono ? 2 : m;   // the caller's residual size
   if (g->cam_kind >= 0 && g->cam_kind != ck)
     return fail(g, GPO_ERR_ARG, "edge kind %d does not fit the graph's camera kind %d", kind, g->cam_kind);
   if (n > 0 && !meas) return fail(g, GPO_ERR_ARG, "null measurements");
@@ -1037,12 +1042,15 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
   }
   std::vector<double> packed;   // packed upper square roots of the information, if given
   bool non_identity = false;
-  if (info) {
+  if (info || mono) {
     packed.resize((size_t)nq * n);
     for (int64_t i = 0; i < n; ++i) {
-      double U[9];
-      if (!sqrt_info(info + (size_t)m * m * i, m, U))
+      double Uu[9], U[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int k = 0; k < mu * mu; ++k) Uu[k] = (k % (mu + 1)) == 0 ? 1.0 : 0.0;   // identity, mu x mu
+      if (info && !sqrt_info(info + (size_t)mu * mu * i, mu, Uu))
         return fail(g, GPO_ERR_ARG, "edge %lld: information matrix is not symmetric positive definite", (long long)i);
+      for (int a = 0; a < mu; ++a)
+        for (int b = 0; b < mu; ++b) U[a * m + b] = Uu[a * mu + b];   // mono: third row stays zero
       int t = 0;
       for (int a = 0; a < m; ++a)
         for (int b = a; b < m; ++b, ++t) {
@@ -1058,7 +1066,15 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
   g->e_eid.resize(base + n);
   g->e_delta.resize(base + n, loss_kind == GPO_LOSS_HUBER ? loss_delta : 0.0);
   g->e_active.resize(base + n, 1);
-  g->e_obs.insert(g->e_obs.end(), meas, meas + (size_t)m * n);
+  if (mono) {
+    for (int64_t i = 0; i < n; ++i) {
+      g->e_obs.push_back(meas[2 * i]);
+      g->e_obs.push_back(meas[2 * i + 1]);
+      g->e_obs.push_back(0.0);
+    }
+  } else {
+    g->e_obs.insert(g->e_obs.end(), meas, meas + (size_t)m * n);
+  }
   for (int64_t i = 0; i < n; ++i) {
     g->e_cam[base + i] = (int32_t)g->v_local[ids[2 * i]];
     g->e_pt[base + i] = (int32_t)g->v_local[ids[2 * i + 1]];
@@ -1073,7 +1089,7 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
         for (int b = a; b < m; ++b, ++t) g->e_sqinfo[(size_t)nq * e + t] = a == b ? 1.0 : 0.0;
   }
   if (g->any_info) {
-    if (info) {
+    if (info || mono) {
       g->e_sqinfo.insert(g->e_sqinfo.end(), packed.begin(), packed.end());
     } else {
       for (int64_t i = 0; i < n; ++i)
@@ -1150,13 +1166,13 @@ gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* v
                          const double* info, int32_t loss_kind, double loss_delta, int64_t* first_id) {
   if (!g) return GPO_ERR_ARG;
   if (g->finalized) return fail(g, GPO_ERR_STATE, "topology is frozen after the first optimize");
-  if (kind < GPO_E_BA_REPROJ || kind > GPO_E_BIAS_PRIOR) return fail(g, GPO_ERR_ARG, "unknown edge kind %d", kind);
+  if (kind < GPO_E_BA_REPROJ || kind > GPO_E_MONO) return fail(g, GPO_ERR_ARG, "unknown edge kind %d", kind);
   if (n < 0 || (n > 0 && !vertex_ids)) return fail(g, GPO_ERR_ARG, "null ids or negative count");
   if (loss_kind != GPO_LOSS_NONE && loss_kind != GPO_LOSS_HUBER) return fail(g, GPO_ERR_ARG, "unknown loss %d", loss_kind);
   if (loss_kind == GPO_LOSS_HUBER && !(loss_delta > 0.0 && std::isfinite(loss_delta)))
     return fail(g, GPO_ERR_ARG, "Huber threshold must be positive and finite");
   const int64_t first = (int64_t)g->ed_kind.size();
-  const gpo_status s = (kind == GPO_E_BA_REPROJ || kind == GPO_E_STEREO)
+  const gpo_status s = (kind == GPO_E_BA_REPROJ || kind == GPO_E_STEREO || kind == GPO_E_MONO)
                            ? add_obs_edges(g, kind, n, vertex_ids, meas, info, loss_kind, loss_delta)
                            : add_nav_edges(g, kind, n, vertex_ids, meas, info, loss_kind, loss_delta);
   if (s == GPO_OK && first_id) *first_id = first;
@@ -1178,7 +1194,7 @@ gpo_status gpo_set_edge_active(gpo_graph* g, int64_t eid, int32_t active) {
   if (g->finalized) return fail(g, GPO_ERR_STATE, "edge activity is frozen after the first optimize");
   if (eid < 0 || eid >= (int64_t)g->ed_kind.size()) return fail(g, GPO_ERR_ARG, "no edge %lld", (long long)eid);
   const int k = g->ed_kind[eid];
-  if (k == GPO_E_BA_REPROJ || k == GPO_E_STEREO) g->e_active[g->ed_local[eid]] = active ? 1 : 0;
+  if (k == GPO_E_BA_REPROJ || k == GPO_E_STEREO || k == GPO_E_MONO) g->e_active[g->ed_local[eid]] = active ? 1 : 0;
   else g->x_active[g->ed_local[eid]] = active ? 1 : 0;
   g->prep.reset();
   return GPO_OK;

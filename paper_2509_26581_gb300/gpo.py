@@ -21,7 +21,7 @@ GPO_ERR_CUDA, GPO_ERR_TIMEOUT, GPO_ERR_UNSUPPORTED = -5, -6, -7
 GPO_SOLVER_SCHUR, GPO_SOLVER_FULL = 0, 1
 GPO_FP64, GPO_FP32, GPO_FP32_BF16 = 0, 1, 2
 GPO_V_BA_CAMERA9, GPO_V_POINT3, GPO_V_NAV15 = 0, 1, 2
-GPO_E_BA_REPROJ, GPO_E_STEREO, GPO_E_IMU, GPO_E_BIAS_RW, GPO_E_BIAS_PRIOR = 0, 1, 2, 3, 4
+GPO_E_BA_REPROJ, GPO_E_STEREO, GPO_E_IMU, GPO_E_BIAS_RW, GPO_E_BIAS_PRIOR, GPO_E_MONO = 0, 1, 2, 3, 4, 5
 GPO_IMU_MEAS_LEN = 67
 GPO_LOSS_NONE, GPO_LOSS_HUBER = 0, 1
 PRECISIONS = {"fp64": GPO_FP64, "fp32": GPO_FP32, "bf16": GPO_FP32_BF16}
@@ -479,14 +479,16 @@ def stereo_rig(camera: dict) -> np.ndarray:
 
 
 def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), huber=True, imu=None,
-             imu_huber=None, **kw):
+             imu_huber=None, mono=None, **kw):
     """Builds the visual-inertial graph of a VIProblem-like record: navigation states get
     ids [0, K), landmarks [K, K + P); edges in this order: stereo (Huber), inertial between
     consecutive keyframes (preintegrated by the library at the initial biases of the first
     keyframe of each pair), bias random walk (information diag 1 / (sigma^2 T)), and a
     zero bias prior on keyframe 0 (information diag 1 / prior_sigma^2).  imu = (records
-    (K-1, GPO_IMU_MEAS_LEN), information (K-1, 9, 9)) supplies the inertial edges instead.
-    Returns (graph, first navigation id, first landmark id, edge-id ranges by kind)."""
+    (K-1, GPO_IMU_MEAS_LEN), information (K-1, 9, 9)) supplies the inertial edges instead;
+    imu_huber puts a Huber loss of that threshold on them; mono (a boolean mask over the
+    observations) adds the masked ones as monocular left-camera edges, after the stereo
+    ones.  Returns (graph, first navigation id, first landmark id, edge-id ranges by kind)."""
     nav = p.nav0 if nav is None else nav
     pts = p.pts0 if pts is None else pts
     kw = _tuned(kw, len(p.kf_idx), precision, "vi")
@@ -497,9 +499,14 @@ def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), 
     g.set_stereo_camera(stereo_rig(p.camera))
     ids = np.stack([np.asarray(p.kf_idx, np.int64) + n0, np.asarray(p.pt_idx, np.int64) + p0], axis=1)
     ranges = {}
-    e0 = g.add_edges(GPO_E_STEREO, ids, p.obs, None, GPO_LOSS_HUBER if huber else GPO_LOSS_NONE,
-                     float(p.huber_delta) if huber else 0.0)
-    ranges["stereo"] = (e0, e0 + ids.shape[0])
+    keep = np.ones(ids.shape[0], bool) if mono is None else ~np.asarray(mono, bool)
+    lk, ld = (GPO_LOSS_HUBER, float(p.huber_delta)) if huber else (GPO_LOSS_NONE, 0.0)
+    obs = np.asarray(p.obs, np.float64)
+    e0 = g.add_edges(GPO_E_STEREO, ids[keep], obs[keep], None, lk, ld)
+    ranges["stereo"] = (e0, e0 + int(keep.sum()))
+    if not keep.all():   # monocular edges: the left camera's two pixels
+        e0 = g.add_edges(GPO_E_MONO, ids[~keep], obs[~keep, :2], None, lk, ld)
+        ranges["mono"] = (e0, e0 + int((~keep).sum()))
     if K > 1:
         if imu is not None:
             meas, info = (np.asarray(a, np.float64) for a in imu)

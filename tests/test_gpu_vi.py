@@ -232,6 +232,29 @@ def test_huber_inertial_edges_match_the_oracle(gpo, small):
     assert plain.cost() > rep.initial_cost   # rho(s) < s beyond the threshold
 
 
+def test_monocular_edges_match_the_oracle(gpo, small):
+    """A third of the observations as monocular (left camera) edges beside stereo ones:
+    their rows against the oracle's (the first two stereo rows; the stored third row is
+    whitened to zero), the initial cost to 1e-12 and the LM run's final cost to 1e-9."""
+    p, pims = small
+    mono = np.zeros(len(p.kf_idx), bool)
+    mono[::3] = True
+    g, _, _, rg = gpo.vi_graph(p, precision="fp64", imu=_records(pims), mono=mono)
+    a, b = rg["mono"]
+    r, J = g.debug_linearize_edges(np.arange(a, b), nav=True)
+    cam = ovi.camera_of(p.camera)
+    ro, (Jn, Jp) = ovi.mono_evaluate(cam)((p.nav0[p.kf_idx[mono]], p.pts0[p.pt_idx[mono]]), p.obs[mono, :2])
+    w = np.sqrt(robust.weight(np.sum(ro * ro, axis=1), ("huber", p.huber_delta)))
+    assert _rel_rows(r[:, :2], ro * w[:, None]) < 1e-12 and np.all(r[:, 2:] == 0)
+    Jg = np.concatenate([J[:, :2, :15], J[:, :2, 15:18]], axis=2)
+    assert _rel_rows(Jg, np.concatenate([Jn, Jp], axis=2) * w[:, None, None]) < 1e-12
+    assert np.all(J[:, 2:] == 0)
+    rep = g.optimize(15, _parity_params(gpo))
+    _, orep = olm.levenberg_marquardt(ovi.problem(p, p.nav0, p.pts0, pims, mono=mono), 15)
+    assert abs(rep.initial_cost - orep.initial_cost) <= 1e-12 * orep.initial_cost
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
+
+
 def test_fixed_keyframe_and_disabled_edges(gpo, small):
     p, pims = small
     g, n0, p0, rg = _graph(gpo, p, pims)

@@ -162,3 +162,21 @@ def test_huber_inertial_edges_reduce_to_the_plain_and_the_huber_forms(small):
     assert (s > delta ** 2).any() and (s <= delta ** 2).any()
     for k in (0, 2, 3):
         assert np.array_equal(hub[k], c0[k])
+
+
+def test_monocular_edges_are_the_left_camera_rows(small):
+    """The monocular edge is the stereo residual's first two rows (left camera), with the
+    matching Jacobian rows (central differences pin the stereo ones); a problem with
+    every observation monocular sums their squared norms."""
+    p = small
+    cam = vi.camera_of(p.camera)
+    states = (p.nav0[p.kf_idx], p.pts0[p.pt_idx])
+    r3, (Jn3, Jp3) = cam.evaluate(states, np.asarray(p.obs, float))
+    r2, (Jn2, Jp2) = vi.mono_evaluate(cam)(states, np.asarray(p.obs, float)[:, :2])
+    assert np.array_equal(r2, r3[:, :2])
+    assert np.array_equal(Jn2, Jn3[:, :2]) and np.array_equal(Jp2, Jp3[:, :2])
+    pims = vi.preintegrate_all(p)
+    allmono = vi.problem(p, p.nav0, p.pts0, pims, huber=False, mono=np.ones(len(p.kf_idx), bool))
+    assert [e.name for e in allmono.edges] == ["mono", "imu", "bias_rw", "bias_prior"]
+    costs = lm.edge_costs(allmono)
+    assert np.allclose(costs[0], 0.5 * np.sum(r2 * r2, axis=1), rtol=1e-15, atol=0)
