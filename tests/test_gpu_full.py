@@ -120,3 +120,38 @@ def test_full_and_schur_forms_agree_on_visual_inertial(gpo):
         params = gpo.default_params(pcg_max_iters=3000, pcg_tol=1e-12, pcg_rejection_ratio=0.0, solver=solver)
         costs.append(g.optimize(15, params).final_cost)
     assert abs(costs[1] - costs[0]) <= 1e-9 * costs[0]
+
+
+def test_full_system_fixed_and_disabled_vertices(gpo):
+    """A fixed camera, a fixed point and a point that loses every observation stay where
+    they are, and the run matches the oracle (whose exact steps eliminate them)."""
+    p = synth.ba_ring(4, 8, 200, 5)
+    cam_fixed = np.zeros(p.n_cams, bool)
+    cam_fixed[0] = True
+    pt_fixed = np.zeros(p.n_pts, bool)
+    pt_fixed[5] = True
+    active = np.ones(p.n_edges, bool)
+    active[p.pt_idx == 9] = False
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64",
+                             cam_fixed=cam_fixed, pt_fixed=pt_fixed, active=active)
+    rep = g.optimize(10, _full_params(gpo))
+    cams, pts = g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)
+    assert np.array_equal(cams[0], p.cams0[0])
+    assert np.array_equal(pts[5], p.pts0[5]) and np.array_equal(pts[9], p.pts0[9])
+    prob = olm.ba_problem(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, cam_fixed=cam_fixed,
+                          pt_fixed=pt_fixed, active=active)
+    _, orep = olm.levenberg_marquardt(prob, 10)
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
+
+
+def test_batched_solves_use_the_schur_form(gpo):
+    """Graphs solved together share launches in the Schur form: asking for the full
+    system there gives the Schur results bit for bit."""
+    from paper_2509_26581_gb300 import serving
+    wins = synth.window_pool(5, 3, kf=(5, 8), pts=(200, 600))
+    out = []
+    for solver in (gpo.GPO_SOLVER_SCHUR, gpo.GPO_SOLVER_FULL):
+        built = [serving.window_graph(w, "fp32") for w in wins]
+        reps = gpo.optimize_batch([b[0] for b in built], 4, gpo.default_params(solver=solver))
+        out.append([(r.final_cost, r.pcg_iters_total) for r in reps])
+    assert out[0] == out[1]

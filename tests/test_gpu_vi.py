@@ -255,6 +255,21 @@ def test_monocular_edges_match_the_oracle(gpo, small):
     assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_monocular_edges_mixed_precision_close_to_fp64(gpo, prec):
+    """Stereo and monocular edges together in the mixed forms: within 1e-6 of FP64 after
+    the run converges (the setting of the stereo-only mixed test)."""
+    p = synth.vi_problem(6, n_kf=12, n_pts=400)
+    mono = np.zeros(len(p.kf_idx), bool)
+    mono[1::3] = True
+    prm = gpo.default_params(pcg_max_iters=500, pcg_tol=1e-10, pcg_rejection_ratio=0.0)
+    costs = {}
+    for pr in ("fp64", prec):
+        g, _, _, _ = gpo.vi_graph(p, precision=pr, mono=mono)
+        costs[pr] = g.optimize(30, prm).final_cost
+    assert abs(costs[prec] - costs["fp64"]) <= 1e-6 * costs["fp64"]
+
+
 def test_fixed_keyframe_and_disabled_edges(gpo, small):
     p, pims = small
     g, n0, p0, rg = _graph(gpo, p, pims)
