@@ -168,7 +168,8 @@ typedef struct {
                                  An exact solve of either gives the same step; the
                                  tolerance and iteration cap apply to the solved system's
                                  residual.  The full form allocates seven [P][3] vectors
-                                 on its first use (counted by gpo_memory_footprint).
+                                 on its first use (counted by gpo_memory_footprint and
+                                 held to the graph's memory budget: GPO_ERR_OOM).
                                  Graphs without cameras, and graphs solved together
                                  (gpo_optimize_batch, a server), use the Schur form. */
 } gpo_lm_params;

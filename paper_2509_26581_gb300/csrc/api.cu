@@ -778,6 +778,9 @@ static gpo_status ensure_full(gpo_graph* g) {
   const size_t vec = (3 * std::max<size_t>(P, 1) * sA + 255) & ~(size_t)255;
   const size_t npb = std::max<size_t>((P + 255) / 256, 1);
   const size_t bytes = 7 * vec + 2 * npb * sizeof(double);
+  if (g->desc.memory_budget && g->arena_bytes + bytes > g->desc.memory_budget)
+    return fail(g, GPO_ERR_OOM, "the full-system solver needs %zu bytes more, beyond the budget of %zu", bytes,
+                (size_t)g->desc.memory_budget);
   void* b = nullptr;
   if (g->desc.alloc && g->desc.free) {
     b = g->desc.alloc(bytes, g->desc.alloc_ctx);
