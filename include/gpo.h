@@ -428,6 +428,37 @@ gpo_status gpo_ba_cost_noalloc(int32_t device, void* cuda_stream, const double* 
                                double huber_delta, double* cost_out);
 
 /* ---------------------------------------------------------------------------
+ * Generic edge kinds (Sec. III: a constraint is declared by its residual over its
+ * vertices; the library differentiates it in forward mode).  Kinds are compiled into
+ * the library; a generic graph has n vertices of one dimension (2 for the kinds below)
+ * and is solved by LM with block-Jacobi PCG on the full damped system, in FP64 (the
+ * damping, PCG and Huber options of gpo_lm_params apply).  The circle kind is the
+ * paper's running example: points pulled onto a circle.
+ * ------------------------------------------------------------------------ */
+enum {
+  GPO_GE_CIRCLE = 0,    /* arity 1, meas [R]: r = x^2 + y^2 - R^2 */
+  GPO_GE_DISTANCE = 1   /* arity 2, meas [d]: r = |x_i - x_j|^2 - d^2 */
+};
+typedef struct gpo_generic gpo_generic;
+/* x0: n_vertices * vertex_dim doubles (copied).  cuda_stream NULL: an own stream.
+ * Errors: GPO_ERR_ARG (vertex_dim != 2, n_vertices out of range, bad device),
+ * GPO_ERR_OOM, GPO_ERR_CUDA. */
+gpo_status gpo_generic_create(int32_t vertex_dim, int64_t n_vertices, const double* x0, int32_t device,
+                              void* cuda_stream, gpo_generic** out);
+gpo_status gpo_generic_destroy(gpo_generic* g);
+/* n edges of a registered kind: vertex_ids n * arity, meas n * (kind's length);
+ * loss as in gpo_add_edges.  Edge ids continue across calls. */
+gpo_status gpo_generic_add_edges(gpo_generic* g, int32_t kind, int64_t n, const int64_t* vertex_ids,
+                                 const double* meas, int32_t loss_kind, double loss_delta, int64_t* first_id);
+gpo_status gpo_generic_set_fixed(gpo_generic* g, int64_t vertex_id, int32_t fixed);
+gpo_status gpo_generic_set_edge_active(gpo_generic* g, int64_t edge_id, int32_t active);
+/* max_iters LM iterations (Nielsen damping, gain ratio in FP64); the states are kept
+ * between calls.  Errors: GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_CUDA. */
+gpo_status gpo_generic_optimize(gpo_generic* g, int32_t max_iters, const gpo_lm_params* params, gpo_report* out);
+/* out: n_vertices * vertex_dim doubles. */
+gpo_status gpo_generic_get_state(gpo_generic* g, double* out);
+
+/* ---------------------------------------------------------------------------
  * FP64 throughput probe (measurement).  The linearisation and cost kernels evaluate
  * the geometry, residuals and cost in FP64 (the state, retraction and cost are FP64 in
  * every precision mode), so their roofline is the FP64 pipe, whose rate this measures.

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgpo.so")
-SOURCES = ["ba_kernels.cu", "vi_kernels.cu", "api.cu", "batch.cu", "noalloc.cu", "peak.cu", "imu.cpp"]
+SOURCES = ["ba_kernels.cu", "vi_kernels.cu", "api.cu", "batch.cu", "noalloc.cu", "peak.cu", "generic.cu", "imu.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

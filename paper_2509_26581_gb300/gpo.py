@@ -121,6 +121,13 @@ _SIGS = {
     "gpo_debug_wait_timeout": (C.c_int, [_P]),
     "gpo_debug_autodiff_edges": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "gpo_fp64_fma_probe": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
+    "gpo_generic_create": (C.c_int, [C.c_int32, C.c_int64, _P, C.c_int32, _P, C.POINTER(_P)]),
+    "gpo_generic_destroy": (C.c_int, [_P]),
+    "gpo_generic_add_edges": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, C.c_int32, C.c_double, _PI64]),
+    "gpo_generic_set_fixed": (C.c_int, [_P, C.c_int64, C.c_int32]),
+    "gpo_generic_set_edge_active": (C.c_int, [_P, C.c_int64, C.c_int32]),
+    "gpo_generic_optimize": (C.c_int, [_P, C.c_int32, C.POINTER(gpo_lm_params), C.POINTER(gpo_report)]),
+    "gpo_generic_get_state": (C.c_int, [_P, _P]),
 }
 
 
@@ -359,6 +366,57 @@ def fp64_fma_probe(stream, n_ctas: int, iters: int, out) -> None:
     stream handle or 0) writing n_ctas * 256 doubles to the device tensor `out`; one
     launch performs n_ctas * 256 * iters * 32 FMAs."""
     _check(lib.gpo_fp64_fma_probe(stream, n_ctas, iters, out.data_ptr()))
+
+
+GPO_GE_CIRCLE, GPO_GE_DISTANCE = 0, 1
+
+
+class Generic:
+    """A graph of 2-dim vertices with edges of the library's generic kinds
+    (gpo_generic_*: residuals differentiated in forward mode)."""
+
+    def __init__(self, x0, device: int = 0, stream=None):
+        x = np.ascontiguousarray(x0, dtype=np.float64)
+        self.n, self.dim = x.shape
+        h = _P()
+        _check(lib.gpo_generic_create(self.dim, self.n, _ptr(x), device, stream, C.byref(h)))
+        self.h = h
+
+    def add_edges(self, kind: int, vertex_ids, meas, loss_kind: int = GPO_LOSS_NONE, loss_delta: float = 0.0) -> int:
+        ids = np.ascontiguousarray(vertex_ids, dtype=np.int64)
+        m = np.ascontiguousarray(meas, dtype=np.float64)
+        first = C.c_int64()
+        _check(lib.gpo_generic_add_edges(self.h, kind, ids.shape[0], _ptr(ids), _ptr(m), loss_kind, loss_delta,
+                                         C.byref(first)))
+        return first.value
+
+    def set_fixed(self, vid: int, fixed: bool = True):
+        _check(lib.gpo_generic_set_fixed(self.h, vid, int(fixed)))
+
+    def set_edge_active(self, eid: int, active: bool):
+        _check(lib.gpo_generic_set_edge_active(self.h, eid, int(active)))
+
+    def optimize(self, max_iters: int, params: gpo_lm_params | None = None) -> gpo_report:
+        rep = gpo_report()
+        _check(lib.gpo_generic_optimize(self.h, max_iters, None if params is None else C.byref(params),
+                                        C.byref(rep)))
+        return rep
+
+    def state(self) -> np.ndarray:
+        out = np.empty((self.n, self.dim))
+        _check(lib.gpo_generic_get_state(self.h, _ptr(out)))
+        return out
+
+    def close(self):
+        if self.h:
+            lib.gpo_generic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
