@@ -238,6 +238,17 @@ gpo_status gpo_add_edges(gpo_graph* g, int32_t kind, int64_t n, const int64_t* v
  * edges.  Errors: GPO_ERR_ARG (null), GPO_ERR_STATE (after the first optimize). */
 gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig);
 
+/* Makes both cameras of the stereo rig Kannala-Brandt (equidistant) fisheye cameras
+ * with coefficients k[4] = [k1 k2 k3 k4] (the fisheye descriptor of the paper's VI
+ * system): for X_c = (x, y, z), theta = atan2(|(x, y)|, z),
+ * theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8), and the
+ * projection (fx theta_d x / r + cx, fy theta_d y / r + cy) replaces (fx x / z + cx,
+ * fy y / z + cy) in the stereo and monocular residuals (the right camera's point is
+ * (x - baseline, y, z)).  Call after gpo_set_stereo_camera (which resets to pinhole).
+ * Errors: GPO_ERR_ARG (null, not finite), GPO_ERR_STATE (no rig yet, or after the first
+ * optimize). */
+gpo_status gpo_set_fisheye(gpo_graph* g, const double* k);
+
 /* On-manifold IMU preintegration (Forster et al., T-RO 2017) of n gyroscope and
  * accelerometer samples gyro[n][3] (rad/s), acc[n][3] (m/s^2) taken every dt seconds,
  * at bias estimates bg0[3], ba0[3], with white-noise densities sigma_g, sigma_a:

@@ -107,11 +107,42 @@ def retract_nav(x: np.ndarray, d: np.ndarray) -> np.ndarray:
 
 # ---------------------------------------------------------------- stereo reprojection
 
+def kb_project(x, y, z, fx, fy, cx, cy, k):
+    """Kannala-Brandt (equidistant) fisheye projection of camera-frame points and its
+    Jacobian d(u, v)/d(x, y, z): theta = atan2(r, z), r = |(x, y)|,
+    theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8),
+    (u, v) = (fx theta_d x / r + cx, fy theta_d y / r + cy)."""
+    k1, k2, k3, k4 = k
+    r = np.sqrt(x * x + y * y)
+    th = np.arctan2(r, z)
+    t2 = th * th
+    thd = th * (1 + t2 * (k1 + t2 * (k2 + t2 * (k3 + t2 * k4))))
+    dthd = 1 + t2 * (3 * k1 + t2 * (5 * k2 + t2 * (7 * k3 + t2 * 9 * k4)))
+    s = thd / r
+    q = r * r + z * z
+    dth = np.stack([x * z / (r * q), y * z / (r * q), -r / q], axis=-1)      # dtheta/d(x, y, z)
+    ds = dthd[..., None] * dth / r[..., None]
+    ds[..., 0] -= thd * x / r ** 3
+    ds[..., 1] -= thd * y / r ** 3
+    u = fx * s * x + cx
+    v = fy * s * y + cy
+    J = np.zeros(x.shape + (2, 3))
+    J[..., 0, :] = fx * x[..., None] * ds
+    J[..., 0, 0] += fx * s
+    J[..., 1, :] = fy * y[..., None] * ds
+    J[..., 1, 1] += fy * s
+    return u, v, J
+
+
 class StereoCamera:
-    def __init__(self, fx, fy, cx, cy, baseline, R_cb, t_cb):
+    """Pinhole stereo rig, or Kannala-Brandt fisheye when `fisheye` holds k1..k4 (both
+    cameras, the right one `baseline` along x)."""
+
+    def __init__(self, fx, fy, cx, cy, baseline, R_cb, t_cb, fisheye=None):
         self.fx, self.fy, self.cx, self.cy, self.b = fx, fy, cx, cy, baseline
         self.R_cb = np.asarray(R_cb, dtype=np.float64)
         self.t_cb = np.asarray(t_cb, dtype=np.float64)
+        self.fisheye = None if fisheye is None else np.asarray(fisheye, dtype=np.float64)
 
     def point_in_camera(self, nav, X):
         R, p, _, _, _ = nav_parts(nav)
@@ -121,6 +152,10 @@ class StereoCamera:
     def project(self, nav, X):
         _, Xc = self.point_in_camera(nav, X)
         x, y, z = Xc[:, 0], Xc[:, 1], Xc[:, 2]
+        if self.fisheye is not None:
+            ul, vl, _ = kb_project(x, y, z, self.fx, self.fy, self.cx, self.cy, self.fisheye)
+            ur, _, _ = kb_project(x - self.b, y, z, self.fx, self.fy, self.cx, self.cy, self.fisheye)
+            return np.stack([ul, vl, ur], axis=1)
         return np.stack([self.fx * x / z + self.cx, self.fy * y / z + self.cy,
                          self.fx * (x - self.b) / z + self.cx], axis=1)
 
@@ -133,12 +168,18 @@ class StereoCamera:
         r = self.project(nav, X) - obs
         n = len(z)
         D = np.zeros((n, 3, 3))          # dr / dX_c
-        D[:, 0, 0] = self.fx / z
-        D[:, 0, 2] = -self.fx * x / z ** 2
-        D[:, 1, 1] = self.fy / z
-        D[:, 1, 2] = -self.fy * y / z ** 2
-        D[:, 2, 0] = self.fx / z
-        D[:, 2, 2] = -self.fx * (x - self.b) / z ** 2
+        if self.fisheye is not None:
+            _, _, Jl = kb_project(x, y, z, self.fx, self.fy, self.cx, self.cy, self.fisheye)
+            _, _, Jr = kb_project(x - self.b, y, z, self.fx, self.fy, self.cx, self.cy, self.fisheye)
+            D[:, 0:2] = Jl
+            D[:, 2] = Jr[:, 0]
+        else:
+            D[:, 0, 0] = self.fx / z
+            D[:, 0, 2] = -self.fx * x / z ** 2
+            D[:, 1, 1] = self.fy / z
+            D[:, 1, 2] = -self.fy * y / z ** 2
+            D[:, 2, 0] = self.fx / z
+            D[:, 2, 2] = -self.fx * (x - self.b) / z ** 2
         DR = D @ self.R_cb
         Jn = np.zeros((n, 3, 15))
         Jn[:, :, 0:3] = DR @ so3.hat(Xb)      # dX_b/dtheta = [X_b]x
@@ -290,7 +331,7 @@ def mono_evaluate(cam: StereoCamera):
 
 def camera_of(cam: dict) -> StereoCamera:
     return StereoCamera(cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["baseline"], cam["R_cb"],
-                        cam["t_cb"])
+                        cam["t_cb"], cam.get("fisheye"))
 
 
 def preintegrate_all(p, bg0=None, ba0=None):

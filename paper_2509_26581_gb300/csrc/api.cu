@@ -1009,6 +1009,19 @@ gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int6
   return GPO_OK;
 }
 
+gpo_status gpo_set_fisheye(gpo_graph* g, const double* k) {
+  if (!g) return GPO_ERR_ARG;
+  if (!k) return fail(g, GPO_ERR_ARG, "null coefficients");
+  if (g->finalized) return fail(g, GPO_ERR_STATE, "the rig is frozen after the first optimize");
+  if (!g->camk_set) return fail(g, GPO_ERR_STATE, "set the stereo rig first");
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(k[i])) return fail(g, GPO_ERR_ARG, "coefficient %d is not finite", i);
+  g->camk[17] = 1.0;
+  for (int i = 0; i < 4; ++i) g->camk[18 + i] = k[i];
+  g->prep.reset();
+  return GPO_OK;
+}
+
 gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig) {
   if (!g) return GPO_ERR_ARG;
   if (!rig) return fail(g, GPO_ERR_ARG, "null rig");

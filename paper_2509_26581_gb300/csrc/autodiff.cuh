@@ -92,6 +92,39 @@ __device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b)
   return c;
 }
 
+template <int N>
+__device__ __forceinline__ Dual<N> dsqrt(const Dual<N>& a) {
+  Dual<N> c;
+  c.v = sqrt(a.v);
+  const double h = 0.5 / c.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) c.g[i] = a.g[i] * h;
+  return c;
+}
+// atan2(y, x): derivative (x dy - y dx) / (x^2 + y^2)
+template <int N>
+__device__ __forceinline__ Dual<N> datan2(const Dual<N>& y, const Dual<N>& x) {
+  Dual<N> c;
+  c.v = atan2(y.v, x.v);
+  const double q = 1.0 / (x.v * x.v + y.v * y.v);
+#pragma unroll
+  for (int i = 0; i < N; ++i) c.g[i] = (x.v * y.g[i] - y.v * x.g[i]) * q;
+  return c;
+}
+
+// Kannala-Brandt fisheye projection (u, v) of a camera-frame point on duals.
+template <int N>
+__device__ void kb_project_ad(const double* camk, const Dual<N>& x, const Dual<N>& y, const Dual<N>& z,
+                              Dual<N>& u, Dual<N>& v) {
+  const double k1 = camk[18], k2 = camk[19], k3 = camk[20], k4 = camk[21];
+  const Dual<N> r = dsqrt(x * x + y * y);
+  const Dual<N> th = datan2(r, z), t2 = th * th;
+  const Dual<N> poly = t2 * (t2 * (t2 * (k4 * t2 + k3) + k2) + k1) + 1.0;
+  const Dual<N> s = (th * poly) / r;
+  u = camk[0] * (s * x) + camk[2];
+  v = camk[1] * (s * y) + camk[3];
+}
+
 // BA reprojection on duals: variables 0..8 the camera tangent (left rotation update dw,
 // translation, f, k1, k2), 9..11 the point.  P = (I + [dw]_x) R X + t, p = -P_xy / P_z,
 // u = f (1 + k1 |p|^2 + k2 |p|^4) p, r = u - z.
@@ -140,6 +173,15 @@ __device__ void stereo_residual_ad(const DevBA& d, const double* rb, const doubl
   for (int i = 0; i < 3; ++i)
     xc[i] = (Rc[3 * i] * xb[0] + Rc[3 * i + 1] * xb[1] + Rc[3 * i + 2] * xb[2]) + d.camk[14 + i];
   const double fx = d.camk[0], fy = d.camk[1], cx = d.camk[2], cy = d.camk[3], b = d.camk[4];
+  if (d.camk[17] != 0.0) {   // fisheye rig
+    Dual<N> u, v, ur, vr;
+    kb_project_ad<N>(d.camk, xc[0], xc[1], xc[2], u, v);
+    kb_project_ad<N>(d.camk, xc[0] + (-b), xc[1], xc[2], ur, vr);
+    r[0] = u + (-z[0]);
+    r[1] = v + (-z[1]);
+    r[2] = ur + (-z[2]);
+    return;
+  }
   r[0] = fx * (xc[0] / xc[2]) + (cx - z[0]);
   r[1] = fy * (xc[1] / xc[2]) + (cy - z[1]);
   r[2] = fx * ((xc[0] + (-b)) / xc[2]) + (cx - z[2]);

@@ -92,7 +92,8 @@ struct DevBA {
   int C, P, E, NCH, NS;
   int NX;                    // extra (camera-side) edges
   int model;                 // ModelKind
-  double camk[20];           // stereo rig: fx fy cx cy baseline, R_cb (9, row-major), t_cb (3)
+  double camk[24];           // stereo rig: fx fy cx cy baseline, R_cb (9, row-major), t_cb (3),
+                             // [17] projection (0 pinhole, 1 Kannala-Brandt fisheye), [18..21] k1..k4
   // topology (point-major edge order)
   const int* e_cam;          // [E]
   const int* e_pt;           // [E]

@@ -77,7 +77,7 @@ struct gpo_graph {
   std::vector<int64_t> x_eid;
   std::vector<double> x_rec;       // [NX][kXRec]
   std::vector<uint8_t> x_active;
-  double camk[20] = {};            // stereo rig
+  double camk[24] = {};            // stereo rig (and fisheye coefficients)
   bool camk_set = false;
 
   // finalized topology

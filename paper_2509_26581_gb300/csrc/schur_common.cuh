@@ -486,6 +486,48 @@ struct ModelBA {
 
 // ---------------------------------------------------------------- stereo / navigation model
 
+// Kannala-Brandt (equidistant) fisheye projection of a camera-frame point by the rig's
+// intrinsics and coefficients k1..k4 (camk[18..21]): theta = atan2(r, z), r = |(x, y)|,
+// theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8),
+// (u, v) = (fx theta_d x / r + cx, fy theta_d y / r + cy); with D also d(u, v)/d(x, y, z).
+// On the optical axis (r = 0) the model's limit is the pinhole projection.
+__device__ __forceinline__ void kb_project(const double* camk, double x, double y, double z, double& u,
+                                          double& v, double (*D)[3]) {
+  const double fx = camk[0], fy = camk[1], cx = camk[2], cy = camk[3];
+  const double k1 = camk[18], k2 = camk[19], k3 = camk[20], k4 = camk[21];
+  const double r = sqrt(x * x + y * y);
+  if (!(r > 1e-12 * fabs(z))) {
+    const double iz = 1.0 / z;
+    u = fx * x * iz + cx;
+    v = fy * y * iz + cy;
+    if (D) {
+      D[0][0] = fx * iz; D[0][1] = 0.0; D[0][2] = -fx * x * iz * iz;
+      D[1][0] = 0.0; D[1][1] = fy * iz; D[1][2] = -fy * y * iz * iz;
+    }
+    return;
+  }
+  const double th = atan2(r, z), t2 = th * th;
+  const double thd = th * (1.0 + t2 * (k1 + t2 * (k2 + t2 * (k3 + t2 * k4))));
+  const double s = thd / r;
+  u = fx * s * x + cx;
+  v = fy * s * y + cy;
+  if (D) {
+    const double dthd = 1.0 + t2 * (3.0 * k1 + t2 * (5.0 * k2 + t2 * (7.0 * k3 + t2 * 9.0 * k4)));
+    const double q = r * r + z * z;
+    const double dth[3] = {x * z / (r * q), y * z / (r * q), -r / q};
+    double ds[3];
+    for (int i = 0; i < 3; ++i) ds[i] = dthd * dth[i] / r;
+    ds[0] -= thd * x / (r * r * r);
+    ds[1] -= thd * y / (r * r * r);
+    for (int i = 0; i < 3; ++i) {
+      D[0][i] = fx * x * ds[i];
+      D[1][i] = fy * y * ds[i];
+    }
+    D[0][0] += fx * s;
+    D[1][1] += fy * s;
+  }
+}
+
 // Navigation state x = [qx qy qz qw, p (3), v (3), bg (3), ba (3)] (16 doubles), tangent
 // [dtheta, dp, dv, dbg, dba] (15): R <- R Exp(dtheta), p <- p + R dp, rest additive.
 // Render block rb[16]: R (body-to-world, row-major, 9), p (3), pad.
@@ -527,6 +569,12 @@ struct ModelStereo {
     for (int i = 0; i < 3; ++i)
       g.Xc[i] = Rc[3 * i] * g.Xb[0] + Rc[3 * i + 1] * g.Xb[1] + Rc[3 * i + 2] * g.Xb[2] + d.camk[14 + i];
     g.iz = 1.0 / g.Xc[2];
+    if (d.camk[17] != 0.0) {   // fisheye rig: both cameras Kannala-Brandt
+      double vr;
+      kb_project(d.camk, g.Xc[0], g.Xc[1], g.Xc[2], g.u[0], g.u[1], nullptr);
+      kb_project(d.camk, g.Xc[0] - d.camk[4], g.Xc[1], g.Xc[2], g.u[2], vr, nullptr);
+      return;
+    }
     g.u[0] = d.camk[0] * g.Xc[0] * g.iz + d.camk[2];
     g.u[1] = d.camk[1] * g.Xc[1] * g.iz + d.camk[3];
     g.u[2] = d.camk[0] * (g.Xc[0] - d.camk[4]) * g.iz + d.camk[2];
@@ -566,9 +614,21 @@ struct ModelStereo {
     const AT fx = (AT)d.camk[0], fy = (AT)d.camk[1], b = (AT)d.camk[4];
     const AT iz = (AT)g.iz, x = (AT)g.Xc[0], y = (AT)g.Xc[1];
     AT D[3][3];
-    D[0][0] = fx * iz; D[0][1] = (AT)0; D[0][2] = -fx * x * iz * iz;
-    D[1][0] = (AT)0;   D[1][1] = fy * iz; D[1][2] = -fy * y * iz * iz;
-    D[2][0] = fx * iz; D[2][1] = (AT)0; D[2][2] = -fx * (x - b) * iz * iz;
+    if (d.camk[17] != 0.0) {   // fisheye: rows of the left projection, u-row of the right
+      double Dl[2][3], Dr[2][3], uu, vv;
+      kb_project(d.camk, g.Xc[0], g.Xc[1], g.Xc[2], uu, vv, Dl);
+      kb_project(d.camk, g.Xc[0] - d.camk[4], g.Xc[1], g.Xc[2], uu, vv, Dr);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        D[0][j] = (AT)Dl[0][j];
+        D[1][j] = (AT)Dl[1][j];
+        D[2][j] = (AT)Dr[0][j];
+      }
+    } else {
+      D[0][0] = fx * iz; D[0][1] = (AT)0; D[0][2] = -fx * x * iz * iz;
+      D[1][0] = (AT)0;   D[1][1] = fy * iz; D[1][2] = -fy * y * iz * iz;
+      D[2][0] = fx * iz; D[2][1] = (AT)0; D[2][2] = -fx * (x - b) * iz * iz;
+    }
     AT DR[3][3];   // D R_cb
 #pragma unroll
     for (int a = 0; a < 3; ++a)

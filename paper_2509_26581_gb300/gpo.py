@@ -112,6 +112,7 @@ _SIGS = {
     "gpo_server_last_error": (C.c_char_p, [_P]),
     "gpo_ba_cost_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_double, _P]),
     "gpo_set_stereo_camera": (C.c_int, [_P, _P]),
+    "gpo_set_fisheye": (C.c_int, [_P, _P]),
     "gpo_imu_preintegrate": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, _P, C.c_double, C.c_double,
                                        _P, _P, _P]),
     "gpo_debug_linearize": (C.c_int, [_P, _P, _P]),
@@ -222,6 +223,14 @@ class Graph:
         if a.shape[0] != 17:
             raise ValueError("the stereo rig has 17 values")
         _check(lib.gpo_set_stereo_camera(self.h, _ptr(a)), self.h)
+
+    def set_fisheye(self, k) -> None:
+        """Kannala-Brandt coefficients [k1 k2 k3 k4] for both cameras of the rig
+        (gpo_set_fisheye; after set_stereo_camera)."""
+        a = np.ascontiguousarray(k, dtype=np.float64).reshape(-1)
+        if a.shape[0] != 4:
+            raise ValueError("four fisheye coefficients")
+        _check(lib.gpo_set_fisheye(self.h, _ptr(a)), self.h)
 
     def set_fixed(self, vid: int, fixed: bool = True):
         _check(lib.gpo_set_fixed(self.h, vid, int(fixed)), self.h)
@@ -555,6 +564,8 @@ def vi_graph(p, nav=None, pts=None, precision="fp64", prior_sigma=(1e-2, 1e-1), 
     n0 = g.add_vertices(GPO_V_NAV15, 15, K)
     p0 = g.add_vertices(GPO_V_POINT3, 3, P)
     g.set_stereo_camera(stereo_rig(p.camera))
+    if p.camera.get("fisheye") is not None:   # Kannala-Brandt coefficients of the rig
+        g.set_fisheye(p.camera["fisheye"])
     ids = np.stack([np.asarray(p.kf_idx, np.int64) + n0, np.asarray(p.pt_idx, np.int64) + p0], axis=1)
     ranges = {}
     keep = np.ones(ids.shape[0], bool) if mono is None else ~np.asarray(mono, bool)

@@ -270,6 +270,45 @@ def test_monocular_edges_mixed_precision_close_to_fp64(gpo, prec):
     assert abs(costs[prec] - costs["fp64"]) <= 1e-6 * costs["fp64"]
 
 
+FISHEYE = (-0.013, 0.021, -0.006, 0.0009)   # Kannala-Brandt k1..k4 of a wide-angle lens
+
+
+def _fisheye_problem(p):
+    """The same trajectory and landmarks seen through a Kannala-Brandt fisheye rig: the
+    observations are the oracle's fisheye projections of the ground truth plus the
+    problem's pixel noise (seeded)."""
+    import dataclasses
+    cam = dict(p.camera, fisheye=FISHEYE)
+    oc = ovi.camera_of(cam)
+    rng = np.random.default_rng(p.seed + 100)
+    obs = oc.project(p.nav_gt[p.kf_idx], p.pts_gt[p.pt_idx]) + rng.normal(size=p.obs.shape)
+    return dataclasses.replace(p, camera=cam, obs=obs)
+
+
+def test_fisheye_rows_and_lm_match_the_oracle(gpo, small):
+    """Stereo edges of a fisheye rig: rows against the oracle's (analytic, pinned by
+    central differences), the autodiff rows against both, and the LM run to the
+    oracle's final cost."""
+    p0, pims = small
+    p = _fisheye_problem(p0)
+    g, _, _, rg = gpo.vi_graph(p, precision="fp64", imu=_records(pims))
+    a, b = rg["stereo"]
+    ids = np.arange(a, b)
+    r, J = g.debug_linearize_edges(ids, nav=True)
+    ra, Ja = g.debug_autodiff_edges(ids, nav=True)
+    cam = ovi.camera_of(p.camera)
+    ro, (Jn, Jp) = cam.evaluate((p.nav0[p.kf_idx], p.pts0[p.pt_idx]), p.obs)
+    w = np.sqrt(robust.weight(np.sum(ro * ro, axis=1), ("huber", p.huber_delta)))
+    assert _rel_rows(r[:, :3], ro * w[:, None]) < 1e-12
+    Jg = np.concatenate([J[:, :3, :15], J[:, :3, 15:18]], axis=2)
+    assert _rel_rows(Jg, np.concatenate([Jn, Jp], axis=2) * w[:, None, None]) < 1e-11
+    assert _rel_rows(Ja[:, :3], J[:, :3]) < 1e-11 and _rel_rows(ra[:, :3], r[:, :3]) < 1e-12
+    rep = g.optimize(15, _parity_params(gpo))
+    _, orep = olm.levenberg_marquardt(ovi.problem(p, p.nav0, p.pts0, pims), 15)
+    assert abs(rep.initial_cost - orep.initial_cost) <= 1e-12 * orep.initial_cost
+    assert abs(rep.final_cost - orep.final_cost) <= 1e-9 * orep.final_cost
+
+
 def test_fixed_keyframe_and_disabled_edges(gpo, small):
     p, pims = small
     g, n0, p0, rg = _graph(gpo, p, pims)

@@ -85,9 +85,28 @@ def _fd_nav(f, x, eps=1e-6):
     return np.stack(cols, axis=-1)
 
 
-def test_stereo_jacobians_central_differences(small):
+FISHEYE = (-0.013, 0.021, -0.006, 0.0009)   # Kannala-Brandt k1..k4 of a wide-angle lens
+
+
+def test_fisheye_projection_closed_form():
+    """With k = 0 the Kannala-Brandt model is the equidistant one: a point at angle
+    theta off the axis lands fx theta from the principal point; with k it lands at
+    fx theta (1 + k1 theta^2 + ... + k4 theta^8)."""
+    th = np.linspace(0.05, 1.4, 12)
+    x, y, z = np.sin(th) * 3.0, np.zeros_like(th), np.cos(th) * 3.0
+    u, v, _ = vi.kb_project(x, y, z, 400.0, 410.0, 320.0, 240.0, (0.0, 0.0, 0.0, 0.0))
+    assert np.allclose(u, 400.0 * th + 320.0, rtol=0, atol=1e-10) and np.allclose(v, 240.0, atol=1e-12)
+    k1, k2, k3, k4 = FISHEYE
+    u, _, _ = vi.kb_project(x, y, z, 400.0, 410.0, 320.0, 240.0, FISHEYE)
+    t2 = th * th
+    assert np.allclose(u, 400.0 * th * (1 + k1 * t2 + k2 * t2 ** 2 + k3 * t2 ** 3 + k4 * t2 ** 4) + 320.0,
+                       rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("fisheye", [False, True])
+def test_stereo_jacobians_central_differences(small, fisheye):
     p = small
-    cam = vi.camera_of(p.camera)
+    cam = vi.camera_of(dict(p.camera, fisheye=FISHEYE) if fisheye else p.camera)
     for e in range(0, p.n_edges, max(1, p.n_edges // 25)):
         x = p.nav0[p.kf_idx[e]][None]
         X = p.pts0[p.pt_idx[e]][None]
