@@ -151,12 +151,12 @@ NOMINAL_HBM_GBS = 7900.0
 # sources they were counted from, so changed kernels report null.
 FP64_SOURCES = ("schur_common.cuh", "schur_kernels.cuh")
 FP64_FLOPS_PER_EDGE = {
-    ("k_linearize", "bf16", "8a95d08774dd"): 49.0,
-    ("k_linearize", "fp64", "8a95d08774dd"): 449.29,
+    ("k_linearize", "bf16", "da6ba9aa4521"): 49.0,
+    ("k_linearize", "fp64", "da6ba9aa4521"): 449.29,
     # one kernel for every precision (FP64 geometry and cost)
-    ("k_cost", "bf16", "8a95d08774dd"): 65.50,
-    ("k_cost", "fp32", "8a95d08774dd"): 65.50,
-    ("k_cost", "fp64", "8a95d08774dd"): 65.50,
+    ("k_cost", "bf16", "da6ba9aa4521"): 65.50,
+    ("k_cost", "fp32", "da6ba9aa4521"): 65.50,
+    ("k_cost", "fp64", "da6ba9aa4521"): 65.50,
 }
 
 
@@ -214,7 +214,7 @@ def load_peaks() -> tuple[float, str]:
 # was taken from (keyed by a hash of them): changed kernels report null.
 # DRAM bytes (read + write) per Schur-product launch from an ncu capture, keyed by
 # (precision, kernel, hash of the kernel sources): stale once the sources change.
-MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "98027b21f19f"): 179.6e6}
+MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "a9188123b2cd"): 179.6e6}
 SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
