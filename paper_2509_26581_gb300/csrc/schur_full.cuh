@@ -93,6 +93,17 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
   int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
   const JT* Jg = reinterpret_cast<const JT*>(d.J);
   const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
+  // the packed positions of this thread's edges (up to four: chunks of at most 1,024
+  // edges) are loaded ahead of the gathers, so their latency overlaps them
+  const bool packed = ls.ch_max <= 1024;
+  uint32_t mw[4] = {0u, 0u, 0u, 0u};
+  if (packed) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = threadIdx.x + m * kThreads;
+      if (i < cr.nE) mw[m] = __ldg(d.e_meta + cr.e0 + i);
+    }
+  }
   // slot cameras: record and direction (the Schur product's gather)
   {
     const AT* zv = reinterpret_cast<const AT*>(restart ? d.x : d.z);
@@ -134,19 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
 
   // ---- per edge: the point term J_p^T (J_c v_c) (edge order) and the camera term
   // J_c^T (J_p v_p) (slot-sorted position)
-  const bool packed = ls.ch_max <= 1024;
-  for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
-    int pos, slot, ptl;
-    if (packed) {
-      const uint32_t w = __ldg(d.e_meta + cr.e0 + i);
-      pos = (int)(w & 1023u);
-      slot = (int)((w >> 10) & 1023u);
-      ptl = (int)(w >> 20);
-    } else {
-      pos = __ldg(d.e_pos + cr.e0 + i);
-      slot = __ldg(d.e_slot + cr.e0 + i);
-      ptl = __ldg(d.e_pt + cr.e0 + i) - cr.p0;
-    }
+  auto edge = [&](int i, int pos, int slot, int ptl) {
     AT row[NJ];
     load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     const AT* xc = xs + DC * slot;
@@ -165,10 +164,10 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      AT s = row[JP0 + k] * qc[0];
+      AT t = row[JP0 + k] * qc[0];
 #pragma unroll
-      for (int a = 1; a < M; ++a) s += row[JP0 + 3 * a + k] * qc[a];
-      tv[k * LD + i] = s;
+      for (int a = 1; a < M; ++a) t += row[JP0 + 3 * a + k] * qc[a];
+      tv[k * LD + i] = t;
     }
 #pragma unroll
     for (int k = 0; k < DC; ++k) {
@@ -177,6 +176,17 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
       for (int a = 1; a < M; ++a) v += row[a * DC + k] * qp[a];
       vv[k * LD + pos] = v;
     }
+  };
+  if (packed) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = threadIdx.x + m * kThreads;
+      if (i >= cr.nE) break;
+      edge(i, (int)(mw[m] & 1023u), (int)((mw[m] >> 10) & 1023u), (int)(mw[m] >> 20));
+    }
+  } else {
+    for (int i = threadIdx.x; i < cr.nE; i += kThreads)
+      edge(i, __ldg(d.e_pos + cr.e0 + i), __ldg(d.e_slot + cr.e0 + i), __ldg(d.e_pt + cr.e0 + i) - cr.p0);
   }
   __syncthreads();
   // ---- point rows: y_p = (H_pp + lambda D_p) v_p + sum_e J_p^T J_c v_c
