@@ -1230,6 +1230,17 @@ static gpo_status check_range(gpo_graph* g, int64_t first, int64_t n, int* kind_
   return GPO_OK;
 }
 
+// The device address of page-locked host memory mapped into the device's address space
+// (e.g. from cudaHostAlloc), or null for pageable memory.
+static const double* mapped_host(const double* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? static_cast<const double*>(at.devicePointer) : nullptr;
+}
+
 gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double* state, int32_t on_device) {
   if (!g) return GPO_ERR_ARG;
   int kind;
@@ -1254,13 +1265,18 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
     GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * w, state, n * w * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else {
-    // points live on the device in sorted order (the id -> row map is resident)
+    // points live on the device in sorted order (the id -> row map is resident); the
+    // scatter reads device or mapped pinned host memory directly, pageable memory
+    // through a device copy
+    const double* src = on_device ? state : mapped_host(state);
     double* tmp = nullptr;
-    GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
-    GPO_CUDA(g, cudaMemcpyAsync(tmp, state, n * 3 * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    k_scatter_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(g->dev.pt, tmp, g->pt_old2new_d + loc, (int)n, 3);
-    GPO_CUDA(g, cudaFreeAsync(tmp, st));
+    if (!src) {
+      GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
+      GPO_CUDA(g, cudaMemcpyAsync(tmp, state, n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+      src = tmp;
+    }
+    k_scatter_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(g->dev.pt, src, g->pt_old2new_d + loc, (int)n, 3);
+    if (tmp) GPO_CUDA(g, cudaFreeAsync(tmp, st));
   }
   GPO_CUDA(g, cudaStreamSynchronize(st));
   return GPO_OK;
@@ -1285,12 +1301,16 @@ gpo_status gpo_get_state(gpo_graph* g, int64_t first, int64_t n, double* out, in
     GPO_CUDA(g, cudaMemcpyAsync(out, g->dev.cam + loc * w, n * w * sizeof(double),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   } else {
+    // the gather writes device or mapped pinned host memory directly, pageable memory
+    // through a device copy
+    double* dst = on_device ? out : const_cast<double*>(mapped_host(out));
     double* tmp = nullptr;
-    GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
-    k_gather_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(tmp, g->dev.pt, g->pt_old2new_d + loc, (int)n, 3);
-    GPO_CUDA(g, cudaMemcpyAsync(out, tmp, n * 3 * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    GPO_CUDA(g, cudaFreeAsync(tmp, st));
+    if (!dst) GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
+    k_gather_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(dst ? dst : tmp, g->dev.pt, g->pt_old2new_d + loc, (int)n, 3);
+    if (tmp) {
+      GPO_CUDA(g, cudaMemcpyAsync(out, tmp, n * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      GPO_CUDA(g, cudaFreeAsync(tmp, st));
+    }
   }
   GPO_CUDA(g, cudaStreamSynchronize(st));
   return GPO_OK;

@@ -324,3 +324,26 @@ def test_captured_pcg_groups_bitwise(gpo):
         assert rep.pcg_iters_total > 16       # several full groups ran
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_state_copies_through_pinned_host_memory(gpo):
+    """Point states copied in from and out to page-locked host memory (read and written
+    by the scatter and gather kernels directly) equal the copies through pageable
+    memory, including a partial range."""
+    import torch
+    p = synth.ba_ring(2, 6, 300, 5)
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64")
+    g.optimize(2)
+    ref = g.get_state(p0, p.n_pts, 3)
+    pinned = torch.empty((p.n_pts, 3), dtype=torch.float64).pin_memory()
+    g.get_state(p0, p.n_pts, 3, out=pinned.numpy())
+    assert np.array_equal(pinned.numpy(), ref)
+    new = ref + 0.01 * np.arange(3 * p.n_pts).reshape(-1, 3) / p.n_pts
+    src = torch.from_numpy(new.copy()).pin_memory()
+    g.set_initial(p0 + 10, src.numpy()[10:110])        # ids 10..109 from pinned memory
+    g.set_initial(p0 + 110, new[110:])                   # the rest from pageable memory
+    g.set_initial(p0, new[:10])
+    assert np.array_equal(g.get_state(p0, p.n_pts, 3), new)
+    part = torch.empty((50, 3), dtype=torch.float64).pin_memory()
+    g.get_state(p0 + 20, 50, 3, out=part.numpy())
+    assert np.array_equal(part.numpy(), new[20:70])
