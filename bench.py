@@ -521,7 +521,9 @@ def extra_served(stream, rate: float = 2000.0, duration: float = 1.0, pool: int 
     return dict(requests=int(len(arr)), rate_per_s=rate, window_edges=[int(edges.min()), int(edges.max())],
                 precision="bf16", lm_iters=10, budget_gb=40,
                 solves_per_s=r["solves_per_s"], p50_s=r["p50"], p99_s=r["p99"],
-                max_resident=r["max_resident"], seconds=r["seconds"],
+                max_resident=r["max_resident"], seconds=r["seconds"], steps=r["steps"],
+                mean_resident=r["mean_resident"], step_seconds=r["step_seconds"],
+                mean_step_ms=1e3 * r["step_seconds"] / max(1, r["steps"]),
                 one_by_one_fp64_solves_per_s=b["solves_per_s"],
                 speedup_vs_one_by_one_fp64=r["solves_per_s"] / b["solves_per_s"],
                 max_rel_cost_diff_served_vs_alone_same_precision=float(same.max()),

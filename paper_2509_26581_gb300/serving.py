@@ -47,6 +47,8 @@ def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str 
     done = 0
     steps = 0
     max_res = 0
+    step_s = 0.0                          # time inside sv.step() (admission + one LM iteration)
+    res_sum = 0
 
     def make(i):
         g, _, _ = window_graph(windows[pick[i]], precision)
@@ -66,8 +68,11 @@ def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str 
                 tickets[sv.submit(g, lm_iters, params)] = nxt
                 graphs[nxt] = g
                 nxt += 1
+            ts = time.perf_counter()
             res, queued, fin = sv.step()
+            step_s += time.perf_counter() - ts
             steps += 1
+            res_sum += res
             max_res = max(max_res, res)
             if fin:
                 tnow = time.perf_counter() - t0
@@ -91,6 +96,7 @@ def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str 
     total = time.perf_counter() - t0
     sv.close()
     return dict(latency=lat, final_cost=cost, seconds=total, steps=steps, max_resident=max_res,
+                mean_resident=res_sum / max(1, steps), step_seconds=step_s,
                 solves_per_s=n / total, p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)))
 
 
