@@ -151,12 +151,12 @@ NOMINAL_HBM_GBS = 7900.0
 # sources they were counted from, so changed kernels report null.
 FP64_SOURCES = ("schur_common.cuh", "schur_kernels.cuh")
 FP64_FLOPS_PER_EDGE = {
-    ("k_linearize", "bf16", "da6ba9aa4521"): 49.0,
-    ("k_linearize", "fp64", "da6ba9aa4521"): 449.29,
+    ("k_linearize", "bf16", "e4505b37f90b"): 49.0,
+    ("k_linearize", "fp64", "e4505b37f90b"): 449.29,
     # one kernel for every precision (FP64 geometry and cost)
-    ("k_cost", "bf16", "da6ba9aa4521"): 65.50,
-    ("k_cost", "fp32", "da6ba9aa4521"): 65.50,
-    ("k_cost", "fp64", "da6ba9aa4521"): 65.50,
+    ("k_cost", "bf16", "e4505b37f90b"): 65.50,
+    ("k_cost", "fp32", "e4505b37f90b"): 65.50,
+    ("k_cost", "fp64", "e4505b37f90b"): 65.50,
 }
 
 
@@ -215,7 +215,7 @@ def load_peaks() -> tuple[float, str]:
 # DRAM bytes (read + write) per Schur-product launch from an ncu capture, keyed by
 # (precision, kernel, hash of the kernel sources): stale once the sources change.
 MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "a9188123b2cd"): 179.6e6}
-SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3}
+SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3, "dynamic": 4}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
 
@@ -231,6 +231,8 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
 def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
     """The Schur-product kernel the library runs for these knobs (gpo_graph_desc)."""
     v = knobs.get("spmv_variant", 0)
+    if v == 4 and ch_max <= 512:
+        return "k_spmv_dyn"
     if ch_max <= 1024 and (v == 3 or (v == 0 and precision != "fp64")):
         return "k_spmv_pp"
     if ch_max <= 1024 and v == 1:
@@ -241,6 +243,7 @@ def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
 KERNEL_LABEL = {"k_spmv_pp": "k_spmv_pp (PCG Schur product, pipelined persistent)",
                 "k_spmv_ws": "k_spmv_ws (PCG Schur product, staged)",
                 "k_spmv": "k_spmv (PCG Schur product, classic)",
+                "k_spmv_dyn": "k_spmv_dyn (PCG Schur product, dynamic Jacobians; bytes of the stored-row product)",
                 "k_full_spmv": "k_full_spmv (PCG product with the full damped system)"}
 
 
@@ -324,6 +327,40 @@ def extra_full_system(args, p, dev, stream, schur_rate: float, schur_cost: float
                             frac=alg / (spmv_ms * 1e-3) / 1e9 / peak, peak=peak, peak_source=peak_kind),
                kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items() if v["launches"]},
                footprint_bytes=g.footprint())
+    g.close()
+    return out
+
+
+def extra_dynamic(args, p, dev, stream, stored_rate: float, stored_cost: float) -> dict:
+    """Dynamic Jacobians (spmv_variant 4: every Schur product recomputes each edge's rows
+    from the state instead of reading the stored ones) on the same workload, precision,
+    LM steps and PCG cap: LM rate, final cost against the stored-row run, and the
+    product's time per launch (profiled pass)."""
+    import torch
+
+    from paper_2509_26581_gb300 import gpo
+    prm = gpo.default_params(pcg_max_iters=100, pcg_tol=1e-6)
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, args.precision,
+                             device=dev, stream=stream.cuda_stream, spmv_variant=4, chunk_edges=512)
+    g.optimize(args.warmup, prm)
+    cams_w = g.get_state(c0, p.n_cams, 9)
+    pts_w = g.get_state(p0, p.n_pts, 3)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rep = g.optimize(args.steps, prm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    g.set_initial(c0, cams_w)
+    g.set_initial(p0, pts_w)
+    g.set_profiling(True)
+    g.optimize(args.steps, prm)
+    sp = g.profile()["spmv"]
+    out = dict(kernel="k_spmv_dyn", precision=args.precision, chunk_edges=g.knobs["chunk_edges"],
+               lm_iter_per_s=args.steps / (ms / 1e3), stored_rows_lm_iter_per_s=stored_rate,
+               final_cost=rep.final_cost, rel_diff_vs_stored=abs(rep.final_cost - stored_cost) / stored_cost,
+               product_avg_ms=sp["active_ms"] / sp["active"] if sp["active"] else None)
     g.close()
     return out
 
@@ -725,6 +762,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                                                     line["fp64"]["peak_tflops"])
         line["full_system"] = extra_full_system(args, p, dev, stream, line["value"], rep.final_cost)
         line["autodiff"] = extra_autodiff(args, p, dev, stream)
+        line["dynamic_jacobians"] = extra_dynamic(args, p, dev, stream, line["value"], rep.final_cost)
         line["vi"] = extra_vi(dev, stream)
         line["served"] = extra_served(stream)
         line["large"] = extra_large(dev, stream)

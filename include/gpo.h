@@ -124,9 +124,15 @@ typedef struct {
                                  (persistent CTAs streaming chunks into shared memory
                                  with bulk copies), 2 = classic (one CTA per chunk),
                                  3 = pipelined (persistent CTAs prefetching the next
-                                 chunk's indices while the current one runs).  1 and 3
-                                 need chunks of at most 1024 edges, else classic runs.
-                                 A tuning knob: all give bit-identical results. */
+                                 chunk's indices while the current one runs),
+                                 4 = dynamic Jacobians (each edge's rows recomputed
+                                 from the state in every product, in the accumulation
+                                 type, instead of read from storage; Sec. IV-D).  1 and
+                                 3 need chunks of at most 1024 edges, 4 of at most 512,
+                                 else classic runs.  0..3 give bit-identical results;
+                                 4 uses unrounded rows, so with BF16 or FP32 storage
+                                 its products agree with the others up to the
+                                 storage's rounding. */
 } gpo_graph_desc;
 
 /* Linear solver of the LM step (gpo_lm_params.solver). */

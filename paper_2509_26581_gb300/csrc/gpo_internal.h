@@ -188,7 +188,7 @@ struct LaunchSet {
                          // the end of every launch); [2] arrivals at the camera kernel's
                          // grid barrier (back to 0 at every barrier), [3] its generation
   int spmv_variant;      // Schur-product kernel: 0 auto, 1 staged (bulk copies), 2 classic,
-                         // 3 pipelined
+                         // 3 pipelined, 4 dynamic Jacobians
   int debug_wait;        // test hook, 0 in production: the camera kernel's grid barrier
                          // waits for this many CTAs more than the grid, so that its
                          // bounded wait gives up

@@ -23,6 +23,7 @@
 
 #include "schur_common.cuh"
 #include "schur_spmv.cuh"
+#include "schur_dynamic.cuh"
 
 namespace gpo {
 
@@ -1533,6 +1534,20 @@ struct Launch {
     else if (ept <= 4) spmv_e<JT, 4>(ls, pr, st);
     else spmv_e<JT, 8>(ls, pr, st);
   }
+  // Dynamic Jacobians: chunks of at most 512 edges (two per thread), else the classic
+  // stored-row product runs.
+  static bool dyn_ok(const LaunchSet& ls) { return ls.spmv_variant == 4 && ls.ch_max <= 2 * kThreads; }
+  template <class AT, int EPT>
+  static void dyn_e(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = spmv_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_spmv_dyn<Mo, AT, EPT>), sm);
+    launch_pdl(k_spmv_dyn<Mo, AT, EPT>, ls.n_ch, kThreads, sm, st, ls);
+  }
+  template <class AT>
+  static void dyn_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    if (ls.ch_max <= kThreads) dyn_e<AT, 1>(ls, pr, st);
+    else dyn_e<AT, 2>(ls, pr, st);
+  }
   static size_t ws_smem(Prec pr, const LaunchSet& ls) {
     const StageLayout L = stage_layout<Mo>(sJ(pr), sA(pr), ls.ch_max, ls.np_max, ls.ns_max);
     return kStages * (size_t)L.size + sA(pr) * (Dm::VW + 3) * (size_t)(ls.ch_max + 1);
@@ -1603,6 +1618,11 @@ struct Launch {
   }
   static int pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
+    if (dyn_ok(ls)) {
+      if (pr == Prec::F64) dyn_t<double>(ls, pr, st);
+      else dyn_t<float>(ls, pr, st);
+      return 1;
+    }
     if (pp_ok(pr, ls)) {
       if (pr == Prec::F64) pp_t<double>(ls, pr, st);
       else if (pr == Prec::F32) pp_t<float>(ls, pr, st);
