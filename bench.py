@@ -762,7 +762,10 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
                                                     line["fp64"]["peak_tflops"])
         line["full_system"] = extra_full_system(args, p, dev, stream, line["value"], rep.final_cost)
         line["autodiff"] = extra_autodiff(args, p, dev, stream)
-        line["dynamic_jacobians"] = extra_dynamic(args, p, dev, stream, line["value"], rep.final_cost)
+        try:
+            line["dynamic_jacobians"] = extra_dynamic(args, p, dev, stream, line["value"], rep.final_cost)
+        except Exception as ex:   # an extra never takes the headline line down with it
+            line["dynamic_jacobians"] = dict(error=repr(ex)[:200])
         line["vi"] = extra_vi(dev, stream)
         line["served"] = extra_served(stream)
         line["large"] = extra_large(dev, stream)
