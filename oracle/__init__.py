@@ -18,4 +18,4 @@ It is test infrastructure only: the tests, the smoke check and the benchmark's
 CPU-baseline leg may import it; the library and its Python binding never do, and
 the oracle never imports them.  It shares no code with the CUDA path.
 """
-from . import so3, robust, ba, circle, lm  # noqa: F401
+from . import so3, robust, ba, lm, generic  # noqa: F401

@@ -299,6 +299,11 @@ def nielsen_update(lam: float, nu: float, rho: float, accepted: bool):
     return lam * nu, nu * 2.0
 
 
+def clamp_lambda(lam: float, params: LMParams) -> float:
+    """The damping after each update is kept in [lambda_min, lambda_max]."""
+    return min(max(lam, params.lambda_min), params.lambda_max)
+
+
 def levenberg_marquardt(problem: Problem, max_iters: int, params: LMParams | None = None):
     """Runs exactly max_iters LM iterations on a copy of `problem`; returns (problem, Report)."""
     params = params or LMParams()
@@ -332,7 +337,7 @@ def levenberg_marquardt(problem: Problem, max_iters: int, params: LMParams | Non
             F = Fc
             rep.accepted += 1
         lam, nu = nielsen_update(lam, nu, rho, accepted)
-        lam = min(max(lam, params.lambda_min), params.lambda_max)
+        lam = clamp_lambda(lam, params)
         rep.iterations += 1
     rep.final_cost = F
     rep.final_lambda = lam

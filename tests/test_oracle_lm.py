@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from oracle import circle, lm, robust
+from oracle import generic, lm, robust
 from paper_2509_26581_gb300 import synth
 
 
@@ -114,8 +114,8 @@ def _circle_problem(n=12, radius=2.0, seed=0):
     fixed[n - 1] = True          # Listing 5: fix the last point
     active = np.ones(n, bool)
     active[2] = False            # Listing 5: disable the constraint of the third point
-    vs = {"p": lm.VertexSet("p", 2, pts, circle.retract, False, fixed)}
-    es = lm.EdgeSet("circle", ["p"], np.arange(n)[:, None], circle.evaluate, radius,
+    vs = {"p": lm.VertexSet("p", 2, pts, lambda s, d: s + d, False, fixed)}
+    es = lm.EdgeSet("circle", ["p"], np.arange(n)[:, None], generic.circle_evaluate, radius,
                     None, None, active)
     return lm.Problem(vs, [es]), pts
 
@@ -145,3 +145,84 @@ def test_circle_example_marquardt_damping():
     free[[2, 11]] = False
     assert np.max(np.abs(np.linalg.norm(pts[free], axis=1) - 2.0)) < 1e-9
     assert np.array_equal(pts[11], pts0[11]) and np.array_equal(pts[2], pts0[2])
+
+
+# ---------------------------------------------------------------- damping clamps
+# Sec. IV-E clamps the Hessian diagonal that scales the damping; the bounds
+# (1e-6, 1e32) and the damping bounds (1e-16, 1e32) are this library's readings.
+
+def _scalar_problem(a, y, x0, active=None):
+    """Independent scalar unknowns x_i with linear residuals r_i = a_i x_i - y_i:
+    H = diag(a^2), b = a r, so every quantity of a damped step has a closed form."""
+    a, y = np.asarray(a, float), np.asarray(y, float)
+    n = len(a)
+
+    def evaluate(states, data):
+        (x,) = states
+        return (data[:, 0] * x[:, 0] - data[:, 1])[:, None], [data[:, 0][:, None, None]]
+
+    vs = {"x": lm.VertexSet("x", 1, np.asarray(x0, float).reshape(n, 1), lambda s, d: s + d)}
+    es = lm.EdgeSet("lin", ["x"], np.arange(n)[:, None], evaluate, np.stack([a, y], axis=1),
+                    None, None, active)
+    return lm.Problem(vs, [es])
+
+
+def test_damping_diagonal_clamp_values():
+    d = np.array([1e-9, 0.0, -3.0, 1e-6, 5.0, 1e32, 1e40, 2.5e31])
+    H = sp.diags(d) + sp.csr_matrix(np.triu(np.ones((8, 8)), 1))   # off-diagonal entries are ignored
+    D = lm.damping_diagonal(H, lm.LMParams())
+    assert np.array_equal(D, [1e-6, 1e-6, 1e-6, 1e-6, 5.0, 1e32, 1e32, 2.5e31])
+    D = lm.damping_diagonal(H, lm.LMParams(diag_min=0.5, diag_max=10.0))
+    assert np.array_equal(D, [0.5, 0.5, 0.5, 0.5, 5.0, 10.0, 10.0, 10.0])
+    assert np.array_equal(lm.damping_diagonal(H, lm.LMParams(damping="identity")), np.ones(8))
+
+
+@pytest.mark.parametrize("lam", [1e-4, 1.0, 1e3])
+def test_damped_step_closed_form_with_clamped_diagonal(lam):
+    # H_ii = a_i^2 below, inside and above the clamp range: the step of Eq. 5 with the
+    # Marquardt scaling is dx_i = -a_i r_i / (a_i^2 + lam clamp(a_i^2, 1e-6, 1e32))
+    a = np.array([1e-4, 3.0, 1e20])
+    y = np.array([2.0, -1.0, 5.0])
+    x0 = np.array([0.7, 0.2, 3e-20])
+    dx, _, H, b, D, _ = lm.step(_scalar_problem(a, y, x0), lam)
+    r = a * x0 - y
+    expect = -a * r / (a * a + lam * np.array([1e-6, 9.0, 1e32]))
+    assert np.allclose(dx, expect, rtol=1e-14, atol=0)
+
+
+def test_lambda_rises_to_upper_bound_at_exact_optimum():
+    # r = 0 at x0: b = 0, dx = 0, model decrease 0, so every step is rejected and
+    # Nielsen's rule multiplies lambda by nu = 2, 4, 8, ...: lambda_k = lambda_0 2^(k(k+1)/2)
+    # until the clamp at lambda_max holds it there.
+    a = np.array([2.0, -0.5])
+    x0 = np.array([1.5, 4.0])
+    prob = _scalar_problem(a, a * x0, x0)
+    prm = lm.LMParams(initial_damping=1e-4, lambda_max=1.0)
+    _, rep = lm.levenberg_marquardt(prob, 8, prm)
+    lams = [h["lam"] for h in rep.history]
+    expect = [min(1e-4 * 2.0 ** (k * (k + 1) // 2), 1.0) for k in range(8)]
+    assert np.allclose(lams, expect, rtol=1e-15, atol=0)
+    assert lams[-1] == 1.0 and rep.final_lambda == 1.0 and rep.accepted == 0
+    assert rep.final_cost == 0.0
+
+
+def test_lambda_falls_to_lower_bound_on_linear_problem():
+    # A linear residual has an exact quadratic model, so rho = 1 on every step and
+    # lambda shrinks by max(1/3, 1 - (2 rho - 1)^3) = 1/3 until lambda_min holds it.
+    a = np.array([1.0, 2.0, 0.5])
+    y = np.array([3.0, -1.0, 2.0])
+    prob = _scalar_problem(a, y, np.zeros(3))
+    prm = lm.LMParams(initial_damping=1e3, lambda_min=10.0)
+    _, rep = lm.levenberg_marquardt(prob, 8, prm)
+    assert rep.accepted == 8
+    for h in rep.history:
+        assert abs(h["rho"] - 1.0) < 1e-9
+    lams = [h["lam"] for h in rep.history]
+    expect = [max(1e3 / 3.0 ** k, 10.0) for k in range(8)]
+    assert np.allclose(lams, expect, rtol=1e-14, atol=0)
+    assert rep.final_lambda == 10.0
+    # each accepted step scales the residual by lambda D / (H + lambda D) = lambda / (1 + lambda)
+    r = -y.copy()
+    for lam in lams:
+        r = r * lam / (1.0 + lam)
+    assert abs(rep.final_cost - 0.5 * r @ r) <= 1e-12 * rep.final_cost

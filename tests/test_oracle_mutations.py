@@ -81,3 +81,41 @@ def test_wrong_model_decrease_sign_fails_identity(monkeypatch):
     monkeypatch.setattr(lm, "model_decrease", bad)
     with pytest.raises(AssertionError):
         pins_lm.test_model_decrease_identity(1e-2)
+
+
+def test_unclamped_damping_diagonal_fails_values(monkeypatch):
+    monkeypatch.setattr(lm, "damping_diagonal", lambda H, params: H.diagonal())
+    with pytest.raises(AssertionError):
+        pins_lm.test_damping_diagonal_clamp_values()
+
+
+def test_clamping_lambda_times_diagonal_fails_closed_form(monkeypatch):
+    # plausible mistake: clamp lambda diag(H) instead of diag(H) before scaling by lambda
+    def bad(problem, lam, params=None):
+        params = params or lm.LMParams()
+        layout = lm.make_layout(problem)
+        lin = lm.linearize(problem, layout)
+        H, b = lm.normal_equations(lin)
+        D = np.clip(lam * H.diagonal(), params.diag_min, params.diag_max) / lam
+        dx, _, _ = lm.schur_solve(H + lm.sp.diags(lam * D), b, layout)
+        return dx, layout, H, b, D, lin
+
+    monkeypatch.setattr(lm, "step", bad)
+    with pytest.raises(AssertionError):
+        pins_lm.test_damped_step_closed_form_with_clamped_diagonal(1e-4)
+
+
+def test_missing_lambda_clamp_fails_bounds(monkeypatch):
+    monkeypatch.setattr(lm, "clamp_lambda", lambda lam, params: lam)
+    with pytest.raises(AssertionError):
+        pins_lm.test_lambda_rises_to_upper_bound_at_exact_optimum()
+    with pytest.raises(AssertionError):
+        pins_lm.test_lambda_falls_to_lower_bound_on_linear_problem()
+
+
+def test_rejected_step_keeping_lambda_fails_bounds(monkeypatch):
+    orig = lm.nielsen_update
+    monkeypatch.setattr(lm, "nielsen_update",
+                        lambda lam, nu, rho, acc: orig(lam, nu, rho, acc) if acc else (lam * 2.0, 2.0))
+    with pytest.raises(AssertionError):
+        pins_lm.test_lambda_rises_to_upper_bound_at_exact_optimum()
