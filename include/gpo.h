@@ -178,6 +178,12 @@ typedef struct {
                                  held to the graph's memory budget: GPO_ERR_OOM).
                                  Graphs without cameras, and graphs solved together
                                  (gpo_optimize_batch, a server), use the Schur form. */
+  double initial_nu;          /* Nielsen's multiplier nu at the start (after a rejected
+                                 step lambda *= nu, nu *= 2; after an accepted one nu = 2).
+                                 Values below 2 (the default 0) start from 2.  With
+                                 initial_damping = the previous report's final_lambda
+                                 and initial_nu = its final_nu, a sequence of calls
+                                 continues one LM run exactly. */
 } gpo_lm_params;
 
 typedef struct {
@@ -188,6 +194,7 @@ typedef struct {
   int32_t accepted;           /* accepted steps */
   int32_t pcg_iters_total;
   int32_t reserved0;
+  double final_nu;            /* Nielsen's nu after the last iteration (see initial_nu) */
 } gpo_report;
 
 /* One LM iteration's record (gpo_get_history). */
@@ -201,7 +208,10 @@ typedef struct {
   int32_t accepted;
   int32_t pcg_iters;
   int32_t pcg_products;       /* Schur products run: PCG iterations plus residual restarts */
-  int32_t reserved0;
+  int32_t pcg_failed;         /* 1: the PCG broke down before its first step (r^T M r or
+                                 p^T S p not positive or not finite, or the best iterate
+                                 kept by the rejection-ratio guard is the zero start); the
+                                 linear solve failed, so the step was rejected */
 } gpo_iter_record;
 
 /* Defaults for the two option structs.  Never fail for non-null pointers. */
@@ -290,8 +300,9 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first_id, int64_t n, const doub
 /* Runs max_iters Levenberg-Marquardt iterations (Listing 5: levenberg_marquardt).
  * The first call freezes the topology (sorts edges point-major, plans and
  * allocates device memory).  params NULL = defaults; out (optional) receives the
- * report.  The damping and the state carry over to the next call only through
- * the state: every call starts from params->initial_damping.
+ * report.  Every call starts from params->initial_damping and params->initial_nu and
+ * evaluates F at the current state; passing the previous report's final_lambda and
+ * final_nu continues the previous call's LM run step for step.
  * Errors: GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_NUMERIC (non-finite initial cost),
  *         GPO_ERR_UNSUPPORTED (a point seen more than the supported maximum of
  *         times), GPO_ERR_CUDA. */

@@ -628,7 +628,7 @@ void gpo_host::prof_resolve(gpo_graph* g) {
 void gpo_host::fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda, Scalars& s) {
   std::memset(&s, 0, sizeof(s));
   s.lambda = lambda;
-  s.nu = 2.0;
+  s.nu = (p.initial_nu >= 2.0 && std::isfinite(p.initial_nu)) ? p.initial_nu : 2.0;
   s.lambda_min = p.lambda_min;
   s.lambda_max = p.lambda_max;
   s.diag_min = p.diag_min;
@@ -1354,6 +1354,7 @@ gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* pa
     out->accepted = g->h_sc->n_accepted;
     out->pcg_iters_total = g->h_sc->pcg_total;
     out->reserved0 = 0;
+    out->final_nu = g->h_sc->nu;
   }
   return GPO_OK;
 }
@@ -1392,7 +1393,7 @@ gpo_status gpo_get_history(gpo_graph* g, gpo_iter_record* out, int32_t cap, int3
     out[i].accepted = h.accepted;
     out[i].pcg_iters = h.pcg_iters;
     out[i].pcg_products = h.pcg_products;
-    out[i].reserved0 = 0;
+    out[i].pcg_failed = h.pcg_failed;
   }
   if (n_out) *n_out = n;
   return GPO_OK;

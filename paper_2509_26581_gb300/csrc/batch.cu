@@ -140,6 +140,7 @@ void report_from(const Scalars& s, double initial_cost, gpo_report* r) {
   r->accepted = s.n_accepted;
   r->pcg_iters_total = s.pcg_total;
   r->reserved0 = 0;
+  r->final_nu = s.nu;
 }
 
 // Device-memory pool of a server: arenas of retired graphs are kept (keyed by size,

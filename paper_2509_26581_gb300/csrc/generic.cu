@@ -479,7 +479,7 @@ gpo_status gpo_generic_optimize(gpo_generic* g, int32_t max_iters, const gpo_lm_
     launch_jv<CircleEdge>(S.s[0], v, w_[0], st);
     launch_jv<DistanceEdge>(S.s[1], v, w_[1], st);
   };
-  double lam = prm.initial_damping, nu = 2.0;
+  double lam = prm.initial_damping, nu = (prm.initial_nu >= 2.0 && std::isfinite(prm.initial_nu)) ? prm.initial_nu : 2.0;
   double F = cost(x, 1);
   if (!ok) return GPO_ERR_CUDA;
   const double F0 = F;
@@ -547,6 +547,7 @@ gpo_status gpo_generic_optimize(gpo_generic* g, int32_t max_iters, const gpo_lm_
     rep->accepted = accepted;
     rep->final_lambda = lam;
     rep->pcg_iters_total = pcg_total;
+    rep->final_nu = nu;
   }
   return GPO_OK;
 }

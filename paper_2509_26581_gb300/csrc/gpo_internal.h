@@ -25,6 +25,7 @@ namespace gpo {
 constexpr int kThreads = 256;       // CTA size of the chunk kernels
 constexpr int kPtDim = 3;
 constexpr int kCamPerBlock = 8;     // cameras (warps) per CTA in camera kernels
+constexpr int kMaxDevices = 64;     // per-device launch caches
 constexpr int kMaxHistory = 4096;
 
 // Edge models (the kernel set a graph runs).
@@ -75,11 +76,15 @@ struct Scalars {
   int pcg_products;      // Schur products of the current solve (iterations + restarts)
   int full;              // PCG on the full damped system (cameras and points) instead of
                          // the camera Schur complement
+  int pcg_fail;          // the solve broke down before its first step (r^T M r or p^T S p not
+                         // positive, or not finite): a failed linear solve, the LM step is
+                         // rejected
+  int have_best;         // the rejection-ratio guard has saved an iterate
 };
 
 struct IterRecord {       // mirrors gpo_iter_record
   double cost, cand_cost, model_decrease, rho, lambda, pcg_residual;
-  int accepted, pcg_iters, pcg_products, pad_;
+  int accepted, pcg_iters, pcg_products, pcg_failed;
 };
 
 // Raw device pointers of one problem.  Arrays marked AT are of the accumulation type

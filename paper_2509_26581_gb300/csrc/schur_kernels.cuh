@@ -20,6 +20,8 @@
 // kernels live with the model (vi_kernels.cu).
 #pragma once
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 
 #include "schur_common.cuh"
 #include "schur_spmv.cuh"
@@ -710,6 +712,10 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     sc->save_best = 0;
     sc->tol_abs = sc->pcg_rel ? sc->pcg_tol * gn : sc->pcg_tol;
     sc->pcg_done = (rr == 0.0 || !(rz > 0.0) || !isfinite(rz)) ? 1 : 0;
+    // a nonzero right-hand side with r^T M r not positive: the preconditioner is not
+    // positive definite at this damping, so no step can be taken
+    sc->pcg_fail = (rr > 0.0 && (!(rz > 0.0) || !isfinite(rz))) ? 1 : 0;
+    sc->have_best = 0;
     if (!sc->pcg_done) atomicAdd(ls.running, 1);
     sc->ticket = 0u;
   }
@@ -853,6 +859,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       sc->alpha = 0.0;
       sc->pcg_done = 1;
+      if (sc->pcg_it == 0) sc->pcg_fail = 1;   // no step taken: S is not positive definite
       atomicSub(ls.running, 1);
     } else {
       sc->alpha = sc->rz / pAp;
@@ -933,6 +940,7 @@ __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, in
       if (rtrue < sc->rmin) {
         sc->rmin = rtrue;
         sc->save_best = 1;
+        sc->have_best = 1;
       } else if (rtrue > sc->ratio * sc->rmin) {
         done = 1;
         sc->use_best = 1;
@@ -993,6 +1001,7 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
         sc->alpha = alpha_d;
         if (bad) {
           sc->pcg_done = 1;
+          if (sc->pcg_it == 0) sc->pcg_fail = 1;   // no step taken: S is not positive definite
           atomicSub(ls.running, 1);
         }
       }
@@ -1308,7 +1317,11 @@ __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
   const double L = block_sum(md, red);
   if (threadIdx.x != 0) return;
   const double F = sc->cost;
-  const bool acc = L > 0.0 && isfinite(Fc) && Fc < F;
+  // a linear solve that broke down before its first step, or whose best iterate is the
+  // zero start, failed: the step is rejected and the damping grows (as a factorisation
+  // that finds the damped system indefinite rejects the step in the oracle)
+  const bool failed = sc->pcg_fail || (sc->use_best && !sc->have_best);
+  const bool acc = !failed && L > 0.0 && isfinite(Fc) && Fc < F;
   const double rho = L != 0.0 ? (F - Fc) / L : 0.0;
   const int it = sc->iter;
   if (it < kMaxHistory) {
@@ -1322,6 +1335,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
     h.accepted = acc ? 1 : 0;
     h.pcg_iters = sc->pcg_it;
     h.pcg_products = sc->pcg_products;
+    h.pcg_failed = failed ? 1 : 0;
   }
   double lam = sc->lambda, nu = sc->nu;
   if (acc) {
@@ -1385,20 +1399,25 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t sme
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Raises a kernel's dynamic shared-memory limit once per (kernel, size).
+// Raises a kernel's dynamic shared-memory limit once per (device, kernel, size).
 static void set_smem(const void* kernel, size_t bytes) {
-  static const void* keys[64];
-  static size_t vals[64];
+  static std::mutex mu;
+  static const void* keys[256];
+  static int devs[256];
+  static size_t vals[256];
   static int n = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
   for (int i = 0; i < n; ++i)
-    if (keys[i] == kernel) {
+    if (keys[i] == kernel && devs[i] == dev) {
       if (vals[i] >= bytes) return;
       cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       vals[i] = bytes;
       return;
     }
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (n < 64) { keys[n] = kernel; vals[n] = bytes; ++n; }
+  if (n < 256) { keys[n] = kernel; devs[n] = dev; vals[n] = bytes; ++n; }
 }
 
 }  // namespace gpo
@@ -1646,29 +1665,84 @@ struct Launch {
     else launch_pdl(k_cam_apply<Mo, float>, ls.n_cb * kApplySplit, kCamPerBlock * 32, 0, st, ls);
     return 1;
   }
+  // Per device: the fused camera kernel's resident-CTA capacity (per accumulation type)
+  // and the launch form the driver accepted on the first use (0 unknown, 1 cooperative
+  // with programmatic serialization, 2 cooperative only, -1 neither: two launches).
+  struct CoopState {
+    std::atomic<int> cap[2];
+    std::atomic<int> mode;
+  };
+  static CoopState& coop_state(int dev) {
+    static CoopState st[kMaxDevices];
+    return st[dev >= 0 && dev < kMaxDevices ? dev : 0];
+  }
   template <class AT>
-  static int pcg_camera_cap() {
-    static int cap = 0;   // resident CTAs of the fused camera kernel
-    if (!cap) {
-      int dev = 0, n_sm = 0, occ = 0;
-      cudaGetDevice(&dev);
+  static int pcg_camera_cap(int dev) {
+    std::atomic<int>& cap = coop_state(dev).cap[std::is_same<AT, double>::value ? 1 : 0];
+    int c = cap.load(std::memory_order_relaxed);
+    if (!c) {
+      int n_sm = 0, occ = 0;
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_camera<Mo, AT>, kCamPerBlock * 32, 0);
-      cap = std::max(1, n_sm) * std::max(1, occ);
+      c = std::max(1, n_sm) * std::max(1, occ);
+      cap.store(c, std::memory_order_relaxed);
     }
-    return cap;
+    return c;
+  }
+  // A cooperative launch: the driver starts the grid only if every CTA can be resident
+  // at once, which the kernel's grid barrier relies on.
+  template <class AT>
+  static cudaError_t launch_coop(int grid, cudaStream_t st, bool pdl, const LaunchSet& ls) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)(kCamPerBlock * 32));
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, k_pcg_camera<Mo, AT>, ls);
   }
   // Launches the fused camera kernel if the camera half's units fit one resident wave
-  // (returns 1); otherwise launches nothing and returns 0 (the caller launches
-  // cam_apply and pcg_update).
+  // (returns 1); otherwise, or if the driver refuses the cooperative launch, launches
+  // nothing and returns 0 (the caller launches cam_apply and pcg_update).  The first
+  // call on a device tries cooperative launch with programmatic serialization, then
+  // without, and keeps the form that was accepted.
+  template <class AT>
+  static int pcg_camera_t(const LaunchSet& ls, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int units = ls.n_cb * kApplySplit;
+    if (units > pcg_camera_cap<AT>(dev)) return 0;
+    std::atomic<int>& mode = coop_state(dev).mode;
+    int m = mode.load(std::memory_order_relaxed);
+    if (m < 0) return 0;
+    if (m == 0) {
+      if (launch_coop<AT>(units, st, true, ls) == cudaSuccess) {
+        mode.store(1, std::memory_order_relaxed);
+        return 1;
+      }
+      cudaGetLastError();
+      if (launch_coop<AT>(units, st, false, ls) == cudaSuccess) {
+        mode.store(2, std::memory_order_relaxed);
+        return 1;
+      }
+      cudaGetLastError();
+      mode.store(-1, std::memory_order_relaxed);
+      return 0;
+    }
+    if (launch_coop<AT>(units, st, m == 1, ls) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return 1;
+  }
   static int pcg_camera(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_cb == 0) return 0;
-    const int units = ls.n_cb * kApplySplit;
-    const int cap = pr == Prec::F64 ? pcg_camera_cap<double>() : pcg_camera_cap<float>();
-    if (units > cap) return 0;
-    if (pr == Prec::F64) launch_pdl(k_pcg_camera<Mo, double>, units, kCamPerBlock * 32, 0, st, ls);
-    else launch_pdl(k_pcg_camera<Mo, float>, units, kCamPerBlock * 32, 0, st, ls);
-    return 1;
+    return pr == Prec::F64 ? pcg_camera_t<double>(ls, st) : pcg_camera_t<float>(ls, st);
   }
   static int pcg_update(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_cb == 0) return 0;

@@ -44,20 +44,21 @@ class gpo_lm_params(C.Structure):
                 ("damping_mode", C.c_int32), ("pcg_max_iters", C.c_int32),
                 ("pcg_tol", C.c_double), ("pcg_tol_relative", C.c_int32),
                 ("pcg_rejection_ratio", C.c_double), ("pcg_normalize", C.c_int32),
-                ("pcg_restart_every", C.c_int32), ("solver", C.c_int32)]
+                ("pcg_restart_every", C.c_int32), ("solver", C.c_int32), ("initial_nu", C.c_double)]
 
 
 class gpo_report(C.Structure):
     _fields_ = [("initial_cost", C.c_double), ("final_cost", C.c_double),
                 ("final_lambda", C.c_double), ("iterations", C.c_int32),
-                ("accepted", C.c_int32), ("pcg_iters_total", C.c_int32), ("reserved0", C.c_int32)]
+                ("accepted", C.c_int32), ("pcg_iters_total", C.c_int32), ("reserved0", C.c_int32),
+                ("final_nu", C.c_double)]
 
 
 class gpo_iter_record(C.Structure):
     _fields_ = [("cost", C.c_double), ("cand_cost", C.c_double), ("model_decrease", C.c_double),
                 ("rho", C.c_double), ("lambda_", C.c_double), ("pcg_residual", C.c_double),
                 ("accepted", C.c_int32), ("pcg_iters", C.c_int32), ("pcg_products", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("pcg_failed", C.c_int32)]
 
 
 class gpo_graph_info_t(C.Structure):
@@ -281,7 +282,8 @@ class Graph:
         _check(lib.gpo_get_history(self.h, buf, cap, C.byref(n)), self.h)
         return [dict(cost=r.cost, cand_cost=r.cand_cost, model_decrease=r.model_decrease,
                      rho=r.rho, lam=r.lambda_, pcg_residual=r.pcg_residual,
-                     accepted=bool(r.accepted), pcg_iters=r.pcg_iters, pcg_products=r.pcg_products)
+                     accepted=bool(r.accepted), pcg_iters=r.pcg_iters, pcg_products=r.pcg_products,
+                     pcg_failed=bool(r.pcg_failed))
                 for r in buf[:n.value]]
 
     def set_profiling(self, on: bool = True):

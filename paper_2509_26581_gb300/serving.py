@@ -24,15 +24,16 @@ def window_graph(p, precision: str, fix_first: bool = True, **kw) -> tuple:
                         cam_fixed=cam_fixed, **kw)
 
 
-def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str = "bf16",
+def serve(windows, arrivals: np.ndarray, pick: np.ndarray | None = None, precision: str = "bf16",
           lm_iters: int = 10, params=None, memory_budget: int = 40 << 30,
           max_resident: int = 1024, stream=None, builders: int = 4) -> dict:
-    """Runs the request stream; request i is a fresh graph of windows[pick[i]] that
-    arrives at arrivals[i] seconds.  Arrived requests are built and planned on
-    `builders` worker threads (graph construction and host planning need no GPU and
-    release the interpreter inside the library), submitted in arrival order, and the
-    server is stepped on this thread.  Returns latencies (arrival to retirement),
-    throughput and final costs."""
+    """Runs the request stream; request i arrives at arrivals[i] seconds and is a fresh
+    graph of windows[pick[i]] (windows a list), or of the problem windows(i) returns
+    (windows a callable, pick unused).  Arrived requests are built and planned on
+    `builders` worker threads (problem and graph construction and host planning need no
+    GPU and release the interpreter inside the library), submitted in arrival order,
+    and the server is stepped on this thread.  Returns latencies (arrival to
+    retirement), throughput and final costs."""
     from concurrent.futures import ThreadPoolExecutor
 
     sv = gpo.Server(precision, stream=stream, memory_budget=memory_budget, max_resident=max_resident)
@@ -51,7 +52,7 @@ def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str 
     res_sum = 0
 
     def make(i):
-        g, _, _ = window_graph(windows[pick[i]], precision)
+        g, _, _ = window_graph(windows(i) if callable(windows) else windows[pick[i]], precision)
         g.plan()
         return g
 
@@ -100,14 +101,15 @@ def serve(windows: list, arrivals: np.ndarray, pick: np.ndarray, precision: str 
                 solves_per_s=n / total, p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)))
 
 
-def one_by_one(windows: list, pick: np.ndarray, precision: str = "fp64", lm_iters: int = 10,
+def one_by_one(windows, pick: np.ndarray, precision: str = "fp64", lm_iters: int = 10,
                params=None) -> dict:
-    """Baseline: the same requests solved one after another with gpo_optimize."""
+    """Baseline: the same requests solved one after another with gpo_optimize (request k
+    is windows[pick[k]], or windows(pick[k]) when windows is a callable)."""
     n = len(pick)
     cost = np.empty(n)
     t0 = time.perf_counter()
     for i in range(n):
-        g, _, _ = window_graph(windows[pick[i]], precision)
+        g, _, _ = window_graph(windows(pick[i]) if callable(windows) else windows[pick[i]], precision)
         cost[i] = g.optimize(lm_iters, params).final_cost
         g.close()
     total = time.perf_counter() - t0

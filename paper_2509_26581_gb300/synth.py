@@ -411,6 +411,25 @@ def window_pool(seed: int, n: int, kf=(5, 40), pts=(300, 8000)) -> list:
     return [ba_window(seed * 1000003 + i, int(k[i]), int(m[i])) for i in range(n)]
 
 
+def fresh_request(base: BAProblem, seed: int, i: int, pixel_sigma: float = 0.5,
+                  trans_noise: float = 0.02, point_noise: float = 0.05) -> BAProblem:
+    """Request i of a served stream built on the window topology `base`: the same
+    cameras, landmarks and visibility, with observation noise and an initial state of
+    its own (N(0, pixel_sigma^2) added to every pixel, N(0, trans_noise^2) to every
+    camera translation, N(0, point_noise^2) to every landmark), drawn from counter-based
+    streams keyed by (seed, i).  Every request is a distinct problem with a distinct
+    optimum, at a cost of a few array operations (generating a new window topology takes
+    milliseconds, too slow for thousands of requests per second)."""
+    rng = Stream(seed * 1000003 + i, 23)
+    E, C, P = base.n_edges, base.n_cams, base.n_pts
+    obs = base.obs + rng.normal(2 * E, pixel_sigma).reshape(E, 2)
+    cams0 = base.cams0.copy()
+    cams0[:, 3:6] += rng.normal(3 * C, trans_noise).reshape(C, 3)
+    pts0 = base.pts0 + rng.normal(3 * P, point_noise).reshape(P, 3)
+    return BAProblem(f"{base.name}_r{i}", base.seed, base.cams_gt, base.pts_gt, cams0, pts0, base.cam_idx,
+                     base.pt_idx, obs, base.is_outlier, base.huber_delta, dict(base.meta))
+
+
 def poisson_arrivals(seed: int, rate: float, duration: float) -> np.ndarray:
     """Arrival times of a Poisson process of `rate` per second over [0, duration)."""
     rng = Stream(seed, 22)

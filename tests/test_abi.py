@@ -51,8 +51,14 @@ def test_struct_sizes_match_the_header():
     """Each parameter struct the binding mirrors has the size the header gives it
     (C layout rules of the header's member types, computed here independently)."""
     from paper_2509_26581_gb300 import gpo
-    # gpo_lm_params: 5 doubles, 2 int32, double, int32 (+4 pad), double, 3 int32 (+4 pad)
-    assert ctypes.sizeof(gpo.gpo_lm_params) == 5 * 8 + 2 * 4 + 8 + 8 + 8 + 16
+    # gpo_lm_params: 5 doubles, 2 int32, double, int32 (+4 pad), double, 3 int32 (+4 pad), double
+    assert ctypes.sizeof(gpo.gpo_lm_params) == 5 * 8 + 2 * 4 + 8 + 8 + 8 + 16 + 8
+    # gpo_report: 3 doubles, 4 int32, double
+    assert ctypes.sizeof(gpo.gpo_report) == 3 * 8 + 4 * 4 + 8
+    src_r = open(os.path.join(ROOT, "include", "gpo.h")).read()
+    body_r = src_r[src_r.rindex("typedef struct {", 0, src_r.index("} gpo_report;")):src_r.index("} gpo_report;")]
+    body_r = re.sub(r"/\*.*?\*/", "", body_r, flags=re.S)
+    assert [f for _, f in re.findall(r"(double|int32_t)\s+(\w+);", body_r)] == [f for f, _ in gpo.gpo_report._fields_]
     src = open(os.path.join(ROOT, "include", "gpo.h")).read()
     body = src[src.index("typedef struct {", src.index("PCGSolver(max_it")):src.index("} gpo_lm_params;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
