@@ -230,7 +230,7 @@ def load_peaks() -> tuple[float, str]:
 # ncu, keyed by (precision, kernel, hash of the kernel sources): stale once the sources
 # change.
 MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "a9188123b2cd"): 179.6e6}
-SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3, "dynamic": 4}
+SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3, "dynamic": 4, "warpgroup": 5}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
 
@@ -246,6 +246,8 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
 def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
     """The Schur-product kernel the library runs for these knobs (gpo_graph_desc)."""
     v = knobs.get("spmv_variant", 0)
+    if v == 5 and ch_max <= 1024 and precision != "fp64":
+        return "k_spmv_wg"
     if v == 4 and ch_max <= 512:
         return "k_spmv_dyn"
     if ch_max <= 1024 and (v == 3 or (v == 0 and precision != "fp64")):
@@ -255,7 +257,8 @@ def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
     return "k_spmv"
 
 
-KERNEL_LABEL = {"k_spmv_pp": "k_spmv_pp (PCG Schur product, pipelined persistent)",
+KERNEL_LABEL = {"k_spmv_wg": "k_spmv_wg (PCG Schur product, warp groups)",
+                "k_spmv_pp": "k_spmv_pp (PCG Schur product, pipelined persistent)",
                 "k_spmv_ws": "k_spmv_ws (PCG Schur product, staged)",
                 "k_spmv": "k_spmv (PCG Schur product, classic)",
                 "k_spmv_dyn": "k_spmv_dyn (PCG Schur product, dynamic Jacobians; bytes of the stored-row product)",
@@ -346,11 +349,12 @@ def extra_full_system(args, p, dev, stream, schur_rate: float, schur_cost: float
     return out
 
 
-def extra_dynamic(args, p, dev, stream, stored_rate: float, stored_cost: float) -> dict:
-    """Dynamic Jacobians (spmv_variant 4: every Schur product recomputes each edge's rows
-    from the state instead of reading the stored ones) on the same workload, precision,
-    LM steps and PCG cap: LM rate, final cost against the stored-row run, and the
-    product's time per launch (profiled pass)."""
+def extra_dynamic(args, p, dev, stream, stored_rate: float, stored_cost: float, stored_footprint: int) -> dict:
+    """Dynamic Jacobians (spmv_variant 4: no rows are stored; the Schur preparation, every
+    Schur product and the back-substitution evaluate each edge's rows from the state, in
+    FP32 for the mixed modes) on the same workload, LM steps and PCG cap: LM rate and
+    device footprint against stored rows (Table II's trade of time for memory), final
+    cost against the stored-row run, and the product's time per launch (profiled pass)."""
     import torch
 
     from paper_2509_26581_gb300 import gpo
@@ -367,15 +371,23 @@ def extra_dynamic(args, p, dev, stream, stored_rate: float, stored_cost: float) 
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    info = g.info()
     g.set_initial(c0, cams_w)
     g.set_initial(p0, pts_w)
     g.set_profiling(True)
     g.optimize(args.steps, prm)
-    sp = g.profile()["spmv"]
-    out = dict(kernel="k_spmv_dyn", precision=args.precision, chunk_edges=g.knobs["chunk_edges"],
-               lm_iter_per_s=args.steps / (ms / 1e3), stored_rows_lm_iter_per_s=stored_rate,
-               final_cost=rep.final_cost, rel_diff_vs_stored=abs(rep.final_cost - stored_cost) / stored_cost,
-               product_avg_ms=sp["active_ms"] / sp["active"] if sp["active"] else None)
+    prof = g.profile()
+    sp = prof["spmv"]
+    fp = g.footprint()
+    out = dict(kernel="k_spmv_dyn", kernel_dispatched=info["spmv_kernel"], precision=args.precision,
+               rows_in="FP32 registers (nothing stored)" if args.precision != "fp64" else "FP64 registers",
+               chunk_edges=g.knobs["chunk_edges"], lm_iter_per_s=args.steps / (ms / 1e3),
+               stored_rows_lm_iter_per_s=stored_rate, footprint_bytes=fp,
+               stored_rows_footprint_bytes=stored_footprint, footprint_vs_stored=fp / stored_footprint,
+               j_bytes=info["j_bytes"], final_cost=rep.final_cost,
+               rel_diff_vs_stored=abs(rep.final_cost - stored_cost) / stored_cost,
+               product_avg_ms=sp["active_ms"] / sp["active"] if sp["active"] else None,
+               kernels_ms={k: round(v["active_ms"], 3) for k, v in prof.items() if v["launches"]})
     g.close()
     return out
 
@@ -857,16 +869,21 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     )
     if not args.no_extras and world == 1:
         g.close()
-        line["convergence"] = extra_convergence(args, p, dev, stream, line["fp64"]["peak_tflops"])
-        line["full_system"] = extra_full_system(args, p, dev, stream, line["value"], rep.final_cost)
-        line["autodiff"] = extra_autodiff(args, p, dev, stream)
-        try:
-            line["dynamic_jacobians"] = extra_dynamic(args, p, dev, stream, line["value"], rep.final_cost)
-        except Exception as ex:   # an extra never takes the headline line down with it
-            line["dynamic_jacobians"] = dict(error=repr(ex)[:200])
-        line["vi"] = extra_vi(dev, stream)
-        line["served"] = extra_served(stream)
-        line["large"] = extra_large(dev, stream)
+
+        def extra(name, fn, *a):
+            try:                  # an extra never takes the headline line down with it
+                line[name] = fn(*a)
+            except Exception as ex:
+                line[name] = dict(error=repr(ex)[:300])
+
+        extra("convergence", extra_convergence, args, p, dev, stream, line["fp64"]["peak_tflops"])
+        extra("full_system", extra_full_system, args, p, dev, stream, line["value"], rep.final_cost)
+        extra("autodiff", extra_autodiff, args, p, dev, stream)
+        extra("dynamic_jacobians", extra_dynamic, args, p, dev, stream, line["value"], rep.final_cost,
+              line["footprint_bytes"])
+        extra("vi", extra_vi, dev, stream)
+        extra("served", extra_served, stream)
+        extra("large", extra_large, dev, stream)
     return line
 
 

@@ -125,14 +125,23 @@ typedef struct {
                                  with bulk copies), 2 = classic (one CTA per chunk),
                                  3 = pipelined (persistent CTAs prefetching the next
                                  chunk's indices while the current one runs),
-                                 4 = dynamic Jacobians (each edge's rows recomputed
-                                 from the state in every product, in the accumulation
-                                 type, instead of read from storage; Sec. IV-D).  1 and
-                                 3 need chunks of at most 1024 edges, 4 of at most 512,
-                                 else classic runs.  0..3 give bit-identical results;
-                                 4 uses unrounded rows, so with BF16 or FP32 storage
-                                 its products agree with the others up to the
-                                 storage's rounding. */
+                                 4 = dynamic Jacobians (no rows are stored: every kernel
+                                 that needs an edge's rows evaluates them from the
+                                 state in the accumulation type, FP32 with FP32 or BF16
+                                 storage, which are then one mode; Sec. IV-D, Table II.
+                                 Needs points of at most 512 observations, else
+                                 GPO_ERR_UNSUPPORTED at the first optimize; not with
+                                 the full-system solver, batches or servers, and
+                                 gpo_debug_linearize has no rows to return),
+                                 5 = warp groups (each warp owns runs of whole points:
+                                 rows read once into registers, point sums by a
+                                 segmented warp scan, one barrier per chunk; BF16 and
+                                 FP32 storage).  1, 3 and 5 need chunks of at most 1024
+                                 edges, 4 of at most 512, else classic runs (5 with
+                                 FP64 storage too).  0..3 give bit-identical results;
+                                 5 sums each point's terms in another order and 4 uses
+                                 unrounded rows, so their products agree with the
+                                 others up to rounding. */
 } gpo_graph_desc;
 
 /* Linear solver of the LM step (gpo_lm_params.solver). */
@@ -333,6 +342,12 @@ typedef struct {
   int64_t slots;              /* (chunk, camera) pairs: rows of the camera-side partials */
   int32_t chunk_edges;        /* edges per chunk in effect */
   int32_t spmv_variant;       /* as requested in gpo_graph_desc */
+  int32_t spmv_kernel;        /* the Schur-product kernel the PCG runs, in spmv_variant's
+                                 numbering (1 staged, 2 classic, 3 pipelined, 4 dynamic,
+                                 5 warp groups; 0: no observation edges) */
+  int32_t reserved0;
+  int64_t j_bytes;            /* device bytes of the stored Jacobian rows (0 with dynamic
+                                 Jacobians, which store none) */
 } gpo_graph_info_t;
 
 /* Fills *out for a graph that has been optimized (or otherwise finalized).

@@ -175,7 +175,7 @@ struct Prepared {
   // sources of the uploaded arrays
   std::vector<int32_t> e_cam_s, e_pt_s, pt_off, ch_e0, ch_p0, ch_s0, slot_e0, slot_cam, cam_s_off, cam_s_list,
       slot_pos, slot_rec, xi_s, xj_s, xk_s, xo_off, xk_off, xk_list, zeros_ch, zeros_cb, zeros_pb, zeros_small;
-  std::vector<uint16_t> e_pos, e_slot, ch_sorted;
+  std::vector<uint16_t> e_pos, e_slot, ch_sorted, ch_grp;
   std::vector<uint32_t> e_meta;
   std::vector<uint8_t> cam_fixed, pt_fixed_s;
   std::vector<double> obs_s, delta_s, info_s, xrec_s, cams, pts, xzeros;
@@ -187,7 +187,7 @@ struct Prepared {
       *xe_kind_d = nullptr, *xo_off_d = nullptr, *xk_off_d = nullptr, *xk_list_d = nullptr, *ch_prob_d = nullptr,
       *cb_prob_d = nullptr, *pb_prob_d = nullptr, *base_d = nullptr, *running_d = nullptr,
       *old2new_d = nullptr;
-  uint16_t *e_pos_d = nullptr, *e_slot_d = nullptr, *ch_sorted_d = nullptr;
+  uint16_t *e_pos_d = nullptr, *e_slot_d = nullptr, *ch_sorted_d = nullptr, *ch_grp_d = nullptr;
   uint32_t* e_meta_d = nullptr;
   uint8_t *cam_fixed_d = nullptr, *pt_fixed_d = nullptr;
   double *obs_d = nullptr, *delta_d = nullptr, *info_d = nullptr, *xe_rec_d = nullptr;
@@ -255,26 +255,48 @@ static gpo_status prepare(gpo_graph* g) {
                 "a point has %d observations; this precision supports at most %d per point", maxdeg,
                 ks.max_supported_ch(g->prec));
   R.ch = ch;
-  // chunks of whole points, at most ch edges and ch points each
+  const bool dyn = g->desc.spmv_variant == 4;   // dynamic Jacobians: no stored rows
+  if (dyn && ch > 2 * gpo::kThreads)
+    return fail(g, GPO_ERR_UNSUPPORTED,
+                "dynamic Jacobians need chunks of at most %d edges (a point has %d observations)",
+                2 * gpo::kThreads, maxdeg);
+  // Chunks of whole points, at most ch edges and ch points each, cut into warp groups:
+  // runs of whole points of at most kGroupEdges edges (a point with more edges is a group
+  // of its own), at most ch / kGroupEdges groups (and kMaxGroups) per chunk, so that
+  // every warp of a chunk kernel can own one group.  ch_grp[k][g] is the local edge
+  // offset where group g of chunk k ends (groups after the last end at the chunk's end).
   R.ch_e0.assign(1, 0);
   R.ch_p0.assign(1, 0);
   {
-    int ne = 0, np = 0;
+    const int GE = gpo::kGroupEdges;
+    const int GPC = std::max(1, std::min(gpo::kMaxGroups, ch / GE));
+    uint16_t cur[gpo::kMaxGroups];
+    int ne = 0, np = 0, ng = 0, ge = 0;
+    auto close_chunk = [&](int p_end) {
+      if (ng > 0) cur[ng - 1] = (uint16_t)ne;
+      for (int q = ng; q < gpo::kMaxGroups; ++q) cur[q] = (uint16_t)ne;
+      R.ch_grp.insert(R.ch_grp.end(), cur, cur + gpo::kMaxGroups);
+      R.ch_e0.push_back(R.pt_off[p_end]);
+      R.ch_p0.push_back(p_end);
+    };
     for (int p = 0; p < P; ++p) {
       const int L = R.pt_off[p + 1] - R.pt_off[p];
-      if (np > 0 && (ne + L > ch || np + 1 > ch)) {
-        R.ch_e0.push_back(R.pt_off[p]);
-        R.ch_p0.push_back(p);
-        ne = 0;
-        np = 0;
+      bool fits = ng > 0 && L <= GE && ge + L <= GE;
+      if (np > 0 && (ne + L > ch || np + 1 > ch || (!fits && ng + 1 > GPC))) {
+        close_chunk(p);
+        ne = np = ng = ge = 0;
+        fits = false;
       }
+      if (!fits) {
+        if (ng > 0) cur[ng - 1] = (uint16_t)ne;
+        ++ng;
+        ge = 0;
+      }
+      ge += L;
       ne += L;
       np += 1;
     }
-    if (np > 0) {
-      R.ch_e0.push_back(E);
-      R.ch_p0.push_back(P);
-    }
+    if (np > 0) close_chunk(P);
   }
   const int NCH = (int)R.ch_e0.size() - 1;
   R.NCH = NCH;
@@ -436,6 +458,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.up(&R.pt_off_d, P + 1, R.pt_off); pl.up(&R.ch_e0_d, NCH + 1, R.ch_e0); pl.up(&R.ch_p0_d, NCH + 1, R.ch_p0);
   pl.up(&R.ch_s0_d, NCH + 1, R.ch_s0); pl.up(&R.e_pos_d, E, R.e_pos); pl.up(&R.e_slot_d, E, R.e_slot);
   pl.up(&R.ch_sorted_d, E, R.ch_sorted); pl.up(&R.slot_e0_d, NS + 1, R.slot_e0);
+  pl.up(&R.ch_grp_d, (size_t)std::max(NCH, 1) * gpo::kMaxGroups, R.ch_grp);
   pl.up(&R.slot_cam_d, std::max(NS, 1), R.slot_cam);
   pl.up(&R.e_meta_d, (size_t)E + 4, R.e_meta); pl.up(&R.slot_rec_d, 4 * (size_t)std::max(NS, 1), R.slot_rec);
   pl.up(&R.cam_s_off_d, C + 1, R.cam_s_off); pl.up(&R.cam_s_list_d, std::max(NS, 1), R.cam_s_list);
@@ -460,7 +483,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.add(&d.cam_cand, (size_t)SS * C);
   pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
   pl.add(&d.pt_cand, 3 * (size_t)P);
-  pl.add_raw(&d.J, std::max<size_t>(R.jpos, 8) * sJ);
+  if (!dyn) pl.add_raw(&d.J, std::max<size_t>(R.jpos, 8) * sJ);   // dynamic Jacobians: none
   pl.add_raw(&d.Hpp, 6 * (size_t)P * sA); pl.add_raw(&d.bp, 3 * (size_t)P * sA);
   pl.add_raw(&d.Hinv, 6 * (size_t)P * sA); pl.add_raw(&d.dp, 3 * (size_t)P * sA);
   pl.add_raw(&d.pt_rec, (size_t)std::max(P, 1) * (pr == Prec::F64 ? 64 : 32));
@@ -528,6 +551,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   d.xe_i = R.xe_i_d; d.xe_j = R.xe_j_d; d.xe_kind = R.xe_kind_d; d.xe_rec = R.xe_rec_d;
   d.xo_off = R.xo_off_d; d.xk_off = R.xk_off_d; d.xk_list = R.xk_list_d;
   d.e_meta = R.e_meta_d; d.slot_rec = reinterpret_cast<const int4*>(R.slot_rec_d);
+  d.ch_grp = R.ch_grp_d;
   d.dbg_r = nullptr;
   const cudaStream_t st = g->stream;
   {
@@ -535,7 +559,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
     const size_t n = R.pl.image(img);
     if (n) GPO_CUDA(g, cudaMemcpyAsync(base, img.data(), n, cudaMemcpyHostToDevice, st));
   }
-  GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(R.jpos, 8) * jt_size(g->prec), st));
+  if (d.J) GPO_CUDA(g, cudaMemsetAsync(d.J, 0, std::max<size_t>(R.jpos, 8) * jt_size(g->prec), st));
   GPO_CUDA(g, cudaMemsetAsync(d.dp, 0, 3 * (size_t)d.P * at_size(g->prec), st));
   GPO_CUDA(g, cudaMemcpyAsync(R.desc_d, &d, sizeof(DevBA), cudaMemcpyHostToDevice, st));
   gpo::LaunchSet ls{};
@@ -946,6 +970,9 @@ gpo_status gpo_graph_create(const gpo_graph_desc* desc, gpo_graph** out) {
   if (!g) return fail(nullptr, GPO_ERR_OOM, "host allocation failed");
   g->desc = *desc;
   g->prec = static_cast<Prec>(desc->precision);
+  // dynamic Jacobians store no rows: BF16 and FP32 storage are then one mode, FP32 rows
+  // evaluated where they are used
+  if (desc->spmv_variant == 4 && g->prec == Prec::BF16) g->prec = Prec::F32;
   // the stream, pinned staging and events are created at the first finalize (a graph
   // handed to a server runs on the server's stream and never needs its own)
   if (desc->cuda_stream) g->stream = static_cast<cudaStream_t>(desc->cuda_stream);
@@ -1324,6 +1351,8 @@ gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* pa
   if (s != GPO_OK) return s;
   const gpo_lm_params prm = params_or_default(params);
   if (!(prm.initial_damping > 0.0)) return fail(g, GPO_ERR_ARG, "initial damping must be positive");
+  if (prm.solver == GPO_SOLVER_FULL && !g->dev.J && g->dev.E > 0)
+    return fail(g, GPO_ERR_UNSUPPORTED, "the full-system solver reads stored rows; dynamic Jacobians keep none");
   Scalars sc;
   fill_scalars(g, prm, prm.initial_damping, sc);
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
@@ -1443,6 +1472,8 @@ gpo_status gpo_graph_info(gpo_graph* g, gpo_graph_info_t* out) {
   out->slots = d.NS;
   out->chunk_edges = g->ch_max;
   out->spmv_variant = g->desc.spmv_variant;
+  out->spmv_kernel = d.E > 0 ? g->ks->spmv_kind(g->ls, g->prec) : 0;
+  out->j_bytes = d.J ? (int64_t)(g->j_elems * jt_size(g->prec)) : 0;
   return GPO_OK;
 }
 
@@ -1496,6 +1527,8 @@ static gpo_status debug_linearize_rows(gpo_graph* g, const int64_t* sel, int64_t
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);
   if (s != GPO_OK) return s;
+  if (!g->dev.J)
+    return fail(g, GPO_ERR_UNSUPPORTED, "dynamic Jacobians keep no rows to return (gpo_debug_autodiff_edges evaluates them)");
   const gpo::KernelSet& ks = *g->ks;
   const int M = ks.M, DC = ks.DC, DB = ks.DB, NJ = ks.NJ;
   const bool nav = ks.model == gpo::ModelKind::STEREO;

@@ -230,6 +230,8 @@ gpo_status gpo_optimize_batch(gpo_graph* const* graphs, int32_t n, int32_t max_i
     if (!graphs[i]) return fail(owner, GPO_ERR_ARG, "graph %d is null", i);
     if (graphs[i]->prec != owner->prec || graphs[i]->desc.device != owner->desc.device)
       return fail(owner, GPO_ERR_ARG, "graphs of a batch must share precision and device");
+    if (graphs[i]->desc.spmv_variant == 4)
+      return fail(owner, GPO_ERR_UNSUPPORTED, "graphs with dynamic Jacobians are solved alone");
     for (int j = 0; j < i; ++j)
       if (graphs[j] == graphs[i]) return fail(owner, GPO_ERR_ARG, "graph %d appears twice", i);
   }
@@ -353,6 +355,8 @@ gpo_status gpo_server_submit(gpo_server* sv, gpo_graph* g, int32_t max_iters, co
   if (!sv || !g || max_iters < 0) return GPO_ERR_ARG;
   if (g->prec != sv->owner->prec || g->desc.device != sv->owner->desc.device)
     return fail(sv->owner, GPO_ERR_ARG, "graph precision or device differs from the server's");
+  if (g->desc.spmv_variant == 4)
+    return fail(sv->owner, GPO_ERR_UNSUPPORTED, "graphs with dynamic Jacobians are solved alone");
   if (g->finalized) return fail(sv->owner, GPO_ERR_STATE, "graph is already resident on the device");
   const gpo::KernelSet* k = &kernels_of(g);
   if (sv->owner->ks && sv->owner->ks != k)

@@ -26,6 +26,8 @@ constexpr int kThreads = 256;       // CTA size of the chunk kernels
 constexpr int kPtDim = 3;
 constexpr int kCamPerBlock = 8;     // cameras (warps) per CTA in camera kernels
 constexpr int kMaxDevices = 64;     // per-device launch caches
+constexpr int kGroupEdges = 64;     // edges of a warp group (two per lane) of a chunk
+constexpr int kMaxGroups = 16;      // warp groups per chunk
 constexpr int kMaxHistory = 4096;
 
 // Edge models (the kernel set a graph runs).
@@ -113,6 +115,9 @@ struct DevBA {
   const uint16_t* e_slot;    // [E] slot of the edge inside its chunk
   const uint16_t* ch_sorted; // [E] per chunk: local edge ids sorted by (slot, id)
   const uint32_t* e_meta;    // [E + 4] packed pos | slot << 10 | local point << 20 (chunks <= 1024)
+  const uint16_t* ch_grp;    // [NCH][kMaxGroups] local edge offset where warp group g of the
+                             // chunk ends (groups of whole points, <= kGroupEdges edges
+                             // unless one point has more)
   const int4* slot_rec;      // [NS] local edge range [x, y) in slot order, camera z, partial row w
   const int* slot_e0;        // [NS+1] range of a slot in ch_sorted (global positions)
   const int* slot_cam;       // [NS]
@@ -229,6 +234,7 @@ struct KernelSet {
   int (*decide)(const LaunchSet& ls, Prec pr, cudaStream_t st);
   int (*commit)(const LaunchSet& ls, cudaStream_t st);
   int (*max_supported_ch)(Prec pr);
+  int (*spmv_kind)(const LaunchSet& ls, Prec pr);   // the Schur-product kernel pcg_spmv runs
 };
 const KernelSet& kernels_ba();       // ba_kernels.cu
 const KernelSet& kernels_stereo();   // vi_kernels.cu

@@ -420,17 +420,54 @@ struct ModelBA {
   }
 
   // Whitened residual, Huber, and the whitened, sqrt(rho')-scaled Jacobian rows on the
-  // chart (left rotation update, additive rest), computed in AT from FP64 geometry.
+  // chart (left rotation update, additive rest).  FP64 accumulation: everything in FP64.
+  // FP32 accumulation (the mixed modes): only the camera-frame point P = R X + t is
+  // formed in FP64 (world coordinates of hundreds of units cancel there down to depths
+  // of a few); the projection, distortion, residual and rows follow in FP32 from it.
   template <class AT>
   __device__ static void eval(const DevBA& d, int e, const double* rb, const double* X, double (&r)[M],
                               double& rho, double& sw, AT (&Jc)[M][DC], AT (&Jp)[M][3]) {
-    Geom g;
-    geom(rb, X, g);
-    residual(d, e, g, r);
     rho = 0.0;
-    sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e));
+    AT y[3], p0, p1, r2, dd, iz;
+    if constexpr (std::is_same<AT, float>::value) {
+      float P[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double yi = rb[3 * i] * X[0] + rb[3 * i + 1] * X[1] + rb[3 * i + 2] * X[2];
+        y[i] = (float)yi;
+        P[i] = (float)(yi + rb[9 + i]);
+      }
+      iz = 1.0f / P[2];
+      p0 = -P[0] * iz;
+      p1 = -P[1] * iz;
+      r2 = p0 * p0 + p1 * p1;
+      dd = 1.0f + r2 * ((float)rb[13] + (float)rb[14] * r2);
+      const float fd = (float)rb[12] * dd;
+      const double2 z = __ldg(reinterpret_cast<const double2*>(d.obs) + e);
+      float r0 = fmaf(fd, p0, -(float)z.x), r1 = fmaf(fd, p1, -(float)z.y);
+      if (d.e_sqinfo) {
+        const double* U = d.e_sqinfo + NQ * (size_t)e;
+        const float a = (float)U[0] * r0 + (float)U[1] * r1;
+        r1 = (float)U[2] * r1;
+        r0 = a;
+      }
+      r[0] = r0;
+      r[1] = r1;
+      sw = huber_weight<float>((double)(r0 * r0 + r1 * r1), __ldg(d.e_delta + e));
+    } else {
+      Geom g;
+      geom(rb, X, g);
+      residual(d, e, g, r);
+      sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e));
+      p0 = g.p[0];
+      p1 = g.p[1];
+      r2 = g.r2;
+      dd = g.d;
+      iz = g.iz;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) y[i] = g.y[i];
+    }
     const AT f = (AT)rb[12], k1 = (AT)rb[13], k2 = (AT)rb[14];
-    const AT p0 = (AT)g.p[0], p1 = (AT)g.p[1], r2 = (AT)g.r2, dd = (AT)g.d, iz = (AT)g.iz;
     const AT c2 = (AT)2 * k1 + (AT)4 * k2 * r2;
     // du/dp = f (d I + c2 p p^T)
     const AT A00 = f * (dd + c2 * p0 * p0), A01 = f * c2 * p0 * p1, A11 = f * (dd + c2 * p1 * p1);
@@ -439,14 +476,13 @@ struct ModelBA {
     AT D[2][3];
     D[0][0] = -A00 * iz; D[0][1] = -A01 * iz; D[0][2] = A00 * B02 + A01 * B12;
     D[1][0] = -A01 * iz; D[1][1] = -A11 * iz; D[1][2] = A01 * B02 + A11 * B12;
-    const AT y0 = (AT)g.y[0], y1 = (AT)g.y[1], y2 = (AT)g.y[2];
     const AT pp[2] = {p0, p1};
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
       // dP/d(dw) = -[y]_x : column k is e_k x y
-      Jc[a][0] = -D[a][1] * y2 + D[a][2] * y1;
-      Jc[a][1] = D[a][0] * y2 - D[a][2] * y0;
-      Jc[a][2] = -D[a][0] * y1 + D[a][1] * y0;
+      Jc[a][0] = -D[a][1] * y[2] + D[a][2] * y[1];
+      Jc[a][1] = D[a][0] * y[2] - D[a][2] * y[0];
+      Jc[a][2] = -D[a][0] * y[1] + D[a][1] * y[0];
       Jc[a][3] = D[a][0];
       Jc[a][4] = D[a][1];
       Jc[a][5] = D[a][2];

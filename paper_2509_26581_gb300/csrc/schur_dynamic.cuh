@@ -34,6 +34,23 @@ __device__ __forceinline__ void dyn_row(const DevBA& d, int e, AT (&row)[Dims<Mo
   }
 }
 
+// The row of edge e for the per-edge kernels: read from storage, or (kDyn: dynamic
+// Jacobians, no rows stored) evaluated from the current state in the accumulation type.
+template <class Mo, class JT, class AT, bool kDyn>
+__device__ __forceinline__ void row_of(const DevBA& d, const JT* J, int e, AT (&row)[Mo::NJ]) {
+  if constexpr (kDyn) {
+    constexpr int NJU = Dims<Mo>::NJU;
+    AT r[NJU];
+    dyn_row<Mo, AT>(d, e, r);
+#pragma unroll
+    for (int k = 0; k < NJU; ++k) row[k] = r[k];
+#pragma unroll
+    for (int k = NJU; k < Mo::NJ; ++k) row[k] = (AT)0;
+  } else {
+    load_row_t<Mo::NJ>(J, (size_t)e, row);
+  }
+}
+
 template <class Mo, class AT, int EPT>
 __global__ void __launch_bounds__(kThreads) k_spmv_dyn(LaunchSet ls) {
   constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, JP0 = Dims<Mo>::JP0, NJU = Dims<Mo>::NJU,

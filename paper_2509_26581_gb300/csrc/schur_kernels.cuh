@@ -25,6 +25,7 @@
 
 #include "schur_common.cuh"
 #include "schur_spmv.cuh"
+#include "schur_wg.cuh"
 #include "schur_dynamic.cuh"
 
 namespace gpo {
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     }
 #pragma unroll
     for (int k = NJU; k < NJ; ++k) row[k] = cvj((AT)0, (const JT*)nullptr);
-    store_row_t<NJ>(Jg, (size_t)e, row);
+    if (Jg) store_row_t<NJ>(Jg, (size_t)e, row);   // dynamic Jacobians keep no rows
     srt[i] = d.ch_sorted[e];
     AT* re = rec + (size_t)i * RSG;
     JT* ye = yrec + (size_t)i * RSY;
@@ -433,7 +434,7 @@ struct SchurRec {
 // One CTA per chunk: damped point inverses H_pp^-1 (and the point records of the Schur
 // product), then per-slot partials of sum_e W_e H_pp^-1 W_e^T and sum_e W_e H_pp^-1 b_p
 // (W_e = Jc^T Jp, from the stored Jacobian rows).
-template <class Mo, class JT>
+template <class Mo, class JT, bool kDyn = false>
 __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_schur_prepare(LaunchSet ls) {
     const AT* hi = pv + 9 * pl;
     const AT* hb = hi + 6;
     AT row[NJ];
-    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
+    row_of<Mo, JT, AT, kDyn>(d, Jg, cr.e0 + i, row);
     srt[i] = d.ch_sorted[cr.e0 + i];
     AT t[M][3];
 #pragma unroll
@@ -1160,7 +1161,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
 // One CTA per chunk: dp = H_pp^-1 (-b_p - sum_e Jp^T Jc dc) (the full-system PCG's
 // point rows instead when it solved them) and the chunk's share of the model decrease
 // -b_p^T dp - 1/2 sum_e |Jc dc + Jp dp|^2 (FP64 accumulation).
-template <class Mo, class JT>
+template <class Mo, class JT, bool kDyn = false>
 __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
@@ -1181,7 +1182,7 @@ __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
   for (int i = threadIdx.x; i < cr.nE; i += kThreads) {
     const int c = __ldg(d.e_cam + cr.e0 + i);
     AT row[NJ];
-    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
+    row_of<Mo, JT, AT, kDyn>(d, Jg, cr.e0 + i, row);
     AT q[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) q[a] = (AT)0;
@@ -1234,7 +1235,7 @@ __global__ void __launch_bounds__(kThreads) k_backsub(LaunchSet ls) {
     const int pj = __ldg(d.e_pt + cr.e0 + i);
     const AT t0 = dp[3 * (size_t)pj], t1 = dp[3 * (size_t)pj + 1], t2 = dp[3 * (size_t)pj + 2];
     AT row[NJ];
-    load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
+    row_of<Mo, JT, AT, kDyn>(d, Jg, cr.e0 + i, row);
     double sq = 0.0;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
@@ -1520,11 +1521,18 @@ struct Launch {
     else lin_t<__nv_bfloat16>(ls, pr, force, st);
     return 1;
   }
+  // Dynamic Jacobians (spmv_variant 4) keep no rows: the per-edge kernels evaluate them.
+  static bool dyn_rows(const LaunchSet& ls) { return ls.spmv_variant == 4; }
+  template <class JT, bool kDyn>
+  static void schur_k(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = schur_smem(pr, ls.ch_max, ls.np_max);
+    set_smem(reinterpret_cast<const void*>(k_schur_prepare<Mo, JT, kDyn>), sm);
+    launch_pdl(k_schur_prepare<Mo, JT, kDyn>, ls.n_ch, kThreads, sm, st, ls);
+  }
   template <class JT>
   static void schur_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-    const size_t sm = schur_smem(pr, ls.ch_max, ls.np_max);
-    set_smem(reinterpret_cast<const void*>(k_schur_prepare<Mo, JT>), sm);
-    launch_pdl(k_schur_prepare<Mo, JT>, ls.n_ch, kThreads, sm, st, ls);
+    if (dyn_rows(ls)) schur_k<JT, true>(ls, pr, st);
+    else schur_k<JT, false>(ls, pr, st);
   }
   static int schur_prepare(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
@@ -1635,8 +1643,56 @@ struct Launch {
     else if (ept <= 2) pp_e<JT, 2>(ls, pr, st);
     else pp_e<JT, 4>(ls, pr, st);
   }
+  static size_t wg_smem(Prec pr, const LaunchSet& ls) {
+    return wg_layout<Mo>(sA(pr), ls.ch_max, ls.ns_max).size;
+  }
+  // The warp-group kernel (spmv_variant 5) reads packed edge words (chunks of at most
+  // 1024 edges) and keeps the rows in registers (BF16 or FP32 storage).
+  static bool wg_ok(Prec pr, const LaunchSet& ls) {
+    return ls.spmv_variant == 5 && pr != Prec::F64 && ls.ch_max <= 1024 && wg_smem(pr, ls) <= 200 * 1024;
+  }
+  template <class JT>
+  static void wg_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = wg_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_spmv_wg<Mo, JT>), sm);
+    struct Occ {
+      std::atomic<int> n_sm{0}, occ{0};
+      std::atomic<size_t> occ_sm{0};
+    };
+    static Occ cache[kMaxDevices];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Occ& o = cache[dev >= 0 && dev < kMaxDevices ? dev : 0];
+    if (!o.n_sm.load()) {
+      int n = 0;
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      o.n_sm.store(std::max(n, 1));
+    }
+    if (o.occ_sm.load() != sm) {
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_wg<Mo, JT>, kThreads, sm);
+      o.occ.store(std::max(occ, 1));
+      o.occ_sm.store(sm);
+    }
+    const int grid = std::max(1, std::min(ls.n_ch, o.n_sm.load() * o.occ.load()));
+    launch_pdl(k_spmv_wg<Mo, JT>, grid, kThreads, sm, st, ls);
+  }
+  // The Schur-product kernel pcg_spmv dispatches for this launch set (spmv_variant
+  // numbering: 1 staged, 2 classic, 3 pipelined, 4 dynamic, 5 warp groups).
+  static int spmv_kind(const LaunchSet& ls, Prec pr) {
+    if (wg_ok(pr, ls)) return 5;
+    if (dyn_ok(ls)) return 4;
+    if (pp_ok(pr, ls)) return 3;
+    if (ws_ok(pr, ls)) return 1;
+    return 2;
+  }
   static int pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
+    if (wg_ok(pr, ls)) {
+      if (pr == Prec::F32) wg_t<float>(ls, pr, st);
+      else wg_t<__nv_bfloat16>(ls, pr, st);
+      return 1;
+    }
     if (dyn_ok(ls)) {
       if (pr == Prec::F64) dyn_t<double>(ls, pr, st);
       else dyn_t<float>(ls, pr, st);
@@ -1750,11 +1806,16 @@ struct Launch {
     else launch_pdl(k_pcg_update<Mo, float>, ls.n_cb, kCamPerBlock * 32, 0, st, ls);
     return 1;
   }
+  template <class JT, bool kDyn>
+  static void backsub_k(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = backsub_smem(pr, ls.ch_max);
+    set_smem(reinterpret_cast<const void*>(k_backsub<Mo, JT, kDyn>), sm);
+    launch_pdl(k_backsub<Mo, JT, kDyn>, ls.n_ch, kThreads, sm, st, ls);
+  }
   template <class JT>
   static void backsub_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
-    const size_t sm = backsub_smem(pr, ls.ch_max);
-    set_smem(reinterpret_cast<const void*>(k_backsub<Mo, JT>), sm);
-    launch_pdl(k_backsub<Mo, JT>, ls.n_ch, kThreads, sm, st, ls);
+    if (dyn_rows(ls)) backsub_k<JT, true>(ls, pr, st);
+    else backsub_k<JT, false>(ls, pr, st);
   }
   static int backsub(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
@@ -1812,6 +1873,7 @@ KernelSet make_kernel_set(ModelKind kind) {
   k.decide = &L::decide;
   k.commit = &L::commit;
   k.max_supported_ch = &L::max_supported_ch;
+  k.spmv_kind = &L::spmv_kind;
   return k;
 }
 

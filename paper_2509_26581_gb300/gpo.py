@@ -35,7 +35,8 @@ class gpo_graph_desc(C.Structure):
                 ("reserve_vertices", C.c_int64), ("reserve_edges", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
                 ("alloc_ctx", C.c_void_p), ("memory_budget", C.c_size_t),
-                ("chunk_edges", C.c_int32), ("spmv_variant", C.c_int32)]
+                ("chunk_edges", C.c_int32), ("spmv_variant", C.c_int32), ("spmv_kernel", C.c_int32),
+                ("reserved0", C.c_int32), ("j_bytes", C.c_int64)]
 
 
 class gpo_lm_params(C.Structure):
@@ -64,7 +65,8 @@ class gpo_iter_record(C.Structure):
 class gpo_graph_info_t(C.Structure):
     _fields_ = [("cameras", C.c_int64), ("points", C.c_int64), ("edges", C.c_int64),
                 ("extra_edges", C.c_int64), ("chunks", C.c_int64), ("slots", C.c_int64),
-                ("chunk_edges", C.c_int32), ("spmv_variant", C.c_int32)]
+                ("chunk_edges", C.c_int32), ("spmv_variant", C.c_int32), ("spmv_kernel", C.c_int32),
+                ("reserved0", C.c_int32), ("j_bytes", C.c_int64)]
 
 
 class gpo_kernel_profile(C.Structure):

@@ -49,8 +49,8 @@ class Stream:
     """
 
     def __init__(self, seed: int, stream: int):
-        base = splitmix64(np.array([seed & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))
-        self.key = splitmix64(base + np.array([stream], dtype=np.uint64) * _GOLDEN)[0]
+        base = splitmix64(np.array([int(seed) & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64))
+        self.key = splitmix64(base + np.array([int(stream)], dtype=np.uint64) * _GOLDEN)[0]
         self.counter = 0
 
     def u64(self, n: int) -> np.ndarray:
@@ -420,7 +420,7 @@ def fresh_request(base: BAProblem, seed: int, i: int, pixel_sigma: float = 0.5,
     streams keyed by (seed, i).  Every request is a distinct problem with a distinct
     optimum, at a cost of a few array operations (generating a new window topology takes
     milliseconds, too slow for thousands of requests per second)."""
-    rng = Stream(seed * 1000003 + i, 23)
+    rng = Stream(int(seed) * 1000003 + int(i), 23)
     E, C, P = base.n_edges, base.n_cams, base.n_pts
     obs = base.obs + rng.normal(2 * E, pixel_sigma).reshape(E, 2)
     cams0 = base.cams0.copy()

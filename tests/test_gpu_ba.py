@@ -212,9 +212,10 @@ def test_mixed_precision_final_cost_close_to_fp64(gpo, prec):
     assert abs(costs["fp64"] - orep.final_cost) <= 1e-6 * orep.final_cost
 
 
-def _check_sampled_edges(p, idx, r, J):
+def _check_sampled_edges(p, idx, r, J, random_sample=True):
     """Rows r, J of the sampled edges idx (GPU, FP64 build) against the oracle's, one edge
-    at a time, within each edge's rounding bound."""
+    at a time, within each edge's rounding bound; a random sample also has a median
+    residual error within 1e-12 (most edges are well conditioned)."""
     sub = synth.BAProblem("s", 0, p.cams_gt, p.pts_gt, p.cams0, p.pts0, p.cam_idx[idx],
                           p.pt_idx[idx], p.obs[idx], p.is_outlier[idx], p.huber_delta)
     ro, Jo = _oracle_weighted_rows(sub)
@@ -238,7 +239,8 @@ def _check_sampled_edges(p, idx, r, J):
     huber = rn > p.huber_delta
     rel = 32 * eps * kappa + 1e-12 + np.where(huber, 32 * eps * cams[:, 6] * kappa / np.maximum(rn, 1.0), 0.0)
     assert np.all(dJ <= rel * Js)
-    assert np.median(dr / np.maximum(np.abs(ro).max(axis=1), 1.0)) < 1e-12
+    if random_sample:
+        assert np.median(dr / np.maximum(np.abs(ro).max(axis=1), 1.0)) < 1e-12
     return kappa
 
 
@@ -274,7 +276,7 @@ def test_large_size_sampled_edges_and_accepted_steps(gpo):
     tail = np.nonzero(first_cam[p.pt_idx] >= p.n_cams - 3)[0][:64]
     assert len(tail) > 8
     rt, Jt = g.debug_linearize_edges(tail)
-    _check_sampled_edges(p, tail, rt, Jt)
+    _check_sampled_edges(p, tail, rt, Jt, random_sample=False)
     for prec, graph in (("fp64", g), ("bf16", None)):
         if graph is None:
             g.close()
@@ -431,3 +433,26 @@ def test_mixed_precision_converges_to_fp64_at_300k_edges(gpo, prec):
         costs[pr] = g.optimize(50, prm).final_cost
         g.close()
     assert abs(costs[prec] - costs["fp64"]) <= 1e-6 * costs["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("case", ["path", "long_tracks"])
+def test_warp_group_product_matches_classic(gpo, prec, case):
+    """The warp-group Schur product (spmv_variant 5: rows in registers, point sums by a
+    segmented warp scan; points with more than 64 edges take the strided path) against
+    the classic one on the same chunks: one damped step solved by three PCG iterations
+    (FP32 products that differ only in summation order: 1e-4 of the step), and four LM
+    iterations (final cost within 1e-5).  The long-track case has 70 views per point."""
+    p = synth.ba_path(3, 40, 6000, "pareto") if case == "path" else synth.ba_ring(21, 80, 400, 70)
+    n_dof = 9 * p.n_cams + 3 * p.n_pts
+    steps, costs = [], []
+    for variant in (2, 5):
+        g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec,
+                               spmv_variant=variant, chunk_edges=512)
+        dx, its = g.debug_step(1e-2, n_dof, gpo.default_params(pcg_max_iters=3, pcg_tol=0.0))
+        assert its == 3
+        steps.append(dx)
+        costs.append(g.optimize(4, gpo.default_params(pcg_max_iters=50, pcg_tol=1e-6)).final_cost)
+        g.close()
+    assert np.max(np.abs(steps[1] - steps[0])) <= 1e-4 * np.max(np.abs(steps[0]))
+    assert abs(costs[1] - costs[0]) <= 1e-5 * costs[0]

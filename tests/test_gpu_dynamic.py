@@ -1,14 +1,16 @@
-"""Schur product with dynamic Jacobians (spmv_variant 4: each edge's rows recomputed
-from the state in every product instead of read from storage) against the FP64
-oracle and against the stored-row product, through the C ABI.
+"""Dynamic Jacobians (spmv_variant 4: no rows are stored; every kernel that needs an
+edge's rows -- the Schur preparation, each Schur product, the back-substitution --
+evaluates them from the state) against the FP64 oracle and against stored rows,
+through the C ABI.
 
 Tolerances (written here, derived from the arithmetic):
   * FP64: the rows are the stored rows (same evaluation, same accumulation order), so
     the LM run matches the stored-row run to 1e-12 relative in cost and 1e-10 in the
     states (rounding and FMA contraction of the same expressions in another kernel),
     and the oracle's exact-step LM run to 1e-9 in cost, as the stored-row tests do;
-  * FP32 accumulation (BF16 or FP32 storage): the product uses the unrounded FP32 rows,
-    so the run converges to the FP64 optimum within 1e-6, the mixed-precision bar.
+  * FP32 accumulation (BF16 or FP32 storage, one mode here since nothing is stored):
+    FP32 rows everywhere, so the run converges to the FP64 optimum within 1e-6, the
+    mixed-precision bar.
 """
 import numpy as np
 import pytest
@@ -41,6 +43,8 @@ def test_dynamic_fp64_matches_stored_rows_and_the_oracle(gpo):
         g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp64", cam_fixed=cf,
                                  pt_fixed=pf, spmv_variant=variant, chunk_edges=256)
         rep = g.optimize(10, _exact(gpo))
+        info = g.info()
+        assert info["spmv_kernel"] == variant and (info["j_bytes"] == 0) == (variant == 4)
         runs.append((rep, g.get_state(c0, p.n_cams, 9), g.get_state(p0, p.n_pts, 3)))
     (rd, cd, pd), (rs, cs, ps) = runs
     assert abs(rd.final_cost - rs.final_cost) <= 1e-12 * rs.final_cost
@@ -60,8 +64,8 @@ def test_dynamic_mixed_precision_reaches_the_fp64_optimum(gpo, prec):
     ref = g.optimize(30).final_cost
     h, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec,
                            spmv_variant=4, chunk_edges=512)
-    assert h.knobs["spmv_variant"] == 4
     cost = h.optimize(30).final_cost
+    assert h.info()["spmv_kernel"] == 4 and h.info()["j_bytes"] == 0
     assert abs(cost - ref) <= 1e-6 * ref
 
 
@@ -72,8 +76,44 @@ def test_dynamic_vi_fp64_matches_stored_rows(gpo):
     for variant in (4, 2):
         g, n0, p0, _ = gpo.vi_graph(p, precision="fp64", spmv_variant=variant, chunk_edges=256)
         rep = g.optimize(6, _exact(gpo))
+        assert g.info()["spmv_kernel"] == variant
         runs.append((rep.final_cost, g.get_state(n0, p.n_kf, 16), g.get_state(p0, p.n_pts, 3)))
     (fd, nd, qd), (fs, ns, qs) = runs
     assert abs(fd - fs) <= 1e-12 * fs
     assert np.abs(nd - ns).max() <= 1e-10 * max(np.abs(ns).max(), 1.0)
     assert np.abs(qd - qs).max() <= 1e-10 * max(np.abs(qs).max(), 1.0)
+
+
+def test_dynamic_rows_are_not_stored(gpo):
+    """The device footprint drops by the row array; BF16 and FP32 requests are one mode
+    (FP32 rows evaluated where used) and give the same run bit for bit; what needs stored
+    rows is refused with GPO_ERR_UNSUPPORTED."""
+    p = synth.ba_path(3, 40, 6000, "pareto")
+    out = {}
+    for prec, variant in (("bf16", 2), ("bf16", 4), ("fp32", 4)):
+        g, _, _ = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec,
+                               spmv_variant=variant, chunk_edges=512)
+        rep = g.optimize(5)
+        out[(prec, variant)] = (rep.final_cost, g.footprint(), g.info())
+        if variant == 4:
+            with pytest.raises(gpo.GpoError) as ei:
+                g.debug_linearize(p.n_edges)
+            assert ei.value.status == gpo.GPO_ERR_UNSUPPORTED
+            with pytest.raises(gpo.GpoError) as ei:
+                g.optimize(1, gpo.default_params(solver=gpo.GPO_SOLVER_FULL))
+            assert ei.value.status == gpo.GPO_ERR_UNSUPPORTED
+        g.close()
+    stored, dyn16, dyn32 = out[("bf16", 2)], out[("bf16", 4)], out[("fp32", 4)]
+    assert stored[2]["j_bytes"] >= 24 * 2 * p.n_edges and dyn16[2]["j_bytes"] == 0
+    assert stored[1] - dyn16[1] >= stored[2]["j_bytes"] - 4096
+    assert dyn16[0] == dyn32[0]
+    assert abs(dyn16[0] - stored[0]) <= 1e-4 * stored[0]
+
+
+def test_dynamic_graphs_are_solved_alone(gpo):
+    p = synth.ba_ring(0, 10, 500, 6)
+    gs = [gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, None, "fp32", spmv_variant=4)[0]
+          for _ in range(2)]
+    with pytest.raises(gpo.GpoError) as ei:
+        gpo.optimize_batch(gs, 2)
+    assert ei.value.status == gpo.GPO_ERR_UNSUPPORTED
