@@ -230,7 +230,8 @@ def load_peaks() -> tuple[float, str]:
 # ncu, keyed by (precision, kernel, hash of the kernel sources): stale once the sources
 # change.
 MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "a9188123b2cd"): 179.6e6}
-SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3, "dynamic": 4, "warpgroup": 5}
+SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3, "dynamic": 4, "warpgroup": 5,
+                 "warpgroup_staged": 6}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
 
 
@@ -246,6 +247,8 @@ def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
 def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
     """The Schur-product kernel the library runs for these knobs (gpo_graph_desc)."""
     v = knobs.get("spmv_variant", 0)
+    if v == 6 and ch_max <= 1024 and precision != "fp64":
+        return "k_spmv_wgs"
     if v == 5 and ch_max <= 1024 and precision != "fp64":
         return "k_spmv_wg"
     if v == 4 and ch_max <= 512:
@@ -257,7 +260,8 @@ def spmv_kernel(precision: str, knobs: dict, ch_max: int) -> str:
     return "k_spmv"
 
 
-KERNEL_LABEL = {"k_spmv_wg": "k_spmv_wg (PCG Schur product, warp groups)",
+KERNEL_LABEL = {"k_spmv_wgs": "k_spmv_wgs (PCG Schur product, warp groups fed through shared-memory stages)",
+                "k_spmv_wg": "k_spmv_wg (PCG Schur product, warp groups)",
                 "k_spmv_pp": "k_spmv_pp (PCG Schur product, pipelined persistent)",
                 "k_spmv_ws": "k_spmv_ws (PCG Schur product, staged)",
                 "k_spmv": "k_spmv (PCG Schur product, classic)",

@@ -78,9 +78,10 @@ struct Scalars {
   int pcg_products;      // Schur products of the current solve (iterations + restarts)
   int full;              // PCG on the full damped system (cameras and points) instead of
                          // the camera Schur complement
-  int pcg_fail;          // the solve broke down before its first step (r^T M r or p^T S p not
-                         // positive, or not finite): a failed linear solve, the LM step is
-                         // rejected
+  int pcg_fail;          // the solve broke down (r^T M r or p^T S p not positive, or not
+                         // finite, before the tolerance was met): the damped system is not
+                         // positive definite in the working precision; a failed linear
+                         // solve, the LM step is rejected
   int have_best;         // the rejection-ratio guard has saved an iterate
 };
 

@@ -363,7 +363,10 @@ struct ModelBA {
   static constexpr int M = 2, DC = 9, DB = 9, SS = 9, NJ = 24, NQ = 3;   // NQ: packed sqrt-info
   static constexpr bool kExtra = false;
 
-  __device__ static void render(const DevBA&, const double* cam, double* rb) {
+  // Not inlined: the retraction and the camera preparation call the same compiled body,
+  // so a state renders to the same bits on both paths (inlined copies may contract the
+  // arithmetic into FMAs differently and differ in the last bit).
+  __device__ static __noinline__ void render(const DevBA&, const double* cam, double* rb) {
     aa_to_R(cam, rb);
     for (int i = 0; i < 6; ++i) rb[9 + i] = cam[3 + i];
     rb[15] = 0.0;
@@ -572,7 +575,7 @@ struct ModelStereo {
   static constexpr int M = 3, DC = 6, DB = 15, SS = 16, NJ = 32, NQ = 6;
   static constexpr bool kExtra = true;
 
-  __device__ static void render(const DevBA&, const double* x, double* rb) {
+  __device__ static __noinline__ void render(const DevBA&, const double* x, double* rb) {   // not inlined: see ModelBA
     const double q[4] = {x[3], x[0], x[1], x[2]};
     q_to_R(q, rb);
     rb[9] = x[4]; rb[10] = x[5]; rb[11] = x[6];

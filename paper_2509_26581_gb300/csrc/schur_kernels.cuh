@@ -860,7 +860,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       sc->alpha = 0.0;
       sc->pcg_done = 1;
-      if (sc->pcg_it == 0) sc->pcg_fail = 1;   // no step taken: S is not positive definite
+      sc->pcg_fail = 1;   // p^T S p not positive: S is not positive definite at this damping
       atomicSub(ls.running, 1);
     } else {
       sc->alpha = sc->rz / pAp;
@@ -950,6 +950,9 @@ __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, in
     if (rtrue <= sc->tol_abs || sc->pcg_it >= sc->max_it || !isfinite(rtrue) || !(rz > 0.0)) {
       done = 1;
       if (!isfinite(rtrue)) sc->use_best = 1;
+      // r^T M r not positive before the tolerance is met: the preconditioned system is
+      // not positive definite at this damping
+      if (!(rz > 0.0) && !(rtrue <= sc->tol_abs)) sc->pcg_fail = 1;
     }
     sc->beta = restart ? 0.0 : rz / sc->rz;   // a restart starts the direction from z
     if (sc->normalize && n > 0.0) {
@@ -1002,7 +1005,7 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
         sc->alpha = alpha_d;
         if (bad) {
           sc->pcg_done = 1;
-          if (sc->pcg_it == 0) sc->pcg_fail = 1;   // no step taken: S is not positive definite
+          sc->pcg_fail = 1;   // p^T S p not positive: S is not positive definite at this damping
           atomicSub(ls.running, 1);
         }
       }
@@ -1318,9 +1321,10 @@ __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
   const double L = block_sum(md, red);
   if (threadIdx.x != 0) return;
   const double F = sc->cost;
-  // a linear solve that broke down before its first step, or whose best iterate is the
-  // zero start, failed: the step is rejected and the damping grows (as a factorisation
-  // that finds the damped system indefinite rejects the step in the oracle)
+  // a linear solve that broke down (the damped system is not positive definite in the
+  // working precision), or whose best iterate is the zero start, failed: the step is
+  // rejected and the damping grows (as a factorisation that finds the damped system
+  // indefinite rejects the step in the oracle)
   const bool failed = sc->pcg_fail || (sc->use_best && !sc->have_best);
   const bool acc = !failed && L > 0.0 && isfinite(Fc) && Fc < F;
   const double rho = L != 0.0 ? (F - Fc) / L : 0.0;
@@ -1679,7 +1683,42 @@ struct Launch {
   }
   // The Schur-product kernel pcg_spmv dispatches for this launch set (spmv_variant
   // numbering: 1 staged, 2 classic, 3 pipelined, 4 dynamic, 5 warp groups).
+  static size_t wgs_smem(Prec pr, const LaunchSet& ls) {
+    const WgsLayout L = wgs_layout<Mo>(sJ(pr), sA(pr), ls.ch_max, ls.np_max, ls.ns_max);
+    return kWgsStages * (size_t)L.size + sA(pr) * Dm::VW * (size_t)(ls.ch_max + 1);
+  }
+  // The staged warp-group kernel (spmv_variant 6): as 5, fed through shared-memory stages.
+  static bool wgs_ok(Prec pr, const LaunchSet& ls) {
+    return ls.spmv_variant == 6 && pr != Prec::F64 && ls.ch_max <= 1024 && wgs_smem(pr, ls) <= 220 * 1024;
+  }
+  template <class JT>
+  static void wgs_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
+    const size_t sm = wgs_smem(pr, ls);
+    set_smem(reinterpret_cast<const void*>(k_spmv_wgs<Mo, JT>), sm);
+    struct Occ {
+      std::atomic<int> n_sm{0}, occ{0};
+      std::atomic<size_t> occ_sm{0};
+    };
+    static Occ cache[kMaxDevices];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Occ& o = cache[dev >= 0 && dev < kMaxDevices ? dev : 0];
+    if (!o.n_sm.load()) {
+      int n = 0;
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      o.n_sm.store(std::max(n, 1));
+    }
+    if (o.occ_sm.load() != sm) {
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_wgs<Mo, JT>, kWsThreads, sm);
+      o.occ.store(std::max(occ, 1));
+      o.occ_sm.store(sm);
+    }
+    const int grid = std::max(1, std::min(ls.n_ch, o.n_sm.load() * o.occ.load()));
+    launch_pdl(k_spmv_wgs<Mo, JT>, grid, kWsThreads, sm, st, ls);
+  }
   static int spmv_kind(const LaunchSet& ls, Prec pr) {
+    if (wgs_ok(pr, ls)) return 6;
     if (wg_ok(pr, ls)) return 5;
     if (dyn_ok(ls)) return 4;
     if (pp_ok(pr, ls)) return 3;
@@ -1688,6 +1727,11 @@ struct Launch {
   }
   static int pcg_spmv(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     if (ls.n_ch == 0) return 0;
+    if (wgs_ok(pr, ls)) {
+      if (pr == Prec::F32) wgs_t<float>(ls, pr, st);
+      else wgs_t<__nv_bfloat16>(ls, pr, st);
+      return 1;
+    }
     if (wg_ok(pr, ls)) {
       if (pr == Prec::F32) wg_t<float>(ls, pr, st);
       else wg_t<__nv_bfloat16>(ls, pr, st);
