@@ -229,7 +229,7 @@ def load_peaks() -> tuple[float, str]:
 # DRAM bytes (read + write) per Schur-product launch on the medium workload, counted by
 # ncu, keyed by (precision, kernel, hash of the kernel sources): stale once the sources
 # change.
-MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "a9188123b2cd"): 179.6e6}
+MEASURED_TRAFFIC = {("bf16", "k_spmv_pp", "e1dfda595ad1"): 181.9e6}
 SPMV_VARIANTS = {"auto": 0, "staged": 1, "classic": 2, "pipelined": 3, "dynamic": 4, "warpgroup": 5,
                  "warpgroup_staged": 6}
 KERNEL_SOURCES = ("schur_common.cuh", "schur_spmv.cuh")
@@ -439,6 +439,7 @@ def _converge(p, prec: str, iters: int, dev, stream, params) -> dict:
     last = h[-1]["cost"] if h else rep.final_cost
     return dict(final_cost=rep.final_cost, initial_cost=rep.initial_cost, accepted=rep.accepted,
                 pcg_iters=rep.pcg_iters_total, pcg_failed=int(sum(r["pcg_failed"] for r in h)),
+                pcg_breakdowns=int(sum(r["pcg_breakdown"] for r in h)),
                 last_step_rel_decrease=(last - rep.final_cost) / rep.final_cost, seconds=dt)
 
 

@@ -217,12 +217,14 @@ typedef struct {
   int32_t accepted;
   int32_t pcg_iters;
   int32_t pcg_products;       /* Schur products run: PCG iterations plus residual restarts */
-  int32_t pcg_failed;         /* 1: the PCG broke down before meeting its tolerance
-                                 (r^T M r or p^T S p not positive or not finite: the
-                                 damped system is not positive definite in the working
-                                 precision), or the best iterate kept by the
-                                 rejection-ratio guard is the zero start; the linear
-                                 solve failed, so the step was rejected */
+  int32_t pcg_failed;         /* 1: the PCG broke down before its first step (r^T M r or
+                                 p^T S p not positive or not finite: the damped system
+                                 is not positive definite in the working precision), or
+                                 the best iterate kept by the rejection-ratio guard is
+                                 the zero start; the linear solve failed, so the step
+                                 was rejected (lambda grows).  2: it broke down after a
+                                 step; the iterate was judged as any step, but lambda
+                                 was not lowered.  0: neither */
 } gpo_iter_record;
 
 /* Defaults for the two option structs.  Never fail for non-null pointers. */

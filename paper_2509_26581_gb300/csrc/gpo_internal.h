@@ -78,10 +78,12 @@ struct Scalars {
   int pcg_products;      // Schur products of the current solve (iterations + restarts)
   int full;              // PCG on the full damped system (cameras and points) instead of
                          // the camera Schur complement
-  int pcg_fail;          // the solve broke down (r^T M r or p^T S p not positive, or not
-                         // finite, before the tolerance was met): the damped system is not
-                         // positive definite in the working precision; a failed linear
-                         // solve, the LM step is rejected
+  int pcg_fail;          // the solve broke down before its first step (r^T M r or p^T S p
+                         // not positive, or not finite): no step; a failed linear solve,
+                         // the LM step is rejected
+  int pcg_breakdown;     // the solve broke down after a step (the damped system is at the
+                         // edge of positive definiteness in the working precision): the
+                         // iterate is a descent step, but the damping is not lowered
   int have_best;         // the rejection-ratio guard has saved an iterate
 };
 

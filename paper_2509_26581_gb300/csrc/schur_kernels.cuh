@@ -716,6 +716,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     // a nonzero right-hand side with r^T M r not positive: the preconditioner is not
     // positive definite at this damping, so no step can be taken
     sc->pcg_fail = (rr > 0.0 && (!(rz > 0.0) || !isfinite(rz))) ? 1 : 0;
+    sc->pcg_breakdown = 0;
     sc->have_best = 0;
     if (!sc->pcg_done) atomicAdd(ls.running, 1);
     sc->ticket = 0u;
@@ -860,7 +861,9 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       sc->alpha = 0.0;
       sc->pcg_done = 1;
-      sc->pcg_fail = 1;   // p^T S p not positive: S is not positive definite at this damping
+      // p^T S p not positive: S is not positive definite at this damping
+      if (sc->pcg_it == 0) sc->pcg_fail = 1;
+      else sc->pcg_breakdown = 1;
       atomicSub(ls.running, 1);
     } else {
       sc->alpha = sc->rz / pAp;
@@ -951,8 +954,8 @@ __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, in
       done = 1;
       if (!isfinite(rtrue)) sc->use_best = 1;
       // r^T M r not positive before the tolerance is met: the preconditioned system is
-      // not positive definite at this damping
-      if (!(rz > 0.0) && !(rtrue <= sc->tol_abs)) sc->pcg_fail = 1;
+      // not positive definite at this damping (after at least one step)
+      if (!(rz > 0.0) && !(rtrue <= sc->tol_abs)) sc->pcg_breakdown = 1;
     }
     sc->beta = restart ? 0.0 : rz / sc->rz;   // a restart starts the direction from z
     if (sc->normalize && n > 0.0) {
@@ -1005,7 +1008,9 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
         sc->alpha = alpha_d;
         if (bad) {
           sc->pcg_done = 1;
-          sc->pcg_fail = 1;   // p^T S p not positive: S is not positive definite at this damping
+          // p^T S p not positive: S is not positive definite at this damping
+          if (sc->pcg_it == 0) sc->pcg_fail = 1;
+          else sc->pcg_breakdown = 1;
           atomicSub(ls.running, 1);
         }
       }
@@ -1321,11 +1326,14 @@ __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
   const double L = block_sum(md, red);
   if (threadIdx.x != 0) return;
   const double F = sc->cost;
-  // a linear solve that broke down (the damped system is not positive definite in the
-  // working precision), or whose best iterate is the zero start, failed: the step is
-  // rejected and the damping grows (as a factorisation that finds the damped system
-  // indefinite rejects the step in the oracle)
+  // a linear solve that broke down before its first step (the damped system is not
+  // positive definite in the working precision), or whose best iterate is the zero
+  // start, failed: the step is rejected and the damping grows (as a factorisation that
+  // finds the damped system indefinite rejects the step in the oracle).  A solve that
+  // broke down after a step returns a descent step, judged as any other, but the
+  // damping that brought the system to the edge of definiteness is not lowered.
   const bool failed = sc->pcg_fail || (sc->use_best && !sc->have_best);
+  const bool hold = sc->pcg_breakdown != 0;
   const bool acc = !failed && L > 0.0 && isfinite(Fc) && Fc < F;
   const double rho = L != 0.0 ? (F - Fc) / L : 0.0;
   const int it = sc->iter;
@@ -1340,12 +1348,12 @@ __global__ void __launch_bounds__(kThreads) k_decide(LaunchSet ls) {
     h.accepted = acc ? 1 : 0;
     h.pcg_iters = sc->pcg_it;
     h.pcg_products = sc->pcg_products;
-    h.pcg_failed = failed ? 1 : 0;
+    h.pcg_failed = failed ? 1 : (hold ? 2 : 0);
   }
   double lam = sc->lambda, nu = sc->nu;
   if (acc) {
     const double t = 2.0 * rho - 1.0;
-    lam *= fmax(1.0 / 3.0, 1.0 - t * t * t);
+    if (!hold) lam *= fmax(1.0 / 3.0, 1.0 - t * t * t);
     nu = 2.0;
     sc->cost = Fc;
     sc->n_accepted += 1;

@@ -285,7 +285,7 @@ class Graph:
         return [dict(cost=r.cost, cand_cost=r.cand_cost, model_decrease=r.model_decrease,
                      rho=r.rho, lam=r.lambda_, pcg_residual=r.pcg_residual,
                      accepted=bool(r.accepted), pcg_iters=r.pcg_iters, pcg_products=r.pcg_products,
-                     pcg_failed=bool(r.pcg_failed))
+                     pcg_failed=r.pcg_failed == 1, pcg_breakdown=r.pcg_failed == 2)
                 for r in buf[:n.value]]
 
     def set_profiling(self, on: bool = True):
