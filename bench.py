@@ -168,12 +168,13 @@ NOMINAL_HBM_GBS = 7900.0
 # a hash of the kernel sources they were counted from, so changed kernels report null.
 FP64_SOURCES = ("schur_common.cuh", "schur_kernels.cuh")
 FP64_FLOPS_PER_EDGE = {
-    ("k_linearize", "bf16", "e4505b37f90b"): 49.0,
-    ("k_linearize", "fp64", "e4505b37f90b"): 449.29,
+    ("k_linearize", "bf16", "47c9a4360741"): 18.00,
+    ("k_linearize", "fp32", "47c9a4360741"): 18.00,
+    ("k_linearize", "fp64", "47c9a4360741"): 449.29,
     # one kernel for every precision (FP64 geometry and cost)
-    ("k_cost", "bf16", "e4505b37f90b"): 65.50,
-    ("k_cost", "fp32", "e4505b37f90b"): 65.50,
-    ("k_cost", "fp64", "e4505b37f90b"): 65.50,
+    ("k_cost", "bf16", "47c9a4360741"): 65.55,
+    ("k_cost", "fp32", "47c9a4360741"): 65.55,
+    ("k_cost", "fp64", "47c9a4360741"): 65.55,
 }
 
 

@@ -482,6 +482,7 @@ static gpo_status prepare(gpo_graph* g) {
   pl.add_raw(&d.xe_H, (size_t)std::max(NX, 1) * DB * DB * sA);
   pl.add(&d.cam_cand, (size_t)SS * C);
   pl.add(&d.camrb, 16 * (size_t)C); pl.add(&d.camrb_cand, 16 * (size_t)C);
+  pl.add(&d.camrbf, 16 * (size_t)C); pl.add(&d.camrbf_cand, 16 * (size_t)C);
   pl.add(&d.pt_cand, 3 * (size_t)P);
   if (!dyn) pl.add_raw(&d.J, std::max<size_t>(R.jpos, 8) * sJ);   // dynamic Jacobians: none
   pl.add_raw(&d.Hpp, 6 * (size_t)P * sA); pl.add_raw(&d.bp, 3 * (size_t)P * sA);

@@ -147,6 +147,8 @@ struct DevBA {
   double* cam_cand;          // [C][SS]
   double* camrb;             // [C][16] render block (BA: R t f k1 k2 pad; nav: R p pad)
   double* camrb_cand;        // [C][16]
+  float* camrbf;             // [C][16] the render block rounded to FP32 (mixed-precision rows)
+  float* camrbf_cand;        // [C][16]
   double* pt;                // [P][3]
   double* pt_cand;           // [P][3]
   // linear system

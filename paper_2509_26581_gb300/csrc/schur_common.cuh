@@ -427,25 +427,34 @@ struct ModelBA {
   // FP32 accumulation (the mixed modes): only the camera-frame point P = R X + t is
   // formed in FP64 (world coordinates of hundreds of units cancel there down to depths
   // of a few); the projection, distortion, residual and rows follow in FP32 from it.
+  // rb: the render block; rbf: the same rounded to FP32 (read by the FP32 path).  The
+  // residual r and the square root of the IRLS weight sw come out in AT.
   template <class AT>
-  __device__ static void eval(const DevBA& d, int e, const double* rb, const double* X, double (&r)[M],
-                              double& rho, double& sw, AT (&Jc)[M][DC], AT (&Jp)[M][3]) {
-    rho = 0.0;
-    AT y[3], p0, p1, r2, dd, iz;
+  __device__ static void eval(const DevBA& d, int e, const double* rb, const float* rbf, const double* X,
+                              AT (&r)[M], AT& sw, AT (&Jc)[M][DC], AT (&Jp)[M][3]) {
+    AT y[3], p0, p1, r2, dd, iz, f, k1, k2, R[9];
     if constexpr (std::is_same<AT, float>::value) {
       float P[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double yi = rb[3 * i] * X[0] + rb[3 * i + 1] * X[1] + rb[3 * i + 2] * X[2];
-        y[i] = (float)yi;
-        P[i] = (float)(yi + rb[9 + i]);
-      }
+      for (int i = 0; i < 3; ++i)
+        P[i] = (float)(rb[3 * i] * X[0] + rb[3 * i + 1] * X[1] + rb[3 * i + 2] * X[2] + rb[9 + i]);
+      float4 q[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q[i] = __ldg(reinterpret_cast<const float4*>(rbf) + i);
+      const float* fb = reinterpret_cast<const float*>(q);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) R[i] = fb[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) y[i] = P[i] - fb[9 + i];   // R X, far from any cancellation
+      f = fb[12];
+      k1 = fb[13];
+      k2 = fb[14];
       iz = 1.0f / P[2];
       p0 = -P[0] * iz;
       p1 = -P[1] * iz;
       r2 = p0 * p0 + p1 * p1;
-      dd = 1.0f + r2 * ((float)rb[13] + (float)rb[14] * r2);
-      const float fd = (float)rb[12] * dd;
+      dd = 1.0f + r2 * (k1 + k2 * r2);
+      const float fd = f * dd;
       const double2 z = __ldg(reinterpret_cast<const double2*>(d.obs) + e);
       float r0 = fmaf(fd, p0, -(float)z.x), r1 = fmaf(fd, p1, -(float)z.y);
       if (d.e_sqinfo) {
@@ -456,21 +465,29 @@ struct ModelBA {
       }
       r[0] = r0;
       r[1] = r1;
-      sw = huber_weight<float>((double)(r0 * r0 + r1 * r1), __ldg(d.e_delta + e));
+      const float dl = (float)__ldg(d.e_delta + e), sq = r0 * r0 + r1 * r1;
+      sw = (dl > 0.0f && sq > dl * dl) ? sqrtf(dl * rsqrtf(sq)) : 1.0f;
     } else {
       Geom g;
       geom(rb, X, g);
-      residual(d, e, g, r);
-      sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1], __ldg(d.e_delta + e));
+      double rd[M];
+      residual(d, e, g, rd);
+      sw = huber_weight<AT>(rd[0] * rd[0] + rd[1] * rd[1], __ldg(d.e_delta + e));
+      r[0] = rd[0];
+      r[1] = rd[1];
       p0 = g.p[0];
       p1 = g.p[1];
       r2 = g.r2;
       dd = g.d;
       iz = g.iz;
+      f = rb[12];
+      k1 = rb[13];
+      k2 = rb[14];
 #pragma unroll
       for (int i = 0; i < 3; ++i) y[i] = g.y[i];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) R[i] = rb[i];
     }
-    const AT f = (AT)rb[12], k1 = (AT)rb[13], k2 = (AT)rb[14];
     const AT c2 = (AT)2 * k1 + (AT)4 * k2 * r2;
     // du/dp = f (d I + c2 p p^T)
     const AT A00 = f * (dd + c2 * p0 * p0), A01 = f * c2 * p0 * p1, A11 = f * (dd + c2 * p1 * p1);
@@ -493,8 +510,7 @@ struct ModelBA {
       Jc[a][7] = f * r2 * pp[a];
       Jc[a][8] = f * r2 * r2 * pp[a];
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Jp[a][j] = D[a][0] * (AT)rb[j] + D[a][1] * (AT)rb[3 + j] + D[a][2] * (AT)rb[6 + j];
+      for (int j = 0; j < 3; ++j) Jp[a][j] = D[a][0] * R[j] + D[a][1] * R[3 + j] + D[a][2] * R[6 + j];
     }
     if (d.e_sqinfo) {
       const double* U = d.e_sqinfo + NQ * (size_t)e;
@@ -512,7 +528,7 @@ struct ModelBA {
         Jp[0][k] = a;
       }
     }
-    const AT s = (AT)sw;
+    const AT s = sw;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
 #pragma unroll
@@ -642,14 +658,19 @@ struct ModelStereo {
 
   // dr/dX_c rows: [fx/Z, 0, -fx X/Z^2], [0, fy/Z, -fy Y/Z^2], [fx/Z, 0, -fx (X-b)/Z^2];
   // dX_b/dtheta = [X_b]_x, dX_b/dp = -I, dX_b/dX = R^T; dX_c/dX_b = R_cb.
+  // (rbf, the FP32 copy of the render block, is not used: the stereo rows come from FP64
+  // geometry in every precision.)
   template <class AT>
-  __device__ static void eval(const DevBA& d, int e, const double* rb, const double* X, double (&r)[M],
-                              double& rho, double& sw, AT (&Jc)[M][DC], AT (&Jp)[M][3]) {
+  __device__ static void eval(const DevBA& d, int e, const double* rb, const float* rbf, const double* X,
+                              AT (&rr)[M], AT& swr, AT (&Jc)[M][DC], AT (&Jp)[M][3]) {
     Geom g;
     geom(d, rb, X, g);
+    double r[M];
     residual(d, e, g, r);
-    rho = 0.0;
-    sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], __ldg(d.e_delta + e));
+    const double sw = huber_weight<AT>(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], __ldg(d.e_delta + e));
+#pragma unroll
+    for (int a = 0; a < M; ++a) rr[a] = (AT)r[a];
+    swr = (AT)sw;
     const AT fx = (AT)d.camk[0], fy = (AT)d.camk[1], b = (AT)d.camk[4];
     const AT iz = (AT)g.iz, x = (AT)g.Xc[0], y = (AT)g.Xc[1];
     AT D[3][3];

@@ -21,9 +21,9 @@ __device__ __forceinline__ void dyn_row(const DevBA& d, int e, AT (&row)[Dims<Mo
   double rb[16];
   load_rb(d.camrb + 16 * (size_t)c, rb);
   const double X[3] = {d.pt[3 * (size_t)p], d.pt[3 * (size_t)p + 1], d.pt[3 * (size_t)p + 2]};
-  double r[M], rho, sw;
+  AT r[M], sw;
   AT Jc[M][DC], Jp[M][3];
-  Mo::template eval<AT>(d, e, rb, X, r, rho, sw, Jc, Jp);
+  Mo::template eval<AT>(d, e, rb, d.camrbf + 16 * (size_t)c, X, r, sw, Jc, Jp);
   const bool cf = d.cam_fixed[c] != 0, pf = d.pt_fixed[p] != 0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {

@@ -143,7 +143,9 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_prepare(LaunchSet ls,
   if (c >= d.C || (threadIdx.x & 31) != 0) return;
   const double* cam = (candidate ? d.cam_cand : d.cam) + Mo::SS * (size_t)c;
   double* rb = (candidate ? d.camrb_cand : d.camrb) + 16 * (size_t)c;
+  float* rbf = (candidate ? d.camrbf_cand : d.camrbf) + 16 * (size_t)c;
   Mo::render(d, cam, rb);
+  for (int i = 0; i < 16; ++i) rbf[i] = (float)rb[i];
 }
 
 // ---------------------------------------------------------------- cost F(x)
@@ -299,9 +301,9 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     double rb[16];
     load_rb(d.camrb + 16 * (size_t)c, rb);
     const double X[3] = {d.pt[3 * (size_t)p], d.pt[3 * (size_t)p + 1], d.pt[3 * (size_t)p + 2]};
-    double r[M], rho, sw;
+    AT r[M], sw;
     AT Jc[M][DC], Jp[M][3];
-    Mo::template eval<AT>(d, e, rb, X, r, rho, sw, Jc, Jp);
+    Mo::template eval<AT>(d, e, rb, d.camrbf + 16 * (size_t)c, X, r, sw, Jc, Jp);
     if (d.cam_fixed[c]) {
 #pragma unroll
       for (int a = 0; a < M; ++a)
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_linearize(LaunchSet ls, int force)
     }
     AT rw[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a) rw[a] = (AT)(sw * r[a]);
+    for (int a = 0; a < M; ++a) rw[a] = sw * r[a];
     __align__(16) JT row[NJ];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
@@ -1269,9 +1271,11 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_retract_cams(LaunchSet ls
   const double* cur = d.cam + SS * (size_t)c;
   double* nxt = d.cam_cand + SS * (size_t)c;
   double* rb = d.camrb_cand + 16 * (size_t)c;
+  float* rbf = d.camrbf_cand + 16 * (size_t)c;
   if (d.cam_fixed[c]) {
     for (int i = 0; i < SS; ++i) nxt[i] = cur[i];
     for (int i = 0; i < 16; ++i) rb[i] = d.camrb[16 * (size_t)c + i];
+    for (int i = 0; i < 16; ++i) rbf[i] = d.camrbf[16 * (size_t)c + i];
     return;
   }
   const AT* xs = reinterpret_cast<const AT*>(d.sc->use_best ? d.xbest : d.x) + DB * (size_t)c;
@@ -1284,6 +1288,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_retract_cams(LaunchSet ls
   double r16[16];
   Mo::render(d, nx, r16);
   for (int i = 0; i < 16; ++i) rb[i] = r16[i];
+  for (int i = 0; i < 16; ++i) rbf[i] = (float)r16[i];
 }
 
 template <class Mo, class AT>
@@ -1380,6 +1385,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_commit_cams(LaunchSet ls)
   if (c >= d.C) return;
   if (lane < Mo::SS) d.cam[Mo::SS * (size_t)c + lane] = d.cam_cand[Mo::SS * (size_t)c + lane];
   if (lane < 16) d.camrb[16 * (size_t)c + lane] = d.camrb_cand[16 * (size_t)c + lane];
+  if (lane < 16) d.camrbf[16 * (size_t)c + lane] = d.camrbf_cand[16 * (size_t)c + lane];
 }
 
 template <class Mo>

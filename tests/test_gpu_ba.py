@@ -414,8 +414,10 @@ def test_stepwise_calls_continue_one_lm_run(gpo, prec):
         lam, nu = r.final_lambda, r.final_nu
         h2 += g2.history()
     for a, b in zip(h1, h2):
-        assert (a["cost"], a["cand_cost"], a["accepted"], a["pcg_iters"], a["lam"]) == \
-               (b["cost"], b["cand_cost"], b["accepted"], b["pcg_iters"], b["lam"])
+        # a step whose solve left the representable range has a NaN candidate cost (and is
+        # rejected) in both runs alike
+        assert (a["cost"], a["accepted"], a["pcg_iters"], a["lam"]) == (b["cost"], b["accepted"], b["pcg_iters"], b["lam"])
+        assert a["cand_cost"] == b["cand_cost"] or (np.isnan(a["cand_cost"]) and np.isnan(b["cand_cost"]))
     assert r.final_cost == rep.final_cost and lam == rep.final_lambda and nu == rep.final_nu
     assert np.array_equal(g1.get_state(c0, p.n_cams, 9), g2.get_state(c0, p.n_cams, 9))
     assert np.array_equal(g1.get_state(p0, p.n_pts, 3), g2.get_state(p0, p.n_pts, 3))
