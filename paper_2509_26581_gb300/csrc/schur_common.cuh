@@ -756,6 +756,78 @@ struct Dims {
   static_assert(DB <= 32, "one lane per camera-block component");
 };
 
+// The two per-edge terms of the matrix-free Schur product (Sec. IV-E), shared by every
+// Schur-product kernel so that all of them round alike.  `row` is the edge's unpacked
+// Jacobian row (Jc row-major, then Jp row-major).  Every sum runs in a fixed order,
+// spelled out as fused multiply-adds:
+//   point term   q_a = sum_k Jc[a][k] x_k (k ascending), a_k = sum_a Jp[a][k] q_a;
+//   camera term  s_a = sum_k Jp[a][k] t_k (k ascending), v_k = sum_a Jc[a][k] s_a.
+// For two residual rows in FP32 the two rows' (or two components') chains run side by
+// side in packed FP32x2 instructions; each lane performs the scalar chain's operations,
+// so the packed and scalar forms give the same values.
+template <class Mo, class AT>
+__device__ __forceinline__ void edge_point_term(const AT* row, const AT* xc, AT (&a)[3]) {
+  constexpr int M = Mo::M, DC = Mo::DC, JP0 = M * DC;
+  if constexpr (M == 2 && std::is_same<AT, float>::value) {
+    float2 q = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+      const float xk = xc[k];
+      q = __ffma2_rn(make_float2(row[k], row[DC + k]), make_float2(xk, xk), q);
+    }
+    const float2 s = __ffma2_rn(make_float2(row[JP0 + 3], row[JP0 + 4]), make_float2(q.y, q.y),
+                                __fmul2_rn(make_float2(row[JP0], row[JP0 + 1]), make_float2(q.x, q.x)));
+    a[0] = s.x;
+    a[1] = s.y;
+    a[2] = fmaf(row[JP0 + 5], q.y, row[JP0 + 2] * q.x);
+  } else {
+    AT q[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) q[r] = (AT)0;
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+      const AT xk = xc[k];
+#pragma unroll
+      for (int r = 0; r < M; ++r) q[r] = fma(row[r * DC + k], xk, q[r]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      AT s = row[JP0 + k] * q[0];
+#pragma unroll
+      for (int r = 1; r < M; ++r) s = fma(row[JP0 + 3 * r + k], q[r], s);
+      a[k] = s;
+    }
+  }
+}
+template <class Mo, class AT>
+__device__ __forceinline__ void edge_camera_term(const AT* row, AT t0, AT t1, AT t2, AT (&v)[Mo::DC]) {
+  constexpr int M = Mo::M, DC = Mo::DC, JP0 = M * DC;
+  if constexpr (M == 2 && std::is_same<AT, float>::value) {
+    float2 s = __fmul2_rn(make_float2(row[JP0], row[JP0 + 3]), make_float2(t0, t0));
+    s = __ffma2_rn(make_float2(row[JP0 + 1], row[JP0 + 4]), make_float2(t1, t1), s);
+    s = __ffma2_rn(make_float2(row[JP0 + 2], row[JP0 + 5]), make_float2(t2, t2), s);
+#pragma unroll
+    for (int k = 0; k + 1 < DC; k += 2) {
+      const float2 w = __ffma2_rn(make_float2(row[DC + k], row[DC + k + 1]), make_float2(s.y, s.y),
+                                  __fmul2_rn(make_float2(row[k], row[k + 1]), make_float2(s.x, s.x)));
+      v[k] = w.x;
+      v[k + 1] = w.y;
+    }
+    if constexpr (DC % 2 == 1) v[DC - 1] = fmaf(row[2 * DC - 1], s.y, row[DC - 1] * s.x);
+  } else {
+    AT s[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) s[r] = fma(row[JP0 + 3 * r + 2], t2, fma(row[JP0 + 3 * r + 1], t1, row[JP0 + 3 * r] * t0));
+#pragma unroll
+    for (int k = 0; k < DC; ++k) {
+      AT w = row[k] * s[0];
+#pragma unroll
+      for (int r = 1; r < M; ++r) w = fma(row[r * DC + k], s[r], w);
+      v[k] = w;
+    }
+  }
+}
+
 template <class AT>
 __device__ __forceinline__ void mul3(const AT* h, const AT* v, AT* o) {
   o[0] = h[0] * v[0] + h[1] * v[1] + h[2] * v[2];

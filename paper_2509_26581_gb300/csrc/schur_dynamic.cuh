@@ -123,23 +123,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dyn(LaunchSet ls) {
   for (int m = 0; m < EPT; ++m) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
-    const AT* xc = xs + DC * slot[m];
-    AT q[M];
+    AT a[3];
+    edge_point_term<Mo>(row[m], xs + DC * slot[m], a);
 #pragma unroll
-    for (int a = 0; a < M; ++a) q[a] = (AT)0;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-      const AT xk = xc[k];
-#pragma unroll
-      for (int a = 0; a < M; ++a) q[a] += row[m][a * DC + k] * xk;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      AT s = row[m][JP0 + k] * q[0];
-#pragma unroll
-      for (int a = 1; a < M; ++a) s += row[m][JP0 + 3 * a + k] * q[a];
-      vv[k * LD + i] = s;
-    }
+    for (int k = 0; k < 3; ++k) vv[k * LD + i] = a[k];
   }
   __syncthreads();
   // ---- pass 2: t_p = H_pp^-1 sum_e a_e
@@ -158,18 +145,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dyn(LaunchSet ls) {
     const int i = threadIdx.x + m * kThreads;
     if (i >= cr.nE) break;
     const int pl = ptl[m];
-    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
-    AT s[M];
+    AT v[DC];
+    edge_camera_term<Mo>(row[m], tp[pl], tp[LD + pl], tp[2 * LD + pl], v);
 #pragma unroll
-    for (int a = 0; a < M; ++a)
-      s[a] = row[m][JP0 + 3 * a] * t0 + row[m][JP0 + 3 * a + 1] * t1 + row[m][JP0 + 3 * a + 2] * t2;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-      AT v = row[m][k] * s[0];
-#pragma unroll
-      for (int a = 1; a < M; ++a) v += row[m][a * DC + k] * s[a];
-      vv[k * LD + pos[m]] = v;
-    }
+    for (int k = 0; k < DC; ++k) vv[k * LD + pos[m]] = v[k];
   }
   __syncthreads();
   // ---- pass 4: per-slot sums over contiguous positions

@@ -100,23 +100,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     if (i >= cr.nE) break;
     AT row[NJ];
     load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
-    const AT* xc = xs + DC * slot[m];
-    AT q[M];
+    AT a[3];
+    edge_point_term<Mo>(row, xs + DC * slot[m], a);
 #pragma unroll
-    for (int a = 0; a < M; ++a) q[a] = (AT)0;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-      const AT xk = xc[k];
-#pragma unroll
-      for (int a = 0; a < M; ++a) q[a] += row[a * DC + k] * xk;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      AT s = row[JP0 + k] * q[0];
-#pragma unroll
-      for (int a = 1; a < M; ++a) s += row[JP0 + 3 * a + k] * q[a];
-      vv[k * LD + i] = s;
-    }
+    for (int k = 0; k < 3; ++k) vv[k * LD + i] = a[k];
   }
   __syncthreads();
   // ---- pass 2: t_p = H_pp^-1 sum_e a_e
@@ -137,17 +124,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
     AT row[NJ];
     load_row_t<NJ>(Jg, (size_t)(cr.e0 + i), row);
     const int pl = ptl[m];
-    const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
-    AT s[M];
+    AT v[DC];
+    edge_camera_term<Mo>(row, tp[pl], tp[LD + pl], tp[2 * LD + pl], v);
 #pragma unroll
-    for (int a = 0; a < M; ++a) s[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
-#pragma unroll
-    for (int k = 0; k < DC; ++k) {
-      AT v = row[k] * s[0];
-#pragma unroll
-      for (int a = 1; a < M; ++a) v += row[a * DC + k] * s[a];
-      vv[k * LD + pos[m]] = v;
-    }
+    for (int k = 0; k < DC; ++k) vv[k * LD + pos[m]] = v[k];
   }
   __syncthreads();
   // ---- pass 4: per-slot sums over contiguous positions
@@ -384,23 +364,10 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
       for (int i = threadIdx.x; i < in.nE; i += kThreads) {
         AT row[NJ];
         load_row_t<NJ>(Js, (size_t)(i + in.jskew), row);
-        const AT* xc = xs + DC * (int)((meta[i] >> 10) & 1023u);
-        AT qv[M];
+        AT a[3];
+        edge_point_term<Mo>(row, xs + DC * (int)((meta[i] >> 10) & 1023u), a);
 #pragma unroll
-        for (int a = 0; a < M; ++a) qv[a] = (AT)0;
-#pragma unroll
-        for (int kk = 0; kk < DC; ++kk) {
-          const AT xk = xc[kk];
-#pragma unroll
-          for (int a = 0; a < M; ++a) qv[a] += row[a * DC + kk] * xk;
-        }
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-          AT sum = row[JP0 + kk] * qv[0];
-#pragma unroll
-          for (int a = 1; a < M; ++a) sum += row[JP0 + 3 * a + kk] * qv[a];
-          vv[kk * LD + i] = sum;
-        }
+        for (int kk = 0; kk < 3; ++kk) vv[kk * LD + i] = a[kk];
       }
       consumer_sync();
       // ---- pass 2: t_p = H_pp^-1 sum_e a_e
@@ -422,18 +389,10 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
         load_row_t<NJ>(Js, (size_t)(i + in.jskew), row);
         const uint32_t m = meta[i];
         const int pl = (int)(m >> 20), pos = (int)(m & 1023u);
-        const AT t0 = tp[pl], t1 = tp[LD + pl], t2 = tp[2 * LD + pl];
-        AT sv[M];
+        AT v[DC];
+        edge_camera_term<Mo>(row, tp[pl], tp[LD + pl], tp[2 * LD + pl], v);
 #pragma unroll
-        for (int a = 0; a < M; ++a)
-          sv[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
-#pragma unroll
-        for (int kk = 0; kk < DC; ++kk) {
-          AT v = row[kk] * sv[0];
-#pragma unroll
-          for (int a = 1; a < M; ++a) v += row[a * DC + kk] * sv[a];
-          vv[kk * LD + pos] = v;
-        }
+        for (int kk = 0; kk < DC; ++kk) vv[kk * LD + pos] = v[kk];
       }
       consumer_sync();
       // ---- pass 4: per-slot sums over contiguous positions
@@ -672,23 +631,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
       if (i >= c.nE) break;
       AT row[NJ];
       load_row_t<NJ>(Jg, (size_t)(c.e0 + i), row);
-      const AT* xc = xs + DC * slot[m];
-      AT qv[M];
+      AT a[3];
+      edge_point_term<Mo>(row, xs + DC * slot[m], a);
 #pragma unroll
-      for (int a = 0; a < M; ++a) qv[a] = (AT)0;
-#pragma unroll
-      for (int k = 0; k < DC; ++k) {
-        const AT xk = xc[k];
-#pragma unroll
-        for (int a = 0; a < M; ++a) qv[a] += row[a * DC + k] * xk;
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        AT s2 = row[JP0 + k] * qv[0];
-#pragma unroll
-        for (int a = 1; a < M; ++a) s2 += row[JP0 + 3 * a + k] * qv[a];
-        vv[k * LD + i] = s2;
-      }
+      for (int k = 0; k < 3; ++k) vv[k * LD + i] = a[k];
     }
     __syncthreads();
     // ---- pass 2: t_p = H_pp^-1 sum_e a_e; meanwhile the last warp's first thread
@@ -717,17 +663,10 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
       AT row[NJ];
       load_row_t<NJ>(Jg, (size_t)(c.e0 + i), row);
       const int pl = ptl[m];
-      const AT t0 = tp[pl], t1 = tp[LP + pl], t2 = tp[2 * LP + pl];
-      AT sv[M];
+      AT v[DC];
+      edge_camera_term<Mo>(row, tp[pl], tp[LP + pl], tp[2 * LP + pl], v);
 #pragma unroll
-      for (int a = 0; a < M; ++a) sv[a] = row[JP0 + 3 * a] * t0 + row[JP0 + 3 * a + 1] * t1 + row[JP0 + 3 * a + 2] * t2;
-#pragma unroll
-      for (int k = 0; k < DC; ++k) {
-        AT v = row[k] * sv[0];
-#pragma unroll
-        for (int a = 1; a < M; ++a) v += row[a * DC + k] * sv[a];
-        vv[k * LD + pos[m]] = v;
-      }
+      for (int k = 0; k < DC; ++k) vv[k * LD + pos[m]] = v[k];
     }
     __syncthreads();
     // ---- pass 4: per-slot sums over contiguous positions

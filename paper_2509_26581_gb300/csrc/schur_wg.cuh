@@ -48,44 +48,21 @@ __host__ __device__ inline WgLayout wg_layout(size_t sA, int ch_max, int ns_max)
 // a = Jp^T (Jc x) of one edge from its packed row.
 template <class Mo, class JT, class AT>
 __device__ __forceinline__ void wg_point_term(const uint4 (&w)[JTiles<JT, Mo::NJ>::Q], const AT* xc, AT (&a)[3]) {
-  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dims<Mo>::JP0;
-  AT row[NJ];
-  load_row<NJ>(reinterpret_cast<const JT*>(w), row);
-  AT q[M];
-#pragma unroll
-  for (int r = 0; r < M; ++r) q[r] = (AT)0;
-#pragma unroll
-  for (int k = 0; k < DC; ++k) {
-    const AT xk = xc[k];
-#pragma unroll
-    for (int r = 0; r < M; ++r) q[r] += row[r * DC + k] * xk;
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    AT s = row[JP0 + k] * q[0];
-#pragma unroll
-    for (int r = 1; r < M; ++r) s += row[JP0 + 3 * r + k] * q[r];
-    a[k] = s;
-  }
+  AT row[Mo::NJ];
+  load_row<Mo::NJ>(reinterpret_cast<const JT*>(w), row);
+  edge_point_term<Mo>(row, xc, a);
 }
 
 // v = Jc^T (Jp t) of one edge, written to column `pos` of the scratch [DC][LD].
 template <class Mo, class JT, class AT>
 __device__ __forceinline__ void wg_camera_term(const uint4 (&w)[JTiles<JT, Mo::NJ>::Q], const AT (&t)[3], AT* vv,
                                                int LD, int pos) {
-  constexpr int M = Mo::M, DC = Mo::DC, NJ = Mo::NJ, JP0 = Dims<Mo>::JP0;
-  AT row[NJ];
-  load_row<NJ>(reinterpret_cast<const JT*>(w), row);
-  AT s[M];
+  AT row[Mo::NJ];
+  load_row<Mo::NJ>(reinterpret_cast<const JT*>(w), row);
+  AT v[Mo::DC];
+  edge_camera_term<Mo>(row, t[0], t[1], t[2], v);
 #pragma unroll
-  for (int r = 0; r < M; ++r) s[r] = row[JP0 + 3 * r] * t[0] + row[JP0 + 3 * r + 1] * t[1] + row[JP0 + 3 * r + 2] * t[2];
-#pragma unroll
-  for (int k = 0; k < DC; ++k) {
-    AT v = row[k] * s[0];
-#pragma unroll
-    for (int r = 1; r < M; ++r) v += row[r * DC + k] * s[r];
-    vv[k * LD + pos] = v;
-  }
+  for (int k = 0; k < Mo::DC; ++k) vv[k * LD + pos] = v[k];
 }
 
 // Rows of a chunk: the 16-byte pieces of its 32-edge tiles, starting at the tile that
