@@ -53,8 +53,7 @@ __device__ __forceinline__ void row_of(const DevBA& d, const JT* J, int e, AT (&
 
 template <class Mo, class AT, int EPT>
 __global__ void __launch_bounds__(kThreads) k_spmv_dyn(LaunchSet ls) {
-  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, JP0 = Dims<Mo>::JP0, NJU = Dims<Mo>::NJU,
-                VW = Dims<Mo>::VW;
+  constexpr int DC = Mo::DC, DB = Mo::DB, NJU = Dims<Mo>::NJU, VW = Dims<Mo>::VW;
   GPO_BIND(ch, kl)
   const Scalars* sc = d.sc;
   const ChunkRange cr = chunk_range(d, kl);

@@ -739,43 +739,78 @@ struct ApplyShared {
   AT quarter[kCamPerBlock][Mo::DC];
   AT qx[Mo::kExtra ? kCamPerBlock : 1][Mo::DB];
 };
+// The camera a warp of a camera-half unit works on (CTA-part `part` of camera block cbl:
+// two cameras, four warps each), and its slot range, a schedule table the host writes
+// before the launches (so a launch may read it before it waits for its predecessor).
+__device__ __forceinline__ int unit_camera(int cbl, int part) {
+  return cbl * kCamPerBlock + part * (kCamPerBlock / kApplySplit) + (int)(threadIdx.x >> 5) / kApplySplit;
+}
+__device__ __forceinline__ int2 cam_slot_range(const DevBA& d, int cbl, int part) {
+  const int c = unit_camera(cbl, part);
+  return c < d.C ? make_int2(d.cam_s_off[c], d.cam_s_off[c + 1]) : make_int2(0, 0);
+}
 // One unit of the camera half: CTA-part `part` of camera block cbl of the problem bound
-// in d (every thread calls; returns uniformly).  kFused: the unit stops after writing
-// its p^T y partial; alpha is formed after the fused kernel's grid barrier by every
-// CTA of the update (the same partials summed in the same order, so the same value).
+// in d, sr the warp's camera's slot range (every thread calls; returns uniformly).
+// kFused: the unit stops after writing its p^T y partial; alpha is formed after the
+// fused kernel's grid barrier by every CTA of the update (the same partials summed in
+// the same order, so the same value).
 template <class Mo, class AT, bool kFused = false>
-__device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int part, ApplyShared<Mo, AT>& S) {
+__device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int part, ApplyShared<Mo, AT>& S,
+                               int2 sr) {
   constexpr int DB = Mo::DB, DC = Mo::DC, TB = Dims<Mo>::TB;
   double* red = S.red;
   auto& quarter = S.quarter;
   auto& qx = S.qx;
   Scalars* sc = d.sc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cams_per_cta = kCamPerBlock / kApplySplit;             // 2
-  const int c = cbl * kCamPerBlock + part * cams_per_cta + warp / kApplySplit;
+  const int c = unit_camera(cbl, part);
   const int q = warp % kApplySplit;                                // quarter of the slots
-  // the camera's slot range is loaded with the solve's flags (one round trip)
-  const int sa = c < d.C ? d.cam_s_off[c] : 0, sb = c < d.C ? d.cam_s_off[c + 1] : 0;
-  if (!sc->active || sc->pcg_done) return;
-  // the vector the product is taken of: the direction p = (z + beta p_old) / n, or in a
-  // restart iteration the current solution x (read as (x + 0 x) / 1, exactly x)
-  const int restart = sc->restart;
-  const AT* z_all = reinterpret_cast<const AT*>(restart ? d.x : d.z);
-  const AT* pold_all = restart ? z_all : reinterpret_cast<const AT*>(sc->pidx ? d.p2 : d.p);
-  const AT beta = restart ? (AT)0 : (AT)sc->beta, inv_n = restart ? (AT)1 : (AT)sc->inv_n;
-  AT dot = (AT)0;   // per-warp partial in AT, accumulated across warps in FP64
-  AT pi = (AT)0;
+  const int sa = sr.x, sb = sr.y;
+  // The unit's loads are issued before any is used (one round trip): the solve's flags
+  // and scalars, the camera's slot partials, and for the camera's first warp the
+  // direction's inputs under either choice of restart (z, x and both direction
+  // buffers) and, in the fused FP32 kernel (registers to spare), its row of the damped
+  // block (the other forms load that row once the slot sums are in).
+  constexpr bool kEarlyH = kFused && sizeof(AT) == 4;
+  const int active = sc->active, done = sc->pcg_done, restart = sc->restart, pidx = sc->pidx;
+  const double beta_d = sc->beta, inv_n_d = sc->inv_n;
+  const int full = sc->full, save_best = sc->save_best;
+  const bool lead = c < d.C && q == 0 && lane < DB;
+  const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)(c < d.C ? c : 0) * TB;
+  AT hrow[kEarlyH ? DB : 1];
+  AT zc = (AT)0, xc = (AT)0, pc0 = (AT)0, pc1 = (AT)0;
+  if (lead) {
+    if constexpr (kEarlyH) {
+#pragma unroll
+      for (int j = 0; j < DB; ++j) hrow[j] = H[sym_idx(DB, lane, j)];
+    }
+    const size_t o = DB * (size_t)c + lane;
+    zc = reinterpret_cast<const AT*>(d.z)[o];
+    xc = reinterpret_cast<const AT*>(d.x)[o];
+    pc0 = reinterpret_cast<const AT*>(d.p)[o];
+    pc1 = reinterpret_cast<const AT*>(d.p2)[o];
+  }
+  AT acc[DC];
+#pragma unroll
+  for (int k = 0; k < DC; ++k) acc[k] = (AT)0;
   if (c < d.C) {   // warp-uniform
     const AT* partV = reinterpret_cast<const AT*>(d.partV);
-    AT acc[DC];
-#pragma unroll
-    for (int k = 0; k < DC; ++k) acc[k] = (AT)0;
 #pragma unroll 4
     for (int s = sa + q * 32 + lane; s < sb; s += 32 * kApplySplit) {
       const AT* src = partV + (size_t)s * DC;   // camera-major rows
 #pragma unroll
       for (int k = 0; k < DC; ++k) acc[k] += src[k];
     }
+  }
+  if (!active || done) return;
+  // the vector the product is taken of: the direction p = (z + beta p_old) / n, or in a
+  // restart iteration the current solution x (read as (x + 0 x) / 1, exactly x)
+  const AT* z_all = reinterpret_cast<const AT*>(restart ? d.x : d.z);
+  const AT* pold_all = restart ? z_all : reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
+  const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
+  AT dot = (AT)0;   // per-warp partial in AT, accumulated across warps in FP64
+  AT pi = (AT)0;
+  if (c < d.C) {   // warp-uniform
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -814,19 +849,22 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     }
     // p_k = (z_k + beta_k p_{k-1}) / n_k for this camera (the same values the Schur
     // product gathered), written to the other direction buffer
-    AT* pnew = reinterpret_cast<AT*>(sc->pidx ? d.p : d.p2) + DB * (size_t)c;
-    pi = lane < DB ? (z_all[DB * (size_t)c + lane] + beta * pold_all[DB * (size_t)c + lane]) * inv_n : (AT)0;
+    AT* pnew = reinterpret_cast<AT*>(pidx ? d.p : d.p2) + DB * (size_t)c;
+    const AT zsel = restart ? xc : zc, psel = restart ? xc : (pidx ? pc1 : pc0);
+    pi = lane < DB ? (zsel + beta * psel) * inv_n : (AT)0;
     if (lane < DB) {
       if (!restart) pnew[lane] = pi;
-      if (sc->save_best)
-        reinterpret_cast<AT*>(d.xbest)[DB * (size_t)c + lane] = reinterpret_cast<const AT*>(d.x)[DB * (size_t)c + lane];
+      if (save_best) reinterpret_cast<AT*>(d.xbest)[DB * (size_t)c + lane] = xc;
     }
-    const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)c * TB;
     AT yi = (AT)0;
 #pragma unroll
     for (int j = 0; j < DB; ++j) {
       const AT pj = __shfl_sync(0xffffffffu, pi, j);
-      if (lane < DB) yi += H[sym_idx(DB, lane, j)] * pj;
+      if constexpr (kEarlyH) {
+        if (lane < DB) yi += hrow[j] * pj;
+      } else {
+        if (lane < DB) yi += H[sym_idx(DB, lane, j)] * pj;
+      }
     }
     if constexpr (Mo::kExtra) {
       if (lane < DB)
@@ -835,7 +873,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
     if (lane < DB) {
       // the Schur complement subtracts the points' coupling; the full system's product
       // adds the edges' coupling terms J_c^T J_p v_p
-      if (sc->full) yi += sv;
+      if (full) yi += sv;
       else yi -= sv;
       reinterpret_cast<AT*>(d.y)[DB * (size_t)c + lane] = yi;
       dot = pi * yi;
@@ -883,8 +921,9 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_apply(LaunchSet ls) {
   const int prob_ = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
   const int cbl = ls.nprob == 1 ? cb : cb - ls.cb_base[prob_];
   bind_problem(d, ls.probs + prob_);
+  const int2 sr = cam_slot_range(d, cbl, part);
   pdl_wait();
-  cam_apply_body<Mo, AT>(ls, d, cbl, part, S);
+  cam_apply_body<Mo, AT>(ls, d, cbl, part, S, sr);
 }
 
 // The update's inputs that the camera half does not write (the fused kernel loads
@@ -1131,8 +1170,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
   __shared__ double red[kCamPerBlock][2];
   __shared__ DevBA d;
   pdl_trigger();
-  pdl_wait();
-  const int G = gridDim.x;
+  const int G = gridDim.x, units = ls.n_cb * kApplySplit;
   int bound = -1;
   auto bind = [&](int q) {
     if (q != bound) {          // CTA-uniform
@@ -1141,11 +1179,20 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
       bound = q;
     }
   };
-  for (int u = blockIdx.x; u < ls.n_cb * kApplySplit; u += G) {
+  // the first unit's descriptor and slot ranges (host-written) before the wait
+  int2 sr0 = make_int2(0, 0);
+  if ((int)blockIdx.x < units) {
+    const int cb = blockIdx.x / kApplySplit, q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
+    bind(q);
+    sr0 = cam_slot_range(d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], blockIdx.x % kApplySplit);
+  }
+  pdl_wait();
+  for (int u = blockIdx.x; u < units; u += G) {
     const int cb = u / kApplySplit, part = u % kApplySplit;
     const int q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
     bind(q);
-    cam_apply_body<Mo, AT, true>(ls, d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], part, S);
+    const int cbl = ls.nprob == 1 ? cb : cb - ls.cb_base[q];
+    cam_apply_body<Mo, AT, true>(ls, d, cbl, part, S, u == (int)blockIdx.x ? sr0 : cam_slot_range(d, cbl, part));
     __syncthreads();
   }
   // the grid has one CTA per unit (n_cb * kApplySplit >= n_cb), so CTA b < n_cb updates

@@ -24,7 +24,7 @@ template <class Mo, class JT, int EPT>
 __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
+  constexpr int DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, VW = Dm::VW;
   GPO_BIND(ch, kl)
   // the chunk's ranges and the solve's scalars are loaded together, ahead of the
   // early exit, so that the index loads below start one round trip sooner
@@ -230,7 +230,7 @@ template <class Mo, class JT>
 __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
+  constexpr int DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, VW = Dm::VW;
   constexpr uint32_t RB = NJ * sizeof(JT);
   constexpr uint32_t PRB = (6 * sizeof(AT) + 8 + 15) & ~15u;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -475,7 +475,7 @@ template <class Mo, class JT, int EPT>
 __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
-  constexpr int M = Mo::M, DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ, JP0 = Dm::JP0, VW = Dm::VW;
+  constexpr int DC = Mo::DC, DB = Mo::DB, NJ = Mo::NJ;
   constexpr size_t PRB = (6 * sizeof(AT) + 8 + 15) & ~(size_t)15;
   constexpr int kWords = (int)(sizeof(DevBA) / 4);
   extern __shared__ __align__(16) unsigned char smem[];
