@@ -266,6 +266,22 @@ __device__ __forceinline__ void sum_partials(const double* part, int n, double& 
   b = rb[0];
 }
 
+// The first members of n partial pairs (stride 2), summed exactly as sum_partials sums
+// them (the same value as its a) without the FP64 work of the second members, which
+// matters on a part whose FP64 rate is a small fraction of its FP32 rate.
+__device__ __forceinline__ double sum_partials_first(const double* part, int n) {
+  __shared__ double ra[256];
+  double x = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x += part[2 * i];
+  ra[threadIdx.x] = x;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) ra[threadIdx.x] += ra[threadIdx.x + s2];
+    __syncthreads();
+  }
+  return ra[0];
+}
+
 // Sums n single per-CTA partials with all threads in a fixed order (as sum_partials);
 // the result is valid in every thread.
 __device__ __forceinline__ double sum_singles(const double* part, int n) {

@@ -893,8 +893,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
   }
   if constexpr (kFused) return;
   if (!last_cta(&sc->ticket, ctas)) return;
-  double pAp, unused;
-  sum_partials(d.cblk_part, ctas, pAp, unused);
+  double pAp = sum_partials_first(d.cblk_part, ctas);
   if (sc->full) pAp += sum_singles(d.md_part, d.NCH);   // the points' p^T H p, per chunk
   if (threadIdx.x == 0) {
     sc->pAp = pAp;
@@ -1036,33 +1035,48 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
   // a restart iteration: y = S x at the current solution, and the residual becomes the
   // true one, g - S x (unit scale), with the direction restarted from z = M r
   const int restart = sc->restart;
-  double alpha_d = 0.0;
+  // The step's scalars in FP64 by one thread, shared in AT (the FP64 pipe is a small
+  // fraction of the FP32 one: no thread repeats the division).
+  __shared__ AT coef[3];   // alpha, sigma alpha, 1 / n
+  __shared__ int bad_s;
+  double pAp = 0.0;
   if constexpr (kFused) {
-    if (!restart) {
-      double pAp, unused;
-      sum_partials(d.cblk_part, d.ncblk * kApplySplit, pAp, unused);
-      const bool bad = !(pAp > 0.0) || !isfinite(pAp);
-      alpha_d = bad ? 0.0 : sc->rz / pAp;
-      __syncthreads();   // every thread has read sc->rz before block 0 may stop the solve
-      if (cbl == 0 && threadIdx.x == 0) {
-        sc->pAp = pAp;
-        sc->alpha = alpha_d;
-        if (bad) {
-          sc->pcg_done = 1;
-          // p^T S p not positive: S is not positive definite at this damping
-          if (sc->pcg_it == 0) sc->pcg_fail = 1;
-          else sc->pcg_breakdown = 1;
-          atomicSub(ls.running, 1);
-        }
-      }
-      if (bad) return;
-    }
-  } else {
-    alpha_d = sc->alpha;
+    if (!restart) pAp = sum_partials_first(d.cblk_part, d.ncblk * kApplySplit);
   }
+  if (threadIdx.x == 0) {
+    double alpha_d;
+    int bad = 0;
+    if constexpr (kFused) {
+      if (!restart) {
+        bad = !(pAp > 0.0) || !isfinite(pAp);
+        alpha_d = bad ? 0.0 : sc->rz / pAp;
+        if (cbl == 0) {
+          sc->pAp = pAp;
+          sc->alpha = alpha_d;
+          if (bad) {
+            sc->pcg_done = 1;
+            // p^T S p not positive: S is not positive definite at this damping
+            if (sc->pcg_it == 0) sc->pcg_fail = 1;
+            else sc->pcg_breakdown = 1;
+            atomicSub(ls.running, 1);
+          }
+        }
+      } else {
+        alpha_d = 0.0;
+      }
+    } else {
+      alpha_d = sc->alpha;
+    }
+    coef[0] = (AT)alpha_d;
+    coef[1] = (AT)(sc->sigma * alpha_d);
+    coef[2] = (AT)sc->inv_n;
+    bad_s = bad;
+  }
+  __syncthreads();
+  if (bad_s) return;
   AT rz_c = (AT)0, rr_c = (AT)0;   // per-warp partials in AT, accumulated across warps in FP64
   if (c < d.C) {   // warp-uniform
-    const AT alpha = (AT)alpha_d, sa = (AT)(sc->sigma * alpha_d), sn = (AT)sc->inv_n;
+    const AT alpha = coef[0], sa = coef[1], sn = coef[2];
     AT* x = reinterpret_cast<AT*>(d.x) + DB * (size_t)c;
     AT* r = reinterpret_cast<AT*>(d.r) + DB * (size_t)c;
     AT* z = reinterpret_cast<AT*>(d.z) + DB * (size_t)c;
