@@ -671,6 +671,8 @@ void gpo_host::fill_scalars(gpo_graph* g, const gpo_lm_params& p, double lambda,
   g->pcg_full = s.full;
   s.sigma = 1.0;
   s.inv_n = 1.0;
+  s.inv_n_f = 1.0f;
+  s.beta_f = 0.0f;
   s.active = 1;
   s.pcg_done = 1;   // until the camera blocks start a PCG solve
 }

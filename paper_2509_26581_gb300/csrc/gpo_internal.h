@@ -85,6 +85,9 @@ struct Scalars {
                          // edge of positive definiteness in the working precision): the
                          // iterate is a descent step, but the damping is not lowered
   int have_best;         // the rejection-ratio guard has saved an iterate
+  float beta_f, inv_n_f; // beta and inv_n rounded to FP32 once, where they are set (the
+                         // FP32 kernels read these: a conversion from FP64 per thread
+                         // would occupy the part's small FP64 pipe)
 };
 
 struct IterRecord {       // mirrors gpo_iter_record

@@ -243,6 +243,28 @@ __device__ __forceinline__ bool last_cta(unsigned int* ticket, int ctas) {
   return is_last;
 }
 
+// The PCG's beta and 1/n in the accumulation type: the FP32 copies the update stores
+// beside the FP64 values (the same rounding a conversion here would give).
+template <class AT>
+__device__ __forceinline__ AT sc_beta(const Scalars* sc) {
+  if constexpr (sizeof(AT) == 4) return sc->beta_f;
+  else return sc->beta;
+}
+template <class AT>
+__device__ __forceinline__ AT sc_inv_n(const Scalars* sc) {
+  if constexpr (sizeof(AT) == 4) return sc->inv_n_f;
+  else return sc->inv_n;
+}
+
+// Width of the reduction trees below: the smallest power of two holding the threads
+// that loaded a partial (the threads past them hold zeros, which the full-width tree
+// would only add, exactly; FP64 adds are scarce on this part).
+__device__ __forceinline__ int tree_width(int n) {
+  int m = 1;
+  while (m < n && m < (int)blockDim.x) m <<= 1;
+  return m;
+}
+
 // Sums the n per-CTA partial pairs (stride 2) with all threads of the CTA in a fixed
 // order (strided per thread, then a fixed tree); the result is valid in every thread.
 __device__ __forceinline__ void sum_partials(const double* part, int n, double& a, double& b) {
@@ -255,7 +277,7 @@ __device__ __forceinline__ void sum_partials(const double* part, int n, double& 
   ra[threadIdx.x] = x;
   rb[threadIdx.x] = y;
   __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+  for (int s2 = tree_width(n) / 2; s2 > 0; s2 >>= 1) {
     if ((int)threadIdx.x < s2) {
       ra[threadIdx.x] += ra[threadIdx.x + s2];
       rb[threadIdx.x] += rb[threadIdx.x + s2];
@@ -275,7 +297,7 @@ __device__ __forceinline__ double sum_partials_first(const double* part, int n) 
   for (int i = threadIdx.x; i < n; i += blockDim.x) x += part[2 * i];
   ra[threadIdx.x] = x;
   __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+  for (int s2 = tree_width(n) / 2; s2 > 0; s2 >>= 1) {
     if ((int)threadIdx.x < s2) ra[threadIdx.x] += ra[threadIdx.x + s2];
     __syncthreads();
   }
@@ -290,7 +312,7 @@ __device__ __forceinline__ double sum_singles(const double* part, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) x += part[i];
   rs[threadIdx.x] = x;
   __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+  for (int s2 = tree_width(n) / 2; s2 > 0; s2 >>= 1) {
     if ((int)threadIdx.x < s2) rs[threadIdx.x] += rs[threadIdx.x + s2];
     __syncthreads();
   }

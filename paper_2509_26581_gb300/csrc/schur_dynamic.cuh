@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dyn(LaunchSet ls) {
   const Scalars* sc = d.sc;
   const ChunkRange cr = chunk_range(d, kl);
   const int act = sc->active, done = sc->pcg_done, pidx = sc->pidx, restart = sc->restart;
-  const double beta_d = sc->beta, inv_n_d = sc->inv_n;
+  const AT beta_a = sc_beta<AT>(sc), inv_n_a = sc_inv_n<AT>(sc);
   if (!act || done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max, LD = CH + 1;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dyn(LaunchSet ls) {
   }
   const AT* zv = reinterpret_cast<const AT*>(restart ? d.x : d.z);
   const AT* pold = restart ? zv : reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
-  const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
+  const AT beta = restart ? (AT)0 : beta_a, inv_n = restart ? (AT)1 : inv_n_a;
   for (int t = threadIdx.x; t < cr.nS; t += kThreads) {
     const int4 r4 = __ldg(d.slot_rec + cr.s0 + t);
     so[t] = r4.x;

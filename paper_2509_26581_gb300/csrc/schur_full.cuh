@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
   const ChunkRange cr = chunk_range(d, kl);
   const int act = sc->active, done = sc->pcg_done, pidx = sc->pidx, restart = sc->restart;
   const int save_best = sc->save_best;
-  const double beta_d = sc->beta, inv_n_d = sc->inv_n, lam_d = sc->lambda;
+  const AT beta_a = sc_beta<AT>(sc), inv_n_a = sc_inv_n<AT>(sc);
+  const double lam_d = sc->lambda;
   if (!act || done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max, LD = CH + 1;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_full_spmv(LaunchSet ls) {
   int* so = po + ls.np_max + 1;                           // [ns + 1] local slot offsets
   int* sp = so + ls.ns_max + 1;                           // [ns] camera-major slot rows
   const JT* Jg = reinterpret_cast<const JT*>(d.J);
-  const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
+  const AT beta = restart ? (AT)0 : beta_a, inv_n = restart ? (AT)1 : inv_n_a;
   // the packed positions of this thread's edges (up to four: chunks of at most 1,024
   // edges) are loaded ahead of the gathers, so their latency overlaps them
   const bool packed = ls.ch_max <= 1024;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_full_update(LaunchSet ls)
   const int restart = sc->restart;
   double rz = 0.0, rr = 0.0;
   for (int p = pbl * kUpdatePoints + threadIdx.x; p < min(d.P, (pbl + 1) * kUpdatePoints); p += kThreads) {
-    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = (AT)sc->inv_n;
+    const AT alpha = (AT)sc->alpha, sa = (AT)(sc->sigma * sc->alpha), sn = sc_inv_n<AT>(sc);
     const size_t o = 3 * (size_t)p;
     AT* x = reinterpret_cast<AT*>(d.xq) + o;
     AT* r = reinterpret_cast<AT*>(d.rq) + o;

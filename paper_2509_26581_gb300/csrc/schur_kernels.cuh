@@ -707,6 +707,8 @@ __global__ void __launch_bounds__(kCamPerBlock * 32) k_cam_finalize(LaunchSet ls
     sc->sigma = 1.0;
     sc->inv_n = 1.0;
     sc->beta = 0.0;
+    sc->inv_n_f = 1.0f;
+    sc->beta_f = 0.0f;
     sc->pidx = 0;
     sc->pcg_it = 0;
     sc->pcg_products = 0;
@@ -773,7 +775,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
   // block (the other forms load that row once the slot sums are in).
   constexpr bool kEarlyH = kFused && sizeof(AT) == 4;
   const int active = sc->active, done = sc->pcg_done, restart = sc->restart, pidx = sc->pidx;
-  const double beta_d = sc->beta, inv_n_d = sc->inv_n;
+  const AT beta_a = sc_beta<AT>(sc), inv_n_a = sc_inv_n<AT>(sc);
   const int full = sc->full, save_best = sc->save_best;
   const bool lead = c < d.C && q == 0 && lane < DB;
   const AT* H = reinterpret_cast<const AT*>(d.Hcl) + (size_t)(c < d.C ? c : 0) * TB;
@@ -807,7 +809,7 @@ __device__ void cam_apply_body(const LaunchSet& ls, const DevBA& d, int cbl, int
   // restart iteration the current solution x (read as (x + 0 x) / 1, exactly x)
   const AT* z_all = reinterpret_cast<const AT*>(restart ? d.x : d.z);
   const AT* pold_all = restart ? z_all : reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
-  const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
+  const AT beta = restart ? (AT)0 : beta_a, inv_n = restart ? (AT)1 : inv_n_a;
   AT dot = (AT)0;   // per-warp partial in AT, accumulated across warps in FP64
   AT pi = (AT)0;
   if (c < d.C) {   // warp-uniform
@@ -1006,6 +1008,8 @@ __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, in
       sc->inv_n = 1.0;
       sc->rz = rz;
     }
+    sc->beta_f = (float)sc->beta;
+    sc->inv_n_f = (float)sc->inv_n;
     if (!restart) sc->pidx ^= 1;            // a restart wrote no new direction
     sc->restart = (!done && !restart && sc->restart_every > 0 && sc->pcg_it % sc->restart_every == 0) ? 1 : 0;
     sc->pcg_done = done;
@@ -1069,7 +1073,7 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
     }
     coef[0] = (AT)alpha_d;
     coef[1] = (AT)(sc->sigma * alpha_d);
-    coef[2] = (AT)sc->inv_n;
+    coef[2] = sc_inv_n<AT>(sc);
     bad_s = bad;
   }
   __syncthreads();

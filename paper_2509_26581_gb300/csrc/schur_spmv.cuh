@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   const Scalars* sc = d.sc;
   const ChunkRange cr = chunk_range(d, kl);
   const int act = sc->active, done = sc->pcg_done, pidx = sc->pidx, restart = sc->restart;
-  const double beta_d = sc->beta, inv_n_d = sc->inv_n;
+  const AT beta_a = sc_beta<AT>(sc), inv_n_a = sc_inv_n<AT>(sc);
   if (!act || done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int CH = d.ch_max, LD = CH + 1;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(LaunchSet ls) {
   // the direction p = (z + beta p_old) / n, or in a restart iteration the solution x
   const AT* zv = reinterpret_cast<const AT*>(restart ? d.x : d.z);
   const AT* pold = restart ? zv : reinterpret_cast<const AT*>(pidx ? d.p2 : d.p);
-  const AT beta = restart ? (AT)0 : (AT)beta_d, inv_n = restart ? (AT)1 : (AT)inv_n_d;
+  const AT beta = restart ? (AT)0 : beta_a, inv_n = restart ? (AT)1 : inv_n_a;
   for (int t = threadIdx.x; t < cr.nS; t += kThreads) {
     const int4 r4 = __ldg(d.slot_rec + cr.s0 + t);
     so[t] = r4.x;
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_ws(LaunchSet ls) {
         const int restart = sc->restart;   // a restart's product is taken of x
         zv = reinterpret_cast<const AT*>(restart ? P->x : P->z);
         pold = restart ? zv : reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-        beta = restart ? (AT)0 : (AT)sc->beta;
-        inv_n = restart ? (AT)1 : (AT)sc->inv_n;
+        beta = restart ? (AT)0 : sc_beta<AT>(sc);
+        inv_n = restart ? (AT)1 : sc_inv_n<AT>(sc);
       }
       const int kl = k - ls.ch_base[q];
       const int e0 = P->ch_e0[kl], e1 = P->ch_e0[kl + 1];
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     const int restart = sc->restart;     // a restart's product is taken of x
     const AT* zv = reinterpret_cast<const AT*>(restart ? P->x : P->z);
     const AT* pold = restart ? zv : reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-    const AT beta = restart ? (AT)0 : (AT)sc->beta, inv_n = restart ? (AT)1 : (AT)sc->inv_n;
+    const AT beta = restart ? (AT)0 : sc_beta<AT>(sc), inv_n = restart ? (AT)1 : sc_inv_n<AT>(sc);
     for (int w = threadIdx.x; w < c.nS * DC; w += kThreads) {
       const int sl = w / DC, k = w - sl * DC;
       const size_t o = DB * (size_t)srec[sl].z + k;

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, WgOcc<JT>::value) k_spmv_wg(LaunchSe
     const int restart = sc->restart;
     const AT* zv = reinterpret_cast<const AT*>(restart ? P->x : P->z);
     const AT* pold = restart ? zv : reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-    const AT beta = restart ? (AT)0 : (AT)sc->beta, inv_n = restart ? (AT)1 : (AT)sc->inv_n;
+    const AT beta = restart ? (AT)0 : sc_beta<AT>(sc), inv_n = restart ? (AT)1 : sc_inv_n<AT>(sc);
     const int4* sr = P->slot_rec + c.s0;
     for (int w = threadIdx.x; w < c.nS * DC; w += kThreads) {
       const int sl = w / DC, k = w - sl * DC;
@@ -449,8 +449,8 @@ __global__ void __launch_bounds__(kWsThreads) k_spmv_wgs(LaunchSet ls) {
         const int restart = sc->restart;   // a restart's product is taken of x
         zv = reinterpret_cast<const AT*>(restart ? P->x : P->z);
         pold = restart ? zv : reinterpret_cast<const AT*>(sc->pidx ? P->p2 : P->p);
-        beta = restart ? (AT)0 : (AT)sc->beta;
-        inv_n = restart ? (AT)1 : (AT)sc->inv_n;
+        beta = restart ? (AT)0 : sc_beta<AT>(sc);
+        inv_n = restart ? (AT)1 : sc_inv_n<AT>(sc);
       }
       const int kl = ls.nprob == 1 ? k : k - ls.ch_base[q];
       const int e0 = P->ch_e0[kl], e1 = P->ch_e0[kl + 1];
