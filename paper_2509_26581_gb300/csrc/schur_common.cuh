@@ -231,15 +231,17 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Call after thread 0 has written the CTA's partial; true in the CTA that finishes last.
+// Thread 0 fences, takes a ticket, and in the last CTA fences again before the barrier
+// that orders the CTA's later reads of the other CTAs' partials after it.
 __device__ __forceinline__ bool last_cta(unsigned int* ticket, int ctas) {
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
     is_last = (t == (unsigned int)ctas - 1u);
+    if (is_last) __threadfence();
   }
   __syncthreads();
-  if (is_last) __threadfence();
   return is_last;
 }
 

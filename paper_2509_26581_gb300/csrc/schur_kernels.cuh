@@ -963,6 +963,24 @@ __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, in
   const int full = sc->full;
   const int npb = full ? update_point_blocks(d.P) : 0;   // the update's point CTAs
   if (!last_cta(&sc->ticket, d.ncblk + npb)) return;
+  // the solve's state, read by thread 0 in one batch while the partials are summed (read
+  // one at a time between the writes below, they were a chain of dependent round trips)
+  double sigma = 0.0, rmin = 0.0, ratio = 0.0, tol_abs = 0.0, rz_old = 0.0;
+  int pcg_it = 0, max_it = 0, normalize = 0, restart_every = 0, pidx = 0, pcg_total = 0, pcg_products = 0;
+  if (threadIdx.x == 0) {
+    sigma = sc->sigma;
+    rmin = sc->rmin;
+    ratio = sc->ratio;
+    tol_abs = sc->tol_abs;
+    rz_old = sc->rz;
+    pcg_it = sc->pcg_it;
+    max_it = sc->max_it;
+    normalize = sc->normalize;
+    restart_every = sc->restart_every;
+    pidx = sc->pidx;
+    pcg_total = sc->pcg_total;
+    pcg_products = sc->pcg_products;
+  }
   double rz, rr;
   sum_partials(d.cblk_part + 2 * kApplySplit * (size_t)d.ncblk, d.ncblk, rz, rr);
   if (full) {
@@ -974,44 +992,54 @@ __device__ inline void pcg_update_finish(const LaunchSet& ls, const DevBA& d, in
   }
   if (threadIdx.x == 0) {
     const double n = sqrt(rr);
-    if (restart) sc->sigma = 1.0;            // r is now the true residual
-    const double rtrue = sc->sigma * n;
-    if (!restart) sc->pcg_it += 1;           // a restart is an extra product, not an iteration
-    sc->pcg_total += 1;
-    sc->pcg_products += 1;
-    sc->rnorm = rtrue;
-    int done = 0;
-    sc->save_best = 0;
-    if (sc->ratio > 0.0) {
-      if (rtrue < sc->rmin) {
-        sc->rmin = rtrue;
-        sc->save_best = 1;
-        sc->have_best = 1;
-      } else if (rtrue > sc->ratio * sc->rmin) {
+    if (restart) sigma = 1.0;                // r is now the true residual
+    const double rtrue = sigma * n;
+    if (!restart) pcg_it += 1;               // a restart is an extra product, not an iteration
+    int done = 0, save_best = 0, have_best = 0, use_best = 0, breakdown = 0;
+    if (ratio > 0.0) {
+      if (rtrue < rmin) {
+        rmin = rtrue;
+        save_best = 1;
+        have_best = 1;
+      } else if (rtrue > ratio * rmin) {
         done = 1;
-        sc->use_best = 1;
+        use_best = 1;
       }
     }
-    if (rtrue <= sc->tol_abs || sc->pcg_it >= sc->max_it || !isfinite(rtrue) || !(rz > 0.0)) {
+    if (rtrue <= tol_abs || pcg_it >= max_it || !isfinite(rtrue) || !(rz > 0.0)) {
       done = 1;
-      if (!isfinite(rtrue)) sc->use_best = 1;
+      if (!isfinite(rtrue)) use_best = 1;
       // r^T M r not positive before the tolerance is met: the preconditioned system is
       // not positive definite at this damping (after at least one step)
-      if (!(rz > 0.0) && !(rtrue <= sc->tol_abs)) sc->pcg_breakdown = 1;
+      if (!(rz > 0.0) && !(rtrue <= tol_abs)) breakdown = 1;
     }
-    sc->beta = restart ? 0.0 : rz / sc->rz;   // a restart starts the direction from z
-    if (sc->normalize && n > 0.0) {
-      sc->inv_n = 1.0 / n;
-      sc->sigma *= n;
-      sc->rz = rz / (n * n);
+    const double beta = restart ? 0.0 : rz / rz_old;   // a restart starts the direction from z
+    double inv_n, rz_new;
+    if (normalize && n > 0.0) {
+      inv_n = 1.0 / n;
+      sigma *= n;
+      rz_new = rz / (n * n);
     } else {
-      sc->inv_n = 1.0;
-      sc->rz = rz;
+      inv_n = 1.0;
+      rz_new = rz;
     }
-    sc->beta_f = (float)sc->beta;
-    sc->inv_n_f = (float)sc->inv_n;
-    if (!restart) sc->pidx ^= 1;            // a restart wrote no new direction
-    sc->restart = (!done && !restart && sc->restart_every > 0 && sc->pcg_it % sc->restart_every == 0) ? 1 : 0;
+    sc->sigma = sigma;
+    sc->pcg_it = pcg_it;
+    sc->pcg_total = pcg_total + 1;
+    sc->pcg_products = pcg_products + 1;
+    sc->rnorm = rtrue;
+    sc->rmin = rmin;
+    sc->save_best = save_best;
+    if (have_best) sc->have_best = 1;
+    if (use_best) sc->use_best = 1;
+    if (breakdown) sc->pcg_breakdown = 1;
+    sc->beta = beta;
+    sc->inv_n = inv_n;
+    sc->rz = rz_new;
+    sc->beta_f = (float)beta;
+    sc->inv_n_f = (float)inv_n;
+    if (!restart) sc->pidx = pidx ^ 1;       // a restart wrote no new direction
+    sc->restart = (!done && !restart && restart_every > 0 && pcg_it % restart_every == 0) ? 1 : 0;
     sc->pcg_done = done;
     if (done) atomicSub(ls.running, 1);
     sc->ticket = 0u;
