@@ -230,17 +230,31 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return out;
 }
 
-// Call after thread 0 has written the CTA's partial; true in the CTA that finishes last.
-// Thread 0 fences, takes a ticket, and in the last CTA fences again before the barrier
-// that orders the CTA's later reads of the other CTAs' partials after it.
+// GPU-scope synchronising accesses (PTX memory model): an add that is both a release of
+// the thread's earlier writes (and of the writes it has observed, such as its CTA's
+// before a barrier) and an acquire of the writes released to the same location; a
+// release add that returns nothing; an acquire load.
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Call after thread 0 has written the CTA's partial (after a barrier if other threads
+// wrote it); true in the CTA that finishes last.  Thread 0 takes the ticket with an
+// acquire-release add: it releases the CTA's writes, and in the last CTA it acquires
+// every other CTA's, which the barrier then orders before the CTA's later reads.
 __device__ __forceinline__ bool last_cta(unsigned int* ticket, int ctas) {
   __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int t = atomicAdd(ticket, 1u);
-    is_last = (t == (unsigned int)ctas - 1u);
-    if (is_last) __threadfence();
-  }
+  if (threadIdx.x == 0) is_last = atom_add_acq_rel(ticket, 1u) == (unsigned int)ctas - 1u;
   __syncthreads();
   return is_last;
 }

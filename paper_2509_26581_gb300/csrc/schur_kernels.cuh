@@ -1169,31 +1169,30 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 constexpr unsigned long long kWaitNs = 1000000000ull;   // bounded waits give up after 1 s
 
-// Grid-wide barrier of the persistent camera kernel (every CTA resident): the last
-// CTA to arrive resets the count and advances the generation the others wait on.  The
-// wait is bounded (kWaitNs of wall time); false if it gave up (the caller raises
-// *ls.err).
+// Grid-wide barrier of the persistent camera kernel (every CTA resident; called after a
+// CTA barrier): thread 0 arrives with an acquire-release add, the last CTA to arrive
+// resets the count and advances the generation with a release add, and the others
+// wait for it with acquire loads.  The wait is bounded (kWaitNs of wall time); false if
+// it gave up (the caller raises *ls.err).
 __device__ __forceinline__ bool grid_sync(int* count, int* gen, int ctas) {
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile int* vg = gen;
-    const int g0 = *vg;
-    __threadfence();
-    if (atomicAdd(count, 1) == ctas - 1) {
-      atomicExch(count, 0);
-      __threadfence();
-      atomicAdd(gen, 1);
+    unsigned int* ucount = reinterpret_cast<unsigned int*>(count);
+    unsigned int* ugen = reinterpret_cast<unsigned int*>(gen);
+    const unsigned int g0 = ld_acquire(ugen);
+    if (atom_add_acq_rel(ucount, 1u) == (unsigned int)ctas - 1u) {
+      atomicExch(ucount, 0u);
+      red_add_release(ugen, 1u);
     } else {
       const unsigned long long t0 = global_ns();
-      while (*vg == g0) {
+      while (ld_acquire(ugen) == g0) {
         if (global_ns() - t0 > kWaitNs) {
           ok = 0;
           break;
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
