@@ -208,24 +208,36 @@ struct OddRow {   // row length in values, N rounded up so the row spans an odd 
 };
 
 // One warp per slot (slots handed out by a shared counter, so long slots do not hold
-// up a fixed set of warps); lane l owns outputs l, l + 32, ... of the row.  All lanes
-// read the same edge's records at a time (broadcasts or distinct banks).  Each output
-// is summed over the slot's edges in slot order: acc += (sum_a Y[i][a] Y[j][a]).
+// up a fixed set of warps).  The camera indices are cut into blocks of three; a lane
+// has a role -- one 3 x 3 tile of the upper block triangle of sum_e Y_e^T Y_e, or one
+// block of sum_e g_e -- and an edge group: the warp's R roles repeat G = 32 / R times,
+// group j takes the slot's edges j, j + G, ... in slot order, and at the end group 0
+// adds the other groups' sums in group order (shuffles).  A tile lane reads its 2 x 3
+// record values per row of Y once per edge and forms nine products from them, so the
+// reduction costs about half the instructions of one output per lane.
 template <class Mo, class YT, class AT, int RSY, int RSG>
 __device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, const YT* Y, const AT* G,
                                           const uint16_t* srt, AT* part, int* next) {
   using Dm = Dims<Mo>;
   constexpr int M = Mo::M, DC = Mo::DC, TC = Dm::TC, NPA = Dm::NPA;
-  constexpr int OPL = (NPA + 31) / 32;
+  constexpr int NB = (DC + 2) / 3;           // index blocks of three
+  constexpr int NT = NB * (NB + 1) / 2;      // tiles of the upper block triangle
+  constexpr int R = NT + NB;                 // roles: the tiles, then the gradient blocks
+  constexpr int NG = 32 / R;                 // edge groups
+  static_assert(NG >= 1, "a warp holds every role");
   const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  int oi[OPL], oj[OPL], kind[OPL];    // kind: 0 H entry, 1 vector entry, 2 padding
-#pragma unroll
-  for (int u = 0; u < OPL; ++u) {
-    const int o = lane + 32 * u;
-    kind[u] = o < TC ? 0 : (o < TC + DC ? 1 : 2);
-    oi[u] = o < TC ? tri_row<DC>(o) * M : (o < TC + DC ? o - TC : 0);
-    oj[u] = o < TC ? tri_col<DC>(o) * M : 0;
+  const int lane = threadIdx.x & 31, role = lane % R, grp = lane / R;   // grp == NG: idle
+  const bool tile = role < NT;
+  int bi = 0, bj = 0;
+  if (tile) {
+    int t = role;
+    while (t >= NB - bi) {
+      t -= NB - bi;
+      ++bi;
+    }
+    bj = bi + t;
+  } else {
+    bi = bj = role - NT;
   }
   for (;;) {
     int sl = 0;
@@ -233,29 +245,63 @@ __device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, 
     sl = __shfl_sync(full, sl, 0);
     if (sl >= cr.nS) break;
     const int qa = d.slot_e0[cr.s0 + sl] - cr.e0, qb = d.slot_e0[cr.s0 + sl + 1] - cr.e0;
-    AT acc[OPL];
+    AT acc[9];
 #pragma unroll
-    for (int u = 0; u < OPL; ++u) acc[u] = (AT)0;
-    for (int q = qa; q < qb; ++q) {
-      const int e = srt[q];
-      const YT* y = Y + (size_t)e * RSY;
-      const AT* g = G + (size_t)e * RSG;
+    for (int c = 0; c < 9; ++c) acc[c] = (AT)0;
+    if (grp < NG) {
+      for (int q = qa + grp; q < qb; q += NG) {
+        const int e = srt[q];
+        if (tile) {
+          const YT* y = Y + (size_t)e * RSY;
+          AT yi[3][M], yj[3][M];
 #pragma unroll
-      for (int u = 0; u < OPL; ++u) {
-        if (kind[u] == 0) {
-          AT s = (AT)ldj(y + oi[u]) * (AT)ldj(y + oj[u]);
+          for (int u = 0; u < 3; ++u) {
+            const int i = 3 * bi + u, j = 3 * bj + u;
 #pragma unroll
-          for (int a = 1; a < M; ++a) s += (AT)ldj(y + oi[u] + a) * (AT)ldj(y + oj[u] + a);
-          acc[u] += s;
-        } else if (kind[u] == 1) {
-          acc[u] += g[oi[u]];
+            for (int r = 0; r < M; ++r) {
+              yi[u][r] = i < DC ? (AT)ldj(y + i * M + r) : (AT)0;
+              yj[u][r] = j < DC ? (AT)ldj(y + j * M + r) : (AT)0;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+#pragma unroll
+              for (int r = 0; r < M; ++r) acc[3 * u + v] = fma(yi[u][r], yj[v][r], acc[3 * u + v]);
+        } else {
+          const AT* g = G + (size_t)e * RSG;
+#pragma unroll
+          for (int u = 0; u < 3; ++u)
+            if (3 * bi + u < DC) acc[u] += g[3 * bi + u];
         }
       }
     }
-    AT* out = part + (size_t)d.slot_pos[cr.s0 + sl] * NPA;
 #pragma unroll
-    for (int u = 0; u < OPL; ++u)
-      if (lane + 32 * u < NPA) out[lane + 32 * u] = acc[u];
+    for (int j = 1; j < NG; ++j) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const AT o = __shfl_sync(full, acc[c], role + R * j);
+        if (grp == 0) acc[c] += o;
+      }
+    }
+    AT* out = part + (size_t)d.slot_pos[cr.s0 + sl] * NPA;
+    if (grp == 0) {
+      if (tile) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            const int i = 3 * bi + u, j = 3 * bj + v;
+            if (i < DC && j < DC && i <= j) out[tri_idx(DC, i, j)] = acc[3 * u + v];
+          }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (3 * bi + u < DC) out[TC + 3 * bi + u] = acc[u];
+      }
+    }
+    for (int o = TC + DC + lane; o < NPA; o += 32) out[o] = (AT)0;
   }
 }
 
