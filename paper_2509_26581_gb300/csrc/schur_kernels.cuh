@@ -209,97 +209,87 @@ struct OddRow {   // row length in values, N rounded up so the row spans an odd 
 
 // One warp per slot (slots handed out by a shared counter, so long slots do not hold
 // up a fixed set of warps).  The camera indices are cut into blocks of three; a lane
-// has a role -- one 3 x 3 tile of the upper block triangle of sum_e Y_e^T Y_e, or one
-// block of sum_e g_e -- and an edge group: the warp's R roles repeat G = 32 / R times,
-// group j takes the slot's edges j, j + G, ... in slot order, and at the end group 0
-// adds the other groups' sums in group order (shuffles).  A tile lane reads its 2 x 3
-// record values per row of Y once per edge and forms nine products from them, so the
-// reduction costs about half the instructions of one output per lane.
+// has a role -- one 3 x 3 tile of the upper block triangle of sum_e Y_e^T Y_e, and the
+// entries role, role + NT, ... of sum_e g_e -- and an edge group: the warp's NT roles
+// repeat NG = 32 / NT times, group j takes the slot's edges j, j + NG, ... in slot
+// order, and at the end group 0 adds the other groups' sums in group order (shuffles).
+// A lane reads its 2 x 3 record values per row of Y once per edge and forms nine
+// products from them, so the reduction costs a fraction of the instructions of one
+// output per lane.
 template <class Mo, class YT, class AT, int RSY, int RSG>
 __device__ __forceinline__ void slot_rows(const DevBA& d, const ChunkRange& cr, const YT* Y, const AT* G,
                                           const uint16_t* srt, AT* part, int* next) {
   using Dm = Dims<Mo>;
   constexpr int M = Mo::M, DC = Mo::DC, TC = Dm::TC, NPA = Dm::NPA;
   constexpr int NB = (DC + 2) / 3;           // index blocks of three
-  constexpr int NT = NB * (NB + 1) / 2;      // tiles of the upper block triangle
-  constexpr int R = NT + NB;                 // roles: the tiles, then the gradient blocks
-  constexpr int NG = 32 / R;                 // edge groups
+  constexpr int NT = NB * (NB + 1) / 2;      // tiles of the upper block triangle: the roles
+  constexpr int KG = (DC + NT - 1) / NT;     // gradient entries per role
+  constexpr int NG = 32 / NT;                // edge groups
+  constexpr int NA = 9 + KG;                 // sums per lane
   static_assert(NG >= 1, "a warp holds every role");
   const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, role = lane % R, grp = lane / R;   // grp == NG: idle
-  const bool tile = role < NT;
-  int bi = 0, bj = 0;
-  if (tile) {
-    int t = role;
-    while (t >= NB - bi) {
-      t -= NB - bi;
-      ++bi;
-    }
-    bj = bi + t;
-  } else {
-    bi = bj = role - NT;
+  const int lane = threadIdx.x & 31, role = lane % NT, grp = lane / NT;   // grp == NG: idle
+  int bi = 0, t = role;
+  while (t >= NB - bi) {
+    t -= NB - bi;
+    ++bi;
   }
+  const int bj = bi + t;
   for (;;) {
     int sl = 0;
     if (lane == 0) sl = atomicAdd(next, 1);
     sl = __shfl_sync(full, sl, 0);
     if (sl >= cr.nS) break;
     const int qa = d.slot_e0[cr.s0 + sl] - cr.e0, qb = d.slot_e0[cr.s0 + sl + 1] - cr.e0;
-    AT acc[9];
+    AT acc[NA];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = (AT)0;
+    for (int c = 0; c < NA; ++c) acc[c] = (AT)0;
     if (grp < NG) {
       for (int q = qa + grp; q < qb; q += NG) {
         const int e = srt[q];
-        if (tile) {
-          const YT* y = Y + (size_t)e * RSY;
-          AT yi[3][M], yj[3][M];
+        const YT* y = Y + (size_t)e * RSY;
+        const AT* g = G + (size_t)e * RSG;
+        AT yi[3][M], yj[3][M];
 #pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            const int i = 3 * bi + u, j = 3 * bj + u;
+        for (int u = 0; u < 3; ++u) {
+          const int i = 3 * bi + u, j = 3 * bj + u;
 #pragma unroll
-            for (int r = 0; r < M; ++r) {
-              yi[u][r] = i < DC ? (AT)ldj(y + i * M + r) : (AT)0;
-              yj[u][r] = j < DC ? (AT)ldj(y + j * M + r) : (AT)0;
-            }
+          for (int r = 0; r < M; ++r) {
+            yi[u][r] = i < DC ? (AT)ldj(y + i * M + r) : (AT)0;
+            yj[u][r] = j < DC ? (AT)ldj(y + j * M + r) : (AT)0;
           }
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-#pragma unroll
-            for (int v = 0; v < 3; ++v)
-#pragma unroll
-              for (int r = 0; r < M; ++r) acc[3 * u + v] = fma(yi[u][r], yj[v][r], acc[3 * u + v]);
-        } else {
-          const AT* g = G + (size_t)e * RSG;
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-            if (3 * bi + u < DC) acc[u] += g[3 * bi + u];
         }
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int r = 0; r < M; ++r) acc[3 * u + v] = fma(yi[u][r], yj[v][r], acc[3 * u + v]);
+#pragma unroll
+        for (int m = 0; m < KG; ++m)
+          if (role + NT * m < DC) acc[9 + m] += g[role + NT * m];
       }
     }
 #pragma unroll
     for (int j = 1; j < NG; ++j) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const AT o = __shfl_sync(full, acc[c], role + R * j);
+      for (int c = 0; c < NA; ++c) {
+        const AT o = __shfl_sync(full, acc[c], role + NT * j);
         if (grp == 0) acc[c] += o;
       }
     }
     AT* out = part + (size_t)d.slot_pos[cr.s0 + sl] * NPA;
     if (grp == 0) {
-      if (tile) {
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+      for (int u = 0; u < 3; ++u)
 #pragma unroll
-          for (int v = 0; v < 3; ++v) {
-            const int i = 3 * bi + u, j = 3 * bj + v;
-            if (i < DC && j < DC && i <= j) out[tri_idx(DC, i, j)] = acc[3 * u + v];
-          }
-      } else {
+        for (int v = 0; v < 3; ++v) {
+          const int i = 3 * bi + u, j = 3 * bj + v;
+          if (i < DC && j < DC && i <= j) out[tri_idx(DC, i, j)] = acc[3 * u + v];
+        }
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
-          if (3 * bi + u < DC) out[TC + 3 * bi + u] = acc[u];
-      }
+      for (int m = 0; m < KG; ++m)
+        if (role + NT * m < DC) out[TC + role + NT * m] = acc[9 + m];
     }
     for (int o = TC + DC + lane; o < NPA; o += 32) out[o] = (AT)0;
   }
