@@ -168,13 +168,13 @@ NOMINAL_HBM_GBS = 7900.0
 # a hash of the kernel sources they were counted from, so changed kernels report null.
 FP64_SOURCES = ("schur_common.cuh", "schur_kernels.cuh")
 FP64_FLOPS_PER_EDGE = {
-    ("k_linearize", "bf16", "621365f371b6"): 18.00,
-    ("k_linearize", "fp32", "621365f371b6"): 18.00,
-    ("k_linearize", "fp64", "621365f371b6"): 449.29,
+    ("k_linearize", "bf16", "cbfa9717498d"): 18.00,
+    ("k_linearize", "fp32", "cbfa9717498d"): 18.00,
+    ("k_linearize", "fp64", "cbfa9717498d"): 588.78,
     # one kernel for every precision (FP64 geometry and cost)
-    ("k_cost", "bf16", "621365f371b6"): 65.55,
-    ("k_cost", "fp32", "621365f371b6"): 65.55,
-    ("k_cost", "fp64", "621365f371b6"): 65.55,
+    ("k_cost", "bf16", "cbfa9717498d"): 65.55,
+    ("k_cost", "fp32", "cbfa9717498d"): 65.55,
+    ("k_cost", "fp64", "cbfa9717498d"): 65.55,
 }
 
 
