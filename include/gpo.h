@@ -305,8 +305,10 @@ gpo_status gpo_set_edge_active(gpo_graph* g, int64_t edge_id, int32_t active);
 
 /* Sets the states of vertices first_id .. first_id + n - 1, which must all be of
  * one kind, from `state` (n rows of the kind's state size, FP64).  on_device = 1:
- * `state` is a device pointer.  Allowed before and between optimize calls.
- * Errors: GPO_ERR_ARG, GPO_ERR_CUDA. */
+ * `state` is a device pointer; a pinned host pointer is read in place by the device.
+ * Allowed before and between optimize calls.  After the first optimize, rows whose
+ * values are bit for bit the ones the graph holds leave it as it was (see
+ * gpo_optimize).  Errors: GPO_ERR_ARG, GPO_ERR_CUDA. */
 gpo_status gpo_set_initial(gpo_graph* g, int64_t first_id, int64_t n, const double* state,
                            int32_t on_device);
 
@@ -315,7 +317,10 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first_id, int64_t n, const doub
  * allocates device memory).  params NULL = defaults; out (optional) receives the
  * report.  Every call starts from params->initial_damping and params->initial_nu and
  * evaluates F at the current state; passing the previous report's final_lambda and
- * final_nu continues the previous call's LM run step for step.
+ * final_nu continues the previous call's LM run step for step.  When no call has
+ * changed the graph or its state since the previous gpo_optimize (with the same
+ * solver), that run's cost is taken as F, and if its last step was rejected its
+ * linearisation is kept: the values a fresh evaluation gives, without the kernels.
  * Errors: GPO_ERR_ARG, GPO_ERR_OOM, GPO_ERR_NUMERIC (non-finite initial cost),
  *         GPO_ERR_UNSUPPORTED (a point seen more than the supported maximum of
  *         times), GPO_ERR_CUDA. */

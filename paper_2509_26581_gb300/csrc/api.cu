@@ -132,6 +132,20 @@ __global__ void k_scatter_rows(double* dst, const double* src, const int32_t* id
   const int t = idx ? idx[i] : i;
   for (int k = 0; k < w; ++k) dst[(size_t)t * w + k] = src[(size_t)i * w + k];
 }
+// dst rows (through idx) = src rows; *changed = 1 if any value's bits differ
+__global__ void k_assign_rows(double* dst, const double* src, const int32_t* idx, int n, int w, int* changed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = idx ? idx[i] : i;
+  bool diff = false;
+  for (int k = 0; k < w; ++k) {
+    const double v = src[(size_t)i * w + k];
+    double* p = dst + (size_t)t * w + k;
+    diff |= __double_as_longlong(*p) != __double_as_longlong(v);
+    *p = v;
+  }
+  if (diff) *changed = 1;
+}
 __global__ void k_gather_rows(double* dst, const double* src, const int32_t* idx, int n, int w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -158,6 +172,7 @@ void gpo_host::release_device(gpo_graph* g) {
   g->arena = nullptr;
   g->arena_bytes = 0;
   g->finalized = false;
+  g->state_same = false;
 }
 
 // ============================================================== topology
@@ -590,6 +605,7 @@ gpo_status gpo_host::finalize(gpo_graph* g, size_t* plan_bytes) {
   g->dev = d;
   g->finalized = true;
   g->prep.reset();
+  g->state_same = false;
   GPO_CUDA(g, cudaGetLastError());
   return GPO_OK;
 }
@@ -916,6 +932,8 @@ gpo_status gpo_host::ensure_runtime(gpo_graph* g) {
   if (g->h_sc) return GPO_OK;
   if (gpo_status s = ensure_stream(g); s != GPO_OK) return s;
   GPO_CUDA(g, cudaMallocHost(&g->h_flag, 4 * sizeof(int)));
+  GPO_CUDA(g, cudaMallocHost(&g->h_changed, sizeof(int)));
+  GPO_CUDA(g, cudaMalloc(&g->d_changed, sizeof(int)));
   GPO_CUDA(g, cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming));
   GPO_CUDA(g, cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming));
   GPO_CUDA(g, cudaMallocHost(&g->h_sc, sizeof(Scalars)));   // last: marks the runtime as ready
@@ -998,6 +1016,8 @@ gpo_status gpo_graph_destroy(gpo_graph* g) {
   release_device(g);
   if (g->h_sc) cudaFreeHost(g->h_sc);
   if (g->h_flag) cudaFreeHost(g->h_flag);
+  if (g->h_changed) cudaFreeHost(g->h_changed);
+  if (g->d_changed) cudaFree(g->d_changed);
   for (auto& ev : g->prof.pool)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : g->ev)
@@ -1035,6 +1055,7 @@ gpo_status gpo_add_vertices(gpo_graph* g, int32_t kind, int32_t block_size, int6
     g->pt_state.insert(g->pt_state.end(), 3 * n, 0.0);
   }
   g->prep.reset();
+  g->state_same = false;
   if (first_id) *first_id = id0;
   return GPO_OK;
 }
@@ -1049,6 +1070,7 @@ gpo_status gpo_set_fisheye(gpo_graph* g, const double* k) {
   g->camk[17] = 1.0;
   for (int i = 0; i < 4; ++i) g->camk[18 + i] = k[i];
   g->prep.reset();
+  g->state_same = false;
   return GPO_OK;
 }
 
@@ -1062,6 +1084,7 @@ gpo_status gpo_set_stereo_camera(gpo_graph* g, const double* rig) {
   std::memcpy(g->camk, rig, 17 * sizeof(double));
   g->camk_set = true;
   g->prep.reset();
+  g->state_same = false;
   return GPO_OK;
 }
 
@@ -1148,6 +1171,7 @@ static gpo_status add_obs_edges(gpo_graph* g, int32_t kind, int64_t n, const int
   for (int64_t i = 0; i < n; ++i) g->ed_local[eid0 + i] = (int64_t)base + i;
   if (n > 0) g->cam_kind = ck;
   g->prep.reset();
+  g->state_same = false;
   return GPO_OK;
 }
 
@@ -1205,6 +1229,7 @@ static gpo_status add_nav_edges(gpo_graph* g, int32_t kind, int64_t n, const int
     g->ed_local.push_back((int64_t)base + i);
   }
   g->prep.reset();
+  g->state_same = false;
   return GPO_OK;
 }
 
@@ -1232,6 +1257,7 @@ gpo_status gpo_set_fixed(gpo_graph* g, int64_t vid, int32_t fixed) {
   if (is_camera(g->v_kind[vid])) g->cam_fixed[g->v_local[vid]] = fixed ? 1 : 0;
   else g->pt_fixed[g->v_local[vid]] = fixed ? 1 : 0;
   g->prep.reset();
+  g->state_same = false;
   return GPO_OK;
 }
 
@@ -1243,6 +1269,7 @@ gpo_status gpo_set_edge_active(gpo_graph* g, int64_t eid, int32_t active) {
   if (k == GPO_E_BA_REPROJ || k == GPO_E_STEREO || k == GPO_E_MONO) g->e_active[g->ed_local[eid]] = active ? 1 : 0;
   else g->x_active[g->ed_local[eid]] = active ? 1 : 0;
   g->prep.reset();
+  g->state_same = false;
   return GPO_OK;
 }
 
@@ -1279,9 +1306,10 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
   if (!state) return fail(g, GPO_ERR_ARG, "null state");
   const int w = state_dim(kind);
   const int64_t loc = g->v_local[first];
-  g->cost_valid = false;
   if (!g->finalized) {
+    g->cost_valid = false;
     g->prep.reset();
+    g->state_same = false;
     std::vector<double>& dst = is_camera(kind) ? g->cam_state : g->pt_state;
     if (on_device) {
       GPO_CUDA(g, cudaMemcpy(dst.data() + loc * w, state, n * w * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1290,25 +1318,31 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
     }
     return GPO_OK;
   }
+  if ((s = ensure_runtime(g)) != GPO_OK) return s;
   cudaStream_t st = g->stream;
-  if (is_camera(kind)) {
-    GPO_CUDA(g, cudaMemcpyAsync(g->dev.cam + loc * w, state, n * w * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  } else {
-    // points live on the device in sorted order (the id -> row map is resident); the
-    // scatter reads device or mapped pinned host memory directly, pageable memory
-    // through a device copy
-    const double* src = on_device ? state : mapped_host(state);
-    double* tmp = nullptr;
-    if (!src) {
-      GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
-      GPO_CUDA(g, cudaMemcpyAsync(tmp, state, n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
-      src = tmp;
-    }
-    k_scatter_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(g->dev.pt, src, g->pt_old2new_d + loc, (int)n, 3);
-    if (tmp) GPO_CUDA(g, cudaFreeAsync(tmp, st));
+  // the rows are written through a kernel that reads device or mapped pinned host
+  // memory directly (pageable memory through a device copy) and flags any value whose
+  // bits change; points live on the device in sorted order (the id -> row map is
+  // resident)
+  GPO_CUDA(g, cudaMemsetAsync(g->d_changed, 0, sizeof(int), st));
+  const double* src = on_device ? state : mapped_host(state);
+  double* tmp = nullptr;
+  if (!src) {
+    GPO_CUDA(g, cudaMallocAsync(&tmp, n * w * sizeof(double), st));
+    GPO_CUDA(g, cudaMemcpyAsync(tmp, state, n * w * sizeof(double), cudaMemcpyHostToDevice, st));
+    src = tmp;
   }
+  double* dst = is_camera(kind) ? g->dev.cam + loc * w : g->dev.pt;
+  const int32_t* idx = is_camera(kind) ? nullptr : g->pt_old2new_d + loc;
+  k_assign_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(dst, src, idx, (int)n, w, g->d_changed);
+  GPO_CUDA(g, cudaGetLastError());
+  if (tmp) GPO_CUDA(g, cudaFreeAsync(tmp, st));
+  GPO_CUDA(g, cudaMemcpyAsync(g->h_changed, g->d_changed, sizeof(int), cudaMemcpyDeviceToHost, st));
   GPO_CUDA(g, cudaStreamSynchronize(st));
+  if (*g->h_changed) {
+    g->cost_valid = false;
+    g->state_same = false;
+  }
   return GPO_OK;
 }
 
@@ -1356,11 +1390,20 @@ gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* pa
   if (!(prm.initial_damping > 0.0)) return fail(g, GPO_ERR_ARG, "initial damping must be positive");
   if (prm.solver == GPO_SOLVER_FULL && !g->dev.J && g->dev.E > 0)
     return fail(g, GPO_ERR_UNSUPPORTED, "the full-system solver reads stored rows; dynamic Jacobians keep none");
+  // a run that continues from the state the last run left (unchanged since) takes its
+  // cost, and its linearisation if its last step was rejected: the same values a fresh
+  // evaluation gives, without the kernels
+  const bool cont = g->state_same && g->cost_valid && g->last_solver == prm.solver;
   Scalars sc;
   fill_scalars(g, prm, prm.initial_damping, sc);
+  if (cont) {
+    sc.need_lin = g->last_need_lin;
+    sc.cost = g->last_cost;
+  }
   if ((s = upload_scalars(g, sc)) != GPO_OK) return s;
   double F0;
-  if ((s = compute_cost(g, &F0)) != GPO_OK) return s;
+  if (cont) F0 = g->last_cost;
+  else if ((s = compute_cost(g, &F0)) != GPO_OK) return s;
   if (!std::isfinite(F0)) return fail(g, GPO_ERR_NUMERIC, "initial cost is not finite (%g)", F0);
   for (int it = 0; it < max_iters; ++it) {
     g->cur_lm_iter = it;
@@ -1378,6 +1421,9 @@ gpo_status gpo_optimize(gpo_graph* g, int32_t max_iters, const gpo_lm_params* pa
   if (g->prof.on) prof_resolve(g);
   g->last_cost = g->h_sc->cost;
   g->cost_valid = true;
+  g->last_need_lin = g->h_sc->need_lin;
+  g->last_solver = prm.solver;
+  g->state_same = true;
   if (out) {
     out->initial_cost = F0;
     out->final_cost = g->h_sc->cost;
@@ -1609,17 +1655,20 @@ static gpo_status debug_linearize_rows(gpo_graph* g, const int64_t* sel, int64_t
 }
 
 gpo_status gpo_debug_linearize(gpo_graph* g, double* r_out, double* J_out) {
+  if (g) g->state_same = false;   // the call overwrites the run's device buffers
   return debug_linearize_rows(g, nullptr, 0, r_out, J_out);
 }
 
 gpo_status gpo_debug_linearize_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
                                      double* J_out) {
+  if (g) g->state_same = false;   // the call overwrites the run's device buffers
   if (!g || n < 0 || (n > 0 && !edge_ids)) return GPO_ERR_ARG;
   return debug_linearize_rows(g, edge_ids, n, r_out, J_out);
 }
 
 gpo_status gpo_debug_autodiff_edges(gpo_graph* g, const int64_t* edge_ids, int64_t n, double* r_out,
                                     double* J_out) {
+  if (g) g->state_same = false;   // the call overwrites the run's device buffers
   if (!g || n < 0 || (n > 0 && !edge_ids)) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);
@@ -1680,6 +1729,7 @@ gpo_status gpo_debug_autodiff_edges(gpo_graph* g, const int64_t* edge_ids, int64
 }
 
 gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* params, double* dx_out, int32_t* pcg_iters) {
+  if (g) g->state_same = false;   // the call overwrites the run's device buffers
   if (!g || !dx_out) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);
@@ -1719,6 +1769,7 @@ gpo_status gpo_debug_step(gpo_graph* g, double lambda, const gpo_lm_params* para
 }
 
 gpo_status gpo_debug_wait_timeout(gpo_graph* g) {
+  if (g) g->state_same = false;   // the call overwrites the run's device buffers
   if (!g) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);
@@ -1748,6 +1799,7 @@ gpo_status gpo_debug_wait_timeout(gpo_graph* g) {
 }
 
 gpo_status gpo_debug_schur(gpo_graph* g, double lambda, const gpo_lm_params* params, double* S_out, double* g_out) {
+  if (g) g->state_same = false;   // the call overwrites the run's device buffers
   if (!g) return GPO_ERR_ARG;
   GPO_CUDA(g, cudaSetDevice(g->desc.device));
   gpo_status s = finalize(g);

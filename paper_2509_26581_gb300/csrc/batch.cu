@@ -278,6 +278,7 @@ gpo_status gpo_optimize_batch(gpo_graph* const* graphs, int32_t n, int32_t max_i
       for (int i = 0; i < n; ++i) {
         graphs[i]->last_cost = sc[i].cost;
         graphs[i]->cost_valid = true;
+        graphs[i]->state_same = false;   // a batched run: the next single run starts afresh
         graphs[i]->hist.clear();
         if (reports) report_from(sc[i], F0[i], &reports[i]);
       }
@@ -473,6 +474,7 @@ gpo_status gpo_server_step(gpo_server* sv, int32_t* n_resident, int32_t* n_queue
         sv->finished[r.ticket] = rep;
         r.g->last_cost = sc[i].cost;
         r.g->cost_valid = true;
+        r.g->state_same = false;   // a served run: the next single run starts afresh
         retire.push_back(r);
       }
       sv->resident.swap(keep);

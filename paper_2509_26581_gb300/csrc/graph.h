@@ -106,6 +106,14 @@ struct gpo_graph {
   std::vector<gpo::IterRecord> hist;
   double last_cost = NAN;
   bool cost_valid = false;
+  // The device state is the one the last gpo_optimize left and no call has changed it
+  // since (gpo_set_initial with the same values keeps it): the next gpo_optimize takes
+  // that run's cost and, if its last step was rejected, its linearisation.
+  bool state_same = false;
+  int last_need_lin = 1;           // the run's need_lin at its end (0: rows at the state)
+  int32_t last_solver = -1;
+  int* d_changed = nullptr;        // device flag: gpo_set_initial changed a value
+  int* h_changed = nullptr;        // pinned
   Profiler prof;
   int cur_lm_iter = -1;
   int cur_pcg_k = 0;

@@ -423,6 +423,42 @@ def test_stepwise_calls_continue_one_lm_run(gpo, prec):
     assert np.array_equal(g1.get_state(p0, p.n_pts, 3), g2.get_state(p0, p.n_pts, 3))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_unchanged_state_continues_and_changed_state_starts_afresh(gpo, prec):
+    """The state read back and written again unchanged (pinned and pageable host
+    buffers) lets the next call continue from the previous run's cost and linearisation;
+    its iterations equal those of a fresh graph set to that state, bit for bit.  A
+    changed value makes the next call evaluate the cost afresh."""
+    torch = pytest.importorskip("torch")
+    p = synth.ba_path(6, 30, 3000, "pareto")
+    prm = dict(pcg_max_iters=60, pcg_tol=1e-6, initial_damping=1e-9)   # early steps rejected
+    g, c0, p0 = gpo.ba_graph(p.cams0, p.pts0, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec)
+    r0 = g.optimize(3, gpo.default_params(**prm))
+    cams = torch.from_numpy(g.get_state(c0, p.n_cams, 9)).pin_memory()
+    pts = g.get_state(p0, p.n_pts, 3)
+    g.set_initial(c0, cams.numpy())
+    g.set_initial(p0, pts)
+    nxt = dict(prm, initial_damping=r0.final_lambda, initial_nu=r0.final_nu)
+    r1 = g.optimize(4, gpo.default_params(**nxt))
+    assert r1.initial_cost == r0.final_cost
+    h1 = g.history()
+    g2, _, _ = gpo.ba_graph(cams.numpy(), pts, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec)
+    r2 = g2.optimize(4, gpo.default_params(**nxt))
+    h2 = g2.history()
+    assert r2.initial_cost == r1.initial_cost and r2.final_cost == r1.final_cost
+    for a, b in zip(h1, h2):
+        assert (a["cost"], a["accepted"], a["pcg_iters"], a["lam"]) == (b["cost"], b["accepted"], b["pcg_iters"], b["lam"])
+    assert np.array_equal(g.get_state(p0, p.n_pts, 3), g2.get_state(p0, p.n_pts, 3))
+    changed = g.get_state(p0, p.n_pts, 3)
+    changed[7, 1] += 0.01
+    cams_now = g.get_state(c0, p.n_cams, 9)
+    g.set_initial(p0, changed)
+    r3 = g.optimize(1, gpo.default_params(**prm))
+    g3, _, _ = gpo.ba_graph(cams_now, changed, p.cam_idx, p.pt_idx, p.obs, p.huber_delta, prec)
+    r4 = g3.optimize(1, gpo.default_params(**prm))
+    assert r3.initial_cost != r1.final_cost and r3.initial_cost == r4.initial_cost
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_mixed_precision_converges_to_fp64_at_300k_edges(gpo, prec):
     """300,000 edges (100 cameras on a ring, 50,000 points seen by 6 cameras each, 1 %
