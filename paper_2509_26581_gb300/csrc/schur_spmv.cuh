@@ -426,10 +426,11 @@ __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-// Index buffers of one chunk in the pipelined kernel's shared memory.
 // Shared memory of the pipelined kernel: the passes' scratch (per-edge terms [VW][LD],
-// point solutions [3][np_max + 1]), the slot cameras' search direction, and two
-// buffers of one chunk's index copies.
+// point solutions [3][np_max + 1]), the slot cameras' search direction, two buffers of
+// one chunk's index copies (packed edge words, slot records), and one buffer of point
+// records (refilled for the next chunk once pass 2 has read it: a second buffer would
+// leave less of the SM's memory to L1).
 struct PipeLayout {
   uint32_t tp, xs, buf;          // offsets
   uint32_t meta, srec, prec;     // offsets inside a buffer
@@ -446,9 +447,9 @@ __host__ __device__ inline PipeLayout pipe_layout(size_t sA, int ch_max, int np_
   L.buf = L.xs + al((uint32_t)(ns_max * Mo::DC * sA));
   L.meta = 0;
   L.srec = al((uint32_t)ch_max * 4u);
-  L.prec = L.srec + al((uint32_t)ns_max * 16u);
-  L.bsize = L.prec + al((uint32_t)np_max * prb);
-  L.size = L.buf + 2 * L.bsize;
+  L.bsize = L.srec + al((uint32_t)ns_max * 16u);
+  L.prec = L.buf + 2 * L.bsize;                // one buffer of point records
+  L.size = L.prec + al((uint32_t)np_max * prb);
   return L;
 }
 
@@ -461,9 +462,10 @@ struct PipeChunk {
 // -- the launch overlaps its predecessor's tail -- simply takes fewer; which CTA sums
 // a chunk does not change any result.  While a chunk's passes run, every thread has
 // already issued its share of the next chunk's index copies (packed edge words, slot
-// records, point records) into the other of two shared-memory buffers, the next
-// chunk's Jacobian tiles are being prefetched into L2, the chunk after that is being
-// taken, and the next chunk's search-direction gather overlaps pass 3.  The sums and
+// records) into the other of two shared-memory buffers and, once pass 2 is done, of its
+// point records, the next chunk's Jacobian tiles are being prefetched into L2, the
+// chunk after that is being taken, and the next chunk's search-direction gather
+// overlaps pass 3.  The sums and
 // their order are those of k_spmv (bit-identical results).  The last CTA to finish
 // puts the counters back to 0.  Requires chunks of at most 1024 edges.
 //
@@ -540,9 +542,6 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     for (int i = threadIdx.x; i < c.nE; i += kThreads) cp_async4(B + PL.meta + 4 * i, meta + i);
     const int4* sr = P->slot_rec + c.s0;
     for (int t = threadIdx.x; t < c.nS; t += kThreads) cp_async16(B + PL.srec + 16 * t, sr + t);
-    const unsigned char* pr = static_cast<const unsigned char*>(P->pt_rec) + (size_t)c.p0 * PRB;
-    const int pieces = (int)(c.nP * (PRB / 16));
-    for (int u = threadIdx.x; u < pieces; u += kThreads) cp_async16(B + PL.prec + 16 * u, pr + 16 * u);
     if (threadIdx.x == 0 && c.nE > 0) {
       const size_t t0 = (size_t)c.e0 >> 5, t1 = (size_t)(c.e0 + c.nE - 1) >> 5;
       prefetch_l2(static_cast<const JT*>(P->J) + t0 * kJTile * NJ,
@@ -550,6 +549,14 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     }
   };
 
+  // a chunk's point records into the one point-record buffer
+  auto issue_prec = [&](const PipeChunk& c, int bound) {
+    if (c.k < 0) return;
+    const DevBA* P = c.q == bound ? &d : ls.probs + c.q;
+    const unsigned char* pr = static_cast<const unsigned char*>(P->pt_rec) + (size_t)c.p0 * PRB;
+    const int pieces = (int)(c.nP * (PRB / 16));
+    for (int u = threadIdx.x; u < pieces; u += kThreads) cp_async16(smem + PL.prec + 16 * u, pr + 16 * u);
+  };
   // the slot cameras' search direction p = (z + beta p_old) / n of a chunk whose slot
   // records are in buffer b
   auto gather = [&](const PipeChunk& c, int b) {
@@ -583,6 +590,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     return;
   }
   issue(ck[0], 0, -1);
+  issue_prec(ck[0], -1);
   cp_async_commit();
   for (int n = 0;; ++n) {
     const int b = n & 1;
@@ -599,8 +607,9 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     issue(cn, b ^ 1, bound_q);
     cp_async_commit();
     // Buffer b: the first chunk's copies are waited for here; a later chunk's landed
-    // during the previous chunk's pass 2 (wait_all, then that pass's barrier), and its
-    // search direction was gathered in the previous pass 3 -- no barrier needed.
+    // at the end of the previous chunk's pass 1 (wait_all, then the barrier before its
+    // pass 2), and its search direction was gathered in the previous pass 3 -- no
+    // barrier needed.  The chunk's point records are waited for at the end of pass 1.
     if (n == 0) {
       cp_async_wait_prev();
       __syncthreads();
@@ -609,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
     unsigned char* B = bufs + b * PL.bsize;
     const uint32_t* meta = reinterpret_cast<const uint32_t*>(B + PL.meta);
     const int4* srec = reinterpret_cast<const int4*>(B + PL.srec);
-    const unsigned char* prec = B + PL.prec;
+    const unsigned char* prec = smem + PL.prec;
     if (n == 0) gather(c, b);    // later chunks' directions were gathered one chunk ahead
     int pos[EPT], slot[EPT], ptl[EPT];
 #pragma unroll
@@ -636,11 +645,11 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
 #pragma unroll
       for (int k = 0; k < 3; ++k) vv[k * LD + i] = a[k];
     }
+    cp_async_wait_all();         // this chunk's point records, the next chunk's indices
     __syncthreads();
     // ---- pass 2: t_p = H_pp^-1 sum_e a_e; meanwhile the last warp's first thread
     // locates the chunk after next (its loads overlap the pass)
     if (threadIdx.x == kThreads - 32) ck[(n + 2) % 3] = plan(cn.k < 0 ? -1 : grab());
-    cp_async_wait_all();         // the next chunk's copies (visible after the barrier)
     for (int j = threadIdx.x; j < c.nP; j += kThreads) {
       const AT* hv = reinterpret_cast<const AT*>(prec + (size_t)j * PRB);
       const int* se = reinterpret_cast<const int*>(prec + (size_t)j * PRB + 6 * sizeof(AT));
@@ -652,6 +661,8 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
       for (int k = 0; k < 3; ++k) tp[k * LP + j] = t[k];
     }
     __syncthreads();
+    issue_prec(cn, bound_q);     // pass 2 was the last reader of the point records
+    cp_async_commit();
     // the next chunk's search direction (its slot records have landed; this chunk's
     // pass 1 was the last reader of xs), overlapping pass 3
     gather(cn, b ^ 1);
