@@ -1099,7 +1099,16 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
   const bool mine = c < d.C && lane < DB;
   const AT y0 = mine ? reinterpret_cast<const AT*>(d.y)[DB * (size_t)c + lane] : (AT)0;
   const AT p0 = mine ? reinterpret_cast<const AT*>(sc->pidx ? d.p : d.p2)[DB * (size_t)c + lane] : (AT)0;
-  if (!sc->active || sc->pcg_done) return;
+  if constexpr (kFused) {
+    // one thread reads the flags for the CTA: camera block 0 may stop the solve (p^T S p
+    // not positive) while other blocks read them, and the CTA's threads must agree
+    __shared__ int stop_s;
+    if (threadIdx.x == 0) stop_s = !sc->active || sc->pcg_done;
+    __syncthreads();
+    if (stop_s) return;
+  } else if (!sc->active || sc->pcg_done) {
+    return;
+  }
   // a restart iteration: y = S x at the current solution, and the residual becomes the
   // true one, g - S x (unit scale), with the direction restarted from z = M r
   const int restart = sc->restart;
@@ -1115,7 +1124,10 @@ __device__ void pcg_update_body(const LaunchSet& ls, const DevBA& d, int cbl, do
     double alpha_d;
     int bad = 0;
     if constexpr (kFused) {
-      if (!restart) {
+      if (sc->pcg_done) {   // stopped by camera block 0 since the check above
+        bad = 1;
+        alpha_d = 0.0;
+      } else if (!restart) {
         bad = !(pAp > 0.0) || !isfinite(pAp);
         alpha_d = bad ? 0.0 : sc->rz / pAp;
         if (cbl == 0) {
