@@ -126,31 +126,33 @@ cudaError_t up(T* dst, const std::vector<T>& src, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
 }
 
-__global__ void k_scatter_rows(double* dst, const double* src, const int32_t* idx, int n, int w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int t = idx ? idx[i] : i;
-  for (int k = 0; k < w; ++k) dst[(size_t)t * w + k] = src[(size_t)i * w + k];
-}
-// dst rows (through idx) = src rows; *changed = 1 if any value's bits differ
+// The row copies between a caller's buffer and the graph's rows (through idx: the
+// graph's row of caller row i) take one value per thread over the flattened rows, so
+// that a warp's accesses to the caller's buffer -- often page-locked host memory read
+// or written in place over the host link -- form one contiguous 256-byte span.  (Two
+// values per thread as 16-byte accesses measured no faster.)
+// dst rows (through idx) = src rows; *changed = 1 if any value's bits differ (one store
+// per CTA at most)
 __global__ void k_assign_rows(double* dst, const double* src, const int32_t* idx, int n, int w, int* changed) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int t = idx ? idx[i] : i;
-  bool diff = false;
-  for (int k = 0; k < w; ++k) {
-    const double v = src[(size_t)i * w + k];
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int diff = 0;
+  if (e < (size_t)n * w) {
+    const int i = (int)(e / (size_t)w), k = (int)(e - (size_t)i * w);
+    const int t = idx ? idx[i] : i;
+    const double v = src[e];
     double* p = dst + (size_t)t * w + k;
-    diff |= __double_as_longlong(*p) != __double_as_longlong(v);
+    diff = __double_as_longlong(*p) != __double_as_longlong(v);
     *p = v;
   }
-  if (diff) *changed = 1;
+  if (__syncthreads_or(diff) && threadIdx.x == 0) *changed = 1;
 }
+// dst rows = src rows through idx (the caller's row i is the graph's row idx[i])
 __global__ void k_gather_rows(double* dst, const double* src, const int32_t* idx, int n, int w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * w) return;
+  const int i = (int)(e / (size_t)w), k = (int)(e - (size_t)i * w);
   const int t = idx ? idx[i] : i;
-  for (int k = 0; k < w; ++k) dst[(size_t)i * w + k] = src[(size_t)t * w + k];
+  dst[e] = src[(size_t)t * w + k];
 }
 
 }  // namespace
@@ -1334,7 +1336,7 @@ gpo_status gpo_set_initial(gpo_graph* g, int64_t first, int64_t n, const double*
   }
   double* dst = is_camera(kind) ? g->dev.cam + loc * w : g->dev.pt;
   const int32_t* idx = is_camera(kind) ? nullptr : g->pt_old2new_d + loc;
-  k_assign_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(dst, src, idx, (int)n, w, g->d_changed);
+  k_assign_rows<<<(int)((n * w + 255) / 256), 256, 0, st>>>(dst, src, idx, (int)n, w, g->d_changed);
   GPO_CUDA(g, cudaGetLastError());
   if (tmp) GPO_CUDA(g, cudaFreeAsync(tmp, st));
   GPO_CUDA(g, cudaMemcpyAsync(g->h_changed, g->d_changed, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1370,7 +1372,7 @@ gpo_status gpo_get_state(gpo_graph* g, int64_t first, int64_t n, double* out, in
     double* dst = on_device ? out : const_cast<double*>(mapped_host(out));
     double* tmp = nullptr;
     if (!dst) GPO_CUDA(g, cudaMallocAsync(&tmp, n * 3 * sizeof(double), st));
-    k_gather_rows<<<(int)((n + 255) / 256), 256, 0, st>>>(dst ? dst : tmp, g->dev.pt, g->pt_old2new_d + loc, (int)n, 3);
+    k_gather_rows<<<(int)((n * 3 + 255) / 256), 256, 0, st>>>(dst ? dst : tmp, g->dev.pt, g->pt_old2new_d + loc, (int)n, 3);
     if (tmp) {
       GPO_CUDA(g, cudaMemcpyAsync(out, tmp, n * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
       GPO_CUDA(g, cudaFreeAsync(tmp, st));

@@ -390,6 +390,25 @@ def test_state_copies_through_pinned_host_memory(gpo):
     part = torch.empty((50, 3), dtype=torch.float64).pin_memory()
     g.get_state(p0 + 20, 50, 3, out=part.numpy())
     assert np.array_equal(part.numpy(), new[20:70])
+    # pinned slices on and off 16-byte boundaries, odd value counts, camera rows
+    new2 = new + 0.02
+    src2 = torch.from_numpy(new2.copy()).pin_memory()
+    g.set_initial(p0 + 10, src2.numpy()[10:111])       # aligned, 303 values
+    g.set_initial(p0 + 111, src2.numpy()[111:140])     # 8 bytes off a 16-byte boundary
+    g.set_initial(p0, new2[:10])
+    g.set_initial(p0 + 140, new2[140:])
+    assert np.array_equal(g.get_state(p0, p.n_pts, 3), new2)
+    big = torch.empty((60, 3), dtype=torch.float64).pin_memory()
+    g.get_state(p0 + 20, 51, 3, out=big.numpy()[:51])   # aligned, 153 values
+    assert np.array_equal(big.numpy()[:51], new2[20:71])
+    g.get_state(p0 + 5, 51, 3, out=big.numpy()[1:52])   # unaligned
+    assert np.array_equal(big.numpy()[1:52], new2[5:56])
+    cams = g.get_state(c0, p.n_cams, 9) + 1e-3
+    cpin = torch.from_numpy(cams.copy()).pin_memory()
+    g.set_initial(c0, cpin.numpy()[:1])                 # aligned, 9 values
+    g.set_initial(c0 + 1, cpin.numpy()[1:4])            # unaligned, 27 values
+    g.set_initial(c0 + 4, cams[4:])
+    assert np.array_equal(g.get_state(c0, p.n_cams, 9), cams)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
