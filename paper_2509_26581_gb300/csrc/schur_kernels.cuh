@@ -1773,10 +1773,10 @@ struct Launch {
     const bool want = ls.spmv_variant == 3 || (ls.spmv_variant == 0 && pr != Prec::F64);
     return want && ls.ch_max <= 1024 && pp_smem(pr, ls) <= 220 * 1024;
   }
-  template <class JT, int EPT>
+  template <class JT, int EPT, int kCH = 0>
   static void pp_e(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     const size_t sm = pp_smem(pr, ls);
-    set_smem(reinterpret_cast<const void*>(k_spmv_pp<Mo, JT, EPT>), sm);
+    set_smem(reinterpret_cast<const void*>(k_spmv_pp<Mo, JT, EPT, kCH>), sm);
     static int n_sm = 0;
     if (!n_sm) {
       int dev = 0;
@@ -1788,16 +1788,18 @@ struct Launch {
     static int occ = 0;
     if (sm != occ_sm) {
       occ = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_pp<Mo, JT, EPT>, kThreads, sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_pp<Mo, JT, EPT, kCH>, kThreads, sm);
       occ_sm = sm;
     }
     const int grid = std::max(1, std::min(ls.n_ch, n_sm * std::max(occ, 1)));
-    launch_pdl(k_spmv_pp<Mo, JT, EPT>, grid, kThreads, sm, st, ls);
+    launch_pdl(k_spmv_pp<Mo, JT, EPT, kCH>, grid, kThreads, sm, st, ls);
   }
+  // the default chunk bound (512 edges) has its own instantiation (compile-time strides)
   template <class JT>
   static void pp_t(const LaunchSet& ls, Prec pr, cudaStream_t st) {
     const int ept = (ls.ch_max + kThreads - 1) / kThreads;
-    if (ept <= 1) pp_e<JT, 1>(ls, pr, st);
+    if (ls.ch_max == 2 * kThreads) pp_e<JT, 2, 2 * kThreads>(ls, pr, st);
+    else if (ept <= 1) pp_e<JT, 1>(ls, pr, st);
     else if (ept <= 2) pp_e<JT, 2>(ls, pr, st);
     else pp_e<JT, 4>(ls, pr, st);
   }

@@ -472,8 +472,11 @@ struct PipeChunk {
 // PipeOcc: resident CTAs per SM the register budget targets.  BF16 rows are re-read
 // from L2 anyway, so more CTAs win; FP32 rows are twice as long and their second read
 // hits L1 only while fewer CTAs share it; FP64 is limited by shared memory.
+//
+// kCH: the launch's chunk bound (ls.ch_max) when known at compile time (0: read at run
+// time), so that the per-edge terms' row stride in shared memory is an immediate offset.
 template <class JT> struct PipeOcc { static constexpr int value = sizeof(JT) == 2 ? 5 : (sizeof(JT) == 4 ? 4 : 2); };
-template <class Mo, class JT, int EPT>
+template <class Mo, class JT, int EPT, int kCH = 0>
 __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(LaunchSet ls) {
   using AT = typename AccOf<JT>::T;
   using Dm = Dims<Mo>;
@@ -484,8 +487,8 @@ __global__ void __launch_bounds__(kThreads, PipeOcc<JT>::value) k_spmv_pp(Launch
   __shared__ DevBA d;
   __shared__ PipeChunk ck[3];
   pdl_trigger();
-  const int LD = ls.ch_max + 1, LP = ls.np_max + 1;
-  const PipeLayout PL = pipe_layout<Mo>(sizeof(AT), ls.ch_max, ls.np_max, ls.ns_max);
+  const int CH = kCH ? kCH : ls.ch_max, LD = CH + 1, LP = ls.np_max + 1;
+  const PipeLayout PL = pipe_layout<Mo>(sizeof(AT), CH, ls.np_max, ls.ns_max);
   AT* vv = reinterpret_cast<AT*>(smem);                 // [VW][LD]; rows 0..2 hold a_e in pass 1
   AT* tp = reinterpret_cast<AT*>(smem + PL.tp);         // [3][LP] point solutions
   AT* xs = reinterpret_cast<AT*>(smem + PL.xs);         // [ns_max][DC] slot cameras' direction
