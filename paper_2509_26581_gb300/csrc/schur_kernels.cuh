@@ -1280,6 +1280,18 @@ __global__ void __launch_bounds__(kCamPerBlock * 32, 4) k_pcg_camera(LaunchSet l
     sr0 = cam_slot_range(d, ls.nprob == 1 ? cb : cb - ls.cb_base[q], blockIdx.x % kApplySplit);
   }
   pdl_wait();
+  if (ls.nprob == 1) {
+    // a stopped solve (the launches of a captured group after the stop): every CTA
+    // returns before the grid barrier.  The flags change only after the barrier, so
+    // every CTA reads the same values.
+    __shared__ int stop;
+    if (threadIdx.x == 0) {
+      const Scalars* sc = ls.probs[0].sc;
+      stop = !sc->active || sc->pcg_done;
+    }
+    __syncthreads();
+    if (stop) return;
+  }
   for (int u = blockIdx.x; u < units; u += G) {
     const int cb = u / kApplySplit, part = u % kApplySplit;
     const int q = ls.nprob == 1 ? 0 : ls.cb_prob[cb];
