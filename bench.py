@@ -177,12 +177,12 @@ NOMINAL_HBM_GBS = 7900.0
 # a hash of the kernel sources they were counted from, so changed kernels report null.
 FP64_SOURCES = ("schur_common.cuh", "schur_kernels.cuh")
 FP64_FLOPS_PER_EDGE = {
-    ("k_linearize", "bf16", "906e1dbd4711"): 18.00,
-    ("k_linearize", "fp64", "906e1dbd4711"): 588.78,
+    ("k_linearize", "bf16", "d06c2de5842b"): 18.00,
+    ("k_linearize", "fp64", "d06c2de5842b"): 588.78,
     # one kernel for every precision (FP64 geometry and cost)
-    ("k_cost", "bf16", "906e1dbd4711"): 65.55,
-    ("k_cost", "fp32", "906e1dbd4711"): 65.55,
-    ("k_cost", "fp64", "906e1dbd4711"): 65.55,
+    ("k_cost", "bf16", "d06c2de5842b"): 65.55,
+    ("k_cost", "fp32", "d06c2de5842b"): 65.55,
+    ("k_cost", "fp64", "d06c2de5842b"): 65.55,
 }
 
 
